@@ -1,0 +1,399 @@
+"""Throughput benchmark: input rows/s to R + sigma of a two-table natural join.
+
+Default workload (N=1): 1,000,000 + 1,000,000 rows, 16 + 16 FP32 features
+N(0,1), int32 keys uniform over 10,000 ids (join of about 1e8 rows x 32
+columns), mixed-precision path.  One step = the whole hot path on one
+instance: key grouping, head/tail of both tables, CholeskyQR2 (two Gram
+passes, two FP64 Cholesky), one-sided Jacobi.  Inputs are resident in HBM
+before the timed region; a 256 MB buffer is rewritten between steps (outside
+the timed events) so that no step starts with a warm L2.
+
+Multi-GPU (torchrun): every rank runs its own independently seeded instance
+(the instances share nothing, so there is no data-path collective); value =
+all ranks' input rows / max-over-ranks time (weak scaling).
+
+--impl reference: the FP64 CPU oracle (materialised join, Householder QR,
+one-sided Jacobi) on bounded samples of the same workload, on host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input rows/s to R+σ on 1 GB300, mixed vs plain FP64 at rel err ≤1e-6; % roofline"
+WORKLOADS = {
+    "c1": "1e6+1e6 rows x 16+16 FP32 N(0,1), int32 keys uniform over 1e4 ids (join ~1e8 x 32)",
+    "c2": "4e6+2e6 rows x 32+32 FP32 U[-1,1], Zipf(1.2) keys over 1e5 ids",
+    "c0": "1000+1000 rows x 4+4 FP64 U[-1,1], 100 keys",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--path", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-materialized", action="store_true")
+    ap.add_argument("--cpu-sample-keys", type=int, default=0)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ clocks ------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- oracle ----
+
+def key_sample(A, B, num_keys):
+    """The rows of both tables whose key is among the first num_keys ids."""
+    keys = np.unique(np.concatenate([A.key, B.key]))[:num_keys]
+    ma, mb = np.isin(A.key, keys), np.isin(B.key, keys)
+    return (A.x[ma], A.key[ma]), (B.x[mb], B.key[mb])
+
+
+def oracle_rows_per_s(A, B, sample_keys):
+    import oracle
+    (ax, ak), (bx, bk) = key_sample(A, B, sample_keys)
+    t0 = time.perf_counter()
+    R = oracle.join_r_materialized(ax, ak, bx, bk)
+    oracle.jacobi_sigma(R)
+    dt = time.perf_counter() - t0
+    rows = ax.shape[0] + bx.shape[0]
+    return rows / dt, dt, rows, oracle.join_rows(ak, bk)
+
+
+def default_sample_keys(cfg):
+    return {"c0": 100, "c1": 150, "c2": 40}.get(cfg, 100)
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from workloads import config
+    A, B = config(args.config)
+    keys = args.cpu_sample_keys or default_sample_keys(args.config)
+    for _ in range(args.warmup):
+        oracle_rows_per_s(A, B, max(1, keys // 10))
+    times, rows = [], 0
+    for _ in range(args.steps):
+        rps, dt, rows, jrows = oracle_rows_per_s(A, B, keys)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = rows / (ms / 1e3)
+    sample = f"rows with one of the first {keys} key ids ({rows} input rows, {jrows} join rows) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "path": "oracle O1 (materialised join, Householder QR, "
+                       "one-sided Jacobi)"},
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------- GPU arm ------
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2503_23385_gb300 as fg
+    from workloads import config
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    A, B = config(args.config, rank=rank)
+    rows = A.m + B.m
+    tA = (torch.from_numpy(A.x).to(dev), torch.from_numpy(A.key).to(dev))
+    tB = (torch.from_numpy(B.x).to(dev), torch.from_numpy(B.key).to(dev))
+    n = A.n + B.n
+
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(fg.NUM_PHASE_EVENTS)]
+    ev_arr = fg.event_array(evs)
+    solver = fg.Solver(tA, tB, path=args.path, phase_events=ev_arr)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            solver(tA, tB, stream=stream)
+        stream.synchronize()
+    status = solver.status(stream)
+    if status != 0:
+        raise fg.FigaroError(status, "warm-up")
+
+    graph = None
+    launches_before = fg.kernel_launches()
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+            solver(tA, tB, stream=stream)
+        launches_per_step = fg.kernel_launches() - launches_before
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+    else:
+        solver(tA, tB, stream=stream)
+        stream.synchronize()
+        launches_per_step = fg.kernel_launches() - launches_before
+
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, phase_ms = [], [[] for _ in range(fg.NUM_PHASE_EVENTS - 1)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.fill_(1)
+                s0.record(stream)
+                if graph is not None:
+                    graph.replay()
+                else:
+                    solver(tA, tB, stream=stream)
+                s1.record(stream)
+                s1.synchronize()
+                step_ms.append(s0.elapsed_time(s1))
+                for i in range(fg.NUM_PHASE_EVENTS - 1):
+                    phase_ms[i].append(evs[i].elapsed_time(evs[i + 1]))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    clocks = clk.summary()
+    status = solver.status(stream)
+    if status != 0:
+        raise fg.FigaroError(status, "timed steps")
+
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * rows / (ms_per_step / 1e3)
+    phases = {name: statistics.mean(v) for name, v in zip(fg.PHASES, phase_ms)}
+
+    # ---- roofline of the head/tail kernel of table A (one launch) --------
+    hbm, peak_kind = measured_peaks()
+    s = 4 if args.path == "mixed" else 8
+    ein = A.x.itemsize
+    ht_bytes = A.m * (4 + 4 + A.n * ein + A.n * s)
+    ht_ms = phases["head_tail_a"]
+    achieved = ht_bytes / (ht_ms / 1e3) / 1e9
+    roofline = {"kernel": "head_tail_kernel (table A)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "bytes_per_launch": ht_bytes, "peak_source": peak_kind}
+
+    # ---- end to end through the C ABI with host buffers -----------------
+    e2e = None
+    try:
+        hA = (torch.from_numpy(A.x).pin_memory(), torch.from_numpy(A.key).pin_memory())
+        hB = (torch.from_numpy(B.x).pin_memory(), torch.from_numpy(B.key).pin_memory())
+        Rh = torch.zeros((n, n), dtype=torch.float64).pin_memory()
+        sh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        wsh = torch.empty(fg.host_workspace_size(hA, hB, path=args.path), dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            fg.join_qr_svd_host(hA, hB, Rh, sh, wsh, stream=stream, path=args.path)
+        stream.synchronize()
+        e_ms = []
+        for _ in range(max(3, min(args.steps, 10))):
+            s0.record(stream)
+            fg.join_qr_svd_host(hA, hB, Rh, sh, wsh, stream=stream, path=args.path)
+            s1.record(stream)
+            s1.synchronize()
+            e_ms.append(s0.elapsed_time(s1))
+        st = fg.get_status(wsh, stream)
+        if st != 0:
+            raise fg.FigaroError(st, "e2e")
+        em = statistics.mean(e_ms)
+        h2d = A.x.nbytes + A.key.nbytes + B.x.nbytes + B.key.nbytes
+        e2e = {"value": world * rows / (em / 1e3), "unit": "rows/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": n * n * 8 + n * 8, "ms_per_step": em}
+        del wsh
+    except Exception as exc:  # reported, not hidden
+        e2e = {"error": repr(exc)}
+
+    # ---- the plain FP64 path on the same instance ------------------------
+    fp64 = None
+    if args.path == "mixed" and args.fp64_steps > 0:
+        try:
+            s64 = fg.Solver(tA, tB, path="fp64")
+            s64(tA, tB, stream=stream)
+            stream.synchronize()
+            f_ms = []
+            for _ in range(args.fp64_steps):
+                flush.fill_(1)
+                s0.record(stream)
+                s64(tA, tB, stream=stream)
+                s1.record(stream)
+                s1.synchronize()
+                f_ms.append(s0.elapsed_time(s1))
+            fm = statistics.mean(f_ms)
+            d = np.linalg.norm((solver.R - s64.R).cpu().numpy()) / np.linalg.norm(s64.R.cpu().numpy())
+            ds = np.linalg.norm((solver.sigma - s64.sigma).cpu().numpy()) / np.linalg.norm(s64.sigma.cpu().numpy())
+            fp64 = {"value": world * rows / (fm / 1e3), "unit": "rows/s", "ms_per_step": fm,
+                    "mixed_vs_fp64_rel_err_R": float(d), "mixed_vs_fp64_rel_err_sigma": float(ds)}
+            del s64
+        except Exception as exc:
+            fp64 = {"error": repr(exc)}
+
+    # ---- materialised-join QR baseline (torch / cuSOLVER on J) ----------
+    mat = None
+    if not args.no_materialized and rank == 0:
+        mat = materialized_baseline(torch, A, B, dev, stream)
+
+    # ---- oracle on host cores ------------------------------------------
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        keys = args.cpu_sample_keys or default_sample_keys(args.config)
+        rps, dt, srows, jrows = oracle_rows_per_s(A, B, keys)
+        cpu = {"value": rps, "unit": "rows/s", "cores": 1, "kind": "oracle",
+               "sample": f"rows with one of the first {keys} key ids: {srows} input rows, {jrows} join rows, "
+                         f"{dt:.1f} s (O1: materialised join, Householder QR, one-sided Jacobi)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.path == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.config], "path": args.path, "rows_per_gpu": rows,
+                           "graph": graph is not None,
+                           "l2": "inputs 136 MB + ~300 MB workspace exceed L2; 256 MB flush between steps"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+                "clocks": clocks, "phases_ms": phases, "fp64_path": fp64, "materialized_baseline": mat}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def materialized_baseline(torch, A, B, dev, stream):
+    """Builds J on the device with torch ops and times torch.linalg.qr (R only)
+    on it: the paper's comparison (Householder QR of the materialised join).
+    Not the product path; reported where J fits in memory."""
+    try:
+        ka, kb = torch.from_numpy(A.key).to(dev).long(), torch.from_numpy(B.key).to(dev).long()
+        pa, pb = torch.argsort(ka, stable=True), torch.argsort(kb, stable=True)
+        ua, ca = torch.unique_consecutive(ka[pa], return_counts=True)
+        ub, cb = torch.unique_consecutive(kb[pb], return_counts=True)
+        common, ia, ib = np.intersect1d(ua.cpu().numpy(), ub.cpu().numpy(), return_indices=True)
+        ca, cb = ca.cpu().numpy()[ia], cb.cpu().numpy()[ib]
+        join_rows = int(np.sum(ca.astype(np.int64) * cb))
+        n = A.n + B.n
+        bytes_needed = join_rows * n * 4
+        free, _ = torch.cuda.mem_get_info(dev)
+        if bytes_needed * 2.5 > free:
+            return {"skipped": f"J needs {bytes_needed / 1e9:.1f} GB (FP32); {free / 1e9:.1f} GB free"}
+        xa, xb = torch.from_numpy(A.x).to(dev).float()[pa], torch.from_numpy(B.x).to(dev).float()[pb]
+        offa = np.concatenate([[0], np.cumsum(ca)])
+        offb = np.concatenate([[0], np.cumsum(cb)])
+        J = torch.empty((join_rows, n), dtype=torch.float32, device=dev)
+        r = 0
+        for g in range(len(common)):
+            a = xa[offa[g]:offa[g + 1]]
+            b = xb[offb[g]:offb[g + 1]]
+            k = a.shape[0] * b.shape[0]
+            J[r:r + k, :A.n] = a.repeat_interleave(b.shape[0], dim=0)
+            J[r:r + k, A.n:] = b.repeat(a.shape[0], 1)
+            r += k
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.linalg.qr(J[:4096], mode="r")
+        t0.record()
+        R = torch.linalg.qr(J, mode="r")[0]
+        torch.linalg.svdvals(R)
+        t1.record()
+        t1.synchronize()
+        ms = t0.elapsed_time(t1)
+        del J
+        return {"value": (A.m + B.m) / (ms / 1e3), "unit": "rows/s", "ms": ms, "join_rows": join_rows,
+                "dtype": "f32", "what": "torch.linalg.qr(J, mode='r') + svdvals(R) on the materialised join"}
+    except Exception as exc:
+        return {"error": repr(exc)}
+
+
+if __name__ == "__main__":
+    main()

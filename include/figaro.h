@@ -1,0 +1,221 @@
+/*
+ * figaro.h -- C ABI of the GB300 (sm_103a) Figaro two-table library.
+ *
+ * Computes, for two tables A (m1 x n1, int32 key per row) and B (m2 x n2,
+ * int32 key per row), the upper-triangular R of QR(J) and the singular values
+ * of J, where J is the natural (inner) join of A and B: one row [A_i, B_j] for
+ * every pair of rows with equal keys ("Figaro on GPUs: Two Tables",
+ * arXiv 2503.23385, Section 1: the Cartesian product, the QR head / QR tail
+ * operators and Claim 1; Section 3: singular values of J as those of R).
+ * J is never formed.  The path is: stable radix sort of each table by key,
+ * runs and matched keys, the per-key-group QR head and QR tail rows of
+ * Claim 1 (weighted by sqrt(m2g) on A's side and sqrt(m1g) on B's side), a
+ * CholeskyQR2 of that reduced matrix, and a one-sided Jacobi SVD of R.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Layout: features are row-major with a leading dimension `ld` >= n
+ *    (elements).  R is n x n row-major (n = n1 + n2) with leading dimension
+ *    `ldr` >= n, columns ordered [A's n1 | B's n2] as in Section 1, lower
+ *    triangle written as zeros, rows scaled so the diagonal is >= 0.
+ *    sigma has n entries, descending; rank-deficient joins give zeros.
+ *  - Memory: every pointer is a device pointer unless the table's `memory`
+ *    field (inputs) or FIGARO_FLAG_HOST_OUTPUT (outputs) says host.  Host
+ *    inputs are staged through the workspace with stream-ordered copies;
+ *    pinned host memory keeps those copies asynchronous.
+ *  - Ownership: the caller owns inputs, outputs and the workspace.  The
+ *    library never allocates device memory in these calls and never frees
+ *    caller memory.  Query the workspace size first.
+ *  - Ordering: calls enqueue work on `stream` (a cudaStream_t; NULL = the
+ *    legacy default stream) and return without waiting.  Argument errors are
+ *    returned at once.  Errors found on the device (numerical breakdown, a
+ *    bounded wait that ran out) are recorded in the workspace; read them with
+ *    figaro_get_status() after the stream has reached that point.
+ *  - Limits: m1, m2 < 2^31; 1 <= n1, n2 and n1 + n2 <= 128 (larger widths
+ *    return FIGARO_ERR_UNSUPPORTED); both tables have the same dtype.
+ *  - Workspace must be 256-byte aligned.  Concurrent calls need distinct
+ *    workspaces.
+ */
+#ifndef FIGARO_H_
+#define FIGARO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FIGARO_API __attribute__((visibility("default")))
+#else
+#define FIGARO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum figaro_status {
+  FIGARO_OK = 0,
+  FIGARO_ERR_INVALID_ARG = 1,          /* null pointer, bad size, bad enum, mismatched dtypes */
+  FIGARO_ERR_WORKSPACE_TOO_SMALL = 2,  /* ws_bytes below figaro_workspace_size() */
+  FIGARO_ERR_CUDA = 3,                 /* a CUDA launch or copy failed */
+  FIGARO_ERR_NOT_SPD = 4,              /* Cholesky met a non-finite pivot (NaN/Inf in the input) */
+  FIGARO_ERR_NO_CONVERGENCE = 5,       /* Jacobi reached max sweeps; sigma is still written */
+  FIGARO_ERR_DEVICE_TIMEOUT = 6,       /* a bounded device-side wait gave up; results are invalid */
+  FIGARO_ERR_UNSUPPORTED = 7           /* width or size outside the limits above */
+} figaro_status;
+
+typedef enum figaro_dtype { FIGARO_F32 = 0, FIGARO_F64 = 1 } figaro_dtype;
+
+/* FIGARO_PATH_FP64: every step in FP64 (the plain reference form).
+ * FIGARO_PATH_MIXED: head/tail in FP32 with compensated sums, Gram products
+ * in FP32 with FP64 cross-block accumulation, CholeskyQR2 correction,
+ * Cholesky and the final Jacobi values in FP64.                             */
+typedef enum figaro_path { FIGARO_PATH_FP64 = 0, FIGARO_PATH_MIXED = 1 } figaro_path;
+
+typedef enum figaro_memory { FIGARO_MEM_DEVICE = 0, FIGARO_MEM_HOST = 1 } figaro_memory;
+
+/* Gram engine for the reduced-matrix products.                               */
+typedef enum figaro_gram_engine {
+  FIGARO_GRAM_AUTO = 0,     /* chosen per width by the library */
+  FIGARO_GRAM_SIMT = 1,     /* CUDA-core FMA */
+  FIGARO_GRAM_TCGEN05 = 2   /* 5th-generation tensor cores (mixed path only) */
+} figaro_gram_engine;
+
+enum {
+  FIGARO_FLAG_HOST_OUTPUT = 1,     /* R / sigma pointers are host memory */
+  /* Fault injection for tests: the first chunk of each table's head/tail
+   * step withholds its look-back status, so the next chunk's bounded wait
+   * runs out and the call records FIGARO_ERR_DEVICE_TIMEOUT. */
+  FIGARO_FLAG_TEST_WITHHOLD = 1 << 8
+};
+
+typedef struct figaro_table {
+  const void* x;       /* features: m rows, row-major, leading dimension ld */
+  const int32_t* key;  /* m join keys */
+  int64_t m;           /* rows (0 allowed) */
+  int64_t ld;          /* leading dimension in elements, >= n */
+  int32_t n;           /* feature columns, >= 1 */
+  int32_t dtype;       /* figaro_dtype */
+  int32_t memory;      /* figaro_memory of x and key */
+  int32_t reserved;
+} figaro_table;
+
+/* Phase boundaries recorded into figaro_options.phase_events (tracing):
+ * start, grouping done, head/tail A done, head/tail B done, Gram pass 1 done,
+ * Cholesky 1 done, Gram pass 2 done, Cholesky 2 done, Jacobi done.         */
+#define FIGARO_NUM_PHASE_EVENTS 9
+
+typedef struct figaro_options {
+  int32_t path;               /* figaro_path */
+  int32_t gram_engine;        /* figaro_gram_engine */
+  int32_t max_jacobi_sweeps;  /* 0 = library default (40) */
+  int32_t flags;              /* FIGARO_FLAG_* */
+  int64_t spin_limit;         /* polls per bounded device wait; 0 = default (about a second) */
+  double rank_tol;            /* relative pivot below which a column counts as dependent; 0 = default */
+  void* const* phase_events;  /* NULL, or FIGARO_NUM_PHASE_EVENTS cudaEvent_t recorded on the stream
+                                 at the phase boundaries (single-instance calls only) */
+} figaro_options;
+
+/* Fills `opt` with the defaults (mixed path, automatic Gram engine). */
+FIGARO_API figaro_status figaro_default_options(figaro_options* opt);
+
+/* Bytes of workspace one call needs for these shapes and options. */
+FIGARO_API figaro_status figaro_workspace_size(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                                    size_t* bytes);
+
+/*
+ * figaro_join_group -- the key grouping of both tables (Section 2 assumes
+ * inputs sorted by the join attribute; this call produces that order).
+ * Per table, into caller device buffers (m = that table's rows):
+ *   perm[m]          input row of the i-th row in key order (stable: equal
+ *                    keys keep their input order)
+ *   sorted_key[m]    key of the i-th row in key order
+ *   run_key[m]       distinct keys ascending (first num_runs entries valid)
+ *   run_offset[m+1]  start of each run in key order, run_offset[num_runs] = m
+ *   other_count[m]   rows with the same key in the other table (0 = the key
+ *                    has no partner and contributes no join rows)
+ *   num_runs[1]      (int64) number of runs
+ * num_groups (device int64[1], may be NULL): keys present in both tables.
+ * All outputs are exact integers (bit-exact against a stable sort).
+ */
+typedef struct figaro_grouping {
+  int32_t* perm;
+  int32_t* sorted_key;
+  int32_t* run_key;
+  int32_t* run_offset;
+  int32_t* other_count;
+  int64_t* num_runs;
+} figaro_grouping;
+
+FIGARO_API figaro_status figaro_join_group(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                                const figaro_grouping* outA, const figaro_grouping* outB, int64_t* num_groups,
+                                void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * figaro_join_head_tail -- the reduced matrix of Claim 1 (Section 1), one
+ * slot per row so that no compaction pass is needed:
+ *   head   [m1 x (n1+n2)]  row u (u < number of runs of A, in key order):
+ *                          [sqrt(m2g) H(A_g), sqrt(m1g) H(B_g)] for the key
+ *                          group g of that run, zero if the key has no
+ *                          partner in B.
+ *   tail_a [m1 x n1]       row i (i-th row of A in key order, local index
+ *                          j >= 1 inside its run): sqrt(m2g) T(A_g)_j; zero
+ *                          for the first row of each run and for runs
+ *                          without a partner.
+ *   tail_b [m2 x n2]       the same for B with weight sqrt(m1g).
+ * H(X) = (1/sqrt m) sum_k X_k;  T(X)_j = (sqrt(j) X_{j+1} - S_j/sqrt(j)) /
+ * sqrt(j+1) with S_j the sum of the first j rows.  Element type: double for
+ * FIGARO_PATH_FP64, float for FIGARO_PATH_MIXED.  Dense, leading dimension
+ * equal to the width.  The Gram matrix of all these rows equals J^T J.
+ */
+FIGARO_API figaro_status figaro_join_head_tail(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                                    void* head, void* tail_a, void* tail_b, void* ws, size_t ws_bytes,
+                                    void* stream);
+
+/*
+ * figaro_join_qr_r -- R of QR(J) (Section 1: R with R^T R = J^T J), by a
+ * CholeskyQR2 of the reduced matrix.  Dependent columns (a short or
+ * rank-deficient join) get zero rows in R.
+ */
+FIGARO_API figaro_status figaro_join_qr_r(const figaro_table* A, const figaro_table* B, const figaro_options* opt, double* R,
+                               int64_t ldr, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * figaro_join_singular_values -- sigma(J) = sigma(R) (Section 3), with R
+ * computed as in figaro_join_qr_r and written to R_out when R_out != NULL.
+ */
+FIGARO_API figaro_status figaro_join_singular_values(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                                          double* sigma, double* R_out, int64_t ldr, void* ws, size_t ws_bytes,
+                                          void* stream);
+
+/*
+ * Batched form: `count` independent instances (A[i], B[i]) with their own
+ * shapes, each writing R[i] (n_i x n_i, leading dimension n_i) and sigma[i].
+ * R and sigma are host arrays of `count` device pointers (entries may be
+ * NULL to skip an output).  One workspace covers the whole batch.
+ */
+FIGARO_API figaro_status figaro_batch_workspace_size(int32_t count, const figaro_table* A, const figaro_table* B,
+                                          const figaro_options* opt, size_t* bytes);
+
+FIGARO_API figaro_status figaro_batch_join(int32_t count, const figaro_table* A, const figaro_table* B,
+                                const figaro_options* opt, double* const* R, double* const* sigma, void* ws,
+                                size_t ws_bytes, void* stream);
+
+/* Waits for `stream`, then returns the device-side status the last call
+ * using workspace `ws` recorded (FIGARO_OK when nothing went wrong).        */
+FIGARO_API figaro_status figaro_get_status(const void* ws, void* stream);
+
+/* Static English text for a status code. */
+FIGARO_API const char* figaro_status_string(figaro_status status);
+
+/* Library version, e.g. 100 for 0.1.0 (major * 10000 + minor * 100 + patch). */
+FIGARO_API int32_t figaro_version(void);
+
+/* Number of kernels this library has launched in this process so far
+ * (host-side count; a replayed CUDA graph does not go through it). */
+FIGARO_API int64_t figaro_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIGARO_H_ */

@@ -1,0 +1,484 @@
+// C ABI entry points (include/figaro.h): argument checks, workspace layout
+// and the stream-ordered pipeline of one instance:
+//   key grouping -> head/tail of A and B -> Gram pass 1 -> Cholesky 1 ->
+//   Gram pass 2 -> Cholesky 2 and R = R2 R1 -> one-sided Jacobi.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/figaro.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace figaro {
+
+int ht_column_groups(int n, int V);
+void gram_geometry(int kout, int* kpad, int* tiles, int* slices);
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+struct Bump {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~static_cast<size_t>(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * (count > 0 ? count : 1);
+    return p;
+  }
+};
+
+int sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2, int n2, int in_f64, int mixed,
+                   int stage_a, int stage_b, int num_sms) {
+  Bump b{static_cast<char*>(const_cast<void*>(ws_base))};
+  p.n1 = n1;
+  p.n2 = n2;
+  p.n = n1 + n2;
+  p.mixed = mixed;
+  p.num_sms = num_sms;
+  const size_t ec = mixed ? 4 : 8;   // compute element
+  const size_t ei = in_f64 ? 8 : 4;  // input element
+  p.hdr = b.take<DevHeader>(1);
+  int64_t ms[2] = {m1, m2};
+  int ns[2] = {n1, n2};
+  int stage[2] = {stage_a, stage_b};
+  for (int t = 0; t < 2; ++t) {
+    TableWork& T = p.t[t];
+    const int64_t m = ms[t];
+    const int n = ns[t];
+    T.m = m;
+    T.n = n;
+    T.in_f64 = in_f64;
+    if (stage[t]) {
+      T.x = b.take<char>(static_cast<size_t>(m) * n * ei);
+      T.key = b.take<int32_t>(static_cast<size_t>(m));
+      T.ld = n;
+    }
+    T.tiles = static_cast<int>(ceil_div(m, kSortTile));
+    for (int k = 0; k < 2; ++k) {
+      T.kb[k] = b.take<uint32_t>(static_cast<size_t>(m));
+      T.vb[k] = b.take<int32_t>(static_cast<size_t>(m));
+    }
+    T.hist = b.take<uint32_t>(static_cast<size_t>(kRadixBins) * (T.tiles > 0 ? T.tiles : 1));
+    T.rle_cnt = b.take<uint32_t>(static_cast<size_t>(T.tiles > 0 ? T.tiles : 1));
+    T.perm = b.take<int32_t>(static_cast<size_t>(m));
+    T.sorted_key = b.take<int32_t>(static_cast<size_t>(m));
+    T.seg = b.take<int32_t>(static_cast<size_t>(m));
+    T.run_key = b.take<int32_t>(static_cast<size_t>(m));
+    T.run_off = b.take<int32_t>(static_cast<size_t>(m) + 1);
+    T.other = b.take<int32_t>(static_cast<size_t>(m));
+    T.hdslot = b.take<int32_t>(static_cast<size_t>(m));
+    T.tail = b.take<char>(static_cast<size_t>(m) * n * ec);
+    // chunks sized for the narrowest vector width (most chunks)
+    const int cg = ht_column_groups(n, 1);
+    const int rows_min = (kHtThreads / cg) * kHtRowsPerThread;
+    T.chunks = static_cast<int>(ceil_div(m, rows_min));
+    T.chunk_rows = rows_min;
+    T.chunk_status = b.take<uint32_t>(static_cast<size_t>(T.chunks));
+    T.chunk_agg = b.take<double>(static_cast<size_t>(T.chunks) * n);
+    T.chunk_inc = b.take<double>(static_cast<size_t>(T.chunks) * n);
+  }
+  const int n = p.n;
+  p.head = b.take<char>(static_cast<size_t>(m1 > 0 ? m1 : 1) * n * ec);
+  // Gram partials, sized for the larger of the two passes
+  for (int blk = 0; blk < 3; ++blk) {
+    const int64_t rows = blk == 0 ? m1 : (blk == 1 ? m1 : m2);
+    int64_t grid = ceil_div(rows, kGramTileRows);
+    if (grid > 2 * num_sms) grid = 2 * num_sms;
+    if (grid < 1) grid = 1;
+    p.ggrid[blk] = static_cast<int>(grid);
+    size_t most = 0;
+    int kouts[2] = {blk == 0 ? n : (blk == 1 ? n1 : n2), blk == 2 ? n2 : n};
+    for (int q = 0; q < 2; ++q) {
+      int kpad, tiles, slices;
+      gram_geometry(kouts[q], &kpad, &tiles, &slices);
+      size_t sz = static_cast<size_t>(grid) * slices * kouts[q] * kouts[q];
+      if (sz > most) most = sz;
+    }
+    p.gslices[blk] = 0;
+    p.gpart[blk] = b.take<double>(most);
+  }
+  const size_t nn = static_cast<size_t>(n) * n;
+  p.G1 = b.take<double>(nn);
+  p.G2 = b.take<double>(nn);
+  p.R1 = b.take<double>(nn);
+  p.W = b.take<double>(nn);
+  p.Wf = b.take<float>(nn);
+  p.R = b.take<double>(nn);
+  p.sigma = b.take<double>(static_cast<size_t>(n));
+  p.active = b.take<int32_t>(static_cast<size_t>(n));
+  return (b.off + 255) & ~static_cast<size_t>(255);
+}
+
+namespace {
+
+struct Call {
+  Plan p;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev[FIGARO_NUM_PHASE_EVENTS] = {};
+  bool events = false;
+  cudaError_t mark(int i) {
+    if (!events) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    // inside a stream capture the record must become an event node of the graph
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev[i], s);
+  }
+};
+
+figaro_status check_table(const figaro_table* T) {
+  if (!T) return FIGARO_ERR_INVALID_ARG;
+  if (T->m < 0 || T->m >= (int64_t{1} << 31)) return T->m < 0 ? FIGARO_ERR_INVALID_ARG : FIGARO_ERR_UNSUPPORTED;
+  if (T->n < 1) return FIGARO_ERR_INVALID_ARG;
+  if (T->ld < T->n) return FIGARO_ERR_INVALID_ARG;
+  if (T->dtype != FIGARO_F32 && T->dtype != FIGARO_F64) return FIGARO_ERR_INVALID_ARG;
+  if (T->memory != FIGARO_MEM_DEVICE && T->memory != FIGARO_MEM_HOST) return FIGARO_ERR_INVALID_ARG;
+  if (T->m > 0 && (!T->x || !T->key)) return FIGARO_ERR_INVALID_ARG;
+  return FIGARO_OK;
+}
+
+figaro_status check_pair(const figaro_table* A, const figaro_table* B, const figaro_options* o) {
+  figaro_status st = check_table(A);
+  if (st != FIGARO_OK) return st;
+  st = check_table(B);
+  if (st != FIGARO_OK) return st;
+  if (A->dtype != B->dtype) return FIGARO_ERR_INVALID_ARG;
+  if (o && o->path != FIGARO_PATH_FP64 && o->path != FIGARO_PATH_MIXED) return FIGARO_ERR_INVALID_ARG;
+  if (o && (o->gram_engine < 0 || o->gram_engine > 2)) return FIGARO_ERR_INVALID_ARG;
+  if (o && (o->max_jacobi_sweeps < 0 || o->spin_limit < 0 || !(o->rank_tol >= 0.0) || o->rank_tol >= 1.0))
+    return FIGARO_ERR_INVALID_ARG;
+  if (static_cast<int64_t>(A->n) + B->n > kMaxWidth) return FIGARO_ERR_UNSUPPORTED;
+  return FIGARO_OK;
+}
+
+figaro_options resolve(const figaro_options* o) {
+  figaro_options r;
+  figaro_default_options(&r);
+  if (o) r = *o;
+  if (r.max_jacobi_sweeps == 0) r.max_jacobi_sweeps = 40;
+  if (r.spin_limit == 0) r.spin_limit = 20000000;  // ~1-2 s of 64 ns naps
+  return r;
+}
+
+// The device that owns the workspace becomes current for this thread.
+figaro_status bind_device(const void* ws) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ws) != cudaSuccess) {
+    cudaGetLastError();
+    return FIGARO_ERR_INVALID_ARG;
+  }
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return FIGARO_ERR_INVALID_ARG;
+  if (cudaSetDevice(attr.device) != cudaSuccess) return FIGARO_ERR_CUDA;
+  return FIGARO_OK;
+}
+
+figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, const figaro_options* opt, void* ws,
+                      size_t ws_bytes, void* stream) {
+  figaro_status st = check_pair(A, B, opt);
+  if (st != FIGARO_OK) return st;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return FIGARO_ERR_INVALID_ARG;
+  st = bind_device(ws);
+  if (st != FIGARO_OK) return st;
+  figaro_options o = resolve(opt);
+  const int in_f64 = A->dtype == FIGARO_F64;
+  const int mixed = o.path == FIGARO_PATH_MIXED;
+  const int sa = A->memory == FIGARO_MEM_HOST, sb = B->memory == FIGARO_MEM_HOST;
+  size_t need = plan_layout(c.p, ws, A->m, A->n, B->m, B->n, in_f64, mixed, sa, sb, sm_count());
+  if (ws_bytes < need) return FIGARO_ERR_WORKSPACE_TOO_SMALL;
+  c.p.gram_engine = o.gram_engine;
+  c.p.max_sweeps = o.max_jacobi_sweeps;
+  c.p.spin_limit = o.spin_limit;
+  c.p.rank_tol = o.rank_tol;
+  c.p.withhold = (o.flags & FIGARO_FLAG_TEST_WITHHOLD) ? 1 : 0;
+  c.s = static_cast<cudaStream_t>(stream);
+  if (o.phase_events) {
+    c.events = true;
+    for (int i = 0; i < FIGARO_NUM_PHASE_EVENTS; ++i) {
+      c.ev[i] = static_cast<cudaEvent_t>(o.phase_events[i]);
+      if (!c.ev[i]) return FIGARO_ERR_INVALID_ARG;
+    }
+  }
+  const figaro_table* tabs[2] = {A, B};
+  const size_t ei = in_f64 ? 8 : 4;
+  for (int t = 0; t < 2; ++t) {
+    TableWork& T = c.p.t[t];
+    const figaro_table* src = tabs[t];
+    if (src->memory == FIGARO_MEM_HOST) {
+      if (src->m > 0) {
+        cudaError_t e1 = cudaMemcpy2DAsync(const_cast<void*>(T.x), static_cast<size_t>(src->n) * ei, src->x,
+                                           static_cast<size_t>(src->ld) * ei, static_cast<size_t>(src->n) * ei,
+                                           static_cast<size_t>(src->m), cudaMemcpyHostToDevice, c.s);
+        cudaError_t e2 = cudaMemcpyAsync(const_cast<int32_t*>(T.key), src->key, sizeof(int32_t) * src->m,
+                                         cudaMemcpyHostToDevice, c.s);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) return FIGARO_ERR_CUDA;
+      }
+    } else {
+      T.x = src->x;
+      T.key = src->key;
+      T.ld = src->ld;
+    }
+  }
+  return FIGARO_OK;
+}
+
+#define FIGARO_TRY(expr)                                   \
+  do {                                                     \
+    cudaError_t e_ = (expr);                               \
+    if (e_ != cudaSuccess) return FIGARO_ERR_CUDA;         \
+  } while (0)
+
+figaro_status run_grouping(Call& c) {
+  FIGARO_TRY(c.mark(0));
+  FIGARO_TRY(launch_reset(c.p, c.s));
+  FIGARO_TRY(launch_grouping(c.p, c.s));
+  FIGARO_TRY(c.mark(1));
+  return FIGARO_OK;
+}
+
+figaro_status run_factor(Call& c, double* R_dev, int64_t ldr) {
+  FIGARO_TRY(launch_head_tail(c.p, 0, c.s));
+  FIGARO_TRY(c.mark(2));
+  FIGARO_TRY(launch_head_tail(c.p, 1, c.s));
+  FIGARO_TRY(c.mark(3));
+  FIGARO_TRY(launch_gram_pass(c.p, 1, c.s));
+  FIGARO_TRY(c.mark(4));
+  FIGARO_TRY(launch_chol_first(c.p, c.s));
+  FIGARO_TRY(c.mark(5));
+  FIGARO_TRY(launch_gram_pass(c.p, 2, c.s));
+  FIGARO_TRY(c.mark(6));
+  FIGARO_TRY(launch_chol_second(c.p, R_dev, ldr, c.s));
+  FIGARO_TRY(c.mark(7));
+  return FIGARO_OK;
+}
+
+figaro_status run_qr_svd(Call& c, double* R_out, int64_t ldr, double* sigma, int host_out) {
+  figaro_status st = run_grouping(c);
+  if (st != FIGARO_OK) return st;
+  const int n = c.p.n;
+  st = run_factor(c, host_out ? nullptr : R_out, ldr);
+  if (st != FIGARO_OK) return st;
+  if (sigma) FIGARO_TRY(launch_jacobi(c.p, c.p.R, n, host_out ? c.p.sigma : sigma, c.s));
+  FIGARO_TRY(c.mark(8));
+  if (host_out) {
+    if (R_out)
+      FIGARO_TRY(cudaMemcpy2DAsync(R_out, sizeof(double) * ldr, c.p.R, sizeof(double) * n, sizeof(double) * n, n,
+                                   cudaMemcpyDeviceToHost, c.s));
+    if (sigma) FIGARO_TRY(cudaMemcpyAsync(sigma, c.p.sigma, sizeof(double) * n, cudaMemcpyDeviceToHost, c.s));
+  }
+  return FIGARO_OK;
+}
+
+}  // namespace
+}  // namespace figaro
+
+using namespace figaro;
+
+extern "C" {
+
+figaro_status figaro_default_options(figaro_options* opt) {
+  if (!opt) return FIGARO_ERR_INVALID_ARG;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->path = FIGARO_PATH_MIXED;
+  opt->gram_engine = FIGARO_GRAM_AUTO;
+  return FIGARO_OK;
+}
+
+figaro_status figaro_workspace_size(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                                    size_t* bytes) {
+  if (!bytes) return FIGARO_ERR_INVALID_ARG;
+  figaro_status st = check_pair(A, B, opt);
+  if (st != FIGARO_OK) return st;
+  figaro_options o = resolve(opt);
+  Plan p;
+  *bytes = plan_layout(p, nullptr, A->m, A->n, B->m, B->n, A->dtype == FIGARO_F64, o.path == FIGARO_PATH_MIXED,
+                       A->memory == FIGARO_MEM_HOST, B->memory == FIGARO_MEM_HOST, sm_count());
+  return FIGARO_OK;
+}
+
+figaro_status figaro_join_group(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                                const figaro_grouping* outA, const figaro_grouping* outB, int64_t* num_groups,
+                                void* ws, size_t ws_bytes, void* stream) {
+  if (!outA || !outB) return FIGARO_ERR_INVALID_ARG;
+  const figaro_grouping* outs[2] = {outA, outB};
+  const int64_t ms[2] = {A ? A->m : 0, B ? B->m : 0};
+  for (int t = 0; t < 2; ++t) {
+    const figaro_grouping* g = outs[t];
+    if (!g->num_runs) return FIGARO_ERR_INVALID_ARG;
+    if (ms[t] > 0 && (!g->perm || !g->sorted_key || !g->run_key || !g->run_offset || !g->other_count))
+      return FIGARO_ERR_INVALID_ARG;
+    if (!g->run_offset) return FIGARO_ERR_INVALID_ARG;
+  }
+  Call c;
+  figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
+  if (st != FIGARO_OK) return st;
+  for (int t = 0; t < 2; ++t) {
+    TableWork& T = c.p.t[t];
+    const figaro_grouping* g = outs[t];
+    if (T.m > 0) {
+      T.perm = g->perm;
+      T.sorted_key = g->sorted_key;
+      T.run_key = g->run_key;
+      T.run_off = g->run_offset;
+      T.other = g->other_count;
+    }
+  }
+  st = run_grouping(c);
+  if (st != FIGARO_OK) return st;
+  for (int t = 0; t < 2; ++t) {
+    FIGARO_TRY(cudaMemcpyAsync(outs[t]->num_runs, &c.p.hdr->num_runs[t], sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                               c.s));
+    if (c.p.t[t].m == 0) FIGARO_TRY(cudaMemsetAsync(outs[t]->run_offset, 0, sizeof(int32_t), c.s));
+  }
+  if (num_groups)
+    FIGARO_TRY(cudaMemcpyAsync(num_groups, &c.p.hdr->num_groups, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.s));
+  return FIGARO_OK;
+}
+
+figaro_status figaro_join_head_tail(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                                    void* head, void* tail_a, void* tail_b, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  Call c;
+  figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
+  if (st != FIGARO_OK) return st;
+  if ((A->m > 0 && (!head || !tail_a)) || (B->m > 0 && !tail_b)) return FIGARO_ERR_INVALID_ARG;
+  if (A->m > 0) {
+    c.p.head = head;
+    c.p.t[0].tail = tail_a;
+  }
+  if (B->m > 0) c.p.t[1].tail = tail_b;
+  st = run_grouping(c);
+  if (st != FIGARO_OK) return st;
+  FIGARO_TRY(launch_head_tail(c.p, 0, c.s));
+  FIGARO_TRY(launch_head_tail(c.p, 1, c.s));
+  return FIGARO_OK;
+}
+
+figaro_status figaro_join_qr_r(const figaro_table* A, const figaro_table* B, const figaro_options* opt, double* R,
+                               int64_t ldr, void* ws, size_t ws_bytes, void* stream) {
+  if (!R) return FIGARO_ERR_INVALID_ARG;
+  Call c;
+  figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
+  if (st != FIGARO_OK) return st;
+  if (ldr < c.p.n) return FIGARO_ERR_INVALID_ARG;
+  const int host_out = opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT);
+  return run_qr_svd(c, R, ldr, nullptr, host_out);
+}
+
+figaro_status figaro_join_singular_values(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                                          double* sigma, double* R_out, int64_t ldr, void* ws, size_t ws_bytes,
+                                          void* stream) {
+  if (!sigma) return FIGARO_ERR_INVALID_ARG;
+  Call c;
+  figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
+  if (st != FIGARO_OK) return st;
+  if (R_out && ldr < c.p.n) return FIGARO_ERR_INVALID_ARG;
+  const int host_out = opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT);
+  return run_qr_svd(c, R_out, R_out ? ldr : c.p.n, sigma, host_out);
+}
+
+figaro_status figaro_batch_workspace_size(int32_t count, const figaro_table* A, const figaro_table* B,
+                                          const figaro_options* opt, size_t* bytes) {
+  if (count < 0 || !bytes || (count > 0 && (!A || !B))) return FIGARO_ERR_INVALID_ARG;
+  size_t total = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    size_t one = 0;
+    figaro_status st = figaro_workspace_size(&A[i], &B[i], opt, &one);
+    if (st != FIGARO_OK) return st;
+    total += (one + 255) & ~static_cast<size_t>(255);
+  }
+  *bytes = total;
+  return FIGARO_OK;
+}
+
+figaro_status figaro_batch_join(int32_t count, const figaro_table* A, const figaro_table* B,
+                                const figaro_options* opt, double* const* R, double* const* sigma, void* ws,
+                                size_t ws_bytes, void* stream) {
+  if (count < 0 || (count > 0 && (!A || !B || !R || !sigma))) return FIGARO_ERR_INVALID_ARG;
+  size_t need = 0;
+  figaro_status st = figaro_batch_workspace_size(count, A, B, opt, &need);
+  if (st != FIGARO_OK) return st;
+  if (ws_bytes < need) return FIGARO_ERR_WORKSPACE_TOO_SMALL;
+  char* base = static_cast<char*>(ws);
+  const int host_out = opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT);
+  for (int32_t i = 0; i < count; ++i) {
+    size_t one = 0;
+    figaro_workspace_size(&A[i], &B[i], opt, &one);
+    one = (one + 255) & ~static_cast<size_t>(255);
+    Call c;
+    figaro_options oi = resolve(opt);
+    oi.phase_events = nullptr;
+    st = prepare(c, &A[i], &B[i], &oi, base, one, stream);
+    if (st != FIGARO_OK) return st;
+    const int n = c.p.n;
+    if (sigma[i]) {
+      st = run_qr_svd(c, R[i], n, sigma[i], host_out);
+    } else if (R[i]) {
+      st = run_qr_svd(c, R[i], n, nullptr, host_out);
+    }
+    if (st != FIGARO_OK) return st;
+    base += one;
+  }
+  return FIGARO_OK;
+}
+
+figaro_status figaro_get_status(const void* ws, void* stream) {
+  if (!ws) return FIGARO_ERR_INVALID_ARG;
+  figaro_status st = bind_device(ws);
+  if (st != FIGARO_OK) return st;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return FIGARO_ERR_CUDA;
+  int32_t bits = 0;
+  if (cudaMemcpy(&bits, &static_cast<const DevHeader*>(ws)->status, sizeof(bits), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return FIGARO_ERR_CUDA;
+  if (bits & kStatusTimeout) return FIGARO_ERR_DEVICE_TIMEOUT;
+  if (bits & kStatusNotSpd) return FIGARO_ERR_NOT_SPD;
+  if (bits & kStatusNoConvergence) return FIGARO_ERR_NO_CONVERGENCE;
+  return FIGARO_OK;
+}
+
+const char* figaro_status_string(figaro_status s) {
+  switch (s) {
+    case FIGARO_OK: return "ok";
+    case FIGARO_ERR_INVALID_ARG: return "invalid argument";
+    case FIGARO_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case FIGARO_ERR_CUDA: return "CUDA error";
+    case FIGARO_ERR_NOT_SPD: return "non-finite pivot in Cholesky (NaN or Inf in the input)";
+    case FIGARO_ERR_NO_CONVERGENCE: return "Jacobi SVD did not converge within the sweep limit";
+    case FIGARO_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait gave up";
+    case FIGARO_ERR_UNSUPPORTED: return "unsupported size or width";
+  }
+  return "unknown status";
+}
+
+int32_t figaro_version(void) { return 100; }
+
+int64_t figaro_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

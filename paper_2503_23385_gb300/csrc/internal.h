@@ -1,0 +1,113 @@
+// Internal interface between the host orchestration (api.cu) and the kernel
+// translation units.  Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace figaro {
+
+constexpr int kMaxWidth = 128;          // n1 + n2 limit of the dense n x n kernels
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per radix tile
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kMaxPasses = 4;
+constexpr int kHtThreads = 256;         // head/tail block size
+constexpr int kHtRowsPerThread = 8;
+constexpr int kGramThreads = 256;
+constexpr int kGramTileRows = 64;
+
+// Device-side header at the start of every workspace.
+struct alignas(256) DevHeader {
+  int32_t status;            // figaro status bits (common.cuh)
+  int32_t pad0;
+  uint32_t ticket[8];        // persistent-grid work tickets
+  uint32_t kmin[2];          // ordered-key range per table (A = 0, B = 1)
+  uint32_t kmax[2];
+  int64_t num_runs[2];
+  int64_t num_groups;
+  int64_t reduced_rows;      // sum over matched keys of (m1g + m2g - 1)
+  int32_t jacobi_sweeps;
+  int32_t pad1;
+};
+
+// Per-table buffers of the grouping and head/tail steps.
+struct TableWork {
+  // input (device; staged copy when the caller passed host memory)
+  const void* x = nullptr;
+  const int32_t* key = nullptr;
+  int64_t m = 0;
+  int64_t ld = 0;
+  int n = 0;
+  int in_f64 = 0;            // input element type: 1 = double, 0 = float
+  // grouping
+  uint32_t* kb[2] = {nullptr, nullptr};
+  int32_t* vb[2] = {nullptr, nullptr};
+  uint32_t* hist = nullptr;  // kRadixBins * tiles
+  uint32_t* rle_cnt = nullptr;
+  int tiles = 0;
+  int32_t* perm = nullptr;
+  int32_t* sorted_key = nullptr;
+  int32_t* seg = nullptr;       // run index of each sorted row
+  int32_t* run_key = nullptr;
+  int32_t* run_off = nullptr;   // m + 1
+  int32_t* other = nullptr;     // partner run size (0 = unmatched)
+  int32_t* hdslot = nullptr;    // head row of the run's key group
+  // head/tail
+  void* tail = nullptr;         // m x n slots, compute type
+  uint32_t* chunk_status = nullptr;
+  double* chunk_agg = nullptr;
+  double* chunk_inc = nullptr;
+  int chunks = 0;
+  int chunk_rows = 0;
+};
+
+// Everything one instance needs, resolved from the workspace.
+struct Plan {
+  TableWork t[2];
+  int n1 = 0, n2 = 0, n = 0;
+  int mixed = 1;                // 1 = mixed path (FP32 compute), 0 = plain FP64
+  int gram_engine = 1;
+  int max_sweeps = 40;
+  int64_t spin_limit = 0;
+  double rank_tol = 0.0;
+  int withhold = 0;             // test-only fault injection (see FIGARO_FLAG_TEST_WITHHOLD)
+  DevHeader* hdr = nullptr;
+  void* head = nullptr;         // m1 x n slots, compute type
+  // Gram partials: [grid x slices x k x k] doubles per block
+  double* gpart[3] = {nullptr, nullptr, nullptr};
+  int ggrid[3] = {0, 0, 0};
+  int gslices[3] = {0, 0, 0};
+  // small dense n x n (doubles unless noted)
+  double* G1 = nullptr;
+  double* G2 = nullptr;
+  double* R1 = nullptr;
+  double* W = nullptr;
+  float* Wf = nullptr;
+  double* R = nullptr;
+  double* sigma = nullptr;
+  int32_t* active = nullptr;
+  int num_sms = 148;
+};
+
+// Host-side count of kernel launches (figaro_kernel_launches()).
+void count_launches(int n);
+
+// Sizes the plan from shapes alone (device pointers stay null when
+// ws == nullptr).  Returns the workspace bytes needed.
+size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2, int n2, int in_f64, int mixed,
+                   int stage_a, int stage_b, int num_sms);
+
+// Launchers (each returns the first CUDA error it meets).
+cudaError_t launch_reset(const Plan& p, cudaStream_t s);
+cudaError_t launch_grouping(const Plan& p, cudaStream_t s);
+cudaError_t launch_head_tail(const Plan& p, int table, cudaStream_t s);
+cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s);
+cudaError_t launch_chol_first(const Plan& p, cudaStream_t s);
+cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);
+cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
+
+}  // namespace figaro

@@ -1,0 +1,277 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars: key grouping bit-exact; R and sigma within relative Frobenius error
+1e-10 on the plain FP64 path and 1e-6 on the mixed path (well-conditioned
+inputs); head/tail rows within 1e-12 (FP64) / 2e-6 (FP32) of the row scale.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import config, make_pair, Table
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def fg():
+    import paper_2503_23385_gb300 as fg
+    fg.library()
+    return fg
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def dev(torch, T):
+    return (torch.from_numpy(np.ascontiguousarray(T.x)).cuda(), torch.from_numpy(np.ascontiguousarray(T.key)).cuda())
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def gpu_r_sigma(fg, torch, A, B, path):
+    R, s = fg.join_qr_svd(dev(torch, A), dev(torch, B), path=path)
+    torch.cuda.synchronize()
+    return R.cpu().numpy(), s.cpu().numpy()
+
+
+def check_against_oracle(fg, torch, A, B, paths=("fp64", "mixed"), route="reduced", tol=None):
+    Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key, route=route)
+    for path in paths:
+        R, s = gpu_r_sigma(fg, torch, A, B, path)
+        t = (tol or TOL)[path]
+        eR, es = rel(R, Rref), rel(s, sref)
+        assert eR <= t and es <= t, f"{path}: err_R={eR:.3e} err_sigma={es:.3e} (tol {t})"
+        assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) >= 0)
+
+
+# ------------------------------------------------------------- grouping --
+
+def grouping_cases():
+    rng = np.random.default_rng(0)
+    i32 = np.iinfo(np.int32)
+    yield "c0", config("c0")
+    adv = np.array([i32.min, i32.max, 0, -1, 1, i32.min, i32.max, -7] * 50, np.int32)
+    yield "adversarial", (Table(np.ones((adv.size, 1), np.float32), adv),
+                          Table(np.ones((9, 1), np.float32), np.array([0, i32.max, i32.min, 5, 5, -1, 3, 3, 3], np.int32)))
+    yield "all_equal", (Table(np.ones((5000, 2), np.float32), np.full(5000, 42, np.int32)),
+                        Table(np.ones((3, 2), np.float32), np.full(3, 42, np.int32)))
+    yield "all_distinct", (Table(np.ones((9000, 2), np.float32), rng.permutation(9000).astype(np.int32) * 3 - 5000),
+                           Table(np.ones((7000, 2), np.float32), rng.permutation(7000).astype(np.int32) * 2))
+    yield "single_row", (Table(np.ones((1, 2), np.float32), np.array([3], np.int32)),
+                         Table(np.ones((1, 2), np.float32), np.array([3], np.int32)))
+    yield "empty_b", (Table(np.ones((100, 2), np.float32), rng.integers(0, 9, 100).astype(np.int32)),
+                      Table(np.ones((0, 2), np.float32), np.zeros(0, np.int32)))
+    yield "wide_range", (Table(np.ones((70000, 1), np.float32), rng.integers(i32.min, i32.max, 70000).astype(np.int32)),
+                         Table(np.ones((50000, 1), np.float32), rng.integers(-1000, 1000, 50000).astype(np.int32)))
+    yield "ragged_tiles", make_pair(4096 * 3 + 17, 2, 4095, 2, 300, np.float32, "normal", seed=3)
+
+
+@pytest.mark.parametrize("name,tables", list(grouping_cases()), ids=[c[0] for c in grouping_cases()])
+def test_grouping_bitexact(fg, torch, name, tables):
+    A, B = tables
+    ga, gb, G = fg.join_group(dev(torch, A), dev(torch, B))
+    oa, ob = oracle.group(A.key), oracle.group(B.key)
+    for g, o, other in ((ga, oa, ob), (gb, ob, oa)):
+        assert np.array_equal(g["perm"].cpu().numpy(), o["perm"])
+        assert np.array_equal(g["sorted_key"].cpu().numpy(), o["sorted_key"])
+        assert g["num_runs"] == o["uniq"].size
+        assert np.array_equal(g["run_key"].cpu().numpy(), o["uniq"])
+        assert np.array_equal(g["run_offset"].cpu().numpy(), o["offset"])
+        cnt = dict(zip(other["uniq"].tolist(), other["count"].tolist()))
+        exp = np.array([cnt.get(k, 0) for k in o["uniq"].tolist()], np.int32)
+        assert np.array_equal(g["other_count"].cpu().numpy(), exp)
+    assert G == oracle.match(oa, ob)["key"].size
+
+
+def test_grouping_is_deterministic(fg, torch):
+    A, B = make_pair(200000, 2, 150000, 2, 5000, np.float32, "normal", seed=4)
+    r1 = fg.join_group(dev(torch, A), dev(torch, B))
+    r2 = fg.join_group(dev(torch, A), dev(torch, B))
+    for a, b in zip(r1[:2], r2[:2]):
+        assert all(torch.equal(a[k], b[k]) for k in ("perm", "sorted_key", "run_key", "run_offset", "other_count"))
+
+
+# ------------------------------------------------------------ head/tail --
+
+def gpu_head_tail_in_oracle_order(fg, torch, A, B, path):
+    head, ta, tb = fg.join_head_tail(dev(torch, A), dev(torch, B), path=path)
+    head, ta, tb = head.double().cpu().numpy(), ta.double().cpu().numpy(), tb.double().cpu().numpy()
+    oa, ob = oracle.group(A.key), oracle.group(B.key)
+    mt = oracle.match(oa, ob)
+    runs_a = {k: u for u, k in enumerate(oa["uniq"].tolist())}
+    Hd = np.array([head[runs_a[k]] for k in mt["key"].tolist()]).reshape(-1, A.n + B.n)
+    TA = np.vstack([ta[o + 1:o + m] for o, m in zip(mt["offA"], mt["m1"])] or [np.zeros((0, A.n))])
+    TB = np.vstack([tb[o + 1:o + m] for o, m in zip(mt["offB"], mt["m2"])] or [np.zeros((0, B.n))])
+    # every other slot is zero
+    mask_a = np.ones(A.m, bool)
+    for o, m in zip(mt["offA"], mt["m1"]):
+        mask_a[o + 1:o + m] = False
+    assert np.all(ta[mask_a] == 0)
+    unmatched = [u for u, k in enumerate(oa["uniq"].tolist()) if k not in set(mt["key"].tolist())]
+    assert np.all(head[unmatched] == 0)
+    return Hd, TA, TB
+
+
+@pytest.mark.parametrize("path,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
+@pytest.mark.parametrize("shape", [(1000, 4, 1000, 4, 100), (30000, 16, 20000, 16, 50), (5000, 3, 7000, 5, 400),
+                                   (20000, 32, 300, 32, 3)])
+def test_head_tail_rows(fg, torch, path, tol, shape):
+    m1, n1, m2, n2, K = shape
+    A, B = make_pair(m1, n1, m2, n2, K, np.float32, "uniform_pm1", seed=m1 + n2)
+    ref = oracle.reduce(A.x, A.key, B.x, B.key)
+    Hd, TA, TB = gpu_head_tail_in_oracle_order(fg, torch, A, B, path)
+    for got, want in ((Hd, ref["Hd"]), (TA, ref["TA"]), (TB, ref["TB"])):
+        assert got.shape == want.shape
+        scale = np.maximum(np.abs(want).max(axis=1, keepdims=True), 1e-300) if want.size else 1
+        assert np.max(np.abs(got - want) / scale, initial=0) <= tol
+
+
+# ------------------------------------------------------------- R, sigma --
+
+def test_c0_matches_materialized_oracle(fg, torch):
+    A, B = config("c0")
+    check_against_oracle(fg, torch, A, B, route="materialized")
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_joins_with_unmatched_keys(fg, torch, seed):
+    rng = np.random.default_rng(50 + seed)
+    m1, m2 = rng.integers(200, 20000, 2)
+    n1, n2 = rng.integers(1, 12, 2)
+    A = Table(rng.standard_normal((m1, n1)), rng.integers(0, 300, m1).astype(np.int32))
+    B = Table(rng.standard_normal((m2, n2)), rng.integers(100, 400, m2).astype(np.int32))
+    check_against_oracle(fg, torch, A, B)
+    A32 = Table(A.x.astype(np.float32), A.key)
+    B32 = Table(B.x.astype(np.float32), B.key)
+    check_against_oracle(fg, torch, A32, B32)
+
+
+@pytest.mark.parametrize("m,n", [(100, 4), (400, 16), (1600, 32)])
+def test_cartesian_paper_shape(fg, torch, m, n):
+    """The paper's own experiment: one key, so J is the Cartesian product."""
+    rng = np.random.default_rng(m)
+    A = Table(rng.uniform(0, 1, (m, n)).astype(np.float32), np.zeros(m, np.int32))
+    B = Table(rng.uniform(0, 1, (m, n)).astype(np.float32), np.zeros(m, np.int32))
+    # U(0,1) columns share a large mean: well above 1 condition number; the
+    # mixed bar is checked with the condition number in mind below
+    Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key)
+    R, s = gpu_r_sigma(fg, torch, A, B, "fp64")
+    assert rel(R, Rref) <= 1e-10 and rel(s, sref) <= 1e-10
+    R, s = gpu_r_sigma(fg, torch, A, B, "mixed")
+    assert rel(R, Rref) <= 1e-6 and rel(s, sref) <= 1e-6
+
+
+def test_groups_spanning_many_chunks(fg, torch):
+    """Few keys, long runs: the segmented scan crosses many chunks."""
+    A, B = make_pair(200000, 16, 150000, 16, 3, np.float32, "normal", seed=9)
+    check_against_oracle(fg, torch, A, B)
+
+
+def test_one_to_one_and_widths(fg, torch):
+    rng = np.random.default_rng(77)
+    m = 5000
+    A = Table(rng.standard_normal((m, 7)).astype(np.float32), rng.permutation(m).astype(np.int32))
+    B = Table(rng.standard_normal((m, 9)).astype(np.float32), rng.permutation(m).astype(np.int32))
+    check_against_oracle(fg, torch, A, B)
+    A, B = make_pair(3000, 64, 2500, 64, 30, np.float32, "normal", seed=78)
+    check_against_oracle(fg, torch, A, B)
+    A, B = make_pair(3000, 1, 2500, 1, 30, np.float64, "normal", seed=79)
+    check_against_oracle(fg, torch, A, B)
+
+
+def test_strided_rows(fg, torch):
+    """Leading dimension larger than the width (views of wider tables)."""
+    A, B = make_pair(4000, 12, 3000, 10, 50, np.float32, "normal", seed=80)
+    Rref, sref = oracle.join_r_sigma(A.x[:, :9], A.key, B.x[:, :7], B.key)
+    ta = (torch.from_numpy(A.x).cuda()[:, :9], torch.from_numpy(A.key).cuda())
+    tb = (torch.from_numpy(B.x).cuda()[:, :7], torch.from_numpy(B.key).cuda())
+    for path in ("fp64", "mixed"):
+        R, s = fg.join_qr_svd(ta, tb, path=path)
+        assert rel(R.cpu().numpy(), Rref) <= TOL[path] and rel(s.cpu().numpy(), sref) <= TOL[path]
+
+
+def test_empty_and_short_joins(fg, torch):
+    rng = np.random.default_rng(81)
+    A = Table(rng.standard_normal((50, 3)), np.zeros(50, np.int32))
+    B = Table(rng.standard_normal((40, 2)), np.ones(40, np.int32))
+    for path in ("fp64", "mixed"):
+        R, s = gpu_r_sigma(fg, torch, A, B, path)
+        assert np.all(R == 0) and np.all(s == 0)
+    # short join: 2 join rows, 5 columns -> R has 3 zero rows
+    A = Table(rng.standard_normal((5, 3)), np.array([0, 1, 2, 3, 4], np.int32))
+    B = Table(rng.standard_normal((4, 2)), np.array([0, 9, 9, 1], np.int32))
+    Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key, route="materialized")
+    for path in ("fp64", "mixed"):
+        R, s = gpu_r_sigma(fg, torch, A, B, path)
+        assert rel(R, Rref) <= TOL[path] and rel(s, sref) <= TOL[path]
+        assert np.all(R[2:] == 0)
+    # an empty table
+    A0 = Table(np.zeros((0, 3)), np.zeros(0, np.int32))
+    R, s = gpu_r_sigma(fg, torch, A0, B, "fp64")
+    assert np.all(R == 0) and np.all(s == 0)
+
+
+def test_results_are_deterministic(fg, torch):
+    A, B = make_pair(100000, 16, 80000, 16, 1000, np.float32, "normal", seed=82)
+    for path in ("fp64", "mixed"):
+        R1, s1 = gpu_r_sigma(fg, torch, A, B, path)
+        R2, s2 = gpu_r_sigma(fg, torch, A, B, path)
+        assert np.array_equal(R1, R2) and np.array_equal(s1, s2)
+
+
+def test_host_buffers_match_device_call(fg, torch):
+    A, B = make_pair(20000, 8, 15000, 8, 500, np.float32, "normal", seed=83)
+    Rd, sd = gpu_r_sigma(fg, torch, A, B, "mixed")
+    n = 16
+    nbytes = fg.host_workspace_size((A.x, A.key), (B.x, B.key))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    R = torch.zeros((n, n), dtype=torch.float64).pin_memory()
+    s = torch.zeros(n, dtype=torch.float64).pin_memory()
+    fg.join_qr_svd_host((A.x, A.key), (B.x, B.key), R, s, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(R.numpy(), Rd) and np.array_equal(s.numpy(), sd)
+
+
+# ---------------------------------------------------------- status codes --
+
+def test_status_codes(fg, torch):
+    A, B = make_pair(1000, 4, 1000, 4, 10, np.float32, "normal", seed=84)
+    ta, tb = dev(torch, A), dev(torch, B)
+    with pytest.raises(fg.FigaroError) as e:
+        fg.join_qr_svd((ta[0], ta[1]), (tb[0].double(), tb[1]))
+    assert e.value.status == 1
+    with pytest.raises(fg.FigaroError) as e:
+        big = torch.zeros((10, 100), device="cuda")
+        fg.join_qr_svd((big, torch.zeros(10, dtype=torch.int32, device="cuda")),
+                       (big, torch.zeros(10, dtype=torch.int32, device="cuda")))
+    assert e.value.status == 7
+    solver = fg.Solver(ta, tb)
+    solver.nbytes -= 1024
+    with pytest.raises(fg.FigaroError) as e:
+        solver(ta, tb)
+    assert e.value.status == 2
+    bad = A.x.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(fg.FigaroError) as e:
+        fg.join_qr_svd((torch.from_numpy(bad).cuda(), ta[1]), tb)
+    assert e.value.status == 4
+
+
+def test_batch_matches_single_calls(fg, torch):
+    pairs = [make_pair(2000 + 500 * i, 4 + 4 * (i % 3), 1500 + 300 * i, 8, 100 + i, np.float32, "normal", seed=90 + i)
+             for i in range(5)]
+    outs, ws = fg.batch_join([(dev(torch, a), dev(torch, b)) for a, b in pairs])
+    torch.cuda.synchronize()
+    for (a, b), (R, s) in zip(pairs, outs):
+        Rref, sref = oracle.join_r_sigma(a.x, a.key, b.x, b.key)
+        assert rel(R.cpu().numpy(), Rref) <= 1e-6 and rel(s.cpu().numpy(), sref) <= 1e-6
