@@ -129,9 +129,9 @@ def _device_table(x, key) -> Table:
         raise ValueError("x must be (m, n) and key (m,)")
     if x.dtype not in (torch.float32, torch.float64) or key.dtype != torch.int32:
         raise ValueError("x must be float32/float64 and key int32")
-    if x.stride(1) != 1:
-        raise ValueError("x must be row-major (unit column stride)")
     m, n = x.shape
+    if m > 0 and n > 1 and x.stride(1) != 1:
+        raise ValueError("x must be row-major (unit column stride)")
     ld = x.stride(0) if m > 1 else n
     return Table(x.data_ptr() if m else None, key.data_ptr() if m else None, m, max(ld, n), n,
                  F64 if x.dtype == torch.float64 else F32, MEM_DEVICE, 0)
@@ -170,10 +170,14 @@ def _options(path=PATH_MIXED, gram_engine=GRAM_AUTO, max_jacobi_sweeps=0, flags=
 
 
 def event_array(events):
-    """ctypes array of raw cudaEvent_t handles from torch.cuda.Event objects."""
+    """ctypes array of raw cudaEvent_t handles from torch.cuda.Event objects
+    (torch creates the CUDA event at its first record, so each is recorded once)."""
     arr = (ctypes.c_void_p * len(events))()
     for i, e in enumerate(events):
+        if not e.cuda_event:
+            e.record()
         arr[i] = e.cuda_event
+    _torch().cuda.synchronize()
     return arr
 
 

@@ -13,7 +13,7 @@
 namespace figaro {
 
 int ht_column_groups(int n, int V);
-void gram_geometry(int kout, int* kpad, int* tiles, int* slices);
+void gram_geometry(int kout, int* kpad, int* ntiles, int* slices, int* tpt);
 
 namespace {
 std::atomic<int64_t> g_launches{0};
@@ -115,9 +115,7 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
     size_t most = 0;
     int kouts[2] = {blk == 0 ? n : (blk == 1 ? n1 : n2), blk == 2 ? n2 : n};
     for (int q = 0; q < 2; ++q) {
-      int kpad, tiles, slices;
-      gram_geometry(kouts[q], &kpad, &tiles, &slices);
-      size_t sz = static_cast<size_t>(grid) * slices * kouts[q] * kouts[q];
+      size_t sz = static_cast<size_t>(grid) * kouts[q] * kouts[q];
       if (sz > most) most = sz;
     }
     p.gslices[blk] = 0;

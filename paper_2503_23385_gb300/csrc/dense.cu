@@ -155,8 +155,21 @@ __global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweep
     U[e] = c < n ? static_cast<T>(R[static_cast<int64_t>(r) * ldr + c]) : T(0);
     if (kWithV) V[e] = (c == r) ? T(1) : T(0);
   }
+  __syncthreads();
   // rotate while |u_p . u_q| > tol ||u_p|| ||u_q||; 4 n eps leaves room for the rounding of the dot products
-  const T tol = T(4) * static_cast<T>(n) * (sizeof(T) == 4 ? T(5.9604645e-8) : T(1.1102230246251565e-16));
+  const T eps = sizeof(T) == 4 ? T(5.9604645e-8) : T(1.1102230246251565e-16);
+  const T tol = T(4) * static_cast<T>(n) * eps;
+  // columns whose squared norm is below (n eps)^2 ||R||_F^2 are rounding
+  // noise of a rank-deficient R: they take no part in rotations
+  __shared__ T s_fro;
+  if (threadIdx.x < 32) {
+    T f = 0;
+    for (int e = threadIdx.x; e < np * n; e += 32) f += U[e] * U[e];
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (threadIdx.x == 0) s_fro = f;
+  }
+  __syncthreads();
+  const T negligible = (static_cast<T>(n) * eps) * (static_cast<T>(n) * eps) * s_fro;
   const int group = threadIdx.x / tpp;
   const int gl = threadIdx.x % tpp;
   const int npairs = np / 2;
@@ -197,7 +210,7 @@ __global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweep
         al = group_sum(al, tpp);
         be = group_sum(be, tpp);
         ga = group_sum(ga, tpp);
-        bool rotate = real && al > T(0) && be > T(0) && ga != T(0) && fabs(ga) > tol * sqrt(al * be);
+        bool rotate = real && al > negligible && be > negligible && ga != T(0) && fabs(ga) > tol * sqrt(al * be);
         if (rotate) {
           T zeta = (be - al) / (T(2) * ga);
           T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));

@@ -8,12 +8,15 @@
 //            A tail rows TA W[0:n1, :]  (all n columns)
 //            B tail rows TB W[n1:, n1:] (B's n2 columns only, since W is
 //                                        upper triangular)
-// Each block accumulates 4x4 register tiles of (X W)^T (X W) over 64-row
-// tiles staged in shared memory.  On the mixed path the tiles are FP32 and
-// are flushed into FP64 every 16 row tiles, so FP32 sums never run over more
-// than 1,024 rows; the plain path accumulates in FP64 throughout.
-// Partials go to [grid][slice] buffers and are reduced in a fixed order, so
-// results are bitwise reproducible.
+// A block streams 64-row tiles of X into shared memory (the next tile is
+// prefetched into registers while the current one is used), forms Q = X W
+// for the tile (W is upper triangular, so column c sums rows 0..c only) and
+// accumulates the upper 4x4 register tiles of Q^T Q.  On the mixed path the
+// register tiles are FP32 and are flushed into FP64 every 16 row tiles, so
+// no FP32 sum runs over more than 1,024 rows; the plain path accumulates in
+// FP64.  Thread groups (slices) that split the rows are summed inside the
+// block in a fixed order, and the per-block partials are reduced in a fixed
+// order as well: results are bitwise reproducible.
 #include "common.cuh"
 #include "internal.h"
 
@@ -21,64 +24,87 @@ namespace figaro {
 namespace {
 
 struct GramArgs {
-  const void* X;          // rows x k (compute type), leading dimension ld
-  int64_t ld;
+  const void* X;          // rows x k (compute type), rows contiguous (leading dimension k)
   int k;
   int64_t rows;           // used when rows_dev == nullptr
   const int64_t* rows_dev;
   const void* W;          // optional n x n row-major (compute type)
   int wld;
-  int wrow0, wcol0;       // the k x kout block of W used
+  int w0;                 // the k x kout block W[w0:w0+k, w0:w0+kout] is used
   int kout;
   int kpad;               // kout rounded up to 4
-  int tiles;              // (kpad/4)^2 register tiles
+  int ntiles;             // upper register tiles (T4 (T4+1) / 2)
   int slices;             // thread groups splitting the rows of a tile
   int tile_rows;
-  double* part;           // [grid][slices][kout][kout]
+  double* part;           // [grid][kout][kout] (upper 4x4 tiles written)
 };
 
 constexpr int kFlushTiles = 16;
 
+__device__ __forceinline__ void tile_of(int t, int T4, int& ti, int& tj) {
+  // t -> (ti, tj), ti <= tj, row-wise over the upper triangle of a T4 x T4 grid
+  ti = 0;
+  int rowlen = T4;
+  while (t >= rowlen) {
+    t -= rowlen;
+    ++ti;
+    --rowlen;
+  }
+  tj = ti + t;
+}
+
+// 16-byte asynchronous global -> shared copy; bytes beyond src_bytes are zero-filled.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 template <typename T, int TPT>
 __global__ void __launch_bounds__(kGramThreads) gram_kernel(GramArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Xs = reinterpret_cast<T*>(smem_raw);                          // tile_rows x k
-  T* Ws = Xs + static_cast<int64_t>(a.tile_rows) * a.k;            // k x kpad (if W)
-  T* Qs = a.W ? Ws + static_cast<int64_t>(a.k) * a.kpad : nullptr; // tile_rows x kpad
-  const int RT = a.tile_rows;
-  const int k = a.k, kp = a.kpad, T4 = kp / 4;
+  const int RT = a.tile_rows, k = a.k, kp = a.kpad, T4 = kp / 4;
+  T* Xb[2] = {reinterpret_cast<T*>(smem_raw), reinterpret_cast<T*>(smem_raw) + RT * k};  // RT x k, two stages
+  T* Ws = Xb[1] + RT * k;                                           // k x kp (if W)
+  T* Qs = Ws + k * kp;                                              // RT x kp (if W)
+  const int qld = a.W ? kp : k;
   const int64_t rows = a.rows_dev ? *a.rows_dev : a.rows;
-  const T* X = static_cast<const T*>(a.X);
+  const char* X = static_cast<const char*>(a.X);
   const int tid = threadIdx.x;
+  const int64_t total_bytes = rows * k * static_cast<int64_t>(sizeof(T));
+  const int tile_bytes = RT * k * static_cast<int>(sizeof(T));  // a multiple of 16 (RT % 4 == 0)
+  auto stage = [&](int64_t rt, T* dst) {
+    const int64_t base = rt * tile_bytes;
+    for (int c = tid * 16; c < tile_bytes; c += kGramThreads * 16) {
+      int64_t left = total_bytes - (base + c);
+      int nb = left >= 16 ? 16 : (left > 0 ? static_cast<int>(left) : 0);
+      cp_async16(reinterpret_cast<char*>(dst) + c, nb > 0 ? X + base + c : X, nb);
+    }
+    cp_async_commit();
+  };
 
   if (a.W) {
     const T* W = static_cast<const T*>(a.W);
     for (int e = tid; e < k * kp; e += blockDim.x) {
-      int l = e / kp, c = e % kp;
-      Ws[e] = c < a.kout ? W[static_cast<int64_t>(a.wrow0 + l) * a.wld + a.wcol0 + c] : T(0);
+      int l = e / kp, c = e - l * kp;
+      Ws[e] = (c < a.kout && l <= c) ? W[static_cast<int64_t>(a.w0 + l) * a.wld + a.w0 + c] : T(0);
     }
   }
-  const T* Q = a.W ? Qs : Xs;
-  const int qld = a.W ? kp : k;
 
-  // thread -> (slice, register tiles)
-  int slice, tile0;
-  if (TPT == 1) {
-    slice = tid / a.tiles;
-    tile0 = tid % a.tiles;
-  } else {
-    slice = 0;
-    tile0 = tid;
-  }
+  // thread -> slice and its upper register tiles
+  const int per_slice = (a.ntiles + TPT - 1) / TPT;
+  const int slice = tid / per_slice;
+  const int lt = tid - slice * per_slice;
   const bool active = slice < a.slices;
   int ti[TPT], tj[TPT];
   bool tv[TPT];
 #pragma unroll
   for (int q = 0; q < TPT; ++q) {
-    int t = tile0 + q * kGramThreads;
-    tv[q] = active && t < a.tiles;
-    ti[q] = tv[q] ? t / T4 : 0;
-    tj[q] = tv[q] ? t % T4 : 0;
+    int t = lt + q * per_slice;
+    tv[q] = active && t < a.ntiles;
+    ti[q] = tj[q] = 0;
+    if (tv[q]) tile_of(t, T4, ti[q], tj[q]);
   }
   T acc[TPT][4][4];
   double tot[TPT][4][4];
@@ -92,31 +118,29 @@ __global__ void __launch_bounds__(kGramThreads) gram_kernel(GramArgs a) {
         tot[q][i][j] = 0.0;
       }
 
-  const int64_t ntiles = (rows + RT - 1) / RT;
+  const int64_t ntiles_rows = (rows + RT - 1) / RT;
+  int64_t rt = blockIdx.x;
+  if (rt < ntiles_rows) stage(rt, Xb[0]);
   int since_flush = 0;
-  for (int64_t rt = blockIdx.x; rt < ntiles; rt += gridDim.x) {
-    __syncthreads();
-    const int64_t r0 = rt * RT;
-    // stage rows (zero beyond the end)
-    for (int e = tid; e < RT * k; e += blockDim.x) {
-      int r = e / k, c = e % k;
-      int64_t gr = r0 + r;
-      Xs[e] = gr < rows ? X[gr * a.ld + c] : T(0);
-    }
-    __syncthreads();
+  for (int buf = 0; rt < ntiles_rows; rt += gridDim.x, buf ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();  // tile rt landed; the other buffer is free
+    if (rt + gridDim.x < ntiles_rows) stage(rt + gridDim.x, Xb[buf ^ 1]);  // overlaps the work below
+    const T* Xs = Xb[buf];
     if (a.W) {
       for (int e = tid; e < RT * kp; e += blockDim.x) {
-        int r = e / kp, c = e % kp;
+        int r = e / kp, c = e - r * kp;
+        int lmax = c < k - 1 ? c : k - 1;
         T s = T(0);
         const T* xr = Xs + r * k;
-        for (int l = 0; l < k; ++l) s += xr[l] * Ws[l * kp + c];
+        for (int l = 0; l <= lmax; ++l) s += xr[l] * Ws[l * kp + c];
         Qs[e] = s;
       }
       __syncthreads();
     }
     if (active) {
       for (int r = slice; r < RT; r += a.slices) {
-        const T* qr = Q + r * qld;
+        const T* qr = (a.W ? static_cast<const T*>(Qs) : Xs) + r * qld;
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
           if (!tv[q]) continue;
@@ -124,8 +148,8 @@ __global__ void __launch_bounds__(kGramThreads) gram_kernel(GramArgs a) {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             int ci = ti[q] * 4 + i, cj = tj[q] * 4 + i;
-            u[i] = (a.W || ci < k) ? qr[ci] : T(0);
-            w[i] = (a.W || cj < k) ? qr[cj] : T(0);
+            u[i] = ci < qld ? qr[ci] : T(0);
+            w[i] = cj < qld ? qr[cj] : T(0);
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i)
@@ -147,94 +171,132 @@ __global__ void __launch_bounds__(kGramThreads) gram_kernel(GramArgs a) {
           }
     }
   }
-  if (!active) return;
-  double* out = a.part + (static_cast<int64_t>(blockIdx.x) * a.slices + slice) * a.kout * a.kout;
 #pragma unroll
-  for (int q = 0; q < TPT; ++q) {
-    if (!tv[q]) continue;
+  for (int q = 0; q < TPT; ++q)
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        int ci = ti[q] * 4 + i, cj = tj[q] * 4 + j;
-        if (ci < a.kout && cj < a.kout) out[ci * a.kout + cj] = tot[q][i][j] + static_cast<double>(acc[q][i][j]);
+      for (int j = 0; j < 4; ++j) tot[q][i][j] += static_cast<double>(acc[q][i][j]);
+
+  // slices summed in a fixed order in shared memory, then one partial per block
+  cp_async_wait_all();
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(smem_raw);  // kpad x kpad
+  for (int e = tid; e < kp * kp; e += blockDim.x) red[e] = 0.0;
+  for (int s = 0; s < a.slices; ++s) {
+    __syncthreads();
+    if (active && slice == s) {
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) {
+        if (!tv[q]) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) red[(ti[q] * 4 + i) * kp + tj[q] * 4 + j] += tot[q][i][j];
       }
+    }
+  }
+  __syncthreads();
+  double* out = a.part + static_cast<int64_t>(blockIdx.x) * a.kout * a.kout;
+  for (int e = tid; e < a.kout * a.kout; e += blockDim.x) {
+    int i = e / a.kout, j = e - i * a.kout;
+    out[e] = red[i * kp + j];
   }
 }
 
 struct ReduceArgs {
   const double* part[3];
-  int count[3];   // grid * slices partials per block
+  int count[3];   // partials (blocks) per Gram block
   int kout[3];
   int off[3];     // diagonal offset of the block inside G
   int n;
   double* G;
 };
 
-// G = sum of the three blocks' partials, in a fixed order (deterministic),
-// symmetrised from the upper triangle.
-__global__ void gram_reduce_kernel(ReduceArgs a) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.n * a.n) return;
-  int i = e / a.n, j = e % a.n;
-  int lo = i < j ? i : j, hi = i < j ? j : i;
-  double s = 0.0;
+constexpr int kReduceWarps = 8;
+
+// G = sum of the three blocks' partials in a fixed order (deterministic),
+// symmetrised from the upper triangle.  Lanes take consecutive outputs,
+// warps interleave over the partials.
+__global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_kernel(ReduceArgs a) {
+  __shared__ double s[kReduceWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  const bool ok = e < a.n * a.n;
+  const int i = ok ? e / a.n : 0, j = ok ? e - (e / a.n) * a.n : 0;
+  const int lo = i < j ? i : j, hi = i < j ? j : i;
+  double tot = 0.0;
   for (int b = 0; b < 3; ++b) {
-    if (!a.part[b]) continue;
-    int ii = lo - a.off[b], jj = hi - a.off[b];
-    int ko = a.kout[b];
+    if (!a.part[b] || !ok) continue;
+    const int ko = a.kout[b];
+    const int ii = lo - a.off[b], jj = hi - a.off[b];
     if (ii < 0 || jj < 0 || ii >= ko || jj >= ko) continue;
     const double* p = a.part[b] + ii * ko + jj;
     const int64_t stride = static_cast<int64_t>(ko) * ko;
-    double t = 0.0;
-    for (int c = 0; c < a.count[b]; ++c) t += p[c * stride];
-    s += t;
+    double t0 = 0.0, t1 = 0.0;
+    int c = warp;
+    for (; c + kReduceWarps < a.count[b]; c += 2 * kReduceWarps) {
+      t0 += p[c * stride];
+      t1 += p[(c + kReduceWarps) * stride];
+    }
+    if (c < a.count[b]) t0 += p[c * stride];
+    tot += t0 + t1;
   }
-  a.G[e] = s;
+  s[warp][lane] = tot;
+  __syncthreads();
+  if (warp == 0 && ok) {
+    double v = 0.0;
+    for (int w = 0; w < kReduceWarps; ++w) v += s[w][lane];
+    a.G[e] = v;
+  }
+}
+
+template <typename T, int TPT>
+cudaError_t launch_tpt(const GramArgs& a, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t err =
+      cudaFuncSetAttribute(gram_kernel<T, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  gram_kernel<T, TPT><<<grid, kGramThreads, smem, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_gram_block(const GramArgs& a0, int grid, cudaStream_t s) {
-  GramArgs a = a0;
-  size_t smem = static_cast<size_t>(a.tile_rows) * a.k * sizeof(T);
+cudaError_t launch_gram_block(const GramArgs& a, int tpt, int grid, cudaStream_t s) {
+  size_t smem = 2 * static_cast<size_t>(a.tile_rows) * a.k * sizeof(T);
   if (a.W) smem += (static_cast<size_t>(a.k) * a.kpad + static_cast<size_t>(a.tile_rows) * a.kpad) * sizeof(T);
-  int tpt = a.tiles <= kGramThreads ? 1 : (a.tiles <= 2 * kGramThreads ? 2 : 4);
-  cudaError_t err;
-  if (tpt == 1) {
-    err = cudaFuncSetAttribute(gram_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (err != cudaSuccess) return err;
-    gram_kernel<T, 1><<<grid, kGramThreads, smem, s>>>(a);
-  } else if (tpt == 2) {
-    err = cudaFuncSetAttribute(gram_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (err != cudaSuccess) return err;
-    gram_kernel<T, 2><<<grid, kGramThreads, smem, s>>>(a);
-  } else {
-    err = cudaFuncSetAttribute(gram_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (err != cudaSuccess) return err;
-    gram_kernel<T, 4><<<grid, kGramThreads, smem, s>>>(a);
+  size_t red = sizeof(double) * a.kpad * a.kpad;
+  if (smem < red) smem = red;
+  switch (tpt) {
+    case 1: return launch_tpt<T, 1>(a, grid, smem, s);
+    case 2: return launch_tpt<T, 2>(a, grid, smem, s);
+    case 4: return launch_tpt<T, 4>(a, grid, smem, s);
+    default: return launch_tpt<T, 8>(a, grid, smem, s);
   }
-  count_launches(1);
-  return cudaGetLastError();
 }
 
 }  // namespace
 
 // Geometry of one Gram block (shared with the workspace planner).
-void gram_geometry(int kout, int* kpad, int* tiles, int* slices) {
+void gram_geometry(int kout, int* kpad, int* ntiles, int* slices, int* tpt) {
   *kpad = (kout + 3) / 4 * 4;
-  int T4 = *kpad / 4;
-  *tiles = T4 * T4;
-  *slices = *tiles <= kGramThreads ? kGramThreads / *tiles : 1;
+  const int T4 = *kpad / 4;
+  *ntiles = T4 * (T4 + 1) / 2;
+  int t = 1;
+  while ((*ntiles + t - 1) / t > kGramThreads) t <<= 1;
+  *tpt = t;
+  const int per_slice = (*ntiles + t - 1) / t;
+  *slices = kGramThreads / per_slice;
 }
 
 int gram_tile_rows(int k, int kout, int with_w, int elem) {
-  int kp = (kout + 3) / 4 * 4;
-  for (int rt = kGramTileRows; rt >= 8; rt /= 2) {
-    size_t smem = static_cast<size_t>(rt) * k * elem;
+  const int kp = (kout + 3) / 4 * 4;
+  for (int rt = kGramTileRows; rt >= 4; rt /= 2) {
+    size_t smem = 2 * static_cast<size_t>(rt) * k * elem;
     if (with_w) smem += (static_cast<size_t>(k) * kp + static_cast<size_t>(rt) * kp) * elem;
     if (smem <= 200 * 1024) return rt;
   }
-  return 8;
+  return 4;
 }
 
 cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
@@ -248,14 +310,12 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     int64_t rows;
     if (b == 0) {
       a.X = p.head;
-      a.ld = p.n;
       a.k = p.n;
       a.rows_dev = &p.hdr->num_runs[0];
       rows = p.t[0].m;
     } else {
       const TableWork& T = p.t[b - 1];
       a.X = T.tail;
-      a.ld = T.n;
       a.k = T.n;
       a.rows = T.m;
       rows = T.m;
@@ -264,25 +324,25 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     if (pass == 2) {
       a.W = p.mixed ? static_cast<const void*>(p.Wf) : static_cast<const void*>(p.W);
       a.wld = p.n;
-      a.wrow0 = b == 2 ? p.n1 : 0;
-      a.wcol0 = b == 2 ? p.n1 : 0;
+      a.w0 = b == 2 ? p.n1 : 0;
       a.kout = b == 2 ? p.n2 : p.n;
     } else {
       a.kout = a.k;
     }
-    gram_geometry(a.kout, &a.kpad, &a.tiles, &a.slices);
+    int tpt;
+    gram_geometry(a.kout, &a.kpad, &a.ntiles, &a.slices, &tpt);
     a.tile_rows = gram_tile_rows(a.k, a.kout, a.W != nullptr, elem);
     a.part = p.gpart[b];
-    int grid = p.ggrid[b];
-    cudaError_t err = p.mixed ? launch_gram_block<float>(a, grid, s) : launch_gram_block<double>(a, grid, s);
+    const int grid = p.ggrid[b];
+    cudaError_t err = p.mixed ? launch_gram_block<float>(a, tpt, grid, s) : launch_gram_block<double>(a, tpt, grid, s);
     if (err != cudaSuccess) return err;
     r.part[b] = p.gpart[b];
-    r.count[b] = grid * a.slices;
+    r.count[b] = grid;
     r.kout[b] = a.kout;
     r.off[b] = b == 2 ? p.n1 : 0;
   }
-  int ne = p.n * p.n;
-  gram_reduce_kernel<<<(ne + 255) / 256, 256, 0, s>>>(r);
+  const int ne = p.n * p.n;
+  gram_reduce_kernel<<<(ne + 31) / 32, 32 * kReduceWarps, 0, s>>>(r);
   count_launches(1);
   return cudaGetLastError();
 }
