@@ -12,7 +12,7 @@
 
 namespace figaro {
 
-int ht_column_groups(int n, int V);
+int ht_chunk_rows(int n);
 void gram_geometry(int kout, int* kpad, int* ntiles, int* slices, int* tpt);
 
 namespace {
@@ -84,8 +84,9 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
       T.kb[k] = b.take<uint32_t>(static_cast<size_t>(m));
       T.vb[k] = b.take<int32_t>(static_cast<size_t>(m));
     }
-    T.hist = b.take<uint32_t>(static_cast<size_t>(kRadixBins) * (T.tiles > 0 ? T.tiles : 1));
-    T.rle_cnt = b.take<uint32_t>(static_cast<size_t>(T.tiles > 0 ? T.tiles : 1));
+    T.hist = b.take<uint32_t>(static_cast<size_t>(kMaxPasses) * kRadixBins);
+    T.sort_status = b.take<uint64_t>(static_cast<size_t>(group_status_words(T.tiles > 0 ? T.tiles : 1)));
+    T.run_status = T.sort_status + static_cast<int64_t>(kMaxPasses) * (T.tiles > 0 ? T.tiles : 1) * kRadixBins;
     T.perm = b.take<int32_t>(static_cast<size_t>(m));
     T.sorted_key = b.take<int32_t>(static_cast<size_t>(m));
     T.seg = b.take<int32_t>(static_cast<size_t>(m));
@@ -94,11 +95,8 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
     T.other = b.take<int32_t>(static_cast<size_t>(m));
     T.hdslot = b.take<int32_t>(static_cast<size_t>(m));
     T.tail = b.take<char>(static_cast<size_t>(m) * n * ec);
-    // chunks sized for the narrowest vector width (most chunks)
-    const int cg = ht_column_groups(n, 1);
-    const int rows_min = (kHtThreads / cg) * kHtRowsPerThread;
-    T.chunks = static_cast<int>(ceil_div(m, rows_min));
-    T.chunk_rows = rows_min;
+    T.chunk_rows = ht_chunk_rows(n);
+    T.chunks = static_cast<int>(ceil_div(m, T.chunk_rows));
     T.chunk_status = b.take<uint32_t>(static_cast<size_t>(T.chunks));
     T.chunk_agg = b.take<double>(static_cast<size_t>(T.chunks) * n);
     T.chunk_inc = b.take<double>(static_cast<size_t>(T.chunks) * n);
@@ -181,7 +179,7 @@ figaro_options resolve(const figaro_options* o) {
   figaro_default_options(&r);
   if (o) r = *o;
   if (r.max_jacobi_sweeps == 0) r.max_jacobi_sweeps = 40;
-  if (r.spin_limit == 0) r.spin_limit = 20000000;  // ~1-2 s of 64 ns naps
+  if (r.spin_limit == 0) r.spin_limit = 20000000;  // ~1-2 s of short naps
   return r;
 }
 

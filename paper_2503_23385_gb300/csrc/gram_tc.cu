@@ -1,0 +1,466 @@
+// Gram products of the reduced matrix on 5th-generation tensor cores
+// (tcgen05, kind::tf32), the mixed-precision engine of the CholeskyQR2
+// passes (same block structure and meaning as gram.cu).
+//
+// Precision: every FP32 operand v is split as v = hi + lo with hi = v with
+// its 13 low mantissa bits cleared (exactly TF32) and lo = v - hi rounded to
+// TF32; a product is formed from hi*hi + hi*lo + lo*hi (3xTF32), so each term
+// carries ~22 significant bits.  Products accumulate in FP32 in tensor memory
+// for at most 1,024 rows, then into FP64 (per-block partials, reduced in a
+// fixed order).
+//
+// Per block (128 threads; thread t owns row t of a 128-row tile):
+//   1. TMA loads the next X tile (128 rows x k, 128-byte swizzle) while the
+//      current one is processed (two buffers, mbarrier transaction counts).
+//   2. Pass 2 only: X is split in place (hi) and into a lo buffer; three
+//      formation MMAs D1 = X W (M = 128 rows, N = kout, K = k) run into tensor
+//      memory; each thread reads its row of D1 back (tcgen05.ld).
+//      Pass 1: each thread reads its row of X from shared memory.
+//   3. The row (Q = X W, or X) is split into hi / lo and written transposed
+//      into K-major operand panels (Q^T: kout rows x 128 tile rows).
+//   4. Three Gram MMAs D2 += Q^T Q (M = 64 or 128, N = kout, K = 128 rows)
+//      accumulate in tensor memory.
+// A single elected thread issues every MMA and TMA; completion is tracked
+// with tcgen05.commit -> mbarrier.  Every wait is bounded: on timeout the
+// block records FIGARO_ERR_DEVICE_TIMEOUT, stops issuing work, waits (again
+// bounded) for what it issued, frees its tensor memory and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace figaro {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTileRows = 128;
+constexpr int kPanelBytes = kTileRows * 128;  // one 32-column panel of an X tile
+constexpr int kFlushTiles = 8;
+
+struct TcArgs {
+  int k;             // columns of X (multiple of 4)
+  int kout;          // Gram width
+  int kpanels;       // ceil(k / 32): 128-byte panels of an X row
+  int ksteps_f;      // formation K steps of 8 (k padded to 8)
+  int np;            // kout padded to 16 (N of both MMAs)
+  int mg;            // Gram M: 64 or 128
+  int qrows;         // rows of each Q^T panel (kout padded to 8)
+  int qpanel_bytes;  // qrows * 128
+  int wpanel_bytes;  // np * 128
+  int64_t rows;
+  const int64_t* rows_dev;
+  const float* W;    // pass 2: W block base (row-major, leading dimension wld); nullptr for pass 1
+  int wld;
+  double* part;      // [grid][kout][kout]
+  int32_t* status;
+  int64_t spin_limit;
+  // shared memory offsets (bytes from the 1024-aligned base)
+  int off_x[2], off_xlo, off_wh, off_wl, off_qh, off_ql;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle (layout type 2):
+// 8-row groups 1,024 bytes apart.
+__device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);
+  d |= static_cast<uint64_t>(1) << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;            // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                    // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, FP32 accumulator, both operands K-major.
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(dtmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+
+// Bounded wait for the given phase parity; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int64_t limit) {
+  for (int64_t i = 0; i < limit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+// Round to the nearest TF32 value (ties away from zero; only the low part of a
+// split is rounded, so the tie rule is immaterial to the error bound).
+__device__ __forceinline__ float tf32_rn(float v) {
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+}
+
+// 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* out) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 32; ++c) out[c] = __uint_as_float(r[c]);
+}
+
+// Byte offset of element (row, col) of a 128-byte-swizzled K-major panel set:
+// 32 columns per panel, rows of 128 bytes, 16-byte chunks XOR (row mod 8).
+__device__ __forceinline__ int sw128_offset(int row, int col, int panel_bytes) {
+  const int p = col >> 5, kk = col & 31;
+  return p * panel_bytes + row * 128 + ((((kk >> 2) ^ (row & 7))) << 4) + ((kk & 3) << 2);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t bar_tma[2], bar_f, bar_g;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const bool pass2 = a.W != nullptr;
+  const int64_t rows = a.rows_dev ? *a.rows_dev : a.rows;
+  const int64_t ntiles = (rows + kTileRows - 1) / kTileRows;
+  const uint32_t tmem_cols = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));
+
+  if (tid == 0) {
+    mbar_init(&bar_tma[0], 1);
+    mbar_init(&bar_tma[1], 1);
+    mbar_init(&bar_f, 1);
+    mbar_init(&bar_g, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (pass2) {  // W^T (np rows x k, K-major): hi and lo parts; padding rows / columns are zero
+    float* wh = reinterpret_cast<float*>(base + a.off_wh);
+    float* wl = reinterpret_cast<float*>(base + a.off_wl);
+    const int wbytes = a.kpanels * a.wpanel_bytes;
+    for (int e = tid; e < wbytes / 4; e += kTcThreads) {
+      wh[e] = 0.f;
+      wl[e] = 0.f;
+    }
+    __syncthreads();
+    for (int e = tid; e < a.kout * a.k; e += kTcThreads) {
+      const int n = e / a.k, kk = e - n * a.k;
+      const float v = (kk <= n) ? a.W[static_cast<int64_t>(kk) * a.wld + n] : 0.f;  // W upper triangular
+      const int off = sw128_offset(n, kk, a.wpanel_bytes);
+      const float h = tf32_hi(v);
+      *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wh) + off) = h;
+      *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wl) + off) = tf32_rn(v - h);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t d1 = tmem;                        // formation result: 128 lanes x NP
+  const uint32_t d2 = tmem + static_cast<uint32_t>(NP);  // Gram accumulator
+  const uint32_t tile_bytes = static_cast<uint32_t>(a.kpanels * kPanelBytes);
+
+  // prologue: first two tiles of this block
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      const int64_t rt = blockIdx.x + static_cast<int64_t>(b) * gridDim.x;
+      if (rt < ntiles) {
+        expect_tx(&bar_tma[b], tile_bytes);
+        for (int p = 0; p < a.kpanels; ++p)
+          tma_load_2d(base + a.off_x[b] + p * kPanelBytes, &tmx, p * 32, static_cast<int>(rt * kTileRows), &bar_tma[b]);
+      }
+    }
+  }
+
+  // FP64 totals of the Gram rows this thread holds (flushed from TMEM)
+  const int lane_row = a.mg == 64 ? (((tid & 31) < 16) ? (warp * 16 + (tid & 31)) : -1) : tid;
+  double* part = a.part + static_cast<int64_t>(blockIdx.x) * a.kout * a.kout;
+  if (lane_row >= 0 && lane_row < a.kout)
+    for (int j = 0; j < a.kout; ++j) part[lane_row * a.kout + j] = 0.0;
+
+  bool fresh = true;  // next Gram MMA starts a new accumulation
+  int it = 0;
+  int pending_g = 0;  // Gram MMAs committed and not yet waited for
+  uint32_t g_phase = 0, f_phase = 0;
+  auto flush = [&]() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float v[NP];
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += 32) tmem_ld32(d2 + (static_cast<uint32_t>(warp * 32) << 16) + c0, v + c0);
+    if (lane_row >= 0 && lane_row < a.kout)
+      for (int j = 0; j < a.kout; ++j) part[lane_row * a.kout + j] += static_cast<double>(v[j]);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  };
+
+  for (int64_t rt = blockIdx.x; rt < ntiles; rt += gridDim.x, ++it) {
+    const int buf = it & 1;
+    float* X = reinterpret_cast<float*>(base + a.off_x[buf]);
+    if (!mbar_wait(&bar_tma[buf], static_cast<uint32_t>((it >> 1) & 1), a.spin_limit)) {
+      if (tid == 0) {
+        set_status(a.status, kStatusTimeout);
+        s_abort = 1;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    float q[NP];
+    if (pass2) {
+      // split X in place (hi) and into the lo buffer, then D1 = X W (3 x TF32)
+      float* Xl = reinterpret_cast<float*>(base + a.off_xlo);
+      for (int e = tid; e < static_cast<int>(tile_bytes / 4); e += kTcThreads) {
+        const float v = X[e];
+        const float h = tf32_hi(v);
+        X[e] = h;
+        Xl[e] = tf32_rn(v - h);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idf = idesc_tf32(128, a.np);
+        const uint32_t xh = smem_u32(X), xl = smem_u32(Xl);
+        const uint32_t wh = smem_u32(base + a.off_wh), wl = smem_u32(base + a.off_wl);
+        uint32_t acc = 0;
+        for (int ks = 0; ks < a.ksteps_f; ++ks) {
+          const uint32_t ao = static_cast<uint32_t>((ks >> 2) * kPanelBytes + (ks & 3) * 32);
+          const uint32_t bo = static_cast<uint32_t>((ks >> 2) * a.wpanel_bytes + (ks & 3) * 32);
+          mma_tf32(d1, desc_kmajor_sw128(xh + ao), desc_kmajor_sw128(wh + bo), idf, acc);
+          acc = 1;
+          mma_tf32(d1, desc_kmajor_sw128(xh + ao), desc_kmajor_sw128(wl + bo), idf, 1);
+          mma_tf32(d1, desc_kmajor_sw128(xl + ao), desc_kmajor_sw128(wh + bo), idf, 1);
+        }
+        mma_commit(&bar_f);
+      }
+      if (!mbar_wait(&bar_f, f_phase, a.spin_limit)) {
+        if (tid == 0) {
+          set_status(a.status, kStatusTimeout);
+          s_abort = 1;
+        }
+      }
+      f_phase ^= 1;
+      __syncthreads();
+      if (s_abort) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c0 = 0; c0 < NP; c0 += 32) tmem_ld32(d1 + (static_cast<uint32_t>(warp * 32) << 16) + c0, q + c0);
+    } else {
+      const unsigned char* Xb = reinterpret_cast<const unsigned char*>(X);
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        q[c] = c < a.k ? *reinterpret_cast<const float*>(Xb + sw128_offset(tid, c, kPanelBytes)) : 0.f;
+    }
+    // rows past the end (only possible for the head block, whose row count
+    // is known on the device) contribute nothing
+    if (rt * kTileRows + tid >= rows) {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) q[c] = 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // X buffer consumed (registers / D1); previous Gram MMAs may still read Q^T
+    if (tid == 0) {   // refill this buffer with the tile two steps ahead
+      const int64_t nt = rt + 2 * static_cast<int64_t>(gridDim.x);
+      if (nt < ntiles) {
+        expect_tx(&bar_tma[buf], tile_bytes);
+        for (int p = 0; p < a.kpanels; ++p)
+          tma_load_2d(base + a.off_x[buf] + p * kPanelBytes, &tmx, p * 32, static_cast<int>(nt * kTileRows),
+                      &bar_tma[buf]);
+      }
+    }
+    if (pending_g) {  // the previous Gram MMAs read Q^T: wait before overwriting it
+      if (!mbar_wait(&bar_g, g_phase, a.spin_limit)) {
+        if (tid == 0) {
+          set_status(a.status, kStatusTimeout);
+          s_abort = 1;
+        }
+      }
+      g_phase ^= 1;
+      pending_g = 0;
+      __syncthreads();
+      if (s_abort) break;
+      if (fresh) flush();  // accumulation window ended with those MMAs
+    }
+    // Q^T hi / lo: thread t writes column t of Q^T (tile row t)
+    {
+      unsigned char* qh = base + a.off_qh;
+      unsigned char* ql = base + a.off_ql;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) {
+        if (c >= a.qrows) break;
+        const float v = q[c];
+        const float h = tf32_hi(v);
+        const int off = sw128_offset(c, tid, a.qpanel_bytes);
+        *reinterpret_cast<float*>(qh + off) = h;
+        *reinterpret_cast<float*>(ql + off) = tf32_rn(v - h);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idg = idesc_tf32(a.mg, a.np);
+      const uint32_t qh = smem_u32(base + a.off_qh), ql = smem_u32(base + a.off_ql);
+      uint32_t acc = fresh ? 0u : 1u;
+      for (int ks = 0; ks < kTileRows / 8; ++ks) {
+        const uint32_t o = static_cast<uint32_t>((ks >> 2) * a.qpanel_bytes + (ks & 3) * 32);
+        mma_tf32(d2, desc_kmajor_sw128(qh + o), desc_kmajor_sw128(qh + o), idg, acc);
+        acc = 1;
+        mma_tf32(d2, desc_kmajor_sw128(qh + o), desc_kmajor_sw128(ql + o), idg, 1);
+        mma_tf32(d2, desc_kmajor_sw128(ql + o), desc_kmajor_sw128(qh + o), idg, 1);
+      }
+      mma_commit(&bar_g);
+    }
+    pending_g = 1;
+    fresh = ((it + 1) % kFlushTiles) == 0;
+  }
+  // drain: the last Gram MMAs, then the final flush
+  if (pending_g) {
+    if (!mbar_wait(&bar_g, g_phase, a.spin_limit)) {
+      if (tid == 0) set_status(a.status, kStatusTimeout);
+      s_abort = 1;
+    }
+    __syncthreads();
+    if (!s_abort) flush();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+struct Geometry {
+  TcArgs a;
+  size_t smem;
+};
+
+Geometry geometry(int k, int kout, bool pass2) {
+  Geometry g{};
+  TcArgs& a = g.a;
+  a.k = k;
+  a.kout = kout;
+  a.kpanels = (k + 31) / 32;
+  a.ksteps_f = (k + 7) / 8;
+  a.np = (kout + 15) / 16 * 16;
+  a.mg = kout <= 64 ? 64 : 128;
+  a.qrows = (kout + 7) / 8 * 8;
+  a.qpanel_bytes = a.qrows * 128;
+  a.wpanel_bytes = a.np * 128;
+  int off = 0;
+  auto take = [&](int bytes) {
+    int o = off;
+    off += (bytes + 1023) / 1024 * 1024;
+    return o;
+  };
+  const int xb = a.kpanels * kPanelBytes;
+  a.off_x[0] = take(xb);
+  a.off_x[1] = take(xb);
+  a.off_xlo = pass2 ? take(xb) : 0;
+  a.off_wh = pass2 ? take(a.kpanels * a.wpanel_bytes) : 0;
+  a.off_wl = pass2 ? take(a.kpanels * a.wpanel_bytes) : 0;
+  a.off_qh = take(4 * a.qpanel_bytes);
+  a.off_ql = take(4 * a.qpanel_bytes);
+  // an M = 64 / 128 Gram reads mg operand rows from each Q^T panel: slack past the end
+  take(a.mg * 128);
+  g.smem = static_cast<size_t>(off) + 1024;  // + alignment of the dynamic base
+  return g;
+}
+
+}  // namespace
+
+// The tensor-core engine handles a Gram block when TMA can address X
+// (k a multiple of 4) and the block fits the 64-column tile.
+bool gram_tc_supported(int k, int kout) { return k % 4 == 0 && k <= 64 && kout <= 64 && encoder() != nullptr; }
+
+cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,
+                                 int kout, double* part, int grid, int32_t* status, int64_t spin_limit,
+                                 cudaStream_t s) {
+  Geometry g = geometry(k, kout, W != nullptr);
+  TcArgs a = g.a;
+  a.rows = rows;
+  a.rows_dev = rows_dev;
+  a.W = W;
+  a.wld = wld;
+  a.part = part;
+  a.status = status;
+  a.spin_limit = spin_limit;
+  CUtensorMap map;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows > 0 ? rows : 1)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(k) * 4};
+  cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kTileRows)};
+  cuuint32_t es[2] = {1, 1};
+  CUresult cr = encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  cudaError_t err;
+  if (a.np <= 32) {
+    err = cudaFuncSetAttribute(gram_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem));
+    if (err != cudaSuccess) return err;
+    gram_tc_kernel<32><<<grid, kTcThreads, g.smem, s>>>(map, a);
+  } else {
+    err = cudaFuncSetAttribute(gram_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem));
+    if (err != cudaSuccess) return err;
+    gram_tc_kernel<64><<<grid, kTcThreads, g.smem, s>>>(map, a);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace figaro

@@ -7,37 +7,78 @@
 // with equal keys in input order, which fixes the order of the QR tail rows
 // inside each key group.
 //
-// Each launch covers both tables: blocks [0, nbA) work on A, the rest on B.
+// Launches (each covers both tables; blocks [0, tiles_A) work on A):
+//   1. key_hist:  one read of the keys: global histograms of all four 8-bit
+//                 digits of the order-preserving uint32 key, and the key range.
+//                 Digits above the highest bit in which min and max differ are
+//                 equal for every key, so only ceil(bits / 8) passes run.
+//   2. sort_pass x4 (passes beyond the needed count return at once): one
+//                 kernel per digit, "one sweep": each 4,096-key tile ranks its
+//                 keys stably in shared memory, publishes its 256 digit counts,
+//                 and finds the counts of all earlier tiles by a decoupled
+//                 look-back (bounded waits).  The last pass writes the final
+//                 perm / sorted keys.
+//   3. runs:      run starts, their count by decoupled look-back, and the run
+//                 index of every sorted row, run keys and run offsets.
+//   4. match:     per run, the size of the run with the same key in the other
+//                 table and the head slot of the key group.
 #include "common.cuh"
 #include "internal.h"
 
 namespace figaro {
 namespace {
 
+constexpr uint64_t kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62;
+constexpr uint64_t kCountMask = (1ull << 62) - 1;
+
 struct TwoTables {
   TableWork t[2];
   DevHeader* h;
-  int nb0;  // blocks belonging to table 0
+  int nb0;  // tiles of table 0
+  int nb;   // tiles of both tables
+  int64_t spin_limit;
 };
 
-__device__ __forceinline__ int table_of_block(const TwoTables& a, int& local) {
-  int b = blockIdx.x;
-  if (b < a.nb0) {
-    local = b;
+__device__ __forceinline__ uint64_t ld_acquire64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release64(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int table_of(const TwoTables& a, int g, int& tile) {
+  if (g < a.nb0) {
+    tile = g;
     return 0;
   }
-  local = b - a.nb0;
+  tile = g - a.nb0;
   return 1;
 }
 
 __device__ __forceinline__ int num_passes(const DevHeader* h, int t) {
-  uint32_t r = h->kmax[t] - h->kmin[t];
-  int bits = r ? 32 - __clz(r) : 0;
+  uint32_t d = h->kmin[t] ^ h->kmax[t];
+  int bits = d ? 32 - __clz(d) : 0;
   int p = (bits + kRadixBits - 1) / kRadixBits;
   return p < 1 ? 1 : p;
 }
 
-__global__ void reset_kernel(DevHeader* h, uint32_t* s0, int n0, uint32_t* s1, int n1) {
+// Bounded wait until the look-back word of a tile is published; returns the
+// word, or 0 after spin_limit polls (the caller records a timeout).
+__device__ __forceinline__ uint64_t wait_word(const uint64_t* p, int64_t limit) {
+  uint64_t v = ld_acquire64(p);
+  int64_t spins = 0;
+  while ((v >> 62) == 0) {
+    if (++spins > limit) return 0;
+    __nanosleep(32);
+    v = ld_acquire64(p);
+  }
+  return v;
+}
+
+__global__ void reset_kernel(DevHeader* h, uint32_t* s0, int n0, uint32_t* s1, int n1, uint64_t* g0, int64_t ng0,
+                             uint64_t* g1, int64_t ng1) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid == 0) {
     h->status = 0;
@@ -49,22 +90,31 @@ __global__ void reset_kernel(DevHeader* h, uint32_t* s0, int n0, uint32_t* s1, i
     h->reduced_rows = 0;
     h->jacobi_sweeps = 0;
   }
-  for (int i = tid; i < n0; i += gridDim.x * blockDim.x) s0[i] = 0u;
-  for (int i = tid; i < n1; i += gridDim.x * blockDim.x) s1[i] = 0u;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = tid; i < n0; i += stride) s0[i] = 0u;
+  for (int i = tid; i < n1; i += stride) s1[i] = 0u;
+  for (int64_t i = tid; i < ng0; i += stride) g0[i] = 0ull;
+  for (int64_t i = tid; i < ng1; i += stride) g1[i] = 0ull;
 }
 
-__global__ void __launch_bounds__(kSortThreads) key_range_kernel(TwoTables a) {
+// Global digit histograms (all kMaxPasses digits) and the key range.
+__global__ void __launch_bounds__(kSortThreads) key_hist_kernel(TwoTables a) {
   int tile;
-  int t = table_of_block(a, tile);
+  const int t = table_of(a, blockIdx.x, tile);
   const TableWork& T = a.t[t];
+  __shared__ uint32_t hist[kMaxPasses][kRadixBins];
+  for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&hist[0][0])[i] = 0u;
+  __syncthreads();
   uint32_t lo = 0xffffffffu, hi = 0u;
-  int64_t base = static_cast<int64_t>(tile) * kSortTile;
+  const int64_t base = static_cast<int64_t>(tile) * kSortTile;
   for (int it = 0; it < kSortItems; ++it) {
-    int64_t i = base + it * kSortThreads + threadIdx.x;
+    const int64_t i = base + it * kSortThreads + threadIdx.x;
     if (i < T.m) {
-      uint32_t u = key_to_ordered(T.key[i]);
+      const uint32_t u = key_to_ordered(T.key[i]);
       lo = min(lo, u);
       hi = max(hi, u);
+#pragma unroll
+      for (int p = 0; p < kMaxPasses; ++p) atomicAdd(&hist[p][(u >> (p * kRadixBits)) & (kRadixBins - 1)], 1u);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -75,112 +125,53 @@ __global__ void __launch_bounds__(kSortThreads) key_range_kernel(TwoTables a) {
     atomicMin(&a.h->kmin[t], lo);
     atomicMax(&a.h->kmax[t], hi);
   }
-}
-
-__device__ __forceinline__ uint32_t load_sort_key(const TableWork& T, const DevHeader* h, int t, int pass,
-                                                  int64_t i) {
-  if (pass == 0) return key_to_ordered(T.key[i]) - h->kmin[t];
-  return T.kb[(pass - 1) & 1][i];
-}
-
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(TwoTables a, int pass) {
-  int tile;
-  int t = table_of_block(a, tile);
-  const TableWork& T = a.t[t];
-  if (pass >= num_passes(a.h, t)) return;
-  __shared__ uint32_t hist[kRadixBins];
-  for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) hist[d] = 0u;
   __syncthreads();
-  int64_t base = static_cast<int64_t>(tile) * kSortTile;
-  int shift = pass * kRadixBits;
-  for (int it = 0; it < kSortItems; ++it) {
-    int64_t i = base + it * kSortThreads + threadIdx.x;
-    if (i < T.m) {
-      uint32_t d = (load_sort_key(T, a.h, t, pass, i) >> shift) & (kRadixBins - 1);
-      atomicAdd(&hist[d], 1u);
-    }
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x)
-    T.hist[static_cast<int64_t>(d) * T.tiles + tile] = hist[d];
-}
-
-// Exclusive scan of one table's digit-major histogram (bins x tiles), in place.
-constexpr int kScanThreads = 1024;
-
-__global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(TwoTables a, int pass) {
-  int t = blockIdx.x;
-  const TableWork& T = a.t[t];
-  if (T.m == 0 || pass >= num_passes(a.h, t)) return;
-  int64_t N = static_cast<int64_t>(kRadixBins) * T.tiles;
-  int64_t per = (N + kScanThreads - 1) / kScanThreads;
-  int64_t lo = per * threadIdx.x;
-  int64_t hi = lo + per < N ? lo + per : N;
-  uint32_t sum = 0;
-  for (int64_t i = lo; i < hi; ++i) sum += T.hist[i];
-  // block exclusive scan of the per-thread sums
-  __shared__ uint32_t wsum[32];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = sum;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = wsum[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    wsum[lane] = w;  // inclusive over warps
-  }
-  __syncthreads();
-  uint32_t run = incl - sum + (warp > 0 ? wsum[warp - 1] : 0u);
-  for (int64_t i = lo; i < hi; ++i) {
-    uint32_t v = T.hist[i];
-    T.hist[i] = run;
-    run += v;
+  for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) {
+    const uint32_t c = (&hist[0][0])[i];
+    if (c) atomicAdd(&T.hist[i], c);
   }
 }
 
-// Stable scatter of one radix pass.  Keys of a tile are ranked in input
-// order: warp w owns keys [w*512, w*512+512) of the tile, visited in 16
-// rounds of 32 consecutive keys; __match_any_sync groups equal digits.
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(TwoTables a, int pass) {
-  int tile;
-  int t = table_of_block(a, tile);
-  const TableWork& T = a.t[t];
-  if (pass >= num_passes(a.h, t)) return;
+// One stable LSD pass over digit `pass`.  Tiles are taken in ticket order,
+// so every earlier tile belongs to a block that is already running.
+__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(TwoTables a, int pass) {
   constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t cnt[kWarps][kRadixBins];
   __shared__ uint32_t sbase[kRadixBins];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kWarps * kRadixBins; i += blockDim.x) (&cnt[0][0])[i] = 0u;
-  for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x)
-    sbase[d] = T.hist[static_cast<int64_t>(d) * T.tiles + tile];
+  __shared__ int s_g;
+  if (threadIdx.x == 0) s_g = static_cast<int>(atomicAdd(&a.h->ticket[4 + pass], 1u));
   __syncthreads();
-  int shift = pass * kRadixBits;
-  int64_t base = static_cast<int64_t>(tile) * kSortTile + warp * (32 * kSortItems);
+  int tile;
+  const int t = table_of(a, s_g, tile);
+  const TableWork& T = a.t[t];
+  const int P = num_passes(a.h, t);
+  if (pass >= P) return;
+  const bool last = pass == P - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kWarps * kRadixBins; i += blockDim.x) (&cnt[0][0])[i] = 0u;
+  __syncthreads();
+  const int shift = pass * kRadixBits;
+  const int64_t base = static_cast<int64_t>(tile) * kSortTile + warp * (32 * kSortItems);
+  const uint32_t* kin = pass == 0 ? nullptr : T.kb[(pass - 1) & 1];
+  const int32_t* vin = pass == 0 ? nullptr : T.vb[(pass - 1) & 1];
   uint32_t key[kSortItems];
   int32_t val[kSortItems];
   uint32_t rank[kSortItems];
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    int64_t i = base + r * 32 + lane;
-    bool valid = i < T.m;
+    const int64_t i = base + r * 32 + lane;
+    const bool valid = i < T.m;
     uint32_t u = 0;
     int32_t v = 0;
     if (valid) {
-      u = load_sort_key(T, a.h, t, pass, i);
-      v = pass == 0 ? static_cast<int32_t>(i) : T.vb[(pass - 1) & 1][i];
+      u = pass == 0 ? key_to_ordered(T.key[i]) : kin[i];
+      v = pass == 0 ? static_cast<int32_t>(i) : vin[i];
     }
     key[r] = u;
     val[r] = v;
-    uint32_t d = valid ? ((u >> shift) & (kRadixBins - 1)) : kRadixBins;  // sentinel bin for padding
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t d = valid ? ((u >> shift) & (kRadixBins - 1)) : kRadixBins;  // padding gets its own bin
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
     if (valid) before = cnt[warp][d];
     __syncwarp();
@@ -189,128 +180,155 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(TwoTables a
     rank[r] = before + __popc(peers & lt_mask);
   }
   __syncthreads();
-  // exclusive prefix over warps, per digit
-  for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
+  // per digit: exclusive prefix over warps, the tile's count, look-back, global base
+  uint64_t* status = T.sort_status + static_cast<int64_t>(pass) * T.tiles * kRadixBins;
+  {
+    const int d = threadIdx.x;  // kSortThreads == kRadixBins
     uint32_t run = 0;
     for (int w = 0; w < kWarps; ++w) {
-      uint32_t c = cnt[w][d];
+      const uint32_t c = cnt[w][d];
       cnt[w][d] = run;
       run += c;
     }
+    uint64_t* mine = status + static_cast<int64_t>(tile) * kRadixBins + d;
+    uint64_t excl = 0;
+    if (tile == 0) {
+      st_release64(mine, kFlagInc | run);
+    } else {
+      st_release64(mine, kFlagAgg | run);
+      for (int j = tile - 1; j >= 0; --j) {
+        const uint64_t w = wait_word(status + static_cast<int64_t>(j) * kRadixBins + d, a.spin_limit);
+        if (w == 0) {
+          set_status(&a.h->status, kStatusTimeout);
+          break;
+        }
+        excl += w & kCountMask;
+        if (w & kFlagInc) break;
+      }
+      st_release64(mine, kFlagInc | (excl + run));
+    }
+    // global exclusive base of digit d for this pass (scan of the histogram)
+    __shared__ uint32_t s_tot[kRadixBins];
+    s_tot[d] = T.hist[pass * kRadixBins + d];
+    __syncthreads();
+    uint32_t gb = 0;
+    for (int e = 0; e < d; ++e) gb += s_tot[e];
+    sbase[d] = gb + static_cast<uint32_t>(excl);
   }
   __syncthreads();
   uint32_t* ko = T.kb[pass & 1];
-  int32_t* vo = T.vb[pass & 1];
+  int32_t* vo = last ? T.perm : T.vb[pass & 1];
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    int64_t i = base + r * 32 + lane;
+    const int64_t i = base + r * 32 + lane;
     if (i < T.m) {
-      uint32_t d = (key[r] >> shift) & (kRadixBins - 1);
-      uint32_t pos = sbase[d] + cnt[warp][d] + rank[r];
-      ko[pos] = key[r];
+      const uint32_t d = (key[r] >> shift) & (kRadixBins - 1);
+      const uint32_t pos = sbase[d] + cnt[warp][d] + rank[r];
+      if (last) {
+        T.sorted_key[pos] = ordered_to_key(key[r]);
+      } else {
+        ko[pos] = key[r];
+      }
       vo[pos] = val[r];
     }
   }
 }
 
-__device__ __forceinline__ const uint32_t* sorted_keys(const TableWork& T, const DevHeader* h, int t) {
-  return T.kb[(num_passes(h, t) - 1) & 1];
-}
-
-// Number of run starts (first row or key change) per tile of sorted keys.
-__global__ void __launch_bounds__(kSortThreads) rle_count_kernel(TwoTables a) {
+// Runs of the sorted keys.  Thread-contiguous rows are staged through shared
+// memory so that global accesses stay coalesced; the run count before each
+// tile comes from a decoupled look-back.
+__global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
+  __shared__ int32_t sk[kSortTile + 1];
+  __shared__ uint32_t s_w[kSortThreads / 32];
+  __shared__ uint64_t s_excl;
+  __shared__ int s_g;
+  if (threadIdx.x == 0) s_g = static_cast<int>(atomicAdd(&a.h->ticket[3], 1u));
+  __syncthreads();
   int tile;
-  int t = table_of_block(a, tile);
+  const int t = table_of(a, s_g, tile);
   const TableWork& T = a.t[t];
-  const uint32_t* u = sorted_keys(T, a.h, t);
-  int64_t base = static_cast<int64_t>(tile) * kSortTile;
-  uint32_t c = 0;
-  for (int it = 0; it < kSortItems; ++it) {
-    int64_t i = base + it * kSortThreads + threadIdx.x;
-    if (i < T.m && (i == 0 || u[i] != u[i - 1])) ++c;
-  }
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  __shared__ uint32_t ws[kSortThreads / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t s = 0;
-    for (int w = 0; w < kSortThreads / 32; ++w) s += ws[w];
-    T.rle_cnt[tile] = s;
-  }
-}
-
-// Writes perm, sorted keys, the run index of every sorted row, and the
-// runs (key, offset).  Each thread owns kSortItems consecutive rows.
-__global__ void __launch_bounds__(kSortThreads) rle_write_kernel(TwoTables a) {
-  int tile;
-  int t = table_of_block(a, tile);
-  const TableWork& T = a.t[t];
-  const DevHeader* h = a.h;
-  int P = num_passes(h, t);
-  const uint32_t* u = T.kb[(P - 1) & 1];
-  const int32_t* v = T.vb[(P - 1) & 1];
-  uint32_t kmin = h->kmin[t];
-  __shared__ uint32_t s_red[kSortThreads / 32];
-  __shared__ uint32_t s_prefix;
-  // runs that start in earlier tiles
-  uint32_t part = 0;
-  for (int i = threadIdx.x; i < tile; i += blockDim.x) part += T.rle_cnt[i];
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t s = 0;
-    for (int w = 0; w < kSortThreads / 32; ++w) s += s_red[w];
-    s_prefix = s;
+  const int64_t base = static_cast<int64_t>(tile) * kSortTile;
+  const int64_t m = T.m;
+  for (int e = threadIdx.x; e < kSortTile + 1; e += blockDim.x) {
+    const int64_t i = base - 1 + e;
+    sk[e] = (i >= 0 && i < m) ? T.sorted_key[i] : 0;
   }
   __syncthreads();
-  int64_t base = static_cast<int64_t>(tile) * kSortTile + static_cast<int64_t>(threadIdx.x) * kSortItems;
+  // flags of my kSortItems consecutive rows
+  const int r0 = threadIdx.x * kSortItems;
   uint32_t flags = 0, c = 0;
+#pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    int64_t i = base + it;
-    if (i < T.m && (i == 0 || u[i] != u[i - 1])) {
+    const int64_t i = base + r0 + it;
+    if (i < m && (i == 0 || sk[r0 + it + 1] != sk[r0 + it])) {
       flags |= 1u << it;
       ++c;
     }
   }
-  // block exclusive scan of c
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t incl = c;
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += y;
   }
-  __shared__ uint32_t s_w[kSortThreads / 32];
-  __syncthreads();
   if (lane == 31) s_w[warp] = incl;
   __syncthreads();
-  uint32_t wpre = 0;
-  for (int w = 0; w < warp; ++w) wpre += s_w[w];
-  int64_t run = static_cast<int64_t>(s_prefix) + wpre + incl - c - 1;  // run of the row before my first
+  uint32_t wpre = 0, tile_total = 0;
+  for (int w = 0; w < kSortThreads / 32; ++w) {
+    if (w < warp) wpre += s_w[w];
+    tile_total += s_w[w];
+  }
+  if (threadIdx.x == 0) {
+    uint64_t* mine = T.run_status + tile;
+    uint64_t excl = 0;
+    if (tile == 0) {
+      st_release64(mine, kFlagInc | tile_total);
+    } else {
+      st_release64(mine, kFlagAgg | tile_total);
+      for (int j = tile - 1; j >= 0; --j) {
+        const uint64_t w = wait_word(T.run_status + j, a.spin_limit);
+        if (w == 0) {
+          set_status(&a.h->status, kStatusTimeout);
+          break;
+        }
+        excl += w & kCountMask;
+        if (w & kFlagInc) break;
+      }
+      st_release64(mine, kFlagInc | (excl + tile_total));
+    }
+    s_excl = excl;
+  }
+  __syncthreads();
+  int64_t run = static_cast<int64_t>(s_excl) + wpre + incl - c - 1;  // run of the row before my first
+  int32_t segs[kSortItems];
+#pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    int64_t i = base + it;
-    if (i >= T.m) break;
-    int32_t key = ordered_to_key(u[i] + kmin);
+    const int64_t i = base + r0 + it;
     if (flags & (1u << it)) {
       ++run;
-      T.run_key[run] = key;
+      T.run_key[run] = sk[r0 + it + 1];
       T.run_off[run] = static_cast<int32_t>(i);
     }
-    T.perm[i] = v[i];
-    T.sorted_key[i] = key;
-    T.seg[i] = static_cast<int32_t>(run);
-    if (i == T.m - 1) {
+    segs[it] = static_cast<int32_t>(run);
+    if (i == m - 1) {
       a.h->num_runs[t] = run + 1;
-      T.run_off[run + 1] = static_cast<int32_t>(T.m);
+      T.run_off[run + 1] = static_cast<int32_t>(m);
     }
+  }
+  __syncthreads();  // reuse sk for the run indices, written back coalesced
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) sk[r0 + it] = segs[it];
+  __syncthreads();
+  for (int e = threadIdx.x; e < kSortTile; e += blockDim.x) {
+    const int64_t i = base + e;
+    if (i < m) T.seg[i] = sk[e];
   }
 }
 
 __device__ __forceinline__ int64_t lower_bound_key(const int32_t* keys, int64_t n, int32_t k) {
   int64_t lo = 0, hi = n;
   while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
+    const int64_t mid = (lo + hi) >> 1;
     if (keys[mid] < k)
       lo = mid + 1;
     else
@@ -323,18 +341,18 @@ __device__ __forceinline__ int64_t lower_bound_key(const int32_t* keys, int64_t 
 // the other table (0 if none) and the head slot of the key group (the run
 // index on A's side).
 __global__ void match_kernel(TwoTables a) {
-  int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   DevHeader* h = a.h;
   const TableWork& A = a.t[0];
   const TableWork& B = a.t[1];
-  int64_t UA = h->num_runs[0], UB = h->num_runs[1];
+  const int64_t UA = h->num_runs[0], UB = h->num_runs[1];
   if (i < UA) {
-    int32_t k = A.run_key[i];
-    int64_t j = lower_bound_key(B.run_key, UB, k);
-    int32_t mine = A.run_off[i + 1] - A.run_off[i];
+    const int32_t k = A.run_key[i];
+    const int64_t j = lower_bound_key(B.run_key, UB, k);
+    const int32_t mine = A.run_off[i + 1] - A.run_off[i];
     A.hdslot[i] = static_cast<int32_t>(i);
     if (j < UB && B.run_key[j] == k) {
-      int32_t other = B.run_off[j + 1] - B.run_off[j];
+      const int32_t other = B.run_off[j + 1] - B.run_off[j];
       A.other[i] = other;
       atomicAdd(reinterpret_cast<unsigned long long*>(&h->num_groups), 1ull);
       atomicAdd(reinterpret_cast<unsigned long long*>(&h->reduced_rows),
@@ -344,8 +362,8 @@ __global__ void match_kernel(TwoTables a) {
     }
   }
   if (i < UB) {
-    int32_t k = B.run_key[i];
-    int64_t j = lower_bound_key(A.run_key, UA, k);
+    const int32_t k = B.run_key[i];
+    const int64_t j = lower_bound_key(A.run_key, UA, k);
     if (j < UA && A.run_key[j] == k) {
       B.other[i] = A.run_off[j + 1] - A.run_off[j];
       B.hdslot[i] = static_cast<int32_t>(j);
@@ -358,16 +376,33 @@ __global__ void match_kernel(TwoTables a) {
 
 }  // namespace
 
+// Look-back words of the grouping step per table: kMaxPasses x tiles x bins
+// for the sort, tiles for the runs, and the kMaxPasses x bins histogram.
+int64_t group_status_words(int tiles) {
+  return static_cast<int64_t>(kMaxPasses) * tiles * kRadixBins + tiles;
+}
+
 cudaError_t launch_reset(const Plan& p, cudaStream_t s) {
-  int n0 = p.t[0].chunks, n1 = p.t[1].chunks;
-  int work = n0 > n1 ? n0 : n1;
-  int blocks = (work + 255) / 256;
+  const int n0 = p.t[0].chunks, n1 = p.t[1].chunks;
+  const int64_t g0 = p.t[0].tiles > 0 ? group_status_words(p.t[0].tiles) : 0;
+  const int64_t g1 = p.t[1].tiles > 0 ? group_status_words(p.t[1].tiles) : 0;
+  int64_t work = n0 > n1 ? n0 : n1;
+  if (g0 > work) work = g0;
+  if (g1 > work) work = g1;
+  int blocks = static_cast<int>((work + 255) / 256);
   if (blocks < 1) blocks = 1;
-  if (blocks > 64) blocks = 64;
+  if (blocks > 1024) blocks = 1024;
   uint32_t* s0 = p.t[0].chunk_status;
   uint32_t* s1 = p.t[1].chunk_status;
-  reset_kernel<<<blocks, 256, 0, s>>>(p.hdr, s0, s0 ? n0 : 0, s1, s1 ? n1 : 0);
+  reset_kernel<<<blocks, 256, 0, s>>>(p.hdr, s0, s0 ? n0 : 0, s1, s1 ? n1 : 0, p.t[0].sort_status, g0,
+                                      p.t[1].sort_status, g1);
   count_launches(1);
+  // the histograms are accumulated with atomics: clear them too
+  for (int t = 0; t < 2; ++t)
+    if (p.t[t].m > 0) {
+      cudaError_t e = cudaMemsetAsync(p.t[t].hist, 0, sizeof(uint32_t) * kMaxPasses * kRadixBins, s);
+      if (e != cudaSuccess) return e;
+    }
   return cudaGetLastError();
 }
 
@@ -377,20 +412,16 @@ cudaError_t launch_grouping(const Plan& p, cudaStream_t s) {
   a.t[1] = p.t[1];
   a.h = p.hdr;
   a.nb0 = p.t[0].tiles;
-  int nb = p.t[0].tiles + p.t[1].tiles;
-  if (nb == 0) return cudaSuccess;
-  key_range_kernel<<<nb, kSortThreads, 0, s>>>(a);
-  for (int pass = 0; pass < kMaxPasses; ++pass) {
-    radix_hist_kernel<<<nb, kSortThreads, 0, s>>>(a, pass);
-    radix_scan_kernel<<<2, kScanThreads, 0, s>>>(a, pass);
-    radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(a, pass);
-  }
-  rle_count_kernel<<<nb, kSortThreads, 0, s>>>(a);
-  rle_write_kernel<<<nb, kSortThreads, 0, s>>>(a);
-  int64_t mm = p.t[0].m > p.t[1].m ? p.t[0].m : p.t[1].m;
-  int mb = static_cast<int>((mm + 255) / 256);
+  a.nb = p.t[0].tiles + p.t[1].tiles;
+  a.spin_limit = p.spin_limit;
+  if (a.nb == 0) return cudaSuccess;
+  key_hist_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
+  for (int pass = 0; pass < kMaxPasses; ++pass) sort_pass_kernel<<<a.nb, kSortThreads, 0, s>>>(a, pass);
+  runs_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
+  const int64_t mm = p.t[0].m > p.t[1].m ? p.t[0].m : p.t[1].m;
+  const int mb = static_cast<int>((mm + 255) / 256);
   if (mb > 0) match_kernel<<<mb, 256, 0, s>>>(a);
-  count_launches(1 + 3 * kMaxPasses + 2 + (mb > 0 ? 1 : 0));
+  count_launches(2 + kMaxPasses + (mb > 0 ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -46,8 +46,9 @@ struct TableWork {
   // grouping
   uint32_t* kb[2] = {nullptr, nullptr};
   int32_t* vb[2] = {nullptr, nullptr};
-  uint32_t* hist = nullptr;  // kRadixBins * tiles
-  uint32_t* rle_cnt = nullptr;
+  uint32_t* hist = nullptr;          // kMaxPasses x kRadixBins global digit counts
+  uint64_t* sort_status = nullptr;   // look-back words: kMaxPasses x tiles x kRadixBins
+  uint64_t* run_status = nullptr;    // look-back words: tiles
   int tiles = 0;
   int32_t* perm = nullptr;
   int32_t* sorted_key = nullptr;
@@ -92,6 +93,9 @@ struct Plan {
   int32_t* active = nullptr;
   int num_sms = 148;
 };
+
+// Look-back words the grouping step needs per table (sort passes + runs).
+int64_t group_status_words(int tiles);
 
 // Host-side count of kernel launches (figaro_kernel_launches()).
 void count_launches(int n);

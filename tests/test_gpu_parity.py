@@ -242,6 +242,23 @@ def test_host_buffers_match_device_call(fg, torch):
     assert np.array_equal(R.numpy(), Rd) and np.array_equal(s.numpy(), sd)
 
 
+@pytest.mark.parametrize("shape", [(50000, 16, 40000, 16, 500), (30000, 32, 20000, 32, 300), (20000, 4, 30000, 8, 100),
+                                   (9000, 12, 7000, 20, 50)])
+def test_gram_engines_agree_with_oracle(fg, torch, shape):
+    """The tensor-core (tcgen05, 3xTF32) and CUDA-core Gram engines both meet
+    the mixed-path bar, and agree with each other."""
+    m1, n1, m2, n2, K = shape
+    A, B = make_pair(m1, n1, m2, n2, K, np.float32, "normal", seed=m1 + n1)
+    Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key)
+    out = {}
+    for eng in (fg.GRAM_SIMT, fg.GRAM_TCGEN05):
+        R, s = fg.join_qr_svd(dev(torch, A), dev(torch, B), path="mixed", gram_engine=eng)
+        R, s = R.cpu().numpy(), s.cpu().numpy()
+        assert rel(R, Rref) <= 1e-6 and rel(s, sref) <= 1e-6, (eng, rel(R, Rref), rel(s, sref))
+        out[eng] = R
+    assert rel(out[fg.GRAM_SIMT], out[fg.GRAM_TCGEN05]) <= 1e-6
+
+
 # ---------------------------------------------------------- status codes --
 
 def test_status_codes(fg, torch):
