@@ -185,13 +185,19 @@ void oracle_sign_normalise(double* R, int n) {
 /* Cyclic sweeps over column pairs, each rotation chosen from the 2 x 2 Gram */
 /* matrix of the pair so that the two columns become orthogonal.             */
 /* sigma: the column norms at convergence, descending.  Returns sweeps used,  */
-/* or -1 if max_sweeps was reached before convergence.                       */
+/* or -1 if max_sweeps was reached before convergence.  A column whose       */
+/* squared norm is at most (n 2^-53)^2 ||R||_F^2 is rounding noise of a      */
+/* rank-deficient R (a zero singular value) and is left out of rotations:    */
+/* the relative orthogonality test can never be met by such columns.         */
 /* ------------------------------------------------------------------------ */
 int oracle_jacobi_sigma(const double* Rin, int n, double* sigma, int max_sweeps) {
   double* U = (double*)malloc(sizeof(double) * (size_t)n * n); /* column-major */
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) U[(int64_t)j * n + i] = Rin[(int64_t)i * n + j];
   const double tol = (double)n * 1.1102230246251565e-16; /* n * 2^-53 */
+  double fro2 = 0.0;
+  for (int64_t e = 0; e < (int64_t)n * n; ++e) fro2 += U[e] * U[e];
+  const double negligible = tol * tol * fro2;
   int sweeps = 0, converged = 0;
   while (sweeps < max_sweeps) {
     double off = 0.0;
@@ -205,7 +211,7 @@ int oracle_jacobi_sigma(const double* Rin, int n, double* sigma, int max_sweeps)
           b += uq[i] * uq[i];
           g += up[i] * uq[i];
         }
-        if (a == 0.0 || b == 0.0 || g == 0.0) continue;
+        if (a <= negligible || b <= negligible || g == 0.0) continue;
         double rel = fabs(g) / sqrt(a * b);
         if (rel > off) off = rel;
         if (rel <= tol) continue;
