@@ -244,6 +244,7 @@ def main():
         if world > 1:
             dist.barrier()
     clocks = clk.summary()
+    info = solver.info(stream)
     status = solver.status(stream)
     if status != 0:
         raise fg.FigaroError(status, "timed steps")
@@ -343,7 +344,7 @@ def main():
                            "graph": graph is not None,
                            "l2": "inputs 136 MB + ~300 MB workspace exceed L2; 256 MB flush between steps"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-                "clocks": clocks, "phases_ms": phases, "fp64_path": fp64, "materialized_baseline": mat}
+                "clocks": clocks, "phases_ms": phases, "instance": info, "fp64_path": fp64, "materialized_baseline": mat}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

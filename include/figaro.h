@@ -204,6 +204,20 @@ FIGARO_API figaro_status figaro_batch_join(int32_t count, const figaro_table* A,
  * using workspace `ws` recorded (FIGARO_OK when nothing went wrong).        */
 FIGARO_API figaro_status figaro_get_status(const void* ws, void* stream);
 
+/* Facts about the last call that used workspace `ws` (waits for `stream`):
+ * distinct keys of A and of B, keys present in both (key groups), rows of
+ * the reduced matrix (sum over groups of m1g + m2g - 1), Jacobi sweeps run. */
+typedef struct figaro_info {
+  int64_t num_runs_a;
+  int64_t num_runs_b;
+  int64_t num_groups;
+  int64_t reduced_rows;
+  int32_t jacobi_sweeps;
+  int32_t reserved;
+} figaro_info;
+
+FIGARO_API figaro_status figaro_get_info(const void* ws, void* stream, figaro_info* info);
+
 /* Static English text for a status code. */
 FIGARO_API const char* figaro_status_string(figaro_status status);
 

@@ -57,6 +57,11 @@ class Options(ctypes.Structure):
                 ("phase_events", ctypes.c_void_p)]
 
 
+class Info(ctypes.Structure):
+    _fields_ = [("num_runs_a", ctypes.c_int64), ("num_runs_b", ctypes.c_int64), ("num_groups", ctypes.c_int64),
+                ("reduced_rows", ctypes.c_int64), ("jacobi_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class Grouping(ctypes.Structure):
     _fields_ = [("perm", ctypes.c_void_p), ("sorted_key", ctypes.c_void_p), ("run_key", ctypes.c_void_p),
                 ("run_offset", ctypes.c_void_p), ("other_count", ctypes.c_void_p), ("num_runs", ctypes.c_void_p)]
@@ -64,7 +69,8 @@ class Grouping(ctypes.Structure):
 
 EXPORTS = ["figaro_default_options", "figaro_workspace_size", "figaro_join_group", "figaro_join_head_tail",
            "figaro_join_qr_r", "figaro_join_singular_values", "figaro_batch_workspace_size", "figaro_batch_join",
-           "figaro_get_status", "figaro_status_string", "figaro_version", "figaro_kernel_launches"]
+           "figaro_get_status", "figaro_get_info", "figaro_status_string", "figaro_version",
+           "figaro_kernel_launches"]
 NUM_PHASE_EVENTS = 9
 PHASES = ["grouping", "head_tail_a", "head_tail_b", "gram1", "chol1", "gram2", "chol2", "jacobi"]
 FLAG_TEST_WITHHOLD = 1 << 8
@@ -93,6 +99,7 @@ def library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.figaro_batch_workspace_size.argtypes = [I32, P(Table), P(Table), P(Options), P(sz)]
         lib.figaro_batch_join.argtypes = [I32, P(Table), P(Table), P(Options), P(vp), P(vp), vp, sz, vp]
         lib.figaro_get_status.argtypes = [vp, vp]
+        lib.figaro_get_info.argtypes = [vp, vp, P(Info)]
         lib.figaro_status_string.argtypes = [ctypes.c_int]
         lib.figaro_status_string.restype = ctypes.c_char_p
         lib.figaro_version.restype = I32
@@ -291,6 +298,9 @@ class Solver:
     def status(self, stream=None) -> int:
         return get_status(self.ws, stream)
 
+    def info(self, stream=None) -> dict:
+        return get_info(self.ws, stream)
+
 
 def join_qr_r(A, B, stream=None, **opts):
     """R of QR(J) as an (n x n) float64 device tensor."""
@@ -369,6 +379,15 @@ def batch_join(pairs, stream=None, workspace=None, **opts):
     _check(lib.figaro_batch_join(count, TA, TB, ctypes.byref(o), Rp, Sp, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                  _stream_handle(stream)), "figaro_batch_join")
     return outs, ws
+
+
+def get_info(workspace, stream=None) -> dict:
+    """Key runs, key groups, reduced rows and Jacobi sweeps of the last call."""
+    lib = library()
+    out = Info()
+    _check(lib.figaro_get_info(ctypes.c_void_p(workspace.data_ptr()), _stream_handle(stream), ctypes.byref(out)),
+           "figaro_get_info")
+    return {f: int(getattr(out, f)) for f, _ in Info._fields_ if f != "reserved"}
 
 
 def get_status(workspace, stream=None) -> int:

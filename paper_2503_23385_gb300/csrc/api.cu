@@ -459,6 +459,22 @@ figaro_status figaro_get_status(const void* ws, void* stream) {
   return FIGARO_OK;
 }
 
+figaro_status figaro_get_info(const void* ws, void* stream, figaro_info* info) {
+  if (!ws || !info) return FIGARO_ERR_INVALID_ARG;
+  figaro_status st = bind_device(ws);
+  if (st != FIGARO_OK) return st;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return FIGARO_ERR_CUDA;
+  DevHeader h;
+  if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return FIGARO_ERR_CUDA;
+  info->num_runs_a = h.num_runs[0];
+  info->num_runs_b = h.num_runs[1];
+  info->num_groups = h.num_groups;
+  info->reduced_rows = h.reduced_rows;
+  info->jacobi_sweeps = h.jacobi_sweeps;
+  info->reserved = 0;
+  return FIGARO_OK;
+}
+
 const char* figaro_status_string(figaro_status s) {
   switch (s) {
     case FIGARO_OK: return "ok";

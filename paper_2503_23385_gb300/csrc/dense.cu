@@ -1,19 +1,27 @@
-// Small dense n x n steps of CholeskyQR2 and the singular values.
+// Small dense n x n steps of CholeskyQR2 and the singular values.  One CTA
+// per instance (n <= 128), everything in shared memory.
 //
-//  * chol_first:  R1 = chol(G1) (FP64, semi-definite: a pivot below
-//                 rank_tol * G1_kk marks column k as dependent and gives a
-//                 zero row), W = R1^{-1} on the independent columns.
-//  * chol_second: R2 = chol(G2) on the same columns, R = R2 R1 (FP64); the
-//                 diagonal is positive, so R already has the sign convention
-//                 of Section 1 (R is the Cholesky factor of J^T J).
+//  * chol_first:  R1 = chol(G1), semi-definite: a pivot below
+//                 rank_tol * G1_kk marks column k as dependent (zero row);
+//                 W = R1^{-1} on the independent columns.
+//  * chol_second: R2 = chol(G2) on the same columns, R = R2 R1 in FP64.  The
+//                 diagonal is positive, so R has the sign convention of
+//                 Section 1 (R is the Cholesky factor of J^T J).
 //  * jacobi:      one-sided (Hestenes) Jacobi on the columns of R (Section 3:
 //                 the singular values of J are those of R), parallel
 //                 round-robin ordering, one thread group per column pair.
-//                 Plain path: FP64 sweeps, sigma = column norms.  Mixed
-//                 path: FP32 sweeps accumulating V, then sigma_j =
-//                 ||R v_j|| / ||v_j|| in FP64 (a Rayleigh quotient, so the
-//                 FP32 error of v_j enters only to second order).
-// All three run as one CTA per instance (n <= 128).
+//
+// Precision.  Plain path: every step in FP64.  Mixed path: the two Cholesky
+// factorisations and the inverse run in FP32 -- R1 is only a preconditioner
+// (its rounding is removed by the second pass, and W is the exact inverse
+// used to form Q), and G2 = I + O(u) so R2 = chol(G2) in FP32 has an absolute
+// error of a few FP32 ulps -- while R = R2 R1 is formed in FP64; the Jacobi
+// sweeps run in FP32 accumulating V and each singular value is then the FP64
+// Rayleigh quotient ||R v_j|| / ||v_j||, whose error is second order in the
+// FP32 error of v_j.  FP64 dependent chains are slow on this GPU (tens of
+// cycles per FMA, hundreds per sqrt or divide), so the FP64 pivots use an
+// FP32 seed refined by two Newton steps for 1/sqrt(d), and dot products are
+// split across lanes.
 #include <cmath>
 
 #include "common.cuh"
@@ -22,113 +30,172 @@
 namespace figaro {
 namespace {
 
+// 1/sqrt(d) for d > 0: FP32 estimate refined by Newton's iteration
+// y <- y (3 - d y^2) / 2 (quadratic convergence; two steps from ~2^-23).
+__device__ __forceinline__ double rsqrt_pivot(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = static_cast<double>(rsqrtf(static_cast<float>(d)));
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+__device__ __forceinline__ float rsqrt_pivot(float d) { return __frsqrt_rn(d); }
+
 // In-place semi-definite Cholesky of the n x n matrix A (shared memory,
-// row-major, upper triangle used).  act[k] (in/out): columns marked 0 on
-// entry stay dependent.  Returns via A the upper factor with zero rows for
-// dependent columns.
-__device__ void chol_inplace(double* A, int n, const double* diag0, int32_t* act, double tol, int32_t* status) {
-  __shared__ double s_inv;
+// row-major, upper triangle used).  act[k]: columns marked 0 on entry stay
+// dependent.  On return the upper triangle holds the factor R.
+template <typename T>
+__device__ void chol_inplace(T* A, int n, const T* diag0, int32_t* act, T tol, T* y, int32_t* status) {
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {
-      double d = A[k * n + k];
+      const T d = A[k * n + k];
       int ok = act[k];
       if (!isfinite(d)) {
         set_status(status, kStatusNotSpd);
         ok = 0;
       }
-      if (!(d > tol * diag0[k]) || !(diag0[k] > 0.0)) ok = 0;
+      if (!(d > tol * diag0[k]) || !(diag0[k] > T(0))) ok = 0;
       act[k] = ok;
-      if (ok) {
-        double r = sqrt(d);
-        A[k * n + k] = r;
-        s_inv = 1.0 / r;
-      } else {
-        A[k * n + k] = 0.0;
-        s_inv = 0.0;
-      }
+      y[k] = ok ? rsqrt_pivot(d) : T(0);
     }
     __syncthreads();
-    const double inv = s_inv;
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) A[k * n + j] *= inv;
-    __syncthreads();
-    if (inv != 0.0) {
+    const T yk = y[k];
+    if (yk != T(0)) {
+      const T y2 = yk * yk;
       const int m = n - k - 1;  // trailing (i, j) with k < i <= j < n
       for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int a = e / m, b = e - a * m;
+        const int a = e / m, b = e - a * m;
         if (b < a) continue;
-        int i = k + 1 + a, j = k + 1 + b;
-        A[i * n + j] -= A[k * n + i] * A[k * n + j];
+        const int i = k + 1 + a, j = k + 1 + b;
+        A[i * n + j] -= (A[k * n + i] * y2) * A[k * n + j];
       }
     }
+    __syncthreads();
+  }
+  // scale rows: R[k][j] = A[k][j] y[k] for j >= k (R[k][k] = sqrt(d_k))
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    if (j >= i) A[e] *= y[i];
+  }
+  __syncthreads();
+}
+
+// Warp-cooperative in-place inverse of the upper-triangular R (n x n, shared
+// memory) on the independent columns: column j of W needs W's leading j x j
+// block and column j of R only.
+template <typename T>
+__device__ void tri_inverse_inplace(T* A, int n, const int32_t* act, T* x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < n; ++j) {
+    const bool aj = act[j] != 0;
+    for (int i = warp; i < j; i += nw) {
+      T s = T(0);
+      if (aj && act[i])
+        for (int k = i + lane; k < j; k += 32) s += A[i * n + k] * A[k * n + j];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) x[i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) A[j * n + j] = aj ? T(1) / A[j * n + j] : T(0);
+    __syncthreads();
+    const T wjj = A[j * n + j];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) A[i * n + j] = (aj && act[i]) ? -x[i] * wjj : T(0);
     __syncthreads();
   }
 }
 
+template <typename T>
 __global__ void chol_first_kernel(const double* G, int n, double tol, double* R1, double* W, float* Wf,
                                   int32_t* active, int32_t* status) {
-  extern __shared__ double sm[];
-  double* A = sm;                // n x n
-  double* diag0 = sm + n * n;    // n
-  int32_t* act = reinterpret_cast<int32_t*>(diag0 + n);
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = G[e];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* A = reinterpret_cast<T*>(smraw);  // n x n
+  T* diag0 = A + n * n;
+  T* y = diag0 + n;
+  T* x = y + n;
+  int32_t* act = reinterpret_cast<int32_t*>(x + n);
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = static_cast<T>(G[e]);
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    diag0[k] = G[k * n + k];
+    diag0[k] = static_cast<T>(G[k * n + k]);
     act[k] = 1;
   }
   __syncthreads();
-  chol_inplace(A, n, diag0, act, tol, status);
+  chol_inplace<T>(A, n, diag0, act, static_cast<T>(tol), y, status);
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int i = e / n, j = e % n;
-    R1[e] = (j >= i && act[i]) ? A[e] : 0.0;
+    const int i = e / n, j = e % n;
+    R1[e] = (j >= i && act[i]) ? static_cast<double>(A[e]) : 0.0;
   }
   for (int k = threadIdx.x; k < n; k += blockDim.x) active[k] = act[k];
   __syncthreads();
-  // W = R1^{-1} on the independent columns, in place (column j of W needs
-  // only W's leading j x j block and column j of R1).
-  double* x = diag0;  // reuse as a length-n temporary
-  for (int j = 0; j < n; ++j) {
-    const bool aj = act[j] != 0;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
-      double s = 0.0;
-      if (aj && act[i])
-        for (int k = i; k < j; ++k) s += A[i * n + k] * A[k * n + j];
-      x[i] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) A[j * n + j] = aj ? 1.0 / A[j * n + j] : 0.0;
-    __syncthreads();
-    const double wjj = A[j * n + j];
-    for (int i = threadIdx.x; i < j; i += blockDim.x) A[i * n + j] = (aj && act[i]) ? -x[i] * wjj : 0.0;
-    __syncthreads();
-  }
+  tri_inverse_inplace<T>(A, n, act, x);
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int i = e / n, j = e % n;
-    double w = (j >= i) ? A[e] : 0.0;
+    const int i = e / n, j = e % n;
+    double w = (j >= i) ? static_cast<double>(A[e]) : 0.0;
+    if (sizeof(T) == 4) {
+      // the value both Gram engines use exactly: hi (TF32) + lo rounded to TF32
+      const float v = static_cast<float>(w);
+      const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+      const float l = __uint_as_float((__float_as_uint(v - h) + 0x1000u) & 0xFFFFE000u);
+      w = static_cast<double>(h + l);
+    }
     W[e] = w;
     Wf[e] = static_cast<float>(w);
   }
 }
 
-__global__ void chol_second_kernel(const double* G2, int n, double tol, const double* R1, const int32_t* active,
-                                   double* R, double* R_out, int64_t ldr, int32_t* status) {
-  extern __shared__ double sm[];
-  double* A = sm;
-  double* diag0 = sm + n * n;
-  int32_t* act = reinterpret_cast<int32_t*>(diag0 + n);
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = G2[e];
+// Upper-triangular product C = A B on n x n row-major matrices, one thread
+// per output, two partial sums to shorten the FP64 dependency chain.
+template <typename TA, typename TB>
+__device__ __forceinline__ double upper_dot(const TA* A, const TB* B, int n, int i, int j) {
+  double s0 = 0.0, s1 = 0.0;
+  int k = i;
+  for (; k + 1 <= j; k += 2) {
+    s0 += static_cast<double>(A[i * n + k]) * static_cast<double>(B[k * n + j]);
+    s1 += static_cast<double>(A[i * n + k + 1]) * static_cast<double>(B[(k + 1) * n + j]);
+  }
+  if (k <= j) s0 += static_cast<double>(A[i * n + k]) * static_cast<double>(B[k * n + j]);
+  return s0 + s1;
+}
+
+template <typename T>
+__global__ void chol_second_kernel(const double* G2, int n, double tol, const double* R1, const double* Wd,
+                                   const int32_t* active, int refine, double* Xg, double* R, double* R_out,
+                                   int64_t ldr, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* A = reinterpret_cast<T*>(smraw);
+  T* diag0 = A + n * n;
+  T* y = diag0 + n;
+  int32_t* act = reinterpret_cast<int32_t*>(y + n);
+  double* E = reinterpret_cast<double*>(smraw + ((sizeof(T) * (static_cast<size_t>(n) * n + 2 * n) +
+                                                  sizeof(int32_t) * n + 15) & ~static_cast<size_t>(15)));
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = static_cast<T>(G2[e]);
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    diag0[k] = G2[k * n + k];
+    diag0[k] = static_cast<T>(G2[k * n + k]);
     act[k] = active[k];
   }
   __syncthreads();
-  chol_inplace(A, n, diag0, act, tol, status);
-  // R = R2 R1 (both upper triangular); rows of dependent columns are zero
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int i = e / n, j = e % n;
-    double s = 0.0;
-    if (j >= i && act[i]) {
-      for (int k = i; k <= j; ++k) s += A[i * n + k] * R1[k * n + j];
+  const double* X = R1;
+  if (refine) {
+    // Q was formed with W, so the consistent factor is R2 W^{-1}; one Newton
+    // step X = R1 + R1 (I - W R1) squares the relative error of R1 as an
+    // inverse of W (FP32 level -> FP64 level)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e % n;
+      E[e] = (j >= i && act[i] && act[j]) ? (i == j ? 1.0 : 0.0) - upper_dot(Wd, R1, n, i, j) : 0.0;
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e % n;
+      Xg[e] = (j >= i && act[i]) ? R1[e] + upper_dot(R1, E, n, i, j) : 0.0;
+    }
+    __threadfence_block();
+    __syncthreads();
+    X = Xg;
+  }
+  chol_inplace<T>(A, n, diag0, act, static_cast<T>(tol), y, status);
+  // R = R2 X (both upper triangular) in FP64; rows of dependent columns are zero
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    const double s = (j >= i && act[i]) ? upper_dot(A, X, n, i, j) : 0.0;
     R[e] = s;
     if (R_out) R_out[static_cast<int64_t>(i) * ldr + j] = s;
   }
@@ -140,28 +207,61 @@ __device__ __forceinline__ T group_sum(T v, int width) {
   return v;
 }
 
-// One-sided Jacobi.  U (and V) column-major in shared memory.
-template <typename T, bool kWithV>
-__global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, int tpp, double* sigma,
+// Rotation (c, s) that makes columns p and q orthogonal, from their 2 x 2
+// Gram [al ga; ga be]: t = sign(z) / (|z| + sqrt(1 + z^2)), z = (be - al) / (2 ga).
+__device__ __forceinline__ void rotation(float al, float be, float ga, float& c, float& s) {
+  const float z = __fdividef(be - al, 2.f * ga);
+  const float az = fabsf(z);
+  const float t = az > 1e18f ? __fdividef(0.5f, z) : copysignf(__frcp_rn(az + __fsqrt_rn(1.f + z * z)), z);
+  c = __frsqrt_rn(1.f + t * t);
+  s = c * t;
+}
+__device__ __forceinline__ void rotation(double al, double be, double ga, double& c, double& s) {
+  const double z = (be - al) / (2.0 * ga);
+  const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = c * t;
+}
+
+// One-sided Jacobi.  U (and V) column-major in shared memory; a warp per
+// column pair, NPL elements of each column per lane; the round-robin pairing
+// is tabulated once.  A pair is rotated while |u_p.u_q|^2 > tol^2 |u_p|^2 |u_q|^2.
+template <typename T, bool kWithV, int NPL>
+__global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in, double* sigma,
                               int32_t* status, int32_t* sweeps_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int np = n + (n & 1);  // even number of columns (one zero column if n is odd)
+  const int npairs = np / 2, rounds = np - 1;
   T* U = reinterpret_cast<T*>(smraw);
   T* V = U + static_cast<int64_t>(np) * n;
   double* sig = reinterpret_cast<double*>(smraw + sizeof(T) * static_cast<size_t>(np) * n * (kWithV ? 2 : 1));
-  __shared__ int s_rot;
+  double* Rs = sig + np;  // R (FP64) for the Rayleigh quotients, when it fits
+  short2* pairs = reinterpret_cast<short2*>(Rs + ((kWithV && n <= 64) ? n * n : 0));
+  const bool r_in_smem = kWithV && n <= 64;
+  __shared__ T s_fro;
   for (int e = threadIdx.x; e < np * n; e += blockDim.x) {
-    int c = e / n, r = e % n;
+    const int c = e / n, r = e % n;
     U[e] = c < n ? static_cast<T>(R[static_cast<int64_t>(r) * ldr + c]) : T(0);
     if (kWithV) V[e] = (c == r) ? T(1) : T(0);
   }
+  if (r_in_smem)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rs[e] = R[static_cast<int64_t>(e / n) * ldr + e % n];
+  for (int e = threadIdx.x; e < rounds * npairs; e += blockDim.x) {
+    const int round = e / npairs, g = e % npairs;
+    int p = g == 0 ? round : (round + g) % (np - 1);
+    int q = g == 0 ? np - 1 : (round - g + (np - 1)) % (np - 1);
+    if (p > q) {
+      const int t = p;
+      p = q;
+      q = t;
+    }
+    pairs[e] = make_short2(static_cast<short>(p), static_cast<short>(q));
+  }
   __syncthreads();
-  // rotate while |u_p . u_q| > tol ||u_p|| ||u_q||; 4 n eps leaves room for the rounding of the dot products
   const T eps = sizeof(T) == 4 ? T(5.9604645e-8) : T(1.1102230246251565e-16);
-  const T tol = T(4) * static_cast<T>(n) * eps;
+  const T tol2 = static_cast<T>(tol_in) * static_cast<T>(tol_in);
   // columns whose squared norm is below (n eps)^2 ||R||_F^2 are rounding
   // noise of a rank-deficient R: they take no part in rotations
-  __shared__ T s_fro;
   if (threadIdx.x < 32) {
     T f = 0;
     for (int e = threadIdx.x; e < np * n; e += 32) f += U[e] * U[e];
@@ -170,111 +270,131 @@ __global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweep
   }
   __syncthreads();
   const T negligible = (static_cast<T>(n) * eps) * (static_cast<T>(n) * eps) * s_fro;
-  const int group = threadIdx.x / tpp;
-  const int gl = threadIdx.x % tpp;
-  const int npairs = np / 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int sweep = 0;
   bool converged = false;
-  __syncthreads();
   for (; sweep < max_sweeps && !converged; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
-    for (int round = 0; round < np - 1; ++round) {
-      {
-        const bool real = group < npairs;
-        int p, q;
-        if (!real) {
-          p = 0;
-          q = 1;
-        } else if (group == 0) {
-          p = round;
-          q = np - 1;
-        } else {
-          p = (round + group) % (np - 1);
-          q = (round - group + (np - 1)) % (np - 1);
-        }
-        if (p > q) {
-          int t = p;
-          p = q;
-          q = t;
-        }
-        T* up = U + static_cast<int64_t>(p) * n;
-        T* uq = U + static_cast<int64_t>(q) * n;
+    int any = 0;
+    for (int round = 0; round < rounds; ++round) {
+      for (int g = warp; g < npairs; g += nwarps) {
+        const short2 pq = pairs[round * npairs + g];
+        T* up = U + static_cast<int64_t>(pq.x) * n;
+        T* uq = U + static_cast<int64_t>(pq.y) * n;
+        T x[NPL], y[NPL];
         T al = 0, be = 0, ga = 0;
-        for (int r = gl; r < n; r += tpp) {
-          T x = up[r], y = uq[r];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+          const int r = lane + 32 * i;
+          x[i] = r < n ? up[r] : T(0);
+          y[i] = r < n ? uq[r] : T(0);
+          al += x[i] * x[i];
+          be += y[i] * y[i];
+          ga += x[i] * y[i];
         }
-        al = group_sum(al, tpp);
-        be = group_sum(be, tpp);
-        ga = group_sum(ga, tpp);
-        bool rotate = real && al > negligible && be > negligible && ga != T(0) && fabs(ga) > tol * sqrt(al * be);
-        if (rotate) {
-          T zeta = (be - al) / (T(2) * ga);
-          T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          T c = T(1) / sqrt(T(1) + t * t);
-          T s = c * t;
-          for (int r = gl; r < n; r += tpp) {
-            T x = up[r], y = uq[r];
-            up[r] = c * x - s * y;
-            uq[r] = s * x + c * y;
-          }
-          if (kWithV) {
-            T* vp = V + static_cast<int64_t>(p) * n;
-            T* vq = V + static_cast<int64_t>(q) * n;
-            for (int r = gl; r < n; r += tpp) {
-              T x = vp[r], y = vq[r];
-              vp[r] = c * x - s * y;
-              vq[r] = s * x + c * y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (al > negligible && be > negligible && ga * ga > tol2 * al * be) {
+          T c, s;
+          rotation(al, be, ga, c, s);
+#pragma unroll
+          for (int i = 0; i < NPL; ++i) {
+            const int r = lane + 32 * i;
+            if (r < n) {
+              up[r] = c * x[i] - s * y[i];
+              uq[r] = s * x[i] + c * y[i];
             }
           }
-          if (gl == 0) s_rot = 1;
+          if (kWithV) {
+            T* vp = V + static_cast<int64_t>(pq.x) * n;
+            T* vq = V + static_cast<int64_t>(pq.y) * n;
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) {
+              const int r = lane + 32 * i;
+              if (r < n) {
+                const T xv = vp[r], yv = vq[r];
+                vp[r] = c * xv - s * yv;
+                vq[r] = s * xv + c * yv;
+              }
+            }
+          }
+          any = 1;
         }
       }
-      __syncthreads();
+      any = __syncthreads_or(any);
     }
-    converged = s_rot == 0;
-    __syncthreads();
+    converged = any == 0;
   }
-  if (!converged) {
-    if (threadIdx.x == 0) set_status(status, kStatusNoConvergence);
-  }
+  if (!converged && threadIdx.x == 0) set_status(status, kStatusNoConvergence);
   if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
   // singular values
-  const int warps = blockDim.x / 32, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int j = wid; j < n; j += warps) {
-    double num = 0.0, den = 0.0;
-    if (kWithV) {
+  if (kWithV) {
+    // sigma_j^2 = sum_i (R v_j)_i^2 / ||v_j||^2 in FP64, one thread per (i, j).
+    // U is no longer needed: its storage (np * n floats = np * n / 2 doubles)
+    // holds the squared terms for np / 2 rows i at a time.
+    double* acc = reinterpret_cast<double*>(U);
+    for (int j = warp; j < n; j += nwarps) sig[j] = 0.0;
+    const int ipass = np / 2;
+    for (int i0 = 0; i0 < n; i0 += ipass) {
+      const int i1 = i0 + ipass < n ? i0 + ipass : n;
+      __syncthreads();
+      for (int e = threadIdx.x; e < (i1 - i0) * n; e += blockDim.x) {
+        const int j = e / (i1 - i0), i = i0 + e % (i1 - i0);
+        const T* vj = V + static_cast<int64_t>(j) * n;
+        double y0 = 0.0, y1 = 0.0;
+        int k = i;
+        if (r_in_smem) {
+          for (; k + 1 < n; k += 2) {
+            y0 += Rs[i * n + k] * static_cast<double>(vj[k]);
+            y1 += Rs[i * n + k + 1] * static_cast<double>(vj[k + 1]);
+          }
+          if (k < n) y0 += Rs[i * n + k] * static_cast<double>(vj[k]);
+        } else {
+          for (; k < n; ++k) y0 += R[static_cast<int64_t>(i) * ldr + k] * static_cast<double>(vj[k]);
+        }
+        const double yy = y0 + y1;
+        acc[e] = yy * yy;
+      }
+      __syncthreads();
+      for (int j = warp; j < n; j += nwarps) {
+        double num = 0.0;
+        for (int i = lane; i < i1 - i0; i += 32) num += acc[j * (i1 - i0) + i];
+        for (int o = 16; o > 0; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
+        if (lane == 0) sig[j] += num;
+      }
+    }
+    __syncthreads();
+    for (int j = warp; j < n; j += nwarps) {
+      double den = 0.0;
       const T* vj = V + static_cast<int64_t>(j) * n;
       for (int i = lane; i < n; i += 32) {
-        double y = 0.0;
-        for (int k = i; k < n; ++k) y += R[static_cast<int64_t>(i) * ldr + k] * static_cast<double>(vj[k]);
-        num += y * y;
-        double v = static_cast<double>(vj[i]);
+        const double v = static_cast<double>(vj[i]);
         den += v * v;
       }
-    } else {
+      for (int o = 16; o > 0; o >>= 1) den += __shfl_xor_sync(0xffffffffu, den, o);
+      if (lane == 0) sig[j] = den > 0.0 ? sqrt(sig[j] / den) : 0.0;
+    }
+  } else {
+    for (int j = warp; j < n; j += nwarps) {
+      double num = 0.0;
       const T* uj = U + static_cast<int64_t>(j) * n;
       for (int i = lane; i < n; i += 32) {
-        double u = static_cast<double>(uj[i]);
+        const double u = static_cast<double>(uj[i]);
         num += u * u;
       }
-      den = 1.0;
+      for (int o = 16; o > 0; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
+      if (lane == 0) sig[j] = sqrt(num);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      num += __shfl_xor_sync(0xffffffffu, num, o);
-      if (kWithV) den += __shfl_xor_sync(0xffffffffu, den, o);
-    }
-    if (lane == 0) sig[j] = den > 0.0 ? sqrt(num / den) : 0.0;
   }
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    double v = sig[j];
+    const double v = sig[j];
     int rank = 0;
     for (int k = 0; k < n; ++k) {
-      double w = sig[k];
+      const double w = sig[k];
       rank += (w > v) || (w == v && k < j);
     }
     sigma[rank] = v;
@@ -286,62 +406,79 @@ __global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweep
 static double default_tol(const Plan& p) { return p.rank_tol > 0 ? p.rank_tol : (p.mixed ? 1e-5 : 1e-13); }
 
 static int dense_threads(int n) {
-  int t = 32;
+  int t = 64;
   while (t < n * 8 && t < 1024) t <<= 1;
   return t;
 }
 
-cudaError_t launch_chol_first(const Plan& p, cudaStream_t s) {
-  int n = p.n;
-  size_t smem = sizeof(double) * (static_cast<size_t>(n) * n + n) + sizeof(int32_t) * n;
-  cudaError_t err = cudaFuncSetAttribute(chol_first_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <typename T>
+static cudaError_t chol_first_t(const Plan& p, cudaStream_t s) {
+  const int n = p.n;
+  const size_t smem = sizeof(T) * (static_cast<size_t>(n) * n + 3 * n) + sizeof(int32_t) * n + 16;
+  cudaError_t err = cudaFuncSetAttribute(chol_first_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  chol_first_kernel<<<1, dense_threads(n), smem, s>>>(p.G1, n, default_tol(p), p.R1, p.W, p.Wf, p.active,
-                                                        &p.hdr->status);
+  chol_first_kernel<T><<<1, dense_threads(n), smem, s>>>(p.G1, n, default_tol(p), p.R1, p.W, p.Wf, p.active,
+                                                           &p.hdr->status);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_first(const Plan& p, cudaStream_t s) {
+  return p.mixed ? chol_first_t<float>(p, s) : chol_first_t<double>(p, s);
+}
+
+template <typename T>
+static cudaError_t chol_second_t(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s) {
+  const int n = p.n;
+  size_t smem = ((sizeof(T) * (static_cast<size_t>(n) * n + 2 * n) + sizeof(int32_t) * n + 15) & ~size_t(15));
+  if (p.mixed) smem += sizeof(double) * static_cast<size_t>(n) * n;
+  cudaError_t err = cudaFuncSetAttribute(chol_second_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  // G1 is consumed by the first factorisation: its storage holds the refined inverse
+  chol_second_kernel<T><<<1, dense_threads(n), smem, s>>>(p.G2, n, default_tol(p), p.R1, p.W, p.active,
+                                                            p.mixed ? 1 : 0, p.G1, p.R, R_out, ldr, &p.hdr->status);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s) {
-  int n = p.n;
-  size_t smem = sizeof(double) * (static_cast<size_t>(n) * n + n) + sizeof(int32_t) * n;
-  cudaError_t err = cudaFuncSetAttribute(chol_second_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return p.mixed ? chol_second_t<float>(p, R_out, ldr, s) : chol_second_t<double>(p, R_out, ldr, s);
+}
+
+template <typename T, bool kWithV, int NPL>
+static cudaError_t jacobi_t(const Plan& p, const double* R, int64_t ldr, double* sigma, double tol, cudaStream_t s) {
+  const int n = p.n;
+  const int np = n + (n & 1);
+  const int npairs = np / 2;
+  int threads = 32 * npairs;
+  if (threads > 1024) threads = 1024;
+  size_t smem = sizeof(T) * static_cast<size_t>(np) * n * (kWithV ? 2 : 1) + sizeof(double) * np;
+  if (kWithV && n <= 64) smem += sizeof(double) * static_cast<size_t>(n) * n;
+  smem += sizeof(short2) * static_cast<size_t>(np - 1) * npairs;
+  cudaError_t err = cudaFuncSetAttribute(jacobi_kernel<T, kWithV, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  chol_second_kernel<<<1, dense_threads(n), smem, s>>>(p.G2, n, default_tol(p), p.R1, p.active, p.R, R_out, ldr,
-                                                         &p.hdr->status);
+  jacobi_kernel<T, kWithV, NPL><<<1, threads, smem, s>>>(R, ldr, n, p.max_sweeps, tol, sigma, &p.hdr->status,
+                                                          &p.hdr->jacobi_sweeps);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s) {
-  int n = p.n;
-  int np = n + (n & 1);
-  int pairs = np / 2;
-  int tpp = 32;
-  while (tpp > 1 && tpp * pairs > 1024) tpp >>= 1;
-  int threads = tpp * pairs;
-  if (threads < 32) threads = 32;
-  threads = (threads + 31) / 32 * 32;
-  cudaError_t err;
+  const int n = p.n;
   if (p.mixed) {
-    size_t smem = sizeof(float) * static_cast<size_t>(np) * n * 2 + sizeof(double) * n;
-    err = cudaFuncSetAttribute(jacobi_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(smem));
-    if (err != cudaSuccess) return err;
-    jacobi_kernel<float, true><<<1, threads, smem, s>>>(R, ldr, n, p.max_sweeps, tpp, sigma, &p.hdr->status,
-                                                         &p.hdr->jacobi_sweeps);
-  } else {
-    size_t smem = sizeof(double) * static_cast<size_t>(np) * n + sizeof(double) * n;
-    err = cudaFuncSetAttribute(jacobi_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(smem));
-    if (err != cudaSuccess) return err;
-    jacobi_kernel<double, false><<<1, threads, smem, s>>>(R, ldr, n, p.max_sweeps, tpp, sigma, &p.hdr->status,
-                                                           &p.hdr->jacobi_sweeps);
+    // FP32 sweeps stop at |u_p . u_q| <= 1e-5 ||u_p|| ||u_q||: the FP64
+    // Rayleigh quotient then has a relative error of order 1e-10 / gap
+    if (n <= 32) return jacobi_t<float, true, 1>(p, R, ldr, sigma, 1e-5, s);
+    if (n <= 64) return jacobi_t<float, true, 2>(p, R, ldr, sigma, 1e-5, s);
+    return jacobi_t<float, true, 4>(p, R, ldr, sigma, 1e-5, s);
   }
-  count_launches(1);
-  return cudaGetLastError();
+  const double tol = 4.0 * n * 1.1102230246251565e-16;
+  if (n <= 32) return jacobi_t<double, false, 1>(p, R, ldr, sigma, tol, s);
+  if (n <= 64) return jacobi_t<double, false, 2>(p, R, ldr, sigma, tol, s);
+  return jacobi_t<double, false, 4>(p, R, ldr, sigma, tol, s);
 }
 
 }  // namespace figaro

@@ -5,9 +5,13 @@
 // Precision: every FP32 operand v is split as v = hi + lo with hi = v with
 // its 13 low mantissa bits cleared (exactly TF32) and lo = v - hi rounded to
 // TF32; a product is formed from hi*hi + hi*lo + lo*hi (3xTF32), so each term
-// carries ~22 significant bits.  Products accumulate in FP32 in tensor memory
-// for at most 1,024 rows, then into FP64 (per-block partials, reduced in a
-// fixed order).
+// carries ~22 significant bits.  The tensor core rounds its FP32 accumulator
+// toward zero at every MMA, a bias that grows with the number of MMAs adding
+// into one accumulator; so the hi*hi products of a 128-row tile go to four
+// accumulators of 32 rows each and both correction terms to a fifth, all five
+// are drained after every tile (summed in FP32 with round-to-nearest) into
+// float-float accumulators held in registers, and the block's partial is
+// written in FP64 at the end (partials are reduced in a fixed order).
 //
 // Per block (128 threads; thread t owns row t of a 128-row tile):
 //   1. TMA loads the next X tile (128 rows x k, 128-byte swizzle) while the
@@ -18,8 +22,8 @@
 //      Pass 1: each thread reads its row of X from shared memory.
 //   3. The row (Q = X W, or X) is split into hi / lo and written transposed
 //      into K-major operand panels (Q^T: kout rows x 128 tile rows).
-//   4. Three Gram MMAs D2 += Q^T Q (M = 64 or 128, N = kout, K = 128 rows)
-//      accumulate in tensor memory.
+//   4. Gram MMAs Q^T Q (M = 64 or 128, N = kout, K = 128 rows) into the five
+//      accumulators; the previous tile's accumulators are drained first.
 // A single elected thread issues every MMA and TMA; completion is tracked
 // with tcgen05.commit -> mbarrier.  Every wait is bounded: on timeout the
 // block records FIGARO_ERR_DEVICE_TIMEOUT, stops issuing work, waits (again
@@ -38,7 +42,7 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTileRows = 128;
 constexpr int kPanelBytes = kTileRows * 128;  // one 32-column panel of an X tile
-constexpr int kFlushTiles = 8;
+constexpr int kHiAcc = 4;  // hi*hi accumulators per tile (4 K-steps of 8 rows each)
 
 struct TcArgs {
   int k;             // columns of X (multiple of 4)
@@ -165,7 +169,9 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
   const bool pass2 = a.W != nullptr;
   const int64_t rows = a.rows_dev ? *a.rows_dev : a.rows;
   const int64_t ntiles = (rows + kTileRows - 1) / kTileRows;
-  const uint32_t tmem_cols = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));
+  // formation result + kHiAcc + 1 Gram accumulators, NP columns each
+  constexpr uint32_t kCols = (kHiAcc + 2) * NP;
+  const uint32_t tmem_cols = kCols <= 32 ? 32 : (kCols <= 64 ? 64 : (kCols <= 128 ? 128 : (kCols <= 256 ? 256 : 512)));
 
   if (tid == 0) {
     mbar_init(&bar_tma[0], 1);
@@ -202,8 +208,8 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const uint32_t d1 = tmem;                        // formation result: 128 lanes x NP
-  const uint32_t d2 = tmem + static_cast<uint32_t>(NP);  // Gram accumulator
+  const uint32_t d1 = tmem;                                   // formation result: 128 lanes x NP
+  const uint32_t dacc = tmem + static_cast<uint32_t>(NP);    // kHiAcc + 1 Gram accumulators of NP columns
   const uint32_t tile_bytes = static_cast<uint32_t>(a.kpanels * kPanelBytes);
 
   // prologue: first two tiles of this block
@@ -218,26 +224,41 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
     }
   }
 
-  // FP64 totals of the Gram rows this thread holds (flushed from TMEM)
+  // Gram row held by this thread's TMEM lane (M = 64: 16 rows per 32-lane quarter)
   const int lane_row = a.mg == 64 ? (((tid & 31) < 16) ? (warp * 16 + (tid & 31)) : -1) : tid;
-  double* part = a.part + static_cast<int64_t>(blockIdx.x) * a.kout * a.kout;
-  if (lane_row >= 0 && lane_row < a.kout)
-    for (int j = 0; j < a.kout; ++j) part[lane_row * a.kout + j] = 0.0;
-
-  bool fresh = true;  // next Gram MMA starts a new accumulation
-  int it = 0;
-  int pending_g = 0;  // Gram MMAs committed and not yet waited for
-  uint32_t g_phase = 0, f_phase = 0;
-  auto flush = [&]() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float v[NP];
+  float acc_hi[NP], acc_lo[NP];  // float-float running sums of that row
 #pragma unroll
-    for (int c0 = 0; c0 < NP; c0 += 32) tmem_ld32(d2 + (static_cast<uint32_t>(warp * 32) << 16) + c0, v + c0);
-    if (lane_row >= 0 && lane_row < a.kout)
-      for (int j = 0; j < a.kout; ++j) part[lane_row * a.kout + j] += static_cast<double>(v[j]);
+  for (int j = 0; j < NP; ++j) {
+    acc_hi[j] = 0.f;
+    acc_lo[j] = 0.f;
+  }
+  // drain the accumulators of the tile whose Gram MMAs just completed
+  auto drain = [&]() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += 32) {
+      float sum[32], v[32];
+      tmem_ld32(dacc + (static_cast<uint32_t>(warp * 32) << 16) + c0, sum);
+#pragma unroll
+      for (int q = 1; q <= kHiAcc; ++q) {
+        tmem_ld32(dacc + (static_cast<uint32_t>(warp * 32) << 16) + q * NP + c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sum[j] = __fadd_rn(sum[j], v[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        float s_, e_;
+        two_sum(acc_hi[c0 + j], sum[j], s_, e_);
+        acc_hi[c0 + j] = s_;
+        acc_lo[c0 + j] = __fadd_rn(acc_lo[c0 + j], e_);
+      }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   };
 
+  int it = 0;
+  bool pending_g = false;  // Gram MMAs committed and not yet waited for
+  uint32_t g_phase = 0, f_phase = 0;
   for (int64_t rt = blockIdx.x; rt < ntiles; rt += gridDim.x, ++it) {
     const int buf = it & 1;
     float* X = reinterpret_cast<float*>(base + a.off_x[buf]);
@@ -270,10 +291,14 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
         for (int ks = 0; ks < a.ksteps_f; ++ks) {
           const uint32_t ao = static_cast<uint32_t>((ks >> 2) * kPanelBytes + (ks & 3) * 32);
           const uint32_t bo = static_cast<uint32_t>((ks >> 2) * a.wpanel_bytes + (ks & 3) * 32);
-          mma_tf32(d1, desc_kmajor_sw128(xh + ao), desc_kmajor_sw128(wh + bo), idf, acc);
+          mma_tf32(d1, desc_kmajor_sw128(xl + ao), desc_kmajor_sw128(wh + bo), idf, acc);
           acc = 1;
           mma_tf32(d1, desc_kmajor_sw128(xh + ao), desc_kmajor_sw128(wl + bo), idf, 1);
-          mma_tf32(d1, desc_kmajor_sw128(xl + ao), desc_kmajor_sw128(wh + bo), idf, 1);
+        }
+        for (int ks = 0; ks < a.ksteps_f; ++ks) {  // the large term last: fewer truncations of large values
+          const uint32_t ao = static_cast<uint32_t>((ks >> 2) * kPanelBytes + (ks & 3) * 32);
+          const uint32_t bo = static_cast<uint32_t>((ks >> 2) * a.wpanel_bytes + (ks & 3) * 32);
+          mma_tf32(d1, desc_kmajor_sw128(xh + ao), desc_kmajor_sw128(wh + bo), idf, 1);
         }
         mma_commit(&bar_f);
       }
@@ -302,7 +327,7 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
       for (int c = 0; c < NP; ++c) q[c] = 0.f;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // X buffer consumed (registers / D1); previous Gram MMAs may still read Q^T
+    __syncthreads();  // X buffer consumed (registers / D1)
     if (tid == 0) {   // refill this buffer with the tile two steps ahead
       const int64_t nt = rt + 2 * static_cast<int64_t>(gridDim.x);
       if (nt < ntiles) {
@@ -312,7 +337,7 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
                       &bar_tma[buf]);
       }
     }
-    if (pending_g) {  // the previous Gram MMAs read Q^T: wait before overwriting it
+    if (pending_g) {  // the previous Gram MMAs read Q^T and fill the accumulators
       if (!mbar_wait(&bar_g, g_phase, a.spin_limit)) {
         if (tid == 0) {
           set_status(a.status, kStatusTimeout);
@@ -320,10 +345,9 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
         }
       }
       g_phase ^= 1;
-      pending_g = 0;
+      pending_g = false;
       __syncthreads();
       if (s_abort) break;
-      if (fresh) flush();  // accumulation window ended with those MMAs
     }
     // Q^T hi / lo: thread t writes column t of Q^T (tile row t)
     {
@@ -339,33 +363,44 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
         *reinterpret_cast<float*>(ql + off) = tf32_rn(v - h);
       }
     }
+    if (it > 0) drain();  // the previous tile's accumulators, before they are overwritten
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t idg = idesc_tf32(a.mg, a.np);
       const uint32_t qh = smem_u32(base + a.off_qh), ql = smem_u32(base + a.off_ql);
-      uint32_t acc = fresh ? 0u : 1u;
-      for (int ks = 0; ks < kTileRows / 8; ++ks) {
+      const uint32_t dc = dacc + kHiAcc * static_cast<uint32_t>(NP);  // correction accumulator
+      constexpr int kSteps = kTileRows / 8;
+      for (int ks = 0; ks < kSteps; ++ks) {
         const uint32_t o = static_cast<uint32_t>((ks >> 2) * a.qpanel_bytes + (ks & 3) * 32);
-        mma_tf32(d2, desc_kmajor_sw128(qh + o), desc_kmajor_sw128(qh + o), idg, acc);
-        acc = 1;
-        mma_tf32(d2, desc_kmajor_sw128(qh + o), desc_kmajor_sw128(ql + o), idg, 1);
-        mma_tf32(d2, desc_kmajor_sw128(ql + o), desc_kmajor_sw128(qh + o), idg, 1);
+        mma_tf32(dc, desc_kmajor_sw128(qh + o), desc_kmajor_sw128(ql + o), idg, ks > 0 ? 1u : 0u);
+        mma_tf32(dc, desc_kmajor_sw128(ql + o), desc_kmajor_sw128(qh + o), idg, 1u);
+      }
+      for (int ks = 0; ks < kSteps; ++ks) {
+        const uint32_t o = static_cast<uint32_t>((ks >> 2) * a.qpanel_bytes + (ks & 3) * 32);
+        const int q = ks / (kSteps / kHiAcc);
+        const uint32_t d = dacc + static_cast<uint32_t>(q * NP);
+        mma_tf32(d, desc_kmajor_sw128(qh + o), desc_kmajor_sw128(qh + o), idg, (ks % (kSteps / kHiAcc)) ? 1u : 0u);
       }
       mma_commit(&bar_g);
     }
-    pending_g = 1;
-    fresh = ((it + 1) % kFlushTiles) == 0;
+    pending_g = true;
   }
-  // drain: the last Gram MMAs, then the final flush
+  // drain: the last Gram MMAs, then their accumulators
   if (pending_g) {
     if (!mbar_wait(&bar_g, g_phase, a.spin_limit)) {
       if (tid == 0) set_status(a.status, kStatusTimeout);
       s_abort = 1;
     }
     __syncthreads();
-    if (!s_abort) flush();
+    if (!s_abort) drain();
+  }
+  double* part = a.part + static_cast<int64_t>(blockIdx.x) * a.kout * a.kout;
+  if (lane_row >= 0 && lane_row < a.kout) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+      if (j < a.kout) part[lane_row * a.kout + j] = static_cast<double>(acc_hi[j]) + static_cast<double>(acc_lo[j]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
