@@ -129,7 +129,10 @@ __global__ void chol_first_kernel(const double* G, int n, double tol, double* R1
   tri_inverse_inplace<T>(A, n, act, x);
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
+    // dependent columns pass through the second pass unchanged (identity
+    // block), so their coupling to the independent ones is measured there
     double w = (j >= i) ? static_cast<double>(A[e]) : 0.0;
+    if (i == j && !act[i]) w = 1.0;
     if (sizeof(T) == 4) {
       // the value both Gram engines use exactly: hi (TF32) + lo rounded to TF32
       const float v = static_cast<float>(w);
@@ -173,7 +176,7 @@ __global__ void chol_second_kernel(const double* G2, int n, double tol, const do
     act[k] = active[k];
   }
   __syncthreads();
-  const double* X = R1;
+  // X = W^{-1} = blockdiag(R1 on the independent columns, I on the others)
   if (refine) {
     // Q was formed with W, so the consistent factor is R2 W^{-1}; one Newton
     // step X = R1 + R1 (I - W R1) squares the relative error of R1 as an
@@ -183,14 +186,17 @@ __global__ void chol_second_kernel(const double* G2, int n, double tol, const do
       E[e] = (j >= i && act[i] && act[j]) ? (i == j ? 1.0 : 0.0) - upper_dot(Wd, R1, n, i, j) : 0.0;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e / n, j = e % n;
-      Xg[e] = (j >= i && act[i]) ? R1[e] + upper_dot(R1, E, n, i, j) : 0.0;
-    }
-    __threadfence_block();
-    __syncthreads();
-    X = Xg;
   }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    double x = 0.0;
+    if (j >= i && act[i] && act[j]) x = R1[e] + (refine ? upper_dot(R1, E, n, i, j) : 0.0);
+    if (i == j && !act[i]) x = 1.0;
+    Xg[e] = x;
+  }
+  __threadfence_block();
+  __syncthreads();
+  const double* X = Xg;
   chol_inplace<T>(A, n, diag0, act, static_cast<T>(tol), y, status);
   // R = R2 X (both upper triangular) in FP64; rows of dependent columns are zero
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {

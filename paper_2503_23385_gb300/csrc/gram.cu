@@ -209,17 +209,18 @@ struct ReduceArgs {
   int count[3];   // partials (blocks) per Gram block
   int kout[3];
   int off[3];     // diagonal offset of the block inside G
+  int sym[3];     // 1: partials hold P with G = (P + P^T) / 2 (tensor-core engine); 0: upper triangle
   int n;
   double* G;
 };
 
-constexpr int kReduceWarps = 8;
+constexpr int kReduceWarps = 32;
 
-// G = sum of the three blocks' partials in a fixed order (deterministic),
-// symmetrised from the upper triangle.  Lanes take consecutive outputs,
-// warps interleave over the partials.
+// G = sum of the three blocks' partials in a fixed order (deterministic).
+// A block owns 32 consecutive outputs (one per lane); its warps interleave
+// over the partials and their sums are combined in warp order.
 __global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_kernel(ReduceArgs a) {
-  __shared__ double s[kReduceWarps][32];
+  __shared__ double s[kReduceWarps][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int e = blockIdx.x * 32 + lane;
   const bool ok = e < a.n * a.n;
@@ -231,16 +232,17 @@ __global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_kernel(ReduceAr
     const int ko = a.kout[b];
     const int ii = lo - a.off[b], jj = hi - a.off[b];
     if (ii < 0 || jj < 0 || ii >= ko || jj >= ko) continue;
-    const double* p = a.part[b] + ii * ko + jj;
     const int64_t stride = static_cast<int64_t>(ko) * ko;
-    double t0 = 0.0, t1 = 0.0;
+    const double* p0 = a.part[b] + ii * ko + jj;
+    const double* p1 = a.part[b] + jj * ko + ii;  // the transposed entry (symmetrised partials)
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
     int c = warp;
-    for (; c + kReduceWarps < a.count[b]; c += 2 * kReduceWarps) {
-      t0 += p[c * stride];
-      t1 += p[(c + kReduceWarps) * stride];
+#pragma unroll 4
+    for (; c < a.count[b]; c += kReduceWarps) {
+      const double v = a.sym[b] ? 0.5 * (p0[c * stride] + p1[c * stride]) : p0[c * stride];
+      t[(c / kReduceWarps) & 3] += v;
     }
-    if (c < a.count[b]) t0 += p[c * stride];
-    tot += t0 + t1;
+    tot += (t[0] + t[1]) + (t[2] + t[3]);
   }
   s[warp][lane] = tot;
   __syncthreads();
@@ -353,6 +355,7 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     r.count[b] = grid;
     r.kout[b] = a.kout;
     r.off[b] = b == 2 ? p.n1 : 0;
+    r.sym[b] = tc ? 1 : 0;
   }
   const int ne = p.n * p.n;
   gram_reduce_kernel<<<(ne + 31) / 32, 32 * kReduceWarps, 0, s>>>(r);

@@ -5,24 +5,31 @@
 // Precision: every FP32 operand v is split as v = hi + lo with hi = v with
 // its 13 low mantissa bits cleared (exactly TF32) and lo = v - hi rounded to
 // TF32; a product is formed from hi*hi + hi*lo + lo*hi (3xTF32), so each term
-// carries ~22 significant bits.  The tensor core rounds its FP32 accumulator
-// toward zero at every MMA, a bias that grows with the number of MMAs adding
-// into one accumulator; so the hi*hi products of a 128-row tile go to four
-// accumulators of 32 rows each and both correction terms to a fifth, all five
-// are drained after every tile (summed in FP32 with round-to-nearest) into
-// float-float accumulators held in registers, and the block's partial is
+// carries ~22 significant bits.  For the symmetric Gram the two correction
+// terms are one MMA: with lo' = 2 lo the block accumulates P = H + 2 C
+// (H = hi^T hi, C = hi^T lo) and the reduction takes G = (P + P^T) / 2 =
+// H + C + C^T exactly.  The tensor core rounds its FP32 accumulator toward
+// zero at every MMA, a bias that grows with the number of MMAs adding large
+// values into one accumulator; so a 128-row tile goes to four accumulators
+// of 32 rows each (small correction terms first, the large hi*hi terms
+// last), drained after every tile (summed in FP32 with round-to-nearest)
+// into float-float accumulators held in registers; the block's partial is
 // written in FP64 at the end (partials are reduced in a fixed order).
 //
 // Per block (128 threads; thread t owns row t of a 128-row tile):
-//   1. TMA loads the next X tile (128 rows x k, 128-byte swizzle) while the
-//      current one is processed (two buffers, mbarrier transaction counts).
-//   2. Pass 2 only: X is split in place (hi) and into a lo buffer; three
-//      formation MMAs D1 = X W (M = 128 rows, N = kout, K = k) run into tensor
-//      memory; each thread reads its row of D1 back (tcgen05.ld).
-//      Pass 1: each thread reads its row of X from shared memory.
-//   3. The row (Q = X W, or X) is split into hi / lo and written transposed
-//      into K-major operand panels (Q^T: kout rows x 128 tile rows).
-//   4. Gram MMAs Q^T Q (M = 64 or 128, N = kout, K = 128 rows) into the five
+//   1. TMA loads the next X tile (128 rows x k in 32-column panels) one tile
+//      ahead (two buffers, mbarrier transaction counts).  Pass 1 loads it with
+//      the 32-byte-atom 128-byte swizzle, the layout the tensor core reads
+//      TF32 operands from when M or N (here: the columns of X) is the
+//      contiguous dimension; pass 2 with the plain 128-byte swizzle, the
+//      K-major layout of the formation product.
+//   2. The tile is split elementwise: hi in place, lo into a second buffer.
+//   3. Pass 2 only: three formation MMAs D1 = X W (M = 128 rows, N = kout,
+//      K = k) into tensor memory; each thread reads its row of D1 back
+//      (tcgen05.ld), splits it and writes the hi / lo rows of Q contiguously
+//      in the 32-byte-atom layout.
+//   4. Gram MMAs hi^T lo' and hi^T hi (Q = X in pass 1; M = 64 or 128,
+//      N = kout, K = 128 rows, both operands MN-major) into the four
 //      accumulators; the previous tile's accumulators are drained first.
 // A single elected thread issues every MMA and TMA; completion is tracked
 // with tcgen05.commit -> mbarrier.  Every wait is bounded: on timeout the
@@ -42,7 +49,7 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTileRows = 128;
 constexpr int kPanelBytes = kTileRows * 128;  // one 32-column panel of an X tile
-constexpr int kHiAcc = 4;  // hi*hi accumulators per tile (4 K-steps of 8 rows each)
+constexpr int kHiAcc = 4;  // accumulators per tile (4 K-steps of 8 rows each)
 
 struct TcArgs {
   int k;             // columns of X (multiple of 4)
@@ -51,8 +58,7 @@ struct TcArgs {
   int ksteps_f;      // formation K steps of 8 (k padded to 8)
   int np;            // kout padded to 16 (N of both MMAs)
   int mg;            // Gram M: 64 or 128
-  int qrows;         // rows of each Q^T panel (kout padded to 8)
-  int qpanel_bytes;  // qrows * 128
+  int qpanels;       // ceil(kout / 32): 32-column panels of a Q row
   int wpanel_bytes;  // np * 128
   int64_t rows;
   const int64_t* rows_dev;
@@ -81,10 +87,24 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: kind::tf32, FP32 accumulator, both operands K-major.
-__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
+// Shared-memory matrix descriptor, MN-major TF32 in the 128-byte swizzle with
+// 32-byte atoms (layout type 1): 4-row groups 512 bytes apart, 32-column
+// panels `panel` bytes apart (0 repeats the first panel).
+__device__ __forceinline__ uint64_t desc_mn_sw128_32b(uint32_t saddr, uint32_t panel) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);
+  d |= static_cast<uint64_t>((panel >> 4) & 0x3FFF) << 16;  // leading byte offset: next 32 M/N columns
+  d |= static_cast<uint64_t>(512 >> 4) << 32;              // stride byte offset: next 4 K rows
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(1) << 61;
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, FP32 accumulator; mn = 1 makes both
+// operands MN-major (A = M x K with M contiguous, B = K x N with N contiguous).
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N, int mn = 0) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(mn) << 15) | (static_cast<uint32_t>(mn) << 16) |
+         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
@@ -158,6 +178,12 @@ __device__ __forceinline__ int sw128_offset(int row, int col, int panel_bytes) {
   return p * panel_bytes + row * 128 + ((((kk >> 2) ^ (row & 7))) << 4) + ((kk & 3) << 2);
 }
 
+// Byte offset of the 32-byte chunk holding columns [8c, 8c + 8) of a row in
+// the 32-byte-atom 128-byte swizzle: chunk c of row r sits at chunk c ^ (r mod 4).
+__device__ __forceinline__ int sw32b_chunk_offset(int row, int chunk) {
+  return ((chunk >> 2) * kTileRows * 128) + row * 128 + (((chunk & 3) ^ (row & 3)) << 5);
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -169,8 +195,8 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
   const bool pass2 = a.W != nullptr;
   const int64_t rows = a.rows_dev ? *a.rows_dev : a.rows;
   const int64_t ntiles = (rows + kTileRows - 1) / kTileRows;
-  // formation result + kHiAcc + 1 Gram accumulators, NP columns each
-  constexpr uint32_t kCols = (kHiAcc + 2) * NP;
+  // formation result + kHiAcc Gram accumulators, NP columns each
+  constexpr uint32_t kCols = (kHiAcc + 1) * NP;
   const uint32_t tmem_cols = kCols <= 32 ? 32 : (kCols <= 64 ? 64 : (kCols <= 128 ? 128 : (kCols <= 256 ? 256 : 512)));
 
   if (tid == 0) {
@@ -209,19 +235,16 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t d1 = tmem;                                   // formation result: 128 lanes x NP
-  const uint32_t dacc = tmem + static_cast<uint32_t>(NP);    // kHiAcc + 1 Gram accumulators of NP columns
+  const uint32_t dacc = tmem + static_cast<uint32_t>(NP);    // kHiAcc Gram accumulators of NP columns
   const uint32_t tile_bytes = static_cast<uint32_t>(a.kpanels * kPanelBytes);
 
-  // prologue: first two tiles of this block
-  if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
-      const int64_t rt = blockIdx.x + static_cast<int64_t>(b) * gridDim.x;
-      if (rt < ntiles) {
-        expect_tx(&bar_tma[b], tile_bytes);
-        for (int p = 0; p < a.kpanels; ++p)
-          tma_load_2d(base + a.off_x[b] + p * kPanelBytes, &tmx, p * 32, static_cast<int>(rt * kTileRows), &bar_tma[b]);
-      }
-    }
+  // prologue: the first tile of this block (each later tile is loaded one
+  // iteration ahead, into the buffer the previous tile's MMAs released)
+  if (tid == 0 && static_cast<int64_t>(blockIdx.x) < ntiles) {
+    expect_tx(&bar_tma[0], tile_bytes);
+    for (int p = 0; p < a.kpanels; ++p)
+      tma_load_2d(base + a.off_x[0] + p * kPanelBytes, &tmx, p * 32, static_cast<int>(blockIdx.x * kTileRows),
+                  &bar_tma[0]);
   }
 
   // Gram row held by this thread's TMEM lane (M = 64: 16 rows per 32-lane quarter)
@@ -235,12 +258,12 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
   // drain the accumulators of the tile whose Gram MMAs just completed
   auto drain = [&]() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
+#pragma unroll 1
     for (int c0 = 0; c0 < NP; c0 += 32) {
       float sum[32], v[32];
       tmem_ld32(dacc + (static_cast<uint32_t>(warp * 32) << 16) + c0, sum);
-#pragma unroll
-      for (int q = 1; q <= kHiAcc; ++q) {
+#pragma unroll 1
+      for (int q = 1; q < kHiAcc; ++q) {
         tmem_ld32(dacc + (static_cast<uint32_t>(warp * 32) << 16) + q * NP + c0, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) sum[j] = __fadd_rn(sum[j], v[j]);
@@ -256,12 +279,36 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   };
 
+  const uint32_t panel_mn = a.kpanels > 1 || a.qpanels > 1 ? static_cast<uint32_t>(kPanelBytes) : 0u;
   int it = 0;
   bool pending_g = false;  // Gram MMAs committed and not yet waited for
   uint32_t g_phase = 0, f_phase = 0;
   for (int64_t rt = blockIdx.x; rt < ntiles; rt += gridDim.x, ++it) {
     const int buf = it & 1;
     float* X = reinterpret_cast<float*>(base + a.off_x[buf]);
+    float* Xl = reinterpret_cast<float*>(base + a.off_xlo);
+    if (pending_g) {  // the previous tile's Gram MMAs: operands and accumulators become free
+      if (!mbar_wait(&bar_g, g_phase, a.spin_limit)) {
+        if (tid == 0) {
+          set_status(a.status, kStatusTimeout);
+          s_abort = 1;
+        }
+      }
+      g_phase ^= 1;
+      pending_g = false;
+      __syncthreads();
+      if (s_abort) break;
+      drain();
+    }
+    if (tid == 0) {  // the other buffer is free: load the next tile into it
+      const int64_t nt = rt + static_cast<int64_t>(gridDim.x);
+      if (nt < ntiles) {
+        expect_tx(&bar_tma[buf ^ 1], tile_bytes);
+        for (int p = 0; p < a.kpanels; ++p)
+          tma_load_2d(base + a.off_x[buf ^ 1] + p * kPanelBytes, &tmx, p * 32, static_cast<int>(nt * kTileRows),
+                      &bar_tma[buf ^ 1]);
+      }
+    }
     if (!mbar_wait(&bar_tma[buf], static_cast<uint32_t>((it >> 1) & 1), a.spin_limit)) {
       if (tid == 0) {
         set_status(a.status, kStatusTimeout);
@@ -270,35 +317,46 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
     }
     __syncthreads();
     if (s_abort) break;
-    float q[NP];
-    if (pass2) {
-      // split X in place (hi) and into the lo buffer, then D1 = X W (3 x TF32)
-      float* Xl = reinterpret_cast<float*>(base + a.off_xlo);
-      for (int e = tid; e < static_cast<int>(tile_bytes / 4); e += kTcThreads) {
-        const float v = X[e];
-        const float h = tf32_hi(v);
-        X[e] = h;
-        Xl[e] = tf32_rn(v - h);
+    // split X elementwise: hi in place, lo in the second buffer (same layout;
+    // 2 lo when it feeds the Gram, lo when it feeds the formation product);
+    // rows past the end (head block: count known on the device) are zeroed
+    {
+      const float lo_scale = pass2 ? 1.f : 2.f;
+      float4* X4 = reinterpret_cast<float4*>(X);
+      float4* L4 = reinterpret_cast<float4*>(Xl);
+      const int n4 = static_cast<int>(tile_bytes / 16);
+      for (int e = tid; e < n4; e += kTcThreads) {
+        const int row = (e % (kTileRows * 8)) / 8;  // 8 float4 per 128-byte row, panels of kTileRows rows
+        float4 v = X4[e];
+        if (rt * kTileRows + row >= rows) v = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 h, l;
+        h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
+        l.x = tf32_rn(v.x - h.x) * lo_scale; l.y = tf32_rn(v.y - h.y) * lo_scale;
+        l.z = tf32_rn(v.z - h.z) * lo_scale; l.w = tf32_rn(v.w - h.w) * lo_scale;
+        X4[e] = h;
+        L4[e] = l;
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    uint32_t ah = smem_u32(X), al = smem_u32(Xl);
+    if (pass2) {
+      if (tid == 0) {  // D1 = X W (3 x TF32), the large term last
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t idf = idesc_tf32(128, a.np);
-        const uint32_t xh = smem_u32(X), xl = smem_u32(Xl);
         const uint32_t wh = smem_u32(base + a.off_wh), wl = smem_u32(base + a.off_wl);
         uint32_t acc = 0;
         for (int ks = 0; ks < a.ksteps_f; ++ks) {
           const uint32_t ao = static_cast<uint32_t>((ks >> 2) * kPanelBytes + (ks & 3) * 32);
           const uint32_t bo = static_cast<uint32_t>((ks >> 2) * a.wpanel_bytes + (ks & 3) * 32);
-          mma_tf32(d1, desc_kmajor_sw128(xl + ao), desc_kmajor_sw128(wh + bo), idf, acc);
+          mma_tf32(d1, desc_kmajor_sw128(al + ao), desc_kmajor_sw128(wh + bo), idf, acc);
           acc = 1;
-          mma_tf32(d1, desc_kmajor_sw128(xh + ao), desc_kmajor_sw128(wl + bo), idf, 1);
+          mma_tf32(d1, desc_kmajor_sw128(ah + ao), desc_kmajor_sw128(wl + bo), idf, 1);
         }
-        for (int ks = 0; ks < a.ksteps_f; ++ks) {  // the large term last: fewer truncations of large values
+        for (int ks = 0; ks < a.ksteps_f; ++ks) {
           const uint32_t ao = static_cast<uint32_t>((ks >> 2) * kPanelBytes + (ks & 3) * 32);
           const uint32_t bo = static_cast<uint32_t>((ks >> 2) * a.wpanel_bytes + (ks & 3) * 32);
-          mma_tf32(d1, desc_kmajor_sw128(xh + ao), desc_kmajor_sw128(wh + bo), idf, 1);
+          mma_tf32(d1, desc_kmajor_sw128(ah + ao), desc_kmajor_sw128(wh + bo), idf, 1);
         }
         mma_commit(&bar_f);
       }
@@ -312,82 +370,61 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
       __syncthreads();
       if (s_abort) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int c0 = 0; c0 < NP; c0 += 32) tmem_ld32(d1 + (static_cast<uint32_t>(warp * 32) << 16) + c0, q + c0);
-    } else {
-      const unsigned char* Xb = reinterpret_cast<const unsigned char*>(X);
-#pragma unroll
-      for (int c = 0; c < NP; ++c)
-        q[c] = c < a.k ? *reinterpret_cast<const float*>(Xb + sw128_offset(tid, c, kPanelBytes)) : 0.f;
-    }
-    // rows past the end (only possible for the head block, whose row count
-    // is known on the device) contribute nothing
-    if (rt * kTileRows + tid >= rows) {
-#pragma unroll
-      for (int c = 0; c < NP; ++c) q[c] = 0.f;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // X buffer consumed (registers / D1)
-    if (tid == 0) {   // refill this buffer with the tile two steps ahead
-      const int64_t nt = rt + 2 * static_cast<int64_t>(gridDim.x);
-      if (nt < ntiles) {
-        expect_tx(&bar_tma[buf], tile_bytes);
-        for (int p = 0; p < a.kpanels; ++p)
-          tma_load_2d(base + a.off_x[buf] + p * kPanelBytes, &tmx, p * 32, static_cast<int>(nt * kTileRows),
-                      &bar_tma[buf]);
-      }
-    }
-    if (pending_g) {  // the previous Gram MMAs read Q^T and fill the accumulators
-      if (!mbar_wait(&bar_g, g_phase, a.spin_limit)) {
-        if (tid == 0) {
-          set_status(a.status, kStatusTimeout);
-          s_abort = 1;
-        }
-      }
-      g_phase ^= 1;
-      pending_g = false;
-      __syncthreads();
-      if (s_abort) break;
-    }
-    // Q^T hi / lo: thread t writes column t of Q^T (tile row t)
-    {
+      // row tid of Q = X W: split and write contiguously (32-byte-atom layout)
       unsigned char* qh = base + a.off_qh;
       unsigned char* ql = base + a.off_ql;
 #pragma unroll
-      for (int c = 0; c < NP; ++c) {
-        if (c >= a.qrows) break;
-        const float v = q[c];
-        const float h = tf32_hi(v);
-        const int off = sw128_offset(c, tid, a.qpanel_bytes);
-        *reinterpret_cast<float*>(qh + off) = h;
-        *reinterpret_cast<float*>(ql + off) = tf32_rn(v - h);
+      for (int c0 = 0; c0 < NP; c0 += 32) {
+        if (c0 >= a.qpanels * 32) break;
+        float q[32];
+        tmem_ld32(d1 + (static_cast<uint32_t>(warp * 32) << 16) + c0, q);
+        if (rt * kTileRows + tid >= rows) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) q[c] = 0.f;
+        }
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          const int off = sw32b_chunk_offset(tid, (c0 >> 3) + ch);
+          float4 h0, h1, l0, l1;
+          const float* v = q + ch * 8;
+          h0 = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
+          h1 = make_float4(tf32_hi(v[4]), tf32_hi(v[5]), tf32_hi(v[6]), tf32_hi(v[7]));
+          l0 = make_float4(2.f * tf32_rn(v[0] - h0.x), 2.f * tf32_rn(v[1] - h0.y), 2.f * tf32_rn(v[2] - h0.z),
+                           2.f * tf32_rn(v[3] - h0.w));
+          l1 = make_float4(2.f * tf32_rn(v[4] - h1.x), 2.f * tf32_rn(v[5] - h1.y), 2.f * tf32_rn(v[6] - h1.z),
+                           2.f * tf32_rn(v[7] - h1.w));
+          reinterpret_cast<float4*>(qh + off)[0] = h0;
+          reinterpret_cast<float4*>(qh + off)[1] = h1;
+          reinterpret_cast<float4*>(ql + off)[0] = l0;
+          reinterpret_cast<float4*>(ql + off)[1] = l1;
+        }
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      ah = smem_u32(qh);
+      al = smem_u32(ql);
     }
-    if (it > 0) drain();  // the previous tile's accumulators, before they are overwritten
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+    if (tid == 0) {  // Gram MMAs, both operands MN-major: P += hi^T (2 lo) + hi^T hi
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t idg = idesc_tf32(a.mg, a.np);
-      const uint32_t qh = smem_u32(base + a.off_qh), ql = smem_u32(base + a.off_ql);
-      const uint32_t dc = dacc + kHiAcc * static_cast<uint32_t>(NP);  // correction accumulator
-      constexpr int kSteps = kTileRows / 8;
-      for (int ks = 0; ks < kSteps; ++ks) {
-        const uint32_t o = static_cast<uint32_t>((ks >> 2) * a.qpanel_bytes + (ks & 3) * 32);
-        mma_tf32(dc, desc_kmajor_sw128(qh + o), desc_kmajor_sw128(ql + o), idg, ks > 0 ? 1u : 0u);
-        mma_tf32(dc, desc_kmajor_sw128(ql + o), desc_kmajor_sw128(qh + o), idg, 1u);
-      }
-      for (int ks = 0; ks < kSteps; ++ks) {
-        const uint32_t o = static_cast<uint32_t>((ks >> 2) * a.qpanel_bytes + (ks & 3) * 32);
-        const int q = ks / (kSteps / kHiAcc);
+      const uint32_t idg = idesc_tf32(a.mg, a.np, 1);
+      constexpr int kSteps = kTileRows / 8, kPer = kSteps / kHiAcc;
+      for (int q = 0; q < kHiAcc; ++q) {
         const uint32_t d = dacc + static_cast<uint32_t>(q * NP);
-        mma_tf32(d, desc_kmajor_sw128(qh + o), desc_kmajor_sw128(qh + o), idg, (ks % (kSteps / kHiAcc)) ? 1u : 0u);
+        for (int s = 0; s < kPer; ++s) {
+          const uint32_t o = static_cast<uint32_t>((q * kPer + s) * 1024);
+          mma_tf32(d, desc_mn_sw128_32b(ah + o, panel_mn), desc_mn_sw128_32b(al + o, panel_mn), idg, s > 0 ? 1u : 0u);
+        }
+        for (int s = 0; s < kPer; ++s) {
+          const uint32_t o = static_cast<uint32_t>((q * kPer + s) * 1024);
+          mma_tf32(d, desc_mn_sw128_32b(ah + o, panel_mn), desc_mn_sw128_32b(ah + o, panel_mn), idg, 1u);
+        }
       }
       mma_commit(&bar_g);
     }
     pending_g = true;
   }
-  // drain: the last Gram MMAs, then their accumulators
+  // the last tile's Gram MMAs, then their accumulators
   if (pending_g) {
     if (!mbar_wait(&bar_g, g_phase, a.spin_limit)) {
       if (tid == 0) set_status(a.status, kStatusTimeout);
@@ -434,8 +471,7 @@ Geometry geometry(int k, int kout, bool pass2) {
   a.ksteps_f = (k + 7) / 8;
   a.np = (kout + 15) / 16 * 16;
   a.mg = kout <= 64 ? 64 : 128;
-  a.qrows = (kout + 7) / 8 * 8;
-  a.qpanel_bytes = a.qrows * 128;
+  a.qpanels = (kout + 31) / 32;
   a.wpanel_bytes = a.np * 128;
   int off = 0;
   auto take = [&](int bytes) {
@@ -446,13 +482,11 @@ Geometry geometry(int k, int kout, bool pass2) {
   const int xb = a.kpanels * kPanelBytes;
   a.off_x[0] = take(xb);
   a.off_x[1] = take(xb);
-  a.off_xlo = pass2 ? take(xb) : 0;
+  a.off_xlo = take(xb);
   a.off_wh = pass2 ? take(a.kpanels * a.wpanel_bytes) : 0;
   a.off_wl = pass2 ? take(a.kpanels * a.wpanel_bytes) : 0;
-  a.off_qh = take(4 * a.qpanel_bytes);
-  a.off_ql = take(4 * a.qpanel_bytes);
-  // an M = 64 / 128 Gram reads mg operand rows from each Q^T panel: slack past the end
-  take(a.mg * 128);
+  a.off_qh = pass2 ? take(a.qpanels * kPanelBytes) : 0;
+  a.off_ql = pass2 ? take(a.qpanels * kPanelBytes) : 0;
   g.smem = static_cast<size_t>(off) + 1024;  // + alignment of the dynamic base
   return g;
 }
@@ -480,8 +514,11 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(k) * 4};
   cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kTileRows)};
   cuuint32_t es[2] = {1, 1};
+  // pass 1 feeds the tile to the Gram as MN-major operands (32-byte atoms);
+  // pass 2 feeds it to the formation product as the K-major operand
+  const CUtensorMapSwizzle sw = W ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B;
   CUresult cr = encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
   cudaError_t err;
