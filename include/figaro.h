@@ -188,6 +188,37 @@ FIGARO_API figaro_status figaro_join_singular_values(const figaro_table* A, cons
                                           void* stream);
 
 /*
+ * figaro_join_singular_values_fixed -- figaro_join_singular_values with
+ * scratch owned by the library instead of a caller-supplied workspace.  The
+ * paper has no counterpart: this is a convenience of this library for
+ * callers that cannot allocate device memory where they call it, e.g. a
+ * plugin whose host framework owns and budgets all device memory, or a
+ * latency-bound loop that must not pay cudaMalloc's implicit device-wide
+ * synchronisation.  The call itself allocates nothing.
+ *
+ * The scratch is one fixed array of FIGARO_FIXED_SCRATCH_BYTES per device,
+ * reserved when the library's device code is loaded on that device.  An
+ * input pair whose figaro_workspace_size exceeds it is rejected with
+ * FIGARO_ERR_WORKSPACE_TOO_SMALL before any device work is enqueued.
+ * Arguments, layouts and outputs are those of figaro_join_singular_values;
+ * the device is the one that holds the first non-empty device-resident
+ * table, else the current device.  The first call on a device looks up the
+ * scratch address (a host-side query, done once per device): make that first
+ * call outside any stream capture.  Nothing in the scratch needs to start at
+ * zero: every call clears the counters and flags it uses before using them.
+ * Calls share the one array, so two calls in flight on the same device at
+ * the same time race (wrong results or FIGARO_ERR_DEVICE_TIMEOUT): order
+ * them on one stream.  *scratch_out (when scratch_out != NULL) receives the
+ * scratch's device address, which figaro_get_status / figaro_get_info accept
+ * as `ws` to read the device status of the last call.
+ */
+#define FIGARO_FIXED_SCRATCH_BYTES ((size_t)32 << 20)
+
+FIGARO_API figaro_status figaro_join_singular_values_fixed(const figaro_table* A, const figaro_table* B,
+                                                const figaro_options* opt, double* sigma, double* R_out,
+                                                int64_t ldr, void** scratch_out, void* stream);
+
+/*
  * Batched form: `count` independent instances (A[i], B[i]) with their own
  * shapes, each writing R[i] (n_i x n_i, leading dimension n_i) and sigma[i].
  * R and sigma are host arrays of `count` device pointers (entries may be

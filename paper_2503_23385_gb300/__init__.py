@@ -20,7 +20,7 @@ __all__ = [
     "FigaroError", "PATH_FP64", "PATH_MIXED", "GRAM_AUTO", "GRAM_SIMT", "GRAM_TCGEN05", "library",
     "workspace_size", "join_group", "join_head_tail", "join_qr_r", "join_singular_values", "join_qr_svd",
     "join_qr_svd_host", "batch_join", "get_status", "Solver", "STATUS_NAMES", "event_array", "kernel_launches",
-    "host_workspace_size", "PHASES", "NUM_PHASE_EVENTS",
+    "host_workspace_size", "PHASES", "NUM_PHASE_EVENTS", "join_singular_values_fixed", "FIXED_SCRATCH_BYTES",
 ]
 
 PATH_FP64, PATH_MIXED = 0, 1
@@ -70,7 +70,8 @@ class Grouping(ctypes.Structure):
 EXPORTS = ["figaro_default_options", "figaro_workspace_size", "figaro_join_group", "figaro_join_head_tail",
            "figaro_join_qr_r", "figaro_join_singular_values", "figaro_batch_workspace_size", "figaro_batch_join",
            "figaro_get_status", "figaro_get_info", "figaro_status_string", "figaro_version",
-           "figaro_kernel_launches"]
+           "figaro_kernel_launches", "figaro_join_singular_values_fixed"]
+FIXED_SCRATCH_BYTES = 32 << 20
 NUM_PHASE_EVENTS = 9
 PHASES = ["grouping", "head_tail_a", "head_tail_b", "gram1", "chol1", "gram2", "chol2", "jacobi"]
 FLAG_TEST_WITHHOLD = 1 << 8
@@ -96,6 +97,7 @@ def library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.figaro_join_head_tail.argtypes = [P(Table), P(Table), P(Options), vp, vp, vp, vp, sz, vp]
         lib.figaro_join_qr_r.argtypes = [P(Table), P(Table), P(Options), vp, I64, vp, sz, vp]
         lib.figaro_join_singular_values.argtypes = [P(Table), P(Table), P(Options), vp, vp, I64, vp, sz, vp]
+        lib.figaro_join_singular_values_fixed.argtypes = [P(Table), P(Table), P(Options), vp, vp, I64, P(vp), vp]
         lib.figaro_batch_workspace_size.argtypes = [I32, P(Table), P(Table), P(Options), P(sz)]
         lib.figaro_batch_join.argtypes = [I32, P(Table), P(Table), P(Options), P(vp), P(vp), vp, sz, vp]
         lib.figaro_get_status.argtypes = [vp, vp]
@@ -342,6 +344,25 @@ def join_qr_svd_host(A, B, R_out, sigma_out, workspace, stream=None, **opts):
     _check(lib.figaro_join_singular_values(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(o), ctypes.c_void_p(sptr),
                                            ctypes.c_void_p(rptr), n, ctypes.c_void_p(workspace.data_ptr()),
                                            workspace.numel(), _stream_handle(stream)), "figaro_join_singular_values")
+
+
+def join_singular_values_fixed(A, B, sigma, R=None, stream=None, **opts) -> int:
+    """figaro_join_singular_values_fixed: sigma (and R when given) of the
+    join into caller-owned float64 device tensors, with the library's own
+    fixed scratch (FIXED_SCRATCH_BYTES per device).  Returns the scratch's
+    device address, which the C calls figaro_get_status / figaro_get_info
+    accept as their workspace argument."""
+    lib = library()
+    ta, tb = _device_table(*A), _device_table(*B)
+    o = _options(**opts)
+    n = ta.n + tb.n
+    rp = ctypes.c_void_p(R.data_ptr()) if R is not None else None
+    ldr = R.stride(0) if R is not None else n
+    scratch = ctypes.c_void_p(0)
+    _check(lib.figaro_join_singular_values_fixed(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(o),
+                                                 ctypes.c_void_p(sigma.data_ptr()), rp, ldr, ctypes.byref(scratch),
+                                                 _stream_handle(stream)), "figaro_join_singular_values_fixed")
+    return int(scratch.value or 0)
 
 
 def host_workspace_size(A, B, **opts) -> int:

@@ -291,6 +291,40 @@ figaro_status run_qr_svd(Call& c, double* R_out, int64_t ldr, double* sigma, int
   return FIGARO_OK;
 }
 
+// Library-owned scratch of figaro_join_singular_values_fixed (a fixed-size
+// device array, so the call needs no allocation).  Its address is looked up
+// once per device, with that device current.
+__device__ __align__(256) unsigned char g_fixed_scratch[FIGARO_FIXED_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_fixed_mu;
+void* g_fixed_ptr[kMaxDevices] = {};
+
+figaro_status fixed_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FIGARO_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return FIGARO_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_fixed_mu);
+  if (!g_fixed_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_fixed_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return FIGARO_ERR_CUDA;
+    }
+    g_fixed_ptr[dev] = p;
+  }
+  *out = g_fixed_ptr[dev];
+  return FIGARO_OK;
+}
+
+// The device of the first non-empty device-resident table becomes current.
+figaro_status bind_input_device(const figaro_table* A, const figaro_table* B) {
+  const figaro_table* tabs[2] = {A, B};
+  for (const figaro_table* T : tabs)
+    if (T->memory == FIGARO_MEM_DEVICE && T->m > 0) return bind_device(T->x);
+  return FIGARO_OK;
+}
+
 }  // namespace
 }  // namespace figaro
 
@@ -397,6 +431,25 @@ figaro_status figaro_join_singular_values(const figaro_table* A, const figaro_ta
   if (R_out && ldr < c.p.n) return FIGARO_ERR_INVALID_ARG;
   const int host_out = opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT);
   return run_qr_svd(c, R_out, R_out ? ldr : c.p.n, sigma, host_out);
+}
+
+figaro_status figaro_join_singular_values_fixed(const figaro_table* A, const figaro_table* B,
+                                                const figaro_options* opt, double* sigma, double* R_out,
+                                                int64_t ldr, void** scratch_out, void* stream) {
+  if (!sigma) return FIGARO_ERR_INVALID_ARG;
+  figaro_status st = check_pair(A, B, opt);
+  if (st != FIGARO_OK) return st;
+  st = bind_input_device(A, B);
+  if (st != FIGARO_OK) return st;
+  size_t need = 0;
+  st = figaro_workspace_size(A, B, opt, &need);
+  if (st != FIGARO_OK) return st;
+  if (need > FIGARO_FIXED_SCRATCH_BYTES) return FIGARO_ERR_WORKSPACE_TOO_SMALL;
+  void* ws = nullptr;
+  st = fixed_scratch(&ws);
+  if (st != FIGARO_OK) return st;
+  if (scratch_out) *scratch_out = ws;
+  return figaro_join_singular_values(A, B, opt, sigma, R_out, ldr, ws, FIGARO_FIXED_SCRATCH_BYTES, stream);
 }
 
 figaro_status figaro_batch_workspace_size(int32_t count, const figaro_table* A, const figaro_table* B,
