@@ -82,9 +82,10 @@ typedef enum figaro_gram_engine {
 
 enum {
   FIGARO_FLAG_HOST_OUTPUT = 1,     /* R / sigma pointers are host memory */
-  /* Fault injection for tests: the first chunk of each table's head/tail
-   * step withholds its look-back status, so the next chunk's bounded wait
-   * runs out and the call records FIGARO_ERR_DEVICE_TIMEOUT. */
+  /* Fault injection for tests: the first tile of table A in the key
+   * grouping step withholds its run-count look-back word, so the next
+   * tile's bounded wait runs out (after spin_limit polls) and the call
+   * records FIGARO_ERR_DEVICE_TIMEOUT; the later steps then skip their work. */
   FIGARO_FLAG_TEST_WITHHOLD = 1 << 8
 };
 

@@ -73,7 +73,7 @@ EXPORTS = ["figaro_default_options", "figaro_workspace_size", "figaro_join_group
            "figaro_kernel_launches", "figaro_join_singular_values_fixed"]
 FIXED_SCRATCH_BYTES = 32 << 20
 NUM_PHASE_EVENTS = 9
-PHASES = ["grouping", "head_tail_a", "head_tail_b", "gram1", "chol1", "gram2", "chol2", "jacobi"]
+PHASES = ["grouping", "ht_carry", "head_tail", "gram1", "chol1", "gram2", "chol2", "jacobi"]
 FLAG_TEST_WITHHOLD = 1 << 8
 
 

@@ -12,7 +12,7 @@
 
 namespace figaro {
 
-int ht_chunk_rows(int n);
+int ht_chunk_rows(int n, int in_f64, int mixed);
 void gram_geometry(int kout, int* kpad, int* ntiles, int* slices, int* tpt);
 
 namespace {
@@ -94,12 +94,14 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
     T.run_off = b.take<int32_t>(static_cast<size_t>(m) + 1);
     T.other = b.take<int32_t>(static_cast<size_t>(m));
     T.hdslot = b.take<int32_t>(static_cast<size_t>(m));
+    T.run_info = b.take<int32_t>(static_cast<size_t>(m) * 4);
     T.tail = b.take<char>(static_cast<size_t>(m) * n * ec);
-    T.chunk_rows = ht_chunk_rows(n);
+    T.chunk_rows = ht_chunk_rows(n, in_f64, mixed);
     T.chunks = static_cast<int>(ceil_div(m, T.chunk_rows));
-    T.chunk_status = b.take<uint32_t>(static_cast<size_t>(T.chunks));
-    T.chunk_agg = b.take<double>(static_cast<size_t>(T.chunks) * n);
-    T.chunk_inc = b.take<double>(static_cast<size_t>(T.chunks) * n);
+    T.cbeg = b.take<int32_t>(static_cast<size_t>(T.chunks) + 1);
+    T.cflag = b.take<uint32_t>(static_cast<size_t>(T.chunks));
+    T.piece = b.take<double>(static_cast<size_t>(T.chunks) * n);
+    T.carry = b.take<double>(static_cast<size_t>(T.chunks) * n);
   }
   const int n = p.n;
   p.head = b.take<char>(static_cast<size_t>(m1 > 0 ? m1 : 1) * n * ec);
@@ -259,9 +261,9 @@ figaro_status run_grouping(Call& c) {
 }
 
 figaro_status run_factor(Call& c, double* R_dev, int64_t ldr) {
-  FIGARO_TRY(launch_head_tail(c.p, 0, c.s));
+  FIGARO_TRY(launch_ht_carry(c.p, c.s));
   FIGARO_TRY(c.mark(2));
-  FIGARO_TRY(launch_head_tail(c.p, 1, c.s));
+  FIGARO_TRY(launch_ht_main(c.p, c.s));
   FIGARO_TRY(c.mark(3));
   FIGARO_TRY(launch_gram_pass(c.p, 1, c.s));
   FIGARO_TRY(c.mark(4));
@@ -405,8 +407,8 @@ figaro_status figaro_join_head_tail(const figaro_table* A, const figaro_table* B
   if (B->m > 0) c.p.t[1].tail = tail_b;
   st = run_grouping(c);
   if (st != FIGARO_OK) return st;
-  FIGARO_TRY(launch_head_tail(c.p, 0, c.s));
-  FIGARO_TRY(launch_head_tail(c.p, 1, c.s));
+  FIGARO_TRY(launch_ht_carry(c.p, c.s));
+  FIGARO_TRY(launch_ht_main(c.p, c.s));
   return FIGARO_OK;
 }
 

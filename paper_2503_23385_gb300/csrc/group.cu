@@ -37,6 +37,7 @@ struct TwoTables {
   int nb0;  // tiles of table 0
   int nb;   // tiles of both tables
   int64_t spin_limit;
+  int withhold;  // test-only: tile 0 of table A never publishes its run count
 };
 
 __device__ __forceinline__ uint64_t ld_acquire64(const uint64_t* p) {
@@ -77,8 +78,7 @@ __device__ __forceinline__ uint64_t wait_word(const uint64_t* p, int64_t limit) 
   return v;
 }
 
-__global__ void reset_kernel(DevHeader* h, uint32_t* s0, int n0, uint32_t* s1, int n1, uint64_t* g0, int64_t ng0,
-                             uint64_t* g1, int64_t ng1) {
+__global__ void reset_kernel(DevHeader* h, uint64_t* g0, int64_t ng0, uint64_t* g1, int64_t ng1) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid == 0) {
     h->status = 0;
@@ -91,8 +91,6 @@ __global__ void reset_kernel(DevHeader* h, uint32_t* s0, int n0, uint32_t* s1, i
     h->jacobi_sweeps = 0;
   }
   const int stride = gridDim.x * blockDim.x;
-  for (int i = tid; i < n0; i += stride) s0[i] = 0u;
-  for (int i = tid; i < n1; i += stride) s1[i] = 0u;
   for (int64_t i = tid; i < ng0; i += stride) g0[i] = 0ull;
   for (int64_t i = tid; i < ng1; i += stride) g1[i] = 0ull;
 }
@@ -282,7 +280,7 @@ __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
     uint64_t* mine = T.run_status + tile;
     uint64_t excl = 0;
     if (tile == 0) {
-      st_release64(mine, kFlagInc | tile_total);
+      if (!(a.withhold && t == 0)) st_release64(mine, kFlagInc | tile_total);
     } else {
       st_release64(mine, kFlagAgg | tile_total);
       for (int j = tile - 1; j >= 0; --j) {
@@ -339,7 +337,8 @@ __device__ __forceinline__ int64_t lower_bound_key(const int32_t* keys, int64_t 
 
 // For every run of either table: the size of the run with the same key in
 // the other table (0 if none) and the head slot of the key group (the run
-// index on A's side).
+// index on A's side), also packed with the run's row range into one 16-byte
+// record for the head/tail step.
 __global__ void match_kernel(TwoTables a) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   DevHeader* h = a.h;
@@ -351,8 +350,9 @@ __global__ void match_kernel(TwoTables a) {
     const int64_t j = lower_bound_key(B.run_key, UB, k);
     const int32_t mine = A.run_off[i + 1] - A.run_off[i];
     A.hdslot[i] = static_cast<int32_t>(i);
+    int32_t other = 0;
     if (j < UB && B.run_key[j] == k) {
-      const int32_t other = B.run_off[j + 1] - B.run_off[j];
+      other = B.run_off[j + 1] - B.run_off[j];
       A.other[i] = other;
       atomicAdd(reinterpret_cast<unsigned long long*>(&h->num_groups), 1ull);
       atomicAdd(reinterpret_cast<unsigned long long*>(&h->reduced_rows),
@@ -360,17 +360,19 @@ __global__ void match_kernel(TwoTables a) {
     } else {
       A.other[i] = 0;
     }
+    reinterpret_cast<int4*>(A.run_info)[i] = make_int4(A.run_off[i], A.run_off[i + 1], other, static_cast<int32_t>(i));
   }
   if (i < UB) {
     const int32_t k = B.run_key[i];
     const int64_t j = lower_bound_key(A.run_key, UA, k);
+    int32_t other = 0, slot = -1;
     if (j < UA && A.run_key[j] == k) {
-      B.other[i] = A.run_off[j + 1] - A.run_off[j];
-      B.hdslot[i] = static_cast<int32_t>(j);
-    } else {
-      B.other[i] = 0;
-      B.hdslot[i] = -1;
+      other = A.run_off[j + 1] - A.run_off[j];
+      slot = static_cast<int32_t>(j);
     }
+    B.other[i] = other;
+    B.hdslot[i] = slot;
+    reinterpret_cast<int4*>(B.run_info)[i] = make_int4(B.run_off[i], B.run_off[i + 1], other, slot);
   }
 }
 
@@ -383,19 +385,13 @@ int64_t group_status_words(int tiles) {
 }
 
 cudaError_t launch_reset(const Plan& p, cudaStream_t s) {
-  const int n0 = p.t[0].chunks, n1 = p.t[1].chunks;
   const int64_t g0 = p.t[0].tiles > 0 ? group_status_words(p.t[0].tiles) : 0;
   const int64_t g1 = p.t[1].tiles > 0 ? group_status_words(p.t[1].tiles) : 0;
-  int64_t work = n0 > n1 ? n0 : n1;
-  if (g0 > work) work = g0;
-  if (g1 > work) work = g1;
+  const int64_t work = g0 > g1 ? g0 : g1;
   int blocks = static_cast<int>((work + 255) / 256);
   if (blocks < 1) blocks = 1;
   if (blocks > 1024) blocks = 1024;
-  uint32_t* s0 = p.t[0].chunk_status;
-  uint32_t* s1 = p.t[1].chunk_status;
-  reset_kernel<<<blocks, 256, 0, s>>>(p.hdr, s0, s0 ? n0 : 0, s1, s1 ? n1 : 0, p.t[0].sort_status, g0,
-                                      p.t[1].sort_status, g1);
+  reset_kernel<<<blocks, 256, 0, s>>>(p.hdr, p.t[0].sort_status, g0, p.t[1].sort_status, g1);
   count_launches(1);
   // the histograms are accumulated with atomics: clear them too
   for (int t = 0; t < 2; ++t)
@@ -414,6 +410,7 @@ cudaError_t launch_grouping(const Plan& p, cudaStream_t s) {
   a.nb0 = p.t[0].tiles;
   a.nb = p.t[0].tiles + p.t[1].tiles;
   a.spin_limit = p.spin_limit;
+  a.withhold = p.withhold;
   if (a.nb == 0) return cudaSuccess;
   key_hist_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
   for (int pass = 0; pass < kMaxPasses; ++pass) sort_pass_kernel<<<a.nb, kSortThreads, 0, s>>>(a, pass);

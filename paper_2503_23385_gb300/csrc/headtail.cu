@@ -12,15 +12,28 @@
 // sqrt(j+1) written around the running mean, so that large column means do
 // not cancel in FP32.
 //
-// Work decomposition: every warp is an independent worker.  It takes a chunk
-// of consecutive sorted rows by ticket; its lanes form CG column groups of 4
-// columns x (32 / CG) row groups of 8 consecutive rows.  Each lane gathers its
-// rows through perm, scans them (compensated float-float sums on the mixed
-// path), the row groups are combined by a warp-shuffle segmented scan, and
-// the carry from earlier chunks comes from a decoupled look-back (bounded
-// waits; no block-wide barriers anywhere).  A second pass over the registers
-// writes the tail rows and, at each run's last row, the head row.
+// Work decomposition.  The sorted rows are cut into chunks whose boundaries
+// sit near multiples of L: the boundary at k L moves back to the start of
+// the run containing row k L when that run has at most L rows, so a chunk
+// (fewer than 2 L rows) holds whole runs, except where a run longer than L
+// crosses a boundary.  Only those long-run pieces need a carry (the sum of
+// the run's rows before the chunk), and it is computed before the main pass,
+// in a fixed order (results are bitwise reproducible):
+//   1. ht_plan:  per chunk (one warp), its first row and flags; for a chunk
+//                whose end falls inside a long run, the FP64 sum of its rows
+//                of that run (the "piece").
+//   2. ht_scan:  per table column, a segmented scan of the pieces along each
+//                long run gives every chunk's carry.
+//   3. ht_stream: persistent CTAs, each streaming a contiguous range of
+//                chunks tile by tile (see below): rows gathered through perm
+//                with cp.async, a segmented scan per (column, row slice)
+//                with compensated float-float sums on the mixed path, tail
+//                rows written back contiguously, the head part at each run's
+//                last row.
+// With uniform keys (runs much shorter than L) steps 1-2 touch only a few
+// words per chunk and step 3 reads every input row once.
 #include <cmath>
+#include <cstring>
 
 #include "common.cuh"
 #include "internal.h"
@@ -28,88 +41,165 @@
 namespace figaro {
 namespace {
 
-constexpr uint32_t kAggReady = 1u, kIncReady = 2u, kHasStart = 4u;
-constexpr int kV = 4;  // columns per lane
+constexpr int kHtBlock = 256;
+constexpr uint32_t kInside = 1u;  // chunk begins inside a run (needs a carry)
+constexpr uint32_t kWhole = 2u;   // chunk lies inside one run that continues past its end
 
-struct HtArgs {
+struct HtTable {
   const void* x;
   int64_t ld;
   int n;
-  int cg;          // column groups (power of two <= 32): lanes per row
   int64_t m;
+  int vec;          // 16-byte gathers (row bytes, leading dimension and base 16-byte aligned)
+  int gather;       // TMA gather4 of the rows (vec, and four rows a multiple of 128 bytes)
   const int32_t* perm;
   const int32_t* seg;
   const int32_t* run_off;
   const int32_t* other;
   const int32_t* hdslot;
-  void* tail;      // m x n, compute type, leading dimension n
-  void* head;      // rows x ld_head, compute type
-  int ld_head;
-  int head_col0;   // first column of this table's part of a head row
-  int zero_col0;   // A side: the other table's part of unmatched head rows is zeroed here
+  const int32_t* run_info;  // per run: first row, end row, partner run size, head slot
+  void* tail;       // m x n, compute type, leading dimension n
+  int head_col0;    // first column of this table's part of a head row
+  int zero_col0;    // A side: the other table's part of unmatched head rows is zeroed here
   int zero_n;
-  uint32_t* chunk_status;
-  double* chunk_agg;
-  double* chunk_inc;
+  int L;
   int chunks;
-  int chunk_rows;
-  uint32_t* ticket;
-  int32_t* status;
-  int64_t spin_limit;
-  int withhold;    // test-only: chunk 0 never publishes its look-back status
+  int32_t* cbeg;    // chunks + 1
+  uint32_t* cflag;  // chunks
+  double* piece;    // chunks x n
+  double* carry;    // chunks x n
 };
 
-template <typename Tin, bool kVec>
-__device__ __forceinline__ void load4(const Tin* src, int ncols, Tin (&out)[kV]) {
-  if constexpr (kVec && sizeof(Tin) == 4) {
-    if (ncols >= 4) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(src));
-      out[0] = q.x; out[1] = q.y; out[2] = q.z; out[3] = q.w;
-      return;
-    }
-  } else if constexpr (kVec && sizeof(Tin) == 8) {
-    if (ncols >= 4) {
-      const double2 q0 = __ldg(reinterpret_cast<const double2*>(src));
-      const double2 q1 = __ldg(reinterpret_cast<const double2*>(src) + 1);
-      out[0] = q0.x; out[1] = q0.y; out[2] = q1.x; out[3] = q1.y;
-      return;
-    }
-  }
-#pragma unroll
-  for (int v = 0; v < kV; ++v) out[v] = v < ncols ? src[v] : Tin(0);
+struct HtArgs {
+  HtTable t[2];
+  int c0;           // chunks of table 0: block g < c0 works on table 0
+  void* head;       // head_rows x ld_head, compute type
+  int ld_head;
+  int64_t head_rows;
+  int32_t* status;
+};
+
+__host__ __device__ inline int ht_align16(int v) { return (v + 15) & ~15; }
+
+__device__ __forceinline__ bool timed_out(const int32_t* status) {
+  return (*reinterpret_cast<const volatile int32_t*>(status) & kStatusTimeout) != 0;
 }
 
-template <typename Tc, bool kVec>
-__device__ __forceinline__ void store4(Tc* dst, int ncols, const Tc (&val)[kV]) {
-  if constexpr (kVec && sizeof(Tc) == 4) {
-    if (ncols >= 4) {
-      *reinterpret_cast<float4*>(dst) = make_float4(val[0], val[1], val[2], val[3]);
-      return;
-    }
-  } else if constexpr (kVec && sizeof(Tc) == 8) {
-    if (ncols >= 4) {
-      reinterpret_cast<double2*>(dst)[0] = make_double2(val[0], val[1]);
-      reinterpret_cast<double2*>(dst)[1] = make_double2(val[2], val[3]);
-      return;
-    }
-  }
-#pragma unroll
-  for (int v = 0; v < kV; ++v)
-    if (v < ncols) dst[v] = val[v];
+__device__ __forceinline__ int64_t clamp_idx(int64_t v, int64_t hi) { return v < 0 ? 0 : (v >= hi ? hi - 1 : v); }
+
+// First row of chunk k and whether it begins inside a run (see above).  The
+// result always lies in (k L - L, k L], so a chunk has fewer than 2 L rows
+// even if the run arrays were inconsistent.
+__device__ int64_t chunk_begin(const HtTable& T, int k, bool& inside) {
+  inside = false;
+  const int64_t i = static_cast<int64_t>(k) * T.L;
+  if (k == 0) return 0;
+  if (i >= T.m) return T.m;
+  const int64_t r = clamp_idx(T.seg[i], T.m);
+  const int64_t s = T.run_off[r], e = T.run_off[r + 1];
+  if (s <= i && i < e && i - s < T.L && e - s <= T.L) return s;
+  inside = s != i;
+  return i;
 }
 
-template <typename T>
-__device__ __forceinline__ void seg_combine(bool ef, const Acc<T> (&ev)[kV], bool& lf, Acc<T> (&lv)[kV]) {
-  // (earlier) then (later): the later sum restarts if a run starts in it
-  if (!lf) {
-#pragma unroll
-    for (int v = 0; v < kV; ++v) {
-      Acc<T> t = ev[v];
-      t.add(lv[v]);
-      lv[v] = t;
+template <typename Tin, typename Tc>
+__device__ __forceinline__ double as_compute_double(const Tin* X, int64_t off) {
+  return static_cast<double>(static_cast<Tc>(X[off]));
+}
+
+// 1. chunk table and long-run pieces: one warp per chunk
+constexpr int kPlanWarps = kHtBlock / 32;
+template <typename Tin, typename Tc>
+__global__ void __launch_bounds__(kHtBlock) ht_plan_kernel(HtArgs a, int total) {
+  const int g = blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= total || timed_out(a.status)) return;
+  const int t = g < a.c0 ? 0 : 1;
+  const int k = t ? g - a.c0 : g;
+  const HtTable& T = a.t[t];
+  int64_t lo = 0, hi = 0;
+  if (lane == 0) {
+    bool in0, in1;
+    const int64_t b0 = chunk_begin(T, k, in0);
+    const int64_t b1 = chunk_begin(T, k + 1, in1);
+    uint32_t f = in0 ? kInside : 0u;
+    if (in1 && b1 < T.m) {  // this chunk ends inside a long run: its piece of that run
+      const int64_t r1 = clamp_idx(T.seg[b1], T.m);
+      const int64_t s1 = T.run_off[r1];
+      lo = s1 > b0 ? s1 : b0;
+      hi = b1 < lo ? lo : b1;
+      if (in0 && clamp_idx(T.seg[b0], T.m) == r1) f |= kWhole;
     }
+    T.cbeg[k] = static_cast<int32_t>(b0);
+    T.cflag[k] = f;
+    if (k == T.chunks - 1) T.cbeg[T.chunks] = static_cast<int32_t>(T.m);
   }
-  lf = lf || ef;
+  lo = __shfl_sync(0xffffffffu, lo, 0);
+  hi = __shfl_sync(0xffffffffu, hi, 0);
+  if (hi <= lo) return;
+  // lanes own columns lane, lane + 32, ...; rows in order (fixed summation order)
+  const Tin* X = static_cast<const Tin*>(T.x);
+  const int n = T.n;
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    const int c = c0 + lane;
+    double sum = 0.0;
+    int64_t i = lo;
+    for (; i + 4 <= hi; i += 4) {
+      int64_t row[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) row[u] = clamp_idx(T.perm[i + u], T.m);
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      if (c < n) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = as_compute_double<Tin, Tc>(X, row[u] * T.ld + c);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sum += v[u];
+    }
+    for (; i < hi; ++i) {
+      const int64_t row = clamp_idx(T.perm[i], T.m);
+      if (c < n) sum += as_compute_double<Tin, Tc>(X, row * T.ld + c);
+    }
+    if (c < n) T.piece[static_cast<int64_t>(k) * n + c] = sum;
+  }
+}
+
+// 2. carries: per (table, column), I_q = piece_q + (whole_q ? I_{q-1} : 0)
+// and carry_k = I_{k-1} for every chunk k that begins inside a run.
+__global__ void __launch_bounds__(kHtBlock) ht_scan_kernel(HtArgs a, int n0) {
+  __shared__ double s_agg[kHtBlock];
+  __shared__ int s_head[kHtBlock];
+  const int t = blockIdx.x < n0 ? 0 : 1;
+  const int c = t ? blockIdx.x - n0 : blockIdx.x;
+  const HtTable& T = a.t[t];
+  const int K = T.chunks;
+  if (K == 0 || timed_out(a.status)) return;
+  const int n = T.n;
+  const int per = (K + kHtBlock - 1) / kHtBlock;
+  const int q0 = threadIdx.x * per, q1 = q0 + per < K ? q0 + per : K;
+  auto value = [&](int q) -> double {
+    return (q + 1 < K && (T.cflag[q + 1] & kInside)) ? T.piece[static_cast<int64_t>(q) * n + c] : 0.0;
+  };
+  double agg = 0.0;
+  int head = 0;
+  for (int q = q0; q < q1; ++q) {
+    if (!(T.cflag[q] & kWhole)) {
+      agg = 0.0;
+      head = 1;
+    }
+    agg += value(q);
+  }
+  s_agg[threadIdx.x] = agg;
+  s_head[threadIdx.x] = head;
+  __syncthreads();
+  int u = static_cast<int>(threadIdx.x) - 1;
+  while (u >= 0 && !s_head[u]) --u;
+  double I = 0.0;
+  for (int v = u < 0 ? 0 : u; v < static_cast<int>(threadIdx.x); ++v) I += s_agg[v];
+  for (int q = q0; q < q1; ++q) {
+    I = ((T.cflag[q] & kWhole) ? I : 0.0) + value(q);
+    if (q + 1 < K && (T.cflag[q + 1] & kInside)) T.carry[static_cast<int64_t>(q + 1) * n + c] = I;
+  }
 }
 
 __device__ __forceinline__ float tail_weight(float mo, int j) {
@@ -124,301 +214,696 @@ __device__ __forceinline__ double head_weight(double mo, int mg) { return sqrt(m
 __device__ __forceinline__ float recip(float j) { return __frcp_rn(j); }
 __device__ __forceinline__ double recip(double j) { return 1.0 / j; }
 
-template <typename Tin, typename Tc, bool kVec>
-__global__ void __launch_bounds__(kHtThreads) head_tail_kernel(HtArgs a) {
-  constexpr int RPT = kHtRowsPerThread;
-  const int CG = a.cg;
-  const int lane = threadIdx.x & 31;
-  const int cg = lane & (CG - 1);
-  const int rg = lane / CG;            // row group inside the warp
-  const int col0 = cg * kV;
-  const int ncols = a.n - col0;        // columns this lane owns (<= 0: none)
-  const int last_rg_lane0 = 32 - CG;   // first lane of the last row group
-  const Tin* X = static_cast<const Tin*>(a.x);
-  Tc* TL = static_cast<Tc*>(a.tail);
-  Tc* HD = static_cast<Tc*>(a.head);
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
 
-  for (;;) {
-    int chunk = 0;
-    if (lane == 0) chunk = static_cast<int>(atomicAdd(a.ticket, 1u));
-    chunk = __shfl_sync(0xffffffffu, chunk, 0);
-    if (chunk >= a.chunks) break;
-    const int64_t row0 = static_cast<int64_t>(chunk) * a.chunk_rows;
-    const int64_t rbase = row0 + static_cast<int64_t>(rg) * RPT;
+// ---- 3. streaming head/tail pass ------------------------------------------
+//
+// Persistent CTAs; CTA b of a table owns a contiguous range of chunks and
+// streams its rows in tiles of TR rows through a ring of kHtStages shared-
+// memory stages.  Warp 0 is the producer: it reads perm and the run index of
+// a tile's rows and issues cp.async copies of the rows (gathered through
+// perm) and of their run data into the next free stage, which completes on
+// that stage's "full" mbarrier (cp.async.mbarrier.arrive).  Warps 1-8 consume
+// the stages in order: per-row weights; a segmented sum per (column, row
+// slice); the slice's carry-in from the earlier slices and the state carried
+// from the previous tile; tail rows stored straight to global memory (each
+// warp writes whole row segments), head parts at run ends; then they free
+// the stage ("empty" mbarrier).  All waits are bounded (spin_limit).
+//
+// Precision on the mixed path: the running sum S of a run is a float-float
+// pair carried across slices and tiles; inside a slice (a few rows) and
+// across the slices of one tile plain FP32 partial sums are added to it, so
+// S / j carries an error of a few FP32 ulps of the partial sums, not of S.
+constexpr int kHtStages = 3;
+constexpr int kIdxRing = 3;  // tiles of perm / run index in flight ahead of the gathers
+constexpr int kHtConsumers = 256;
+constexpr int kHtStreamThreads = kHtConsumers + 32;
 
-    // ---- rows and their run structure ------------------------------------
-    // seg of the row before my first and of the row after my last tell where
-    // runs start and end; run-level data is loaded once per run.
-    int32_t segs[RPT + 1];
-#pragma unroll
-    for (int r = 0; r <= RPT; ++r) {
-      const int64_t i = rbase + r;
-      segs[r] = i < a.m ? a.seg[i] : -1;
-    }
-    const int32_t seg_prev = (rbase > 0 && rbase - 1 < a.m) ? a.seg[rbase - 1] : -1;
-    Tc x[RPT][kV];
-    int jl[RPT];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int64_t i = rbase + r;
-#pragma unroll
-      for (int v = 0; v < kV; ++v) x[r][v] = Tc(0);
-      if (i < a.m && ncols > 0) {
-        const int32_t p = a.perm[i];
-        Tin tmp[kV];
-        load4<Tin, kVec>(X + static_cast<int64_t>(p) * a.ld + col0, ncols, tmp);
-#pragma unroll
-        for (int v = 0; v < kV; ++v) x[r][v] = static_cast<Tc>(tmp[v]);
-      }
-    }
-    // local index of each row inside its run
-    {
-      int j = 0;
-      if (segs[0] >= 0) j = segs[0] == seg_prev ? static_cast<int>(rbase - a.run_off[segs[0]]) : 0;
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        if (r > 0) j = (segs[r] == segs[r - 1]) ? j + 1 : 0;
-        jl[r] = segs[r] >= 0 ? j : -1;
-      }
-    }
+__host__ __device__ inline int ht_tile_rows(int n, int es_in) {
+  int tr = 256;
+  while (tr > 16 && tr * n * es_in > 16384) tr >>= 1;
+  return tr;
+}
 
-    // ---- thread-local segmented scan -------------------------------------
-    bool f = false;
-    Acc<Tc> sv[kV];
-#pragma unroll
-    for (int v = 0; v < kV; ++v) sv[v].zero();
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      if (jl[r] == 0) {
-        f = true;
-#pragma unroll
-        for (int v = 0; v < kV; ++v) sv[v].zero();
-      }
-#pragma unroll
-      for (int v = 0; v < kV; ++v) sv[v].add(x[r][v]);
-    }
+struct HtStream {
+  int TR, P;
+  int stage_bytes;  // per stage: the rows (128-byte aligned), their run records
+  int x, info;
+  int w, rj, hw, hs, agg, flag, state, perm, bars, bytes;
+};
 
-    // ---- warp scan across row groups (lanes with the same cg) ------------
-    bool inf = f;
-    Acc<Tc> inv[kV];
-#pragma unroll
-    for (int v = 0; v < kV; ++v) inv[v] = sv[v];
-    for (int d = CG; d < 32; d <<= 1) {
-      const bool of = __shfl_up_sync(0xffffffffu, inf, d);
-      Acc<Tc> ov[kV];
-#pragma unroll
-      for (int v = 0; v < kV; ++v) ov[v] = shfl_up_acc(inv[v], d);
-      if (lane >= d) seg_combine<Tc>(of, ov, inf, inv);
-    }
-    // exclusive value of my row group (the inclusive one of the group before)
-    bool exf = false;
-    Acc<Tc> exv[kV];
-    {
-      const bool of = __shfl_up_sync(0xffffffffu, inf, CG);
-#pragma unroll
-      for (int v = 0; v < kV; ++v) {
-        exv[v] = shfl_up_acc(inv[v], CG);
-        if (lane < CG) exv[v].zero();
-      }
-      exf = lane >= CG ? of : false;
-    }
-    // chunk aggregate = inclusive value of the last row group
-    const bool chunk_start = __shfl_sync(0xffffffffu, inf, last_rg_lane0);
-    if (lane >= last_rg_lane0 && ncols > 0) {
-#pragma unroll
-      for (int v = 0; v < kV; ++v)
-        if (v < ncols) a.chunk_agg[static_cast<int64_t>(chunk) * a.n + col0 + v] = inv[v].to_double();
-      __threadfence();
-    }
-    __syncwarp();
+__host__ __device__ inline int ht_align128(int v) { return (v + 127) & ~127; }
 
-    // ---- publish the aggregate, then look back for the carry -------------
-    const bool publish = !(a.withhold && chunk == 0);
-    const bool need = __shfl_sync(0xffffffffu, jl[0] > 0, 0);  // chunk starts inside a run
-    int stop = -1, kind = 0;
-    if (lane == 0) {
-      if (publish) st_release(&a.chunk_status[chunk], kAggReady | (chunk_start ? kHasStart : 0u));
-      if (need) {
-        int j = chunk - 1;
-        for (;;) {
-          uint32_t st = ld_acquire(&a.chunk_status[j]);
-          int64_t spins = 0;
-          while (st == 0u) {
-            if (++spins > a.spin_limit) break;
-            __nanosleep(32);
-            st = ld_acquire(&a.chunk_status[j]);
-          }
-          if (st == 0u) {  // gave up: record it and continue with a zero carry
-            set_status(a.status, kStatusTimeout);
-            stop = j;
-            kind = 3;
-            break;
-          }
-          if (st & kHasStart) {
-            stop = j;
-            kind = 1;
-            break;
-          }
-          if (st & kIncReady) {
-            stop = j;
-            kind = 2;
-            break;
-          }
-          --j;  // aggregate only: include it and keep walking
-        }
-      }
+// Layout relative to a 128-byte aligned base (the launch adds 128 bytes of slack).
+__host__ __device__ inline HtStream ht_stream_layout(int n, int es_in, int es_c) {
+  HtStream L;
+  L.TR = ht_tile_rows(n, es_in);
+  L.P = kHtConsumers / n;
+  const int TR = L.TR;
+  int o = 0;
+  L.x = o;
+  o = ht_align128(o + TR * n * es_in);
+  L.info = o;
+  o = ht_align128(o + TR * 16);
+  L.stage_bytes = o;
+  o = kHtStages * L.stage_bytes;
+  L.w = o;
+  o = ht_align16(o + TR * es_c);
+  L.rj = o;
+  o = ht_align16(o + TR * es_c);
+  L.hw = o;
+  o = ht_align16(o + TR * es_c);
+  L.hs = o;
+  o = ht_align16(o + TR * 4);
+  L.agg = o;  // slice sums (scalar path) or per-warp column-group totals (vector path)
+  const int agg_elems = L.P * n > 8 * n ? L.P * n : 8 * n;
+  o = ht_align16(o + agg_elems * es_c);
+  L.flag = o;
+  o = ht_align16(o + (L.P > 8 * n ? L.P : 8 * n) * 4);
+  L.state = o;  // two buffers x n columns x (hi, lo) in the compute type
+  o = ht_align16(o + 2 * n * 2 * es_c);
+  L.perm = o;   // producer ring of row indices and run indices, kIdxRing tiles ahead
+  o = ht_align16(o + kIdxRing * 2 * TR * 4);
+  L.bars = o;
+  o = ht_align16(o + 2 * kHtStages * 8);
+  L.bytes = o + 128;
+  return L;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+// Bounded wait that lets the hardware suspend the thread (up to ~20 us per
+// try) until the phase completes, so waiting threads take no issue slots.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* b, uint32_t parity, int64_t limit) {
+  const int64_t tries = limit / 1024 + 1;
+  for (int64_t i = 0; i < tries; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity), "r"(20000u)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+// Arrives on the mbarrier once all earlier cp.async copies of this thread are done.
+__device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+// TMA gather of four rows (row indices r0..r3, all columns of the box) into
+// shared memory, completing on the mbarrier's transaction count.
+__device__ __forceinline__ void tma_gather4(void* dst, const CUtensorMap* map, int r0, int r1, int r2, int r3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kHtConsumers) : "memory"); }
+
+// Running sum of a run: float-float (hi, lo) on the mixed path, one double
+// on the plain path; x is added exactly into the pair (TwoSum).
+__device__ __forceinline__ void run_add(float& hi, float& lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+__device__ __forceinline__ void run_add(double& hi, double& lo, double x) { hi += x; }
+
+// Four consecutive elements: shared-memory input row piece, global tail row piece.
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const float* p, double (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+__device__ __forceinline__ void load4(const double* p, float (&v)[4]) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = static_cast<float>(q0.x); v[1] = static_cast<float>(q0.y);
+  v[2] = static_cast<float>(q1.x); v[3] = static_cast<float>(q1.y);
+}
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// V = 4: every consumer thread owns 4 consecutive columns (n a multiple of 4
+// with n / 4 a power of two <= 32, tail rows 16-byte aligned); the sums of
+// the row slices of one warp are combined by a warp-shuffle segmented scan,
+// those of the 8 consumer warps through shared memory.  V = 1: one column
+// per thread, any n.
+template <typename Tin, typename Tc, int V>
+__global__ void __launch_bounds__(kHtStreamThreads)
+    ht_stream_kernel(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1, HtArgs a,
+                     int g0, int g1, int64_t spin_limit) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  unsigned char* sm = sm_raw + ((128u - (smem_addr(sm_raw) & 127u)) & 127u);
+  const int t = static_cast<int>(blockIdx.x) < g0 ? 0 : 1;
+  const int cb = t ? static_cast<int>(blockIdx.x) - g0 : static_cast<int>(blockIdx.x);
+  const int G = t ? g1 : g0;
+  const HtTable& T = a.t[t];
+  const int n = T.n;
+  const HtStream L = ht_stream_layout(n, static_cast<int>(sizeof(Tin)), static_cast<int>(sizeof(Tc)));
+  const int TR = L.TR, P = L.P;
+  // chunk range of this CTA, and its rows
+  const int k_lo = static_cast<int>(static_cast<int64_t>(cb) * T.chunks / G);
+  const int k_hi = static_cast<int>(static_cast<int64_t>(cb + 1) * T.chunks / G);
+  const int64_t R0 = T.cbeg[k_lo], R1 = T.cbeg[k_hi];
+  if (!(R0 >= 0 && R1 <= T.m && R1 >= R0)) return;  // impossible for a consistent chunk table
+  const bool inside = (T.cflag[k_lo] & kInside) != 0;
+  const int ntiles = static_cast<int>((R1 - R0 + TR - 1) / TR);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bars);
+  uint64_t* empty = full + kHtStages;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kHtStages; ++q) {
+      mbar_init(&full[q], T.gather ? 33 : 32);  // 32 cp.async arrivals (+ the TMA byte count)
+      mbar_init(&empty[q], 1);
     }
-    stop = __shfl_sync(0xffffffffu, stop, 0);
-    kind = __shfl_sync(0xffffffffu, kind, 0);
-    double carry[kV];
-#pragma unroll
-    for (int v = 0; v < kV; ++v) carry[v] = 0.0;
-    if (need && kind != 3 && rg == 0 && ncols > 0) {
-#pragma unroll
-      for (int v = 0; v < kV; ++v) {
-        if (v >= ncols) continue;
-        const int col = col0 + v;
-        double c = (kind == 1) ? __ldcg(&a.chunk_agg[static_cast<int64_t>(stop) * a.n + col])
-                               : __ldcg(&a.chunk_inc[static_cast<int64_t>(stop) * a.n + col]);
-        for (int j = stop + 1; j < chunk; ++j) c += __ldcg(&a.chunk_agg[static_cast<int64_t>(j) * a.n + col]);
-        carry[v] = c;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_skip = timed_out(a.status) ? 1 : 0;  // an earlier step gave up: skip (one decision per CTA)
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    // Per tile u: the perm / run-index rows of tile u + 2 are copied into the
+    // index ring (their own cp.async group), then, once tile u's indices have
+    // landed (wait_group), the run data and the feature rows of tile u are
+    // gathered into the stage, completing on its "full" barrier.
+    const char* xb = static_cast<const char*>(T.x);
+    const int64_t ldb = T.ld * static_cast<int64_t>(sizeof(Tin));
+    const int row_bytes = n * static_cast<int>(sizeof(Tin));
+    int32_t* ring = reinterpret_cast<int32_t*>(sm + L.perm);  // [kIdxRing][2][TR]
+    auto fetch = [&](int u) {  // asynchronous copy of tile u's perm and run indices
+      const int64_t r0 = R0 + static_cast<int64_t>(u) * TR;
+      const int cnt = static_cast<int>(R1 - r0 < TR ? R1 - r0 : TR);
+      int32_t* dp = ring + (u % kIdxRing) * 2 * TR;
+      for (int r = lane; r < cnt; r += 32) {
+        cp_async(dp + r, T.perm + r0 + r, 4);
+        cp_async(dp + TR + r, T.seg + r0 + r, 4);
       }
+    };
+    for (int u = 0; u < 2; ++u) {  // always two groups, so that wait_group 2 below finds tile u's
+      if (u < ntiles) fetch(u);
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-#pragma unroll
-    for (int v = 0; v < kV; ++v) carry[v] = __shfl_sync(0xffffffffu, carry[v], cg);  // from row group 0
-    if (!chunk_start) {  // inclusive prefix = carry + aggregate
-      if (lane >= last_rg_lane0 && ncols > 0) {
-#pragma unroll
-        for (int v = 0; v < kV; ++v)
-          if (v < ncols) a.chunk_inc[static_cast<int64_t>(chunk) * a.n + col0 + v] = carry[v] + inv[v].to_double();
-        __threadfence();
+    for (int u = 0; u < ntiles; ++u) {
+      const int st = u % kHtStages;
+      if (u >= kHtStages &&
+          !mbar_wait_sleep(&empty[st], static_cast<uint32_t>(((u / kHtStages) - 1) & 1), spin_limit)) {
+        set_status(a.status, kStatusTimeout);
+        break;
       }
+      if (u + 2 < ntiles) fetch(u + 2);
+      asm volatile("cp.async.commit_group;\n" ::: "memory");  // (possibly empty) group of tile u + 2
+      asm volatile("cp.async.wait_group 2;\n" ::: "memory");  // tile u's indices have landed
       __syncwarp();
-      if (lane == 0 && publish) st_release(&a.chunk_status[chunk], kAggReady | kIncReady);
+      const int32_t* perm_s = ring + (u % kIdxRing) * 2 * TR;
+      const int32_t* seg_s = perm_s + TR;
+      unsigned char* sb = sm + st * L.stage_bytes;
+      const int64_t r0 = R0 + static_cast<int64_t>(u) * TR;
+      const int cnt = static_cast<int>(R1 - r0 < TR ? R1 - r0 : TR);
+      if (T.gather && lane == 0) expect_tx(&full[st], static_cast<uint32_t>((cnt + 3) / 4 * 4 * row_bytes));
+      __syncwarp();
+      for (int r = lane; r < cnt; r += 32)  // the run record of each row
+        cp_async(sb + L.info + r * 16, T.run_info + clamp_idx(seg_s[r], T.m) * 4, 16);
+      if (T.gather) {
+        // the rows, four per TMA gather (a short last group repeats its last row)
+        const CUtensorMap* tm = t ? &tm1 : &tm0;
+        for (int g4 = lane; g4 * 4 < cnt; g4 += 32) {
+          int rr[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int r = g4 * 4 + q < cnt ? g4 * 4 + q : cnt - 1;
+            rr[q] = static_cast<int>(clamp_idx(perm_s[r], T.m));
+          }
+          tma_gather4(sb + L.x + g4 * 4 * row_bytes, tm, rr[0], rr[1], rr[2], rr[3], &full[st]);
+        }
+      } else if (T.vec) {
+        // consecutive lanes copy consecutive 16-byte pieces of the stage
+        const int sp = row_bytes / 16;
+        for (int idx = lane; idx < cnt * sp; idx += 32) {
+          const int r = idx / sp, q16 = idx - r * sp;
+          cp_async(sb + L.x + idx * 16, xb + clamp_idx(perm_s[r], T.m) * ldb + q16 * 16, 16);
+        }
+      } else {
+        for (int idx = lane; idx < cnt * n; idx += 32) {
+          const int r = idx / n, c = idx - r * n;
+          cp_async(sb + L.x + idx * static_cast<int>(sizeof(Tin)),
+                   xb + clamp_idx(perm_s[r], T.m) * ldb + c * static_cast<int64_t>(sizeof(Tin)),
+                   static_cast<int>(sizeof(Tin)));
+        }
+      }
+      cp_async_arrive(&full[st]);
+      __syncwarp();  // the index ring slot of tile u is refilled at iteration u + 1
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
 
-    // ---- second pass: tail rows and head rows ----------------------------
-    Acc<Tc> run[kV];
-#pragma unroll
-    for (int v = 0; v < kV; ++v) {
-      run[v].zero();
-      if (!exf) run[v].set_double(carry[v]);
-      run[v].add(exv[v]);
+  // -------------------------------------------------------------- consumers
+  const int ct = threadIdx.x - 32;
+  Tc* w_s = reinterpret_cast<Tc*>(sm + L.w);
+  Tc* rj_s = reinterpret_cast<Tc*>(sm + L.rj);
+  Tc* hw_s = reinterpret_cast<Tc*>(sm + L.hw);
+  int32_t* hs_s = reinterpret_cast<int32_t*>(sm + L.hs);
+  Tc* agg_s = reinterpret_cast<Tc*>(sm + L.agg);
+  int32_t* flag_s = reinterpret_cast<int32_t*>(sm + L.flag);
+  Tc* state = reinterpret_cast<Tc*>(sm + L.state);  // [2][n][2]
+  const int c = ct % n, p = ct / n;
+  if (ct < n) {  // carried state entering the first tile
+    Acc<Tc> s0;
+    s0.zero();
+    if (inside) s0.set_double(T.carry[static_cast<int64_t>(k_lo) * n + ct]);
+    Tc hi, lo;
+    if constexpr (sizeof(Tc) == 4) {
+      hi = s0.hi;
+      lo = s0.lo;
+    } else {
+      hi = s0.v;
+      lo = 0.0;
     }
-    int32_t cur_seg = -2, mo = 0, slot = -1;
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int64_t i = rbase + r;
-      if (jl[r] < 0) continue;
-      if (segs[r] != cur_seg) {  // run-level data, once per run
-        cur_seg = segs[r];
-        mo = a.other[cur_seg];
-        slot = a.hdslot[cur_seg];
+    state[ct * 2] = hi;
+    state[ct * 2 + 1] = lo;
+  }
+  Tc* HD = static_cast<Tc*>(a.head);
+  Tc* TL = static_cast<Tc*>(T.tail);
+  __shared__ int s_failed;
+  if (ct == 0) s_failed = 0;
+  for (int u = 0; u < ntiles; ++u) {
+    const int st = u % kHtStages;
+    // one thread waits for the stage (suspended in hardware), the others at the named barrier
+    if (ct == 0 && !mbar_wait_sleep(&full[st], static_cast<uint32_t>((u / kHtStages) & 1), spin_limit)) {
+      set_status(a.status, kStatusTimeout);
+      s_failed = 1;
+    }
+    consumers_sync();
+    if (s_failed) break;
+    const unsigned char* sb = sm + st * L.stage_bytes;
+    const Tin* xs = reinterpret_cast<const Tin*>(sb + L.x);
+    const int64_t r0 = R0 + static_cast<int64_t>(u) * TR;
+    const int cnt = static_cast<int>(R1 - r0 < TR ? R1 - r0 : TR);
+
+    // per-row weights and head slots; rj = 0 marks the first row of a run
+    for (int r = ct; r < cnt; r += kHtConsumers) {
+      const int64_t i = r0 + r;
+      const int4 info = reinterpret_cast<const int4*>(sb + L.info)[r];
+      const int64_t ro = info.x, re = info.y;
+      const int32_t mo = info.z;
+      const int j = static_cast<int>(i - ro);
+      w_s[r] = (mo > 0 && j > 0) ? tail_weight(static_cast<Tc>(mo), j) : Tc(0);
+      rj_s[r] = j > 0 ? recip(static_cast<Tc>(j)) : Tc(0);
+      int32_t slot = -1;
+      Tc hw = Tc(0);
+      if (i + 1 == re) {
+        slot = info.w;
+        if (slot >= a.head_rows) slot = -1;
+        if (mo > 0) hw = head_weight(static_cast<Tc>(mo), j + 1);
       }
-      if (jl[r] == 0) {
+      hs_s[r] = slot;
+      hw_s[r] = hw;
+    }
+    consumers_sync();
+
+    if constexpr (V == 4) {
+      const int CG = n >> 2;  // column groups of 4, a power of two <= 32
+      const int PV = kHtConsumers / CG;
+      const int cg = ct & (CG - 1), pv = ct / CG;
+      const int lane = ct & 31, wc = ct >> 5;
+      int per = (cnt + PV - 1) / PV;
+      per |= 1;  // odd slice length: the slices of a quarter warp start in different banks
+      const int q0 = pv * per < cnt ? pv * per : cnt;
+      const int q1 = q0 + per < cnt ? q0 + per : cnt;
+      const Tin* xrow = xs + cg * 4;
+      // pass 1: the slice's sums since its last run start
+      Tc ai[4] = {Tc(0), Tc(0), Tc(0), Tc(0)};
+      int fi = 0;
+      for (int r = q0; r < q1; ++r) {
+        if (rj_s[r] == Tc(0)) {
 #pragma unroll
-        for (int v = 0; v < kV; ++v) run[v].zero();
-      }
-      if (ncols > 0) {
-        Tc out[kV];
-        if (mo > 0 && jl[r] > 0) {
-          const Tc w = tail_weight(static_cast<Tc>(mo), jl[r]);
-          const Tc rj = recip(static_cast<Tc>(jl[r]));
-#pragma unroll
-          for (int v = 0; v < kV; ++v) out[v] = w * (x[r][v] - run[v].value() * rj);
-        } else {
-#pragma unroll
-          for (int v = 0; v < kV; ++v) out[v] = Tc(0);
+          for (int k = 0; k < 4; ++k) ai[k] = Tc(0);
+          fi = 1;
         }
-        store4<Tc, kVec>(TL + i * a.n + col0, ncols, out);
+        Tc xv[4];
+        load4(xrow + r * n, xv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ai[k] += xv[k];
+      }
+      // inclusive segmented scan over the warp's slices of this column group
+      for (int d = CG; d < 32; d <<= 1) {
+        const int of = __shfl_up_sync(0xffffffffu, fi, d);
+        Tc oa[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) oa[k] = __shfl_up_sync(0xffffffffu, ai[k], d);
+        if (lane >= d) {
+          if (!fi) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ai[k] = oa[k] + ai[k];
+          }
+          fi |= of;
+        }
+      }
+      int ef = __shfl_up_sync(0xffffffffu, fi, CG);
+      Tc ea[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ea[k] = __shfl_up_sync(0xffffffffu, ai[k], CG);
+      if (lane < CG) {
+        ef = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ea[k] = Tc(0);
+      }
+      if (lane >= 32 - CG) {  // the warp's totals per column group
+#pragma unroll
+        for (int k = 0; k < 4; ++k) agg_s[(wc * CG + cg) * 4 + k] = ai[k];
+        flag_s[wc * CG + cg] = fi;
+      }
+      consumers_sync();
+      // carry from the earlier warps, then from the previous tile
+      int v0 = wc - 1;
+      while (v0 >= 0 && !flag_s[v0 * CG + cg]) --v0;
+      Tc hi[4], lo[4], loc[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        hi[k] = Tc(0);
+        lo[k] = Tc(0);
+        loc[k] = Tc(0);
+      }
+      if (!ef) {
+        for (int v = v0 < 0 ? 0 : v0; v < wc; ++v) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) loc[k] += agg_s[(v * CG + cg) * 4 + k];
+        }
+        if (v0 < 0) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            hi[k] = state[((u & 1) * n + cg * 4 + k) * 2];
+            lo[k] = state[((u & 1) * n + cg * 4 + k) * 2 + 1];
+          }
+        }
       }
 #pragma unroll
-      for (int v = 0; v < kV; ++v) run[v].add(x[r][v]);
-      if (segs[r + 1] != segs[r] && slot >= 0) {  // last row of its run: head row
-        Tc* hrow = HD + static_cast<int64_t>(slot) * a.ld_head;
-        const int mg = jl[r] + 1;
-        if (mo > 0) {
-          const Tc hw = head_weight(static_cast<Tc>(mo), mg);
+      for (int k = 0; k < 4; ++k) loc[k] += ea[k];
+      // pass 2: tail rows and head parts
+      for (int r = q0; r < q1; ++r) {
+        const Tc rj = rj_s[r];
+        if (rj == Tc(0)) {
 #pragma unroll
-          for (int v = 0; v < kV; ++v)
-            if (v < ncols) hrow[a.head_col0 + col0 + v] = hw * run[v].value();
-        } else {
+          for (int k = 0; k < 4; ++k) {
+            hi[k] = Tc(0);
+            lo[k] = Tc(0);
+            loc[k] = Tc(0);
+          }
+        }
+        Tc xv[4], out[4];
+        load4(xrow + r * n, xv);
+        const Tc w = w_s[r];
 #pragma unroll
-          for (int v = 0; v < kV; ++v)
-            if (v < ncols) hrow[a.head_col0 + col0 + v] = Tc(0);
-          if (cg == 0)
-            for (int c = 0; c < a.zero_n; ++c) hrow[a.zero_col0 + c] = Tc(0);
+        for (int k = 0; k < 4; ++k) {
+          const Tc S = hi[k] + (lo[k] + loc[k]);  // the run's sum of the rows before this one
+          out[k] = w * fma(-S, rj, xv[k]);
+          loc[k] += xv[k];
+        }
+        store4(TL + (r0 + r) * n + cg * 4, out);
+        const int32_t slot = hs_s[r];
+        if (slot >= 0) {
+          Tc* hrow = HD + static_cast<int64_t>(slot) * a.ld_head;
+          const Tc hw = hw_s[r];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int col = cg * 4 + k;
+            if (hw > Tc(0)) {
+              hrow[T.head_col0 + col] = hw * (hi[k] + (lo[k] + loc[k]));
+            } else {
+              hrow[T.head_col0 + col] = Tc(0);
+              for (int cc = col; cc < T.zero_n; cc += n) hrow[T.zero_col0 + cc] = Tc(0);
+            }
+          }
+        }
+      }
+      if (q1 == cnt && q0 < q1) {  // the slice holding the tile's last row carries the state on
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          run_add(hi[k], lo[k], loc[k]);
+          state[(((u + 1) & 1) * n + cg * 4 + k) * 2] = hi[k];
+          state[(((u + 1) & 1) * n + cg * 4 + k) * 2 + 1] = lo[k];
+        }
+      }
+    } else {
+      // pass 1: per (column, row slice), the sum since the slice's last run start
+      int per = (cnt + P - 1) / P;
+      per |= 1;  // odd slice length: slices of one warp start in different banks
+      const int q0 = p * per < cnt ? p * per : cnt;
+      const int q1 = q0 + per < cnt ? q0 + per : cnt;
+      if (p < P) {
+        Tc acc = Tc(0);
+        int f = 0;
+        for (int r = q0; r < q1; ++r) {
+          if (rj_s[r] == Tc(0)) {
+            acc = Tc(0);
+            f = 1;
+          }
+          acc += static_cast<Tc>(xs[r * n + c]);
+        }
+        agg_s[p * n + c] = acc;
+        if (c == 0) flag_s[p] = f;
+      }
+      consumers_sync();
+
+      // pass 2: carry into the slice, tail rows, head parts
+      if (p < P) {
+        int v0 = p - 1;
+        while (v0 >= 0 && !flag_s[v0]) --v0;
+        Tc hi = Tc(0), lo = Tc(0), loc = Tc(0);
+        if (v0 < 0) {
+          hi = state[((u & 1) * n + c) * 2];
+          lo = state[((u & 1) * n + c) * 2 + 1];
+        }
+        for (int v = v0 < 0 ? 0 : v0; v < p; ++v) loc += agg_s[v * n + c];
+        for (int r = q0; r < q1; ++r) {
+          const Tc rj = rj_s[r];
+          if (rj == Tc(0)) {
+            hi = Tc(0);
+            lo = Tc(0);
+            loc = Tc(0);
+          }
+          const Tc xv = static_cast<Tc>(xs[r * n + c]);
+          const Tc S = hi + (lo + loc);  // the run's sum of the rows before this one
+          TL[(r0 + r) * n + c] = w_s[r] * fma(-S, rj, xv);
+          loc += xv;
+          const int32_t slot = hs_s[r];
+          if (slot >= 0) {
+            Tc* hrow = HD + static_cast<int64_t>(slot) * a.ld_head;
+            const Tc hw = hw_s[r];
+            if (hw > Tc(0)) {
+              hrow[T.head_col0 + c] = hw * (hi + (lo + loc));
+            } else {
+              hrow[T.head_col0 + c] = Tc(0);
+              for (int cc = c; cc < T.zero_n; cc += n) hrow[T.zero_col0 + cc] = Tc(0);
+            }
+          }
+        }
+        if (q1 == cnt && q0 < q1) {  // the slice holding the tile's last row carries the state on
+          run_add(hi, lo, loc);
+          state[(((u + 1) & 1) * n + c) * 2] = hi;
+          state[(((u + 1) & 1) * n + c) * 2 + 1] = lo;
         }
       }
     }
+    consumers_sync();
+    if (ct == 0) mbar_arrive(&empty[st]);
   }
 }
 
-template <typename Tin, typename Tc, bool kVec>
-cudaError_t launch_one(const HtArgs& a, int grid, cudaStream_t s) {
-  head_tail_kernel<Tin, Tc, kVec><<<grid, kHtThreads, 0, s>>>(a);
+template <typename Tin, typename Tc>
+cudaError_t launch_typed_carry(const HtArgs& a, int total, int ncols, cudaStream_t s) {
+  ht_plan_kernel<Tin, Tc><<<(total + kPlanWarps - 1) / kPlanWarps, kHtBlock, 0, s>>>(a, total);
+  ht_scan_kernel<<<ncols, kHtBlock, 0, s>>>(a, a.t[0].chunks > 0 ? a.t[0].n : 0);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+// Tensor map for TMA row gathers of a table: box = one full row.  Returns
+// false (the caller then copies rows with cp.async) when TMA cannot address it.
+bool row_gather_map(CUtensorMap* map, const HtTable& T, int es_in) {
+  const int row_bytes = T.n * es_in;
+  if (!T.vec || T.m < 1 || T.n > 256 || row_bytes % 32 != 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(T.n), static_cast<cuuint64_t>(T.m)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(T.ld) * es_in};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(T.n), 1};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(map, es_in == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                         const_cast<void*>(T.x), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <typename Tin, typename Tc, int V>
+cudaError_t launch_typed_main(HtArgs a, int num_sms, int64_t spin_limit, cudaStream_t s) {
+  CUtensorMap maps[2];
+  std::memset(maps, 0, sizeof(maps));
+  for (int t = 0; t < 2; ++t)
+    a.t[t].gather = a.t[t].chunks > 0 && row_gather_map(&maps[t], a.t[t], static_cast<int>(sizeof(Tin)));
+  int smem = 0;
+  for (int t = 0; t < 2; ++t)
+    if (a.t[t].chunks > 0) {
+      const HtStream L = ht_stream_layout(a.t[t].n, sizeof(Tin), sizeof(Tc));
+      if (L.bytes > smem) smem = L.bytes;
+    }
+  static int granted[64] = {0};
+  static int per_sm[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  const bool cache = dev >= 0 && dev < 64;
+  if (smem > 48 * 1024 && (!cache || granted[dev] < smem)) {  // opt in to more than the default 48 KB
+    err = cudaFuncSetAttribute(ht_stream_kernel<Tin, Tc, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    if (cache) granted[dev] = smem;
+  }
+  int occ = cache ? per_sm[dev] : 0;
+  if (occ <= 0) {
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ht_stream_kernel<Tin, Tc, V>, kHtStreamThreads, smem);
+    if (err != cudaSuccess) return err;
+    if (occ < 1) occ = 1;
+    if (cache) per_sm[dev] = occ;
+  }
+  // CTAs per table in proportion to its chunks, at most one per chunk
+  const int c0 = a.t[0].chunks, c1 = a.t[1].chunks;
+  const int G = num_sms * occ;
+  int g0 = c0 > 0 ? static_cast<int>((static_cast<int64_t>(G) * c0 + (c0 + c1) - 1) / (c0 + c1)) : 0;
+  if (c0 > 0 && g0 < 1) g0 = 1;
+  if (g0 > c0) g0 = c0;
+  int g1 = c1 > 0 ? G - g0 : 0;
+  if (c1 > 0 && g1 < 1) g1 = 1;
+  if (g1 > c1) g1 = c1;
+  if (g0 + g1 == 0) return cudaSuccess;
+  ht_stream_kernel<Tin, Tc, V><<<g0 + g1, kHtStreamThreads, smem, s>>>(maps[0], maps[1], a, g0, g1, spin_limit);
   count_launches(1);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-// Lanes per row for a table of width n: ceil(n / 4) rounded up to a power of
-// two (at most 32 for n <= 128).
-int ht_column_groups(int n) {
-  const int g = (n + kV - 1) / kV;
-  int p = 1;
-  while (p < g) p <<= 1;
-  return p;
-}
-
-int ht_chunk_rows(int n) { return (32 / ht_column_groups(n)) * kHtRowsPerThread; }
-
-static bool ht_vector_ok(int n, int64_t ld, const void* x, int in_f64) {
+bool ht_vector_ok(int n, int64_t ld, const void* x, int in_f64) {
   const int e = in_f64 ? 8 : 4;
-  return (n % kV == 0) && ((ld * e) % 16 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0);
+  return ((n * e) % 16 == 0) && ((ld * e) % 16 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0);
 }
 
-cudaError_t launch_head_tail(const Plan& p, int table, cudaStream_t s) {
-  const TableWork& T = p.t[table];
-  if (T.m == 0 || T.chunks == 0) return cudaSuccess;
-  HtArgs a;
-  a.x = T.x;
-  a.ld = T.ld;
-  a.n = T.n;
-  a.m = T.m;
-  a.perm = T.perm;
-  a.seg = T.seg;
-  a.run_off = T.run_off;
-  a.other = T.other;
-  a.hdslot = T.hdslot;
-  a.tail = T.tail;
+HtArgs make_args(const Plan& p) {
+  HtArgs a{};
+  for (int t = 0; t < 2; ++t) {
+    const TableWork& W = p.t[t];
+    HtTable& T = a.t[t];
+    T.x = W.x;
+    T.ld = W.ld;
+    T.n = W.n;
+    T.m = W.m;
+    T.vec = W.m > 0 && ht_vector_ok(W.n, W.ld, W.x, W.in_f64);
+    T.perm = W.perm;
+    T.seg = W.seg;
+    T.run_off = W.run_off;
+    T.other = W.other;
+    T.hdslot = W.hdslot;
+    T.run_info = W.run_info;
+    T.tail = W.tail;
+    T.head_col0 = t == 0 ? 0 : p.n1;
+    T.zero_col0 = t == 0 ? p.n1 : 0;
+    T.zero_n = t == 0 ? p.n2 : 0;
+    T.L = W.chunk_rows;
+    T.chunks = W.m > 0 ? W.chunks : 0;
+    T.cbeg = W.cbeg;
+    T.cflag = W.cflag;
+    T.piece = W.piece;
+    T.carry = W.carry;
+  }
+  a.c0 = a.t[0].chunks;
   a.head = p.head;
   a.ld_head = p.n;
-  a.head_col0 = table == 0 ? 0 : p.n1;
-  a.zero_col0 = table == 0 ? p.n1 : 0;
-  a.zero_n = table == 0 ? p.n2 : 0;
-  a.chunk_status = T.chunk_status;
-  a.chunk_agg = T.chunk_agg;
-  a.chunk_inc = T.chunk_inc;
-  a.cg = ht_column_groups(T.n);
-  a.chunk_rows = ht_chunk_rows(T.n);
-  a.chunks = T.chunks;
-  a.ticket = &p.hdr->ticket[table];
+  a.head_rows = p.t[0].m;
   a.status = &p.hdr->status;
-  a.spin_limit = p.spin_limit;
-  a.withhold = p.withhold;
-  const bool vec = ht_vector_ok(T.n, T.ld, T.x, T.in_f64);
-  const int warps_per_block = kHtThreads / 32;
-  int grid = p.num_sms * 8;
-  const int need = (a.chunks + warps_per_block - 1) / warps_per_block;
-  if (grid > need) grid = need;
-  if (T.in_f64) {
-    if (p.mixed) return vec ? launch_one<double, float, true>(a, grid, s) : launch_one<double, float, false>(a, grid, s);
-    return vec ? launch_one<double, double, true>(a, grid, s) : launch_one<double, double, false>(a, grid, s);
+  return a;
+}
+
+}  // namespace
+
+// Chunk spacing L for a table of width n: the largest power of two in
+// [16, 512] with (2 L - 1) rows of input (and output, when its type differs)
+// within 32 KB of shared memory.
+int ht_chunk_rows(int n, int in_f64, int mixed) {
+  const int es_in = in_f64 ? 8 : 4, es_c = mixed ? 4 : 8;
+  const int row = n * (es_in + (es_in != es_c ? es_c : 0));
+  int L = 512;
+  while (L > 16 && (2 * L - 1) * row > 32 * 1024) L >>= 1;
+  return L;
+}
+
+cudaError_t launch_ht_carry(const Plan& p, cudaStream_t s) {
+  const HtArgs a = make_args(p);
+  const int grid = a.t[0].chunks + a.t[1].chunks;
+  if (grid == 0) return cudaSuccess;
+  const int ncols = (a.t[0].chunks > 0 ? a.t[0].n : 0) + (a.t[1].chunks > 0 ? a.t[1].n : 0);
+  const bool in64 = p.t[0].in_f64 != 0;
+  if (in64) return p.mixed ? launch_typed_carry<double, float>(a, grid, ncols, s)
+                           : launch_typed_carry<double, double>(a, grid, ncols, s);
+  return p.mixed ? launch_typed_carry<float, float>(a, grid, ncols, s)
+                 : launch_typed_carry<float, double>(a, grid, ncols, s);
+}
+
+cudaError_t launch_ht_main(const Plan& p, cudaStream_t s) {
+  const HtArgs a = make_args(p);
+  const int grid = a.t[0].chunks + a.t[1].chunks;
+  if (grid == 0) return cudaSuccess;
+  const bool in64 = p.t[0].in_f64 != 0;
+  const int sms = p.num_sms;
+  const int64_t sl = p.spin_limit;
+  // the 4-column path needs both tables' widths to be 4 x a power of two <= 128
+  // and 16-byte aligned tail rows
+  bool v4 = true;
+  for (int t = 0; t < 2; ++t) {
+    if (a.t[t].chunks == 0) continue;
+    const int n = a.t[t].n, cg = n / 4;
+    v4 = v4 && n % 4 == 0 && cg >= 1 && cg <= 32 && (cg & (cg - 1)) == 0 &&
+         (reinterpret_cast<uintptr_t>(a.t[t].tail) & 15u) == 0;
   }
-  if (p.mixed) return vec ? launch_one<float, float, true>(a, grid, s) : launch_one<float, float, false>(a, grid, s);
-  return vec ? launch_one<float, double, true>(a, grid, s) : launch_one<float, double, false>(a, grid, s);
+  if (in64) {
+    if (p.mixed) return v4 ? launch_typed_main<double, float, 4>(a, sms, sl, s) : launch_typed_main<double, float, 1>(a, sms, sl, s);
+    return v4 ? launch_typed_main<double, double, 4>(a, sms, sl, s) : launch_typed_main<double, double, 1>(a, sms, sl, s);
+  }
+  if (p.mixed) return v4 ? launch_typed_main<float, float, 4>(a, sms, sl, s) : launch_typed_main<float, float, 1>(a, sms, sl, s);
+  return v4 ? launch_typed_main<float, double, 4>(a, sms, sl, s) : launch_typed_main<float, double, 1>(a, sms, sl, s);
 }
 
 }  // namespace figaro

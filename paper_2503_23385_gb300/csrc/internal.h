@@ -4,7 +4,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 namespace figaro {
 
@@ -15,8 +17,6 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // keys per radix tile
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;
-constexpr int kHtThreads = 256;         // head/tail block size
-constexpr int kHtRowsPerThread = 8;
 constexpr int kGramThreads = 256;
 constexpr int kGramTileRows = 64;
 
@@ -57,13 +57,15 @@ struct TableWork {
   int32_t* run_off = nullptr;   // m + 1
   int32_t* other = nullptr;     // partner run size (0 = unmatched)
   int32_t* hdslot = nullptr;    // head row of the run's key group
+  int32_t* run_info = nullptr;  // per run: {first row, end row, partner run size, head slot}
   // head/tail
   void* tail = nullptr;         // m x n slots, compute type
-  uint32_t* chunk_status = nullptr;
-  double* chunk_agg = nullptr;
-  double* chunk_inc = nullptr;
-  int chunks = 0;
-  int chunk_rows = 0;
+  int chunk_rows = 0;           // chunk spacing L of the head/tail step
+  int chunks = 0;               // ceil(m / L)
+  int32_t* cbeg = nullptr;      // chunks + 1 first rows
+  uint32_t* cflag = nullptr;    // chunks flags
+  double* piece = nullptr;      // chunks x n long-run piece sums
+  double* carry = nullptr;      // chunks x n carries
 };
 
 // Everything one instance needs, resolved from the workspace.
@@ -94,6 +96,9 @@ struct Plan {
   int num_sms = 148;
 };
 
+// cuTensorMapEncodeTiled from the driver (null when unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
 // Look-back words the grouping step needs per table (sort passes + runs).
 int64_t group_status_words(int tiles);
 
@@ -108,7 +113,8 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
 // Launchers (each returns the first CUDA error it meets).
 cudaError_t launch_reset(const Plan& p, cudaStream_t s);
 cudaError_t launch_grouping(const Plan& p, cudaStream_t s);
-cudaError_t launch_head_tail(const Plan& p, int table, cudaStream_t s);
+cudaError_t launch_ht_carry(const Plan& p, cudaStream_t s);
+cudaError_t launch_ht_main(const Plan& p, cudaStream_t s);
 cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s);
 cudaError_t launch_chol_first(const Plan& p, cudaStream_t s);
 cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);

@@ -304,3 +304,14 @@ def test_batch_matches_single_calls(fg, torch):
     for (a, b), (R, s) in zip(pairs, outs):
         Rref, sref = oracle.join_r_sigma(a.x, a.key, b.x, b.key)
         assert rel(R.cpu().numpy(), Rref) <= 1e-6 and rel(s.cpu().numpy(), sref) <= 1e-6
+
+
+def test_withheld_lookback_word_times_out_and_context_survives(fg, torch):
+    """Fault injection on the host's request: the first tile of table A never
+    publishes its run count, so the next tile's bounded wait gives up; the call
+    reports FIGARO_ERR_DEVICE_TIMEOUT and the next normal call is correct."""
+    A, B = make_pair(10000, 4, 3000, 4, 50, np.float32, "normal", seed=91)
+    with pytest.raises(fg.FigaroError) as e:
+        fg.join_qr_svd(dev(torch, A), dev(torch, B), flags=fg.FLAG_TEST_WITHHOLD, spin_limit=2000)
+    assert e.value.status == 6
+    check_against_oracle(fg, torch, A, B, paths=("mixed",))
