@@ -303,8 +303,8 @@ int gram_tile_rows(int k, int kout, int with_w, int elem) {
 
 bool gram_tc_supported(int k, int kout);
 cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,
-                                 int kout, double* part, int grid, int32_t* status, int64_t spin_limit,
-                                 cudaStream_t s);
+                                 int kout, double* part, int grid_max, int num_sms, int* grid_used, int32_t* status,
+                                 int64_t spin_limit, cudaStream_t s);
 
 cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   const int elem = p.mixed ? 4 : 8;
@@ -340,13 +340,13 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     gram_geometry(a.kout, &a.kpad, &a.ntiles, &a.slices, &tpt);
     a.tile_rows = gram_tile_rows(a.k, a.kout, a.W != nullptr, elem);
     a.part = p.gpart[b];
-    const int grid = p.ggrid[b];
+    int grid = p.ggrid[b];
     const bool tc = p.mixed && p.gram_engine != 1 && gram_tc_supported(a.k, a.kout);
     cudaError_t err;
     if (tc) {
       const float* Wb = pass == 2 ? p.Wf + static_cast<int64_t>(a.w0) * p.n + a.w0 : nullptr;
-      err = launch_gram_tc_block(a.X, a.k, rows, a.rows_dev, Wb, p.n, a.kout, a.part, grid, &p.hdr->status,
-                                 p.spin_limit, s);
+      err = launch_gram_tc_block(a.X, a.k, rows, a.rows_dev, Wb, p.n, a.kout, a.part, p.ggrid[b], p.num_sms, &grid,
+                                 &p.hdr->status, p.spin_limit, s);
     } else {
       err = p.mixed ? launch_gram_block<float>(a, tpt, grid, s) : launch_gram_block<double>(a, tpt, grid, s);
     }

@@ -444,6 +444,397 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined engine for k <= 32 and kout <= 32 (one 32-column panel per row).
+//
+// Warp roles (10 warps):
+//   warp 0     TMA producer: X tiles into a ring of kPipeStages stages.
+//   warp 1     allocates tensor memory; one thread issues every MMA.
+//   warps 2-9  workers: split each landed tile (hi in place, lo in the
+//              stage's second buffer); pass 2: read the formation result
+//              D1 = X W back from tensor memory (warp w reads TMEM lanes
+//              32 (w mod 4) .. + 31, half of the columns each), split Q and
+//              write it as the Gram operands; drain the Gram accumulators.
+// Double buffers in tensor memory (D1 and the Gram accumulator sets) let
+// the MMAs of tile i overlap the workers' draining of tile i - 1.  The
+// workers sum the four accumulators of a tile in FP32 (round to nearest),
+// add up to kDrainGroup tiles in FP32 and fold that into float-float sums.
+// Every wait is bounded; a timeout sets the status bit and an abort flag
+// that makes every role leave its loop.
+constexpr int kPipeStages = 4;
+constexpr int kWorkWarps = 8;
+constexpr int kPipeThreads = 64 + 32 * kWorkWarps;
+constexpr int kDrainGroup = 8;
+
+struct PipeArgs {
+  int k, kout, np, ksteps_f;
+  int64_t rows;
+  const int64_t* rows_dev;
+  const float* W;  // pass 2: W block base (row-major, leading dimension wld); nullptr for pass 1
+  int wld;
+  double* part;    // [grid][kout][kout]
+  int32_t* status;
+  int64_t spin_limit;
+};
+
+struct PipeSmem {
+  uint64_t tma_full[kPipeStages], stage_empty[kPipeStages], op_full[kPipeStages];
+  uint64_t d1_full[2], d1_empty[2], q_full[2], q_empty[2], acc_full[2], acc_empty[2], done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+// byte offsets from the 1024-aligned dynamic base
+constexpr int kOffRaw = 0;                                   // kPipeStages x 16 KB
+constexpr int kOffLo = kOffRaw + kPipeStages * kPanelBytes;  // kPipeStages x 16 KB
+constexpr int kOffQh = kOffLo + kPipeStages * kPanelBytes;   // 2 x 16 KB
+constexpr int kOffQl = kOffQh + 2 * kPanelBytes;             // 2 x 16 KB
+constexpr int kOffWh = kOffQl + 2 * kPanelBytes;             // 32 rows x 128 B
+constexpr int kOffWl = kOffWh + 32 * 128;
+constexpr int kPipeSmemBytes = kOffWl + 32 * 128 + 1024;
+
+__device__ __forceinline__ bool pipe_wait(PipeSmem& S, uint64_t* b, uint32_t parity, int64_t limit, int32_t* status) {
+  for (int64_t i = 0; i < limit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 63) == 63 && *reinterpret_cast<volatile int*>(&S.abort)) return false;
+  }
+  set_status(status, kStatusTimeout);
+  *reinterpret_cast<volatile int*>(&S.abort) = 1;
+  return false;
+}
+
+// Bounded wait that ignores the abort flag: used before the CTA exits, for
+// copies and MMAs already issued.
+__device__ __forceinline__ void drain_wait(uint64_t* b, uint32_t parity, int64_t limit, int32_t* status) {
+  for (int64_t i = 0; i < limit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (ok) return;
+  }
+  set_status(status, kStatusTimeout);
+}
+
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// 16 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 16; ++c) out[c] = __uint_as_float(r[c]);
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    gram_pipe_kernel(const __grid_constant__ CUtensorMap tmx, PipeArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ PipeSmem S;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool pass2 = a.W != nullptr;
+  const int64_t rows = a.rows_dev ? *a.rows_dev : a.rows;
+  const int64_t ntiles_all = (rows + kTileRows - 1) / kTileRows;
+  const int G = gridDim.x;
+  const int n = ntiles_all > blockIdx.x ? static_cast<int>((ntiles_all - 1 - blockIdx.x) / G + 1) : 0;
+  auto tile_row0 = [&](int i) -> int64_t { return (static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(i) * G) * kTileRows; };
+
+  if (tid == 0) {
+    for (int q = 0; q < kPipeStages; ++q) {
+      mbar_init(&S.tma_full[q], 1);
+      mbar_init(&S.stage_empty[q], 1);
+      mbar_init(&S.op_full[q], kWorkWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.d1_full[b], 1);
+      mbar_init(&S.d1_empty[b], kWorkWarps);
+      mbar_init(&S.q_full[b], kWorkWarps);
+      mbar_init(&S.q_empty[b], 1);
+      mbar_init(&S.acc_full[b], 1);
+      mbar_init(&S.acc_empty[b], kWorkWarps);
+    }
+    mbar_init(&S.done, 1);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (pass2 && warp >= 2) {  // W^T (np rows x k, K-major 128-byte swizzle): hi and lo parts, zero padded
+    const int wt = tid - 64;
+    float* wh = reinterpret_cast<float*>(base + kOffWh);
+    float* wl = reinterpret_cast<float*>(base + kOffWl);
+    for (int e = wt; e < 32 * 32; e += 32 * kWorkWarps) {
+      wh[e] = 0.f;
+      wl[e] = 0.f;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
+    for (int e = wt; e < a.kout * a.k; e += 32 * kWorkWarps) {
+      const int nn = e / a.k, kk = e - nn * a.k;
+      const float v = (kk <= nn) ? a.W[static_cast<int64_t>(kk) * a.wld + nn] : 0.f;  // W upper triangular
+      const int off = sw128_offset(nn, kk, 32 * 128);
+      const float h = tf32_hi(v);
+      *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wh) + off) = h;
+      *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wl) + off) = tf32_rn(v - h);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem_base;
+  auto d1_addr = [&](int b) { return tmem + static_cast<uint32_t>(b * 32); };
+  auto acc_addr = [&](int b, int q) { return tmem + 64u + static_cast<uint32_t>(b * 128 + q * 32); };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < n; ++i) {
+        const int s = i % kPipeStages;
+        if (i >= kPipeStages &&
+            !pipe_wait(S, &S.stage_empty[s], static_cast<uint32_t>(((i / kPipeStages) - 1) & 1), a.spin_limit, a.status))
+          break;
+        expect_tx(&S.tma_full[s], kPanelBytes);
+        tma_load_2d(base + kOffRaw + s * kPanelBytes, &tmx, 0, static_cast<int>(tile_row0(i)), &S.tma_full[s]);
+        issued = i + 1;
+      }
+      // every load issued has landed before the CTA may exit (bounded)
+      for (int i = issued > kPipeStages ? issued - kPipeStages : 0; i < issued; ++i)
+        drain_wait(&S.tma_full[i % kPipeStages], static_cast<uint32_t>((i / kPipeStages) & 1), a.spin_limit, a.status);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t idg = idesc_tf32(64, a.np, 1);
+      const uint32_t idf = idesc_tf32(128, a.np);
+      const uint32_t wh = smem_u32(base + kOffWh), wl = smem_u32(base + kOffWl);
+      // descriptors are linear in the start address (bits 0-13 hold addr >> 4),
+      // so a K step of 8 rows (1,024 bytes) adds 64
+      auto gram = [&](uint32_t ah, uint32_t al, int b) {
+        constexpr int kSteps = kTileRows / 8, kPer = kSteps / kHiAcc;
+        const uint64_t dh = desc_mn_sw128_32b(ah, 0), dl = desc_mn_sw128_32b(al, 0);
+        // round robin over the independent accumulators (consecutive MMAs do
+        // not depend on each other); per accumulator the small terms come first
+#pragma unroll
+        for (int st = 0; st < kPer; ++st)
+#pragma unroll
+          for (int q = 0; q < kHiAcc; ++q) {
+            const uint64_t o = static_cast<uint64_t>((q * kPer + st) * 64);
+            mma_tf32(acc_addr(b, q), dh + o, dl + o, idg, st > 0 ? 1u : 0u);
+          }
+#pragma unroll
+        for (int st = 0; st < kPer; ++st)
+#pragma unroll
+          for (int q = 0; q < kHiAcc; ++q) {
+            const uint64_t o = static_cast<uint64_t>((q * kPer + st) * 64);
+            mma_tf32(acc_addr(b, q), dh + o, dh + o, idg, 1u);
+          }
+      };
+      auto formation = [&](int j) -> bool {  // D1[j & 1] = X_j W (3 x TF32, the large term last)
+        const int s = j % kPipeStages, bd = j & 1;
+        if (!pipe_wait(S, &S.op_full[s], static_cast<uint32_t>((j / kPipeStages) & 1), a.spin_limit, a.status))
+          return false;
+        if (j >= 2 && !pipe_wait(S, &S.d1_empty[bd], static_cast<uint32_t>(((j / 2) - 1) & 1), a.spin_limit, a.status))
+          return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(base + kOffRaw + s * kPanelBytes), al = smem_u32(base + kOffLo + s * kPanelBytes);
+        for (int ks = 0; ks < a.ksteps_f; ++ks) {
+          const uint32_t o = static_cast<uint32_t>(ks * 32);
+          mma_tf32(d1_addr(bd), desc_kmajor_sw128(al + o), desc_kmajor_sw128(wh + o), idf, ks > 0 ? 1u : 0u);
+          mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wl + o), idf, 1u);
+        }
+        for (int ks = 0; ks < a.ksteps_f; ++ks) {
+          const uint32_t o = static_cast<uint32_t>(ks * 32);
+          mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wh + o), idf, 1u);
+        }
+        mma_commit(&S.stage_empty[s]);
+        mma_commit(&S.d1_full[bd]);
+        return true;
+      };
+      if (!pass2) {
+        for (int i = 0; i < n; ++i) {
+          const int s = i % kPipeStages, b = i & 1;
+          if (!pipe_wait(S, &S.op_full[s], static_cast<uint32_t>((i / kPipeStages) & 1), a.spin_limit, a.status)) break;
+          if (i >= 2 && !pipe_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
+            break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          gram(smem_u32(base + kOffRaw + s * kPanelBytes), smem_u32(base + kOffLo + s * kPanelBytes), b);
+          mma_commit(&S.stage_empty[s]);
+          mma_commit(&S.acc_full[b]);
+        }
+      } else if (n > 0 && formation(0)) {
+        for (int i = 0; i < n; ++i) {
+          const int b = i & 1;
+          if (i + 1 < n && !formation(i + 1)) break;
+          if (!pipe_wait(S, &S.q_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) break;
+          if (i >= 2 && !pipe_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
+            break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          gram(smem_u32(base + kOffQh + b * kPanelBytes), smem_u32(base + kOffQl + b * kPanelBytes), b);
+          mma_commit(&S.q_empty[b]);
+          mma_commit(&S.acc_full[b]);
+        }
+      }
+      // all MMAs issued by this thread have completed before tensor memory is freed (bounded)
+      mma_commit(&S.done);
+      drain_wait(&S.done, 0u, a.spin_limit, a.status);
+    }
+  } else {
+    // ------------------------------------------------------------ workers
+    const int wt = tid - 64;
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const int c0 = half * 16;  // this warp's 16 columns of D1 and of the accumulators
+    const float lo_scale = pass2 ? 1.f : 2.f;
+    auto split = [&](int i) -> bool {
+      const int s = i % kPipeStages;
+      if (!pipe_wait(S, &S.tma_full[s], static_cast<uint32_t>((i / kPipeStages) & 1), a.spin_limit, a.status))
+        return false;
+      float4* X4 = reinterpret_cast<float4*>(base + kOffRaw + s * kPanelBytes);
+      float4* L4 = reinterpret_cast<float4*>(base + kOffLo + s * kPanelBytes);
+      const int64_t r0 = tile_row0(i);
+      for (int e = wt; e < kPanelBytes / 16; e += 32 * kWorkWarps) {
+        const int row = e >> 3;  // 8 float4 per 128-byte row
+        float4 v = X4[e];
+        if (r0 + row >= rows) v = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 h, l;
+        h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
+        l.x = tf32_rn(v.x - h.x) * lo_scale; l.y = tf32_rn(v.y - h.y) * lo_scale;
+        l.z = tf32_rn(v.z - h.z) * lo_scale; l.w = tf32_rn(v.w - h.w) * lo_scale;
+        X4[e] = h;
+        L4[e] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&S.op_full[s]);
+      return true;
+    };
+    auto make_q = [&](int i) -> bool {
+      const int b = i & 1;
+      if (!pipe_wait(S, &S.d1_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) return false;
+      if (i >= 2 && !pipe_wait(S, &S.q_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
+        return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = quarter * 32 + lane;  // TMEM lane = row of the tile
+      float q[16];
+      tmem_ld16(d1_addr(b) + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(c0), q);
+      const bool live = tile_row0(i) + row < rows;
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (!live || c0 + c >= a.kout) q[c] = 0.f;  // padding rows and columns of Q are zero
+      unsigned char* qh = base + kOffQh + b * kPanelBytes;
+      unsigned char* ql = base + kOffQl + b * kPanelBytes;
+#pragma unroll
+      for (int ch = 0; ch < 2; ++ch) {
+        const int off = sw32b_chunk_offset(row, (c0 >> 3) + ch);
+        const float* v = q + ch * 8;
+        float4 h0 = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
+        float4 h1 = make_float4(tf32_hi(v[4]), tf32_hi(v[5]), tf32_hi(v[6]), tf32_hi(v[7]));
+        float4 l0 = make_float4(2.f * tf32_rn(v[0] - h0.x), 2.f * tf32_rn(v[1] - h0.y), 2.f * tf32_rn(v[2] - h0.z),
+                                2.f * tf32_rn(v[3] - h0.w));
+        float4 l1 = make_float4(2.f * tf32_rn(v[4] - h1.x), 2.f * tf32_rn(v[5] - h1.y), 2.f * tf32_rn(v[6] - h1.z),
+                                2.f * tf32_rn(v[7] - h1.w));
+        reinterpret_cast<float4*>(qh + off)[0] = h0;
+        reinterpret_cast<float4*>(qh + off)[1] = h1;
+        reinterpret_cast<float4*>(ql + off)[0] = l0;
+        reinterpret_cast<float4*>(ql + off)[1] = l1;
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive_cta(&S.d1_empty[b]);
+        mbar_arrive_cta(&S.q_full[b]);
+      }
+      return true;
+    };
+    // Gram row of this thread's TMEM lane (M = 64: 16 rows per 32-lane quarter)
+    const int grow = lane < 16 ? quarter * 16 + lane : -1;
+    const bool has_cols = c0 < a.np;
+    float grp[16], fh[16], fl[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      grp[j] = 0.f;
+      fh[j] = 0.f;
+      fl[j] = 0.f;
+    }
+    auto fold = [&]() {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        float s_, e_;
+        two_sum(fh[j], grp[j], s_, e_);
+        fh[j] = s_;
+        fl[j] = __fadd_rn(fl[j], e_);
+        grp[j] = 0.f;
+      }
+    };
+    int grouped = 0;
+    auto drain = [&](int i) -> bool {
+      const int b = i & 1;
+      if (!pipe_wait(S, &S.acc_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (has_cols) {
+        float sum[16], v[16];
+        const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
+        tmem_ld16(acc_addr(b, 0) + lanes + static_cast<uint32_t>(c0), sum);
+#pragma unroll 1
+        for (int q = 1; q < kHiAcc; ++q) {
+          tmem_ld16(acc_addr(b, q) + lanes + static_cast<uint32_t>(c0), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sum[j] = __fadd_rn(sum[j], v[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) grp[j] = __fadd_rn(grp[j], sum[j]);
+        if (++grouped == kDrainGroup) {
+          fold();
+          grouped = 0;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&S.acc_empty[b]);
+      return true;
+    };
+    bool ok = n == 0 || split(0);
+    for (int i = 0; ok && i < n; ++i) {
+      if (i + 1 < n && !split(i + 1)) break;
+      if (pass2 && !make_q(i)) break;
+      if (i >= 1 && !drain(i - 1)) break;
+      if (i == n - 1) ok = drain(i);
+    }
+    fold();
+    double* part = a.part + static_cast<int64_t>(blockIdx.x) * a.kout * a.kout;
+    if (grow >= 0 && grow < a.kout && has_cols) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j < a.kout) part[grow * a.kout + c0 + j] = static_cast<double>(fh[j]) + static_cast<double>(fl[j]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() { return tensor_map_encoder(); }
 
 struct Geometry {
@@ -487,8 +878,51 @@ Geometry geometry(int k, int kout, bool pass2) {
 bool gram_tc_supported(int k, int kout) { return k % 4 == 0 && k <= 64 && kout <= 64 && encoder() != nullptr; }
 
 cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,
-                                 int kout, double* part, int grid, int32_t* status, int64_t spin_limit,
-                                 cudaStream_t s) {
+                                 int kout, double* part, int grid_max, int num_sms, int* grid_used, int32_t* status,
+                                 int64_t spin_limit, cudaStream_t s) {
+  if (k <= 32 && kout <= 32) {  // pipelined engine: persistent CTAs, one per SM
+    int grid = static_cast<int>((rows + kTileRows - 1) / kTileRows);
+    if (grid > num_sms) grid = num_sms;
+    if (grid > grid_max) grid = grid_max;
+    if (grid < 1) grid = 1;
+    *grid_used = grid;
+    PipeArgs a{};
+    a.k = k;
+    a.kout = kout;
+    a.np = (kout + 15) / 16 * 16;
+    a.ksteps_f = (k + 7) / 8;
+    a.rows = rows;
+    a.rows_dev = rows_dev;
+    a.W = W;
+    a.wld = wld;
+    a.part = part;
+    a.status = status;
+    a.spin_limit = spin_limit;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows > 0 ? rows : 1)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(k) * 4};
+    cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kTileRows)};
+    cuuint32_t es[2] = {1, 1};
+    const CUtensorMapSwizzle sw = W ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B;
+    CUresult cr = encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    static int granted[64] = {0};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= 64 || !granted[dev]) {
+      err = cudaFuncSetAttribute(gram_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemBytes);
+      if (err != cudaSuccess) return err;
+      if (dev >= 0 && dev < 64) granted[dev] = 1;
+    }
+    gram_pipe_kernel<<<grid, kPipeThreads, kPipeSmemBytes, s>>>(map, a);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  const int grid = grid_max;
+  *grid_used = grid;
   Geometry g = geometry(k, kout, W != nullptr);
   TcArgs a = g.a;
   a.rows = rows;
