@@ -64,6 +64,39 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(total_ms, world, device):
+    """The slowest rank's time (every rank runs its own instance; the job
+    ends when the slowest one does)."""
+    if world <= 1:
+        return float(total_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(rows_per_rank, world, ms_per_step):
+    """Input rows of all ranks per second (weak scaling: each rank has its own rows)."""
+    return world * rows_per_rank / (ms_per_step / 1e3)
+
+
+def measured_traffic(kernel, cfg):
+    """DRAM bytes (read + write) per launch from the committed ncu capture, or
+    None when the capture is for another workload or the kernel's source has
+    changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        src = os.path.join(ROOT, "paper_2503_23385_gb300", "csrc", "headtail.cu")
+        with open(src, "rb") as f:
+            same = hashlib.sha256(f.read()).hexdigest() == rec["source_sha256"]
+        return float(rec["traffic_bytes"]) if same and rec["workload"] == cfg else None
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------ clocks ------
 
 class ClockSampler:
@@ -253,13 +286,9 @@ def main():
     if status != 0:
         raise fg.FigaroError(status, "timed steps")
 
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * rows / (ms_per_step / 1e3)
+    value = job_throughput(rows, world, ms_per_step)
     phases = {name: statistics.mean(v) for name, v in zip(fg.PHASES, phase_ms)}
 
     # ---- roofline of the head/tail kernel (one launch covers both tables) --
@@ -270,8 +299,8 @@ def main():
     ht_bytes = sum(T.m * (4 + 4 + T.n * ein + T.n * s) for T in (A, B))
     ht_ms = phases["head_tail"]
     achieved = ht_bytes / (ht_ms / 1e3) / 1e9
-    roofline = {"kernel": "ht_main_kernel (both tables)", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+    roofline = {"kernel": "ht_stream_kernel (both tables)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": measured_traffic("ht_stream_kernel", args.config),
                 "bytes_per_launch": ht_bytes, "peak_source": peak_kind}
 
     # ---- end to end through the C ABI with host buffers -----------------
