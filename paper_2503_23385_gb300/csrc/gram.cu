@@ -302,6 +302,7 @@ int gram_tile_rows(int k, int kout, int with_w, int elem) {
 }
 
 bool gram_tc_supported(int k, int kout);
+bool gram_tc_packs(int k, int kout, bool pass2);
 cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,
                                  int kout, double* part, int grid_max, int num_sms, int* grid_used, int32_t* status,
                                  int64_t spin_limit, cudaStream_t s);
@@ -355,7 +356,7 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     r.count[b] = grid;
     r.kout[b] = a.kout;
     r.off[b] = b == 2 ? p.n1 : 0;
-    r.sym[b] = tc ? 1 : 0;
+    r.sym[b] = (tc && !gram_tc_packs(a.k, a.kout, pass == 2)) ? 1 : 0;
   }
   const int ne = p.n * p.n;
   gram_reduce_kernel<<<(ne + 31) / 32, 32 * kReduceWarps, 0, s>>>(r);

@@ -493,16 +493,19 @@ constexpr int kOffWh = kOffQl + 2 * kPanelBytes;             // 32 rows x 128 B
 constexpr int kOffWl = kOffWh + 32 * 128;
 constexpr int kPipeSmemBytes = kOffWl + 32 * 128 + 1024;
 
+// The waiting thread is suspended in hardware between tries (hint 1 us), so
+// waiting warps do not take issue slots from the working ones.
 __device__ __forceinline__ bool pipe_wait(PipeSmem& S, uint64_t* b, uint32_t parity, int64_t limit, int32_t* status) {
-  for (int64_t i = 0; i < limit; ++i) {
+  const int64_t tries = limit / 16 + 1;
+  for (int64_t i = 0; i < tries; ++i) {
     uint32_t ok;
     asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
         : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
+        : "r"(smem_u32(b)), "r"(parity), "r"(1000u)
         : "memory");
     if (ok) return true;
-    if ((i & 63) == 63 && *reinterpret_cast<volatile int*>(&S.abort)) return false;
+    if (*reinterpret_cast<volatile int*>(&S.abort)) return false;
   }
   set_status(status, kStatusTimeout);
   *reinterpret_cast<volatile int*>(&S.abort) = 1;
@@ -522,6 +525,16 @@ __device__ __forceinline__ void drain_wait(uint64_t* b, uint32_t parity, int64_t
     if (ok) return;
   }
   set_status(status, kStatusTimeout);
+}
+
+// A warp waits through its lane 0 (the other lanes do not poll); __syncwarp
+// then orders what lane 0 observed before the rest of the warp reads it.
+__device__ __forceinline__ bool warp_wait(PipeSmem& S, uint64_t* b, uint32_t parity, int64_t limit, int32_t* status) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = pipe_wait(S, b, parity, limit, status) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
 }
 
 __device__ __forceinline__ void mbar_arrive_cta(uint64_t* b) {
@@ -835,6 +848,420 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Packed-operand engine: one M = N = 128 MMA per K step.
+//
+// tcgen05.mma costs about the same issue time for every shape up to
+// M = 128 x N = 64, so the Gram is laid out to make each MMA as large as the
+// tensor core allows.  For a block of width kk in {4, 8, 16, 32}, R = 64 / kk
+// consecutive rows are packed side by side into one 64-column "wide row",
+// and the split parts form Z = [hi | lo] (128 columns, MN-major, 32-byte-atom
+// 128-byte swizzle, four 32-column panels).  D = Z^T Z then holds, for each
+// packed row position r, the blocks hi_r^T hi_r, hi_r^T lo_r, lo_r^T hi_r and
+// lo_r^T lo_r on the diagonal of its 2 x 2 block grid; their sum over r is
+// the Gram of the full FP32 values (every cross term kept, so the split adds
+// no truncation).  Pass 1 reads the packed rows straight from memory (the
+// rows of a block are contiguous).  Pass 2 forms Q = X W per tile of 128 rows
+// (M = 128, N = kout, 3 x TF32 in tensor memory) and the workers write Q's
+// split parts into the packed layout of the Gram of Q.
+//
+// Roles as in gram_pipe_kernel (TMA producer warp, MMA warp, 8 worker warps).
+// Tensor memory: pass 1 two sets x two accumulators of 128 columns; pass 2
+// two formation buffers of 32 columns and two accumulator sets of 128.
+// Each worker thread drains its TMEM lane (one row of D) into float-float
+// sums of the kk-wide row piece that belongs to its packed row position; the
+// pieces are added in a fixed order at the end.
+constexpr int kPackStages = 3;
+constexpr int kP1Stage = 4 * kPanelBytes;         // pass 1: raw (2 panels) + lo (2 panels)
+constexpr int kP2Stage = 2 * kPanelBytes;         // pass 2: raw (1 panel) + lo (1 panel)
+constexpr int kP2Zq = kPackStages * kP2Stage;     // 2 buffers x 4 panels x (64 rows x 128 B)
+constexpr int kP2ZqBytes = 4 * 64 * 128;
+constexpr int kP2Wh = kP2Zq + 2 * kP2ZqBytes;
+constexpr int kP2Wl = kP2Wh + 32 * 128;
+constexpr int kPackSmemBytes = (kPackStages * kP1Stage > kP2Wl + 32 * 128 ? kPackStages * kP1Stage : kP2Wl + 32 * 128) + 1024;
+
+// N (4, 8, 16 or 32) consecutive TMEM columns of this thread's lane, no wait.
+template <int N>
+__device__ __forceinline__ void tmem_ld_nowait(uint32_t taddr, uint32_t (&r)[N]) {
+  if constexpr (N == 4) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+  } else if constexpr (N == 8) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+  } else if constexpr (N == 16) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+  }
+}
+
+struct PackArgs {
+  int k, kout, np, ksteps_f;
+  int kk, rr;      // Gram width (k in pass 1, kout in pass 2) and rows per packed row (64 / kk)
+  int64_t rows;
+  const int64_t* rows_dev;
+  const float* W;  // pass 2: W block base; nullptr for pass 1
+  int wld;
+  double* part;    // [grid][kout][kout]
+  int32_t* status;
+  int64_t spin_limit;
+};
+
+// Byte offset of column col (0..127) of packed row w in a Z panel set whose
+// panels hold `wr` packed rows each (32-byte-atom 128-byte swizzle).
+__device__ __forceinline__ int z_offset(int w, int col, int wr) {
+  const int p = col >> 5, c = col & 31;
+  return p * wr * 128 + w * 128 + ((((c >> 3) ^ (w & 3))) << 5) + ((c & 7) << 2);
+}
+
+template <int KK>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    gram_pack_kernel(const __grid_constant__ CUtensorMap tmx, PackArgs a) {
+  constexpr int RR = 64 / KK;  // rows per packed row
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ PipeSmem S;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool pass2 = a.W != nullptr;
+  const int64_t rows = a.rows_dev ? *a.rows_dev : a.rows;
+  // pass 1: tiles of 128 packed rows (128 R rows); pass 2: tiles of 128 rows
+  const int64_t tile_rows = pass2 ? kTileRows : static_cast<int64_t>(kTileRows) * a.rr;
+  const int64_t ntiles_all = (rows + tile_rows - 1) / tile_rows;
+  const int G = gridDim.x;
+  const int n = ntiles_all > blockIdx.x ? static_cast<int>((ntiles_all - 1 - blockIdx.x) / G + 1) : 0;
+  auto tile_index = [&](int i) -> int64_t { return static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(i) * G; };
+  const int stage_bytes = pass2 ? kP2Stage : kP1Stage;
+  const int raw_bytes = stage_bytes / 2;  // the lo parts follow the raw (hi) parts of a stage
+  const int wrq = kTileRows / a.rr;       // pass 2: packed rows of Q per tile
+
+  if (tid == 0) {
+    for (int q = 0; q < kPipeStages; ++q) {
+      mbar_init(&S.tma_full[q], 1);
+      mbar_init(&S.stage_empty[q], 1);
+      mbar_init(&S.op_full[q], kWorkWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.d1_full[b], 1);
+      mbar_init(&S.d1_empty[b], kWorkWarps);
+      mbar_init(&S.q_full[b], kWorkWarps);
+      mbar_init(&S.q_empty[b], 1);
+      mbar_init(&S.acc_full[b], 1);
+      mbar_init(&S.acc_empty[b], kWorkWarps);
+    }
+    mbar_init(&S.done, 1);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (pass2 && warp >= 2) {  // W^T (np rows x k, K-major 128-byte swizzle): hi and lo parts, zero padded
+    const int wt = tid - 64;
+    float* wh = reinterpret_cast<float*>(base + kP2Wh);
+    float* wl = reinterpret_cast<float*>(base + kP2Wl);
+    for (int e = wt; e < 32 * 32; e += 32 * kWorkWarps) {
+      wh[e] = 0.f;
+      wl[e] = 0.f;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
+    for (int e = wt; e < a.kout * a.k; e += 32 * kWorkWarps) {
+      const int nn = e / a.k, kc = e - nn * a.k;
+      const float v = (kc <= nn) ? a.W[static_cast<int64_t>(kc) * a.wld + nn] : 0.f;  // W upper triangular
+      const int off = sw128_offset(nn, kc, 32 * 128);
+      const float h = tf32_hi(v);
+      *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wh) + off) = h;
+      *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wl) + off) = tf32_rn(v - h);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem_base;
+  auto d1_addr = [&](int b) { return tmem + static_cast<uint32_t>(b * 32); };
+  auto acc_addr = [&](int b, int q) {
+    return pass2 ? tmem + 64u + static_cast<uint32_t>(b * 128) : tmem + static_cast<uint32_t>(b * 256 + q * 128);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < n; ++i) {
+        const int s = i % kPackStages;
+        if (i >= kPackStages &&
+            !pipe_wait(S, &S.stage_empty[s], static_cast<uint32_t>(((i / kPackStages) - 1) & 1), a.spin_limit, a.status))
+          break;
+        unsigned char* dst = base + s * stage_bytes;
+        const int y = static_cast<int>(tile_index(i) * kTileRows);
+        if (pass2) {
+          expect_tx(&S.tma_full[s], kPanelBytes);
+          tma_load_2d(dst, &tmx, 0, y, &S.tma_full[s]);
+        } else {  // 128 packed rows x 64 columns: two 32-column panels
+          expect_tx(&S.tma_full[s], 2 * kPanelBytes);
+          tma_load_2d(dst, &tmx, 0, y, &S.tma_full[s]);
+          tma_load_2d(dst + kPanelBytes, &tmx, 32, y, &S.tma_full[s]);
+        }
+        issued = i + 1;
+      }
+      for (int i = issued > kPackStages ? issued - kPackStages : 0; i < issued; ++i)
+        drain_wait(&S.tma_full[i % kPackStages], static_cast<uint32_t>((i / kPackStages) & 1), a.spin_limit, a.status);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t idg = idesc_tf32(128, 128, 1);
+      const uint32_t idf = idesc_tf32(128, a.np);
+      const uint32_t wh = smem_u32(base + kP2Wh), wl = smem_u32(base + kP2Wl);
+      auto formation = [&](int j) -> bool {  // D1[j & 1] = X_j W (3 x TF32, the large term last)
+        const int s = j % kPackStages, bd = j & 1;
+        if (!pipe_wait(S, &S.op_full[s], static_cast<uint32_t>((j / kPackStages) & 1), a.spin_limit, a.status))
+          return false;
+        if (j >= 2 && !pipe_wait(S, &S.d1_empty[bd], static_cast<uint32_t>(((j / 2) - 1) & 1), a.spin_limit, a.status))
+          return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(base + s * stage_bytes), al = ah + static_cast<uint32_t>(raw_bytes);
+        for (int ks = 0; ks < a.ksteps_f; ++ks) {
+          const uint32_t o = static_cast<uint32_t>(ks * 32);
+          mma_tf32(d1_addr(bd), desc_kmajor_sw128(al + o), desc_kmajor_sw128(wh + o), idf, ks > 0 ? 1u : 0u);
+          mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wl + o), idf, 1u);
+        }
+        for (int ks = 0; ks < a.ksteps_f; ++ks) {
+          const uint32_t o = static_cast<uint32_t>(ks * 32);
+          mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wh + o), idf, 1u);
+        }
+        mma_commit(&S.stage_empty[s]);
+        mma_commit(&S.d1_full[bd]);
+        return true;
+      };
+      if (!pass2) {
+        for (int i = 0; i < n; ++i) {
+          const int s = i % kPackStages, b = i & 1;
+          if (!pipe_wait(S, &S.op_full[s], static_cast<uint32_t>((i / kPackStages) & 1), a.spin_limit, a.status)) break;
+          if (i >= 2 && !pipe_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
+            break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // Z = raw (hi) panels followed by the lo panels; K steps of 8 packed rows alternate accumulators
+          const uint64_t dz = desc_mn_sw128_32b(smem_u32(base + s * stage_bytes), kPanelBytes);
+#pragma unroll
+          for (int ks = 0; ks < kTileRows / 8; ++ks)
+            mma_tf32(acc_addr(b, ks & 1), dz + static_cast<uint64_t>(ks * 64), dz + static_cast<uint64_t>(ks * 64), idg,
+                     ks >= 2 ? 1u : 0u);
+          mma_commit(&S.stage_empty[s]);
+          mma_commit(&S.acc_full[b]);
+        }
+      } else if (n > 0 && formation(0)) {
+        for (int i = 0; i < n; ++i) {
+          const int b = i & 1;
+          if (i + 1 < n && !formation(i + 1)) break;
+          if (!pipe_wait(S, &S.q_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) break;
+          if (i >= 2 && !pipe_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
+            break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t dz = desc_mn_sw128_32b(smem_u32(base + kP2Zq + b * kP2ZqBytes), static_cast<uint32_t>(wrq * 128));
+          for (int ks = 0; ks < wrq / 8; ++ks)
+            mma_tf32(acc_addr(b, 0), dz + static_cast<uint64_t>(ks * 64), dz + static_cast<uint64_t>(ks * 64), idg,
+                     ks > 0 ? 1u : 0u);
+          mma_commit(&S.q_empty[b]);
+          mma_commit(&S.acc_full[b]);
+        }
+      }
+      mma_commit(&S.done);
+      drain_wait(&S.done, 0u, a.spin_limit, a.status);
+    }
+  } else {
+    // ------------------------------------------------------------ workers
+    const int wt = tid - 64;
+    const int quarter = warp & 3, sub = (warp - 2) >> 2;
+    auto split = [&](int i) -> bool {
+      const int s = i % kPackStages;
+      if (!warp_wait(S, &S.tma_full[s], static_cast<uint32_t>((i / kPackStages) & 1), a.spin_limit, a.status))
+        return false;
+      float4* X4 = reinterpret_cast<float4*>(base + s * stage_bytes);
+      float4* L4 = reinterpret_cast<float4*>(base + s * stage_bytes + raw_bytes);
+      const int64_t t0 = tile_index(i);
+      const bool full = (t0 + 1) * tile_rows <= rows;  // no row of the tile lies past the end
+      for (int e = wt; e < raw_bytes / 16; e += 32 * kWorkWarps) {
+        float4 v = X4[e];
+        if (!full) {
+          int64_t row;
+          if (pass2) {
+            row = t0 * kTileRows + (e >> 3);  // K-major: 8 float4 per 128-byte row
+          } else {  // packed row w of panel p: the logical column gives the row inside the packed row
+            const int p = e >> 10, w = (e & 1023) >> 3, slot = e & 7;
+            const int col = p * 32 + (((slot >> 1) ^ (w & 3)) << 3) + ((slot & 1) << 2);
+            row = (t0 * kTileRows + w) * RR + col / KK;
+          }
+          if (row >= rows) v = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float4 h, l;
+        h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
+        l.x = tf32_rn(v.x - h.x); l.y = tf32_rn(v.y - h.y); l.z = tf32_rn(v.z - h.z); l.w = tf32_rn(v.w - h.w);
+        X4[e] = h;
+        L4[e] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&S.op_full[s]);
+      return true;
+    };
+    // this thread's places in the packed Q layout (fixed for the whole launch)
+    const int qt = quarter * 32 + lane, qc0 = sub * 16;
+    int qoff_h[4], qoff_l[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const int w = qt / RR, cbq = (qt % RR) * KK + qc0 + 4 * g;
+      qoff_h[g] = z_offset(w, cbq, wrq);
+      qoff_l[g] = z_offset(w, 64 + cbq, wrq);
+    }
+    auto make_q = [&](int i) -> bool {
+      const int b = i & 1;
+      if (!warp_wait(S, &S.d1_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) return false;
+      if (i >= 2 && !warp_wait(S, &S.q_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
+        return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // TMEM lane qt = row of the tile; columns qc0 .. qc0 + 15 of Q
+      float q[16];
+      tmem_ld16(d1_addr(b) + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(qc0), q);
+      const bool live = tile_index(i) * kTileRows + qt < rows;
+      if (qc0 < KK) {
+        unsigned char* zq = base + kP2Zq + b * kP2ZqBytes;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          if (qc0 + 4 * g >= KK) break;
+          float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+          if (live) {
+            const float* v = q + 4 * g;
+            h = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
+            l = make_float4(tf32_rn(v[0] - h.x), tf32_rn(v[1] - h.y), tf32_rn(v[2] - h.z), tf32_rn(v[3] - h.w));
+          }
+          *reinterpret_cast<float4*>(zq + qoff_h[g]) = h;
+          *reinterpret_cast<float4*>(zq + qoff_l[g]) = l;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive_cta(&S.d1_empty[b]);
+        mbar_arrive_cta(&S.q_full[b]);
+      }
+      return true;
+    };
+    // This thread's TMEM lane is row i = 32 quarter + lane of D; within its
+    // 64-row half it is position r * KK + a of a packed row.  Its piece of the
+    // Gram row a sits in the 32-column chunk cb (hi columns) and 64 + cb (lo),
+    // at columns (lane / KK) * KK ... + KK of the chunk: every KK-column group
+    // of the chunk is loaded (warp-uniform addresses) and each lane keeps its own.
+    const int cb = (quarter & 1) * 32;
+    const int mine = lane / KK;
+    const bool drains = !pass2 || sub == 0;
+    float grp[KK], fh[KK], fl[KK];
+#pragma unroll
+    for (int j = 0; j < KK; ++j) {
+      grp[j] = 0.f;
+      fh[j] = 0.f;
+      fl[j] = 0.f;
+    }
+    int grouped = 0;
+    auto fold = [&]() {
+#pragma unroll
+      for (int j = 0; j < KK; ++j) {
+        float s_, e_;
+        two_sum(fh[j], grp[j], s_, e_);
+        fh[j] = s_;
+        fl[j] = __fadd_rn(fl[j], e_);
+        grp[j] = 0.f;
+      }
+    };
+    auto drain = [&](int i) -> bool {
+      const int b = i & 1;
+      if (!warp_wait(S, &S.acc_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (drains) {
+        const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
+        const uint32_t acc = acc_addr(b, pass2 ? 0 : sub) + lanes + static_cast<uint32_t>(cb);
+        constexpr int C = 32 / KK;
+        uint32_t rh[C][KK], rl[C][KK];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          tmem_ld_nowait<KK>(acc + static_cast<uint32_t>(c * KK), rh[c]);
+          tmem_ld_nowait<KK>(acc + 64u + static_cast<uint32_t>(c * KK), rl[c]);
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+          if (c == mine) {
+#pragma unroll
+            for (int j = 0; j < KK; ++j)
+              grp[j] = __fadd_rn(grp[j], __fadd_rn(__uint_as_float(rh[c][j]), __uint_as_float(rl[c][j])));
+          }
+        if (++grouped == kDrainGroup) {
+          fold();
+          grouped = 0;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&S.acc_empty[b]);
+      return true;
+    };
+    bool ok = n == 0 || split(0);
+    for (int i = 0; ok && i < n; ++i) {
+      if (i + 1 < n && !split(i + 1)) break;
+      if (pass2 && !make_q(i)) break;
+      if (i >= 1 && !drain(i - 1)) break;
+      if (i == n - 1) ok = drain(i);
+    }
+    // pieces of each Gram row a: 2 halves x R positions x (2 accumulators in pass 1), summed in a fixed order
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
+    double* pieces = reinterpret_cast<double*>(base);  // [sub][128 lanes][32]; the stages are idle now
+    fold();
+    if (drains) {
+      const int i128 = quarter * 32 + lane;
+#pragma unroll
+      for (int j = 0; j < KK; ++j)
+        pieces[(sub * 128 + i128) * 32 + j] = static_cast<double>(fh[j]) + static_cast<double>(fl[j]);
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
+    double* part = a.part + static_cast<int64_t>(blockIdx.x) * a.kout * a.kout;
+    const int nsub = pass2 ? 1 : 2;
+    auto gram_entry = [&](int ra, int cbb) {
+      double g = 0.0;
+      for (int sb = 0; sb < nsub; ++sb)
+        for (int half = 0; half < 2; ++half)
+          for (int r = 0; r < RR; ++r) g += pieces[(sb * 128 + half * 64 + r * KK + ra) * 32 + cbb];
+      return g;
+    };
+    for (int e = wt; e < KK * KK; e += 32 * kWorkWarps) {  // upper triangle, symmetrised
+      const int ra = e / KK, cbb = e - ra * KK;
+      if (ra <= cbb) part[ra * a.kout + cbb] = 0.5 * (gram_entry(ra, cbb) + gram_entry(cbb, ra));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() { return tensor_map_encoder(); }
 
 struct Geometry {
@@ -873,6 +1300,13 @@ Geometry geometry(int k, int kout, bool pass2) {
 
 }  // namespace
 
+// The packed engine writes symmetrised upper-triangle partials; the others
+// write P with G = (P + P^T) / 2.
+bool gram_tc_packs(int k, int kout, bool pass2) {
+  const int kk = pass2 ? kout : k;
+  return (kk == 4 || kk == 8 || kk == 16 || kk == 32) && k <= 32;
+}
+
 // The tensor-core engine handles a Gram block when TMA can address X
 // (k a multiple of 4) and the block fits the 64-column tile.
 bool gram_tc_supported(int k, int kout) { return k % 4 == 0 && k <= 64 && kout <= 64 && encoder() != nullptr; }
@@ -880,6 +1314,64 @@ bool gram_tc_supported(int k, int kout) { return k % 4 == 0 && k <= 64 && kout <
 cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,
                                  int kout, double* part, int grid_max, int num_sms, int* grid_used, int32_t* status,
                                  int64_t spin_limit, cudaStream_t s) {
+  const int kk = W ? kout : k;
+  if (gram_tc_packs(k, kout, W != nullptr)) {  // packed-operand engine: persistent CTAs, one per SM
+    const int rr = 64 / kk;
+    const int64_t tile_rows = W ? kTileRows : static_cast<int64_t>(kTileRows) * rr;
+    int grid = static_cast<int>((rows + tile_rows - 1) / tile_rows);
+    if (grid > num_sms) grid = num_sms;
+    if (grid > grid_max) grid = grid_max;
+    if (grid < 1) grid = 1;
+    *grid_used = grid;
+    PackArgs a{};
+    a.k = k;
+    a.kout = kout;
+    a.np = (kout + 15) / 16 * 16;
+    a.ksteps_f = (k + 7) / 8;
+    a.kk = kk;
+    a.rr = rr;
+    a.rows = rows;
+    a.rows_dev = rows_dev;
+    a.W = W;
+    a.wld = wld;
+    a.part = part;
+    a.status = status;
+    a.spin_limit = spin_limit;
+    CUtensorMap map;
+    cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kTileRows)};
+    cuuint32_t es[2] = {1, 1};
+    CUresult cr;
+    if (W) {  // rows of X, K-major operand of the formation product
+      cuuint64_t dims[2] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows > 0 ? rows : 1)};
+      cuuint64_t strides[1] = {static_cast<cuuint64_t>(k) * 4};
+      cr = encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {  // packed rows: rr consecutive rows = one 64-column row (the last one may run into the next array)
+      const int64_t wrows = (rows + rr - 1) / rr;
+      cuuint64_t dims[2] = {64, static_cast<cuuint64_t>(wrows > 0 ? wrows : 1)};
+      cuuint64_t strides[1] = {256};
+      cr = encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    static int granted[64][4] = {};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    const int which = kk == 4 ? 0 : (kk == 8 ? 1 : (kk == 16 ? 2 : 3));
+    void (*kern)(const CUtensorMap, PackArgs) =
+        which == 0 ? gram_pack_kernel<4> : (which == 1 ? gram_pack_kernel<8> : (which == 2 ? gram_pack_kernel<16> : gram_pack_kernel<32>));
+    if (dev < 0 || dev >= 64 || !granted[dev][which]) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPackSmemBytes);
+      if (err != cudaSuccess) return err;
+      if (dev >= 0 && dev < 64) granted[dev][which] = 1;
+    }
+    kern<<<grid, kPipeThreads, kPackSmemBytes, s>>>(map, a);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   if (k <= 32 && kout <= 32) {  // pipelined engine: persistent CTAs, one per SM
     int grid = static_cast<int>((rows + kTileRows - 1) / kTileRows);
     if (grid > num_sms) grid = num_sms;
