@@ -40,11 +40,6 @@ struct TwoTables {
   int withhold;  // test-only: tile 0 of table A never publishes its run count
 };
 
-__device__ __forceinline__ uint64_t ld_acquire64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 __device__ __forceinline__ void st_release64(uint64_t* p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -65,17 +60,51 @@ __device__ __forceinline__ int num_passes(const DevHeader* h, int t) {
   return p < 1 ? 1 : p;
 }
 
-// Bounded wait until the look-back word of a tile is published; returns the
-// word, or 0 after spin_limit polls (the caller records a timeout).
-__device__ __forceinline__ uint64_t wait_word(const uint64_t* p, int64_t limit) {
-  uint64_t v = ld_acquire64(p);
-  int64_t spins = 0;
-  while ((v >> 62) == 0) {
-    if (++spins > limit) return 0;
-    __nanosleep(32);
-    v = ld_acquire64(p);
-  }
+__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+// Per-tile digit counts and output offsets of a pass (reduce-then-scan),
+// kept in the table's sort word area: [pass][counts | offsets][tile][digit].
+__device__ __forceinline__ uint32_t* tile_counts(const TableWork& T, int pass) {
+  return reinterpret_cast<uint32_t*>(T.sort_status) + static_cast<int64_t>(pass) * 2 * T.tiles * kRadixBins;
+}
+__device__ __forceinline__ uint32_t* tile_offsets(const TableWork& T, int pass) {
+  return tile_counts(T, pass) + static_cast<int64_t>(T.tiles) * kRadixBins;
+}
+
+// Decoupled look-back over the words of tiles tile-1, tile-2, ... (each word
+// holds a flag and a count, written at once): the sum of the counts back to
+// and including the first inclusive word.  Eight predecessors are read at a
+// time (independent relaxed loads; the count travels with its flag, so no
+// ordering beyond the word itself is needed).  Returns false if a word stayed
+// unpublished for spin_limit polls.
+__device__ __forceinline__ bool lookback(const uint64_t* words, int64_t stride, int tile, int64_t limit,
+                                         uint64_t& excl) {
+  excl = 0;
+  int j = tile - 1;
+  while (j >= 0) {
+    uint64_t w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) w[u] = j - u >= 0 ? ld_relaxed64(words + static_cast<int64_t>(j - u) * stride) : 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (j - u < 0) return true;
+      uint64_t v = w[u];
+      int64_t spins = 0;
+      while ((v >> 62) == 0) {
+        if (++spins > limit) return false;
+        __nanosleep(32);
+        v = ld_relaxed64(words + static_cast<int64_t>(j - u) * stride);
+      }
+      excl += v & kCountMask;
+      if (v & kFlagInc) return true;
+    }
+    j -= 8;
+  }
+  return true;
 }
 
 __global__ void reset_kernel(DevHeader* h, uint64_t* g0, int64_t ng0, uint64_t* g1, int64_t ng1) {
@@ -95,25 +124,33 @@ __global__ void reset_kernel(DevHeader* h, uint64_t* g0, int64_t ng0, uint64_t* 
   for (int64_t i = tid; i < ng1; i += stride) g1[i] = 0ull;
 }
 
-// Global digit histograms (all kMaxPasses digits) and the key range.
+// The key range, the first pass's digit counts per tile and their global
+// sum (the later passes' counts come from tile_count_kernel, once the key
+// range has fixed how many passes run).
 __global__ void __launch_bounds__(kSortThreads) key_hist_kernel(TwoTables a) {
   int tile;
   const int t = table_of(a, blockIdx.x, tile);
   const TableWork& T = a.t[t];
-  __shared__ uint32_t hist[kMaxPasses][kRadixBins];
-  for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&hist[0][0])[i] = 0u;
+  __shared__ uint32_t hist[kRadixBins];
+  for (int i = threadIdx.x; i < kRadixBins; i += blockDim.x) hist[i] = 0u;
   __syncthreads();
   uint32_t lo = 0xffffffffu, hi = 0u;
   const int64_t base = static_cast<int64_t>(tile) * kSortTile;
+  uint32_t u[kSortItems];
+#pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
     const int64_t i = base + it * kSortThreads + threadIdx.x;
-    if (i < T.m) {
-      const uint32_t u = key_to_ordered(T.key[i]);
-      lo = min(lo, u);
-      hi = max(hi, u);
+    u[it] = i < T.m ? key_to_ordered(T.key[i]) : 0u;
+  }
 #pragma unroll
-      for (int p = 0; p < kMaxPasses; ++p) atomicAdd(&hist[p][(u >> (p * kRadixBits)) & (kRadixBins - 1)], 1u);
+  for (int it = 0; it < kSortItems; ++it) {
+    const int64_t i = base + it * kSortThreads + threadIdx.x;
+    const bool valid = i < T.m;
+    if (valid) {
+      lo = min(lo, u[it]);
+      hi = max(hi, u[it]);
     }
+    if (valid) atomicAdd(&hist[u[it] & (kRadixBins - 1)], 1u);
   }
   for (int o = 16; o > 0; o >>= 1) {
     lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
@@ -124,23 +161,109 @@ __global__ void __launch_bounds__(kSortThreads) key_hist_kernel(TwoTables a) {
     atomicMax(&a.h->kmax[t], hi);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) {
-    const uint32_t c = (&hist[0][0])[i];
-    if (c) atomicAdd(&T.hist[i], c);
+  uint32_t* tc = tile_counts(T, 0) + static_cast<int64_t>(tile) * kRadixBins;
+  for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
+    const uint32_t c = hist[d];
+    tc[d] = c;
+    if (c) atomicAdd(&T.hist[d], c);
   }
 }
 
-// One stable LSD pass over digit `pass`.  Tiles are taken in ticket order,
-// so every earlier tile belongs to a block that is already running.
-__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(TwoTables a, int pass) {
-  constexpr int kWarps = kSortThreads / 32;
-  __shared__ uint32_t cnt[kWarps][kRadixBins];
-  __shared__ uint32_t sbase[kRadixBins];
-  __shared__ int s_g;
-  if (threadIdx.x == 0) s_g = static_cast<int>(atomicAdd(&a.h->ticket[4 + pass], 1u));
-  __syncthreads();
+// Digit counts of every tile for a later pass (the keys as the previous pass left them).
+__global__ void __launch_bounds__(kSortThreads) tile_count_kernel(TwoTables a, int pass) {
   int tile;
-  const int t = table_of(a, s_g, tile);
+  const int t = table_of(a, blockIdx.x, tile);
+  const TableWork& T = a.t[t];
+  if (pass >= num_passes(a.h, t)) return;
+  __shared__ uint32_t hist[kRadixBins];
+  for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) hist[d] = 0u;
+  __syncthreads();
+  const uint32_t* kin = T.kb[(pass - 1) & 1];
+  const int shift = pass * kRadixBits;
+  const int64_t base = static_cast<int64_t>(tile) * kSortTile;
+  uint32_t u[kSortItems];
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const int64_t i = base + it * kSortThreads + threadIdx.x;
+    u[it] = i < T.m ? kin[i] : 0u;
+  }
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const int64_t i = base + it * kSortThreads + threadIdx.x;
+    const bool valid = i < T.m;
+    if (valid) atomicAdd(&hist[(u[it] >> shift) & (kRadixBins - 1)], 1u);
+  }
+  __syncthreads();
+  uint32_t* tc = tile_counts(T, pass) + static_cast<int64_t>(tile) * kRadixBins;
+  for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
+    const uint32_t c = hist[d];
+    tc[d] = c;
+    if (c) atomicAdd(&T.hist[pass * kRadixBins + d], c);  // the pass's global counts
+  }
+}
+
+// Per (table, digit): the position of each tile's first key of that digit in
+// the pass's output, = (keys of smaller digits) + (keys of this digit in
+// earlier tiles): an exclusive scan over tiles.
+__global__ void __launch_bounds__(kRadixBins) tile_scan_kernel(TwoTables a, int pass) {
+  const int t = blockIdx.x / kRadixBins, d = blockIdx.x % kRadixBins;
+  const TableWork& T = a.t[t];
+  if (T.tiles == 0 || pass >= num_passes(a.h, t)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ uint32_t s_w[kRadixBins / 32];
+  __shared__ uint32_t s_carry;
+  // keys of digits below d
+  uint32_t v = threadIdx.x < d ? T.hist[pass * kRadixBins + threadIdx.x] : 0u;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) s_w[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t g = 0;
+    for (int w = 0; w < kRadixBins / 32; ++w) g += s_w[w];
+    s_carry = g;
+  }
+  __syncthreads();
+  const uint32_t* tc = tile_counts(T, pass);
+  uint32_t* to = tile_offsets(T, pass);
+  for (int c0 = 0; c0 < T.tiles; c0 += kRadixBins) {
+    const int tile = c0 + threadIdx.x;
+    const uint32_t x = tile < T.tiles ? tc[static_cast<int64_t>(tile) * kRadixBins + d] : 0u;
+    uint32_t incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint32_t before = s_carry;
+    for (int w = 0; w < warp; ++w) before += s_w[w];
+    if (tile < T.tiles) to[static_cast<int64_t>(tile) * kRadixBins + d] = before + incl - x;
+    __syncthreads();
+    if (threadIdx.x == kRadixBins - 1) s_carry = before + incl;
+    __syncthreads();
+  }
+}
+
+// One stable LSD pass over digit `pass` (the scatter of reduce-then-scan).
+// Each tile ranks its keys stably (warp multi-split with match_any, then a
+// prefix over warps), places keys and payloads in shared memory in digit
+// order, and writes them out so that consecutive threads write consecutive
+// positions of each digit's output run (coalesced), at the digit offsets
+// from tile_scan_kernel.
+constexpr int kSortSmem = (kSortThreads / 32) * kRadixBins * 4 + 3 * kRadixBins * 4 + 2 * kSortTile * 4;
+
+__global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(TwoTables a, int pass) {
+  constexpr int kWarps = kSortThreads / 32;
+  extern __shared__ __align__(16) uint32_t sm_sort[];
+  uint32_t (*cnt)[kRadixBins] = reinterpret_cast<uint32_t (*)[kRadixBins]>(sm_sort);
+  uint32_t* sbase = sm_sort + kWarps * kRadixBins;   // output offset of the tile's first key of digit d
+  uint32_t* tpre = sbase + kRadixBins;               // tile-local start of digit d
+  uint32_t* s_w = tpre + kRadixBins;                 // per-warp sums of the local scan
+  uint32_t* sk = s_w + kRadixBins;                   // keys in digit order
+  int32_t* sv = reinterpret_cast<int32_t*>(sk + kSortTile);  // payloads in digit order
+  int tile;
+  const int t = table_of(a, blockIdx.x, tile);
   const TableWork& T = a.t[t];
   const int P = num_passes(a.h, t);
   if (pass >= P) return;
@@ -149,27 +272,33 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(TwoTables a, in
   for (int i = threadIdx.x; i < kWarps * kRadixBins; i += blockDim.x) (&cnt[0][0])[i] = 0u;
   __syncthreads();
   const int shift = pass * kRadixBits;
-  const int64_t base = static_cast<int64_t>(tile) * kSortTile + warp * (32 * kSortItems);
+  const int64_t tile0 = static_cast<int64_t>(tile) * kSortTile;
+  const int64_t base = tile0 + warp * (32 * kSortItems);
   const uint32_t* kin = pass == 0 ? nullptr : T.kb[(pass - 1) & 1];
   const int32_t* vin = pass == 0 ? nullptr : T.vb[(pass - 1) & 1];
   uint32_t key[kSortItems];
-  int32_t val[kSortItems];
   uint32_t rank[kSortItems];
   const uint32_t lt_mask = (1u << lane) - 1u;
+  // all loads first (the warp barriers of the ranking would serialise them)
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = base + r * 32 + lane;
+    key[r] = i < T.m ? (pass == 0 ? key_to_ordered(T.key[i]) : kin[i]) : 0u;
+  }
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t i = base + r * 32 + lane;
     const bool valid = i < T.m;
-    uint32_t u = 0;
-    int32_t v = 0;
-    if (valid) {
-      u = pass == 0 ? key_to_ordered(T.key[i]) : kin[i];
-      v = pass == 0 ? static_cast<int32_t>(i) : vin[i];
-    }
-    key[r] = u;
-    val[r] = v;
+    const uint32_t u = key[r];
     const uint32_t d = valid ? ((u >> shift) & (kRadixBins - 1)) : kRadixBins;  // padding gets its own bin
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // lanes with the same digit: the AND over the digit's 9 bits of the
+    // matching ballot (the padding bin 256 needs the ninth bit)
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int bit = 0; bit <= kRadixBits; ++bit) {
+      const uint32_t m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+      peers &= ((d >> bit) & 1u) ? m : ~m;
+    }
     uint32_t before = 0;
     if (valid) before = cnt[warp][d];
     __syncwarp();
@@ -178,57 +307,60 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(TwoTables a, in
     rank[r] = before + __popc(peers & lt_mask);
   }
   __syncthreads();
-  // per digit: exclusive prefix over warps, the tile's count, look-back, global base
-  uint64_t* status = T.sort_status + static_cast<int64_t>(pass) * T.tiles * kRadixBins;
-  {
-    const int d = threadIdx.x;  // kSortThreads == kRadixBins
-    uint32_t run = 0;
+  // per digit: exclusive prefix over warps, the digit's total in the tile,
+  // its tile-local start (scan over digits) and the output offset
+  uint32_t tot = 0;
+  if (threadIdx.x < kRadixBins) {
+    const int d = threadIdx.x;
     for (int w = 0; w < kWarps; ++w) {
       const uint32_t c = cnt[w][d];
-      cnt[w][d] = run;
-      run += c;
+      cnt[w][d] = tot;
+      tot += c;
     }
-    uint64_t* mine = status + static_cast<int64_t>(tile) * kRadixBins + d;
-    uint64_t excl = 0;
-    if (tile == 0) {
-      st_release64(mine, kFlagInc | run);
-    } else {
-      st_release64(mine, kFlagAgg | run);
-      for (int j = tile - 1; j >= 0; --j) {
-        const uint64_t w = wait_word(status + static_cast<int64_t>(j) * kRadixBins + d, a.spin_limit);
-        if (w == 0) {
-          set_status(&a.h->status, kStatusTimeout);
-          break;
-        }
-        excl += w & kCountMask;
-        if (w & kFlagInc) break;
-      }
-      st_release64(mine, kFlagInc | (excl + run));
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    // global exclusive base of digit d for this pass (scan of the histogram)
-    __shared__ uint32_t s_tot[kRadixBins];
-    s_tot[d] = T.hist[pass * kRadixBins + d];
-    __syncthreads();
-    uint32_t gb = 0;
-    for (int e = 0; e < d; ++e) gb += s_tot[e];
-    sbase[d] = gb + static_cast<uint32_t>(excl);
+    if (lane == 31) s_w[warp] = incl;
+    tpre[d] = incl - tot;  // within-warp part; the earlier warps are added below
+    sbase[d] = tile_offsets(T, pass)[static_cast<int64_t>(tile) * kRadixBins + d];
   }
   __syncthreads();
-  uint32_t* ko = T.kb[pass & 1];
-  int32_t* vo = last ? T.perm : T.vb[pass & 1];
+  if (threadIdx.x < kRadixBins) {
+    uint32_t add = 0;
+    for (int w = 0; w < warp; ++w) add += s_w[w];
+    tpre[threadIdx.x] += add;
+  }
+  __syncthreads();
+  // keys and payloads into shared memory in digit order
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t i = base + r * 32 + lane;
     if (i < T.m) {
       const uint32_t d = (key[r] >> shift) & (kRadixBins - 1);
-      const uint32_t pos = sbase[d] + cnt[warp][d] + rank[r];
-      if (last) {
-        T.sorted_key[pos] = ordered_to_key(key[r]);
-      } else {
-        ko[pos] = key[r];
-      }
-      vo[pos] = val[r];
+      const uint32_t lpos = tpre[d] + cnt[warp][d] + rank[r];
+      sk[lpos] = key[r];
+      sv[lpos] = pass == 0 ? static_cast<int32_t>(i) : vin[i];  // the payload is read again (cached)
     }
+  }
+  __syncthreads();
+  // coalesced writes: position j of the tile's digit-ordered keys goes to
+  // sbase[d] + (j - tpre[d])
+  const int cnt_tile = static_cast<int>(T.m - tile0 < kSortTile ? T.m - tile0 : kSortTile);
+  uint32_t* ko = T.kb[pass & 1];
+  int32_t* vo = last ? T.perm : T.vb[pass & 1];
+  for (int j = threadIdx.x; j < cnt_tile; j += kSortThreads) {
+    const uint32_t k = sk[j];
+    const uint32_t d = (k >> shift) & (kRadixBins - 1);
+    const uint32_t pos = sbase[d] + (static_cast<uint32_t>(j) - tpre[d]);
+    if (last) {
+      T.sorted_key[pos] = ordered_to_key(k);
+    } else {
+      ko[pos] = k;
+    }
+    vo[pos] = sv[j];
   }
 }
 
@@ -283,15 +415,7 @@ __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
       if (!(a.withhold && t == 0)) st_release64(mine, kFlagInc | tile_total);
     } else {
       st_release64(mine, kFlagAgg | tile_total);
-      for (int j = tile - 1; j >= 0; --j) {
-        const uint64_t w = wait_word(T.run_status + j, a.spin_limit);
-        if (w == 0) {
-          set_status(&a.h->status, kStatusTimeout);
-          break;
-        }
-        excl += w & kCountMask;
-        if (w & kFlagInc) break;
-      }
+      if (!lookback(T.run_status, 1, tile, a.spin_limit, excl)) set_status(&a.h->status, kStatusTimeout);
       st_release64(mine, kFlagInc | (excl + tile_total));
     }
     s_excl = excl;
@@ -385,13 +509,14 @@ int64_t group_status_words(int tiles) {
 }
 
 cudaError_t launch_reset(const Plan& p, cudaStream_t s) {
-  const int64_t g0 = p.t[0].tiles > 0 ? group_status_words(p.t[0].tiles) : 0;
-  const int64_t g1 = p.t[1].tiles > 0 ? group_status_words(p.t[1].tiles) : 0;
+  // only the run-count look-back words need to start at zero (the sort's
+  // per-tile counts and offsets are rewritten by every call)
+  const int64_t g0 = p.t[0].tiles, g1 = p.t[1].tiles;
   const int64_t work = g0 > g1 ? g0 : g1;
   int blocks = static_cast<int>((work + 255) / 256);
   if (blocks < 1) blocks = 1;
   if (blocks > 1024) blocks = 1024;
-  reset_kernel<<<blocks, 256, 0, s>>>(p.hdr, p.t[0].sort_status, g0, p.t[1].sort_status, g1);
+  reset_kernel<<<blocks, 256, 0, s>>>(p.hdr, p.t[0].run_status, g0, p.t[1].run_status, g1);
   count_launches(1);
   // the histograms are accumulated with atomics: clear them too
   for (int t = 0; t < 2; ++t)
@@ -412,13 +537,27 @@ cudaError_t launch_grouping(const Plan& p, cudaStream_t s) {
   a.spin_limit = p.spin_limit;
   a.withhold = p.withhold;
   if (a.nb == 0) return cudaSuccess;
+  static int granted[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64 || !granted[dev]) {
+    err = cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
+    if (err != cudaSuccess) return err;
+    if (dev >= 0 && dev < 64) granted[dev] = 1;
+  }
   key_hist_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
-  for (int pass = 0; pass < kMaxPasses; ++pass) sort_pass_kernel<<<a.nb, kSortThreads, 0, s>>>(a, pass);
+  // passes past the key range's highest differing digit return at once
+  for (int pass = 0; pass < kMaxPasses; ++pass) {
+    if (pass > 0) tile_count_kernel<<<a.nb, kSortThreads, 0, s>>>(a, pass);
+    tile_scan_kernel<<<2 * kRadixBins, kRadixBins, 0, s>>>(a, pass);
+    sort_pass_kernel<<<a.nb, kSortThreads, kSortSmem, s>>>(a, pass);
+  }
   runs_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
   const int64_t mm = p.t[0].m > p.t[1].m ? p.t[0].m : p.t[1].m;
   const int mb = static_cast<int>((mm + 255) / 256);
   if (mb > 0) match_kernel<<<mb, 256, 0, s>>>(a);
-  count_launches(2 + kMaxPasses + (mb > 0 ? 1 : 0));
+  count_launches(2 + 3 * kMaxPasses - 1 + (mb > 0 ? 1 : 0));
   return cudaGetLastError();
 }
 

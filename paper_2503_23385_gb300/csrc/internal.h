@@ -11,7 +11,7 @@
 namespace figaro {
 
 constexpr int kMaxWidth = 128;          // n1 + n2 limit of the dense n x n kernels
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 512;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per radix tile
 constexpr int kRadixBits = 8;
