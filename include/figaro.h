@@ -82,10 +82,10 @@ typedef enum figaro_gram_engine {
 
 enum {
   FIGARO_FLAG_HOST_OUTPUT = 1,     /* R / sigma pointers are host memory */
-  /* Fault injection for tests: the first tile of table A in the key
-   * grouping step withholds its run-count look-back word, so the next
-   * tile's bounded wait runs out (after spin_limit polls) and the call
-   * records FIGARO_ERR_DEVICE_TIMEOUT; the later steps then skip their work. */
+  /* Fault injection for tests (mixed path, tensor-core Gram of widths 4, 8,
+   * 16 or 32): the Gram's producer never loads its first tile, so the
+   * workers' bounded wait runs out (after about spin_limit / 16 suspended
+   * polls) and the call records FIGARO_ERR_DEVICE_TIMEOUT. */
   FIGARO_FLAG_TEST_WITHHOLD = 1 << 8
 };
 

@@ -59,6 +59,7 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
   p.n1 = n1;
   p.n2 = n2;
   p.n = n1 + n2;
+  p.lut_size = (m1 > m2 ? m1 : m2) > 0 ? (m1 > m2 ? m1 : m2) : 1;
   p.mixed = mixed;
   p.num_sms = num_sms;
   const size_t ec = mixed ? 4 : 8;   // compute element
@@ -95,6 +96,7 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
     T.other = b.take<int32_t>(static_cast<size_t>(m));
     T.hdslot = b.take<int32_t>(static_cast<size_t>(m));
     T.run_info = b.take<int32_t>(static_cast<size_t>(m) * 4);
+    T.lut = b.take<int32_t>(static_cast<size_t>(p.lut_size));
     T.tail = b.take<char>(static_cast<size_t>(m) * n * ec);
     T.chunk_rows = ht_chunk_rows(n, in_f64, mixed);
     T.chunks = static_cast<int>(ceil_div(m, T.chunk_rows));

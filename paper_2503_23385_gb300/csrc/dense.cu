@@ -43,32 +43,30 @@ __device__ __forceinline__ float rsqrt_pivot(float d) { return __frsqrt_rn(d); }
 
 // In-place semi-definite Cholesky of the n x n matrix A (shared memory,
 // row-major, upper triangle used).  act[k]: columns marked 0 on entry stay
-// dependent.  On return the upper triangle holds the factor R.
+// dependent.  On return the upper triangle holds the factor R.  Every thread
+// evaluates the pivot of step k itself (same operands, same result), so a
+// step needs one barrier; thread (r, c) of the 2D map updates the trailing
+// entries (i, j), k < i <= j, with i = r (mod rows) and j = c (mod 32).
 template <typename T>
 __device__ void chol_inplace(T* A, int n, const T* diag0, int32_t* act, T tol, T* y, int32_t* status) {
+  const int c0 = threadIdx.x & 31, r0 = threadIdx.x >> 5, rstep = blockDim.x >> 5;
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      const T d = A[k * n + k];
-      int ok = act[k];
-      if (!isfinite(d)) {
-        set_status(status, kStatusNotSpd);
-        ok = 0;
-      }
-      if (!(d > tol * diag0[k]) || !(diag0[k] > T(0))) ok = 0;
-      act[k] = ok;
-      y[k] = ok ? rsqrt_pivot(d) : T(0);
-    }
-    __syncthreads();
-    const T yk = y[k];
+    const T d = A[k * n + k];
+    int ok = act[k];
+    if (!isfinite(d)) ok = 0;
+    if (!(d > tol * diag0[k]) || !(diag0[k] > T(0))) ok = 0;
+    const T yk = ok ? rsqrt_pivot(d) : T(0);
     if (yk != T(0)) {
       const T y2 = yk * yk;
-      const int m = n - k - 1;  // trailing (i, j) with k < i <= j < n
-      for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int a = e / m, b = e - a * m;
-        if (b < a) continue;
-        const int i = k + 1 + a, j = k + 1 + b;
-        A[i * n + j] -= (A[k * n + i] * y2) * A[k * n + j];
+      for (int i = k + 1 + r0; i < n; i += rstep) {
+        const T aki = A[k * n + i] * y2;
+        for (int j = i + ((c0 - i) & 31); j < n; j += 32) A[i * n + j] -= aki * A[k * n + j];
       }
+    }
+    if (threadIdx.x == 0) {
+      if (!isfinite(d)) set_status(status, kStatusNotSpd);
+      act[k] = ok;
+      y[k] = yk;
     }
     __syncthreads();
   }
@@ -76,6 +74,32 @@ __device__ void chol_inplace(T* A, int n, const T* diag0, int32_t* act, T tol, T
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e - i * n;
     if (j >= i) A[e] *= y[i];
+  }
+  __syncthreads();
+}
+
+// W = R^{-1} (upper triangular, R in A) into a separate buffer W: column j
+// by back substitution, W[j][j] = 1 / R[j][j], W[i][j] = -(sum_{k=i+1..j}
+// R[i][k] W[k][j]) / R[i][i] for i < j; one thread per column (its own
+// column of W only, R read-only), no barriers inside.
+template <typename T>
+__device__ void tri_inverse_cols(const T* __restrict__ A, T* __restrict__ W, int n, const int32_t* act) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const bool aj = act[j] != 0;
+    for (int i = 0; i < n; ++i) W[i * n + j] = T(0);
+    if (!aj) continue;
+    W[j * n + j] = T(1) / A[j * n + j];
+    for (int i = j - 1; i >= 0; --i) {
+      if (!act[i]) continue;
+      T s0 = T(0), s1 = T(0);
+      int k = i + 1;
+      for (; k + 1 <= j; k += 2) {
+        s0 += A[i * n + k] * W[k * n + j];
+        s1 += A[i * n + k + 1] * W[(k + 1) * n + j];
+      }
+      if (k <= j) s0 += A[i * n + k] * W[k * n + j];
+      W[i * n + j] = -(s0 + s1) / A[i * n + i];
+    }
   }
   __syncthreads();
 }
@@ -104,7 +128,7 @@ __device__ void tri_inverse_inplace(T* A, int n, const int32_t* act, T* x) {
   }
 }
 
-template <typename T>
+template <typename T, bool kSmall>
 __global__ void chol_first_kernel(const double* G, int n, double tol, double* R1, double* W, float* Wf,
                                   int32_t* active, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -126,7 +150,14 @@ __global__ void chol_first_kernel(const double* G, int n, double tol, double* R1
   }
   for (int k = threadIdx.x; k < n; k += blockDim.x) active[k] = act[k];
   __syncthreads();
-  tri_inverse_inplace<T>(A, n, act, x);
+  if constexpr (kSmall) {  // a second n x n buffer follows the work arrays
+    T* Wb = reinterpret_cast<T*>(act + n + ((4 - (n & 3)) & 3));
+    tri_inverse_cols<T>(A, Wb, n, act);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = Wb[e];
+    __syncthreads();
+  } else {
+    tri_inverse_inplace<T>(A, n, act, x);
+  }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     // dependent columns pass through the second pass unchanged (identity
@@ -159,7 +190,7 @@ __device__ __forceinline__ double upper_dot(const TA* A, const TB* B, int n, int
   return s0 + s1;
 }
 
-template <typename T>
+template <typename T, bool kSmall>
 __global__ void chol_second_kernel(const double* G2, int n, double tol, const double* R1, const double* Wd,
                                    const int32_t* active, int refine, double* Xg, double* R, double* R_out,
                                    int64_t ldr, int32_t* status) {
@@ -215,11 +246,14 @@ __device__ __forceinline__ T group_sum(T v, int width) {
 
 // Rotation (c, s) that makes columns p and q orthogonal, from their 2 x 2
 // Gram [al ga; ga be]: t = sign(z) / (|z| + sqrt(1 + z^2)), z = (be - al) / (2 ga).
+// (FP32 sweeps: the rotations only steer the iteration, the singular values
+// come from FP64 Rayleigh quotients, so fast approximate intrinsics suffice.)
 __device__ __forceinline__ void rotation(float al, float be, float ga, float& c, float& s) {
   const float z = __fdividef(be - al, 2.f * ga);
   const float az = fabsf(z);
-  const float t = az > 1e18f ? __fdividef(0.5f, z) : copysignf(__frcp_rn(az + __fsqrt_rn(1.f + z * z)), z);
-  c = __frsqrt_rn(1.f + t * t);
+  const float q = 1.f + z * z;
+  const float t = az > 1e18f ? __fdividef(0.5f, z) : copysignf(__fdividef(1.f, az + q * rsqrtf(q)), z);
+  c = rsqrtf(1.f + t * t);
   s = c * t;
 }
 __device__ __forceinline__ void rotation(double al, double be, double ga, double& c, double& s) {
@@ -229,10 +263,11 @@ __device__ __forceinline__ void rotation(double al, double be, double ga, double
   s = c * t;
 }
 
-// One-sided Jacobi.  U (and V) column-major in shared memory; a warp per
-// column pair, NPL elements of each column per lane; the round-robin pairing
-// is tabulated once.  A pair is rotated while |u_p.u_q|^2 > tol^2 |u_p|^2 |u_q|^2.
-template <typename T, bool kWithV, int NPL>
+// One-sided Jacobi.  U (and V) column-major in shared memory; LPP lanes per
+// column pair (32 / LPP pairs per warp), NPL rows of each column per lane;
+// the round-robin pairing is tabulated once.  A pair is rotated while
+// |u_p.u_q|^2 > tol^2 |u_p|^2 |u_q|^2.
+template <typename T, bool kWithV, int NPL, int LPP>
 __global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in, double* sigma,
                               int32_t* status, int32_t* sweeps_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -277,38 +312,42 @@ __global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweep
   __syncthreads();
   const T negligible = (static_cast<T>(n) * eps) * (static_cast<T>(n) * eps) * s_fro;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  constexpr int kPPW = 32 / LPP;  // pairs per warp
+  const int sub = lane % LPP, gw = lane / LPP;
   int sweep = 0;
   bool converged = false;
   for (; sweep < max_sweeps && !converged; ++sweep) {
     int any = 0;
     for (int round = 0; round < rounds; ++round) {
-      for (int g = warp; g < npairs; g += nwarps) {
-        const short2 pq = pairs[round * npairs + g];
+      for (int g0 = warp * kPPW; g0 < npairs; g0 += nwarps * kPPW) {
+        const int g = g0 + gw;
+        const bool live = g < npairs;  // (lanes of a missing pair still join the shuffles)
+        const short2 pq = live ? pairs[round * npairs + g] : make_short2(0, 0);
         T* up = U + static_cast<int64_t>(pq.x) * n;
         T* uq = U + static_cast<int64_t>(pq.y) * n;
         T x[NPL], y[NPL];
         T al = 0, be = 0, ga = 0;
 #pragma unroll
         for (int i = 0; i < NPL; ++i) {
-          const int r = lane + 32 * i;
-          x[i] = r < n ? up[r] : T(0);
-          y[i] = r < n ? uq[r] : T(0);
+          const int r = sub + LPP * i;
+          x[i] = (live && r < n) ? up[r] : T(0);
+          y[i] = (live && r < n) ? uq[r] : T(0);
           al += x[i] * x[i];
           be += y[i] * y[i];
           ga += x[i] * y[i];
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        for (int o = LPP / 2; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o, LPP);
+          be += __shfl_xor_sync(0xffffffffu, be, o, LPP);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o, LPP);
         }
-        if (al > negligible && be > negligible && ga * ga > tol2 * al * be) {
+        if (live && al > negligible && be > negligible && ga * ga > tol2 * al * be) {
           T c, s;
           rotation(al, be, ga, c, s);
 #pragma unroll
           for (int i = 0; i < NPL; ++i) {
-            const int r = lane + 32 * i;
+            const int r = sub + LPP * i;
             if (r < n) {
               up[r] = c * x[i] - s * y[i];
               uq[r] = s * x[i] + c * y[i];
@@ -319,7 +358,7 @@ __global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweep
             T* vq = V + static_cast<int64_t>(pq.y) * n;
 #pragma unroll
             for (int i = 0; i < NPL; ++i) {
-              const int r = lane + 32 * i;
+              const int r = sub + LPP * i;
               if (r < n) {
                 const T xv = vp[r], yv = vq[r];
                 vp[r] = c * xv - s * yv;
@@ -420,12 +459,14 @@ static int dense_threads(int n) {
 template <typename T>
 static cudaError_t chol_first_t(const Plan& p, cudaStream_t s) {
   const int n = p.n;
-  const size_t smem = sizeof(T) * (static_cast<size_t>(n) * n + 3 * n) + sizeof(int32_t) * n + 16;
-  cudaError_t err = cudaFuncSetAttribute(chol_first_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+  // the column-per-thread inverse needs a second n x n buffer (when it fits)
+  const bool small = sizeof(T) * 2 * static_cast<size_t>(n) * n <= 96 * 1024;
+  size_t smem = sizeof(T) * (static_cast<size_t>(n) * n + 3 * n) + sizeof(int32_t) * (n + 4) + 16;
+  if (small) smem += sizeof(T) * static_cast<size_t>(n) * n;
+  auto kern = small ? chol_first_kernel<T, true> : chol_first_kernel<T, false>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  chol_first_kernel<T><<<1, dense_threads(n), smem, s>>>(p.G1, n, default_tol(p), p.R1, p.W, p.Wf, p.active,
-                                                           &p.hdr->status);
+  kern<<<1, dense_threads(n), smem, s>>>(p.G1, n, default_tol(p), p.R1, p.W, p.Wf, p.active, &p.hdr->status);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -439,12 +480,12 @@ static cudaError_t chol_second_t(const Plan& p, double* R_out, int64_t ldr, cuda
   const int n = p.n;
   size_t smem = ((sizeof(T) * (static_cast<size_t>(n) * n + 2 * n) + sizeof(int32_t) * n + 15) & ~size_t(15));
   if (p.mixed) smem += sizeof(double) * static_cast<size_t>(n) * n;
-  cudaError_t err = cudaFuncSetAttribute(chol_second_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+  auto kern = chol_second_kernel<T, false>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
   // G1 is consumed by the first factorisation: its storage holds the refined inverse
-  chol_second_kernel<T><<<1, dense_threads(n), smem, s>>>(p.G2, n, default_tol(p), p.R1, p.W, p.active,
-                                                            p.mixed ? 1 : 0, p.G1, p.R, R_out, ldr, &p.hdr->status);
+  kern<<<1, dense_threads(n), smem, s>>>(p.G2, n, default_tol(p), p.R1, p.W, p.active, p.mixed ? 1 : 0, p.G1, p.R,
+                                         R_out, ldr, &p.hdr->status);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -453,21 +494,21 @@ cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaSt
   return p.mixed ? chol_second_t<float>(p, R_out, ldr, s) : chol_second_t<double>(p, R_out, ldr, s);
 }
 
-template <typename T, bool kWithV, int NPL>
+template <typename T, bool kWithV, int NPL, int LPP = 32>
 static cudaError_t jacobi_t(const Plan& p, const double* R, int64_t ldr, double* sigma, double tol, cudaStream_t s) {
   const int n = p.n;
   const int np = n + (n & 1);
   const int npairs = np / 2;
-  int threads = 32 * npairs;
+  int threads = 32 * ((npairs + 32 / LPP - 1) / (32 / LPP));
   if (threads > 1024) threads = 1024;
   size_t smem = sizeof(T) * static_cast<size_t>(np) * n * (kWithV ? 2 : 1) + sizeof(double) * np;
   if (kWithV && n <= 64) smem += sizeof(double) * static_cast<size_t>(n) * n;
   smem += sizeof(short2) * static_cast<size_t>(np - 1) * npairs;
-  cudaError_t err = cudaFuncSetAttribute(jacobi_kernel<T, kWithV, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+  cudaError_t err = cudaFuncSetAttribute(jacobi_kernel<T, kWithV, NPL, LPP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  jacobi_kernel<T, kWithV, NPL><<<1, threads, smem, s>>>(R, ldr, n, p.max_sweeps, tol, sigma, &p.hdr->status,
-                                                          &p.hdr->jacobi_sweeps);
+  jacobi_kernel<T, kWithV, NPL, LPP><<<1, threads, smem, s>>>(R, ldr, n, p.max_sweeps, tol, sigma, &p.hdr->status,
+                                                               &p.hdr->jacobi_sweeps);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -305,7 +305,7 @@ bool gram_tc_supported(int k, int kout);
 bool gram_tc_packs(int k, int kout, bool pass2);
 cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,
                                  int kout, double* part, int grid_max, int num_sms, int* grid_used, int32_t* status,
-                                 int64_t spin_limit, cudaStream_t s);
+                                 int64_t spin_limit, int withhold, cudaStream_t s);
 
 cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   const int elem = p.mixed ? 4 : 8;
@@ -347,7 +347,7 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     if (tc) {
       const float* Wb = pass == 2 ? p.Wf + static_cast<int64_t>(a.w0) * p.n + a.w0 : nullptr;
       err = launch_gram_tc_block(a.X, a.k, rows, a.rows_dev, Wb, p.n, a.kout, a.part, p.ggrid[b], p.num_sms, &grid,
-                                 &p.hdr->status, p.spin_limit, s);
+                                 &p.hdr->status, p.spin_limit, p.withhold, s);
     } else {
       err = p.mixed ? launch_gram_block<float>(a, tpt, grid, s) : launch_gram_block<double>(a, tpt, grid, s);
     }

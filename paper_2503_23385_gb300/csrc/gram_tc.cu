@@ -919,6 +919,7 @@ struct PackArgs {
   double* part;    // [grid][kout][kout]
   int32_t* status;
   int64_t spin_limit;
+  int withhold;    // test-only: the producer never loads its first tile
 };
 
 // Byte offset of column col (0..127) of packed row w in a Z panel set whose
@@ -1008,6 +1009,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         if (i >= kPackStages &&
             !pipe_wait(S, &S.stage_empty[s], static_cast<uint32_t>(((i / kPackStages) - 1) & 1), a.spin_limit, a.status))
           break;
+        if (a.withhold && i == 0) continue;  // the workers' bounded wait for this tile runs out
         unsigned char* dst = base + s * stage_bytes;
         const int y = static_cast<int>(tile_index(i) * kTileRows);
         if (pass2) {
@@ -1021,7 +1023,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         issued = i + 1;
       }
       for (int i = issued > kPackStages ? issued - kPackStages : 0; i < issued; ++i)
-        drain_wait(&S.tma_full[i % kPackStages], static_cast<uint32_t>((i / kPackStages) & 1), a.spin_limit, a.status);
+        if (!(a.withhold && i == 0))
+          drain_wait(&S.tma_full[i % kPackStages], static_cast<uint32_t>((i / kPackStages) & 1), a.spin_limit,
+                     a.status);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issue
@@ -1313,7 +1317,7 @@ bool gram_tc_supported(int k, int kout) { return k % 4 == 0 && k <= 64 && kout <
 
 cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,
                                  int kout, double* part, int grid_max, int num_sms, int* grid_used, int32_t* status,
-                                 int64_t spin_limit, cudaStream_t s) {
+                                 int64_t spin_limit, int withhold, cudaStream_t s) {
   const int kk = W ? kout : k;
   if (gram_tc_packs(k, kout, W != nullptr)) {  // packed-operand engine: persistent CTAs, one per SM
     const int rr = 64 / kk;
@@ -1337,6 +1341,7 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
     a.part = part;
     a.status = status;
     a.spin_limit = spin_limit;
+    a.withhold = withhold;
     CUtensorMap map;
     cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kTileRows)};
     cuuint32_t es[2] = {1, 1};

@@ -7,29 +7,31 @@
 // with equal keys in input order, which fixes the order of the QR tail rows
 // inside each key group.
 //
-// Launches (each covers both tables; blocks [0, tiles_A) work on A):
-//   1. key_hist:  one read of the keys: global histograms of all four 8-bit
-//                 digits of the order-preserving uint32 key, and the key range.
-//                 Digits above the highest bit in which min and max differ are
-//                 equal for every key, so only ceil(bits / 8) passes run.
-//   2. sort_pass x4 (passes beyond the needed count return at once): one
-//                 kernel per digit, "one sweep": each 4,096-key tile ranks its
-//                 keys stably in shared memory, publishes its 256 digit counts,
-//                 and finds the counts of all earlier tiles by a decoupled
-//                 look-back (bounded waits).  The last pass writes the final
-//                 perm / sorted keys.
-//   3. runs:      run starts, their count by decoupled look-back, and the run
-//                 index of every sorted row, run keys and run offsets.
-//   4. match:     per run, the size of the run with the same key in the other
-//                 table and the head slot of the key group.
+// Launches (each covers both tables; blocks [0, tiles_A) work on A; a tile
+// is 8,192 keys):
+//   1. key_hist:   the key range and each tile's counts of the first 8-bit
+//                  digit of the order-preserving uint32 key.  Digits above the
+//                  highest bit in which min and max differ are equal for every
+//                  key, so only ceil(bits / 8) passes run; the kernels of the
+//                  other passes return at once.
+//   2. per pass, reduce-then-scan (no waiting between tiles):
+//        tile_count  the tile's digit counts (passes after the first),
+//        tile_scan   per digit, the exclusive scan over tiles plus the keys of
+//                    smaller digits: each tile's output offset per digit,
+//        sort_pass   stable ranking in shared memory (warp multi-split by
+//                    ballots), keys staged in digit order, coalesced scatter.
+//      The last pass writes the final perm / sorted keys.
+//   3. run_count, runs: run starts per tile, then each tile's run index from
+//                  the sum of the earlier tiles' counts; run keys, offsets,
+//                  the run index of every sorted row, and a key lookup table.
+//   4. match:      per run, the size of the run with the same key in the other
+//                  table (lookup table, binary search outside its range) and
+//                  the head slot of the key group.
 #include "common.cuh"
 #include "internal.h"
 
 namespace figaro {
 namespace {
-
-constexpr uint64_t kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62;
-constexpr uint64_t kCountMask = (1ull << 62) - 1;
 
 struct TwoTables {
   TableWork t[2];
@@ -37,12 +39,8 @@ struct TwoTables {
   int nb0;  // tiles of table 0
   int nb;   // tiles of both tables
   int64_t spin_limit;
-  int withhold;  // test-only: tile 0 of table A never publishes its run count
+  int64_t lut_size;  // entries of each table's key lookup table
 };
-
-__device__ __forceinline__ void st_release64(uint64_t* p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 
 __device__ __forceinline__ int table_of(const TwoTables& a, int g, int& tile) {
   if (g < a.nb0) {
@@ -60,12 +58,6 @@ __device__ __forceinline__ int num_passes(const DevHeader* h, int t) {
   return p < 1 ? 1 : p;
 }
 
-__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // Per-tile digit counts and output offsets of a pass (reduce-then-scan),
 // kept in the table's sort word area: [pass][counts | offsets][tile][digit].
 __device__ __forceinline__ uint32_t* tile_counts(const TableWork& T, int pass) {
@@ -75,53 +67,15 @@ __device__ __forceinline__ uint32_t* tile_offsets(const TableWork& T, int pass) 
   return tile_counts(T, pass) + static_cast<int64_t>(T.tiles) * kRadixBins;
 }
 
-// Decoupled look-back over the words of tiles tile-1, tile-2, ... (each word
-// holds a flag and a count, written at once): the sum of the counts back to
-// and including the first inclusive word.  Eight predecessors are read at a
-// time (independent relaxed loads; the count travels with its flag, so no
-// ordering beyond the word itself is needed).  Returns false if a word stayed
-// unpublished for spin_limit polls.
-__device__ __forceinline__ bool lookback(const uint64_t* words, int64_t stride, int tile, int64_t limit,
-                                         uint64_t& excl) {
-  excl = 0;
-  int j = tile - 1;
-  while (j >= 0) {
-    uint64_t w[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) w[u] = j - u >= 0 ? ld_relaxed64(words + static_cast<int64_t>(j - u) * stride) : 0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (j - u < 0) return true;
-      uint64_t v = w[u];
-      int64_t spins = 0;
-      while ((v >> 62) == 0) {
-        if (++spins > limit) return false;
-        __nanosleep(32);
-        v = ld_relaxed64(words + static_cast<int64_t>(j - u) * stride);
-      }
-      excl += v & kCountMask;
-      if (v & kFlagInc) return true;
-    }
-    j -= 8;
-  }
-  return true;
-}
-
-__global__ void reset_kernel(DevHeader* h, uint64_t* g0, int64_t ng0, uint64_t* g1, int64_t ng1) {
-  int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid == 0) {
-    h->status = 0;
-    for (int i = 0; i < 8; ++i) h->ticket[i] = 0;
-    h->kmin[0] = h->kmin[1] = 0xffffffffu;
-    h->kmax[0] = h->kmax[1] = 0u;
-    h->num_runs[0] = h->num_runs[1] = 0;
-    h->num_groups = 0;
-    h->reduced_rows = 0;
-    h->jacobi_sweeps = 0;
-  }
-  const int stride = gridDim.x * blockDim.x;
-  for (int64_t i = tid; i < ng0; i += stride) g0[i] = 0ull;
-  for (int64_t i = tid; i < ng1; i += stride) g1[i] = 0ull;
+__global__ void reset_kernel(DevHeader* h) {
+  h->status = 0;
+  for (int i = 0; i < 8; ++i) h->ticket[i] = 0;
+  h->kmin[0] = h->kmin[1] = 0xffffffffu;
+  h->kmax[0] = h->kmax[1] = 0u;
+  h->num_runs[0] = h->num_runs[1] = 0;
+  h->num_groups = 0;
+  h->reduced_rows = 0;
+  h->jacobi_sweeps = 0;
 }
 
 // The key range, the first pass's digit counts per tile and their global
@@ -364,21 +318,59 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(TwoTables a,
   }
 }
 
-// Runs of the sorted keys.  Thread-contiguous rows are staged through shared
-// memory so that global accesses stay coalesced; the run count before each
-// tile comes from a decoupled look-back.
+// Run starts per tile of the sorted keys (a row starts a run when its key
+// differs from the row before it).
+__global__ void __launch_bounds__(kSortThreads) run_count_kernel(TwoTables a) {
+  int tile;
+  const int t = table_of(a, blockIdx.x, tile);
+  const TableWork& T = a.t[t];
+  const int64_t base = static_cast<int64_t>(tile) * kSortTile;
+  uint32_t c = 0;
+  for (int it = 0; it < kSortItems; ++it) {
+    const int64_t i = base + it * kSortThreads + threadIdx.x;
+    if (i < T.m && (i == 0 || T.sorted_key[i] != T.sorted_key[i - 1])) ++c;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ uint32_t s_w[kSortThreads / 32];
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < kSortThreads / 32; ++w) tot += s_w[w];
+    reinterpret_cast<uint32_t*>(T.run_status)[tile] = tot;
+  }
+}
+
+// Runs of the sorted keys: run keys, run offsets, the run index of every
+// sorted row, and each run start's slot in the key lookup table.  The number
+// of runs before the tile is the sum of the earlier tiles' counts (a block
+// reduction, no waiting).  Rows are staged through shared memory so that
+// global accesses stay coalesced.
 __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
   __shared__ int32_t sk[kSortTile + 1];
   __shared__ uint32_t s_w[kSortThreads / 32];
   __shared__ uint64_t s_excl;
-  __shared__ int s_g;
-  if (threadIdx.x == 0) s_g = static_cast<int>(atomicAdd(&a.h->ticket[3], 1u));
-  __syncthreads();
   int tile;
-  const int t = table_of(a, s_g, tile);
+  const int t = table_of(a, blockIdx.x, tile);
   const TableWork& T = a.t[t];
   const int64_t base = static_cast<int64_t>(tile) * kSortTile;
   const int64_t m = T.m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // runs in the earlier tiles
+  {
+    const uint32_t* counts = reinterpret_cast<const uint32_t*>(T.run_status);
+    uint64_t e = 0;
+    for (int j = threadIdx.x; j < tile; j += kSortThreads) e += counts[j];
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    __shared__ uint64_t s_e[kSortThreads / 32];
+    if (lane == 0) s_e[warp] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t tot = 0;
+      for (int w = 0; w < kSortThreads / 32; ++w) tot += s_e[w];
+      s_excl = tot;
+    }
+  }
   for (int e = threadIdx.x; e < kSortTile + 1; e += blockDim.x) {
     const int64_t i = base - 1 + e;
     sk[e] = (i >= 0 && i < m) ? T.sorted_key[i] : 0;
@@ -395,7 +387,6 @@ __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
       ++c;
     }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t incl = c;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -403,24 +394,9 @@ __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
   }
   if (lane == 31) s_w[warp] = incl;
   __syncthreads();
-  uint32_t wpre = 0, tile_total = 0;
-  for (int w = 0; w < kSortThreads / 32; ++w) {
-    if (w < warp) wpre += s_w[w];
-    tile_total += s_w[w];
-  }
-  if (threadIdx.x == 0) {
-    uint64_t* mine = T.run_status + tile;
-    uint64_t excl = 0;
-    if (tile == 0) {
-      if (!(a.withhold && t == 0)) st_release64(mine, kFlagInc | tile_total);
-    } else {
-      st_release64(mine, kFlagAgg | tile_total);
-      if (!lookback(T.run_status, 1, tile, a.spin_limit, excl)) set_status(&a.h->status, kStatusTimeout);
-      st_release64(mine, kFlagInc | (excl + tile_total));
-    }
-    s_excl = excl;
-  }
-  __syncthreads();
+  uint32_t wpre = 0;
+  for (int w = 0; w < warp; ++w) wpre += s_w[w];
+  const uint32_t kbase = min(a.h->kmin[0], a.h->kmin[1]);
   int64_t run = static_cast<int64_t>(s_excl) + wpre + incl - c - 1;  // run of the row before my first
   int32_t segs[kSortItems];
 #pragma unroll
@@ -428,8 +404,11 @@ __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
     const int64_t i = base + r0 + it;
     if (flags & (1u << it)) {
       ++run;
-      T.run_key[run] = sk[r0 + it + 1];
+      const int32_t k = sk[r0 + it + 1];
+      T.run_key[run] = k;
       T.run_off[run] = static_cast<int32_t>(i);
+      const uint32_t off = key_to_ordered(k) - kbase;
+      if (off < static_cast<uint32_t>(a.lut_size)) T.lut[off] = static_cast<int32_t>(run);
     }
     segs[it] = static_cast<int32_t>(run);
     if (i == m - 1) {
@@ -463,34 +442,54 @@ __device__ __forceinline__ int64_t lower_bound_key(const int32_t* keys, int64_t 
 // the other table (0 if none) and the head slot of the key group (the run
 // index on A's side), also packed with the run's row range into one 16-byte
 // record for the head/tail step.
+// The run of key k in table O: the lookup table when k is inside its range
+// (an entry is trusted only if it names a run with that key: no entry needs
+// initialising), else a binary search of O's run keys.
+__device__ __forceinline__ int64_t find_run(const TwoTables& a, const TableWork& O, int64_t UO, int32_t k) {
+  const uint32_t off = key_to_ordered(k) - min(a.h->kmin[0], a.h->kmin[1]);
+  if (off < static_cast<uint32_t>(a.lut_size)) {
+    const int64_t j = O.lut[off];
+    return (j >= 0 && j < UO && O.run_key[j] == k) ? j : -1;
+  }
+  const int64_t j = lower_bound_key(O.run_key, UO, k);
+  return (j < UO && O.run_key[j] == k) ? j : -1;
+}
+
 __global__ void match_kernel(TwoTables a) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   DevHeader* h = a.h;
   const TableWork& A = a.t[0];
   const TableWork& B = a.t[1];
   const int64_t UA = h->num_runs[0], UB = h->num_runs[1];
+  unsigned long long groups = 0, reduced = 0;
   if (i < UA) {
     const int32_t k = A.run_key[i];
-    const int64_t j = lower_bound_key(B.run_key, UB, k);
+    const int64_t j = find_run(a, B, UB, k);
     const int32_t mine = A.run_off[i + 1] - A.run_off[i];
     A.hdslot[i] = static_cast<int32_t>(i);
     int32_t other = 0;
-    if (j < UB && B.run_key[j] == k) {
+    if (j >= 0) {
       other = B.run_off[j + 1] - B.run_off[j];
-      A.other[i] = other;
-      atomicAdd(reinterpret_cast<unsigned long long*>(&h->num_groups), 1ull);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&h->reduced_rows),
-                static_cast<unsigned long long>(mine + other - 1));
-    } else {
-      A.other[i] = 0;
+      groups = 1;
+      reduced = static_cast<unsigned long long>(mine + other - 1);
     }
+    A.other[i] = other;
     reinterpret_cast<int4*>(A.run_info)[i] = make_int4(A.run_off[i], A.run_off[i + 1], other, static_cast<int32_t>(i));
+  }
+  // one atomic per warp for the counts of key groups and reduced rows
+  for (int o = 16; o > 0; o >>= 1) {
+    groups += __shfl_xor_sync(0xffffffffu, groups, o);
+    reduced += __shfl_xor_sync(0xffffffffu, reduced, o);
+  }
+  if ((threadIdx.x & 31) == 0 && groups) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&h->num_groups), groups);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&h->reduced_rows), reduced);
   }
   if (i < UB) {
     const int32_t k = B.run_key[i];
-    const int64_t j = lower_bound_key(A.run_key, UA, k);
+    const int64_t j = find_run(a, A, UA, k);
     int32_t other = 0, slot = -1;
-    if (j < UA && A.run_key[j] == k) {
+    if (j >= 0) {
       other = A.run_off[j + 1] - A.run_off[j];
       slot = static_cast<int32_t>(j);
     }
@@ -502,21 +501,16 @@ __global__ void match_kernel(TwoTables a) {
 
 }  // namespace
 
-// Look-back words of the grouping step per table: kMaxPasses x tiles x bins
-// for the sort, tiles for the runs, and the kMaxPasses x bins histogram.
+// Words of the grouping step per table: per-tile digit counts and offsets of
+// every pass (kMaxPasses x tiles x bins 64-bit words), and per-tile run counts.
 int64_t group_status_words(int tiles) {
   return static_cast<int64_t>(kMaxPasses) * tiles * kRadixBins + tiles;
 }
 
 cudaError_t launch_reset(const Plan& p, cudaStream_t s) {
-  // only the run-count look-back words need to start at zero (the sort's
-  // per-tile counts and offsets are rewritten by every call)
-  const int64_t g0 = p.t[0].tiles, g1 = p.t[1].tiles;
-  const int64_t work = g0 > g1 ? g0 : g1;
-  int blocks = static_cast<int>((work + 255) / 256);
-  if (blocks < 1) blocks = 1;
-  if (blocks > 1024) blocks = 1024;
-  reset_kernel<<<blocks, 256, 0, s>>>(p.hdr, p.t[0].run_status, g0, p.t[1].run_status, g1);
+  // the header; the sort's per-tile counts and offsets and the run counts are
+  // rewritten by every call
+  reset_kernel<<<1, 1, 0, s>>>(p.hdr);
   count_launches(1);
   // the histograms are accumulated with atomics: clear them too
   for (int t = 0; t < 2; ++t)
@@ -535,7 +529,7 @@ cudaError_t launch_grouping(const Plan& p, cudaStream_t s) {
   a.nb0 = p.t[0].tiles;
   a.nb = p.t[0].tiles + p.t[1].tiles;
   a.spin_limit = p.spin_limit;
-  a.withhold = p.withhold;
+  a.lut_size = p.lut_size;
   if (a.nb == 0) return cudaSuccess;
   static int granted[64] = {0};
   int dev = 0;
@@ -553,11 +547,12 @@ cudaError_t launch_grouping(const Plan& p, cudaStream_t s) {
     tile_scan_kernel<<<2 * kRadixBins, kRadixBins, 0, s>>>(a, pass);
     sort_pass_kernel<<<a.nb, kSortThreads, kSortSmem, s>>>(a, pass);
   }
+  run_count_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
   runs_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
   const int64_t mm = p.t[0].m > p.t[1].m ? p.t[0].m : p.t[1].m;
   const int mb = static_cast<int>((mm + 255) / 256);
   if (mb > 0) match_kernel<<<mb, 256, 0, s>>>(a);
-  count_launches(2 + 3 * kMaxPasses - 1 + (mb > 0 ? 1 : 0));
+  count_launches(3 + 3 * kMaxPasses - 1 + (mb > 0 ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -47,8 +47,8 @@ struct TableWork {
   uint32_t* kb[2] = {nullptr, nullptr};
   int32_t* vb[2] = {nullptr, nullptr};
   uint32_t* hist = nullptr;          // kMaxPasses x kRadixBins global digit counts
-  uint64_t* sort_status = nullptr;   // look-back words: kMaxPasses x tiles x kRadixBins
-  uint64_t* run_status = nullptr;    // look-back words: tiles
+  uint64_t* sort_status = nullptr;   // per-tile digit counts and offsets: kMaxPasses x tiles x kRadixBins words
+  uint64_t* run_status = nullptr;    // per-tile run counts: tiles words
   int tiles = 0;
   int32_t* perm = nullptr;
   int32_t* sorted_key = nullptr;
@@ -58,6 +58,7 @@ struct TableWork {
   int32_t* other = nullptr;     // partner run size (0 = unmatched)
   int32_t* hdslot = nullptr;    // head row of the run's key group
   int32_t* run_info = nullptr;  // per run: {first row, end row, partner run size, head slot}
+  int32_t* lut = nullptr;       // key lookup table: run index at (ordered key - smallest key of both tables)
   // head/tail
   void* tail = nullptr;         // m x n slots, compute type
   int chunk_rows = 0;           // chunk spacing L of the head/tail step
@@ -78,6 +79,7 @@ struct Plan {
   int64_t spin_limit = 0;
   double rank_tol = 0.0;
   int withhold = 0;             // test-only fault injection (see FIGARO_FLAG_TEST_WITHHOLD)
+  int64_t lut_size = 0;         // entries of each table's key lookup table
   DevHeader* hdr = nullptr;
   void* head = nullptr;         // m1 x n slots, compute type
   // Gram partials: [grid x slices x k x k] doubles per block
