@@ -36,6 +36,8 @@ WORKLOADS = {
     "c1": "1e6+1e6 rows x 16+16 FP32 N(0,1), int32 keys uniform over 1e4 ids (join ~1e8 x 32)",
     "c2": "4e6+2e6 rows x 32+32 FP32 U[-1,1], Zipf(1.2) keys over 1e5 ids",
     "c0": "1000+1000 rows x 4+4 FP64 U[-1,1], 100 keys",
+    "c4": "2e5+2e5 rows x 256+256 FP32, B column-scaled to condition 1e8, int32 keys uniform over 100 ids "
+          "(join ~4e8 x 512)",
 }
 
 

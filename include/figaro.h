@@ -31,8 +31,12 @@
  *    returned at once.  Errors found on the device (numerical breakdown, a
  *    bounded wait that ran out) are recorded in the workspace; read them with
  *    figaro_get_status() after the stream has reached that point.
- *  - Limits: m1, m2 < 2^31; 1 <= n1, n2 and n1 + n2 <= 128 (larger widths
- *    return FIGARO_ERR_UNSUPPORTED); both tables have the same dtype.
+ *  - Limits: m1, m2 < 2^31; 1 <= n1, n2 and n1 + n2 <= 512, and each table
+ *    at most 256 columns when n1 + n2 > 128 (other widths return
+ *    FIGARO_ERR_UNSUPPORTED); both tables have the same dtype.  Up to 128
+ *    columns the n x n steps run in one CTA each; wider joins take the
+ *    multi-CTA path (Q = X W written to the workspace, cooperative launches
+ *    for the Cholesky factorisations and the Jacobi SVD).
  *  - Workspace must be 256-byte aligned.  Concurrent calls need distinct
  *    workspaces.
  */

@@ -107,6 +107,7 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
   }
   const int n = p.n;
   p.head = b.take<char>(static_cast<size_t>(m1 > 0 ? m1 : 1) * n * ec);
+  p.wide = n > kMaxWidth ? 1 : 0;
   // Gram partials, sized for the larger of the two passes
   for (int blk = 0; blk < 3; ++blk) {
     const int64_t rows = blk == 0 ? m1 : (blk == 1 ? m1 : m2);
@@ -121,7 +122,25 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
       if (sz > most) most = sz;
     }
     p.gslices[blk] = 0;
-    p.gpart[blk] = b.take<double>(most);
+    p.gpart[blk] = b.take<double>(p.wide ? 1 : most);
+  }
+  if (p.wide) {
+    const size_t qrows[3] = {static_cast<size_t>(m1), static_cast<size_t>(m1), static_cast<size_t>(m2)};
+    const size_t qcols[3] = {static_cast<size_t>(n), static_cast<size_t>(n), static_cast<size_t>(n2)};
+    for (int blk = 0; blk < 3; ++blk) p.wq[blk] = b.take<char>(qrows[blk] * qcols[blk] * ec);
+    int64_t jobs = wide_gram_jobs(1, m1, n1, m2, n2, num_sms);
+    const int64_t j2 = wide_gram_jobs(2, m1, n1, m2, n2, num_sms);
+    if (j2 > jobs) jobs = j2;
+    p.wpart = b.take<double>(static_cast<size_t>(jobs) * 64 * 64);
+    const size_t nn = static_cast<size_t>(n) * n;
+    p.Aw = b.take<char>(nn * ec);
+    p.Tw = b.take<char>(nn * ec);
+    p.Xw = b.take<double>(nn);
+    p.Uw = b.take<char>(static_cast<size_t>(n + 32) * n * ec);
+    p.Vw = b.take<char>(static_cast<size_t>(n + 32) * n * ec);
+    p.yw = b.take<char>(static_cast<size_t>(n) * ec);
+    p.d0w = b.take<char>(static_cast<size_t>(n) * ec);
+    p.sigw = b.take<double>(2 * static_cast<size_t>(n));  // Rayleigh quotients, column norms
   }
   const size_t nn = static_cast<size_t>(n) * n;
   p.G1 = b.take<double>(nn);
@@ -174,7 +193,9 @@ figaro_status check_pair(const figaro_table* A, const figaro_table* B, const fig
   if (o && (o->gram_engine < 0 || o->gram_engine > 2)) return FIGARO_ERR_INVALID_ARG;
   if (o && (o->max_jacobi_sweeps < 0 || o->spin_limit < 0 || !(o->rank_tol >= 0.0) || o->rank_tol >= 1.0))
     return FIGARO_ERR_INVALID_ARG;
-  if (static_cast<int64_t>(A->n) + B->n > kMaxWidth) return FIGARO_ERR_UNSUPPORTED;
+  const int64_t n = static_cast<int64_t>(A->n) + B->n;
+  if (n > kMaxWideWidth || (n > kMaxWidth && (A->n > kMaxTableWidth || B->n > kMaxTableWidth)))
+    return FIGARO_ERR_UNSUPPORTED;
   return FIGARO_OK;
 }
 

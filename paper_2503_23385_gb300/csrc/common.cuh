@@ -37,6 +37,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// 1/sqrt(d) for d > 0: FP32 estimate refined by Newton's iteration
+// y <- y (3 - d y^2) / 2 (quadratic convergence; two steps from ~2^-23).
+__device__ __forceinline__ double rsqrt_pivot(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = static_cast<double>(rsqrtf(static_cast<float>(d)));
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+__device__ __forceinline__ float rsqrt_pivot(float d) { return __frsqrt_rn(d); }
+
 // Compensated accumulator: float-float pair for FP32, plain sum for FP64.
 template <typename T>
 struct Acc;

@@ -30,16 +30,6 @@
 namespace figaro {
 namespace {
 
-// 1/sqrt(d) for d > 0: FP32 estimate refined by Newton's iteration
-// y <- y (3 - d y^2) / 2 (quadratic convergence; two steps from ~2^-23).
-__device__ __forceinline__ double rsqrt_pivot(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-  double y = static_cast<double>(rsqrtf(static_cast<float>(d)));
-  y = y * (1.5 - 0.5 * d * y * y);
-  y = y * (1.5 - 0.5 * d * y * y);
-  return y;
-}
-__device__ __forceinline__ float rsqrt_pivot(float d) { return __frsqrt_rn(d); }
 
 // In-place semi-definite Cholesky of the n x n matrix A (shared memory,
 // row-major, upper triangle used).  act[k]: columns marked 0 on entry stay
@@ -472,6 +462,7 @@ static cudaError_t chol_first_t(const Plan& p, cudaStream_t s) {
 }
 
 cudaError_t launch_chol_first(const Plan& p, cudaStream_t s) {
+  if (p.wide) return launch_wide_chol_first(p, s);
   return p.mixed ? chol_first_t<float>(p, s) : chol_first_t<double>(p, s);
 }
 
@@ -491,6 +482,7 @@ static cudaError_t chol_second_t(const Plan& p, double* R_out, int64_t ldr, cuda
 }
 
 cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s) {
+  if (p.wide) return launch_wide_chol_second(p, R_out, ldr, s);
   return p.mixed ? chol_second_t<float>(p, R_out, ldr, s) : chol_second_t<double>(p, R_out, ldr, s);
 }
 
@@ -514,6 +506,7 @@ static cudaError_t jacobi_t(const Plan& p, const double* R, int64_t ldr, double*
 }
 
 cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s) {
+  if (p.wide) return launch_wide_jacobi(p, R, ldr, sigma, s);
   const int n = p.n;
   if (p.mixed) {
     // FP32 sweeps stop at |u_p . u_q| <= 1e-5 ||u_p|| ||u_q||: the FP64

@@ -308,6 +308,7 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
                                  int64_t spin_limit, int withhold, cudaStream_t s);
 
 cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
+  if (p.wide) return launch_wide_gram_pass(p, pass, s);
   const int elem = p.mixed ? 4 : 8;
   // block 0 = head rows, 1 = A tails, 2 = B tails
   ReduceArgs r{};

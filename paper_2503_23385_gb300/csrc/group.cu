@@ -76,6 +76,9 @@ __global__ void reset_kernel(DevHeader* h) {
   h->num_groups = 0;
   h->reduced_rows = 0;
   h->jacobi_sweeps = 0;
+  h->bar_count = 0u;
+  h->bar_gen = 0u;
+  h->sweep_any[0] = h->sweep_any[1] = h->sweep_any[2] = 0u;
 }
 
 // The key range, the first pass's digit counts per tile and their global

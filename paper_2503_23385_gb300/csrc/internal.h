@@ -10,7 +10,9 @@
 
 namespace figaro {
 
-constexpr int kMaxWidth = 128;          // n1 + n2 limit of the dense n x n kernels
+constexpr int kMaxWidth = 128;          // n1 + n2 limit of the one-CTA dense n x n kernels
+constexpr int kMaxWideWidth = 512;      // n1 + n2 limit of the wide (multi-CTA) path
+constexpr int kMaxTableWidth = 256;     // per-table width limit of the wide path
 constexpr int kSortThreads = 512;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per radix tile
@@ -32,6 +34,10 @@ struct alignas(256) DevHeader {
   int64_t reduced_rows;      // sum over matched keys of (m1g + m2g - 1)
   int32_t jacobi_sweeps;
   int32_t pad1;
+  uint32_t bar_count;        // grid barrier of the cooperative dense kernels (wide path)
+  uint32_t bar_gen;
+  uint32_t sweep_any[3];     // per-sweep "a pair was rotated" flags of the wide Jacobi
+  uint32_t pad2;
 };
 
 // Per-table buffers of the grouping and head/tail steps.
@@ -96,6 +102,19 @@ struct Plan {
   double* sigma = nullptr;
   int32_t* active = nullptr;
   int num_sms = 148;
+  // wide path (n1 + n2 > kMaxWidth): Q = X W per Gram block, 64 x 64 tile
+  // partials, and n x n work arrays of the multi-CTA dense steps
+  int wide = 0;
+  void* wq[3] = {nullptr, nullptr, nullptr};  // head (m1 x n), A tails (m1 x n), B tails (m2 x n2)
+  double* wpart = nullptr;                    // wide Gram partials, 64 x 64 doubles per job
+  void* Aw = nullptr;                         // n x n compute type (in-place Cholesky)
+  void* Tw = nullptr;                         // n x n compute type (inverse)
+  double* Xw = nullptr;                       // n x n FP64 (refined R1)
+  void* Uw = nullptr;                         // Jacobi columns: (n + 32) x n compute type
+  void* Vw = nullptr;
+  void* yw = nullptr;                         // n pivots 1 / sqrt(d)
+  void* d0w = nullptr;                        // n diagonal of the factored Gram
+  double* sigw = nullptr;                     // 2n: unsorted singular values, FP32-sweep column norms
 };
 
 // cuTensorMapEncodeTiled from the driver (null when unavailable).
@@ -121,5 +140,12 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s);
 cudaError_t launch_chol_first(const Plan& p, cudaStream_t s);
 cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);
 cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
+
+// Wide path (wide.cu).
+int64_t wide_gram_jobs(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms);
+cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s);
+cudaError_t launch_wide_chol_first(const Plan& p, cudaStream_t s);
+cudaError_t launch_wide_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);
+cudaError_t launch_wide_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
 
 }  // namespace figaro

@@ -61,8 +61,12 @@ def test_workspace_size_and_argument_checks_on_host(lib_path):
     A.x, A.key = 16, 16  # non-null placeholders: the size query never dereferences them
     assert lib.figaro_workspace_size(ctypes.byref(A), ctypes.byref(B), None, ctypes.byref(sz)) == 0
     assert sz.value > 1000 * 16 * 4
-    wide = fg.Table(16, 16, 10, 100, 100, fg.F32, fg.MEM_DEVICE, 0)
-    assert lib.figaro_workspace_size(ctypes.byref(wide), ctypes.byref(wide), None, ctypes.byref(sz)) == 7
+    # widths: n1 + n2 <= 512 with each table at most 256 columns once n1 + n2 > 128
+    for (na, nb), code in (((100, 100), 0), ((256, 256), 0), ((300, 10), 7), ((257, 200), 7), ((300, 300), 7),
+                           ((64, 64), 0), ((120, 8), 0)):
+        ta = fg.Table(16, 16, 10, na, na, fg.F32, fg.MEM_DEVICE, 0)
+        tb = fg.Table(16, 16, 10, nb, nb, fg.F32, fg.MEM_DEVICE, 0)
+        assert lib.figaro_workspace_size(ctypes.byref(ta), ctypes.byref(tb), None, ctypes.byref(sz)) == code, (na, nb)
     bad = fg.Table(16, 16, 10, 3, 4, fg.F32, fg.MEM_DEVICE, 0)  # ld < n
     assert lib.figaro_workspace_size(ctypes.byref(bad), ctypes.byref(A), None, ctypes.byref(sz)) == 1
     mixed = fg.Table(16, 16, 10, 4, 4, fg.F64, fg.MEM_DEVICE, 0)  # dtype mismatch with A

@@ -280,7 +280,7 @@ def test_status_codes(fg, torch):
         fg.join_qr_svd((ta[0], ta[1]), (tb[0].double(), tb[1]))
     assert e.value.status == 1
     with pytest.raises(fg.FigaroError) as e:
-        big = torch.zeros((10, 100), device="cuda")
+        big = torch.zeros((10, 300), device="cuda")  # 300 + 300 columns: above the 512-column limit
         fg.join_qr_svd((big, torch.zeros(10, dtype=torch.int32, device="cuda")),
                        (big, torch.zeros(10, dtype=torch.int32, device="cuda")))
     assert e.value.status == 7
