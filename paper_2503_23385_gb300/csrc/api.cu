@@ -2,9 +2,11 @@
 // and the stream-ordered pipeline of one instance:
 //   key grouping -> head/tail of A and B -> Gram pass 1 -> Cholesky 1 ->
 //   Gram pass 2 -> Cholesky 2 and R = R2 R1 -> one-sided Jacobi.
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/figaro.h"
 #include "common.cuh"
@@ -350,6 +352,171 @@ figaro_status bind_input_device(const figaro_table* A, const figaro_table* B) {
   return FIGARO_OK;
 }
 
+
+// ------------------------------------------------------------- batching ----
+//
+// figaro_batch_join runs every narrow, device-resident instance of a batch
+// with one launch per phase: the per-instance plans and, per launch, a job
+// list (job -> instance, CTAs) are built on the host, written into the front
+// of the workspace by copy kernels whose arguments carry the bytes (so the
+// whole call can be captured in a CUDA graph), and each batched kernel maps
+// its CTA to (instance, CTA within the job).
+
+constexpr int kUploadBytes = 30 * 1024;  // kernel arguments of up to 32,764 bytes
+
+struct UploadChunk {
+  unsigned char* dst;
+  int bytes;
+  int pad[1];
+  alignas(16) unsigned char data[kUploadBytes];
+};
+
+__global__ void upload_kernel(const __grid_constant__ UploadChunk c) {
+  for (int i = threadIdx.x; i < c.bytes; i += blockDim.x) c.dst[i] = c.data[i];
+}
+
+// Bytes of the batch area (plans, outputs, job lists) for `count` instances.
+size_t batch_area_bytes(int count) {
+  const size_t lists = 24, per_list = (3 * static_cast<size_t>(count) + 1) * 3 * sizeof(int32_t) + 256;
+  return ((sizeof(Plan) + sizeof(BatchOut)) * static_cast<size_t>(count) + lists * per_list + 4096 + 255) &
+         ~static_cast<size_t>(255);
+}
+
+struct JobList {
+  std::vector<int32_t> first{0}, inst, aux;
+  void add(int i, int a, int ctas) {
+    if (ctas <= 0) return;
+    inst.push_back(i);
+    aux.push_back(a);
+    first.push_back(first.back() + ctas);
+  }
+  int njobs() const { return static_cast<int>(inst.size()); }
+};
+
+struct Blob {
+  std::vector<unsigned char> bytes;
+  size_t put(const void* src, size_t n) {
+    size_t off = (bytes.size() + 15) & ~static_cast<size_t>(15);
+    bytes.resize(off + n);
+    if (n) std::memcpy(bytes.data() + off, src, n);
+    return off;
+  }
+};
+
+BatchJobs stage_jobs(Blob& blob, const JobList& L, std::vector<std::pair<BatchJobs*, size_t[3]>>& fix, BatchJobs* dst) {
+  BatchJobs J{};
+  J.njobs = L.njobs();
+  J.ctas = L.first.back();
+  fix.emplace_back();
+  fix.back().first = dst;
+  fix.back().second[0] = blob.put(L.first.data(), L.first.size() * sizeof(int32_t));
+  fix.back().second[1] = blob.put(L.inst.data(), L.inst.size() * sizeof(int32_t));
+  fix.back().second[2] = blob.put(L.aux.data(), L.aux.size() * sizeof(int32_t));
+  return J;
+}
+
+figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>& outs, char* area, size_t area_bytes,
+                          cudaStream_t s) {
+  const int count = static_cast<int>(calls.size());
+  if (count == 0) return FIGARO_OK;
+  const Plan& p0 = calls[0].p;
+  const int mixed = p0.mixed, in_f64 = p0.t[0].in_f64;
+  // ---- job lists
+  JobList tiles, match, htplan, htscan, htstream[2], gram[2][4], reduce, dense1[3], dense2[3], dense3[3];
+  int ht_smem[2] = {0, 0};
+  size_t gram_smem[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  size_t dsm[3][3] = {};
+  int dthr[3][3] = {};
+  int64_t total_chunks = 0;
+  for (int i = 0; i < count; ++i)
+    for (int t = 0; t < 2; ++t) total_chunks += calls[i].p.t[t].m > 0 ? calls[i].p.t[t].chunks : 0;
+  const int64_t gtot = 2 * static_cast<int64_t>(p0.num_sms);
+  for (int i = 0; i < count; ++i) {
+    const Plan& p = calls[i].p;
+    for (int t = 0; t < 2; ++t) {
+      tiles.add(i, t, p.t[t].tiles);
+      int v = 0, sm = 0, chunks = 0;
+      ht_batch_table(p, t, &v, &sm, &chunks);
+      if (chunks == 0) continue;
+      htplan.add(i, t, chunks);
+      htscan.add(i, t, p.t[t].n);
+      int64_t g = (static_cast<int64_t>(chunks) * gtot + total_chunks - 1) / total_chunks;
+      g = std::max<int64_t>(1, std::min<int64_t>(g, chunks));
+      htstream[v].add(i, t, static_cast<int>(g));
+      ht_smem[v] = std::max(ht_smem[v], sm);
+    }
+    const int64_t mm = std::max(p.t[0].m, p.t[1].m);
+    match.add(i, 0, static_cast<int>((mm + 255) / 256));
+    for (int pass = 1; pass <= 2; ++pass)
+      for (int b = 0; b < 3; ++b) {
+        int v = 0, ctas = 0;
+        size_t sm = 0;
+        gram_batch_block(p, pass, b, &v, &ctas, &sm);
+        if (ctas == 0) continue;
+        gram[pass - 1][v].add(i, b, ctas);
+        gram_smem[pass - 1][v] = std::max(gram_smem[pass - 1][v], sm);
+      }
+    reduce.add(i, 0, (p.n * p.n + 31) / 32);
+    JobList* dl[3] = {dense1, dense2, dense3};
+    for (int step = 1; step <= 3; ++step) {
+      if (step == 3 && !outs[i].sigma) continue;
+      int v = 0, thr = 0;
+      size_t sm = 0;
+      dense_batch_info(p, step, &v, &sm, &thr);
+      dl[step - 1][v].add(i, 0, 1);
+      dsm[step - 1][v] = std::max(dsm[step - 1][v], sm);
+      dthr[step - 1][v] = std::max(dthr[step - 1][v], thr);
+    }
+  }
+  // ---- the batch area: plans, outputs, job lists
+  Blob blob;
+  std::vector<Plan> plans(count);
+  for (int i = 0; i < count; ++i) plans[i] = calls[i].p;
+  const size_t off_plans = blob.put(plans.data(), sizeof(Plan) * count);
+  const size_t off_outs = blob.put(outs.data(), sizeof(BatchOut) * count);
+  std::vector<std::pair<BatchJobs*, size_t[3]>> fix;
+  BatchJobs Jtiles, Jmatch, Jplan, Jscan, Jstream[2], Jgram[2][4], Jreduce, Jd[3][3];
+  Jtiles = stage_jobs(blob, tiles, fix, &Jtiles);
+  Jmatch = stage_jobs(blob, match, fix, &Jmatch);
+  Jplan = stage_jobs(blob, htplan, fix, &Jplan);
+  Jscan = stage_jobs(blob, htscan, fix, &Jscan);
+  for (int v = 0; v < 2; ++v) Jstream[v] = stage_jobs(blob, htstream[v], fix, &Jstream[v]);
+  for (int q = 0; q < 2; ++q)
+    for (int v = 0; v < 4; ++v) Jgram[q][v] = stage_jobs(blob, gram[q][v], fix, &Jgram[q][v]);
+  Jreduce = stage_jobs(blob, reduce, fix, &Jreduce);
+  JobList* dl[3] = {dense1, dense2, dense3};
+  for (int st = 0; st < 3; ++st)
+    for (int v = 0; v < 3; ++v) Jd[st][v] = stage_jobs(blob, dl[st][v], fix, &Jd[st][v]);
+  if (blob.bytes.size() > area_bytes) return FIGARO_ERR_WORKSPACE_TOO_SMALL;
+  for (auto& f : fix) {
+    f.first->first = reinterpret_cast<const int32_t*>(area + f.second[0]);
+    f.first->inst = reinterpret_cast<const int32_t*>(area + f.second[1]);
+    f.first->aux = reinterpret_cast<const int32_t*>(area + f.second[2]);
+  }
+  for (size_t o = 0; o < blob.bytes.size(); o += kUploadBytes) {
+    UploadChunk c;
+    c.dst = reinterpret_cast<unsigned char*>(area) + o;
+    c.bytes = static_cast<int>(std::min<size_t>(kUploadBytes, blob.bytes.size() - o));
+    std::memcpy(c.data, blob.bytes.data() + o, c.bytes);
+    upload_kernel<<<1, 512, 0, s>>>(c);
+    count_launches(1);
+  }
+  FIGARO_TRY(cudaGetLastError());
+  BatchDev b;
+  b.plans = reinterpret_cast<const Plan*>(area + off_plans);
+  b.out = reinterpret_cast<const BatchOut*>(area + off_outs);
+  b.count = count;
+  // ---- the phases
+  FIGARO_TRY(launch_batch_grouping(b, Jtiles, Jmatch, s));
+  FIGARO_TRY(launch_batch_ht(b, Jplan, Jplan.ctas, Jscan, Jstream, ht_smem, in_f64, mixed, s));
+  FIGARO_TRY(launch_batch_gram(b, 1, Jgram[0], gram_smem[0], Jreduce, mixed, s));
+  FIGARO_TRY(launch_batch_dense(b, 1, Jd[0], dsm[0], dthr[0], mixed, s));
+  FIGARO_TRY(launch_batch_gram(b, 2, Jgram[1], gram_smem[1], Jreduce, mixed, s));
+  FIGARO_TRY(launch_batch_dense(b, 2, Jd[1], dsm[1], dthr[1], mixed, s));
+  FIGARO_TRY(launch_batch_dense(b, 3, Jd[2], dsm[2], dthr[2], mixed, s));
+  return FIGARO_OK;
+}
+
 }  // namespace
 }  // namespace figaro
 
@@ -480,7 +647,7 @@ figaro_status figaro_join_singular_values_fixed(const figaro_table* A, const fig
 figaro_status figaro_batch_workspace_size(int32_t count, const figaro_table* A, const figaro_table* B,
                                           const figaro_options* opt, size_t* bytes) {
   if (count < 0 || !bytes || (count > 0 && (!A || !B))) return FIGARO_ERR_INVALID_ARG;
-  size_t total = 0;
+  size_t total = batch_area_bytes(count);
   for (int32_t i = 0; i < count; ++i) {
     size_t one = 0;
     figaro_status st = figaro_workspace_size(&A[i], &B[i], opt, &one);
@@ -499,25 +666,44 @@ figaro_status figaro_batch_join(int32_t count, const figaro_table* A, const figa
   figaro_status st = figaro_batch_workspace_size(count, A, B, opt, &need);
   if (st != FIGARO_OK) return st;
   if (ws_bytes < need) return FIGARO_ERR_WORKSPACE_TOO_SMALL;
-  char* base = static_cast<char*>(ws);
+  char* area = static_cast<char*>(ws);
+  const size_t area_bytes = batch_area_bytes(count);
+  char* base = area + area_bytes;
   const int host_out = opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT);
+  // instances the batched launches take: narrow widths, device-resident
+  // tables and device outputs; the others run one after another
+  std::vector<Call> batched;
+  std::vector<BatchOut> outs;
+  std::vector<int> single;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int32_t i = 0; i < count; ++i) {
     size_t one = 0;
     figaro_workspace_size(&A[i], &B[i], opt, &one);
     one = (one + 255) & ~static_cast<size_t>(255);
-    Call c;
     figaro_options oi = resolve(opt);
     oi.phase_events = nullptr;
+    Call c;
     st = prepare(c, &A[i], &B[i], &oi, base, one, stream);
     if (st != FIGARO_OK) return st;
-    const int n = c.p.n;
-    if (sigma[i]) {
-      st = run_qr_svd(c, R[i], n, sigma[i], host_out);
-    } else if (R[i]) {
-      st = run_qr_svd(c, R[i], n, nullptr, host_out);
-    }
-    if (st != FIGARO_OK) return st;
     base += one;
+    if (!R[i] && !sigma[i]) continue;
+    const bool narrow = c.p.n <= kMaxWidth;
+    const bool device_io = A[i].memory == FIGARO_MEM_DEVICE && B[i].memory == FIGARO_MEM_DEVICE && !host_out;
+    if (narrow && device_io) {
+      batched.push_back(c);
+      outs.push_back(BatchOut{R[i], sigma[i]});
+    } else {
+      const int n = c.p.n;
+      st = run_qr_svd(c, R[i], n, sigma[i], host_out);
+      if (st != FIGARO_OK) return st;
+    }
+  }
+  if (!batched.empty()) {
+    // every batched instance was prepared on the workspace's device
+    st = bind_device(area);
+    if (st != FIGARO_OK) return st;
+    st = run_batched(batched, outs, area, area_bytes, s);
+    if (st != FIGARO_OK) return st;
   }
   return FIGARO_OK;
 }

@@ -119,8 +119,8 @@ __device__ void tri_inverse_inplace(T* A, int n, const int32_t* act, T* x) {
 }
 
 template <typename T, bool kSmall>
-__global__ void chol_first_kernel(const double* G, int n, double tol, double* R1, double* W, float* Wf,
-                                  int32_t* active, int32_t* status) {
+__device__ __forceinline__ void chol_first_body(const double* G, int n, double tol, double* R1, double* W, float* Wf,
+                                                int32_t* active, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* A = reinterpret_cast<T*>(smraw);  // n x n
   T* diag0 = A + n * n;
@@ -166,6 +166,12 @@ __global__ void chol_first_kernel(const double* G, int n, double tol, double* R1
   }
 }
 
+template <typename T, bool kSmall>
+__global__ void chol_first_kernel(const double* G, int n, double tol, double* R1, double* W, float* Wf,
+                                  int32_t* active, int32_t* status) {
+  chol_first_body<T, kSmall>(G, n, tol, R1, W, Wf, active, status);
+}
+
 // Upper-triangular product C = A B on n x n row-major matrices, one thread
 // per output, two partial sums to shorten the FP64 dependency chain.
 template <typename TA, typename TB>
@@ -180,10 +186,10 @@ __device__ __forceinline__ double upper_dot(const TA* A, const TB* B, int n, int
   return s0 + s1;
 }
 
-template <typename T, bool kSmall>
-__global__ void chol_second_kernel(const double* G2, int n, double tol, const double* R1, const double* Wd,
-                                   const int32_t* active, int refine, double* Xg, double* R, double* R_out,
-                                   int64_t ldr, int32_t* status) {
+template <typename T>
+__device__ __forceinline__ void chol_second_body(const double* G2, int n, double tol, const double* R1, const double* Wd,
+                                                 const int32_t* active, int refine, double* Xg, double* R,
+                                                 double* R_out, int64_t ldr, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* A = reinterpret_cast<T*>(smraw);
   T* diag0 = A + n * n;
@@ -228,6 +234,13 @@ __global__ void chol_second_kernel(const double* G2, int n, double tol, const do
   }
 }
 
+template <typename T, bool kSmall>
+__global__ void chol_second_kernel(const double* G2, int n, double tol, const double* R1, const double* Wd,
+                                   const int32_t* active, int refine, double* Xg, double* R, double* R_out,
+                                   int64_t ldr, int32_t* status) {
+  chol_second_body<T>(G2, n, tol, R1, Wd, active, refine, Xg, R, R_out, ldr, status);
+}
+
 template <typename T>
 __device__ __forceinline__ T group_sum(T v, int width) {
   for (int o = width >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, width);
@@ -258,8 +271,8 @@ __device__ __forceinline__ void rotation(double al, double be, double ga, double
 // the round-robin pairing is tabulated once.  A pair is rotated while
 // |u_p.u_q|^2 > tol^2 |u_p|^2 |u_q|^2.
 template <typename T, bool kWithV, int NPL, int LPP>
-__global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in, double* sigma,
-                              int32_t* status, int32_t* sweeps_out) {
+__device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in,
+                                            double* sigma, int32_t* status, int32_t* sweeps_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int np = n + (n & 1);  // even number of columns (one zero column if n is odd)
   const int npairs = np / 2, rounds = np - 1;
@@ -436,9 +449,45 @@ __global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweep
   }
 }
 
+template <typename T, bool kWithV, int NPL, int LPP>
+__global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in, double* sigma,
+                              int32_t* status, int32_t* sweeps_out) {
+  jacobi_body<T, kWithV, NPL, LPP>(R, ldr, n, max_sweeps, tol_in, sigma, status, sweeps_out);
+}
+
+__host__ __device__ inline double dense_tol(const Plan& p) {
+  return p.rank_tol > 0 ? p.rank_tol : (p.mixed ? 1e-5 : 1e-13);
+}
+__host__ __device__ inline double jacobi_tol(const Plan& p) {
+  return p.mixed ? 1e-5 : 4.0 * p.n * 1.1102230246251565e-16;
+}
+
+// ---- batched forms: one CTA per instance (job j = CTA j)
+template <typename T, bool kSmall>
+__global__ void chol_first_batched(BatchDev b, BatchJobs J) {
+  const Plan& P = b.plans[J.inst[blockIdx.x]];
+  chol_first_body<T, kSmall>(P.G1, P.n, dense_tol(P), P.R1, P.W, P.Wf, P.active, &P.hdr->status);
+}
+
+template <typename T>
+__global__ void chol_second_batched(BatchDev b, BatchJobs J) {
+  const int i = J.inst[blockIdx.x];
+  const Plan& P = b.plans[i];
+  chol_second_body<T>(P.G2, P.n, dense_tol(P), P.R1, P.W, P.active, P.mixed, P.G1, P.R, b.out[i].R, P.n,
+                      &P.hdr->status);
+}
+
+template <typename T, bool kWithV, int NPL>
+__global__ void jacobi_batched(BatchDev b, BatchJobs J) {
+  const int i = J.inst[blockIdx.x];
+  const Plan& P = b.plans[i];
+  jacobi_body<T, kWithV, NPL, 32>(P.R, P.n, P.n, P.max_sweeps, jacobi_tol(P), b.out[i].sigma, &P.hdr->status,
+                                  &P.hdr->jacobi_sweeps);
+}
+
 }  // namespace
 
-static double default_tol(const Plan& p) { return p.rank_tol > 0 ? p.rank_tol : (p.mixed ? 1e-5 : 1e-13); }
+static double default_tol(const Plan& p) { return dense_tol(p); }
 
 static int dense_threads(int n) {
   int t = 64;
@@ -519,6 +568,82 @@ cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* s
   if (n <= 32) return jacobi_t<double, false, 1>(p, R, ldr, sigma, tol, s);
   if (n <= 64) return jacobi_t<double, false, 2>(p, R, ldr, sigma, tol, s);
   return jacobi_t<double, false, 4>(p, R, ldr, sigma, tol, s);
+}
+
+// Batched dense steps.  step 1: first Cholesky (variant 0: column-per-thread
+// inverse with a second n x n buffer, 1: in-place inverse); step 2: second
+// Cholesky and R; step 3: Jacobi (variant = rows per lane 1, 2, 4 -> 0, 1, 2).
+template <typename T>
+static size_t chol_first_smem(int n, bool small) {
+  size_t smem = sizeof(T) * (static_cast<size_t>(n) * n + 3 * n) + sizeof(int32_t) * (n + 4) + 16;
+  if (small) smem += sizeof(T) * static_cast<size_t>(n) * n;
+  return smem;
+}
+
+void dense_batch_info(const Plan& p, int step, int* variant, size_t* smem, int* threads) {
+  const int n = p.n;
+  const size_t es = p.mixed ? 4 : 8;
+  if (step == 1) {
+    const bool small = es * 2 * static_cast<size_t>(n) * n <= 96 * 1024;
+    *variant = small ? 0 : 1;
+    *smem = p.mixed ? chol_first_smem<float>(n, small) : chol_first_smem<double>(n, small);
+    *threads = dense_threads(n);
+  } else if (step == 2) {
+    *variant = 0;
+    *smem = ((es * (static_cast<size_t>(n) * n + 2 * n) + sizeof(int32_t) * n + 15) & ~size_t(15)) +
+            (p.mixed ? sizeof(double) * static_cast<size_t>(n) * n : 0);
+    *threads = dense_threads(n);
+  } else {
+    const int np = n + (n & 1), npairs = np / 2;
+    const int npl = n <= 32 ? 1 : (n <= 64 ? 2 : 4);
+    *variant = npl == 1 ? 0 : (npl == 2 ? 1 : 2);
+    int t = 32 * npairs;  // one warp per pair (32 lanes per pair)
+    *threads = t > 1024 ? 1024 : t;
+    const bool with_v = p.mixed != 0;
+    size_t sm = es * static_cast<size_t>(np) * n * (with_v ? 2 : 1) + sizeof(double) * np;
+    if (with_v && n <= 64) sm += sizeof(double) * static_cast<size_t>(n) * n;
+    sm += sizeof(short2) * static_cast<size_t>(np - 1) * npairs;
+    *smem = sm;
+  }
+}
+
+template <typename K>
+static cudaError_t launch_bucket(K kern, const BatchDev& b, const BatchJobs& J, size_t smem, int threads,
+                                 cudaStream_t s) {
+  if (J.njobs == 0) return cudaSuccess;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  kern<<<J.njobs, threads, smem, s>>>(b, J);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_dense(const BatchDev& b, int step, const BatchJobs jobs[3], const size_t smem[3],
+                               const int threads[3], int mixed, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (step == 1) {
+    if (mixed) {
+      e = launch_bucket(chol_first_batched<float, true>, b, jobs[0], smem[0], threads[0], s);
+      if (e == cudaSuccess) e = launch_bucket(chol_first_batched<float, false>, b, jobs[1], smem[1], threads[1], s);
+    } else {
+      e = launch_bucket(chol_first_batched<double, true>, b, jobs[0], smem[0], threads[0], s);
+      if (e == cudaSuccess) e = launch_bucket(chol_first_batched<double, false>, b, jobs[1], smem[1], threads[1], s);
+    }
+  } else if (step == 2) {
+    e = mixed ? launch_bucket(chol_second_batched<float>, b, jobs[0], smem[0], threads[0], s)
+              : launch_bucket(chol_second_batched<double>, b, jobs[0], smem[0], threads[0], s);
+  } else {
+    if (mixed) {
+      e = launch_bucket(jacobi_batched<float, true, 1>, b, jobs[0], smem[0], threads[0], s);
+      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<float, true, 2>, b, jobs[1], smem[1], threads[1], s);
+      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<float, true, 4>, b, jobs[2], smem[2], threads[2], s);
+    } else {
+      e = launch_bucket(jacobi_batched<double, false, 1>, b, jobs[0], smem[0], threads[0], s);
+      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<double, false, 2>, b, jobs[1], smem[1], threads[1], s);
+      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<double, false, 4>, b, jobs[2], smem[2], threads[2], s);
+    }
+  }
+  return e;
 }
 
 }  // namespace figaro

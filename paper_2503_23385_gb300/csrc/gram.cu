@@ -62,7 +62,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <typename T, int TPT>
-__global__ void __launch_bounds__(kGramThreads) gram_kernel(GramArgs a) {
+__device__ __forceinline__ void gram_body(const GramArgs& a, int bid, int nb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int RT = a.tile_rows, k = a.k, kp = a.kpad, T4 = kp / 4;
   T* Xb[2] = {reinterpret_cast<T*>(smem_raw), reinterpret_cast<T*>(smem_raw) + RT * k};  // RT x k, two stages
@@ -119,13 +119,13 @@ __global__ void __launch_bounds__(kGramThreads) gram_kernel(GramArgs a) {
       }
 
   const int64_t ntiles_rows = (rows + RT - 1) / RT;
-  int64_t rt = blockIdx.x;
+  int64_t rt = bid;
   if (rt < ntiles_rows) stage(rt, Xb[0]);
   int since_flush = 0;
-  for (int buf = 0; rt < ntiles_rows; rt += gridDim.x, buf ^= 1) {
+  for (int buf = 0; rt < ntiles_rows; rt += nb, buf ^= 1) {
     cp_async_wait_all();
     __syncthreads();  // tile rt landed; the other buffer is free
-    if (rt + gridDim.x < ntiles_rows) stage(rt + gridDim.x, Xb[buf ^ 1]);  // overlaps the work below
+    if (rt + nb < ntiles_rows) stage(rt + nb, Xb[buf ^ 1]);  // overlaps the work below
     const T* Xs = Xb[buf];
     if (a.W) {
       for (int e = tid; e < RT * kp; e += blockDim.x) {
@@ -197,11 +197,16 @@ __global__ void __launch_bounds__(kGramThreads) gram_kernel(GramArgs a) {
     }
   }
   __syncthreads();
-  double* out = a.part + static_cast<int64_t>(blockIdx.x) * a.kout * a.kout;
+  double* out = a.part + static_cast<int64_t>(bid) * a.kout * a.kout;
   for (int e = tid; e < a.kout * a.kout; e += blockDim.x) {
     int i = e / a.kout, j = e - i * a.kout;
     out[e] = red[i * kp + j];
   }
+}
+
+template <typename T, int TPT>
+__global__ void __launch_bounds__(kGramThreads) gram_kernel(GramArgs a) {
+  gram_body<T, TPT>(a, blockIdx.x, gridDim.x);
 }
 
 struct ReduceArgs {
@@ -219,10 +224,10 @@ constexpr int kReduceWarps = 32;
 // G = sum of the three blocks' partials in a fixed order (deterministic).
 // A block owns 32 consecutive outputs (one per lane); its warps interleave
 // over the partials and their sums are combined in warp order.
-__global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_kernel(ReduceArgs a) {
+__device__ __forceinline__ void gram_reduce_body(const ReduceArgs& a, int bid) {
   __shared__ double s[kReduceWarps][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int e = blockIdx.x * 32 + lane;
+  const int e = bid * 32 + lane;
   const bool ok = e < a.n * a.n;
   const int i = ok ? e / a.n : 0, j = ok ? e - (e / a.n) * a.n : 0;
   const int lo = i < j ? i : j, hi = i < j ? j : i;
@@ -253,6 +258,130 @@ __global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_kernel(ReduceAr
   }
 }
 
+__global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_kernel(ReduceArgs a) {
+  gram_reduce_body(a, blockIdx.x);
+}
+
+// Geometry of one Gram block: kout padded to 4, the upper 4 x 4 register
+// tiles, thread groups (slices) splitting a row tile, tiles per thread.
+__host__ __device__ inline void gram_geom(int kout, int* kpad, int* ntiles, int* slices, int* tpt) {
+  *kpad = (kout + 3) / 4 * 4;
+  const int T4 = *kpad / 4;
+  *ntiles = T4 * (T4 + 1) / 2;
+  int t = 1;
+  while ((*ntiles + t - 1) / t > kGramThreads) t <<= 1;
+  *tpt = t;
+  const int per_slice = (*ntiles + t - 1) / t;
+  *slices = kGramThreads / per_slice;
+}
+
+__host__ __device__ inline int gram_rows_per_tile(int k, int kout, int with_w, int elem) {
+  const int kp = (kout + 3) / 4 * 4;
+  for (int rt = kGramTileRows; rt >= 4; rt /= 2) {
+    size_t smem = 2 * static_cast<size_t>(rt) * k * elem;
+    if (with_w) smem += (static_cast<size_t>(k) * kp + static_cast<size_t>(rt) * kp) * elem;
+    if (smem <= 200 * 1024) return rt;
+  }
+  return 4;
+}
+
+__host__ __device__ inline size_t gram_smem_bytes(const GramArgs& a, int elem) {
+  size_t smem = 2 * static_cast<size_t>(a.tile_rows) * a.k * elem;
+  if (a.W) smem += (static_cast<size_t>(a.k) * a.kpad + static_cast<size_t>(a.tile_rows) * a.kpad) * elem;
+  const size_t red = sizeof(double) * a.kpad * a.kpad;
+  return smem < red ? red : smem;
+}
+
+// The CUDA-core arguments of Gram block b (0 head rows, 1 A tails, 2 B tails)
+// of a pass; *rows_host = the block's row bound (0: the block is empty).
+__host__ __device__ inline GramArgs gram_args_of(const Plan& p, int pass, int b, int64_t* rows_host, int* tpt) {
+  GramArgs a{};
+  if (b == 0) {
+    a.X = p.head;
+    a.k = p.n;
+    a.rows_dev = &p.hdr->num_runs[0];
+    *rows_host = p.t[0].m;
+  } else {
+    const TableWork& T = p.t[b - 1];
+    a.X = T.tail;
+    a.k = T.n;
+    a.rows = T.m;
+    *rows_host = T.m;
+  }
+  if (pass == 2) {
+    a.W = p.mixed ? static_cast<const void*>(p.Wf) : static_cast<const void*>(p.W);
+    a.wld = p.n;
+    a.w0 = b == 2 ? p.n1 : 0;
+    a.kout = b == 2 ? p.n2 : p.n;
+  } else {
+    a.kout = a.k;
+  }
+  gram_geom(a.kout, &a.kpad, &a.ntiles, &a.slices, tpt);
+  a.tile_rows = gram_rows_per_tile(a.k, a.kout, a.W != nullptr, p.mixed ? 4 : 8);
+  a.part = p.gpart[b];
+  return a;
+}
+
+__host__ __device__ inline ReduceArgs reduce_args_of(const Plan& p, int pass) {
+  ReduceArgs r{};
+  r.n = p.n;
+  r.G = pass == 1 ? p.G1 : p.G2;
+  for (int b = 0; b < 3; ++b) {
+    int64_t rows = 0;
+    int tpt = 0;
+    const GramArgs a = gram_args_of(p, pass, b, &rows, &tpt);
+    if (rows == 0) continue;
+    r.part[b] = p.gpart[b];
+    r.count[b] = p.ggrid[b];
+    r.kout[b] = a.kout;
+    r.off[b] = b == 2 ? p.n1 : 0;
+    r.sym[b] = 0;
+  }
+  return r;
+}
+
+// ---- batched forms (CUDA-core Gram): Gram jobs are (instance, block) with
+// aux = block and p.ggrid[block] CTAs; reduce jobs are instances with
+// ceil(n^2 / 32) CTAs
+template <typename T, int TPT>
+__global__ void __launch_bounds__(kGramThreads) gram_batched(BatchDev bd, BatchJobs J, int pass) {
+  __shared__ GramArgs s_a;
+  const int j = batch_job(J, blockIdx.x);
+  if (threadIdx.x == 0) {
+    int64_t rows = 0;
+    int tpt = 0;
+    s_a = gram_args_of(bd.plans[J.inst[j]], pass, J.aux[j], &rows, &tpt);
+  }
+  __syncthreads();
+  gram_body<T, TPT>(s_a, blockIdx.x - J.first[j], J.first[j + 1] - J.first[j]);
+}
+
+__global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_batched(BatchDev bd, BatchJobs J, int pass) {
+  __shared__ ReduceArgs s_r;
+  const int j = batch_job(J, blockIdx.x);
+  if (threadIdx.x == 0) s_r = reduce_args_of(bd.plans[J.inst[j]], pass);
+  __syncthreads();
+  gram_reduce_body(s_r, blockIdx.x - J.first[j]);
+}
+
+template <typename T>
+cudaError_t launch_batch_gram_t(const BatchDev& b, int pass, const BatchJobs* by_tpt, const size_t* smem,
+                                const BatchJobs& reduce, cudaStream_t s) {
+  for (int q = 0; q < 4; ++q) {
+    if (by_tpt[q].njobs == 0) continue;
+    auto kern = q == 0 ? gram_batched<T, 1> : (q == 1 ? gram_batched<T, 2> : (q == 2 ? gram_batched<T, 4> : gram_batched<T, 8>));
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem[q]));
+    if (err != cudaSuccess) return err;
+    kern<<<by_tpt[q].ctas, kGramThreads, smem[q], s>>>(b, by_tpt[q], pass);
+    count_launches(1);
+  }
+  if (reduce.njobs > 0) {
+    gram_reduce_batched<<<reduce.ctas, 32 * kReduceWarps, 0, s>>>(b, reduce, pass);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T, int TPT>
 cudaError_t launch_tpt(const GramArgs& a, int grid, size_t smem, cudaStream_t s) {
   cudaError_t err =
@@ -265,10 +394,7 @@ cudaError_t launch_tpt(const GramArgs& a, int grid, size_t smem, cudaStream_t s)
 
 template <typename T>
 cudaError_t launch_gram_block(const GramArgs& a, int tpt, int grid, cudaStream_t s) {
-  size_t smem = 2 * static_cast<size_t>(a.tile_rows) * a.k * sizeof(T);
-  if (a.W) smem += (static_cast<size_t>(a.k) * a.kpad + static_cast<size_t>(a.tile_rows) * a.kpad) * sizeof(T);
-  size_t red = sizeof(double) * a.kpad * a.kpad;
-  if (smem < red) smem = red;
+  const size_t smem = gram_smem_bytes(a, sizeof(T));
   switch (tpt) {
     case 1: return launch_tpt<T, 1>(a, grid, smem, s);
     case 2: return launch_tpt<T, 2>(a, grid, smem, s);
@@ -280,25 +406,25 @@ cudaError_t launch_gram_block(const GramArgs& a, int tpt, int grid, cudaStream_t
 }  // namespace
 
 // Geometry of one Gram block (shared with the workspace planner).
-void gram_geometry(int kout, int* kpad, int* ntiles, int* slices, int* tpt) {
-  *kpad = (kout + 3) / 4 * 4;
-  const int T4 = *kpad / 4;
-  *ntiles = T4 * (T4 + 1) / 2;
-  int t = 1;
-  while ((*ntiles + t - 1) / t > kGramThreads) t <<= 1;
-  *tpt = t;
-  const int per_slice = (*ntiles + t - 1) / t;
-  *slices = kGramThreads / per_slice;
+void gram_geometry(int kout, int* kpad, int* ntiles, int* slices, int* tpt) { gram_geom(kout, kpad, ntiles, slices, tpt); }
+
+int gram_tile_rows(int k, int kout, int with_w, int elem) { return gram_rows_per_tile(k, kout, with_w, elem); }
+
+// Batched Gram jobs of one instance: for each block with rows, its
+// tiles-per-thread variant (0..3 for 1, 2, 4, 8), CTAs and shared memory.
+void gram_batch_block(const Plan& p, int pass, int b, int* variant, int* ctas, size_t* smem) {
+  int64_t rows = 0;
+  int tpt = 1;
+  const GramArgs a = gram_args_of(p, pass, b, &rows, &tpt);
+  *ctas = rows > 0 ? p.ggrid[b] : 0;
+  *variant = tpt <= 1 ? 0 : (tpt == 2 ? 1 : (tpt == 4 ? 2 : 3));
+  *smem = gram_smem_bytes(a, p.mixed ? 4 : 8);
 }
 
-int gram_tile_rows(int k, int kout, int with_w, int elem) {
-  const int kp = (kout + 3) / 4 * 4;
-  for (int rt = kGramTileRows; rt >= 4; rt /= 2) {
-    size_t smem = 2 * static_cast<size_t>(rt) * k * elem;
-    if (with_w) smem += (static_cast<size_t>(k) * kp + static_cast<size_t>(rt) * kp) * elem;
-    if (smem <= 200 * 1024) return rt;
-  }
-  return 4;
+cudaError_t launch_batch_gram(const BatchDev& b, int pass, const BatchJobs by_tpt[4], const size_t smem[4],
+                              const BatchJobs& reduce, int mixed, cudaStream_t s) {
+  return mixed ? launch_batch_gram_t<float>(b, pass, by_tpt, smem, reduce, s)
+               : launch_batch_gram_t<double>(b, pass, by_tpt, smem, reduce, s);
 }
 
 bool gram_tc_supported(int k, int kout);

@@ -84,10 +84,7 @@ __global__ void reset_kernel(DevHeader* h) {
 // The key range, the first pass's digit counts per tile and their global
 // sum (the later passes' counts come from tile_count_kernel, once the key
 // range has fixed how many passes run).
-__global__ void __launch_bounds__(kSortThreads) key_hist_kernel(TwoTables a) {
-  int tile;
-  const int t = table_of(a, blockIdx.x, tile);
-  const TableWork& T = a.t[t];
+__device__ __forceinline__ void key_hist_body(const TableWork& T, int t, DevHeader* h, int tile) {
   __shared__ uint32_t hist[kRadixBins];
   for (int i = threadIdx.x; i < kRadixBins; i += blockDim.x) hist[i] = 0u;
   __syncthreads();
@@ -114,8 +111,8 @@ __global__ void __launch_bounds__(kSortThreads) key_hist_kernel(TwoTables a) {
     hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicMin(&a.h->kmin[t], lo);
-    atomicMax(&a.h->kmax[t], hi);
+    atomicMin(&h->kmin[t], lo);
+    atomicMax(&h->kmax[t], hi);
   }
   __syncthreads();
   uint32_t* tc = tile_counts(T, 0) + static_cast<int64_t>(tile) * kRadixBins;
@@ -126,12 +123,21 @@ __global__ void __launch_bounds__(kSortThreads) key_hist_kernel(TwoTables a) {
   }
 }
 
-// Digit counts of every tile for a later pass (the keys as the previous pass left them).
-__global__ void __launch_bounds__(kSortThreads) tile_count_kernel(TwoTables a, int pass) {
+__global__ void __launch_bounds__(kSortThreads) key_hist_kernel(TwoTables a) {
   int tile;
   const int t = table_of(a, blockIdx.x, tile);
-  const TableWork& T = a.t[t];
-  if (pass >= num_passes(a.h, t)) return;
+  key_hist_body(a.t[t], t, a.h, tile);
+}
+
+__global__ void __launch_bounds__(kSortThreads) key_hist_batched(BatchDev b, BatchJobs J) {
+  const int j = batch_job(J, blockIdx.x);
+  const Plan& P = b.plans[J.inst[j]];
+  key_hist_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x - J.first[j]);
+}
+
+// Digit counts of every tile for a later pass (the keys as the previous pass left them).
+__device__ __forceinline__ void tile_count_body(const TableWork& T, int t, const DevHeader* h, int tile, int pass) {
+  if (pass >= num_passes(h, t)) return;
   __shared__ uint32_t hist[kRadixBins];
   for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) hist[d] = 0u;
   __syncthreads();
@@ -159,13 +165,23 @@ __global__ void __launch_bounds__(kSortThreads) tile_count_kernel(TwoTables a, i
   }
 }
 
+__global__ void __launch_bounds__(kSortThreads) tile_count_kernel(TwoTables a, int pass) {
+  int tile;
+  const int t = table_of(a, blockIdx.x, tile);
+  tile_count_body(a.t[t], t, a.h, tile, pass);
+}
+
+__global__ void __launch_bounds__(kSortThreads) tile_count_batched(BatchDev b, BatchJobs J, int pass) {
+  const int j = batch_job(J, blockIdx.x);
+  const Plan& P = b.plans[J.inst[j]];
+  tile_count_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x - J.first[j], pass);
+}
+
 // Per (table, digit): the position of each tile's first key of that digit in
 // the pass's output, = (keys of smaller digits) + (keys of this digit in
 // earlier tiles): an exclusive scan over tiles.
-__global__ void __launch_bounds__(kRadixBins) tile_scan_kernel(TwoTables a, int pass) {
-  const int t = blockIdx.x / kRadixBins, d = blockIdx.x % kRadixBins;
-  const TableWork& T = a.t[t];
-  if (T.tiles == 0 || pass >= num_passes(a.h, t)) return;
+__device__ __forceinline__ void tile_scan_body(const TableWork& T, int t, const DevHeader* h, int d, int pass) {
+  if (T.tiles == 0 || pass >= num_passes(h, t)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ uint32_t s_w[kRadixBins / 32];
   __shared__ uint32_t s_carry;
@@ -202,6 +218,18 @@ __global__ void __launch_bounds__(kRadixBins) tile_scan_kernel(TwoTables a, int 
   }
 }
 
+__global__ void __launch_bounds__(kRadixBins) tile_scan_kernel(TwoTables a, int pass) {
+  const int t = blockIdx.x / kRadixBins;
+  tile_scan_body(a.t[t], t, a.h, blockIdx.x % kRadixBins, pass);
+}
+
+// one CTA per (table job, digit)
+__global__ void __launch_bounds__(kRadixBins) tile_scan_batched(BatchDev b, BatchJobs J, int pass) {
+  const int j = blockIdx.x / kRadixBins;
+  const Plan& P = b.plans[J.inst[j]];
+  tile_scan_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x % kRadixBins, pass);
+}
+
 // One stable LSD pass over digit `pass` (the scatter of reduce-then-scan).
 // Each tile ranks its keys stably (warp multi-split with match_any, then a
 // prefix over warps), places keys and payloads in shared memory in digit
@@ -210,7 +238,7 @@ __global__ void __launch_bounds__(kRadixBins) tile_scan_kernel(TwoTables a, int 
 // from tile_scan_kernel.
 constexpr int kSortSmem = (kSortThreads / 32) * kRadixBins * 4 + 3 * kRadixBins * 4 + 2 * kSortTile * 4;
 
-__global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(TwoTables a, int pass) {
+__device__ __forceinline__ void sort_pass_body(const TableWork& T, int t, const DevHeader* h, int tile, int pass) {
   constexpr int kWarps = kSortThreads / 32;
   extern __shared__ __align__(16) uint32_t sm_sort[];
   uint32_t (*cnt)[kRadixBins] = reinterpret_cast<uint32_t (*)[kRadixBins]>(sm_sort);
@@ -219,10 +247,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(TwoTables a,
   uint32_t* s_w = tpre + kRadixBins;                 // per-warp sums of the local scan
   uint32_t* sk = s_w + kRadixBins;                   // keys in digit order
   int32_t* sv = reinterpret_cast<int32_t*>(sk + kSortTile);  // payloads in digit order
-  int tile;
-  const int t = table_of(a, blockIdx.x, tile);
-  const TableWork& T = a.t[t];
-  const int P = num_passes(a.h, t);
+  const int P = num_passes(h, t);
   if (pass >= P) return;
   const bool last = pass == P - 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -321,12 +346,21 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(TwoTables a,
   }
 }
 
-// Run starts per tile of the sorted keys (a row starts a run when its key
-// differs from the row before it).
-__global__ void __launch_bounds__(kSortThreads) run_count_kernel(TwoTables a) {
+__global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(TwoTables a, int pass) {
   int tile;
   const int t = table_of(a, blockIdx.x, tile);
-  const TableWork& T = a.t[t];
+  sort_pass_body(a.t[t], t, a.h, tile, pass);
+}
+
+__global__ void __launch_bounds__(kSortThreads, 2) sort_pass_batched(BatchDev b, BatchJobs J, int pass) {
+  const int j = batch_job(J, blockIdx.x);
+  const Plan& P = b.plans[J.inst[j]];
+  sort_pass_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x - J.first[j], pass);
+}
+
+// Run starts per tile of the sorted keys (a row starts a run when its key
+// differs from the row before it).
+__device__ __forceinline__ void run_count_body(const TableWork& T, int tile) {
   const int64_t base = static_cast<int64_t>(tile) * kSortTile;
   uint32_t c = 0;
   for (int it = 0; it < kSortItems; ++it) {
@@ -344,18 +378,26 @@ __global__ void __launch_bounds__(kSortThreads) run_count_kernel(TwoTables a) {
   }
 }
 
+__global__ void __launch_bounds__(kSortThreads) run_count_kernel(TwoTables a) {
+  int tile;
+  const int t = table_of(a, blockIdx.x, tile);
+  run_count_body(a.t[t], tile);
+}
+
+__global__ void __launch_bounds__(kSortThreads) run_count_batched(BatchDev b, BatchJobs J) {
+  const int j = batch_job(J, blockIdx.x);
+  run_count_body(b.plans[J.inst[j]].t[J.aux[j]], blockIdx.x - J.first[j]);
+}
+
 // Runs of the sorted keys: run keys, run offsets, the run index of every
 // sorted row, and each run start's slot in the key lookup table.  The number
 // of runs before the tile is the sum of the earlier tiles' counts (a block
 // reduction, no waiting).  Rows are staged through shared memory so that
 // global accesses stay coalesced.
-__global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
+__device__ __forceinline__ void runs_body(const TableWork& T, int t, DevHeader* h, int tile, int64_t lut_size) {
   __shared__ int32_t sk[kSortTile + 1];
   __shared__ uint32_t s_w[kSortThreads / 32];
   __shared__ uint64_t s_excl;
-  int tile;
-  const int t = table_of(a, blockIdx.x, tile);
-  const TableWork& T = a.t[t];
   const int64_t base = static_cast<int64_t>(tile) * kSortTile;
   const int64_t m = T.m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -399,7 +441,7 @@ __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
   __syncthreads();
   uint32_t wpre = 0;
   for (int w = 0; w < warp; ++w) wpre += s_w[w];
-  const uint32_t kbase = min(a.h->kmin[0], a.h->kmin[1]);
+  const uint32_t kbase = min(h->kmin[0], h->kmin[1]);
   int64_t run = static_cast<int64_t>(s_excl) + wpre + incl - c - 1;  // run of the row before my first
   int32_t segs[kSortItems];
 #pragma unroll
@@ -411,11 +453,11 @@ __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
       T.run_key[run] = k;
       T.run_off[run] = static_cast<int32_t>(i);
       const uint32_t off = key_to_ordered(k) - kbase;
-      if (off < static_cast<uint32_t>(a.lut_size)) T.lut[off] = static_cast<int32_t>(run);
+      if (off < static_cast<uint32_t>(lut_size)) T.lut[off] = static_cast<int32_t>(run);
     }
     segs[it] = static_cast<int32_t>(run);
     if (i == m - 1) {
-      a.h->num_runs[t] = run + 1;
+      h->num_runs[t] = run + 1;
       T.run_off[run + 1] = static_cast<int32_t>(m);
     }
   }
@@ -427,6 +469,18 @@ __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
     const int64_t i = base + e;
     if (i < m) T.seg[i] = sk[e];
   }
+}
+
+__global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
+  int tile;
+  const int t = table_of(a, blockIdx.x, tile);
+  runs_body(a.t[t], t, a.h, tile, a.lut_size);
+}
+
+__global__ void __launch_bounds__(kSortThreads) runs_batched(BatchDev b, BatchJobs J) {
+  const int j = batch_job(J, blockIdx.x);
+  const Plan& P = b.plans[J.inst[j]];
+  runs_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x - J.first[j], P.lut_size);
 }
 
 __device__ __forceinline__ int64_t lower_bound_key(const int32_t* keys, int64_t n, int32_t k) {
@@ -448,9 +502,10 @@ __device__ __forceinline__ int64_t lower_bound_key(const int32_t* keys, int64_t 
 // The run of key k in table O: the lookup table when k is inside its range
 // (an entry is trusted only if it names a run with that key: no entry needs
 // initialising), else a binary search of O's run keys.
-__device__ __forceinline__ int64_t find_run(const TwoTables& a, const TableWork& O, int64_t UO, int32_t k) {
-  const uint32_t off = key_to_ordered(k) - min(a.h->kmin[0], a.h->kmin[1]);
-  if (off < static_cast<uint32_t>(a.lut_size)) {
+__device__ __forceinline__ int64_t find_run(const DevHeader* h, int64_t lut_size, const TableWork& O, int64_t UO,
+                                            int32_t k) {
+  const uint32_t off = key_to_ordered(k) - min(h->kmin[0], h->kmin[1]);
+  if (off < static_cast<uint32_t>(lut_size)) {
     const int64_t j = O.lut[off];
     return (j >= 0 && j < UO && O.run_key[j] == k) ? j : -1;
   }
@@ -458,16 +513,14 @@ __device__ __forceinline__ int64_t find_run(const TwoTables& a, const TableWork&
   return (j < UO && O.run_key[j] == k) ? j : -1;
 }
 
-__global__ void match_kernel(TwoTables a) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  DevHeader* h = a.h;
-  const TableWork& A = a.t[0];
-  const TableWork& B = a.t[1];
+__device__ __forceinline__ void match_body(const TableWork& A, const TableWork& B, DevHeader* h, int64_t lut_size,
+                                           int block) {
+  const int64_t i = static_cast<int64_t>(block) * blockDim.x + threadIdx.x;
   const int64_t UA = h->num_runs[0], UB = h->num_runs[1];
   unsigned long long groups = 0, reduced = 0;
   if (i < UA) {
     const int32_t k = A.run_key[i];
-    const int64_t j = find_run(a, B, UB, k);
+    const int64_t j = find_run(h, lut_size, B, UB, k);
     const int32_t mine = A.run_off[i + 1] - A.run_off[i];
     A.hdslot[i] = static_cast<int32_t>(i);
     int32_t other = 0;
@@ -490,7 +543,7 @@ __global__ void match_kernel(TwoTables a) {
   }
   if (i < UB) {
     const int32_t k = B.run_key[i];
-    const int64_t j = find_run(a, A, UA, k);
+    const int64_t j = find_run(h, lut_size, A, UA, k);
     int32_t other = 0, slot = -1;
     if (j >= 0) {
       other = A.run_off[j + 1] - A.run_off[j];
@@ -502,7 +555,67 @@ __global__ void match_kernel(TwoTables a) {
   }
 }
 
+__global__ void match_kernel(TwoTables a) { match_body(a.t[0], a.t[1], a.h, a.lut_size, blockIdx.x); }
+
+__global__ void match_batched(BatchDev b, BatchJobs J) {
+  const int j = batch_job(J, blockIdx.x);
+  const Plan& P = b.plans[J.inst[j]];
+  match_body(P.t[0], P.t[1], P.hdr, P.lut_size, blockIdx.x - J.first[j]);
+}
+
+// Reset of every instance's header and digit histograms (one CTA each).
+__global__ void batch_reset_kernel(BatchDev b) {
+  const Plan& P = b.plans[blockIdx.x];
+  if (threadIdx.x == 0) {
+    DevHeader* h = P.hdr;
+    h->status = 0;
+    for (int i = 0; i < 8; ++i) h->ticket[i] = 0;
+    h->kmin[0] = h->kmin[1] = 0xffffffffu;
+    h->kmax[0] = h->kmax[1] = 0u;
+    h->num_runs[0] = h->num_runs[1] = 0;
+    h->num_groups = 0;
+    h->reduced_rows = 0;
+    h->jacobi_sweeps = 0;
+    h->bar_count = 0u;
+    h->bar_gen = 0u;
+    h->sweep_any[0] = h->sweep_any[1] = h->sweep_any[2] = 0u;
+  }
+  for (int t = 0; t < 2; ++t)
+    if (P.t[t].m > 0)
+      for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) P.t[t].hist[i] = 0u;
+}
+
 }  // namespace
+
+cudaError_t launch_batch_grouping(const BatchDev& b, const BatchJobs& tiles, const BatchJobs& match, cudaStream_t s) {
+  batch_reset_kernel<<<b.count, 256, 0, s>>>(b);
+  count_launches(1);
+  if (tiles.njobs > 0) {
+    static int granted[64] = {0};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= 64 || !granted[dev]) {
+      err = cudaFuncSetAttribute(sort_pass_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
+      if (err != cudaSuccess) return err;
+      if (dev >= 0 && dev < 64) granted[dev] = 1;
+    }
+    key_hist_batched<<<tiles.ctas, kSortThreads, 0, s>>>(b, tiles);
+    for (int pass = 0; pass < kMaxPasses; ++pass) {
+      if (pass > 0) tile_count_batched<<<tiles.ctas, kSortThreads, 0, s>>>(b, tiles, pass);
+      tile_scan_batched<<<tiles.njobs * kRadixBins, kRadixBins, 0, s>>>(b, tiles, pass);
+      sort_pass_batched<<<tiles.ctas, kSortThreads, kSortSmem, s>>>(b, tiles, pass);
+    }
+    run_count_batched<<<tiles.ctas, kSortThreads, 0, s>>>(b, tiles);
+    runs_batched<<<tiles.ctas, kSortThreads, 0, s>>>(b, tiles);
+    count_launches(3 + 3 * kMaxPasses - 1);
+  }
+  if (match.njobs > 0) {
+    match_batched<<<match.ctas, 256, 0, s>>>(b, match);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
 
 // Words of the grouping step per table: per-tile digit counts and offsets of
 // every pass (kMaxPasses x tiles x bins 64-bit words), and per-tile run counts.

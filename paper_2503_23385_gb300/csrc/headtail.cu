@@ -110,13 +110,9 @@ __device__ __forceinline__ double as_compute_double(const Tin* X, int64_t off) {
 // 1. chunk table and long-run pieces: one warp per chunk
 constexpr int kPlanWarps = kHtBlock / 32;
 template <typename Tin, typename Tc>
-__global__ void __launch_bounds__(kHtBlock) ht_plan_kernel(HtArgs a, int total) {
-  const int g = blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
+__device__ __forceinline__ void ht_plan_body(const HtTable& T, const int32_t* status, int k) {
   const int lane = threadIdx.x & 31;
-  if (g >= total || timed_out(a.status)) return;
-  const int t = g < a.c0 ? 0 : 1;
-  const int k = t ? g - a.c0 : g;
-  const HtTable& T = a.t[t];
+  if (timed_out(status)) return;
   int64_t lo = 0, hi = 0;
   if (lane == 0) {
     bool in0, in1;
@@ -164,16 +160,21 @@ __global__ void __launch_bounds__(kHtBlock) ht_plan_kernel(HtArgs a, int total) 
   }
 }
 
+template <typename Tin, typename Tc>
+__global__ void __launch_bounds__(kHtBlock) ht_plan_kernel(HtArgs a, int total) {
+  const int g = blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
+  if (g >= total) return;
+  const int t = g < a.c0 ? 0 : 1;
+  ht_plan_body<Tin, Tc>(a.t[t], a.status, t ? g - a.c0 : g);
+}
+
 // 2. carries: per (table, column), I_q = piece_q + (whole_q ? I_{q-1} : 0)
 // and carry_k = I_{k-1} for every chunk k that begins inside a run.
-__global__ void __launch_bounds__(kHtBlock) ht_scan_kernel(HtArgs a, int n0) {
+__device__ __forceinline__ void ht_scan_body(const HtTable& T, const int32_t* status, int c) {
   __shared__ double s_agg[kHtBlock];
   __shared__ int s_head[kHtBlock];
-  const int t = blockIdx.x < n0 ? 0 : 1;
-  const int c = t ? blockIdx.x - n0 : blockIdx.x;
-  const HtTable& T = a.t[t];
   const int K = T.chunks;
-  if (K == 0 || timed_out(a.status)) return;
+  if (K == 0 || timed_out(status)) return;
   const int n = T.n;
   const int per = (K + kHtBlock - 1) / kHtBlock;
   const int q0 = threadIdx.x * per, q1 = q0 + per < K ? q0 + per : K;
@@ -200,6 +201,11 @@ __global__ void __launch_bounds__(kHtBlock) ht_scan_kernel(HtArgs a, int n0) {
     I = ((T.cflag[q] & kWhole) ? I : 0.0) + value(q);
     if (q + 1 < K && (T.cflag[q + 1] & kInside)) T.carry[static_cast<int64_t>(q + 1) * n + c] = I;
   }
+}
+
+__global__ void __launch_bounds__(kHtBlock) ht_scan_kernel(HtArgs a, int n0) {
+  const int t = static_cast<int>(blockIdx.x) < n0 ? 0 : 1;
+  ht_scan_body(a.t[t], a.status, t ? blockIdx.x - n0 : blockIdx.x);
 }
 
 __device__ __forceinline__ float tail_weight(float mo, int j) {
@@ -383,14 +389,10 @@ __device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
 // those of the 8 consumer warps through shared memory.  V = 1: one column
 // per thread, any n.
 template <typename Tin, typename Tc, int V>
-__global__ void __launch_bounds__(kHtStreamThreads)
-    ht_stream_kernel(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1, HtArgs a,
-                     int g0, int g1, int64_t spin_limit) {
+__device__ __forceinline__ void ht_stream_body(const CUtensorMap* tm, const HtArgs& a, int t, int cb, int G,
+                                               int64_t spin_limit) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   unsigned char* sm = sm_raw + ((128u - (smem_addr(sm_raw) & 127u)) & 127u);
-  const int t = static_cast<int>(blockIdx.x) < g0 ? 0 : 1;
-  const int cb = t ? static_cast<int>(blockIdx.x) - g0 : static_cast<int>(blockIdx.x);
-  const int G = t ? g1 : g0;
   const HtTable& T = a.t[t];
   const int n = T.n;
   const HtStream L = ht_stream_layout(n, static_cast<int>(sizeof(Tin)), static_cast<int>(sizeof(Tc)));
@@ -462,7 +464,6 @@ __global__ void __launch_bounds__(kHtStreamThreads)
         cp_async(sb + L.info + r * 16, T.run_info + clamp_idx(seg_s[r], T.m) * 4, 16);
       if (T.gather) {
         // the rows, four per TMA gather (a short last group repeats its last row)
-        const CUtensorMap* tm = t ? &tm1 : &tm0;
         for (int g4 = lane; g4 * 4 < cnt; g4 += 32) {
           int rr[4];
 #pragma unroll
@@ -747,6 +748,15 @@ __global__ void __launch_bounds__(kHtStreamThreads)
   }
 }
 
+template <typename Tin, typename Tc, int V>
+__global__ void __launch_bounds__(kHtStreamThreads)
+    ht_stream_kernel(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1, HtArgs a,
+                     int g0, int g1, int64_t spin_limit) {
+  const int t = static_cast<int>(blockIdx.x) < g0 ? 0 : 1;
+  ht_stream_body<Tin, Tc, V>(t ? &tm1 : &tm0, a, t, t ? static_cast<int>(blockIdx.x) - g0 : static_cast<int>(blockIdx.x),
+                             t ? g1 : g0, spin_limit);
+}
+
 template <typename Tin, typename Tc>
 cudaError_t launch_typed_carry(const HtArgs& a, int total, int ncols, cudaStream_t s) {
   ht_plan_kernel<Tin, Tc><<<(total + kPlanWarps - 1) / kPlanWarps, kHtBlock, 0, s>>>(a, total);
@@ -817,38 +827,43 @@ cudaError_t launch_typed_main(HtArgs a, int num_sms, int64_t spin_limit, cudaStr
   return cudaGetLastError();
 }
 
-bool ht_vector_ok(int n, int64_t ld, const void* x, int in_f64) {
+__host__ __device__ inline bool ht_vector_ok(int n, int64_t ld, const void* x, int in_f64) {
   const int e = in_f64 ? 8 : 4;
   return ((n * e) % 16 == 0) && ((ld * e) % 16 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0);
 }
 
-HtArgs make_args(const Plan& p) {
+__host__ __device__ inline HtTable ht_table(const Plan& p, int t) {
+  const TableWork& W = p.t[t];
+  HtTable T{};
+  T.x = W.x;
+  T.ld = W.ld;
+  T.n = W.n;
+  T.m = W.m;
+  T.vec = W.m > 0 && ht_vector_ok(W.n, W.ld, W.x, W.in_f64);
+  T.gather = 0;
+  T.perm = W.perm;
+  T.seg = W.seg;
+  T.run_off = W.run_off;
+  T.other = W.other;
+  T.hdslot = W.hdslot;
+  T.run_info = W.run_info;
+  T.tail = W.tail;
+  T.head_col0 = t == 0 ? 0 : p.n1;
+  T.zero_col0 = t == 0 ? p.n1 : 0;
+  T.zero_n = t == 0 ? p.n2 : 0;
+  T.L = W.chunk_rows;
+  T.chunks = W.m > 0 ? W.chunks : 0;
+  T.cbeg = W.cbeg;
+  T.cflag = W.cflag;
+  T.piece = W.piece;
+  T.carry = W.carry;
+  return T;
+}
+
+__host__ __device__ inline HtArgs make_args(const Plan& p) {
   HtArgs a{};
-  for (int t = 0; t < 2; ++t) {
-    const TableWork& W = p.t[t];
-    HtTable& T = a.t[t];
-    T.x = W.x;
-    T.ld = W.ld;
-    T.n = W.n;
-    T.m = W.m;
-    T.vec = W.m > 0 && ht_vector_ok(W.n, W.ld, W.x, W.in_f64);
-    T.perm = W.perm;
-    T.seg = W.seg;
-    T.run_off = W.run_off;
-    T.other = W.other;
-    T.hdslot = W.hdslot;
-    T.run_info = W.run_info;
-    T.tail = W.tail;
-    T.head_col0 = t == 0 ? 0 : p.n1;
-    T.zero_col0 = t == 0 ? p.n1 : 0;
-    T.zero_n = t == 0 ? p.n2 : 0;
-    T.L = W.chunk_rows;
-    T.chunks = W.m > 0 ? W.chunks : 0;
-    T.cbeg = W.cbeg;
-    T.cflag = W.cflag;
-    T.piece = W.piece;
-    T.carry = W.carry;
-  }
+  a.t[0] = ht_table(p, 0);
+  a.t[1] = ht_table(p, 1);
   a.c0 = a.t[0].chunks;
   a.head = p.head;
   a.ld_head = p.n;
@@ -857,7 +872,83 @@ HtArgs make_args(const Plan& p) {
   return a;
 }
 
+// 4-column consumers: a width of 4 x a power of two <= 128 and 16-byte aligned tail rows.
+__host__ __device__ inline bool ht_v4_ok(const HtTable& T) {
+  const int cg = T.n / 4;
+  return T.n % 4 == 0 && cg >= 1 && cg <= 32 && (cg & (cg - 1)) == 0 &&
+         (reinterpret_cast<uintptr_t>(T.tail) & 15u) == 0;
+}
+
+// ---- batched forms: jobs are (instance, table); aux = table
+// chunk plan: first[] counts chunks, one warp per chunk
+template <typename Tin, typename Tc>
+__global__ void __launch_bounds__(kHtBlock) ht_plan_batched(BatchDev b, BatchJobs J, int total) {
+  const int g = blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
+  if (g >= total) return;
+  const int j = batch_job(J, g);
+  const Plan& P = b.plans[J.inst[j]];
+  const HtTable T = ht_table(P, J.aux[j]);
+  ht_plan_body<Tin, Tc>(T, &P.hdr->status, g - J.first[j]);
+}
+
+// carries: first[] counts columns, one CTA per column
+__global__ void __launch_bounds__(kHtBlock) ht_scan_batched(BatchDev b, BatchJobs J) {
+  const int j = batch_job(J, blockIdx.x);
+  const Plan& P = b.plans[J.inst[j]];
+  const HtTable T = ht_table(P, J.aux[j]);
+  ht_scan_body(T, &P.hdr->status, blockIdx.x - J.first[j]);
+}
+
+// streaming pass: first[] counts CTAs; rows are copied with cp.async (no TMA)
+template <typename Tin, typename Tc, int V>
+__global__ void __launch_bounds__(kHtStreamThreads) ht_stream_batched(BatchDev b, BatchJobs J) {
+  __shared__ HtArgs s_a;
+  const int j = batch_job(J, blockIdx.x);
+  const Plan& P = b.plans[J.inst[j]];
+  if (threadIdx.x == 0) s_a = make_args(P);
+  __syncthreads();
+  ht_stream_body<Tin, Tc, V>(nullptr, s_a, J.aux[j], blockIdx.x - J.first[j], J.first[j + 1] - J.first[j],
+                             P.spin_limit);
+}
+
+template <typename Tin, typename Tc>
+cudaError_t launch_batch_ht_typed(const BatchDev& b, const BatchJobs& plan, int plan_total, const BatchJobs& scan,
+                                  const BatchJobs* stream, const int* smem, cudaStream_t s) {
+  if (plan.njobs > 0) {
+    ht_plan_batched<Tin, Tc><<<(plan_total + kPlanWarps - 1) / kPlanWarps, kHtBlock, 0, s>>>(b, plan, plan_total);
+    ht_scan_batched<<<scan.ctas, kHtBlock, 0, s>>>(b, scan);
+    count_launches(2);
+  }
+  for (int v = 0; v < 2; ++v) {
+    if (stream[v].njobs == 0) continue;
+    auto kern = v == 0 ? ht_stream_batched<Tin, Tc, 4> : ht_stream_batched<Tin, Tc, 1>;
+    if (smem[v] > 48 * 1024) {
+      cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem[v]);
+      if (err != cudaSuccess) return err;
+    }
+    kern<<<stream[v].ctas, kHtStreamThreads, smem[v], s>>>(b, stream[v]);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+void ht_batch_table(const Plan& p, int t, int* variant, int* smem, int* chunks) {
+  const HtTable T = ht_table(p, t);
+  *chunks = T.chunks;
+  *variant = ht_v4_ok(T) ? 0 : 1;
+  const int ein = p.t[t].in_f64 ? 8 : 4, ec = p.mixed ? 4 : 8;
+  *smem = T.chunks > 0 ? ht_stream_layout(T.n, ein, ec).bytes : 0;
+}
+
+cudaError_t launch_batch_ht(const BatchDev& b, const BatchJobs& plan, int plan_total, const BatchJobs& scan,
+                            const BatchJobs stream[2], const int smem[2], int in_f64, int mixed, cudaStream_t s) {
+  if (in_f64) return mixed ? launch_batch_ht_typed<double, float>(b, plan, plan_total, scan, stream, smem, s)
+                           : launch_batch_ht_typed<double, double>(b, plan, plan_total, scan, stream, smem, s);
+  return mixed ? launch_batch_ht_typed<float, float>(b, plan, plan_total, scan, stream, smem, s)
+               : launch_batch_ht_typed<float, double>(b, plan, plan_total, scan, stream, smem, s);
+}
 
 // Chunk spacing L for a table of width n: the largest power of two in
 // [16, 512] with (2 L - 1) rows of input (and output, when its type differs)

@@ -117,6 +117,42 @@ struct Plan {
   double* sigw = nullptr;                     // 2n: unsorted singular values, FP32-sweep column norms
 };
 
+// Batched execution (figaro_batch_join): every instance's plan sits in device
+// memory, and each batched launch gets a job list that maps its CTAs to
+// (instance, CTA within the job): job j owns CTAs [first[j], first[j+1]).
+struct BatchJobs {
+  const int32_t* first;  // njobs + 1
+  const int32_t* inst;   // njobs: instance index
+  const int32_t* aux;    // njobs: job detail (table, Gram block, ...)
+  int njobs;
+  int ctas;              // first[njobs]
+};
+
+// Per-instance outputs of a batch.
+struct BatchOut {
+  double* R;             // n x n, leading dimension n (device), or null
+  double* sigma;         // n (device), or null
+};
+
+struct BatchDev {
+  const Plan* plans;     // count plans (device)
+  const BatchOut* out;   // count outputs (device)
+  int count;
+};
+
+// Job j of a launch for CTA b (binary search over first[]).
+__device__ __forceinline__ int batch_job(const BatchJobs& J, int b) {
+  int lo = 0, hi = J.njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (J.first[mid] <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // cuTensorMapEncodeTiled from the driver (null when unavailable).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
@@ -140,6 +176,29 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s);
 cudaError_t launch_chol_first(const Plan& p, cudaStream_t s);
 cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);
 cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
+
+// Batched launchers: every instance of a batch in one launch per phase.
+//   tiles: one job per (instance, table with rows), CTAs = radix tiles, aux = table
+//   match: one job per instance, CTAs = ceil(max(m1, m2) / 256)
+cudaError_t launch_batch_grouping(const BatchDev& b, const BatchJobs& tiles, const BatchJobs& match, cudaStream_t s);
+//   head/tail: plan jobs count chunks (plan_total in all), scan jobs count
+//   columns, stream[0] / stream[1] are the 4-column / scalar-path tables
+//   (CTAs per table), smem[] their dynamic shared memory
+void ht_batch_table(const Plan& p, int t, int* variant, int* smem, int* chunks);
+cudaError_t launch_batch_ht(const BatchDev& b, const BatchJobs& plan, int plan_total, const BatchJobs& scan,
+                            const BatchJobs stream[2], const int smem[2], int in_f64, int mixed, cudaStream_t s);
+
+//   Gram (CUDA cores): by_tpt[v] = (instance, block) jobs of variant v with
+//   the block's CTAs (aux = block), reduce = one job per instance
+void gram_batch_block(const Plan& p, int pass, int b, int* variant, int* ctas, size_t* smem);
+cudaError_t launch_batch_gram(const BatchDev& b, int pass, const BatchJobs by_tpt[4], const size_t smem[4],
+                              const BatchJobs& reduce, int mixed, cudaStream_t s);
+
+//   dense n x n steps (step 1, 2, 3 = first Cholesky, second Cholesky + R,
+//   Jacobi): one CTA per instance, jobs[v] the instances of variant v
+void dense_batch_info(const Plan& p, int step, int* variant, size_t* smem, int* threads);
+cudaError_t launch_batch_dense(const BatchDev& b, int step, const BatchJobs jobs[3], const size_t smem[3],
+                               const int threads[3], int mixed, cudaStream_t s);
 
 // Wide path (wide.cu).
 int64_t wide_gram_jobs(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms);
