@@ -38,6 +38,8 @@ WORKLOADS = {
     "c0": "1000+1000 rows x 4+4 FP64 U[-1,1], 100 keys",
     "c4": "2e5+2e5 rows x 256+256 FP32, B column-scaled to condition 1e8, int32 keys uniform over 100 ids "
           "(join ~4e8 x 512)",
+    "c3": "512 independent instances, m1, m2 log-uniform in [1e3, 1e5], n1, n2 from {8, 16, 32, 64}, FP32 N(0,1), "
+          "int32 keys uniform over max(1, min(m1, m2) / 10) ids; one batched call replayed as a CUDA graph",
 }
 
 
@@ -170,6 +172,24 @@ def oracle_rows_per_s(A, B, sample_keys):
     return rows / dt, dt, rows, oracle.join_rows(ak, bk)
 
 
+def oracle_batch_rows_per_s(instances, budget_s):
+    """The oracle (O1) on whole instances of a batch, in order, until about
+    budget_s seconds have passed."""
+    import oracle
+    t0 = time.perf_counter()
+    rows, used, jrows = 0, 0, 0
+    for A, B in instances:
+        R = oracle.join_r_materialized(A.x, A.key, B.x, B.key)
+        oracle.jacobi_sigma(R)
+        rows += A.m + B.m
+        jrows += oracle.join_rows(A.key, B.key)
+        used += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return rows / dt, dt, rows, used, jrows
+
+
 def default_sample_keys(cfg, reference_arm=False):
     """Key ids in the oracle's sample: about 15 s of single-core work for the
     cpu_baseline leg, about 4 s per step for the reference arm."""
@@ -183,6 +203,25 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from workloads import config
+    if args.config == "c3":
+        inst = config("c3")
+        for _ in range(args.warmup):
+            oracle_batch_rows_per_s(inst[:1], 0.0)
+        times, rows, used = [], 0, 0
+        for _ in range(args.steps):
+            rps, dt, rows, used, jrows = oracle_batch_rows_per_s(inst, 4.0)
+            times.append(dt)
+        ms = 1e3 * sum(times) / len(times)
+        value = rows / (ms / 1e3)
+        sample = f"the first {used} of the 512 instances ({rows} input rows, {jrows} join rows) per step"
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.config], "path": "oracle O1 per instance"},
+                "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     A, B = config(args.config)
     keys = args.cpu_sample_keys or default_sample_keys(args.config, reference_arm=True)
     for _ in range(args.warmup):
@@ -224,6 +263,11 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
+    if args.config == "c3":
+        run_batch(args, rank, world, torch, dist, fg, dev, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     A, B = config(args.config, rank=rank)
     rows = A.m + B.m
@@ -384,6 +428,154 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batch(args, rank, world, torch, dist, fg, dev, local):
+    """The batching workload: 512 independent instances in one
+    figaro_batch_join call (one launch per phase for all of them), captured
+    once in a CUDA graph and replayed every step.  The instances' tables are
+    views of two flat device buffers, so that the end-to-end leg moves them
+    with one host-to-device copy each and reads all outputs back with one
+    device-to-host copy."""
+    from workloads import config
+    inst = config("c3", rank=rank)
+    rows = sum(A.m + B.m for A, B in inst)
+    xs = np.concatenate([T.x.reshape(-1) for AB in inst for T in AB])
+    ks = np.concatenate([T.key for AB in inst for T in AB])
+    x_dev = torch.from_numpy(xs).to(dev)
+    k_dev = torch.from_numpy(ks).to(dev)
+    pairs, xo, ko = [], 0, 0
+    for A, B in inst:
+        pr = []
+        for T in (A, B):
+            pr.append((x_dev[xo:xo + T.m * T.n].view(T.m, T.n), k_dev[ko:ko + T.m]))
+            xo += T.m * T.n
+            ko += T.m
+        pairs.append(tuple(pr))
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(fg.NUM_PHASE_EVENTS)]
+    ev_arr = fg.event_array(evs)
+    # the first call tunes the schedule on this batch (outside the capture)
+    solver = fg.BatchSolver(pairs, path=args.path, flags=fg.FLAG_AUTOTUNE)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            solver(stream=stream, phase_events=ev_arr)
+    st = solver.status(stream)
+    if st != 0:
+        raise fg.FigaroError(st, "warm-up")
+    launches_before = fg.kernel_launches()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        solver(stream=stream, phase_events=ev_arr)
+    launches_per_step = fg.kernel_launches() - launches_before
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, phase_ms = [], [[] for _ in range(fg.NUM_PHASE_EVENTS - 1)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.fill_(1)
+                s0.record(stream)
+                graph.replay()
+                s1.record(stream)
+                s1.synchronize()
+                step_ms.append(s0.elapsed_time(s1))
+                for i in range(fg.NUM_PHASE_EVENTS - 1):
+                    phase_ms[i].append(evs[i].elapsed_time(evs[i + 1]))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    clocks = clk.summary()
+    st = solver.status(stream)
+    if st != 0:
+        raise fg.FigaroError(st, "timed steps")
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    ms_per_step = total_ms / args.steps
+    value = job_throughput(rows, world, ms_per_step)
+    phases = {name: statistics.mean(v) for name, v in zip(fg.PHASES, phase_ms)}
+    hbm, peak_kind = measured_peaks()
+    s_c = 4 if args.path == "mixed" else 8
+    # head/tail (both tables of every instance, carry pre-pass included)
+    ht_bytes = sum(T.m * (4 + 4 + T.n * T.x.itemsize + T.n * s_c) for AB in inst for T in AB)
+    ht_ms = phases["head_tail"]
+    achieved = ht_bytes / (ht_ms / 1e3) / 1e9
+    roofline = {"kernel": "ht_plan/ht_scan/ht_stream_batched (all instances)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "bytes_per_launch": ht_bytes,
+                "peak_source": peak_kind}
+    # ---- end to end: inputs from pinned host memory, every R and sigma back
+    e2e = None
+    try:
+        hx = torch.from_numpy(xs).pin_memory()
+        hk = torch.from_numpy(ks).pin_memory()
+        out_elems = sum(R.numel() + sg.numel() for R, sg in solver.outs)
+        hout = torch.empty(out_elems, dtype=torch.float64).pin_memory()
+        e_ms = []
+        with torch.cuda.stream(stream):
+            for it in range(max(3, min(args.steps, 10)) + 1):
+                s0.record(stream)
+                x_dev.copy_(hx, non_blocking=True)
+                k_dev.copy_(hk, non_blocking=True)
+                graph.replay()
+                flat = torch.cat([t.reshape(-1) for R, sg in solver.outs for t in (R, sg)])
+                hout.copy_(flat, non_blocking=True)
+                s1.record(stream)
+                s1.synchronize()
+                if it > 0:
+                    e_ms.append(s0.elapsed_time(s1))
+        em = statistics.mean(e_ms)
+        e2e = {"value": world * rows / (em / 1e3), "unit": "rows/s", "h2d_bytes_per_step": xs.nbytes + ks.nbytes,
+               "d2h_bytes_per_step": out_elems * 8, "ms_per_step": em}
+    except Exception as exc:
+        e2e = {"error": repr(exc)}
+    # ---- the plain FP64 path, mixed-vs-FP64 error over all instances
+    fp64 = None
+    if args.path == "mixed" and args.fp64_steps > 0:
+        try:
+            s64 = fg.BatchSolver(pairs, path="fp64")
+            with torch.cuda.stream(stream):
+                s64(stream=stream)
+                stream.synchronize()
+                f_ms = []
+                for _ in range(args.fp64_steps):
+                    flush.fill_(1)
+                    s0.record(stream)
+                    s64(stream=stream)
+                    s1.record(stream)
+                    s1.synchronize()
+                    f_ms.append(s0.elapsed_time(s1))
+            fm = statistics.mean(f_ms)
+            eR = max(float(torch.linalg.norm(R - R64) / torch.linalg.norm(R64))
+                     for (R, _), (R64, _) in zip(solver.outs, s64.outs))
+            es = max(float(torch.linalg.norm(sg - s6) / torch.linalg.norm(s6))
+                     for (_, sg), (_, s6) in zip(solver.outs, s64.outs))
+            fp64 = {"value": world * rows / (fm / 1e3), "unit": "rows/s", "ms_per_step": fm,
+                    "mixed_vs_fp64_max_rel_err_R": eR, "mixed_vs_fp64_max_rel_err_sigma": es,
+                    "timing": "direct call (host plan building included), not a graph replay"}
+            del s64
+        except Exception as exc:
+            fp64 = {"error": repr(exc)}
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        rps, dt, srows, used, jrows = oracle_batch_rows_per_s(inst, 12.0)
+        cpu = {"value": rps, "unit": "rows/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first {used} of the 512 instances: {srows} input rows, {jrows} join rows, {dt:.1f} s "
+                         f"(O1: materialised join, Householder QR, one-sided Jacobi, per instance)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.path == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOADS["c3"], "path": args.path, "rows_per_gpu": rows, "graph": True,
+                           "instances": len(inst), "schedule (autotuned)": solver.schedule(),
+                           "l2": f"inputs {(xs.nbytes + ks.nbytes) / 1e9:.1f} GB exceed L2; 256 MB flush between steps"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+                "clocks": clocks, "phases_ms": phases, "fp64_path": fp64}
+        print(json.dumps(line), flush=True)
 
 
 def materialized_baseline(torch, A, B, dev, stream):

@@ -90,7 +90,12 @@ enum {
    * 16 or 32): the Gram's producer never loads its first tile, so the
    * workers' bounded wait runs out (after about spin_limit / 16 suspended
    * polls) and the call records FIGARO_ERR_DEVICE_TIMEOUT. */
-  FIGARO_FLAG_TEST_WITHHOLD = 1 << 8
+  FIGARO_FLAG_TEST_WITHHOLD = 1 << 8,
+  /* figaro_batch_join: when the batch's shape class has no tuned schedule
+   * yet, time the candidate schedules on this batch first (the call then
+   * waits for the stream; it must not be made during stream capture, where
+   * the flag is ignored) and keep the fastest for later calls. */
+  FIGARO_FLAG_AUTOTUNE = 1 << 2
 };
 
 typedef struct figaro_table {
@@ -227,7 +232,18 @@ FIGARO_API figaro_status figaro_join_singular_values_fixed(const figaro_table* A
  * Batched form: `count` independent instances (A[i], B[i]) with their own
  * shapes, each writing R[i] (n_i x n_i, leading dimension n_i) and sigma[i].
  * R and sigma are host arrays of `count` device pointers (entries may be
- * NULL to skip an output).  One workspace covers the whole batch.
+ * NULL to skip an output; an instance with neither is skipped).  One
+ * workspace covers the whole batch: its front holds the instances' plans and
+ * job lists, the rest one workspace per instance.
+ *
+ * Instances with n_i <= 128, device-resident tables and device outputs run
+ * together, one launch per phase for the whole batch (grouping, head/tail,
+ * each Gram pass, each dense step), the Gram products on CUDA cores; the
+ * plans reach the device as kernel arguments, so the call can be captured in
+ * a CUDA graph and replayed.  Other instances (wider joins, host memory) run
+ * one after another in the same call.  figaro_options.phase_events, when
+ * set, is recorded around the batched phases.  Device-side status is
+ * recorded per instance, in that instance's part of the workspace.
  */
 FIGARO_API figaro_status figaro_batch_workspace_size(int32_t count, const figaro_table* A, const figaro_table* B,
                                           const figaro_options* opt, size_t* bytes);
@@ -235,6 +251,20 @@ FIGARO_API figaro_status figaro_batch_workspace_size(int32_t count, const figaro
 FIGARO_API figaro_status figaro_batch_join(int32_t count, const figaro_table* A, const figaro_table* B,
                                 const figaro_options* opt, double* const* R, double* const* sigma, void* ws,
                                 size_t ws_bytes, void* stream);
+
+/* The schedule figaro_batch_join uses for these shapes and options: rows of
+ * a Gram block per CTA and the head/tail CTA budget per SM, as tuned by an
+ * earlier FIGARO_FLAG_AUTOTUNE call of the same shape class (instances,
+ * path, and the batch's input rows and summed widths rounded down to powers
+ * of two), else the defaults (4096 rows, 2 CTAs per SM).  Host only.        */
+FIGARO_API figaro_status figaro_batch_schedule(int32_t count, const figaro_table* A, const figaro_table* B,
+                                    const figaro_options* opt, int64_t* gram_rows_per_cta, int32_t* ht_ctas_per_sm);
+
+/* Waits for `stream`, then returns the first non-OK device-side status the
+ * instances of the last figaro_batch_join on workspace `ws` recorded (same
+ * count, tables and options as that call), else FIGARO_OK.                 */
+FIGARO_API figaro_status figaro_batch_get_status(int32_t count, const figaro_table* A, const figaro_table* B,
+                                      const figaro_options* opt, const void* ws, void* stream);
 
 /* Waits for `stream`, then returns the device-side status the last call
  * using workspace `ws` recorded (FIGARO_OK when nothing went wrong).        */

@@ -21,6 +21,7 @@ __all__ = [
     "workspace_size", "join_group", "join_head_tail", "join_qr_r", "join_singular_values", "join_qr_svd",
     "join_qr_svd_host", "batch_join", "get_status", "Solver", "STATUS_NAMES", "event_array", "kernel_launches",
     "host_workspace_size", "PHASES", "NUM_PHASE_EVENTS", "join_singular_values_fixed", "FIXED_SCRATCH_BYTES",
+    "BatchSolver", "FLAG_AUTOTUNE",
 ]
 
 PATH_FP64, PATH_MIXED = 0, 1
@@ -28,6 +29,7 @@ GRAM_AUTO, GRAM_SIMT, GRAM_TCGEN05 = 0, 1, 2
 F32, F64 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 FLAG_HOST_OUTPUT = 1
+FLAG_AUTOTUNE = 1 << 2
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "WORKSPACE_TOO_SMALL", 3: "CUDA", 4: "NOT_SPD",
                 5: "NO_CONVERGENCE", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED"}
 
@@ -400,6 +402,56 @@ def batch_join(pairs, stream=None, workspace=None, **opts):
     _check(lib.figaro_batch_join(count, TA, TB, ctypes.byref(o), Rp, Sp, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                  _stream_handle(stream)), "figaro_batch_join")
     return outs, ws
+
+
+class BatchSolver:
+    """Reusable workspace and outputs for repeated batched calls with fixed
+    shapes (figaro_batch_join): nothing is allocated per call, so a call can
+    be captured in a CUDA graph and replayed."""
+
+    def __init__(self, pairs, **opts):
+        torch = _torch()
+        self.lib = library()
+        self.opts = opts
+        self.count = len(pairs)
+        self.TA = (Table * max(self.count, 1))(*[_device_table(*a) for a, _ in pairs])
+        self.TB = (Table * max(self.count, 1))(*[_device_table(*b) for _, b in pairs])
+        o = _options(**opts)
+        need = ctypes.c_size_t(0)
+        _check(self.lib.figaro_batch_workspace_size(self.count, self.TA, self.TB, ctypes.byref(o), ctypes.byref(need)),
+               "figaro_batch_workspace_size")
+        dev = pairs[0][0][0].device if self.count else torch.device("cuda")
+        self.ws = _workspace(need.value, dev)
+        self.outs = []
+        self.Rp = (ctypes.c_void_p * max(self.count, 1))()
+        self.Sp = (ctypes.c_void_p * max(self.count, 1))()
+        for i, (a, b) in enumerate(pairs):
+            n = a[0].shape[1] + b[0].shape[1]
+            R = torch.zeros((n, n), dtype=torch.float64, device=dev)
+            sg = torch.zeros(n, dtype=torch.float64, device=dev)
+            self.outs.append((R, sg))
+            self.Rp[i], self.Sp[i] = R.data_ptr(), sg.data_ptr()
+
+    def __call__(self, stream=None, phase_events=None):
+        o = _options(phase_events=phase_events, **self.opts)
+        _check(self.lib.figaro_batch_join(self.count, self.TA, self.TB, ctypes.byref(o), self.Rp, self.Sp,
+                                          ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), _stream_handle(stream)),
+               "figaro_batch_join")
+        return self.outs
+
+    def schedule(self) -> dict:
+        """The batch schedule in use (tuned by a FLAG_AUTOTUNE call, else the defaults)."""
+        o = _options(**self.opts)
+        rpc, hts = ctypes.c_int64(0), ctypes.c_int32(0)
+        _check(self.lib.figaro_batch_schedule(self.count, self.TA, self.TB, ctypes.byref(o), ctypes.byref(rpc),
+                                              ctypes.byref(hts)), "figaro_batch_schedule")
+        return {"gram_rows_per_cta": int(rpc.value), "ht_ctas_per_sm": int(hts.value)}
+
+    def status(self, stream=None) -> int:
+        """Waits for the stream; the first non-OK device status among the instances."""
+        o = _options(**self.opts)
+        return int(self.lib.figaro_batch_get_status(self.count, self.TA, self.TB, ctypes.byref(o),
+                                                    ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream)))
 
 
 def get_info(workspace, stream=None) -> dict:

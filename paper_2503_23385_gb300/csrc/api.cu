@@ -5,7 +5,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/figaro.h"
@@ -415,10 +417,25 @@ BatchJobs stage_jobs(Blob& blob, const JobList& L, std::vector<std::pair<BatchJo
   return J;
 }
 
+// The schedule of a batched call: rows of a Gram block per CTA, and the
+// head/tail CTA budget in multiples of the SM count.
+struct BatchSchedule {
+  int64_t gram_rows_per_cta = 4096;
+  int ht_ctas_per_sm = 2;
+};
+
 figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>& outs, char* area, size_t area_bytes,
-                          cudaStream_t s) {
+                          cudaStream_t s, void* const* phase_events, const BatchSchedule& sched) {
   const int count = static_cast<int>(calls.size());
   if (count == 0) return FIGARO_OK;
+  // Gram grids from the schedule (never above the partial buffers the plans reserved)
+  for (Call& c : calls) {
+    const int64_t rows[3] = {c.p.t[0].m, c.p.t[0].m, c.p.t[1].m};
+    for (int b = 0; b < 3; ++b) {
+      const int64_t g = (rows[b] + sched.gram_rows_per_cta - 1) / sched.gram_rows_per_cta;
+      c.p.ggrid[b] = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, c.p.ggrid[b])));
+    }
+  }
   const Plan& p0 = calls[0].p;
   const int mixed = p0.mixed, in_f64 = p0.t[0].in_f64;
   // ---- job lists
@@ -430,7 +447,7 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   int64_t total_chunks = 0;
   for (int i = 0; i < count; ++i)
     for (int t = 0; t < 2; ++t) total_chunks += calls[i].p.t[t].m > 0 ? calls[i].p.t[t].chunks : 0;
-  const int64_t gtot = 2 * static_cast<int64_t>(p0.num_sms);
+  const int64_t gtot = static_cast<int64_t>(sched.ht_ctas_per_sm) * p0.num_sms;
   for (int i = 0; i < count; ++i) {
     const Plan& p = calls[i].p;
     for (int t = 0; t < 2; ++t) {
@@ -506,17 +523,137 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   b.plans = reinterpret_cast<const Plan*>(area + off_plans);
   b.out = reinterpret_cast<const BatchOut*>(area + off_outs);
   b.count = count;
-  // ---- the phases
+  // ---- the phases (with the phase events of single calls; the head/tail
+  // carry and streaming launches share one interval)
+  Call ev;
+  ev.s = s;
+  if (phase_events) {
+    ev.events = true;
+    for (int i = 0; i < FIGARO_NUM_PHASE_EVENTS; ++i) ev.ev[i] = static_cast<cudaEvent_t>(phase_events[i]);
+  }
+  FIGARO_TRY(ev.mark(0));
   FIGARO_TRY(launch_batch_grouping(b, Jtiles, Jmatch, s));
+  FIGARO_TRY(ev.mark(1));
+  FIGARO_TRY(ev.mark(2));
   FIGARO_TRY(launch_batch_ht(b, Jplan, Jplan.ctas, Jscan, Jstream, ht_smem, in_f64, mixed, s));
+  FIGARO_TRY(ev.mark(3));
   FIGARO_TRY(launch_batch_gram(b, 1, Jgram[0], gram_smem[0], Jreduce, mixed, s));
+  FIGARO_TRY(ev.mark(4));
   FIGARO_TRY(launch_batch_dense(b, 1, Jd[0], dsm[0], dthr[0], mixed, s));
+  FIGARO_TRY(ev.mark(5));
   FIGARO_TRY(launch_batch_gram(b, 2, Jgram[1], gram_smem[1], Jreduce, mixed, s));
+  FIGARO_TRY(ev.mark(6));
   FIGARO_TRY(launch_batch_dense(b, 2, Jd[1], dsm[1], dthr[1], mixed, s));
+  FIGARO_TRY(ev.mark(7));
   FIGARO_TRY(launch_batch_dense(b, 3, Jd[2], dsm[2], dthr[2], mixed, s));
+  FIGARO_TRY(ev.mark(8));
   return FIGARO_OK;
 }
 
+
+// ------------------------------------------------------------ autotuner ----
+//
+// A batch's schedule is chosen by timing candidates on the batch itself
+// (FIGARO_FLAG_AUTOTUNE, outside stream capture): rows per Gram CTA from
+// {1024, ..., 32768} with the Gram passes timed, then head/tail CTA budgets
+// of {1, 2, 4, 8} x the SM count with the head/tail phase timed.  The
+// fastest values are kept in a process-wide cache keyed by the batch's
+// shape class (instances, path, input rows and summed widths, each rounded
+// to a power of two) and used by every later call of that class.
+
+struct TuneKey {
+  int count, path, in_f64;
+  int rows_log2, width_log2;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(count, path, in_f64, rows_log2, width_log2) <
+           std::tie(o.count, o.path, o.in_f64, o.rows_log2, o.width_log2);
+  }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, BatchSchedule> g_tuned;
+
+int ilog2(int64_t v) {
+  int r = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++r;
+  }
+  return r;
+}
+
+TuneKey tune_key(const std::vector<Call>& calls) {
+  int64_t rows = 0, widths = 0;
+  for (const Call& c : calls) {
+    rows += c.p.t[0].m + c.p.t[1].m;
+    widths += c.p.n;
+  }
+  TuneKey k{};
+  k.count = static_cast<int>(calls.size());
+  k.path = calls.empty() ? 0 : calls[0].p.mixed;
+  k.in_f64 = calls.empty() ? 0 : calls[0].p.t[0].in_f64;
+  k.rows_log2 = ilog2(rows + 1);
+  k.width_log2 = ilog2(widths + 1);
+  return k;
+}
+
+// Milliseconds between phase events a and b of one batched run.
+figaro_status time_batched(std::vector<Call> calls, const std::vector<BatchOut>& outs, char* area, size_t area_bytes,
+                           cudaStream_t s, const BatchSchedule& sched, int a, int b, float* ms) {
+  cudaEvent_t ev[FIGARO_NUM_PHASE_EVENTS];
+  for (int i = 0; i < FIGARO_NUM_PHASE_EVENTS; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) return FIGARO_ERR_CUDA;
+  void* evp[FIGARO_NUM_PHASE_EVENTS];
+  for (int i = 0; i < FIGARO_NUM_PHASE_EVENTS; ++i) evp[i] = ev[i];
+  figaro_status st = run_batched(calls, outs, area, area_bytes, s, evp, sched);
+  if (st == FIGARO_OK && cudaStreamSynchronize(s) != cudaSuccess) st = FIGARO_ERR_CUDA;
+  if (st == FIGARO_OK && cudaEventElapsedTime(ms, ev[a], ev[b]) != cudaSuccess) st = FIGARO_ERR_CUDA;
+  for (int i = 0; i < FIGARO_NUM_PHASE_EVENTS; ++i) cudaEventDestroy(ev[i]);
+  return st;
+}
+
+figaro_status tune_batch(const std::vector<Call>& calls, const std::vector<BatchOut>& outs, char* area,
+                         size_t area_bytes, cudaStream_t s, BatchSchedule* best) {
+  BatchSchedule cur;
+  // warm the kernels once so that no candidate pays first-launch costs
+  float ms = 0.f;
+  figaro_status st = time_batched(calls, outs, area, area_bytes, s, cur, 0, 8, &ms);
+  if (st != FIGARO_OK) return st;
+  float best_ms = 1e30f;
+  for (int64_t rpc = 1024; rpc <= 32768; rpc *= 2) {
+    BatchSchedule c = cur;
+    c.gram_rows_per_cta = rpc;
+    float g1 = 0.f, g2 = 0.f;
+    st = time_batched(calls, outs, area, area_bytes, s, c, 3, 4, &g1);
+    if (st == FIGARO_OK) st = time_batched(calls, outs, area, area_bytes, s, c, 5, 6, &g2);
+    if (st != FIGARO_OK) return st;
+    if (g1 + g2 < best_ms) {
+      best_ms = g1 + g2;
+      cur.gram_rows_per_cta = rpc;
+    }
+  }
+  best_ms = 1e30f;
+  const int ht_candidates[4] = {1, 2, 4, 8};
+  for (int h : ht_candidates) {
+    BatchSchedule c = cur;
+    c.ht_ctas_per_sm = h;
+    float t = 0.f;
+    st = time_batched(calls, outs, area, area_bytes, s, c, 2, 3, &t);
+    if (st != FIGARO_OK) return st;
+    if (t < best_ms) {
+      best_ms = t;
+      cur.ht_ctas_per_sm = h;
+    }
+  }
+  *best = cur;
+  return FIGARO_OK;
+}
+
+BatchSchedule schedule_for(const std::vector<Call>& calls) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(tune_key(calls));
+  return it == g_tuned.end() ? BatchSchedule{} : it->second;
+}
 }  // namespace
 }  // namespace figaro
 
@@ -702,10 +839,64 @@ figaro_status figaro_batch_join(int32_t count, const figaro_table* A, const figa
     // every batched instance was prepared on the workspace's device
     st = bind_device(area);
     if (st != FIGARO_OK) return st;
-    st = run_batched(batched, outs, area, area_bytes, s);
+    BatchSchedule sched = schedule_for(batched);
+    if (opt && (opt->flags & FIGARO_FLAG_AUTOTUNE)) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return FIGARO_ERR_CUDA;
+      if (cs == cudaStreamCaptureStatusNone) {
+        const TuneKey key = tune_key(batched);
+        bool have = false;
+        {
+          std::lock_guard<std::mutex> lock(g_tune_mu);
+          have = g_tuned.count(key) != 0;
+        }
+        if (!have) {
+          st = tune_batch(batched, outs, area, area_bytes, s, &sched);
+          if (st != FIGARO_OK) return st;
+          std::lock_guard<std::mutex> lock(g_tune_mu);
+          g_tuned[key] = sched;
+        }
+      }
+    }
+    st = run_batched(batched, outs, area, area_bytes, s, opt ? opt->phase_events : nullptr, sched);
     if (st != FIGARO_OK) return st;
   }
   return FIGARO_OK;
+}
+
+figaro_status figaro_batch_schedule(int32_t count, const figaro_table* A, const figaro_table* B,
+                                    const figaro_options* opt, int64_t* gram_rows_per_cta, int32_t* ht_ctas_per_sm) {
+  if (count < 0 || (count > 0 && (!A || !B)) || !gram_rows_per_cta || !ht_ctas_per_sm) return FIGARO_ERR_INVALID_ARG;
+  std::vector<Call> calls;
+  for (int32_t i = 0; i < count; ++i) {
+    figaro_status st = check_pair(&A[i], &B[i], opt);
+    if (st != FIGARO_OK) return st;
+    const figaro_options o = resolve(opt);
+    Call c;
+    plan_layout(c.p, nullptr, A[i].m, A[i].n, B[i].m, B[i].n, A[i].dtype == FIGARO_F64, o.path == FIGARO_PATH_MIXED,
+                0, 0, sm_count());
+    if (c.p.n <= kMaxWidth) calls.push_back(c);
+  }
+  const BatchSchedule sc = schedule_for(calls);
+  *gram_rows_per_cta = sc.gram_rows_per_cta;
+  *ht_ctas_per_sm = sc.ht_ctas_per_sm;
+  return FIGARO_OK;
+}
+
+figaro_status figaro_batch_get_status(int32_t count, const figaro_table* A, const figaro_table* B,
+                                     const figaro_options* opt, const void* ws, void* stream) {
+  if (count < 0 || !ws || (count > 0 && (!A || !B))) return FIGARO_ERR_INVALID_ARG;
+  const char* base = static_cast<const char*>(ws) + batch_area_bytes(count);
+  figaro_status worst = FIGARO_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    size_t one = 0;
+    figaro_status st = figaro_workspace_size(&A[i], &B[i], opt, &one);
+    if (st != FIGARO_OK) return st;
+    st = figaro_get_status(base, stream);
+    if (st != FIGARO_OK && worst == FIGARO_OK) worst = st;
+    base += (one + 255) & ~static_cast<size_t>(255);
+  }
+  return worst;
 }
 
 figaro_status figaro_get_status(const void* ws, void* stream) {

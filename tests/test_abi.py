@@ -71,3 +71,17 @@ def test_workspace_size_and_argument_checks_on_host(lib_path):
     assert lib.figaro_workspace_size(ctypes.byref(bad), ctypes.byref(A), None, ctypes.byref(sz)) == 1
     mixed = fg.Table(16, 16, 10, 4, 4, fg.F64, fg.MEM_DEVICE, 0)  # dtype mismatch with A
     assert lib.figaro_workspace_size(ctypes.byref(A), ctypes.byref(mixed), None, ctypes.byref(sz)) == 1
+
+
+def test_batch_schedule_query_on_host(lib_path):
+    """Without a tuned entry the batch schedule is the default one (host-only call)."""
+    import paper_2503_23385_gb300 as fg
+    lib = fg.library()
+    TA = (fg.Table * 2)(fg.Table(16, 16, 1000, 8, 8, fg.F32, fg.MEM_DEVICE, 0),
+                        fg.Table(16, 16, 5000, 16, 16, fg.F32, fg.MEM_DEVICE, 0))
+    TB = (fg.Table * 2)(fg.Table(16, 16, 2000, 8, 8, fg.F32, fg.MEM_DEVICE, 0),
+                        fg.Table(16, 16, 300, 32, 32, fg.F32, fg.MEM_DEVICE, 0))
+    rpc, hts = ctypes.c_int64(0), ctypes.c_int32(0)
+    assert lib.figaro_batch_schedule(2, TA, TB, None, ctypes.byref(rpc), ctypes.byref(hts)) == 0
+    assert (rpc.value, hts.value) == (4096, 2)
+    assert lib.figaro_batch_schedule(2, TA, TB, None, None, ctypes.byref(hts)) == 1
