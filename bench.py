@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--config", default="c1", choices=sorted(WORKLOADS))
     ap.add_argument("--path", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--gram-engine", default="auto", choices=["auto", "simt", "tcgen05"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-materialized", action="store_true")
@@ -93,7 +94,7 @@ def measured_traffic(kernel, cfg):
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f)[kernel]
-        src = os.path.join(ROOT, "paper_2503_23385_gb300", "csrc", "headtail.cu")
+        src = os.path.join(ROOT, "paper_2503_23385_gb300", "csrc", rec.get("source", "headtail.cu"))
         with open(src, "rb") as f:
             same = hashlib.sha256(f.read()).hexdigest() == rec["source_sha256"]
         return float(rec["traffic_bytes"]) if same and rec["workload"] == cfg else None
@@ -277,7 +278,8 @@ def main():
 
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(fg.NUM_PHASE_EVENTS)]
     ev_arr = fg.event_array(evs)
-    solver = fg.Solver(tA, tB, path=args.path, phase_events=ev_arr)
+    engine = {"auto": fg.GRAM_AUTO, "simt": fg.GRAM_SIMT, "tcgen05": fg.GRAM_TCGEN05}[args.gram_engine]
+    solver = fg.Solver(tA, tB, path=args.path, phase_events=ev_arr, gram_engine=engine)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -337,17 +339,30 @@ def main():
     value = job_throughput(rows, world, ms_per_step)
     phases = {name: statistics.mean(v) for name, v in zip(fg.PHASES, phase_ms)}
 
-    # ---- roofline of the head/tail kernel (one launch covers both tables) --
+    # ---- roofline of the dominant kernel: the Gram passes ----------------
+    # (the tensor-core Gram of the reduced matrix, HBM-bound at these widths:
+    # a tail row of n_t FP32 values is read once per CholeskyQR pass, a head
+    # row of n values likewise; per pass: three Gram launches and a reduce)
     hbm, peak_kind = measured_peaks()
     s = 4 if args.path == "mixed" else 8
     ein = A.x.itemsize
+    heads = info.get("num_runs_a", 0) if isinstance(info, dict) else 0
+    gram_bytes = sum(T.m * T.n * s for T in (A, B)) + heads * n * s
+    gram_ms = (phases["gram1"] + phases["gram2"]) / 2
+    g_achieved = gram_bytes / (gram_ms / 1e3) / 1e9
+    roofline = {"kernel": "gram_pack_kernel: one CholeskyQR Gram pass (head, A-tail and B-tail launches + reduce), "
+                          "average of the two passes",
+                "bound": "hbm", "achieved": g_achieved, "peak": hbm, "unit": "GB/s", "frac": g_achieved / hbm,
+                "traffic": measured_traffic("gram_pass", args.config), "bytes_per_launch": gram_bytes,
+                "peak_source": peak_kind}
+    # the head/tail kernel (one launch covers both tables)
     # per input row: perm + run index (4 + 4 B), the gathered features, the tail row written
     ht_bytes = sum(T.m * (4 + 4 + T.n * ein + T.n * s) for T in (A, B))
     ht_ms = phases["head_tail"]
     achieved = ht_bytes / (ht_ms / 1e3) / 1e9
-    roofline = {"kernel": "ht_stream_kernel (both tables)", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": measured_traffic("ht_stream_kernel", args.config),
-                "bytes_per_launch": ht_bytes, "peak_source": peak_kind}
+    roofline_ht = {"kernel": "ht_stream_kernel (both tables)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                   "unit": "GB/s", "frac": achieved / hbm, "traffic": measured_traffic("ht_stream_kernel", args.config),
+                   "bytes_per_launch": ht_bytes, "peak_source": peak_kind}
 
     # ---- end to end through the C ABI with host buffers -----------------
     e2e = None
@@ -421,10 +436,11 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.path == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.config], "path": args.path, "rows_per_gpu": rows,
-                           "graph": graph is not None,
+                           "graph": graph is not None, "gram_engine": args.gram_engine,
                            "l2": "inputs 136 MB + ~300 MB workspace exceed L2; 256 MB flush between steps"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-                "clocks": clocks, "phases_ms": phases, "instance": info, "fp64_path": fp64, "materialized_baseline": mat}
+                "roofline": roofline, "roofline_head_tail": roofline_ht, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "phases_ms": phases, "instance": info,
+                "fp64_path": fp64, "materialized_baseline": mat}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -3,6 +3,7 @@
 //   key grouping -> head/tail of A and B -> Gram pass 1 -> Cholesky 1 ->
 //   Gram pass 2 -> Cholesky 2 and R = R2 R1 -> one-sided Jacobi.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -429,6 +430,9 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   const int count = static_cast<int>(calls.size());
   if (count == 0) return FIGARO_OK;
   // Gram grids from the schedule (never above the partial buffers the plans reserved)
+  std::vector<std::array<int, 3>> grid0(calls.size());
+  for (size_t i = 0; i < calls.size(); ++i)
+    for (int b = 0; b < 3; ++b) grid0[i][b] = calls[i].p.ggrid[b];
   for (Call& c : calls) {
     const int64_t rows[3] = {c.p.t[0].m, c.p.t[0].m, c.p.t[1].m};
     for (int b = 0; b < 3; ++b) {
@@ -440,6 +444,8 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   const int mixed = p0.mixed, in_f64 = p0.t[0].in_f64;
   // ---- job lists
   JobList tiles, match, htplan, htscan, htstream[2], gram[2][4], reduce, dense1[3], dense2[3], dense3[3];
+  std::vector<TcJob> tc[2][2][4];  // [pass][engine - 1][variant]
+  size_t tc_smem[2][2][4] = {};
   int ht_smem[2] = {0, 0};
   size_t gram_smem[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   size_t dsm[3][3] = {};
@@ -466,12 +472,28 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
     match.add(i, 0, static_cast<int>((mm + 255) / 256));
     for (int pass = 1; pass <= 2; ++pass)
       for (int b = 0; b < 3; ++b) {
+        int tv = 0;
+        int64_t tile_rows = 0;
+        size_t tsm = 0;
+        const int eng = gram_tc_batch_engine(p, pass, b, &tv, &tile_rows, &tsm);
+        if (eng > 0) {  // tensor cores: CTAs by the schedule's rows per CTA
+          const int64_t rows = b == 2 ? p.t[1].m : p.t[0].m;
+          const int64_t per = std::max<int64_t>(sched.gram_rows_per_cta, tile_rows);
+          const int ctas = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows + per - 1) / per, grid0[i][b])));
+          tc[pass - 1][eng - 1][tv].push_back(TcJob{i, b, ctas});
+          tc_smem[pass - 1][eng - 1][tv] = std::max(tc_smem[pass - 1][eng - 1][tv], tsm);
+          calls[i].p.gcount[pass - 1][b] = ctas;
+          calls[i].p.gsym[pass - 1][b] = eng == 2 ? 1 : 0;
+          continue;
+        }
         int v = 0, ctas = 0;
         size_t sm = 0;
         gram_batch_block(p, pass, b, &v, &ctas, &sm);
         if (ctas == 0) continue;
         gram[pass - 1][v].add(i, b, ctas);
         gram_smem[pass - 1][v] = std::max(gram_smem[pass - 1][v], sm);
+        calls[i].p.gcount[pass - 1][b] = ctas;
+        calls[i].p.gsym[pass - 1][b] = 0;
       }
     reduce.add(i, 0, (p.n * p.n + 31) / 32);
     JobList* dl[3] = {dense1, dense2, dense3};
@@ -537,11 +559,27 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   FIGARO_TRY(ev.mark(2));
   FIGARO_TRY(launch_batch_ht(b, Jplan, Jplan.ctas, Jscan, Jstream, ht_smem, in_f64, mixed, s));
   FIGARO_TRY(ev.mark(3));
-  FIGARO_TRY(launch_batch_gram(b, 1, Jgram[0], gram_smem[0], Jreduce, mixed, s));
+  const BatchJobs none[4] = {};
+  const size_t none_smem[4] = {0, 0, 0, 0};
+  auto gram_pass = [&](int pass) -> figaro_status {
+    const BatchJobs empty{};
+    FIGARO_TRY(launch_batch_gram(b, pass, Jgram[pass - 1], gram_smem[pass - 1], empty, mixed, s));
+    for (int e = 0; e < 2; ++e)
+      for (int v = 0; v < 4; ++v) {
+        const auto& jobs = tc[pass - 1][e][v];
+        FIGARO_TRY(launch_gram_tc_batch(b.plans, plans.data(), pass, e + 1, v, jobs.data(), static_cast<int>(jobs.size()),
+                                        tc_smem[pass - 1][e][v], s));
+      }
+    FIGARO_TRY(launch_batch_gram(b, pass, none, none_smem, Jreduce, mixed, s));
+    return FIGARO_OK;
+  };
+  figaro_status gs = gram_pass(1);
+  if (gs != FIGARO_OK) return gs;
   FIGARO_TRY(ev.mark(4));
   FIGARO_TRY(launch_batch_dense(b, 1, Jd[0], dsm[0], dthr[0], mixed, s));
   FIGARO_TRY(ev.mark(5));
-  FIGARO_TRY(launch_batch_gram(b, 2, Jgram[1], gram_smem[1], Jreduce, mixed, s));
+  gs = gram_pass(2);
+  if (gs != FIGARO_OK) return gs;
   FIGARO_TRY(ev.mark(6));
   FIGARO_TRY(launch_batch_dense(b, 2, Jd[1], dsm[1], dthr[1], mixed, s));
   FIGARO_TRY(ev.mark(7));

@@ -279,7 +279,8 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
   T* U = reinterpret_cast<T*>(smraw);
   T* V = U + static_cast<int64_t>(np) * n;
   double* sig = reinterpret_cast<double*>(smraw + sizeof(T) * static_cast<size_t>(np) * n * (kWithV ? 2 : 1));
-  double* Rs = sig + np;  // R (FP64) for the Rayleigh quotients, when it fits
+  double* unrm = sig + np;  // column norms of the converged U
+  double* Rs = unrm + np;   // R (FP64) for the Rayleigh quotients, when it fits
   short2* pairs = reinterpret_cast<short2*>(Rs + ((kWithV && n <= 64) ? n * n : 0));
   const bool r_in_smem = kWithV && n <= 64;
   __shared__ T s_fro;
@@ -302,7 +303,6 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
     pairs[e] = make_short2(static_cast<short>(p), static_cast<short>(q));
   }
   __syncthreads();
-  const T eps = sizeof(T) == 4 ? T(5.9604645e-8) : T(1.1102230246251565e-16);
   const T tol2 = static_cast<T>(tol_in) * static_cast<T>(tol_in);
   // columns whose squared norm is below (n eps)^2 ||R||_F^2 are rounding
   // noise of a rank-deficient R: they take no part in rotations
@@ -313,7 +313,12 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
     if (threadIdx.x == 0) s_fro = f;
   }
   __syncthreads();
-  const T negligible = (static_cast<T>(n) * eps) * (static_cast<T>(n) * eps) * s_fro;
+  // columns below n eps64 ||R||_F are rounding noise of a rank-deficient R
+  // and take no part in rotations (the FP64 unit even for FP32 sweeps: FP32
+  // dot products keep their relative accuracy under column scaling, so the
+  // legitimately small columns of a graded R must keep rotating)
+  const double eps64 = 1.1102230246251565e-16;
+  const T negligible = static_cast<T>((n * eps64) * (n * eps64) * static_cast<double>(s_fro));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   constexpr int kPPW = 32 / LPP;  // pairs per warp
   const int sub = lane % LPP, gw = lane / LPP;
@@ -380,6 +385,20 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
   if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
   // singular values
   if (kWithV) {
+    // ||u_j|| in FP64 from the FP32 columns (kept for the smallest values: the
+    // Rayleigh quotient below has an error of order tol sigma_max when
+    // sigma_j is near zero, the column norm one of a few FP32 ulps)
+    for (int j = warp; j < n; j += nwarps) {
+      double un = 0.0;
+      const T* uj = U + static_cast<int64_t>(j) * n;
+      for (int i = lane; i < n; i += 32) {
+        const double u = static_cast<double>(uj[i]);
+        un += u * u;
+      }
+      for (int o = 16; o > 0; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
+      if (lane == 0) unrm[j] = sqrt(un);
+    }
+    __syncthreads();
     // sigma_j^2 = sum_i (R v_j)_i^2 / ||v_j||^2 in FP64, one thread per (i, j).
     // U is no longer needed: its storage (np * n floats = np * n / 2 doubles)
     // holds the squared terms for np / 2 rows i at a time.
@@ -425,6 +444,12 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
       for (int o = 16; o > 0; o >>= 1) den += __shfl_xor_sync(0xffffffffu, den, o);
       if (lane == 0) sig[j] = den > 0.0 ? sqrt(sig[j] / den) : 0.0;
     }
+    __syncthreads();
+    double umax = 0.0;
+    for (int k = 0; k < n; ++k) umax = unrm[k] > umax ? unrm[k] : umax;
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      if (unrm[j] < 1e-3 * umax) sig[j] = unrm[j];
   } else {
     for (int j = warp; j < n; j += nwarps) {
       double num = 0.0;
@@ -542,7 +567,7 @@ static cudaError_t jacobi_t(const Plan& p, const double* R, int64_t ldr, double*
   const int npairs = np / 2;
   int threads = 32 * ((npairs + 32 / LPP - 1) / (32 / LPP));
   if (threads > 1024) threads = 1024;
-  size_t smem = sizeof(T) * static_cast<size_t>(np) * n * (kWithV ? 2 : 1) + sizeof(double) * np;
+  size_t smem = sizeof(T) * static_cast<size_t>(np) * n * (kWithV ? 2 : 1) + 2 * sizeof(double) * np;
   if (kWithV && n <= 64) smem += sizeof(double) * static_cast<size_t>(n) * n;
   smem += sizeof(short2) * static_cast<size_t>(np - 1) * npairs;
   cudaError_t err = cudaFuncSetAttribute(jacobi_kernel<T, kWithV, NPL, LPP>,
@@ -600,7 +625,7 @@ void dense_batch_info(const Plan& p, int step, int* variant, size_t* smem, int* 
     int t = 32 * npairs;  // one warp per pair (32 lanes per pair)
     *threads = t > 1024 ? 1024 : t;
     const bool with_v = p.mixed != 0;
-    size_t sm = es * static_cast<size_t>(np) * n * (with_v ? 2 : 1) + sizeof(double) * np;
+    size_t sm = es * static_cast<size_t>(np) * n * (with_v ? 2 : 1) + 2 * sizeof(double) * np;
     if (with_v && n <= 64) sm += sizeof(double) * static_cast<size_t>(n) * n;
     sm += sizeof(short2) * static_cast<size_t>(np - 1) * npairs;
     *smem = sm;

@@ -332,10 +332,10 @@ __host__ __device__ inline ReduceArgs reduce_args_of(const Plan& p, int pass) {
     const GramArgs a = gram_args_of(p, pass, b, &rows, &tpt);
     if (rows == 0) continue;
     r.part[b] = p.gpart[b];
-    r.count[b] = p.ggrid[b];
+    r.count[b] = p.gcount[pass - 1][b] > 0 ? p.gcount[pass - 1][b] : p.ggrid[b];
     r.kout[b] = a.kout;
     r.off[b] = b == 2 ? p.n1 : 0;
-    r.sym[b] = 0;
+    r.sym[b] = p.gsym[pass - 1][b];
   }
   return r;
 }

@@ -38,6 +38,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -185,7 +186,7 @@ __device__ __forceinline__ int sw32b_chunk_offset(int row, int chunk) {
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, TcArgs a) {
+__device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArgs& a, int cta, int G) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t bar_tma[2], bar_f, bar_g;
@@ -240,10 +241,10 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
 
   // prologue: the first tile of this block (each later tile is loaded one
   // iteration ahead, into the buffer the previous tile's MMAs released)
-  if (tid == 0 && static_cast<int64_t>(blockIdx.x) < ntiles) {
+  if (tid == 0 && static_cast<int64_t>(cta) < ntiles) {
     expect_tx(&bar_tma[0], tile_bytes);
     for (int p = 0; p < a.kpanels; ++p)
-      tma_load_2d(base + a.off_x[0] + p * kPanelBytes, &tmx, p * 32, static_cast<int>(blockIdx.x * kTileRows),
+      tma_load_2d(base + a.off_x[0] + p * kPanelBytes, tmx, p * 32, static_cast<int>(cta * kTileRows),
                   &bar_tma[0]);
   }
 
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
   int it = 0;
   bool pending_g = false;  // Gram MMAs committed and not yet waited for
   uint32_t g_phase = 0, f_phase = 0;
-  for (int64_t rt = blockIdx.x; rt < ntiles; rt += gridDim.x, ++it) {
+  for (int64_t rt = cta; rt < ntiles; rt += G, ++it) {
     const int buf = it & 1;
     float* X = reinterpret_cast<float*>(base + a.off_x[buf]);
     float* Xl = reinterpret_cast<float*>(base + a.off_xlo);
@@ -301,11 +302,11 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
       drain();
     }
     if (tid == 0) {  // the other buffer is free: load the next tile into it
-      const int64_t nt = rt + static_cast<int64_t>(gridDim.x);
+      const int64_t nt = rt + static_cast<int64_t>(G);
       if (nt < ntiles) {
         expect_tx(&bar_tma[buf ^ 1], tile_bytes);
         for (int p = 0; p < a.kpanels; ++p)
-          tma_load_2d(base + a.off_x[buf ^ 1] + p * kPanelBytes, &tmx, p * 32, static_cast<int>(nt * kTileRows),
+          tma_load_2d(base + a.off_x[buf ^ 1] + p * kPanelBytes, tmx, p * 32, static_cast<int>(nt * kTileRows),
                       &bar_tma[buf ^ 1]);
       }
     }
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
     __syncthreads();
     if (!s_abort) drain();
   }
-  double* part = a.part + static_cast<int64_t>(blockIdx.x) * a.kout * a.kout;
+  double* part = a.part + static_cast<int64_t>(cta) * a.kout * a.kout;
   if (lane_row >= 0 && lane_row < a.kout) {
 #pragma unroll
     for (int j = 0; j < NP; ++j)
@@ -442,6 +443,11 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_consta
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, TcArgs a) {
+  gram_tc_body<NP>(&tmx, a, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -930,8 +936,7 @@ __device__ __forceinline__ int z_offset(int w, int col, int wr) {
 }
 
 template <int KK>
-__global__ void __launch_bounds__(kPipeThreads, 1)
-    gram_pack_kernel(const __grid_constant__ CUtensorMap tmx, PackArgs a) {
+__device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const PackArgs& a, int cta, int G) {
   constexpr int RR = 64 / KK;  // rows per packed row
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -942,9 +947,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   // pass 1: tiles of 128 packed rows (128 R rows); pass 2: tiles of 128 rows
   const int64_t tile_rows = pass2 ? kTileRows : static_cast<int64_t>(kTileRows) * a.rr;
   const int64_t ntiles_all = (rows + tile_rows - 1) / tile_rows;
-  const int G = gridDim.x;
-  const int n = ntiles_all > blockIdx.x ? static_cast<int>((ntiles_all - 1 - blockIdx.x) / G + 1) : 0;
-  auto tile_index = [&](int i) -> int64_t { return static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(i) * G; };
+  const int n = ntiles_all > cta ? static_cast<int>((ntiles_all - 1 - cta) / G + 1) : 0;
+  auto tile_index = [&](int i) -> int64_t { return static_cast<int64_t>(cta) + static_cast<int64_t>(i) * G; };
   const int stage_bytes = pass2 ? kP2Stage : kP1Stage;
   const int raw_bytes = stage_bytes / 2;  // the lo parts follow the raw (hi) parts of a stage
   const int wrq = kTileRows / a.rr;       // pass 2: packed rows of Q per tile
@@ -1014,11 +1018,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         const int y = static_cast<int>(tile_index(i) * kTileRows);
         if (pass2) {
           expect_tx(&S.tma_full[s], kPanelBytes);
-          tma_load_2d(dst, &tmx, 0, y, &S.tma_full[s]);
+          tma_load_2d(dst, tmx, 0, y, &S.tma_full[s]);
         } else {  // 128 packed rows x 64 columns: two 32-column panels
           expect_tx(&S.tma_full[s], 2 * kPanelBytes);
-          tma_load_2d(dst, &tmx, 0, y, &S.tma_full[s]);
-          tma_load_2d(dst + kPanelBytes, &tmx, 32, y, &S.tma_full[s]);
+          tma_load_2d(dst, tmx, 0, y, &S.tma_full[s]);
+          tma_load_2d(dst + kPanelBytes, tmx, 32, y, &S.tma_full[s]);
         }
         issued = i + 1;
       }
@@ -1244,7 +1248,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         pieces[(sub * 128 + i128) * 32 + j] = static_cast<double>(fh[j]) + static_cast<double>(fl[j]);
     }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
-    double* part = a.part + static_cast<int64_t>(blockIdx.x) * a.kout * a.kout;
+    double* part = a.part + static_cast<int64_t>(cta) * a.kout * a.kout;
     const int nsub = pass2 ? 1 : 2;
     auto gram_entry = [&](int ra, int cbb) {
       double g = 0.0;
@@ -1266,6 +1270,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   }
 }
 
+template <int KK>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    gram_pack_kernel(const __grid_constant__ CUtensorMap tmx, PackArgs a) {
+  gram_pack_body<KK>(&tmx, a, blockIdx.x, gridDim.x);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() { return tensor_map_encoder(); }
 
 struct Geometry {
@@ -1273,7 +1283,13 @@ struct Geometry {
   size_t smem;
 };
 
-Geometry geometry(int k, int kout, bool pass2) {
+__host__ __device__ inline int geo_take(int& off, int bytes) {
+  const int o = off;
+  off += (bytes + 1023) / 1024 * 1024;
+  return o;
+}
+
+__host__ __device__ inline Geometry geometry(int k, int kout, bool pass2) {
   Geometry g{};
   TcArgs& a = g.a;
   a.k = k;
@@ -1285,21 +1301,119 @@ Geometry geometry(int k, int kout, bool pass2) {
   a.qpanels = (kout + 31) / 32;
   a.wpanel_bytes = a.np * 128;
   int off = 0;
-  auto take = [&](int bytes) {
-    int o = off;
-    off += (bytes + 1023) / 1024 * 1024;
-    return o;
-  };
   const int xb = a.kpanels * kPanelBytes;
-  a.off_x[0] = take(xb);
-  a.off_x[1] = take(xb);
-  a.off_xlo = take(xb);
-  a.off_wh = pass2 ? take(a.kpanels * a.wpanel_bytes) : 0;
-  a.off_wl = pass2 ? take(a.kpanels * a.wpanel_bytes) : 0;
-  a.off_qh = pass2 ? take(a.qpanels * kPanelBytes) : 0;
-  a.off_ql = pass2 ? take(a.qpanels * kPanelBytes) : 0;
+  a.off_x[0] = geo_take(off, xb);
+  a.off_x[1] = geo_take(off, xb);
+  a.off_xlo = geo_take(off, xb);
+  a.off_wh = pass2 ? geo_take(off, a.kpanels * a.wpanel_bytes) : 0;
+  a.off_wl = pass2 ? geo_take(off, a.kpanels * a.wpanel_bytes) : 0;
+  a.off_qh = pass2 ? geo_take(off, a.qpanels * kPanelBytes) : 0;
+  a.off_ql = pass2 ? geo_take(off, a.qpanels * kPanelBytes) : 0;
   g.smem = static_cast<size_t>(off) + 1024;  // + alignment of the dynamic base
   return g;
+}
+
+// ---- batched forms: one launch carries up to kTcJobs jobs (instance, Gram
+// block) with their tensor maps as kernel arguments; job j owns CTAs
+// [first[j], first[j+1]), and each CTA runs the engine's body over its
+// job's tiles
+constexpr int kTcJobs = 192;
+
+struct TcBatch {
+  CUtensorMap maps[kTcJobs];
+  int32_t first[kTcJobs + 1];
+  int32_t inst[kTcJobs];
+  int8_t blk[kTcJobs];
+  const Plan* plans;
+  int njobs;
+  int pass;
+};
+
+// Shape of Gram block b (0 head rows, 1 A tails, 2 B tails) in a pass.
+struct BlockShape {
+  const void* X;
+  int k, kout;
+  int64_t rows;
+  const int64_t* rows_dev;
+  const float* W;
+};
+
+__host__ __device__ inline BlockShape block_shape(const Plan& p, int pass, int b) {
+  BlockShape sh{};
+  if (b == 0) {
+    sh.X = p.head;
+    sh.k = p.n;
+    sh.rows = p.t[0].m;
+    sh.rows_dev = &p.hdr->num_runs[0];
+  } else {
+    sh.X = p.t[b - 1].tail;
+    sh.k = p.t[b - 1].n;
+    sh.rows = p.t[b - 1].m;
+  }
+  const int w0 = b == 2 ? p.n1 : 0;
+  sh.kout = pass == 2 ? (b == 2 ? p.n2 : p.n) : sh.k;
+  sh.W = pass == 2 ? p.Wf + static_cast<int64_t>(w0) * p.n + w0 : nullptr;
+  return sh;
+}
+
+__device__ __forceinline__ PackArgs pack_args_of(const Plan& p, int pass, int b) {
+  const BlockShape sh = block_shape(p, pass, b);
+  PackArgs a{};
+  const int kk = pass == 2 ? sh.kout : sh.k;
+  a.k = sh.k;
+  a.kout = sh.kout;
+  a.np = (sh.kout + 15) / 16 * 16;
+  a.ksteps_f = (sh.k + 7) / 8;
+  a.kk = kk;
+  a.rr = 64 / kk;
+  a.rows = sh.rows;
+  a.rows_dev = sh.rows_dev;
+  a.W = sh.W;
+  a.wld = p.n;
+  a.part = p.gpart[b];
+  a.status = &p.hdr->status;
+  a.spin_limit = p.spin_limit;
+  a.withhold = 0;
+  return a;
+}
+
+__device__ __forceinline__ TcArgs tc_args_of(const Plan& p, int pass, int b) {
+  const BlockShape sh = block_shape(p, pass, b);
+  TcArgs a = geometry(sh.k, sh.kout, pass == 2).a;
+  a.rows = sh.rows;
+  a.rows_dev = sh.rows_dev;
+  a.W = sh.W;
+  a.wld = p.n;
+  a.part = p.gpart[b];
+  a.status = &p.hdr->status;
+  a.spin_limit = p.spin_limit;
+  return a;
+}
+
+__device__ __forceinline__ int tc_batch_job(const TcBatch& B, int cta) {
+  int lo = 0, hi = B.njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.first[mid] <= cta)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int KK>
+__global__ void __launch_bounds__(kPipeThreads, 1) gram_pack_batched(const __grid_constant__ TcBatch B) {
+  const int j = tc_batch_job(B, blockIdx.x);
+  const PackArgs a = pack_args_of(B.plans[B.inst[j]], B.pass, B.blk[j]);
+  gram_pack_body<KK>(&B.maps[j], a, blockIdx.x - B.first[j], B.first[j + 1] - B.first[j]);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTcThreads) gram_tc_batched(const __grid_constant__ TcBatch B) {
+  const int j = tc_batch_job(B, blockIdx.x);
+  const TcArgs a = tc_args_of(B.plans[B.inst[j]], B.pass, B.blk[j]);
+  gram_tc_body<NP>(&B.maps[j], a, blockIdx.x - B.first[j], B.first[j + 1] - B.first[j]);
 }
 
 }  // namespace
@@ -1453,6 +1567,95 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
   }
   count_launches(1);
   return cudaGetLastError();
+}
+
+// Batched tensor-core Gram.  Engine of Gram block b in a pass: 0 = none (the
+// CUDA-core engine takes it), 1 = packed (variant 0..3 for widths 4, 8, 16,
+// 32), 2 = general (variant 0, 1 for N = 32, 64); with its tile rows and
+// shared memory.
+int gram_tc_batch_engine(const Plan& p, int pass, int b, int* variant, int64_t* tile_rows, size_t* smem) {
+  if (!p.mixed || p.gram_engine == 1) return 0;
+  const BlockShape sh = block_shape(p, pass, b);
+  if (sh.rows == 0 || !gram_tc_supported(sh.k, sh.kout)) return 0;
+  if (gram_tc_packs(sh.k, sh.kout, pass == 2)) {
+    const int kk = pass == 2 ? sh.kout : sh.k;
+    *variant = kk == 4 ? 0 : (kk == 8 ? 1 : (kk == 16 ? 2 : 3));
+    *tile_rows = pass == 2 ? kTileRows : static_cast<int64_t>(kTileRows) * (64 / kk);
+    *smem = kPackSmemBytes;
+    return 1;
+  }
+  const Geometry g = geometry(sh.k, sh.kout, pass == 2);
+  *variant = g.a.np <= 32 ? 0 : 1;
+  *tile_rows = kTileRows;
+  *smem = g.smem;
+  return 2;
+}
+
+namespace {
+
+// The tensor map of a batched job, encoded as the single-instance launcher does.
+bool batch_map(const Plan& p, int pass, int b, int engine, CUtensorMap* map) {
+  const BlockShape sh = block_shape(p, pass, b);
+  cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kTileRows)};
+  cuuint32_t es[2] = {1, 1};
+  CUresult cr;
+  if (engine == 1 && pass == 1) {  // packed rows of 64 values
+    const int rr = 64 / sh.k;
+    const int64_t wrows = (sh.rows + rr - 1) / rr;
+    cuuint64_t dims[2] = {64, static_cast<cuuint64_t>(wrows > 0 ? wrows : 1)};
+    cuuint64_t strides[1] = {256};
+    cr = encoder()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(sh.X), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(sh.k), static_cast<cuuint64_t>(sh.rows > 0 ? sh.rows : 1)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(sh.k) * 4};
+    // the packed engine's pass 2 and the general engine's pass 2 read X as the
+    // K-major operand of the formation product; the general engine's pass 1
+    // as MN-major Gram operands (32-byte atoms)
+    const CUtensorMapSwizzle sw =
+        pass == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B;
+    cr = encoder()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(sh.X), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  return cr == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_gram_tc_batch(const Plan* dev_plans, const Plan* host_plans, int pass, int engine, int variant,
+                                 const TcJob* jobs, int njobs, size_t smem, cudaStream_t s) {
+  if (njobs == 0) return cudaSuccess;
+  void (*kern)(const TcBatch) = nullptr;
+  if (engine == 1)
+    kern = variant == 0 ? gram_pack_batched<4>
+                        : (variant == 1 ? gram_pack_batched<8> : (variant == 2 ? gram_pack_batched<16> : gram_pack_batched<32>));
+  else
+    kern = variant == 0 ? gram_tc_batched<32> : gram_tc_batched<64>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  TcBatch B;
+  std::memset(&B, 0, sizeof(B));
+  for (int j0 = 0; j0 < njobs; j0 += kTcJobs) {
+    const int nj = njobs - j0 < kTcJobs ? njobs - j0 : kTcJobs;
+    B.plans = dev_plans;
+    B.njobs = nj;
+    B.pass = pass;
+    B.first[0] = 0;
+    for (int j = 0; j < nj; ++j) {
+      const TcJob& J = jobs[j0 + j];
+      if (!batch_map(host_plans[J.inst], pass, J.blk, engine, &B.maps[j])) return cudaErrorInvalidValue;
+      B.inst[j] = J.inst;
+      B.blk[j] = static_cast<int8_t>(J.blk);
+      B.first[j + 1] = B.first[j] + J.ctas;
+    }
+    kern<<<B.first[nj], engine == 1 ? kPipeThreads : kTcThreads, smem, s>>>(B);
+    count_launches(1);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {

@@ -115,6 +115,10 @@ struct Plan {
   void* yw = nullptr;                         // n pivots 1 / sqrt(d)
   void* d0w = nullptr;                        // n diagonal of the factored Gram
   double* sigw = nullptr;                     // 2n: unsorted singular values, FP32-sweep column norms
+  // batched calls: Gram partials written per (pass, block) and whether they
+  // hold P with G = (P + P^T) / 2 (general tensor-core engine)
+  int gcount[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  int gsym[2][3] = {{0, 0, 0}, {0, 0, 0}};
 };
 
 // Batched execution (figaro_batch_join): every instance's plan sits in device
@@ -199,6 +203,15 @@ cudaError_t launch_batch_gram(const BatchDev& b, int pass, const BatchJobs by_tp
 void dense_batch_info(const Plan& p, int step, int* variant, size_t* smem, int* threads);
 cudaError_t launch_batch_dense(const BatchDev& b, int step, const BatchJobs jobs[3], const size_t smem[3],
                                const int threads[3], int mixed, cudaStream_t s);
+
+//   Gram (tensor cores): jobs of one engine variant, in launches of up to
+//   192 jobs whose tensor maps travel as kernel arguments
+struct TcJob {
+  int inst, blk, ctas;
+};
+int gram_tc_batch_engine(const Plan& p, int pass, int b, int* variant, int64_t* tile_rows, size_t* smem);
+cudaError_t launch_gram_tc_batch(const Plan* dev_plans, const Plan* host_plans, int pass, int engine, int variant,
+                                 const TcJob* jobs, int njobs, size_t smem, cudaStream_t s);
 
 // Wide path (wide.cu).
 int64_t wide_gram_jobs(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms);

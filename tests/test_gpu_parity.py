@@ -315,3 +315,19 @@ def test_withheld_lookback_word_times_out_and_context_survives(fg, torch):
         fg.join_qr_svd(dev(torch, A), dev(torch, B), flags=fg.FLAG_TEST_WITHHOLD, spin_limit=2000)
     assert e.value.status == 6
     check_against_oracle(fg, torch, A, B, paths=("mixed",))
+
+
+def test_narrow_graded_columns(fg, torch):
+    """B's columns scaled by 10^(-6 j / 15) (condition number ~1e6): the
+    column-scaled error of R and the relative error of every singular value
+    stay at the working precision, as the one-sided Jacobi on a graded R allows."""
+    A, B = make_pair(20000, 16, 15000, 16, 200, np.float64, "normal", seed=95)
+    d = 10.0 ** (-6.0 * np.arange(16) / 15.0)
+    B = Table(np.ascontiguousarray(B.x * d), B.key)
+    dd = np.concatenate([np.ones(16), d])
+    for path, tol, tol_sv in (("fp64", 1e-10, 1e-9), ("mixed", 1e-6, 1e-3)):
+        Rref, sref = oracle_ref(A, B, path)
+        R, s = gpu_r_sigma(fg, torch, A, B, path)
+        assert rel(R, Rref) <= tol and rel(s, sref) <= tol
+        assert rel(R / dd, Rref / dd) <= 100 * tol
+        assert np.max(np.abs(s - sref) / sref) <= tol_sv, np.max(np.abs(s - sref) / sref)
