@@ -291,15 +291,22 @@ def main():
     if status != 0:
         raise fg.FigaroError(status, "warm-up")
 
-    graph = None
+    # The timed graph holds the call without phase events (an event between two
+    # kernels would stop the next one from starting early); a second graph with
+    # the events gives the per-phase breakdown from separate replays.
+    graph = graph_ph = None
     launches_before = fg.kernel_launches()
     if not args.no_graph:
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
-            solver(tA, tB, stream=stream)
+            solver(tA, tB, stream=stream, record_phases=False)
         launches_per_step = fg.kernel_launches() - launches_before
+        graph_ph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph_ph, stream=stream, capture_error_mode="relaxed"):
+            solver(tA, tB, stream=stream)
         for _ in range(2):
             graph.replay()
+            graph_ph.replay()
         torch.cuda.synchronize()
     else:
         solver(tA, tB, stream=stream)
@@ -323,12 +330,22 @@ def main():
                 s1.record(stream)
                 s1.synchronize()
                 step_ms.append(s0.elapsed_time(s1))
-                for i in range(fg.NUM_PHASE_EVENTS - 1):
-                    phase_ms[i].append(evs[i].elapsed_time(evs[i + 1]))
+                if graph is None:
+                    for i in range(fg.NUM_PHASE_EVENTS - 1):
+                        phase_ms[i].append(evs[i].elapsed_time(evs[i + 1]))
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
     clocks = clk.summary()
+    if graph_ph is not None:  # the phase breakdown, outside the timed region
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.fill_(1)
+                graph_ph.replay()
+                evs[-1].synchronize()
+                for i in range(fg.NUM_PHASE_EVENTS - 1):
+                    phase_ms[i].append(evs[i].elapsed_time(evs[i + 1]))
+        torch.cuda.synchronize()
     info = solver.info(stream)
     status = solver.status(stream)
     if status != 0:
@@ -483,10 +500,14 @@ def run_batch(args, rank, world, torch, dist, fg, dev, local):
     launches_before = fg.kernel_launches()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
-        solver(stream=stream, phase_events=ev_arr)
+        solver(stream=stream)
     launches_per_step = fg.kernel_launches() - launches_before
+    graph_ph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_ph, stream=stream, capture_error_mode="relaxed"):
+        solver(stream=stream, phase_events=ev_arr)
     for _ in range(2):
         graph.replay()
+        graph_ph.replay()
     torch.cuda.synchronize()
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms, phase_ms = [], [[] for _ in range(fg.NUM_PHASE_EVENTS - 1)]
@@ -502,12 +523,18 @@ def run_batch(args, rank, world, torch, dist, fg, dev, local):
                 s1.record(stream)
                 s1.synchronize()
                 step_ms.append(s0.elapsed_time(s1))
-                for i in range(fg.NUM_PHASE_EVENTS - 1):
-                    phase_ms[i].append(evs[i].elapsed_time(evs[i + 1]))
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
     clocks = clk.summary()
+    with torch.cuda.stream(stream):  # the phase breakdown, outside the timed region
+        for _ in range(args.steps):
+            flush.fill_(1)
+            graph_ph.replay()
+            evs[-1].synchronize()
+            for i in range(fg.NUM_PHASE_EVENTS - 1):
+                phase_ms[i].append(evs[i].elapsed_time(evs[i + 1]))
+    torch.cuda.synchronize()
     st = solver.status(stream)
     if st != 0:
         raise fg.FigaroError(st, "timed steps")

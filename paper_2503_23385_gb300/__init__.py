@@ -283,9 +283,11 @@ class Solver:
         self.R = torch.zeros((n, n), dtype=torch.float64, device=self.dev)
         self.sigma = torch.zeros(n, dtype=torch.float64, device=self.dev)
 
-    def __call__(self, A, B, stream=None, want_r=True, want_sigma=True):
+    def __call__(self, A, B, stream=None, want_r=True, want_sigma=True, record_phases=True):
+        """record_phases=False leaves out the phase events given at construction."""
         ta, tb = _device_table(*A), _device_table(*B)
-        o = _options(**self.opts)
+        opts = self.opts if record_phases else {k: v for k, v in self.opts.items() if k != "phase_events"}
+        o = _options(**opts)
         s = _stream_handle(stream)
         ws = ctypes.c_void_p(self.ws.data_ptr())
         if want_sigma:

@@ -375,6 +375,7 @@ struct UploadChunk {
 };
 
 __global__ void upload_kernel(const __grid_constant__ UploadChunk c) {
+  pdl_enter();
   for (int i = threadIdx.x; i < c.bytes; i += blockDim.x) c.dst[i] = c.data[i];
 }
 
@@ -537,7 +538,7 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
     c.dst = reinterpret_cast<unsigned char*>(area) + o;
     c.bytes = static_cast<int>(std::min<size_t>(kUploadBytes, blob.bytes.size() - o));
     std::memcpy(c.data, blob.bytes.data() + o, c.bytes);
-    upload_kernel<<<1, 512, 0, s>>>(c);
+    pdl_launch(upload_kernel, 1, 512, 0, s, c);
     count_launches(1);
   }
   FIGARO_TRY(cudaGetLastError());

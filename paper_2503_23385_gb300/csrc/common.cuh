@@ -16,6 +16,15 @@ enum : int32_t {
 
 __device__ __forceinline__ void set_status(int32_t* word, int32_t bit) { atomicOr(word, bit); }
 
+// Programmatic dependent launch: every kernel first waits until the kernel
+// before it in the stream has completed and its memory is visible, then lets
+// the next kernel be scheduled while it runs (both are no-ops for a launch
+// without the programmatic-serialization attribute).
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Keys: int32 mapped to uint32 so that unsigned order equals signed order.
 __device__ __forceinline__ uint32_t key_to_ordered(int32_t k) { return static_cast<uint32_t>(k) ^ 0x80000000u; }
 __device__ __forceinline__ int32_t ordered_to_key(uint32_t u) { return static_cast<int32_t>(u ^ 0x80000000u); }

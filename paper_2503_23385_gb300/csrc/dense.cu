@@ -169,6 +169,7 @@ __device__ __forceinline__ void chol_first_body(const double* G, int n, double t
 template <typename T, bool kSmall>
 __global__ void chol_first_kernel(const double* G, int n, double tol, double* R1, double* W, float* Wf,
                                   int32_t* active, int32_t* status) {
+  pdl_enter();
   chol_first_body<T, kSmall>(G, n, tol, R1, W, Wf, active, status);
 }
 
@@ -238,6 +239,7 @@ template <typename T, bool kSmall>
 __global__ void chol_second_kernel(const double* G2, int n, double tol, const double* R1, const double* Wd,
                                    const int32_t* active, int refine, double* Xg, double* R, double* R_out,
                                    int64_t ldr, int32_t* status) {
+  pdl_enter();
   chol_second_body<T>(G2, n, tol, R1, Wd, active, refine, Xg, R, R_out, ldr, status);
 }
 
@@ -477,6 +479,7 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
 template <typename T, bool kWithV, int NPL, int LPP>
 __global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in, double* sigma,
                               int32_t* status, int32_t* sweeps_out) {
+  pdl_enter();
   jacobi_body<T, kWithV, NPL, LPP>(R, ldr, n, max_sweeps, tol_in, sigma, status, sweeps_out);
 }
 
@@ -490,12 +493,14 @@ __host__ __device__ inline double jacobi_tol(const Plan& p) {
 // ---- batched forms: one CTA per instance (job j = CTA j)
 template <typename T, bool kSmall>
 __global__ void chol_first_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
   const Plan& P = b.plans[J.inst[blockIdx.x]];
   chol_first_body<T, kSmall>(P.G1, P.n, dense_tol(P), P.R1, P.W, P.Wf, P.active, &P.hdr->status);
 }
 
 template <typename T>
 __global__ void chol_second_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
   const int i = J.inst[blockIdx.x];
   const Plan& P = b.plans[i];
   chol_second_body<T>(P.G2, P.n, dense_tol(P), P.R1, P.W, P.active, P.mixed, P.G1, P.R, b.out[i].R, P.n,
@@ -504,6 +509,7 @@ __global__ void chol_second_batched(BatchDev b, BatchJobs J) {
 
 template <typename T, bool kWithV, int NPL>
 __global__ void jacobi_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
   const int i = J.inst[blockIdx.x];
   const Plan& P = b.plans[i];
   jacobi_body<T, kWithV, NPL, 32>(P.R, P.n, P.n, P.max_sweeps, jacobi_tol(P), b.out[i].sigma, &P.hdr->status,
@@ -516,7 +522,7 @@ static double default_tol(const Plan& p) { return dense_tol(p); }
 
 static int dense_threads(int n) {
   int t = 64;
-  while (t < n * 8 && t < 1024) t <<= 1;
+  while (t < n * 32 && t < 1024) t <<= 1;
   return t;
 }
 
@@ -530,7 +536,7 @@ static cudaError_t chol_first_t(const Plan& p, cudaStream_t s) {
   auto kern = small ? chol_first_kernel<T, true> : chol_first_kernel<T, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  kern<<<1, dense_threads(n), smem, s>>>(p.G1, n, default_tol(p), p.R1, p.W, p.Wf, p.active, &p.hdr->status);
+  pdl_launch(kern, 1, dense_threads(n), smem, s, p.G1, n, default_tol(p), p.R1, p.W, p.Wf, p.active, &p.hdr->status);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -549,7 +555,7 @@ static cudaError_t chol_second_t(const Plan& p, double* R_out, int64_t ldr, cuda
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
   // G1 is consumed by the first factorisation: its storage holds the refined inverse
-  kern<<<1, dense_threads(n), smem, s>>>(p.G2, n, default_tol(p), p.R1, p.W, p.active, p.mixed ? 1 : 0, p.G1, p.R,
+  pdl_launch(kern, 1, dense_threads(n), smem, s, p.G2, n, default_tol(p), p.R1, p.W, p.active, p.mixed ? 1 : 0, p.G1, p.R,
                                          R_out, ldr, &p.hdr->status);
   count_launches(1);
   return cudaGetLastError();
@@ -573,7 +579,7 @@ static cudaError_t jacobi_t(const Plan& p, const double* R, int64_t ldr, double*
   cudaError_t err = cudaFuncSetAttribute(jacobi_kernel<T, kWithV, NPL, LPP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  jacobi_kernel<T, kWithV, NPL, LPP><<<1, threads, smem, s>>>(R, ldr, n, p.max_sweeps, tol, sigma, &p.hdr->status,
+  pdl_launch(jacobi_kernel<T, kWithV, NPL, LPP>, 1, threads, smem, s, R, ldr, n, p.max_sweeps, tol, sigma, &p.hdr->status,
                                                                &p.hdr->jacobi_sweeps);
   count_launches(1);
   return cudaGetLastError();
@@ -638,7 +644,7 @@ static cudaError_t launch_bucket(K kern, const BatchDev& b, const BatchJobs& J, 
   if (J.njobs == 0) return cudaSuccess;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  kern<<<J.njobs, threads, smem, s>>>(b, J);
+  pdl_launch(kern, J.njobs, threads, smem, s, b, J);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -206,6 +206,7 @@ __device__ __forceinline__ void gram_body(const GramArgs& a, int bid, int nb) {
 
 template <typename T, int TPT>
 __global__ void __launch_bounds__(kGramThreads) gram_kernel(GramArgs a) {
+  pdl_enter();
   gram_body<T, TPT>(a, blockIdx.x, gridDim.x);
 }
 
@@ -259,6 +260,7 @@ __device__ __forceinline__ void gram_reduce_body(const ReduceArgs& a, int bid) {
 }
 
 __global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_kernel(ReduceArgs a) {
+  pdl_enter();
   gram_reduce_body(a, blockIdx.x);
 }
 
@@ -345,6 +347,7 @@ __host__ __device__ inline ReduceArgs reduce_args_of(const Plan& p, int pass) {
 // ceil(n^2 / 32) CTAs
 template <typename T, int TPT>
 __global__ void __launch_bounds__(kGramThreads) gram_batched(BatchDev bd, BatchJobs J, int pass) {
+  pdl_enter();
   __shared__ GramArgs s_a;
   const int j = batch_job(J, blockIdx.x);
   if (threadIdx.x == 0) {
@@ -357,6 +360,7 @@ __global__ void __launch_bounds__(kGramThreads) gram_batched(BatchDev bd, BatchJ
 }
 
 __global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_batched(BatchDev bd, BatchJobs J, int pass) {
+  pdl_enter();
   __shared__ ReduceArgs s_r;
   const int j = batch_job(J, blockIdx.x);
   if (threadIdx.x == 0) s_r = reduce_args_of(bd.plans[J.inst[j]], pass);
@@ -372,11 +376,11 @@ cudaError_t launch_batch_gram_t(const BatchDev& b, int pass, const BatchJobs* by
     auto kern = q == 0 ? gram_batched<T, 1> : (q == 1 ? gram_batched<T, 2> : (q == 2 ? gram_batched<T, 4> : gram_batched<T, 8>));
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem[q]));
     if (err != cudaSuccess) return err;
-    kern<<<by_tpt[q].ctas, kGramThreads, smem[q], s>>>(b, by_tpt[q], pass);
+    pdl_launch(kern, by_tpt[q].ctas, kGramThreads, smem[q], s, b, by_tpt[q], pass);
     count_launches(1);
   }
   if (reduce.njobs > 0) {
-    gram_reduce_batched<<<reduce.ctas, 32 * kReduceWarps, 0, s>>>(b, reduce, pass);
+    pdl_launch(gram_reduce_batched, reduce.ctas, 32 * kReduceWarps, 0, s, b, reduce, pass);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -387,7 +391,7 @@ cudaError_t launch_tpt(const GramArgs& a, int grid, size_t smem, cudaStream_t s)
   cudaError_t err =
       cudaFuncSetAttribute(gram_kernel<T, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  gram_kernel<T, TPT><<<grid, kGramThreads, smem, s>>>(a);
+  pdl_launch(gram_kernel<T, TPT>, grid, kGramThreads, smem, s, a);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -486,7 +490,7 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     r.sym[b] = (tc && !gram_tc_packs(a.k, a.kout, pass == 2)) ? 1 : 0;
   }
   const int ne = p.n * p.n;
-  gram_reduce_kernel<<<(ne + 31) / 32, 32 * kReduceWarps, 0, s>>>(r);
+  pdl_launch(gram_reduce_kernel, (ne + 31) / 32, 32 * kReduceWarps, 0, s, r);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -447,6 +447,7 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArg
 
 template <int NP>
 __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, TcArgs a) {
+  pdl_enter();
   gram_tc_body<NP>(&tmx, a, blockIdx.x, gridDim.x);
 }
 
@@ -562,6 +563,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
 
 __global__ void __launch_bounds__(kPipeThreads, 1)
     gram_pipe_kernel(const __grid_constant__ CUtensorMap tmx, PipeArgs a) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ PipeSmem S;
@@ -1273,6 +1275,7 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
 template <int KK>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     gram_pack_kernel(const __grid_constant__ CUtensorMap tmx, PackArgs a) {
+  pdl_enter();
   gram_pack_body<KK>(&tmx, a, blockIdx.x, gridDim.x);
 }
 
@@ -1404,6 +1407,7 @@ __device__ __forceinline__ int tc_batch_job(const TcBatch& B, int cta) {
 
 template <int KK>
 __global__ void __launch_bounds__(kPipeThreads, 1) gram_pack_batched(const __grid_constant__ TcBatch B) {
+  pdl_enter();
   const int j = tc_batch_job(B, blockIdx.x);
   const PackArgs a = pack_args_of(B.plans[B.inst[j]], B.pass, B.blk[j]);
   gram_pack_body<KK>(&B.maps[j], a, blockIdx.x - B.first[j], B.first[j + 1] - B.first[j]);
@@ -1411,6 +1415,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) gram_pack_batched(const __gri
 
 template <int NP>
 __global__ void __launch_bounds__(kTcThreads) gram_tc_batched(const __grid_constant__ TcBatch B) {
+  pdl_enter();
   const int j = tc_batch_job(B, blockIdx.x);
   const TcArgs a = tc_args_of(B.plans[B.inst[j]], B.pass, B.blk[j]);
   gram_tc_body<NP>(&B.maps[j], a, blockIdx.x - B.first[j], B.first[j + 1] - B.first[j]);
@@ -1487,7 +1492,7 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
       if (err != cudaSuccess) return err;
       if (dev >= 0 && dev < 64) granted[dev][which] = 1;
     }
-    kern<<<grid, kPipeThreads, kPackSmemBytes, s>>>(map, a);
+    pdl_launch(kern, grid, kPipeThreads, kPackSmemBytes, s, map, a);
     count_launches(1);
     return cudaGetLastError();
   }
@@ -1528,7 +1533,7 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
       if (err != cudaSuccess) return err;
       if (dev >= 0 && dev < 64) granted[dev] = 1;
     }
-    gram_pipe_kernel<<<grid, kPipeThreads, kPipeSmemBytes, s>>>(map, a);
+    pdl_launch(gram_pipe_kernel, grid, kPipeThreads, kPipeSmemBytes, s, map, a);
     count_launches(1);
     return cudaGetLastError();
   }
@@ -1559,11 +1564,11 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
   if (a.np <= 32) {
     err = cudaFuncSetAttribute(gram_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem));
     if (err != cudaSuccess) return err;
-    gram_tc_kernel<32><<<grid, kTcThreads, g.smem, s>>>(map, a);
+    pdl_launch(gram_tc_kernel<32>, grid, kTcThreads, g.smem, s, map, a);
   } else {
     err = cudaFuncSetAttribute(gram_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem));
     if (err != cudaSuccess) return err;
-    gram_tc_kernel<64><<<grid, kTcThreads, g.smem, s>>>(map, a);
+    pdl_launch(gram_tc_kernel<64>, grid, kTcThreads, g.smem, s, map, a);
   }
   count_launches(1);
   return cudaGetLastError();
@@ -1650,7 +1655,7 @@ cudaError_t launch_gram_tc_batch(const Plan* dev_plans, const Plan* host_plans, 
       B.blk[j] = static_cast<int8_t>(J.blk);
       B.first[j + 1] = B.first[j] + J.ctas;
     }
-    kern<<<B.first[nj], engine == 1 ? kPipeThreads : kTcThreads, smem, s>>>(B);
+    pdl_launch(kern, B.first[nj], engine == 1 ? kPipeThreads : kTcThreads, smem, s, B);
     count_launches(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;

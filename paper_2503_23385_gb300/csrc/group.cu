@@ -68,6 +68,7 @@ __device__ __forceinline__ uint32_t* tile_offsets(const TableWork& T, int pass) 
 }
 
 __global__ void reset_kernel(DevHeader* h) {
+  pdl_enter();
   h->status = 0;
   for (int i = 0; i < 8; ++i) h->ticket[i] = 0;
   h->kmin[0] = h->kmin[1] = 0xffffffffu;
@@ -124,12 +125,14 @@ __device__ __forceinline__ void key_hist_body(const TableWork& T, int t, DevHead
 }
 
 __global__ void __launch_bounds__(kSortThreads) key_hist_kernel(TwoTables a) {
+  pdl_enter();
   int tile;
   const int t = table_of(a, blockIdx.x, tile);
   key_hist_body(a.t[t], t, a.h, tile);
 }
 
 __global__ void __launch_bounds__(kSortThreads) key_hist_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
   const int j = batch_job(J, blockIdx.x);
   const Plan& P = b.plans[J.inst[j]];
   key_hist_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x - J.first[j]);
@@ -166,12 +169,14 @@ __device__ __forceinline__ void tile_count_body(const TableWork& T, int t, const
 }
 
 __global__ void __launch_bounds__(kSortThreads) tile_count_kernel(TwoTables a, int pass) {
+  pdl_enter();
   int tile;
   const int t = table_of(a, blockIdx.x, tile);
   tile_count_body(a.t[t], t, a.h, tile, pass);
 }
 
 __global__ void __launch_bounds__(kSortThreads) tile_count_batched(BatchDev b, BatchJobs J, int pass) {
+  pdl_enter();
   const int j = batch_job(J, blockIdx.x);
   const Plan& P = b.plans[J.inst[j]];
   tile_count_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x - J.first[j], pass);
@@ -219,12 +224,14 @@ __device__ __forceinline__ void tile_scan_body(const TableWork& T, int t, const 
 }
 
 __global__ void __launch_bounds__(kRadixBins) tile_scan_kernel(TwoTables a, int pass) {
+  pdl_enter();
   const int t = blockIdx.x / kRadixBins;
   tile_scan_body(a.t[t], t, a.h, blockIdx.x % kRadixBins, pass);
 }
 
 // one CTA per (table job, digit)
 __global__ void __launch_bounds__(kRadixBins) tile_scan_batched(BatchDev b, BatchJobs J, int pass) {
+  pdl_enter();
   const int j = blockIdx.x / kRadixBins;
   const Plan& P = b.plans[J.inst[j]];
   tile_scan_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x % kRadixBins, pass);
@@ -347,12 +354,14 @@ __device__ __forceinline__ void sort_pass_body(const TableWork& T, int t, const 
 }
 
 __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(TwoTables a, int pass) {
+  pdl_enter();
   int tile;
   const int t = table_of(a, blockIdx.x, tile);
   sort_pass_body(a.t[t], t, a.h, tile, pass);
 }
 
 __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_batched(BatchDev b, BatchJobs J, int pass) {
+  pdl_enter();
   const int j = batch_job(J, blockIdx.x);
   const Plan& P = b.plans[J.inst[j]];
   sort_pass_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x - J.first[j], pass);
@@ -379,12 +388,14 @@ __device__ __forceinline__ void run_count_body(const TableWork& T, int tile) {
 }
 
 __global__ void __launch_bounds__(kSortThreads) run_count_kernel(TwoTables a) {
+  pdl_enter();
   int tile;
   const int t = table_of(a, blockIdx.x, tile);
   run_count_body(a.t[t], tile);
 }
 
 __global__ void __launch_bounds__(kSortThreads) run_count_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
   const int j = batch_job(J, blockIdx.x);
   run_count_body(b.plans[J.inst[j]].t[J.aux[j]], blockIdx.x - J.first[j]);
 }
@@ -472,12 +483,14 @@ __device__ __forceinline__ void runs_body(const TableWork& T, int t, DevHeader* 
 }
 
 __global__ void __launch_bounds__(kSortThreads) runs_kernel(TwoTables a) {
+  pdl_enter();
   int tile;
   const int t = table_of(a, blockIdx.x, tile);
   runs_body(a.t[t], t, a.h, tile, a.lut_size);
 }
 
 __global__ void __launch_bounds__(kSortThreads) runs_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
   const int j = batch_job(J, blockIdx.x);
   const Plan& P = b.plans[J.inst[j]];
   runs_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x - J.first[j], P.lut_size);
@@ -555,9 +568,11 @@ __device__ __forceinline__ void match_body(const TableWork& A, const TableWork& 
   }
 }
 
-__global__ void match_kernel(TwoTables a) { match_body(a.t[0], a.t[1], a.h, a.lut_size, blockIdx.x); }
+__global__ void match_kernel(TwoTables a) {
+  pdl_enter(); match_body(a.t[0], a.t[1], a.h, a.lut_size, blockIdx.x); }
 
 __global__ void match_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
   const int j = batch_job(J, blockIdx.x);
   const Plan& P = b.plans[J.inst[j]];
   match_body(P.t[0], P.t[1], P.hdr, P.lut_size, blockIdx.x - J.first[j]);
@@ -565,6 +580,7 @@ __global__ void match_batched(BatchDev b, BatchJobs J) {
 
 // Reset of every instance's header and digit histograms (one CTA each).
 __global__ void batch_reset_kernel(BatchDev b) {
+  pdl_enter();
   const Plan& P = b.plans[blockIdx.x];
   if (threadIdx.x == 0) {
     DevHeader* h = P.hdr;
@@ -588,7 +604,7 @@ __global__ void batch_reset_kernel(BatchDev b) {
 }  // namespace
 
 cudaError_t launch_batch_grouping(const BatchDev& b, const BatchJobs& tiles, const BatchJobs& match, cudaStream_t s) {
-  batch_reset_kernel<<<b.count, 256, 0, s>>>(b);
+  pdl_launch(batch_reset_kernel, b.count, 256, 0, s, b);
   count_launches(1);
   if (tiles.njobs > 0) {
     static int granted[64] = {0};
@@ -600,18 +616,18 @@ cudaError_t launch_batch_grouping(const BatchDev& b, const BatchJobs& tiles, con
       if (err != cudaSuccess) return err;
       if (dev >= 0 && dev < 64) granted[dev] = 1;
     }
-    key_hist_batched<<<tiles.ctas, kSortThreads, 0, s>>>(b, tiles);
+    pdl_launch(key_hist_batched, tiles.ctas, kSortThreads, 0, s, b, tiles);
     for (int pass = 0; pass < kMaxPasses; ++pass) {
-      if (pass > 0) tile_count_batched<<<tiles.ctas, kSortThreads, 0, s>>>(b, tiles, pass);
-      tile_scan_batched<<<tiles.njobs * kRadixBins, kRadixBins, 0, s>>>(b, tiles, pass);
-      sort_pass_batched<<<tiles.ctas, kSortThreads, kSortSmem, s>>>(b, tiles, pass);
+      if (pass > 0) pdl_launch(tile_count_batched, tiles.ctas, kSortThreads, 0, s, b, tiles, pass);
+      pdl_launch(tile_scan_batched, tiles.njobs * kRadixBins, kRadixBins, 0, s, b, tiles, pass);
+      pdl_launch(sort_pass_batched, tiles.ctas, kSortThreads, kSortSmem, s, b, tiles, pass);
     }
-    run_count_batched<<<tiles.ctas, kSortThreads, 0, s>>>(b, tiles);
-    runs_batched<<<tiles.ctas, kSortThreads, 0, s>>>(b, tiles);
+    pdl_launch(run_count_batched, tiles.ctas, kSortThreads, 0, s, b, tiles);
+    pdl_launch(runs_batched, tiles.ctas, kSortThreads, 0, s, b, tiles);
     count_launches(3 + 3 * kMaxPasses - 1);
   }
   if (match.njobs > 0) {
-    match_batched<<<match.ctas, 256, 0, s>>>(b, match);
+    pdl_launch(match_batched, match.ctas, 256, 0, s, b, match);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -626,7 +642,7 @@ int64_t group_status_words(int tiles) {
 cudaError_t launch_reset(const Plan& p, cudaStream_t s) {
   // the header; the sort's per-tile counts and offsets and the run counts are
   // rewritten by every call
-  reset_kernel<<<1, 1, 0, s>>>(p.hdr);
+  pdl_launch(reset_kernel, 1, 1, 0, s, p.hdr);
   count_launches(1);
   // the histograms are accumulated with atomics: clear them too
   for (int t = 0; t < 2; ++t)
@@ -656,18 +672,18 @@ cudaError_t launch_grouping(const Plan& p, cudaStream_t s) {
     if (err != cudaSuccess) return err;
     if (dev >= 0 && dev < 64) granted[dev] = 1;
   }
-  key_hist_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
+  pdl_launch(key_hist_kernel, a.nb, kSortThreads, 0, s, a);
   // passes past the key range's highest differing digit return at once
   for (int pass = 0; pass < kMaxPasses; ++pass) {
-    if (pass > 0) tile_count_kernel<<<a.nb, kSortThreads, 0, s>>>(a, pass);
-    tile_scan_kernel<<<2 * kRadixBins, kRadixBins, 0, s>>>(a, pass);
-    sort_pass_kernel<<<a.nb, kSortThreads, kSortSmem, s>>>(a, pass);
+    if (pass > 0) pdl_launch(tile_count_kernel, a.nb, kSortThreads, 0, s, a, pass);
+    pdl_launch(tile_scan_kernel, 2 * kRadixBins, kRadixBins, 0, s, a, pass);
+    pdl_launch(sort_pass_kernel, a.nb, kSortThreads, kSortSmem, s, a, pass);
   }
-  run_count_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
-  runs_kernel<<<a.nb, kSortThreads, 0, s>>>(a);
+  pdl_launch(run_count_kernel, a.nb, kSortThreads, 0, s, a);
+  pdl_launch(runs_kernel, a.nb, kSortThreads, 0, s, a);
   const int64_t mm = p.t[0].m > p.t[1].m ? p.t[0].m : p.t[1].m;
   const int mb = static_cast<int>((mm + 255) / 256);
-  if (mb > 0) match_kernel<<<mb, 256, 0, s>>>(a);
+  if (mb > 0) pdl_launch(match_kernel, mb, 256, 0, s, a);
   count_launches(3 + 3 * kMaxPasses - 1 + (mb > 0 ? 1 : 0));
   return cudaGetLastError();
 }

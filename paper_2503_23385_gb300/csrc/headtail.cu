@@ -162,6 +162,7 @@ __device__ __forceinline__ void ht_plan_body(const HtTable& T, const int32_t* st
 
 template <typename Tin, typename Tc>
 __global__ void __launch_bounds__(kHtBlock) ht_plan_kernel(HtArgs a, int total) {
+  pdl_enter();
   const int g = blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
   if (g >= total) return;
   const int t = g < a.c0 ? 0 : 1;
@@ -204,6 +205,7 @@ __device__ __forceinline__ void ht_scan_body(const HtTable& T, const int32_t* st
 }
 
 __global__ void __launch_bounds__(kHtBlock) ht_scan_kernel(HtArgs a, int n0) {
+  pdl_enter();
   const int t = static_cast<int>(blockIdx.x) < n0 ? 0 : 1;
   ht_scan_body(a.t[t], a.status, t ? blockIdx.x - n0 : blockIdx.x);
 }
@@ -752,6 +754,7 @@ template <typename Tin, typename Tc, int V>
 __global__ void __launch_bounds__(kHtStreamThreads)
     ht_stream_kernel(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1, HtArgs a,
                      int g0, int g1, int64_t spin_limit) {
+  pdl_enter();
   const int t = static_cast<int>(blockIdx.x) < g0 ? 0 : 1;
   ht_stream_body<Tin, Tc, V>(t ? &tm1 : &tm0, a, t, t ? static_cast<int>(blockIdx.x) - g0 : static_cast<int>(blockIdx.x),
                              t ? g1 : g0, spin_limit);
@@ -759,8 +762,8 @@ __global__ void __launch_bounds__(kHtStreamThreads)
 
 template <typename Tin, typename Tc>
 cudaError_t launch_typed_carry(const HtArgs& a, int total, int ncols, cudaStream_t s) {
-  ht_plan_kernel<Tin, Tc><<<(total + kPlanWarps - 1) / kPlanWarps, kHtBlock, 0, s>>>(a, total);
-  ht_scan_kernel<<<ncols, kHtBlock, 0, s>>>(a, a.t[0].chunks > 0 ? a.t[0].n : 0);
+  pdl_launch(ht_plan_kernel<Tin, Tc>, (total + kPlanWarps - 1) / kPlanWarps, kHtBlock, 0, s, a, total);
+  pdl_launch(ht_scan_kernel, ncols, kHtBlock, 0, s, a, a.t[0].chunks > 0 ? a.t[0].n : 0);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -822,7 +825,7 @@ cudaError_t launch_typed_main(HtArgs a, int num_sms, int64_t spin_limit, cudaStr
   if (c1 > 0 && g1 < 1) g1 = 1;
   if (g1 > c1) g1 = c1;
   if (g0 + g1 == 0) return cudaSuccess;
-  ht_stream_kernel<Tin, Tc, V><<<g0 + g1, kHtStreamThreads, smem, s>>>(maps[0], maps[1], a, g0, g1, spin_limit);
+  pdl_launch(ht_stream_kernel<Tin, Tc, V>, g0 + g1, kHtStreamThreads, smem, s, maps[0], maps[1], a, g0, g1, spin_limit);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -883,6 +886,7 @@ __host__ __device__ inline bool ht_v4_ok(const HtTable& T) {
 // chunk plan: first[] counts chunks, one warp per chunk
 template <typename Tin, typename Tc>
 __global__ void __launch_bounds__(kHtBlock) ht_plan_batched(BatchDev b, BatchJobs J, int total) {
+  pdl_enter();
   const int g = blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
   if (g >= total) return;
   const int j = batch_job(J, g);
@@ -893,6 +897,7 @@ __global__ void __launch_bounds__(kHtBlock) ht_plan_batched(BatchDev b, BatchJob
 
 // carries: first[] counts columns, one CTA per column
 __global__ void __launch_bounds__(kHtBlock) ht_scan_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
   const int j = batch_job(J, blockIdx.x);
   const Plan& P = b.plans[J.inst[j]];
   const HtTable T = ht_table(P, J.aux[j]);
@@ -902,6 +907,7 @@ __global__ void __launch_bounds__(kHtBlock) ht_scan_batched(BatchDev b, BatchJob
 // streaming pass: first[] counts CTAs; rows are copied with cp.async (no TMA)
 template <typename Tin, typename Tc, int V>
 __global__ void __launch_bounds__(kHtStreamThreads) ht_stream_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
   __shared__ HtArgs s_a;
   const int j = batch_job(J, blockIdx.x);
   const Plan& P = b.plans[J.inst[j]];
@@ -915,8 +921,8 @@ template <typename Tin, typename Tc>
 cudaError_t launch_batch_ht_typed(const BatchDev& b, const BatchJobs& plan, int plan_total, const BatchJobs& scan,
                                   const BatchJobs* stream, const int* smem, cudaStream_t s) {
   if (plan.njobs > 0) {
-    ht_plan_batched<Tin, Tc><<<(plan_total + kPlanWarps - 1) / kPlanWarps, kHtBlock, 0, s>>>(b, plan, plan_total);
-    ht_scan_batched<<<scan.ctas, kHtBlock, 0, s>>>(b, scan);
+    pdl_launch(ht_plan_batched<Tin, Tc>, (plan_total + kPlanWarps - 1) / kPlanWarps, kHtBlock, 0, s, b, plan, plan_total);
+    pdl_launch(ht_scan_batched, scan.ctas, kHtBlock, 0, s, b, scan);
     count_launches(2);
   }
   for (int v = 0; v < 2; ++v) {
@@ -926,7 +932,7 @@ cudaError_t launch_batch_ht_typed(const BatchDev& b, const BatchJobs& plan, int 
       cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem[v]);
       if (err != cudaSuccess) return err;
     }
-    kern<<<stream[v].ctas, kHtStreamThreads, smem[v], s>>>(b, stream[v]);
+    pdl_launch(kern, stream[v].ctas, kHtStreamThreads, smem[v], s, b, stream[v]);
     count_launches(1);
   }
   return cudaGetLastError();

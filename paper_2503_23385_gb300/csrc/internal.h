@@ -157,6 +157,24 @@ __device__ __forceinline__ int batch_job(const BatchJobs& J, int b) {
   return lo;
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the previous kernel in the stream finishes (every kernel of this
+// library calls pdl_enter() first, which waits for that kernel).
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+
 // cuTensorMapEncodeTiled from the driver (null when unavailable).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 

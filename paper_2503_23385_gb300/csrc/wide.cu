@@ -100,6 +100,7 @@ __device__ __forceinline__ int64_t block_rows(const WideBlock& B) {
 
 template <typename T>
 __global__ void __launch_bounds__(kWThreads) wide_gram_kernel(WideArgs a) {
+  pdl_enter();
   __shared__ __align__(16) T xi[kWRows][kWT];
   __shared__ __align__(16) T xj[kWRows][kWT];
   int b = 0;
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(kWThreads) wide_gram_kernel(WideArgs a) {
 // G (n x n, both triangles) = sum over blocks and row splits of the tile
 // partials, splits in ascending order.
 __global__ void __launch_bounds__(kWThreads) wide_reduce_kernel(WideArgs a) {
+  pdl_enter();
   const int64_t e = static_cast<int64_t>(blockIdx.x) * kWThreads + threadIdx.x;
   const int n = a.n;
   if (e >= static_cast<int64_t>(n) * n) return;
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(kWThreads) wide_reduce_kernel(WideArgs a) {
 // column c of Q sums the input columns 0..c).
 template <typename T>
 __global__ void __launch_bounds__(kWThreads) wide_form_kernel(WideArgs a) {
+  pdl_enter();
   __shared__ __align__(16) T xs[kWT][kPanel + 1];
   __shared__ __align__(16) T ws[kPanel][kWT];
   int b = 0;
@@ -476,6 +479,7 @@ __device__ __forceinline__ Sync make_sync(const DenseArgs& a) {
 
 template <typename T>
 __global__ void __launch_bounds__(kWThreads) wide_chol_first_kernel(DenseArgs a) {
+  pdl_enter();
   __shared__ CholSmem<T> sm;
   extern __shared__ __align__(16) unsigned char wcol_raw[];
   if (timed_out(&a.h->status)) return;
@@ -529,6 +533,7 @@ __device__ __forceinline__ double upper_dot_n(const TA* A, const TB* B, int n, i
 
 template <typename T>
 __global__ void __launch_bounds__(kWThreads) wide_chol_second_kernel(DenseArgs a) {
+  pdl_enter();
   __shared__ CholSmem<T> sm;
   if (timed_out(&a.h->status)) return;
   const Sync sync = make_sync(a);
@@ -612,6 +617,7 @@ __device__ __forceinline__ void rr_pair(int round, int g, int m, int& p, int& q)
 // JW: block width in columns (JW warps, one column pair each per inner round).
 template <typename T, bool kWithV, int JW>
 __global__ void __launch_bounds__(32 * JW) wide_jacobi_kernel(JacArgs a) {
+  pdl_enter();
   constexpr int kJacW = JW;
   extern __shared__ __align__(16) unsigned char jsm[];
   const int n = a.n;
@@ -749,6 +755,7 @@ template <typename T, bool kWithV>
 __global__ void __launch_bounds__(kWThreads) wide_sigma_kernel(const double* R, int64_t ldr, int n, const T* U,
                                                                const T* V, double* sig, double* unorm,
                                                                const int32_t* status) {
+  pdl_enter();
   __shared__ double vj[kMaxWideWidth];
   __shared__ double red[kWThreads / 32], redu[kWThreads / 32];
   if (timed_out(status)) return;
@@ -794,6 +801,7 @@ __global__ void __launch_bounds__(kWThreads) wide_sigma_kernel(const double* R, 
 
 __global__ void __launch_bounds__(kMaxWideWidth) wide_sort_kernel(const double* sig, const double* unorm, int n,
                                                                  double* sigma, const int32_t* status) {
+  pdl_enter();
   __shared__ double s_val[kMaxWideWidth];
   __shared__ double s_max;
   if (timed_out(status)) return;
@@ -929,9 +937,9 @@ cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   (void)es;
   if (pass == 2 && a.form_jobs > 0) {
     if (p.mixed)
-      wide_form_kernel<float><<<a.form_jobs, kWThreads, 0, s>>>(a);
+      pdl_launch(wide_form_kernel<float>, a.form_jobs, kWThreads, 0, s, a);
     else
-      wide_form_kernel<double><<<a.form_jobs, kWThreads, 0, s>>>(a);
+      pdl_launch(wide_form_kernel<double>, a.form_jobs, kWThreads, 0, s, a);
     count_launches(1);
     // the Grams of pass 2 read Q
     for (int i = 0; i < 3; ++i) {
@@ -941,13 +949,13 @@ cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   }
   if (a.gram_jobs > 0) {
     if (p.mixed)
-      wide_gram_kernel<float><<<a.gram_jobs, kWThreads, 0, s>>>(a);
+      pdl_launch(wide_gram_kernel<float>, a.gram_jobs, kWThreads, 0, s, a);
     else
-      wide_gram_kernel<double><<<a.gram_jobs, kWThreads, 0, s>>>(a);
+      pdl_launch(wide_gram_kernel<double>, a.gram_jobs, kWThreads, 0, s, a);
     count_launches(1);
   }
   const int64_t ne = static_cast<int64_t>(p.n) * p.n;
-  wide_reduce_kernel<<<static_cast<int>((ne + kWThreads - 1) / kWThreads), kWThreads, 0, s>>>(a);
+  pdl_launch(wide_reduce_kernel, static_cast<int>((ne + kWThreads - 1) / kWThreads), kWThreads, 0, s, a);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1010,7 +1018,7 @@ cudaError_t launch_wide_jacobi(const Plan& p, const double* R, int64_t ldr, doub
     // FP32 sweeps: blocks of 16 columns (n / 32 CTAs of 16 warps)
     err = launch_jacobi_w<float, true, 16>(p, a, s);
     if (err != cudaSuccess) return err;
-    wide_sigma_kernel<float, true><<<n, kWThreads, 0, s>>>(R, ldr, n, static_cast<const float*>(p.Uw),
+    pdl_launch(wide_sigma_kernel<float, true>, n, kWThreads, 0, s, R, ldr, n, static_cast<const float*>(p.Uw),
                                                            static_cast<const float*>(p.Vw), p.sigw, p.sigw + n,
                                                            &p.hdr->status);
   } else {
@@ -1018,11 +1026,11 @@ cudaError_t launch_wide_jacobi(const Plan& p, const double* R, int64_t ldr, doub
     // them over n / 8 CTAs
     err = launch_jacobi_w<double, false, 4>(p, a, s);
     if (err != cudaSuccess) return err;
-    wide_sigma_kernel<double, false><<<n, kWThreads, 0, s>>>(R, ldr, n, static_cast<const double*>(p.Uw),
+    pdl_launch(wide_sigma_kernel<double, false>, n, kWThreads, 0, s, R, ldr, n, static_cast<const double*>(p.Uw),
                                                              static_cast<const double*>(p.Vw), p.sigw, p.sigw + n,
                                                              &p.hdr->status);
   }
-  wide_sort_kernel<<<1, kMaxWideWidth, 0, s>>>(p.sigw, p.sigw + n, n, sigma, &p.hdr->status);
+  pdl_launch(wide_sort_kernel, 1, kMaxWideWidth, 0, s, p.sigw, p.sigw + n, n, sigma, &p.hdr->status);
   count_launches(3);
   return cudaGetLastError();
 }
