@@ -101,8 +101,11 @@ __device__ __forceinline__ int64_t block_rows(const WideBlock& B) {
 template <typename T>
 __global__ void __launch_bounds__(kWThreads) wide_gram_kernel(WideArgs a) {
   pdl_enter();
-  __shared__ __align__(16) T xi[kWRows][kWT];
-  __shared__ __align__(16) T xj[kWRows][kWT];
+  // rows per chunk: 32 (FP32) or 16 (FP64), two buffers each for the two column blocks
+  constexpr int RC = sizeof(T) == 4 ? kWRows : kWRows / 2;
+  constexpr int PER = RC * kWT / kWThreads;  // elements of a chunk each thread stages
+  __shared__ __align__(16) T xi[2][RC][kWT];
+  __shared__ __align__(16) T xj[2][RC][kWT];
   int b = 0;
   while (b < 2 && static_cast<int>(blockIdx.x) >= a.b[b].job0 + a.b[b].njobs) ++b;
   const WideBlock& B = a.b[b];
@@ -114,6 +117,7 @@ __global__ void __launch_bounds__(kWThreads) wide_gram_kernel(WideArgs a) {
   const int64_t r0 = static_cast<int64_t>(split) * B.split_rows;
   const int64_t r1 = r0 + B.split_rows < rows ? r0 + B.split_rows : rows;
   const int ci0 = ti * kWT, cj0 = tj * kWT;
+  const bool two = ti != tj;
   const T* X = static_cast<const T*>(B.X);
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   T acc[4][4];
@@ -125,23 +129,43 @@ __global__ void __launch_bounds__(kWThreads) wide_gram_kernel(WideArgs a) {
       acc[i][j] = T(0);
       tot[i][j] = 0.0;
     }
-  int chunk = 0;
-  for (int64_t c0 = r0; c0 < r1; c0 += kWRows) {
-    for (int e = tid; e < kWRows * kWT; e += kWThreads) {
-      const int rr = e / kWT, cc = e - rr * kWT;
+  // the next chunk is read into registers while the current one is used
+  T ri[PER], rj[PER];
+  auto fetch = [&](int64_t c0) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + q * kWThreads, rr = e / kWT, cc = e - rr * kWT;
       const int64_t row = c0 + rr;
       const bool in = row < r1;
-      xi[rr][cc] = (in && ci0 + cc < B.kout) ? X[row * B.ldx + ci0 + cc] : T(0);
-      if (ti != tj) xj[rr][cc] = (in && cj0 + cc < B.kout) ? X[row * B.ldx + cj0 + cc] : T(0);
+      ri[q] = (in && ci0 + cc < B.kout) ? X[row * B.ldx + ci0 + cc] : T(0);
+      rj[q] = (two && in && cj0 + cc < B.kout) ? X[row * B.ldx + cj0 + cc] : T(0);
     }
-    __syncthreads();
-    const T(*yj)[kWT] = ti != tj ? xj : xi;
+  };
+  auto stage = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + q * kWThreads, rr = e / kWT, cc = e - rr * kWT;
+      xi[buf][rr][cc] = ri[q];
+      if (two) xj[buf][rr][cc] = rj[q];
+    }
+  };
+  if (r0 < r1) {
+    fetch(r0);
+    stage(0);
+  }
+  __syncthreads();
+  int chunk = 0, buf = 0;
+  for (int64_t c0 = r0; c0 < r1; c0 += RC) {
+    const bool more = c0 + RC < r1;
+    if (more) fetch(c0 + RC);
+    const T(*yi)[kWT] = xi[buf];
+    const T(*yj)[kWT] = two ? xj[buf] : xi[buf];
 #pragma unroll 4
-    for (int rr = 0; rr < kWRows; ++rr) {
+    for (int rr = 0; rr < RC; ++rr) {
       T u[4], v[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        u[q] = xi[rr][ty * 4 + q];
+        u[q] = yi[rr][ty * 4 + q];
         v[q] = yj[rr][tx * 4 + q];
       }
 #pragma unroll
@@ -149,7 +173,10 @@ __global__ void __launch_bounds__(kWThreads) wide_gram_kernel(WideArgs a) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] += u[i] * v[j];
     }
+    // the other buffer was last read before the previous barrier
+    if (more) stage(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
     if (sizeof(T) == 4 && ++chunk == kWFlushChunks) {
       chunk = 0;
 #pragma unroll
@@ -1015,7 +1042,8 @@ cudaError_t launch_wide_jacobi(const Plan& p, const double* R, int64_t ldr, doub
   a.spin_limit = p.spin_limit;
   cudaError_t err;
   if (p.mixed) {
-    // FP32 sweeps: blocks of 16 columns (n / 32 CTAs of 16 warps)
+    // FP32 sweeps: blocks of 16 columns (n / 32 CTAs of 16 warps; narrower
+    // blocks double the rounds, whose barrier and staging costs dominate)
     err = launch_jacobi_w<float, true, 16>(p, a, s);
     if (err != cudaSuccess) return err;
     pdl_launch(wide_sigma_kernel<float, true>, n, kWThreads, 0, s, R, ldr, n, static_cast<const float*>(p.Uw),
