@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--path", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--gram-engine", default="auto", choices=["auto", "simt", "tcgen05"])
+    ap.add_argument("--task", default="qr_svd", choices=["qr_svd", "lstsq"],
+                    help="lstsq: least squares over the join with B's last column as the label")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-materialized", action="store_true")
@@ -279,7 +281,8 @@ def main():
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(fg.NUM_PHASE_EVENTS)]
     ev_arr = fg.event_array(evs)
     engine = {"auto": fg.GRAM_AUTO, "simt": fg.GRAM_SIMT, "tcgen05": fg.GRAM_TCGEN05}[args.gram_engine]
-    solver = fg.Solver(tA, tB, path=args.path, phase_events=ev_arr, gram_engine=engine)
+    solver_cls = fg.LsqSolver if args.task == "lstsq" else fg.Solver
+    solver = solver_cls(tA, tB, path=args.path, phase_events=ev_arr, gram_engine=engine)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -384,6 +387,8 @@ def main():
     # ---- end to end through the C ABI with host buffers -----------------
     e2e = None
     try:
+        if args.task != "qr_svd":
+            raise RuntimeError("the end-to-end leg times the qr_svd task")
         hA = (torch.from_numpy(A.x).pin_memory(), torch.from_numpy(A.key).pin_memory())
         hB = (torch.from_numpy(B.x).pin_memory(), torch.from_numpy(B.key).pin_memory())
         Rh = torch.zeros((n, n), dtype=torch.float64).pin_memory()
@@ -412,7 +417,7 @@ def main():
 
     # ---- the plain FP64 path on the same instance ------------------------
     fp64 = None
-    if args.path == "mixed" and args.fp64_steps > 0:
+    if args.path == "mixed" and args.fp64_steps > 0 and args.task == "qr_svd":
         try:
             s64 = fg.Solver(tA, tB, path="fp64")
             s64(tA, tB, stream=stream)
@@ -453,7 +458,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.path == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.config], "path": args.path, "rows_per_gpu": rows,
-                           "graph": graph is not None, "gram_engine": args.gram_engine,
+                           "graph": graph is not None, "gram_engine": args.gram_engine, "task": args.task,
                            "l2": "inputs 136 MB + ~300 MB workspace exceed L2; 256 MB flush between steps"},
                 "roofline": roofline, "roofline_head_tail": roofline_ht, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "phases_ms": phases, "instance": info,

@@ -198,6 +198,41 @@ FIGARO_API figaro_status figaro_join_singular_values(const figaro_table* A, cons
                                           void* stream);
 
 /*
+ * figaro_join_svd -- singular values and right singular vectors of J
+ * (Section 1's applications: the SVD of J for its principal components;
+ * Section 3: J = Q R, so J and R share sigma and V).  sigma[n] (device,
+ * descending) as in figaro_join_singular_values; V (device, n x n
+ * row-major, leading dimension ldv >= n): column j is the unit right
+ * singular vector of sigma_j, with the sign that makes its largest-magnitude
+ * component positive (the principal axes of J, which is not centred).
+ * Computed by one-sided Jacobi on R with the rotations accumulated (FP32
+ * sweeps and FP64 Rayleigh quotients on the mixed path, so V is accurate to
+ * FP32 level there; FP64 on the plain path); for repeated singular values
+ * any orthonormal basis of their subspace is returned.  R_out (may be NULL)
+ * receives R as in figaro_join_qr_r.  Device outputs only
+ * (FIGARO_FLAG_HOST_OUTPUT returns FIGARO_ERR_UNSUPPORTED).
+ */
+FIGARO_API figaro_status figaro_join_svd(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                              double* sigma, double* V, int64_t ldv, double* R_out, int64_t ldr, void* ws,
+                              size_t ws_bytes, void* stream);
+
+/*
+ * figaro_join_least_squares -- least squares over the join (Section 1's
+ * applications: the closed-form solution of linear regression).  The label
+ * y is B's last column, so J = [J_x | y] with J_x = the n - 1 other columns
+ * ([A's n1 | B's first n2 - 1]).  From R = [[R11, r], [0, rho]] of QR(J)
+ * (the same path as figaro_join_qr_r): beta = R11^{-1} r, which minimises
+ * ||J_x beta - y||_2, written to beta[n - 1] (device, FP64), and the
+ * residual norm |rho| = min ||J_x beta - y||_2 to residual[1].  A feature
+ * column that depends on the others (zero row of R) gets beta_i = 0.
+ * Requires n1 + n2 >= 2.  FIGARO_FLAG_HOST_OUTPUT makes beta and residual
+ * host pointers.
+ */
+FIGARO_API figaro_status figaro_join_least_squares(const figaro_table* A, const figaro_table* B,
+                                        const figaro_options* opt, double* beta, double* residual, void* ws,
+                                        size_t ws_bytes, void* stream);
+
+/*
  * figaro_join_singular_values_fixed -- figaro_join_singular_values with
  * scratch owned by the library instead of a caller-supplied workspace.  The
  * paper has no counterpart: this is a convenience of this library for

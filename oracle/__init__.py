@@ -15,6 +15,7 @@ Functions (paper: "Figaro on GPUs: Two Tables", arXiv 2503.23385):
 * :func:`reduce` -- the head/tail rows themselves, in group order.
 * :func:`join_gram` (O3) -- J^T J from per-group sums.
 * :func:`jacobi_sigma` -- one-sided Jacobi singular values of a square matrix.
+* :func:`join_least_squares` -- least squares over the materialised join.
 * :func:`qr_r` -- Householder R of a dense matrix (sign-normalised).
 * :func:`materialize` -- rows of J, for brute-force checks on small inputs.
 """
@@ -197,6 +198,17 @@ def join_gram(A, kA, B, kB):
     G = np.zeros((n, n), dtype=np.float64)
     lib.oracle_join_gram(*ta, *tb, G)
     return G
+
+
+def join_least_squares(A, kA, B, kB):
+    """Least squares over the join with B's last column as the label (the
+    paper's Section 1 names the closed-form solution of linear regression as
+    an application of QR): J materialised, then min ||J_x beta - y||_2 by
+    numpy's lstsq.  Returns (beta, residual norm)."""
+    J = materialize(A, kA, B, kB)
+    X, y = J[:, :-1], J[:, -1]
+    beta = np.linalg.lstsq(X, y, rcond=None)[0]
+    return beta, float(np.linalg.norm(X @ beta - y))
 
 
 def qr_r(X, block_rows: int = 65536):

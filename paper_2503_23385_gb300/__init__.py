@@ -21,7 +21,7 @@ __all__ = [
     "workspace_size", "join_group", "join_head_tail", "join_qr_r", "join_singular_values", "join_qr_svd",
     "join_qr_svd_host", "batch_join", "get_status", "Solver", "STATUS_NAMES", "event_array", "kernel_launches",
     "host_workspace_size", "PHASES", "NUM_PHASE_EVENTS", "join_singular_values_fixed", "FIXED_SCRATCH_BYTES",
-    "BatchSolver", "FLAG_AUTOTUNE",
+    "BatchSolver", "FLAG_AUTOTUNE", "join_least_squares", "LsqSolver", "join_svd",
 ]
 
 PATH_FP64, PATH_MIXED = 0, 1
@@ -308,6 +308,28 @@ class Solver:
         return get_info(self.ws, stream)
 
 
+class LsqSolver(Solver):
+    """Reusable workspace and outputs for repeated least-squares calls
+    (figaro_join_least_squares: B's last column is the label)."""
+
+    def __init__(self, A, B, **opts):
+        super().__init__(A, B, **opts)
+        torch = _torch()
+        self.beta = torch.zeros(max(self.n - 1, 1), dtype=torch.float64, device=self.dev)
+        self.residual = torch.zeros(1, dtype=torch.float64, device=self.dev)
+
+    def __call__(self, A, B, stream=None, record_phases=True, **_):
+        ta, tb = _device_table(*A), _device_table(*B)
+        opts = self.opts if record_phases else {k: v for k, v in self.opts.items() if k != "phase_events"}
+        o = _options(**opts)
+        _check(self.lib.figaro_join_least_squares(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(o),
+                                                  ctypes.c_void_p(self.beta.data_ptr()),
+                                                  ctypes.c_void_p(self.residual.data_ptr()),
+                                                  ctypes.c_void_p(self.ws.data_ptr()), self.nbytes,
+                                                  _stream_handle(stream)), "figaro_join_least_squares")
+        return self.beta, self.residual
+
+
 def join_qr_r(A, B, stream=None, **opts):
     """R of QR(J) as an (n x n) float64 device tensor."""
     s = Solver(A, B, **opts)
@@ -348,6 +370,49 @@ def join_qr_svd_host(A, B, R_out, sigma_out, workspace, stream=None, **opts):
     _check(lib.figaro_join_singular_values(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(o), ctypes.c_void_p(sptr),
                                            ctypes.c_void_p(rptr), n, ctypes.c_void_p(workspace.data_ptr()),
                                            workspace.numel(), _stream_handle(stream)), "figaro_join_singular_values")
+
+
+def join_svd(A, B, stream=None, workspace=None, **opts):
+    """(sigma, V, R) of the join as float64 device tensors: sigma descending,
+    column j of V the unit right singular vector of sigma_j."""
+    torch = _torch()
+    lib = library()
+    ta, tb = _device_table(*A), _device_table(*B)
+    o = _options(**opts)
+    nbytes = workspace_size(A, B, **opts)
+    dev = A[0].device
+    ws = _workspace(nbytes, dev, workspace)
+    n = ta.n + tb.n
+    sigma = torch.zeros(n, dtype=torch.float64, device=dev)
+    V = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    R = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    _check(lib.figaro_join_svd(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(o), ctypes.c_void_p(sigma.data_ptr()),
+                               ctypes.c_void_p(V.data_ptr()), n, ctypes.c_void_p(R.data_ptr()), n,
+                               ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream)), "figaro_join_svd")
+    _check(get_status(ws, stream), "figaro_join_svd (device status)")
+    return sigma, V, R
+
+
+def join_least_squares(A, B, stream=None, workspace=None, **opts):
+    """Least squares over the join: the label is B's last column.  Returns
+    (beta, residual) as float64 device tensors of n - 1 and 1 entries:
+    beta minimises ||J_x beta - y||, residual = that minimum."""
+    torch = _torch()
+    lib = library()
+    ta, tb = _device_table(*A), _device_table(*B)
+    o = _options(**opts)
+    nbytes = workspace_size(A, B, **opts)
+    dev = A[0].device
+    ws = _workspace(nbytes, dev, workspace)
+    n = ta.n + tb.n
+    beta = torch.zeros(max(n - 1, 1), dtype=torch.float64, device=dev)
+    res = torch.zeros(1, dtype=torch.float64, device=dev)
+    _check(lib.figaro_join_least_squares(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(o),
+                                         ctypes.c_void_p(beta.data_ptr()), ctypes.c_void_p(res.data_ptr()),
+                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream)),
+           "figaro_join_least_squares")
+    _check(get_status(ws, stream), "figaro_join_least_squares (device status)")
+    return beta, res
 
 
 def join_singular_values_fixed(A, B, sigma, R=None, stream=None, **opts) -> int:

@@ -141,12 +141,13 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
     p.Aw = b.take<char>(nn * ec);
     p.Tw = b.take<char>(nn * ec);
     p.Xw = b.take<double>(nn);
-    p.Uw = b.take<char>(static_cast<size_t>(n + 32) * n * ec);
-    p.Vw = b.take<char>(static_cast<size_t>(n + 32) * n * ec);
     p.yw = b.take<char>(static_cast<size_t>(n) * ec);
     p.d0w = b.take<char>(static_cast<size_t>(n) * ec);
-    p.sigw = b.take<double>(2 * static_cast<size_t>(n));  // Rayleigh quotients, column norms
   }
+  // the block Jacobi's columns (wide widths, and singular vectors at every width)
+  p.Uw = b.take<char>(static_cast<size_t>(n + 32) * n * ec);
+  p.Vw = b.take<char>(static_cast<size_t>(n + 32) * n * ec);
+  p.sigw = b.take<double>(2 * static_cast<size_t>(n));  // Rayleigh quotients, column norms
   const size_t nn = static_cast<size_t>(n) * n;
   p.G1 = b.take<double>(nn);
   p.G2 = b.take<double>(nn);
@@ -799,6 +800,48 @@ figaro_status figaro_join_singular_values(const figaro_table* A, const figaro_ta
   if (R_out && ldr < c.p.n) return FIGARO_ERR_INVALID_ARG;
   const int host_out = opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT);
   return run_qr_svd(c, R_out, R_out ? ldr : c.p.n, sigma, host_out);
+}
+
+figaro_status figaro_join_svd(const figaro_table* A, const figaro_table* B, const figaro_options* opt, double* sigma,
+                              double* V, int64_t ldv, double* R_out, int64_t ldr, void* ws, size_t ws_bytes,
+                              void* stream) {
+  if (!sigma || !V) return FIGARO_ERR_INVALID_ARG;
+  if (opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT)) return FIGARO_ERR_UNSUPPORTED;
+  Call c;
+  figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
+  if (st != FIGARO_OK) return st;
+  if (ldv < c.p.n || (R_out && ldr < c.p.n)) return FIGARO_ERR_INVALID_ARG;
+  st = run_grouping(c);
+  if (st != FIGARO_OK) return st;
+  st = run_factor(c, R_out, R_out ? ldr : c.p.n);
+  if (st != FIGARO_OK) return st;
+  FIGARO_TRY(launch_svd_v(c.p, c.p.R, c.p.n, sigma, V, ldv, c.s));
+  FIGARO_TRY(c.mark(8));
+  return FIGARO_OK;
+}
+
+figaro_status figaro_join_least_squares(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
+                                        double* beta, double* residual, void* ws, size_t ws_bytes, void* stream) {
+  if (!beta || !residual) return FIGARO_ERR_INVALID_ARG;
+  Call c;
+  figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
+  if (st != FIGARO_OK) return st;
+  if (c.p.n < 2) return FIGARO_ERR_INVALID_ARG;  // at least one feature besides the label
+  const int host_out = opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT);
+  st = run_grouping(c);
+  if (st != FIGARO_OK) return st;
+  st = run_factor(c, nullptr, c.p.n);
+  if (st != FIGARO_OK) return st;
+  // host outputs go through the workspace's sigma array (n doubles: beta, then the residual)
+  double* b_dev = host_out ? c.p.sigma : beta;
+  double* r_dev = host_out ? c.p.sigma + (c.p.n - 1) : residual;
+  FIGARO_TRY(launch_lsq(c.p, b_dev, r_dev, c.s));
+  FIGARO_TRY(c.mark(8));
+  if (host_out) {
+    FIGARO_TRY(cudaMemcpyAsync(beta, b_dev, sizeof(double) * (c.p.n - 1), cudaMemcpyDeviceToHost, c.s));
+    FIGARO_TRY(cudaMemcpyAsync(residual, r_dev, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  }
+  return FIGARO_OK;
 }
 
 figaro_status figaro_join_singular_values_fixed(const figaro_table* A, const figaro_table* B,

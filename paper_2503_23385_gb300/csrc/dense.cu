@@ -677,4 +677,52 @@ cudaError_t launch_batch_dense(const BatchDev& b, int step, const BatchJobs jobs
   return e;
 }
 
+// Least squares over the join (Section 1's applications: the closed-form
+// solution of linear regression).  With J = [J_x | y] (the label y is J's last
+// column) and R = [[R11, r], [0, rho]] its QR factor, beta = R11^{-1} r
+// minimises ||J_x beta - y|| and |rho| is the residual norm.  One warp, back
+// substitution in FP64 (R staged in shared memory up to n = 128); a dependent
+// feature column (zero row of R) gets beta_i = 0.
+namespace {
+constexpr int kLsqThreads = 256;
+
+// R is staged in shared memory when it fits (n <= 128); beta lives there too.
+__global__ void __launch_bounds__(kLsqThreads) lsq_kernel(const double* R, int n, double* beta, double* residual,
+                                                          const int32_t* status, int staged) {
+  pdl_enter();
+  extern __shared__ __align__(16) double lsq_sm[];
+  __shared__ double sb[kMaxWideWidth];
+  if (*reinterpret_cast<const volatile int32_t*>(status) & kStatusTimeout) return;
+  const int f = n - 1;  // features
+  if (staged)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) lsq_sm[e] = R[e];
+  __syncthreads();
+  const double* Rs = staged ? lsq_sm : R;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = f - 1; i >= 0; --i) {
+      const double* Ri = Rs + static_cast<int64_t>(i) * n;
+      double s = 0.0;
+      for (int k = i + 1 + lane; k < f; k += 32) s += Ri[k] * sb[k];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) sb[i] = Ri[i] != 0.0 ? (Ri[f] - s) / Ri[i] : 0.0;
+      __syncwarp();
+    }
+    for (int i = lane; i < f; i += 32) beta[i] = sb[i];
+    if (lane == 0) *residual = fabs(Rs[static_cast<int64_t>(f) * n + f]);
+  }
+}
+}  // namespace
+
+cudaError_t launch_lsq(const Plan& p, double* beta, double* residual, cudaStream_t s) {
+  const int staged = p.n <= kMaxWidth ? 1 : 0;
+  const size_t smem = staged ? sizeof(double) * static_cast<size_t>(p.n) * p.n : 0;
+  cudaError_t err = cudaFuncSetAttribute(lsq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  pdl_launch(lsq_kernel, 1, kLsqThreads, smem, s, static_cast<const double*>(p.R), p.n, beta, residual,
+             static_cast<const int32_t*>(&p.hdr->status), staged);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace figaro

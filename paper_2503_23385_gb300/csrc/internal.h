@@ -198,6 +198,7 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s);
 cudaError_t launch_chol_first(const Plan& p, cudaStream_t s);
 cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);
 cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
+cudaError_t launch_lsq(const Plan& p, double* beta, double* residual, cudaStream_t s);
 
 // Batched launchers: every instance of a batch in one launch per phase.
 //   tiles: one job per (instance, table with rows), CTAs = radix tiles, aux = table
@@ -237,5 +238,7 @@ cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s);
 cudaError_t launch_wide_chol_first(const Plan& p, cudaStream_t s);
 cudaError_t launch_wide_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);
 cudaError_t launch_wide_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
+cudaError_t launch_svd_v(const Plan& p, const double* R, int64_t ldr, double* sigma, double* V, int64_t ldv,
+                         cudaStream_t s);
 
 }  // namespace figaro

@@ -851,6 +851,69 @@ __global__ void __launch_bounds__(kMaxWideWidth) wide_sort_kernel(const double* 
   }
 }
 
+// sigma descending and, for each value, its right singular vector: column
+// j of V (n x n row-major, leading dimension ldv) is the unit-norm column of
+// the accumulated rotations that belongs to sigma_j, its sign chosen so that
+// its largest-magnitude component is positive.  One CTA.
+template <typename T>
+__global__ void __launch_bounds__(kMaxWideWidth) wide_sort_v_kernel(const double* sig, const double* unorm, int n,
+                                                                   const T* V, double* sigma, double* V_out,
+                                                                   int64_t ldv, const int32_t* status) {
+  pdl_enter();
+  __shared__ double s_val[kMaxWideWidth], s_scale[kMaxWideWidth];
+  __shared__ int s_rank[kMaxWideWidth];
+  __shared__ double s_max;
+  if (timed_out(status)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int k = 0; k < n; ++k) m = unorm[k] > m ? unorm[k] : m;
+    s_max = m;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s_val[j] = unorm[j] < 1e-3 * s_max ? unorm[j] : sig[j];
+  // per column: 1 / ||v_j|| times the sign of its largest-magnitude entry
+  for (int j = warp; j < n; j += nw) {
+    const T* vj = V + static_cast<int64_t>(j) * n;
+    double ss = 0.0, big = 0.0;
+    int at = 0;
+    for (int i = lane; i < n; i += 32) {
+      const double v = static_cast<double>(vj[i]);
+      ss += v * v;
+      if (fabs(v) > fabs(big)) {
+        big = v;
+        at = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      const double ob = __shfl_xor_sync(0xffffffffu, big, o);
+      const int oa = __shfl_xor_sync(0xffffffffu, at, o);
+      if (fabs(ob) > fabs(big) || (fabs(ob) == fabs(big) && oa < at)) {
+        big = ob;
+        at = oa;
+      }
+    }
+    if (lane == 0) s_scale[j] = ss > 0.0 ? (big < 0.0 ? -1.0 : 1.0) / sqrt(ss) : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = s_val[j];
+    int rank = 0;
+    for (int k = 0; k < n; ++k) {
+      const double w = s_val[k];
+      rank += (w > v) || (w == v && k < j);
+    }
+    s_rank[j] = rank;
+    sigma[rank] = v;
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < static_cast<int64_t>(n) * n; e += blockDim.x) {
+    const int j = static_cast<int>(e / n), i = static_cast<int>(e - static_cast<int64_t>(j) * n);
+    V_out[static_cast<int64_t>(i) * ldv + s_rank[j]] = static_cast<double>(V[e]) * s_scale[j];
+  }
+}
+
 // ---------------------------------------------------------- host side ----
 
 void wide_geometry(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms, WideBlock b[3], int* gram_jobs,
@@ -1024,6 +1087,44 @@ cudaError_t launch_jacobi_w(const Plan& p, JacArgs a, cudaStream_t s) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
   return launch_cooperative(wide_jacobi_kernel<T, kWithV, JW>, nblk / 2, 32 * JW, smem, s, a);
+}
+
+// sigma and V of R for any width: the block Jacobi with accumulated
+// rotations (FP32 sweeps + FP64 Rayleigh quotients on the mixed path, FP64
+// sweeps on the plain path).
+cudaError_t launch_svd_v(const Plan& p, const double* R, int64_t ldr, double* sigma, double* V, int64_t ldv,
+                         cudaStream_t s) {
+  const int n = p.n;
+  JacArgs a{};
+  a.R = R;
+  a.ldr = ldr;
+  a.n = n;
+  a.max_sweeps = p.max_sweeps;
+  a.tol = p.mixed ? 1e-5 : 4.0 * n * 1.1102230246251565e-16;
+  a.U = p.Uw;
+  a.V = p.Vw;
+  a.h = p.hdr;
+  a.spin_limit = p.spin_limit;
+  cudaError_t err;
+  if (p.mixed) {
+    err = launch_jacobi_w<float, true, 16>(p, a, s);
+    if (err != cudaSuccess) return err;
+    pdl_launch(wide_sigma_kernel<float, true>, n, kWThreads, 0, s, R, ldr, n, static_cast<const float*>(p.Uw),
+               static_cast<const float*>(p.Vw), p.sigw, p.sigw + n, static_cast<const int32_t*>(&p.hdr->status));
+    pdl_launch(wide_sort_v_kernel<float>, 1, kMaxWideWidth, 0, s, static_cast<const double*>(p.sigw),
+               static_cast<const double*>(p.sigw + n), n, static_cast<const float*>(p.Vw), sigma, V, ldv,
+               static_cast<const int32_t*>(&p.hdr->status));
+  } else {
+    err = launch_jacobi_w<double, true, 4>(p, a, s);
+    if (err != cudaSuccess) return err;
+    pdl_launch(wide_sigma_kernel<double, true>, n, kWThreads, 0, s, R, ldr, n, static_cast<const double*>(p.Uw),
+               static_cast<const double*>(p.Vw), p.sigw, p.sigw + n, static_cast<const int32_t*>(&p.hdr->status));
+    pdl_launch(wide_sort_v_kernel<double>, 1, kMaxWideWidth, 0, s, static_cast<const double*>(p.sigw),
+               static_cast<const double*>(p.sigw + n), n, static_cast<const double*>(p.Vw), sigma, V, ldv,
+               static_cast<const int32_t*>(&p.hdr->status));
+  }
+  count_launches(3);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_wide_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s) {
