@@ -167,7 +167,7 @@ __device__ __forceinline__ void chol_first_body(const double* G, int n, double t
 }
 
 template <typename T, bool kSmall>
-__global__ void chol_first_kernel(const double* G, int n, double tol, double* R1, double* W, float* Wf,
+__global__ void __launch_bounds__(1024) chol_first_kernel(const double* G, int n, double tol, double* R1, double* W, float* Wf,
                                   int32_t* active, int32_t* status) {
   pdl_enter();
   chol_first_body<T, kSmall>(G, n, tol, R1, W, Wf, active, status);
@@ -236,7 +236,7 @@ __device__ __forceinline__ void chol_second_body(const double* G2, int n, double
 }
 
 template <typename T, bool kSmall>
-__global__ void chol_second_kernel(const double* G2, int n, double tol, const double* R1, const double* Wd,
+__global__ void __launch_bounds__(1024) chol_second_kernel(const double* G2, int n, double tol, const double* R1, const double* Wd,
                                    const int32_t* active, int refine, double* Xg, double* R, double* R_out,
                                    int64_t ldr, int32_t* status) {
   pdl_enter();
@@ -477,7 +477,7 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
 }
 
 template <typename T, bool kWithV, int NPL, int LPP>
-__global__ void jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in, double* sigma,
+__global__ void __launch_bounds__(1024) jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in, double* sigma,
                               int32_t* status, int32_t* sweeps_out) {
   pdl_enter();
   jacobi_body<T, kWithV, NPL, LPP>(R, ldr, n, max_sweeps, tol_in, sigma, status, sweeps_out);
@@ -492,14 +492,14 @@ __host__ __device__ inline double jacobi_tol(const Plan& p) {
 
 // ---- batched forms: one CTA per instance (job j = CTA j)
 template <typename T, bool kSmall>
-__global__ void chol_first_batched(BatchDev b, BatchJobs J) {
+__global__ void __launch_bounds__(1024) chol_first_batched(BatchDev b, BatchJobs J) {
   pdl_enter();
   const Plan& P = b.plans[J.inst[blockIdx.x]];
   chol_first_body<T, kSmall>(P.G1, P.n, dense_tol(P), P.R1, P.W, P.Wf, P.active, &P.hdr->status);
 }
 
 template <typename T>
-__global__ void chol_second_batched(BatchDev b, BatchJobs J) {
+__global__ void __launch_bounds__(1024) chol_second_batched(BatchDev b, BatchJobs J) {
   pdl_enter();
   const int i = J.inst[blockIdx.x];
   const Plan& P = b.plans[i];
@@ -508,7 +508,7 @@ __global__ void chol_second_batched(BatchDev b, BatchJobs J) {
 }
 
 template <typename T, bool kWithV, int NPL>
-__global__ void jacobi_batched(BatchDev b, BatchJobs J) {
+__global__ void __launch_bounds__(1024) jacobi_batched(BatchDev b, BatchJobs J) {
   pdl_enter();
   const int i = J.inst[blockIdx.x];
   const Plan& P = b.plans[i];
