@@ -46,8 +46,8 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="c1", choices=sorted(WORKLOADS))
     ap.add_argument("--path", default="mixed", choices=["mixed", "fp64"])
@@ -119,7 +119,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "10"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
@@ -206,13 +206,15 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from workloads import config
+    # each step is a bounded sample, sized so that the whole run stays near a minute
+    per_step_s = 60.0 / max(1, args.steps + args.warmup)
     if args.config == "c3":
         inst = config("c3")
         for _ in range(args.warmup):
             oracle_batch_rows_per_s(inst[:1], 0.0)
         times, rows, used = [], 0, 0
         for _ in range(args.steps):
-            rps, dt, rows, used, jrows = oracle_batch_rows_per_s(inst, 4.0)
+            rps, dt, rows, used, jrows = oracle_batch_rows_per_s(inst, min(4.0, per_step_s))
             times.append(dt)
         ms = 1e3 * sum(times) / len(times)
         value = rows / (ms / 1e3)
@@ -226,7 +228,9 @@ def run_reference(args, rank, world):
         print(json.dumps(line), flush=True)
         return
     A, B = config(args.config)
-    keys = args.cpu_sample_keys or default_sample_keys(args.config, reference_arm=True)
+    # the default sample takes about 3 s per step on one core; the oracle's time grows with the sampled keys
+    keys = args.cpu_sample_keys or max(5, int(default_sample_keys(args.config, reference_arm=True) *
+                                              min(1.0, per_step_s / 3.2)))
     for _ in range(args.warmup):
         oracle_rows_per_s(A, B, max(1, keys // 10))
     times, rows = [], 0
@@ -368,13 +372,25 @@ def main():
     ein = A.x.itemsize
     heads = info.get("num_runs_a", 0) if isinstance(info, dict) else 0
     gram_bytes = sum(T.m * T.n * s for T in (A, B)) + heads * n * s
-    gram_ms = (phases["gram1"] + phases["gram2"]) / 2
-    g_achieved = gram_bytes / (gram_ms / 1e3) / 1e9
-    roofline = {"kernel": "gram_pack_kernel: one CholeskyQR Gram pass (head, A-tail and B-tail launches + reduce), "
-                          "average of the two passes",
-                "bound": "hbm", "achieved": g_achieved, "peak": hbm, "unit": "GB/s", "frac": g_achieved / hbm,
-                "traffic": measured_traffic("gram_pass", args.config), "bytes_per_launch": gram_bytes,
-                "peak_source": peak_kind}
+    if n <= 128:
+        gram_ms = (phases["gram1"] + phases["gram2"]) / 2
+        g_achieved = gram_bytes / (gram_ms / 1e3) / 1e9
+        roofline = {"kernel": "gram_pack_kernel: one CholeskyQR Gram pass (head, A-tail and B-tail launches + "
+                              "reduce), average of the two passes",
+                    "bound": "hbm", "achieved": g_achieved, "peak": hbm, "unit": "GB/s", "frac": g_achieved / hbm,
+                    "traffic": measured_traffic("gram_pass", args.config), "bytes_per_launch": gram_bytes,
+                    "peak_source": peak_kind}
+    else:
+        # wide joins: pass 1 of the CUDA-core tile Gram (64 x 64 upper tiles), bound by FP32 FMA issue;
+        # flops of the tiles it computes, against 152 SMs x 128 FP32 lanes x 2 flops x the max SM clock
+        tiles = lambda k: ((k + 63) // 64) * ((k + 63) // 64 + 1) // 2
+        flops = 2.0 * 64 * 64 * (A.m * tiles(A.n) + B.m * tiles(B.n) + heads * tiles(n))
+        alu_peak = 152 * 128 * 2 * 2070e6 / 1e12
+        achieved_tf = flops / (phases["gram1"] / 1e3) / 1e12
+        roofline = {"kernel": "wide_gram_kernel, Gram pass 1 (CUDA cores, FP32 products)", "bound": "alu",
+                    "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
+                    "traffic": None, "flops_per_launch": flops,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
     # the head/tail kernel (one launch covers both tables)
     # per input row: perm + run index (4 + 4 B), the gathered features, the tail row written
     ht_bytes = sum(T.m * (4 + 4 + T.n * ein + T.n * s) for T in (A, B))
