@@ -490,6 +490,466 @@ __host__ __device__ inline double jacobi_tol(const Plan& p) {
   return p.mixed ? 1e-5 : 4.0 * p.n * 1.1102230246251565e-16;
 }
 
+// ---- register-resident forms for n <= 32 (one column per lane) ----------
+//
+// At these widths a barrier per elimination step or per rotation round
+// dominates, so the work per step must be short: column c of the n x n
+// matrix is held by lane c, and row i by warp i mod 8 (register i / 8) for
+// the factorisations, or by warp i / (32 / JW) for the Jacobi sweeps.
+constexpr int kSmallN = 32;
+constexpr int kC8Warps = 8;  // warps of the small factorisations (rows i = warp + 8 s, s < 4)
+constexpr int kC8Threads = 32 * kC8Warps;
+
+template <typename T>
+__device__ __forceinline__ T row_reg(const T (&a)[4], int s) {  // a[s], s warp-uniform
+  return s == 0 ? a[0] : (s == 1 ? a[1] : (s == 2 ? a[2] : a[3]));
+}
+template <typename T>
+__device__ __forceinline__ void set_row_reg(T (&a)[4], int s, T v) {
+  a[0] = s == 0 ? v : a[0];
+  a[1] = s == 1 ? v : a[1];
+  a[2] = s == 2 ? v : a[2];
+  a[3] = s == 3 ? v : a[3];
+}
+
+// Semi-definite Cholesky on the 8-warp layout, in place: on entry a[s] =
+// A[warp + 8 s][lane] (upper triangle used), on return R (zero below the
+// diagonal and in the rows of dependent columns).  Bit k of `mask`: column
+// k independent (on entry and on return).  Step k: warp k mod 8 forms row k
+// of R from its own registers (the pivot A[k][k] comes from lane k) and
+// posts it; after one barrier every thread takes R[k][i] R[k][lane] off its
+// rows i > k.  The posted rows alternate between two buffers, so one
+// barrier per step suffices.
+template <typename T>
+__device__ __forceinline__ uint32_t chol8w(T (&a)[4], int n, T tol, uint32_t mask, T* rbuf, T* diag0,
+                                           int32_t* status) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    if (warp + 8 * s == lane) diag0[lane] = a[s];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    T* rb = rbuf + (k & 1) * kSmallN;
+    if (warp == (k & 7)) {
+      const T ak = row_reg(a, k >> 3);
+      const T d = __shfl_sync(0xffffffffu, ak, k);
+      const T d0 = diag0[k];
+      bool ok = (mask >> k) & 1u;
+      if (!isfinite(d)) {
+        ok = false;
+        if (lane == 0) set_status(status, kStatusNotSpd);
+      }
+      if (!(d > tol * d0) || !(d0 > T(0))) ok = false;
+      const T yk = ok ? rsqrt_pivot(d) : T(0);
+      const T rk = lane >= k ? ak * yk : T(0);
+      set_row_reg(a, k >> 3, rk);
+      rb[lane] = rk;
+    }
+    __syncthreads();
+    const T rkc = rb[lane];
+    if (!(rb[k] != T(0))) mask &= ~(1u << k);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int i = warp + 8 * s;
+      if (i > k && i < n && lane >= i) a[s] = fma(-rb[i], rkc, a[s]);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    if (warp + 8 * s > lane) a[s] = T(0);
+  return mask;
+}
+
+// W = R^{-1} on the same layout (R in a, upper triangular), backward and
+// column-oriented: when row k of W is final (posted by warp k mod 8), every
+// thread takes R[i][k] W[k][lane] off its rows i < k.  Rows and columns of
+// dependent columns are zero.
+template <typename T>
+__device__ __forceinline__ void inv8w(const T (&a)[4], T (&w)[4], int n, uint32_t mask, T* wbuf, T* dinv) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = warp + 8 * s;
+    if (i == lane && i < n) dinv[i] = ((mask >> i) & 1u) ? T(1) / a[s] : T(0);
+    w[s] = i == lane ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int k = n - 1; k >= 0; --k) {
+    T* wb = wbuf + (k & 1) * kSmallN;
+    if (warp == (k & 7)) {
+      const T wk = row_reg(w, k >> 3) * dinv[k];
+      set_row_reg(w, k >> 3, wk);
+      wb[lane] = wk;
+    }
+    T rik[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) rik[s] = __shfl_sync(0xffffffffu, a[s], k);
+    __syncthreads();
+    const T wkc = wb[lane];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (warp + 8 * s < k) w[s] = fma(-rik[s], wkc, w[s]);
+  }
+  if (!((mask >> lane) & 1u))
+#pragma unroll
+    for (int s = 0; s < 4; ++s) w[s] = T(0);
+}
+
+// First factorisation for n <= 32: R1 = chol(G1), W = R1^{-1} (8 warps).
+template <typename T>
+__device__ __forceinline__ void chol_first32_body(const double* G, int n, double tol, double* R1, double* W, float* Wf,
+                                                  int32_t* active, int32_t* status) {
+  __shared__ T buf[2 * kSmallN], diag0[kSmallN], dinv[kSmallN];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool col = lane < n;
+  T a[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = warp + 8 * s;
+    a[s] = (i < n && col) ? static_cast<T>(G[i * n + lane]) : T(0);
+  }
+  const uint32_t all = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+  const uint32_t mask = chol8w<T>(a, n, static_cast<T>(tol), all, buf, diag0, status);
+  if (warp == 0 && col) active[lane] = (mask >> lane) & 1u;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = warp + 8 * s;
+    if (i < n && col) R1[i * n + lane] = static_cast<double>(a[s]);
+  }
+  __syncthreads();  // buf is reused by the inverse
+  T w[4];
+  inv8w<T>(a, w, n, mask, buf, dinv);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = warp + 8 * s;
+    if (i < n && col) {
+      // dependent columns pass through the second pass unchanged (identity block)
+      double v = i == lane && !((mask >> i) & 1u) ? 1.0 : static_cast<double>(w[s]);
+      if (sizeof(T) == 4) {  // the value both Gram engines use exactly: hi (TF32) + lo rounded to TF32
+        const float f = static_cast<float>(v);
+        const float h = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
+        const float l = __uint_as_float((__float_as_uint(f - h) + 0x1000u) & 0xFFFFE000u);
+        v = static_cast<double>(h + l);
+      }
+      W[i * n + lane] = v;
+      Wf[i * n + lane] = static_cast<float>(v);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kC8Threads) chol_first32_kernel(const double* G, int n, double tol, double* R1,
+                                                                  double* W, float* Wf, int32_t* active,
+                                                                  int32_t* status) {
+  pdl_enter();
+  chol_first32_body<T>(G, n, tol, R1, W, Wf, active, status);
+}
+
+// Float-float helpers for the mixed path's second factorisation (FP64
+// arithmetic is slow on this GPU): exact products by FMA, compensated sums.
+__device__ __forceinline__ void ff_add_prod(float& hi, float& lo, float x, float y) {
+  const float p = x * y;
+  const float e = fmaf(x, y, -p);
+  float s, t;
+  two_sum(hi, p, s, t);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+}
+
+// Second factorisation and R for n <= 32 (8 warps).  R2 = chol(G2) on the
+// columns the first factorisation kept.  Mixed path (T = float): X = R1 + R1 E
+// with E = I - W R1 formed in float-float from the exact FP32 values of W
+// and R1, kept as the pair (R1, R1 E); R = R2 X in float-float.  Plain path
+// (T = double): X = R1, R = R2 X in FP64.
+template <typename T>
+__device__ __forceinline__ void chol_second32_body(const double* G2, int n, double tol, const double* R1,
+                                                   const float* Wf, const int32_t* active, int refine, double* R,
+                                                   double* R_out, int64_t ldr, int32_t* status) {
+  constexpr int LD = kSmallN + 1;
+  __shared__ T buf[2 * kSmallN], diag0[kSmallN];
+  __shared__ T sR2[kSmallN * LD], sX[kSmallN * LD];
+  __shared__ float sW[kSmallN * LD], sE[kSmallN * LD], sXlo[kSmallN * LD];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool col = lane < n;
+  const uint32_t mask1 = __ballot_sync(0xffffffffu, col && active[lane] != 0);
+  T a[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = warp + 8 * s;
+    a[s] = (i < n && col) ? static_cast<T>(G2[i * n + lane]) : T(0);
+    // X = R1 on the independent columns, identity on the dependent diagonal
+    T x = T(0);
+    if (i < n && col && ((mask1 >> i) & 1u) && ((mask1 >> lane) & 1u)) x = static_cast<T>(R1[i * n + lane]);
+    if (i == lane && col && !((mask1 >> i) & 1u)) x = T(1);
+    sX[i * LD + lane] = x;
+    if (refine) sW[i * LD + lane] = (i < n && col) ? Wf[i * n + lane] : 0.f;
+  }
+  chol8w<T>(a, n, static_cast<T>(tol), mask1, buf, diag0, status);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) sR2[(warp + 8 * s) * LD + lane] = a[s];
+  if constexpr (sizeof(T) == 4) {
+    if (refine) {
+      // E = I - W R1 (upper triangle, independent columns), float-float
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = warp + 8 * s, j = lane;
+        float e = 0.f;
+        if (i <= j && j < n && ((mask1 >> i) & 1u) && ((mask1 >> j) & 1u)) {
+          float hi = 0.f, lo = 0.f;
+          for (int k = i; k <= j; ++k) ff_add_prod(hi, lo, sW[i * LD + k], sX[k * LD + j]);
+          float t0, t1;
+          two_sum(i == j ? 1.f : 0.f, -hi, t0, t1);
+          e = __fadd_rn(t0, __fadd_rn(t1, -lo));
+        }
+        sE[i * LD + j] = e;
+      }
+      __syncthreads();
+      // X = R1 + R1 E: the correction in FP32 (it is ~1e-7 of R1)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = warp + 8 * s, j = lane;
+        float c = 0.f;
+        if (i <= j && j < n && ((mask1 >> i) & 1u) && ((mask1 >> j) & 1u))
+          for (int k = i; k <= j; ++k) c = fmaf(sX[i * LD + k], sE[k * LD + j], c);
+        sXlo[i * LD + j] = c;
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) sXlo[(warp + 8 * s) * LD + lane] = 0.f;
+    }
+  }
+  __syncthreads();
+  // R = R2 X (both upper triangular); rows of dependent columns are zero
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = warp + 8 * s, j = lane;
+    if (i < n && j < n) {
+      double r = 0.0;
+      if (i <= j && sR2[i * LD + i] != T(0)) {
+        if constexpr (sizeof(T) == 4) {
+          float hi = 0.f, lo = 0.f;
+          for (int k = i; k <= j; ++k) {
+            const float r2 = sR2[i * LD + k];
+            ff_add_prod(hi, lo, r2, sX[k * LD + j]);
+            lo = fmaf(r2, sXlo[k * LD + j], lo);
+          }
+          r = static_cast<double>(hi) + static_cast<double>(lo);
+        } else {
+          double s0 = 0.0, s1 = 0.0;
+          int k = i;
+          for (; k + 1 <= j; k += 2) {
+            s0 = fma(sR2[i * LD + k], sX[k * LD + j], s0);
+            s1 = fma(sR2[i * LD + k + 1], sX[(k + 1) * LD + j], s1);
+          }
+          if (k <= j) s0 = fma(sR2[i * LD + k], sX[k * LD + j], s0);
+          r = s0 + s1;
+        }
+      }
+      R[i * n + j] = r;
+      if (R_out) R_out[static_cast<int64_t>(i) * ldr + j] = r;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kC8Threads) chol_second32_kernel(const double* G2, int n, double tol,
+                                                                   const double* R1, const float* Wf,
+                                                                   const int32_t* active, int refine, double* R,
+                                                                   double* R_out, int64_t ldr, int32_t* status) {
+  pdl_enter();
+  chol_second32_body<T>(G2, n, tol, R1, Wf, active, refine, R, R_out, ldr, status);
+}
+
+// One-sided Jacobi for n <= 32 with U (and V) in registers: lane l of each
+// of the JW warps holds column l, warp w rows [RPW w, RPW (w + 1)), RPW =
+// 32 / JW.  Rounds follow the circle method over np columns: column np - 1
+// stays and the others rotate, so in round r lane l meets r if l = np - 1,
+// np - 1 if l = r, and (2r - l) mod (np - 1) otherwise.  The two lanes of a
+// pair swap their rows by shuffles and both form the partial 2 x 2 Gram of
+// the lower-indexed column (x) against the higher one (y); the lower lane
+// posts it, and after the round's barrier both sum the JW partials in warp
+// order -- the same sums, hence the same rotation, in both lanes.  The
+// convergence test, the negligible-column rule and the singular values
+// (FP64 Rayleigh quotients with V, column norms without) are those of
+// jacobi_body.
+template <typename T, bool kWithV, int JW>
+__device__ __forceinline__ void jacobi32_body(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in,
+                                              double* sigma, int32_t* status, int32_t* sweeps_out) {
+  constexpr int RPW = kSmallN / JW;
+  struct Part {
+    T a, b, c, d;
+  };
+  __shared__ Part part[2][JW][kSmallN];
+  __shared__ double red[JW][kSmallN];
+  __shared__ double sig[kSmallN], unrm[kSmallN];
+  __shared__ double Rs[kWithV ? kSmallN * kSmallN : 1];
+  __shared__ T Vs[kWithV ? kSmallN * (kSmallN + 1) : 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int np = n + (n & 1), m = np - 1;
+  T u[RPW], v[RPW];
+#pragma unroll
+  for (int t = 0; t < RPW; ++t) {
+    const int row = warp * RPW + t;
+    u[t] = (row < n && lane < n) ? static_cast<T>(R[static_cast<int64_t>(row) * ldr + lane]) : T(0);
+    v[t] = (kWithV && row == lane && lane < n) ? T(1) : T(0);
+  }
+  if (kWithV)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, k = e - i * n;
+      Rs[i * kSmallN + k] = R[static_cast<int64_t>(i) * ldr + k];
+    }
+  for (int e = threadIdx.x; e < 2 * JW * kSmallN; e += blockDim.x)
+    (&part[0][0][0])[e] = Part{T(0), T(0), T(0), T(0)};  // idle lanes read slots nobody posts
+  // ||R||_F^2 for the negligible-column rule
+  {
+    T f = T(0);
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) f = fma(u[t], u[t], f);
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0) red[warp][0] = static_cast<double>(f);
+  }
+  __syncthreads();
+  double fro = 0.0;
+  for (int w = 0; w < JW; ++w) fro += red[w][0];
+  const double eps64 = 1.1102230246251565e-16;
+  const T negligible = static_cast<T>((n * eps64) * (n * eps64) * fro);
+  const T tol2 = static_cast<T>(tol_in) * static_cast<T>(tol_in);
+  __syncthreads();  // red[][0] is read above and written again below
+  int sweep = 0, buf = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    int any = 0;
+    for (int r = 0; r < m; ++r) {
+      int q = 2 * r - lane;  // (branch-free: the lanes of a warp take different cases)
+      q += q < 0 ? m : 0;
+      q -= q >= m ? m : 0;
+      q = lane == r ? m : q;
+      q = lane == m ? r : q;
+      q = lane >= np ? lane : q;
+      const bool lo = lane < q;
+      // own and partner rows; the lower lane's (|own|^2, |other|^2, own.other)
+      // over its rows is the pair's partial (alpha, beta, gamma)
+      T o[RPW];
+      T a = T(0), b = T(0), c = T(0);
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) {
+        o[t] = __shfl_sync(0xffffffffu, u[t], q);
+        a = fma(u[t], u[t], a);
+        b = fma(o[t], o[t], b);
+        c = fma(u[t], o[t], c);
+      }
+      if (lo) part[buf][warp][lane] = Part{a, b, c, T(0)};
+      __syncthreads();
+      const int slot = lo ? lane : q;
+      T al = T(0), be = T(0), ga = T(0);
+#pragma unroll
+      for (int w = 0; w < JW; ++w) {
+        const Part p = part[buf][w][slot];
+        al += p.a;
+        be += p.b;
+        ga += p.c;
+      }
+      buf ^= 1;
+      const bool rot = q != lane && al > negligible && be > negligible && ga * ga > tol2 * al * be;
+      // the rotation is formed in every lane (no divergent branch) and applied
+      // as the identity where it is not wanted
+      T cs, sn;
+      rotation(al, be, rot ? ga : T(1), cs, sn);
+      cs = rot ? cs : T(1);
+      // lower column: c x - s y; upper column: s x + c y
+      const T sg = rot ? (lo ? -sn : sn) : T(0);
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) u[t] = fma(sg, o[t], cs * u[t]);
+      if (kWithV) {
+#pragma unroll
+        for (int t = 0; t < RPW; ++t) {
+          const T ov = __shfl_sync(0xffffffffu, v[t], q);
+          v[t] = fma(sg, ov, cs * v[t]);
+        }
+      }
+      any |= rot ? 1 : 0;
+    }
+    converged = __syncthreads_or(any) == 0;
+  }
+  if (!converged && threadIdx.x == 0) set_status(status, kStatusNoConvergence);
+  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+  // column norms ||u_j|| in FP64
+  {
+    double un = 0.0;
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) un = fma(static_cast<double>(u[t]), static_cast<double>(u[t]), un);
+    red[warp][lane] = un;
+    if (kWithV)
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) Vs[(warp * RPW + t) * (kSmallN + 1) + lane] = v[t];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double s = 0.0;
+    for (int w = 0; w < JW; ++w) s += red[w][lane];
+    unrm[lane] = sqrt(s);
+  }
+  __syncthreads();
+  if (kWithV) {
+    // sigma_j^2 = ||R v_j||^2 / ||v_j||^2 in FP64: thread (warp, lane) takes
+    // column j = lane and rows i = warp, warp + JW, ...
+    const int j = lane;
+    double num = 0.0;
+    if (j < n)
+      for (int i = warp; i < n; i += JW) {
+        double y0 = 0.0, y1 = 0.0;
+        int k = i;
+        for (; k + 1 < n; k += 2) {
+          y0 = fma(Rs[i * kSmallN + k], static_cast<double>(Vs[k * (kSmallN + 1) + j]), y0);
+          y1 = fma(Rs[i * kSmallN + k + 1], static_cast<double>(Vs[(k + 1) * (kSmallN + 1) + j]), y1);
+        }
+        if (k < n) y0 = fma(Rs[i * kSmallN + k], static_cast<double>(Vs[k * (kSmallN + 1) + j]), y0);
+        const double yy = y0 + y1;
+        num = fma(yy, yy, num);
+      }
+    red[warp][lane] = num;
+    __syncthreads();
+    if (warp == 0) {
+      double s = 0.0, den = 0.0;
+      for (int w = 0; w < JW; ++w) s += red[w][lane];
+      for (int k = 0; k < n; ++k) {
+        const double vk = static_cast<double>(Vs[k * (kSmallN + 1) + lane]);
+        den = fma(vk, vk, den);
+      }
+      double umax = 0.0;
+      for (int k = 0; k < n; ++k) umax = unrm[k] > umax ? unrm[k] : umax;
+      double sg = (lane < n && den > 0.0) ? sqrt(s / den) : 0.0;
+      // below 1e-3 sigma_max the column norm is the more accurate value
+      if (unrm[lane] < 1e-3 * umax) sg = unrm[lane];
+      sig[lane] = sg;
+    }
+  } else {
+    if (warp == 0) sig[lane] = unrm[lane];
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    const int j = threadIdx.x;
+    const double val = sig[j];
+    int rank = 0;
+    for (int k = 0; k < n; ++k) {
+      const double w = sig[k];
+      rank += (w > val) || (w == val && k < j);
+    }
+    sigma[rank] = val;
+  }
+}
+
+template <typename T, bool kWithV, int JW>
+__global__ void __launch_bounds__(32 * JW) jacobi32_kernel(const double* R, int64_t ldr, int n, int max_sweeps,
+                                                           double tol_in, double* sigma, int32_t* status,
+                                                           int32_t* sweeps_out) {
+  pdl_enter();
+  jacobi32_body<T, kWithV, JW>(R, ldr, n, max_sweeps, tol_in, sigma, status, sweeps_out);
+}
+
+// Warps of the register-resident Jacobi (rows per warp = 32 / JW).
+constexpr int kJacobi32Warps = 4;
+
 // ---- batched forms: one CTA per instance (job j = CTA j)
 template <typename T, bool kSmall>
 __global__ void __launch_bounds__(1024) chol_first_batched(BatchDev b, BatchJobs J) {
@@ -516,6 +976,31 @@ __global__ void __launch_bounds__(1024) jacobi_batched(BatchDev b, BatchJobs J) 
                                   &P.hdr->jacobi_sweeps);
 }
 
+
+template <typename T>
+__global__ void __launch_bounds__(kC8Threads) chol_first32_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
+  const Plan& P = b.plans[J.inst[blockIdx.x]];
+  chol_first32_body<T>(P.G1, P.n, dense_tol(P), P.R1, P.W, P.Wf, P.active, &P.hdr->status);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kC8Threads) chol_second32_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
+  const int i = J.inst[blockIdx.x];
+  const Plan& P = b.plans[i];
+  chol_second32_body<T>(P.G2, P.n, dense_tol(P), P.R1, P.Wf, P.active, P.mixed, P.R, b.out[i].R, P.n,
+                        &P.hdr->status);
+}
+
+template <typename T, bool kWithV>
+__global__ void __launch_bounds__(32 * kJacobi32Warps) jacobi32_batched(BatchDev b, BatchJobs J) {
+  pdl_enter();
+  const int i = J.inst[blockIdx.x];
+  const Plan& P = b.plans[i];
+  jacobi32_body<T, kWithV, kJacobi32Warps>(P.R, P.n, P.n, P.max_sweeps, jacobi_tol(P), b.out[i].sigma,
+                                           &P.hdr->status, &P.hdr->jacobi_sweeps);
+}
 }  // namespace
 
 static double default_tol(const Plan& p) { return dense_tol(p); }
@@ -533,6 +1018,12 @@ static cudaError_t chol_first_t(const Plan& p, cudaStream_t s) {
   const bool small = sizeof(T) * 2 * static_cast<size_t>(n) * n <= 96 * 1024;
   size_t smem = sizeof(T) * (static_cast<size_t>(n) * n + 3 * n) + sizeof(int32_t) * (n + 4) + 16;
   if (small) smem += sizeof(T) * static_cast<size_t>(n) * n;
+  if (n <= kSmallN) {
+    pdl_launch(chol_first32_kernel<T>, 1, kC8Threads, 0, s, p.G1, n, default_tol(p), p.R1, p.W, p.Wf, p.active,
+               &p.hdr->status);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   auto kern = small ? chol_first_kernel<T, true> : chol_first_kernel<T, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
@@ -551,6 +1042,12 @@ static cudaError_t chol_second_t(const Plan& p, double* R_out, int64_t ldr, cuda
   const int n = p.n;
   size_t smem = ((sizeof(T) * (static_cast<size_t>(n) * n + 2 * n) + sizeof(int32_t) * n + 15) & ~size_t(15));
   if (p.mixed) smem += sizeof(double) * static_cast<size_t>(n) * n;
+  if (n <= kSmallN) {
+    pdl_launch(chol_second32_kernel<T>, 1, kC8Threads, 0, s, p.G2, n, default_tol(p), p.R1, p.Wf, p.active,
+               p.mixed ? 1 : 0, p.R, R_out, ldr, &p.hdr->status);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   auto kern = chol_second_kernel<T, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
@@ -585,25 +1082,34 @@ static cudaError_t jacobi_t(const Plan& p, const double* R, int64_t ldr, double*
   return cudaGetLastError();
 }
 
+template <typename T, bool kWithV>
+static cudaError_t jacobi32_t(const Plan& p, const double* R, int64_t ldr, double* sigma, double tol, cudaStream_t s) {
+  pdl_launch(jacobi32_kernel<T, kWithV, kJacobi32Warps>, 1, 32 * kJacobi32Warps, 0, s, R, ldr, p.n, p.max_sweeps, tol,
+             sigma, &p.hdr->status, &p.hdr->jacobi_sweeps);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s) {
   if (p.wide) return launch_wide_jacobi(p, R, ldr, sigma, s);
   const int n = p.n;
   if (p.mixed) {
     // FP32 sweeps stop at |u_p . u_q| <= 1e-5 ||u_p|| ||u_q||: the FP64
     // Rayleigh quotient then has a relative error of order 1e-10 / gap
-    if (n <= 32) return jacobi_t<float, true, 1>(p, R, ldr, sigma, 1e-5, s);
+    if (n <= kSmallN) return jacobi32_t<float, true>(p, R, ldr, sigma, 1e-5, s);
     if (n <= 64) return jacobi_t<float, true, 2>(p, R, ldr, sigma, 1e-5, s);
     return jacobi_t<float, true, 4>(p, R, ldr, sigma, 1e-5, s);
   }
   const double tol = 4.0 * n * 1.1102230246251565e-16;
-  if (n <= 32) return jacobi_t<double, false, 1>(p, R, ldr, sigma, tol, s);
+  if (n <= kSmallN) return jacobi32_t<double, false>(p, R, ldr, sigma, tol, s);
   if (n <= 64) return jacobi_t<double, false, 2>(p, R, ldr, sigma, tol, s);
   return jacobi_t<double, false, 4>(p, R, ldr, sigma, tol, s);
 }
 
 // Batched dense steps.  step 1: first Cholesky (variant 0: column-per-thread
-// inverse with a second n x n buffer, 1: in-place inverse); step 2: second
-// Cholesky and R; step 3: Jacobi (variant = rows per lane 1, 2, 4 -> 0, 1, 2).
+// inverse with a second n x n buffer, 1: in-place inverse, 2: n <= 32 in one
+// warp); step 2: second Cholesky and R (variant 1: n <= 32); step 3: Jacobi
+// (variant 0: n <= 32 in registers, 1 and 2: 2 and 4 rows per lane).
 template <typename T>
 static size_t chol_first_smem(int n, bool small) {
   size_t smem = sizeof(T) * (static_cast<size_t>(n) * n + 3 * n) + sizeof(int32_t) * (n + 4) + 16;
@@ -615,11 +1121,23 @@ void dense_batch_info(const Plan& p, int step, int* variant, size_t* smem, int* 
   const int n = p.n;
   const size_t es = p.mixed ? 4 : 8;
   if (step == 1) {
+    if (n <= kSmallN) {
+      *variant = 2;
+      *smem = 0;
+      *threads = kC8Threads;
+      return;
+    }
     const bool small = es * 2 * static_cast<size_t>(n) * n <= 96 * 1024;
     *variant = small ? 0 : 1;
     *smem = p.mixed ? chol_first_smem<float>(n, small) : chol_first_smem<double>(n, small);
     *threads = dense_threads(n);
   } else if (step == 2) {
+    if (n <= kSmallN) {
+      *variant = 1;
+      *smem = 0;
+      *threads = kC8Threads;
+      return;
+    }
     *variant = 0;
     *smem = ((es * (static_cast<size_t>(n) * n + 2 * n) + sizeof(int32_t) * n + 15) & ~size_t(15)) +
             (p.mixed ? sizeof(double) * static_cast<size_t>(n) * n : 0);
@@ -628,6 +1146,11 @@ void dense_batch_info(const Plan& p, int step, int* variant, size_t* smem, int* 
     const int np = n + (n & 1), npairs = np / 2;
     const int npl = n <= 32 ? 1 : (n <= 64 ? 2 : 4);
     *variant = npl == 1 ? 0 : (npl == 2 ? 1 : 2);
+    if (npl == 1) {  // register-resident form
+      *threads = 32 * kJacobi32Warps;
+      *smem = 0;
+      return;
+    }
     int t = 32 * npairs;  // one warp per pair (32 lanes per pair)
     *threads = t > 1024 ? 1024 : t;
     const bool with_v = p.mixed != 0;
@@ -656,20 +1179,25 @@ cudaError_t launch_batch_dense(const BatchDev& b, int step, const BatchJobs jobs
     if (mixed) {
       e = launch_bucket(chol_first_batched<float, true>, b, jobs[0], smem[0], threads[0], s);
       if (e == cudaSuccess) e = launch_bucket(chol_first_batched<float, false>, b, jobs[1], smem[1], threads[1], s);
+      if (e == cudaSuccess) e = launch_bucket(chol_first32_batched<float>, b, jobs[2], smem[2], threads[2], s);
     } else {
       e = launch_bucket(chol_first_batched<double, true>, b, jobs[0], smem[0], threads[0], s);
       if (e == cudaSuccess) e = launch_bucket(chol_first_batched<double, false>, b, jobs[1], smem[1], threads[1], s);
+      if (e == cudaSuccess) e = launch_bucket(chol_first32_batched<double>, b, jobs[2], smem[2], threads[2], s);
     }
   } else if (step == 2) {
     e = mixed ? launch_bucket(chol_second_batched<float>, b, jobs[0], smem[0], threads[0], s)
               : launch_bucket(chol_second_batched<double>, b, jobs[0], smem[0], threads[0], s);
+    if (e == cudaSuccess)
+      e = mixed ? launch_bucket(chol_second32_batched<float>, b, jobs[1], smem[1], threads[1], s)
+                : launch_bucket(chol_second32_batched<double>, b, jobs[1], smem[1], threads[1], s);
   } else {
     if (mixed) {
-      e = launch_bucket(jacobi_batched<float, true, 1>, b, jobs[0], smem[0], threads[0], s);
+      e = launch_bucket(jacobi32_batched<float, true>, b, jobs[0], smem[0], threads[0], s);
       if (e == cudaSuccess) e = launch_bucket(jacobi_batched<float, true, 2>, b, jobs[1], smem[1], threads[1], s);
       if (e == cudaSuccess) e = launch_bucket(jacobi_batched<float, true, 4>, b, jobs[2], smem[2], threads[2], s);
     } else {
-      e = launch_bucket(jacobi_batched<double, false, 1>, b, jobs[0], smem[0], threads[0], s);
+      e = launch_bucket(jacobi32_batched<double, false>, b, jobs[0], smem[0], threads[0], s);
       if (e == cudaSuccess) e = launch_bucket(jacobi_batched<double, false, 2>, b, jobs[1], smem[1], threads[1], s);
       if (e == cudaSuccess) e = launch_bucket(jacobi_batched<double, false, 4>, b, jobs[2], smem[2], threads[2], s);
     }

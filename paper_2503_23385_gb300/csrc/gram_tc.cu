@@ -1240,28 +1240,37 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
       if (i == n - 1) ok = drain(i);
     }
     // pieces of each Gram row a: 2 halves x R positions x (2 accumulators in pass 1), summed in a fixed order
+    // in float-float (FP64 arithmetic is slow on this GPU: only the final entries are converted)
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
-    double* pieces = reinterpret_cast<double*>(base);  // [sub][128 lanes][32]; the stages are idle now
+    float2* pieces = reinterpret_cast<float2*>(base);  // [sub][128 lanes][32]; the stages are idle now
     fold();
     if (drains) {
       const int i128 = quarter * 32 + lane;
 #pragma unroll
-      for (int j = 0; j < KK; ++j)
-        pieces[(sub * 128 + i128) * 32 + j] = static_cast<double>(fh[j]) + static_cast<double>(fl[j]);
+      for (int j = 0; j < KK; ++j) pieces[(sub * 128 + i128) * 32 + j] = make_float2(fh[j], fl[j]);
     }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
     double* part = a.part + static_cast<int64_t>(cta) * a.kout * a.kout;
     const int nsub = pass2 ? 1 : 2;
-    auto gram_entry = [&](int ra, int cbb) {
-      double g = 0.0;
+    auto gram_entry = [&](int ra, int cbb, float& h, float& l) {
       for (int sb = 0; sb < nsub; ++sb)
         for (int half = 0; half < 2; ++half)
-          for (int r = 0; r < RR; ++r) g += pieces[(sb * 128 + half * 64 + r * KK + ra) * 32 + cbb];
-      return g;
+          for (int r = 0; r < RR; ++r) {
+            const float2 p = pieces[(sb * 128 + half * 64 + r * KK + ra) * 32 + cbb];
+            float s_, e_;
+            two_sum(h, p.x, s_, e_);
+            h = s_;
+            l = __fadd_rn(l, __fadd_rn(e_, p.y));
+          }
     };
     for (int e = wt; e < KK * KK; e += 32 * kWorkWarps) {  // upper triangle, symmetrised
       const int ra = e / KK, cbb = e - ra * KK;
-      if (ra <= cbb) part[ra * a.kout + cbb] = 0.5 * (gram_entry(ra, cbb) + gram_entry(cbb, ra));
+      if (ra <= cbb) {
+        float h = 0.f, l = 0.f;
+        gram_entry(ra, cbb, h, l);
+        gram_entry(cbb, ra, h, l);
+        part[ra * a.kout + cbb] = 0.5 * (static_cast<double>(h) + static_cast<double>(l));
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
