@@ -782,8 +782,9 @@ __device__ __forceinline__ void jacobi32_body(const double* R, int64_t ldr, int 
   __shared__ Part part[2][JW][kSmallN];
   __shared__ double red[JW][kSmallN];
   __shared__ double sig[kSmallN], unrm[kSmallN];
-  __shared__ double Rs[kWithV ? kSmallN * kSmallN : 1];
+  __shared__ float Rh[kWithV ? kSmallN * kSmallN : 1], Rl[kWithV ? kSmallN * kSmallN : 1];  // R = Rh + Rl
   __shared__ T Vs[kWithV ? kSmallN * (kSmallN + 1) : 1];
+  __shared__ float2 redf[JW][kSmallN];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int np = n + (n & 1), m = np - 1;
   T u[RPW], v[RPW];
@@ -796,7 +797,10 @@ __device__ __forceinline__ void jacobi32_body(const double* R, int64_t ldr, int 
   if (kWithV)
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       const int i = e / n, k = e - i * n;
-      Rs[i * kSmallN + k] = R[static_cast<int64_t>(i) * ldr + k];
+      const double r = R[static_cast<int64_t>(i) * ldr + k];
+      const float h = static_cast<float>(r);
+      Rh[i * kSmallN + k] = h;
+      Rl[i * kSmallN + k] = static_cast<float>(r - static_cast<double>(h));
     }
   for (int e = threadIdx.x; e < 2 * JW * kSmallN; e += blockDim.x)
     (&part[0][0][0])[e] = Part{T(0), T(0), T(0), T(0)};  // idle lanes read slots nobody posts
@@ -873,58 +877,83 @@ __device__ __forceinline__ void jacobi32_body(const double* R, int64_t ldr, int 
   }
   if (!converged && threadIdx.x == 0) set_status(status, kStatusNoConvergence);
   if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
-  // column norms ||u_j|| in FP64
-  {
+  if (kWithV) {
+    // Mixed path: the singular values are FP64-accurate Rayleigh quotients
+    // sigma_j^2 = ||R v_j||^2 / ||v_j||^2, formed in float-float (R = Rh + Rl,
+    // exact products by FMA; FP64 arithmetic is slow on this GPU) with one
+    // FP64 division and square root per column.  Column norms ||u_j|| (the
+    // fallback below 1e-3 sigma_max) likewise.
+    {
+      float uh = 0.f, ul = 0.f;
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) ff_add_prod(uh, ul, static_cast<float>(u[t]), static_cast<float>(u[t]));
+      redf[warp][lane] = make_float2(uh, ul);
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) Vs[(warp * RPW + t) * (kSmallN + 1) + lane] = v[t];
+    }
+    __syncthreads();
+    float2 un = make_float2(0.f, 0.f);
+    if (warp == 0)
+      for (int w = 0; w < JW; ++w) {
+        float s_, e_;
+        two_sum(un.x, redf[w][lane].x, s_, e_);
+        un = make_float2(s_, __fadd_rn(un.y, __fadd_rn(e_, redf[w][lane].y)));
+      }
+    // thread (warp, lane): column j = lane, rows i = warp, warp + JW, ...
+    const int j = lane;
+    float nh = 0.f, nl = 0.f;
+    if (j < n)
+      for (int i = warp; i < n; i += JW) {
+        float yh = 0.f, yl = 0.f;
+        for (int k = i; k < n; ++k) {
+          const float vk = static_cast<float>(Vs[k * (kSmallN + 1) + j]);
+          ff_add_prod(yh, yl, Rh[i * kSmallN + k], vk);
+          yl = fmaf(Rl[i * kSmallN + k], vk, yl);
+        }
+        float s_, e_;
+        two_sum(yh, yl, s_, e_);  // normalise the pair before squaring
+        ff_add_prod(nh, nl, s_, s_);
+        nl = fmaf(2.f * s_, e_, nl);
+      }
+    __syncthreads();  // redf is read above by warp 0
+    redf[warp][lane] = make_float2(nh, nl);
+    __syncthreads();
+    if (warp == 0) {
+      float sh = 0.f, sl = 0.f, dh = 0.f, dl = 0.f;
+      for (int w = 0; w < JW; ++w) {
+        float s_, e_;
+        two_sum(sh, redf[w][lane].x, s_, e_);
+        sh = s_;
+        sl = __fadd_rn(sl, __fadd_rn(e_, redf[w][lane].y));
+      }
+      for (int k = 0; k < n; ++k) {
+        const float vk = static_cast<float>(Vs[k * (kSmallN + 1) + lane]);
+        ff_add_prod(dh, dl, vk, vk);
+      }
+      const double unorm = sqrt(static_cast<double>(un.x) + static_cast<double>(un.y));
+      unrm[lane] = lane < n ? unorm : 0.0;
+      __syncwarp();
+      double umax = 0.0;
+      for (int k = 0; k < n; ++k) umax = unrm[k] > umax ? unrm[k] : umax;
+      const double num = static_cast<double>(sh) + static_cast<double>(sl);
+      const double den = static_cast<double>(dh) + static_cast<double>(dl);
+      double sg = (lane < n && den > 0.0) ? sqrt(num / den) : 0.0;
+      // below 1e-3 sigma_max the column norm is the more accurate value
+      if (unorm < 1e-3 * umax) sg = unorm;
+      sig[lane] = sg;
+    }
+  } else {
+    // plain path: sigma_j = ||u_j|| in FP64
     double un = 0.0;
 #pragma unroll
     for (int t = 0; t < RPW; ++t) un = fma(static_cast<double>(u[t]), static_cast<double>(u[t]), un);
     red[warp][lane] = un;
-    if (kWithV)
-#pragma unroll
-      for (int t = 0; t < RPW; ++t) Vs[(warp * RPW + t) * (kSmallN + 1) + lane] = v[t];
-  }
-  __syncthreads();
-  if (warp == 0) {
-    double s = 0.0;
-    for (int w = 0; w < JW; ++w) s += red[w][lane];
-    unrm[lane] = sqrt(s);
-  }
-  __syncthreads();
-  if (kWithV) {
-    // sigma_j^2 = ||R v_j||^2 / ||v_j||^2 in FP64: thread (warp, lane) takes
-    // column j = lane and rows i = warp, warp + JW, ...
-    const int j = lane;
-    double num = 0.0;
-    if (j < n)
-      for (int i = warp; i < n; i += JW) {
-        double y0 = 0.0, y1 = 0.0;
-        int k = i;
-        for (; k + 1 < n; k += 2) {
-          y0 = fma(Rs[i * kSmallN + k], static_cast<double>(Vs[k * (kSmallN + 1) + j]), y0);
-          y1 = fma(Rs[i * kSmallN + k + 1], static_cast<double>(Vs[(k + 1) * (kSmallN + 1) + j]), y1);
-        }
-        if (k < n) y0 = fma(Rs[i * kSmallN + k], static_cast<double>(Vs[k * (kSmallN + 1) + j]), y0);
-        const double yy = y0 + y1;
-        num = fma(yy, yy, num);
-      }
-    red[warp][lane] = num;
     __syncthreads();
     if (warp == 0) {
-      double s = 0.0, den = 0.0;
-      for (int w = 0; w < JW; ++w) s += red[w][lane];
-      for (int k = 0; k < n; ++k) {
-        const double vk = static_cast<double>(Vs[k * (kSmallN + 1) + lane]);
-        den = fma(vk, vk, den);
-      }
-      double umax = 0.0;
-      for (int k = 0; k < n; ++k) umax = unrm[k] > umax ? unrm[k] : umax;
-      double sg = (lane < n && den > 0.0) ? sqrt(s / den) : 0.0;
-      // below 1e-3 sigma_max the column norm is the more accurate value
-      if (unrm[lane] < 1e-3 * umax) sg = unrm[lane];
-      sig[lane] = sg;
+      double s_ = 0.0;
+      for (int w = 0; w < JW; ++w) s_ += red[w][lane];
+      sig[lane] = sqrt(s_);
     }
-  } else {
-    if (warp == 0) sig[lane] = unrm[lane];
   }
   __syncthreads();
   if (threadIdx.x < n) {

@@ -544,6 +544,17 @@ __device__ __forceinline__ bool warp_wait(PipeSmem& S, uint64_t* b, uint32_t par
   return ok != 0;
 }
 
+// Non-blocking test of a phase parity.
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 __device__ __forceinline__ void mbar_arrive_cta(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
@@ -879,10 +890,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 // Each worker thread drains its TMEM lane (one row of D) into float-float
 // sums of the kk-wide row piece that belongs to its packed row position; the
 // pieces are added in a fixed order at the end.
-constexpr int kPackStages = 3;
+constexpr int kPackStages = 3;  // pass-1 X stages (64 KB each)
+constexpr int kP2Stages = 4;    // pass-2 X stages (32 KB each)
+constexpr int kGroupWarps = 4;  // warps of the drain and Q-formation groups (one per TMEM lane quarter)
+constexpr int kSplitWarps = 2;  // pass-2 split warps (pass 1 splits with these and the Q-formation group)
+constexpr int kPackWarps = 2 + 2 * kGroupWarps + kSplitWarps;
+constexpr int kPackThreads = 32 * kPackWarps;
 constexpr int kP1Stage = 4 * kPanelBytes;         // pass 1: raw (2 panels) + lo (2 panels)
 constexpr int kP2Stage = 2 * kPanelBytes;         // pass 2: raw (1 panel) + lo (1 panel)
-constexpr int kP2Zq = kPackStages * kP2Stage;     // 2 buffers x 4 panels x (64 rows x 128 B)
+constexpr int kP2Zq = kP2Stages * kP2Stage;       // 2 buffers x 4 panels x (64 rows x 128 B)
 constexpr int kP2ZqBytes = 4 * 64 * 128;
 constexpr int kP2Wh = kP2Zq + 2 * kP2ZqBytes;
 constexpr int kP2Wl = kP2Wh + 32 * 128;
@@ -951,23 +967,27 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
   const int64_t ntiles_all = (rows + tile_rows - 1) / tile_rows;
   const int n = ntiles_all > cta ? static_cast<int>((ntiles_all - 1 - cta) / G + 1) : 0;
   auto tile_index = [&](int i) -> int64_t { return static_cast<int64_t>(cta) + static_cast<int64_t>(i) * G; };
+  const int nst = pass2 ? kP2Stages : kPackStages;  // X stages in flight
   const int stage_bytes = pass2 ? kP2Stage : kP1Stage;
   const int raw_bytes = stage_bytes / 2;  // the lo parts follow the raw (hi) parts of a stage
   const int wrq = kTileRows / a.rr;       // pass 2: packed rows of Q per tile
+  // warps: 0 TMA, 1 MMA, 2-5 drain (D), 6-9 Q formation in pass 2 / split in pass 1, 10-11 split
+  const int split_warp0 = pass2 ? 2 + 2 * kGroupWarps : 2 + kGroupWarps;
+  const int split_warps = kPackWarps - split_warp0;
 
   if (tid == 0) {
     for (int q = 0; q < kPipeStages; ++q) {
       mbar_init(&S.tma_full[q], 1);
       mbar_init(&S.stage_empty[q], 1);
-      mbar_init(&S.op_full[q], kWorkWarps);
+      mbar_init(&S.op_full[q], split_warps);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&S.d1_full[b], 1);
-      mbar_init(&S.d1_empty[b], kWorkWarps);
-      mbar_init(&S.q_full[b], kWorkWarps);
+      mbar_init(&S.d1_empty[b], kGroupWarps);
+      mbar_init(&S.q_full[b], kGroupWarps);
       mbar_init(&S.q_empty[b], 1);
       mbar_init(&S.acc_full[b], 1);
-      mbar_init(&S.acc_empty[b], kWorkWarps);
+      mbar_init(&S.acc_empty[b], kGroupWarps);
     }
     mbar_init(&S.done, 1);
     S.abort = 0;
@@ -979,15 +999,16 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (pass2 && warp >= 2) {  // W^T (np rows x k, K-major 128-byte swizzle): hi and lo parts, zero padded
+    constexpr int kStagers = kPackThreads - 64;
     const int wt = tid - 64;
     float* wh = reinterpret_cast<float*>(base + kP2Wh);
     float* wl = reinterpret_cast<float*>(base + kP2Wl);
-    for (int e = wt; e < 32 * 32; e += 32 * kWorkWarps) {
+    for (int e = wt; e < 32 * 32; e += kStagers) {
       wh[e] = 0.f;
       wl[e] = 0.f;
     }
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
-    for (int e = wt; e < a.kout * a.k; e += 32 * kWorkWarps) {
+    asm volatile("bar.sync 1, %0;" ::"n"(kStagers) : "memory");
+    for (int e = wt; e < a.kout * a.k; e += kStagers) {
       const int nn = e / a.k, kc = e - nn * a.k;
       const float v = (kc <= nn) ? a.W[static_cast<int64_t>(kc) * a.wld + nn] : 0.f;  // W upper triangular
       const int off = sw128_offset(nn, kc, 32 * 128);
@@ -1005,15 +1026,23 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
   auto acc_addr = [&](int b, int q) {
     return pass2 ? tmem + 64u + static_cast<uint32_t>(b * 128) : tmem + static_cast<uint32_t>(b * 256 + q * 128);
   };
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // The tensor core reads an FP32 operand as TF32 by ignoring its low 13
+  // mantissa bits, so raw values serve as hi parts as they are; only the lo
+  // parts (v - hi rounded to TF32) are written.
+  auto lo_of = [](float4 v) {
+    return make_float4(tf32_rn(v.x - tf32_hi(v.x)), tf32_rn(v.y - tf32_hi(v.y)), tf32_rn(v.z - tf32_hi(v.z)),
+                       tf32_rn(v.w - tf32_hi(v.w)));
+  };
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int issued = 0;
       for (int i = 0; i < n; ++i) {
-        const int s = i % kPackStages;
-        if (i >= kPackStages &&
-            !pipe_wait(S, &S.stage_empty[s], static_cast<uint32_t>(((i / kPackStages) - 1) & 1), a.spin_limit, a.status))
+        const int s = i % nst;
+        if (i >= nst && !pipe_wait(S, &S.stage_empty[s], static_cast<uint32_t>(((i / nst) - 1) & 1), a.spin_limit,
+                                   a.status))
           break;
         if (a.withhold && i == 0) continue;  // the workers' bounded wait for this tile runs out
         unsigned char* dst = base + s * stage_bytes;
@@ -1028,10 +1057,9 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         }
         issued = i + 1;
       }
-      for (int i = issued > kPackStages ? issued - kPackStages : 0; i < issued; ++i)
+      for (int i = issued > nst ? issued - nst : 0; i < issued; ++i)
         if (!(a.withhold && i == 0))
-          drain_wait(&S.tma_full[i % kPackStages], static_cast<uint32_t>((i / kPackStages) & 1), a.spin_limit,
-                     a.status);
+          drain_wait(&S.tma_full[i % nst], static_cast<uint32_t>((i / nst) & 1), a.spin_limit, a.status);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issue
@@ -1039,31 +1067,10 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
       const uint32_t idg = idesc_tf32(128, 128, 1);
       const uint32_t idf = idesc_tf32(128, a.np);
       const uint32_t wh = smem_u32(base + kP2Wh), wl = smem_u32(base + kP2Wl);
-      auto formation = [&](int j) -> bool {  // D1[j & 1] = X_j W (3 x TF32, the large term last)
-        const int s = j % kPackStages, bd = j & 1;
-        if (!pipe_wait(S, &S.op_full[s], static_cast<uint32_t>((j / kPackStages) & 1), a.spin_limit, a.status))
-          return false;
-        if (j >= 2 && !pipe_wait(S, &S.d1_empty[bd], static_cast<uint32_t>(((j / 2) - 1) & 1), a.spin_limit, a.status))
-          return false;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = smem_u32(base + s * stage_bytes), al = ah + static_cast<uint32_t>(raw_bytes);
-        for (int ks = 0; ks < a.ksteps_f; ++ks) {
-          const uint32_t o = static_cast<uint32_t>(ks * 32);
-          mma_tf32(d1_addr(bd), desc_kmajor_sw128(al + o), desc_kmajor_sw128(wh + o), idf, ks > 0 ? 1u : 0u);
-          mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wl + o), idf, 1u);
-        }
-        for (int ks = 0; ks < a.ksteps_f; ++ks) {
-          const uint32_t o = static_cast<uint32_t>(ks * 32);
-          mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wh + o), idf, 1u);
-        }
-        mma_commit(&S.stage_empty[s]);
-        mma_commit(&S.d1_full[bd]);
-        return true;
-      };
       if (!pass2) {
         for (int i = 0; i < n; ++i) {
-          const int s = i % kPackStages, b = i & 1;
-          if (!pipe_wait(S, &S.op_full[s], static_cast<uint32_t>((i / kPackStages) & 1), a.spin_limit, a.status)) break;
+          const int s = i % nst, b = i & 1;
+          if (!pipe_wait(S, &S.op_full[s], static_cast<uint32_t>((i / nst) & 1), a.spin_limit, a.status)) break;
           if (i >= 2 && !pipe_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
             break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1076,94 +1083,154 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
           mma_commit(&S.stage_empty[s]);
           mma_commit(&S.acc_full[b]);
         }
-      } else if (n > 0 && formation(0)) {
-        for (int i = 0; i < n; ++i) {
-          const int b = i & 1;
-          if (i + 1 < n && !formation(i + 1)) break;
-          if (!pipe_wait(S, &S.q_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) break;
-          if (i >= 2 && !pipe_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
+      } else {
+        // Formations F(j) (D1[j & 1] = X_j W, 3 x TF32, the large term last) and
+        // Grams G(i) are issued as their inputs become ready: F one or two
+        // tiles ahead of G as the formation buffers allow.  Every barrier
+        // tested here is at most one phase behind the phase tested (each test
+        // follows the issue that consumed the previous phase), so the parity
+        // tests are exact.  The loop gives up after spin_limit idle polls.
+        int nf = 0, ng = 0;
+        int64_t idle = 0;
+        while (ng < n) {
+          bool progress = false;
+          if (nf < n) {
+            const int s = nf % nst, bd = nf & 1;
+            if (mbar_test(&S.op_full[s], static_cast<uint32_t>((nf / nst) & 1)) &&
+                (nf < 2 || mbar_test(&S.d1_empty[bd], static_cast<uint32_t>(((nf / 2) - 1) & 1)))) {
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const uint32_t ah = smem_u32(base + s * stage_bytes), al = ah + static_cast<uint32_t>(raw_bytes);
+              for (int ks = 0; ks < a.ksteps_f; ++ks) {
+                const uint32_t o = static_cast<uint32_t>(ks * 32);
+                mma_tf32(d1_addr(bd), desc_kmajor_sw128(al + o), desc_kmajor_sw128(wh + o), idf, ks > 0 ? 1u : 0u);
+                mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wl + o), idf, 1u);
+              }
+              for (int ks = 0; ks < a.ksteps_f; ++ks) {
+                const uint32_t o = static_cast<uint32_t>(ks * 32);
+                mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wh + o), idf, 1u);
+              }
+              mma_commit(&S.stage_empty[s]);
+              mma_commit(&S.d1_full[bd]);
+              ++nf;
+              progress = true;
+            }
+          }
+          if (ng < nf) {
+            const int b = ng & 1;
+            if (mbar_test(&S.q_full[b], static_cast<uint32_t>((ng / 2) & 1)) &&
+                (ng < 2 || mbar_test(&S.acc_empty[b], static_cast<uint32_t>(((ng / 2) - 1) & 1)))) {
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const uint64_t dz =
+                  desc_mn_sw128_32b(smem_u32(base + kP2Zq + b * kP2ZqBytes), static_cast<uint32_t>(wrq * 128));
+              for (int ks = 0; ks < wrq / 8; ++ks)
+                mma_tf32(acc_addr(b, 0), dz + static_cast<uint64_t>(ks * 64), dz + static_cast<uint64_t>(ks * 64), idg,
+                         ks > 0 ? 1u : 0u);
+              mma_commit(&S.q_empty[b]);
+              mma_commit(&S.acc_full[b]);
+              ++ng;
+              progress = true;
+            }
+          }
+          if (progress) {
+            idle = 0;
+          } else if (*reinterpret_cast<volatile int*>(&S.abort)) {
             break;
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t dz = desc_mn_sw128_32b(smem_u32(base + kP2Zq + b * kP2ZqBytes), static_cast<uint32_t>(wrq * 128));
-          for (int ks = 0; ks < wrq / 8; ++ks)
-            mma_tf32(acc_addr(b, 0), dz + static_cast<uint64_t>(ks * 64), dz + static_cast<uint64_t>(ks * 64), idg,
-                     ks > 0 ? 1u : 0u);
-          mma_commit(&S.q_empty[b]);
-          mma_commit(&S.acc_full[b]);
+          } else if (++idle > a.spin_limit) {
+            set_status(a.status, kStatusTimeout);
+            *reinterpret_cast<volatile int*>(&S.abort) = 1;
+            break;
+          } else if (idle > 8) {
+            __nanosleep(32);  // leave the issue slots to the worker warps while nothing is ready
+          }
         }
       }
       mma_commit(&S.done);
       drain_wait(&S.done, 0u, a.spin_limit, a.status);
     }
-  } else {
-    // ------------------------------------------------------------ workers
-    const int wt = tid - 64;
-    const int quarter = warp & 3, sub = (warp - 2) >> 2;
-    auto split = [&](int i) -> bool {
-      const int s = i % kPackStages;
-      if (!warp_wait(S, &S.tma_full[s], static_cast<uint32_t>((i / kPackStages) & 1), a.spin_limit, a.status))
-        return false;
+  } else if (warp >= split_warp0) {
+    // ------------------------------------------------------------ split
+    const int st = tid - 32 * split_warp0, nth = 32 * split_warps;
+    for (int i = 0; i < n; ++i) {
+      const int s = i % nst;
+      if (!warp_wait(S, &S.tma_full[s], static_cast<uint32_t>((i / nst) & 1), a.spin_limit, a.status)) break;
       float4* X4 = reinterpret_cast<float4*>(base + s * stage_bytes);
       float4* L4 = reinterpret_cast<float4*>(base + s * stage_bytes + raw_bytes);
       const int64_t t0 = tile_index(i);
       const bool full = (t0 + 1) * tile_rows <= rows;  // no row of the tile lies past the end
-      for (int e = wt; e < raw_bytes / 16; e += 32 * kWorkWarps) {
-        float4 v = X4[e];
-        if (!full) {
-          int64_t row;
-          if (pass2) {
-            row = t0 * kTileRows + (e >> 3);  // K-major: 8 float4 per 128-byte row
-          } else {  // packed row w of panel p: the logical column gives the row inside the packed row
-            const int p = e >> 10, w = (e & 1023) >> 3, slot = e & 7;
-            const int col = p * 32 + (((slot >> 1) ^ (w & 3)) << 3) + ((slot & 1) << 2);
-            row = (t0 * kTileRows + w) * RR + col / KK;
+      if (!pass2) {
+        // 2 panels of 128 packed rows (2,048 float4), loads before stores in batches of 4
+        constexpr int kVec = kP1Stage / 2 / 16;
+        for (int e0 = st; e0 < kVec; e0 += 4 * nth) {
+          float4 v[4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int e = e0 + m * nth;
+            v[m] = e < kVec ? X4[e] : zero4;
           }
-          if (row >= rows) v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int e = e0 + m * nth;
+            if (e < kVec) {
+              bool clear = false;
+              if (!full) {  // packed row w of panel p: the logical column gives the row inside the packed row
+                const int p = e >> 10, w = (e & 1023) >> 3, slot = e & 7;
+                const int col = p * 32 + (((slot >> 1) ^ (w & 3)) << 3) + ((slot & 1) << 2);
+                clear = (t0 * kTileRows + w) * RR + col / KK >= rows;
+              }
+              if (clear) X4[e] = zero4;
+              L4[e] = clear ? zero4 : lo_of(v[m]);
+            }
+          }
         }
-        float4 h, l;
-        h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
-        l.x = tf32_rn(v.x - h.x); l.y = tf32_rn(v.y - h.y); l.z = tf32_rn(v.z - h.z); l.w = tf32_rn(v.w - h.w);
-        X4[e] = h;
-        L4[e] = l;
+      } else {
+        // rows r = st, st + nth, ...: the 16-byte chunks c < 2 ceil(k / 8) the
+        // formation reads (chunk c sits at c ^ (r mod 8) of the 128-byte
+        // swizzle; columns past k are zero-filled by the copy)
+        const int cpr = 2 * a.ksteps_f;
+        for (int r = st; r < kTileRows; r += nth) {
+          const bool clear = !full && t0 * kTileRows + r >= rows;
+          float4 v[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) v[c] = c < cpr ? X4[r * 8 + (c ^ (r & 7))] : zero4;
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c < cpr) {
+              const int e = r * 8 + (c ^ (r & 7));
+              if (clear) X4[e] = zero4;
+              L4[e] = clear ? zero4 : lo_of(v[c]);
+            }
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_cta(&S.op_full[s]);
-      return true;
-    };
-    // this thread's places in the packed Q layout (fixed for the whole launch)
-    const int qt = quarter * 32 + lane, qc0 = sub * 16;
-    int qoff_h[4], qoff_l[4];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const int w = qt / RR, cbq = (qt % RR) * KK + qc0 + 4 * g;
-      qoff_h[g] = z_offset(w, cbq, wrq);
-      qoff_l[g] = z_offset(w, 64 + cbq, wrq);
     }
-    auto make_q = [&](int i) -> bool {
+  } else if (warp >= 2 + kGroupWarps) {
+    // ------------------------------------------------------------ Q formation (pass 2)
+    // Q = X W (TMEM lane qt = row of the tile) into the packed Gram operand:
+    // row qt is packed row qt / R, position qt mod R (columns (qt mod R) KK + c)
+    const int quarter = warp & 3;
+    const int qt = quarter * 32 + lane;
+    const int w = qt / RR, c0 = (qt % RR) * KK;
+    for (int i = 0; i < n; ++i) {
       const int b = i & 1;
-      if (!warp_wait(S, &S.d1_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) return false;
+      if (!warp_wait(S, &S.d1_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) break;
       if (i >= 2 && !warp_wait(S, &S.q_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
-        return false;
+        break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // TMEM lane qt = row of the tile; columns qc0 .. qc0 + 15 of Q
-      float q[16];
-      tmem_ld16(d1_addr(b) + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(qc0), q);
+      uint32_t q[KK];
+      tmem_ld_nowait<KK>(d1_addr(b) + (static_cast<uint32_t>(quarter * 32) << 16), q);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       const bool live = tile_index(i) * kTileRows + qt < rows;
-      if (qc0 < KK) {
-        unsigned char* zq = base + kP2Zq + b * kP2ZqBytes;
+      unsigned char* zq = base + kP2Zq + b * kP2ZqBytes;
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          if (qc0 + 4 * g >= KK) break;
-          float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-          if (live) {
-            const float* v = q + 4 * g;
-            h = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
-            l = make_float4(tf32_rn(v[0] - h.x), tf32_rn(v[1] - h.y), tf32_rn(v[2] - h.z), tf32_rn(v[3] - h.w));
-          }
-          *reinterpret_cast<float4*>(zq + qoff_h[g]) = h;
-          *reinterpret_cast<float4*>(zq + qoff_l[g]) = l;
-        }
+      for (int g = 0; g < KK / 4; ++g) {
+        float4 h = zero4;
+        if (live)
+          h = make_float4(__uint_as_float(q[4 * g]), __uint_as_float(q[4 * g + 1]), __uint_as_float(q[4 * g + 2]),
+                          __uint_as_float(q[4 * g + 3]));
+        *reinterpret_cast<float4*>(zq + z_offset(w, c0 + 4 * g, wrq)) = h;
+        *reinterpret_cast<float4*>(zq + z_offset(w, 64 + c0 + 4 * g, wrq)) = lo_of(h);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1172,16 +1239,18 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         mbar_arrive_cta(&S.d1_empty[b]);
         mbar_arrive_cta(&S.q_full[b]);
       }
-      return true;
-    };
+    }
+  } else {
+    // ------------------------------------------------------------ drain
     // This thread's TMEM lane is row i = 32 quarter + lane of D; within its
     // 64-row half it is position r * KK + a of a packed row.  Its piece of the
     // Gram row a sits in the 32-column chunk cb (hi columns) and 64 + cb (lo),
     // at columns (lane / KK) * KK ... + KK of the chunk: every KK-column group
-    // of the chunk is loaded (warp-uniform addresses) and each lane keeps its own.
+    // of the chunk is loaded (warp-uniform addresses) and each lane keeps its
+    // own.  Pass 1 has two accumulators (alternate K steps), added alike.
+    const int quarter = warp & 3, gt = tid - 64;
     const int cb = (quarter & 1) * 32;
     const int mine = lane / KK;
-    const bool drains = !pass2 || sub == 0;
     float grp[KK], fh[KK], fl[KK];
 #pragma unroll
     for (int j = 0; j < KK; ++j) {
@@ -1200,70 +1269,71 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         grp[j] = 0.f;
       }
     };
-    auto drain = [&](int i) -> bool {
+    for (int i = 0; i < n; ++i) {
       const int b = i & 1;
-      if (!warp_wait(S, &S.acc_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) return false;
+      if (!warp_wait(S, &S.acc_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (drains) {
-        const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
-        const uint32_t acc = acc_addr(b, pass2 ? 0 : sub) + lanes + static_cast<uint32_t>(cb);
-        constexpr int C = 32 / KK;
-        uint32_t rh[C][KK], rl[C][KK];
+      const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
+      constexpr int C = 32 / KK;
+      for (int q = 0; q < (pass2 ? 1 : 2); ++q) {
+        const uint32_t acc = acc_addr(b, q) + lanes + static_cast<uint32_t>(cb);
+        if constexpr (KK == 32) {  // the whole chunk is this lane's: two halves of 16 columns
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          tmem_ld_nowait<KK>(acc + static_cast<uint32_t>(c * KK), rh[c]);
-          tmem_ld_nowait<KK>(acc + 64u + static_cast<uint32_t>(c * KK), rl[c]);
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          for (int hh = 0; hh < 2; ++hh) {
+            uint32_t rh[16], rl[16];
+            tmem_ld_nowait<16>(acc + static_cast<uint32_t>(hh * 16), rh);
+            tmem_ld_nowait<16>(acc + 64u + static_cast<uint32_t>(hh * 16), rl);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < C; ++c)
-          if (c == mine) {
-#pragma unroll
-            for (int j = 0; j < KK; ++j)
-              grp[j] = __fadd_rn(grp[j], __fadd_rn(__uint_as_float(rh[c][j]), __uint_as_float(rl[c][j])));
+            for (int j = 0; j < 16; ++j)
+              grp[hh * 16 + j] = __fadd_rn(grp[hh * 16 + j], __fadd_rn(__uint_as_float(rh[j]), __uint_as_float(rl[j])));
           }
-        if (++grouped == kDrainGroup) {
-          fold();
-          grouped = 0;
+        } else {
+          uint32_t rh[C][KK], rl[C][KK];
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            tmem_ld_nowait<KK>(acc + static_cast<uint32_t>(c * KK), rh[c]);
+            tmem_ld_nowait<KK>(acc + 64u + static_cast<uint32_t>(c * KK), rl[c]);
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < C; ++c)
+            if (c == mine) {
+#pragma unroll
+              for (int j = 0; j < KK; ++j)
+                grp[j] = __fadd_rn(grp[j], __fadd_rn(__uint_as_float(rh[c][j]), __uint_as_float(rl[c][j])));
+            }
         }
+      }
+      if (++grouped == kDrainGroup) {
+        fold();
+        grouped = 0;
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_cta(&S.acc_empty[b]);
-      return true;
-    };
-    bool ok = n == 0 || split(0);
-    for (int i = 0; ok && i < n; ++i) {
-      if (i + 1 < n && !split(i + 1)) break;
-      if (pass2 && !make_q(i)) break;
-      if (i >= 1 && !drain(i - 1)) break;
-      if (i == n - 1) ok = drain(i);
     }
-    // pieces of each Gram row a: 2 halves x R positions x (2 accumulators in pass 1), summed in a fixed order
+    // pieces of each Gram row a: 2 halves x R positions, summed in a fixed order
     // in float-float (FP64 arithmetic is slow on this GPU: only the final entries are converted)
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
-    float2* pieces = reinterpret_cast<float2*>(base);  // [sub][128 lanes][32]; the stages are idle now
+    asm volatile("bar.sync 2, %0;" ::"n"(32 * kGroupWarps) : "memory");
+    float2* pieces = reinterpret_cast<float2*>(base);  // [128 lanes][32]; the stages are idle now
     fold();
-    if (drains) {
-      const int i128 = quarter * 32 + lane;
+    const int i128 = quarter * 32 + lane;
 #pragma unroll
-      for (int j = 0; j < KK; ++j) pieces[(sub * 128 + i128) * 32 + j] = make_float2(fh[j], fl[j]);
-    }
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kWorkWarps) : "memory");
+    for (int j = 0; j < KK; ++j) pieces[i128 * 32 + j] = make_float2(fh[j], fl[j]);
+    asm volatile("bar.sync 2, %0;" ::"n"(32 * kGroupWarps) : "memory");
     double* part = a.part + static_cast<int64_t>(cta) * a.kout * a.kout;
-    const int nsub = pass2 ? 1 : 2;
     auto gram_entry = [&](int ra, int cbb, float& h, float& l) {
-      for (int sb = 0; sb < nsub; ++sb)
-        for (int half = 0; half < 2; ++half)
-          for (int r = 0; r < RR; ++r) {
-            const float2 p = pieces[(sb * 128 + half * 64 + r * KK + ra) * 32 + cbb];
-            float s_, e_;
-            two_sum(h, p.x, s_, e_);
-            h = s_;
-            l = __fadd_rn(l, __fadd_rn(e_, p.y));
-          }
+      for (int half = 0; half < 2; ++half)
+        for (int r = 0; r < RR; ++r) {
+          const float2 p = pieces[(half * 64 + r * KK + ra) * 32 + cbb];
+          float s_, e_;
+          two_sum(h, p.x, s_, e_);
+          h = s_;
+          l = __fadd_rn(l, __fadd_rn(e_, p.y));
+        }
     };
-    for (int e = wt; e < KK * KK; e += 32 * kWorkWarps) {  // upper triangle, symmetrised
+    for (int e = gt; e < KK * KK; e += 32 * kGroupWarps) {  // upper triangle, symmetrised
       const int ra = e / KK, cbb = e - ra * KK;
       if (ra <= cbb) {
         float h = 0.f, l = 0.f;
@@ -1282,7 +1352,7 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
 }
 
 template <int KK>
-__global__ void __launch_bounds__(kPipeThreads, 1)
+__global__ void __launch_bounds__(kPackThreads, 1)
     gram_pack_kernel(const __grid_constant__ CUtensorMap tmx, PackArgs a) {
   pdl_enter();
   gram_pack_body<KK>(&tmx, a, blockIdx.x, gridDim.x);
@@ -1415,7 +1485,7 @@ __device__ __forceinline__ int tc_batch_job(const TcBatch& B, int cta) {
 }
 
 template <int KK>
-__global__ void __launch_bounds__(kPipeThreads, 1) gram_pack_batched(const __grid_constant__ TcBatch B) {
+__global__ void __launch_bounds__(kPackThreads, 1) gram_pack_batched(const __grid_constant__ TcBatch B) {
   pdl_enter();
   const int j = tc_batch_job(B, blockIdx.x);
   const PackArgs a = pack_args_of(B.plans[B.inst[j]], B.pass, B.blk[j]);
@@ -1501,7 +1571,7 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
       if (err != cudaSuccess) return err;
       if (dev >= 0 && dev < 64) granted[dev][which] = 1;
     }
-    pdl_launch(kern, grid, kPipeThreads, kPackSmemBytes, s, map, a);
+    pdl_launch(kern, grid, kPackThreads, kPackSmemBytes, s, map, a);
     count_launches(1);
     return cudaGetLastError();
   }
@@ -1664,7 +1734,7 @@ cudaError_t launch_gram_tc_batch(const Plan* dev_plans, const Plan* host_plans, 
       B.blk[j] = static_cast<int8_t>(J.blk);
       B.first[j + 1] = B.first[j] + J.ctas;
     }
-    pdl_launch(kern, B.first[nj], engine == 1 ? kPipeThreads : kTcThreads, smem, s, B);
+    pdl_launch(kern, B.first[nj], engine == 1 ? kPackThreads : kTcThreads, smem, s, B);
     count_launches(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
