@@ -485,7 +485,7 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
           tc[pass - 1][eng - 1][tv].push_back(TcJob{i, b, ctas});
           tc_smem[pass - 1][eng - 1][tv] = std::max(tc_smem[pass - 1][eng - 1][tv], tsm);
           calls[i].p.gcount[pass - 1][b] = ctas;
-          calls[i].p.gsym[pass - 1][b] = eng == 2 ? 1 : 0;
+          calls[i].p.gsym[pass - 1][b] = eng == 2 ? 1 : 2;  // general engine: P pairs; packed: float-float
           continue;
         }
         int v = 0, ctas = 0;

@@ -215,47 +215,100 @@ struct ReduceArgs {
   int count[3];   // partials (blocks) per Gram block
   int kout[3];
   int off[3];     // diagonal offset of the block inside G
-  int sym[3];     // 1: partials hold P with G = (P + P^T) / 2 (tensor-core engine); 0: upper triangle
+  int sym[3];     // partial format: 0 FP64 upper triangle; 1 FP64 P with G = (P + P^T) / 2 (general
+                  // tensor-core engine); 2 float-float pairs, upper triangle (packed tensor-core engine)
   int n;
   double* G;
 };
 
-constexpr int kReduceWarps = 32;
+constexpr int kReduceWarps = 16;
 
 // G = sum of the three blocks' partials in a fixed order (deterministic).
 // A block owns 32 consecutive outputs (one per lane); its warps interleave
-// over the partials and their sums are combined in warp order.
+// over the partials.  Each thread issues the loads of up to five partials of
+// every block before its first addition (the loads are latency-bound).
+// Partials of the packed tensor-core engine are float-float pairs and are
+// summed in float-float (FP64 arithmetic is slow on this GPU); the others are
+// FP64.  Warp 0 adds the warps' sums.
 __device__ __forceinline__ void gram_reduce_body(const ReduceArgs& a, int bid) {
-  __shared__ double s[kReduceWarps][33];
+  __shared__ double sd[kReduceWarps][33];
+  __shared__ float2 sf[kReduceWarps][33];
+  constexpr int kPer = 5;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int e = bid * 32 + lane;
   const bool ok = e < a.n * a.n;
   const int i = ok ? e / a.n : 0, j = ok ? e - (e / a.n) * a.n : 0;
   const int lo = i < j ? i : j, hi = i < j ? j : i;
-  double tot = 0.0;
+  const unsigned long long* p0[3];
+  const unsigned long long* p1[3];
+  int64_t stride[3];
+  int cnt[3];
+  int maxc = 0;
+  bool any64 = false;
+#pragma unroll
   for (int b = 0; b < 3; ++b) {
-    if (!a.part[b] || !ok) continue;
     const int ko = a.kout[b];
     const int ii = lo - a.off[b], jj = hi - a.off[b];
-    if (ii < 0 || jj < 0 || ii >= ko || jj >= ko) continue;
-    const int64_t stride = static_cast<int64_t>(ko) * ko;
-    const double* p0 = a.part[b] + ii * ko + jj;
-    const double* p1 = a.part[b] + jj * ko + ii;  // the transposed entry (symmetrised partials)
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
-    int c = warp;
-#pragma unroll 4
-    for (; c < a.count[b]; c += kReduceWarps) {
-      const double v = a.sym[b] ? 0.5 * (p0[c * stride] + p1[c * stride]) : p0[c * stride];
-      t[(c / kReduceWarps) & 3] += v;
-    }
-    tot += (t[0] + t[1]) + (t[2] + t[3]);
+    const bool in = a.part[b] && ok && ii >= 0 && jj >= 0 && ii < ko && jj < ko;
+    cnt[b] = in ? a.count[b] : 0;
+    stride[b] = static_cast<int64_t>(ko) * ko;
+    const unsigned long long* base = reinterpret_cast<const unsigned long long*>(a.part[b]);
+    p0[b] = in ? base + ii * ko + jj : nullptr;
+    p1[b] = in ? base + jj * ko + ii : nullptr;  // the transposed entry (symmetrised partials)
+    maxc = a.count[b] > maxc ? a.count[b] : maxc;
+    any64 = any64 || (a.part[b] && a.sym[b] != 2);
   }
-  s[warp][lane] = tot;
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  float fh = 0.f, fl = 0.f;
+  for (int c0 = 0; c0 < maxc; c0 += kPer * kReduceWarps) {
+    unsigned long long v[3][kPer], w[3][kPer];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int c = c0 + warp + k * kReduceWarps;
+        const bool live = c < cnt[b];
+        v[b][k] = live ? p0[b][c * stride[b]] : 0ull;
+        w[b][k] = live && a.sym[b] == 1 ? p1[b][c * stride[b]] : 0ull;
+      }
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        if (a.sym[b] == 2) {
+          const float2 q = make_float2(__uint_as_float(static_cast<uint32_t>(v[b][k])),
+                                       __uint_as_float(static_cast<uint32_t>(v[b][k] >> 32)));
+          float s_, e_;
+          two_sum(fh, q.x, s_, e_);
+          fh = s_;
+          fl = __fadd_rn(fl, __fadd_rn(e_, q.y));
+        } else if (c0 + warp + k * kReduceWarps < cnt[b]) {
+          const double d = __longlong_as_double(static_cast<long long>(v[b][k]));
+          t[k & 3] += a.sym[b] == 1 ? 0.5 * (d + __longlong_as_double(static_cast<long long>(w[b][k]))) : d;
+        }
+      }
+  }
+  sd[warp][lane] = any64 ? (t[0] + t[1]) + (t[2] + t[3]) : 0.0;
+  sf[warp][lane] = make_float2(fh, fl);
   __syncthreads();
   if (warp == 0 && ok) {
-    double v = 0.0;
-    for (int w = 0; w < kReduceWarps; ++w) v += s[w][lane];
-    a.G[e] = v;
+    float gh = 0.f, gl = 0.f;
+#pragma unroll
+    for (int w = 0; w < kReduceWarps; ++w) {
+      const float2 q = sf[w][lane];
+      float s_, e_;
+      two_sum(gh, q.x, s_, e_);
+      gh = s_;
+      gl = __fadd_rn(gl, __fadd_rn(e_, q.y));
+    }
+    double g = static_cast<double>(gh) + static_cast<double>(gl);
+    if (any64) {
+      double u[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int w = 0; w < kReduceWarps; ++w) u[w & 3] += sd[w][lane];
+      g += (u[0] + u[1]) + (u[2] + u[3]);
+    }
+    a.G[e] = g;
   }
 }
 
@@ -487,7 +540,7 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     r.count[b] = grid;
     r.kout[b] = a.kout;
     r.off[b] = b == 2 ? p.n1 : 0;
-    r.sym[b] = (tc && !gram_tc_packs(a.k, a.kout, pass == 2)) ? 1 : 0;
+    r.sym[b] = tc ? (gram_tc_packs(a.k, a.kout, pass == 2) ? 2 : 1) : 0;
   }
   const int ne = p.n * p.n;
   pdl_launch(gram_reduce_kernel, (ne + 31) / 32, 32 * kReduceWarps, 0, s, r);

@@ -1339,7 +1339,8 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         float h = 0.f, l = 0.f;
         gram_entry(ra, cbb, h, l);
         gram_entry(cbb, ra, h, l);
-        part[ra * a.kout + cbb] = 0.5 * (static_cast<double>(h) + static_cast<double>(l));
+        // the partial as a float-float pair (8 bytes, the slot of an FP64 value)
+        reinterpret_cast<float2*>(part)[ra * a.kout + cbb] = make_float2(0.5f * h, 0.5f * l);
       }
     }
   }

@@ -115,8 +115,9 @@ struct Plan {
   void* yw = nullptr;                         // n pivots 1 / sqrt(d)
   void* d0w = nullptr;                        // n diagonal of the factored Gram
   double* sigw = nullptr;                     // 2n: unsorted singular values, FP32-sweep column norms
-  // batched calls: Gram partials written per (pass, block) and whether they
-  // hold P with G = (P + P^T) / 2 (general tensor-core engine)
+  // batched calls: Gram partials written per (pass, block) and their format
+  // (0 FP64 upper triangle, 1 FP64 P with G = (P + P^T) / 2 from the general
+  // tensor-core engine, 2 float-float pairs from the packed engine)
   int gcount[2][3] = {{0, 0, 0}, {0, 0, 0}};
   int gsym[2][3] = {{0, 0, 0}, {0, 0, 0}};
 };
