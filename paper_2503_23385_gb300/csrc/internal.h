@@ -14,7 +14,7 @@ constexpr int kMaxWidth = 128;          // n1 + n2 limit of the one-CTA dense n 
 constexpr int kMaxWideWidth = 512;      // n1 + n2 limit of the wide (multi-CTA) path
 constexpr int kMaxTableWidth = 256;     // per-table width limit of the wide path
 constexpr int kSortThreads = 512;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 13;  // 6,656-key tiles: 2 x 151 tiles for 1e6-row tables fill 152 SMs twice
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per radix tile
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
