@@ -331,3 +331,40 @@ def test_narrow_graded_columns(fg, torch):
         assert rel(R, Rref) <= tol and rel(s, sref) <= tol
         assert rel(R / dd, Rref / dd) <= 100 * tol
         assert np.max(np.abs(s - sref) / sref) <= tol_sv, np.max(np.abs(s - sref) / sref)
+
+
+@pytest.mark.parametrize("n1,n2", [(15, 16), (16, 16), (17, 16)], ids=["31", "32", "33"])
+def test_widths_around_the_register_kernels(fg, torch, n1, n2):
+    """n = 31 and 32 take the register-resident factorisations and Jacobi
+    (one column per lane), n = 33 the shared-memory forms: both against the
+    oracle, including an odd n (a zero column pads the Jacobi pairing)."""
+    A, B = make_pair(6000, n1, 5000, n2, 60, np.float32, "normal", seed=500 + n1)
+    check_against_oracle(fg, torch, A, B)
+
+
+@pytest.mark.parametrize("n1,n2,dup", [(16, 16, (3, 11)), (12, 11, (20, 14)), (4, 3, (1, 0))],
+                         ids=["32", "23-odd", "7"])
+def test_narrow_rank_deficient(fg, torch, n1, n2, dup):
+    """A column that repeats another (in A, or in B across the tables' block
+    boundary): the semi-definite factorisations mark it dependent, its row of
+    R is zero, R^T R matches the oracle's J^T J, sigma matches the oracle's and
+    the smallest singular value is at rounding level."""
+    A, B = make_pair(4000, n1, 3500, n2, 40, np.float64, "normal", seed=510 + n1 + n2)
+    xa, xb = A.x.copy(), B.x.copy()
+    i, j = dup  # column i of J repeats column j (indices in J = [A | B])
+    src = xa[:, j] if j < n1 else None
+    if i < n1:
+        xa[:, i] = src
+    else:
+        assert j >= n1
+        xb[:, i - n1] = xb[:, j - n1]
+    A, B = Table(xa, A.key), Table(xb, B.key)
+    for path, tol in (("fp64", 1e-10), ("mixed", 1e-6)):
+        Ar, Br = (A, B) if path == "fp64" else (as_f32(A), as_f32(B))
+        G = oracle.join_gram(Ar.x, Ar.key, Br.x, Br.key)
+        _, sref = oracle.join_r_sigma(Ar.x, Ar.key, Br.x, Br.key, route="reduced")
+        R, s = gpu_r_sigma(fg, torch, A, B, path)
+        assert np.all(R[max(i, j)] == 0), path
+        assert s[-1] <= 10 * tol * s[0], (path, s[-1] / s[0])
+        assert rel(s, sref) <= tol, (path, rel(s, sref))
+        assert rel(R.T @ R, G) <= tol, (path, rel(R.T @ R, G))
