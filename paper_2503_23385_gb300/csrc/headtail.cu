@@ -133,35 +133,64 @@ __device__ __forceinline__ void ht_plan_body(const HtTable& T, const int32_t* st
   lo = __shfl_sync(0xffffffffu, lo, 0);
   hi = __shfl_sync(0xffffffffu, hi, 0);
   if (hi <= lo) return;
-  // lanes own columns lane, lane + 32, ...; rows in order (fixed summation order)
+  // lanes own columns lane, lane + 32, ...; rows in order (fixed summation
+  // order).  FP32 compute type: float-float sums (FP64 adds are slow on this
+  // GPU); FP64 compute type: FP64 sums.
   const Tin* X = static_cast<const Tin*>(T.x);
   const int n = T.n;
   for (int c0 = 0; c0 < n; c0 += 32) {
     const int c = c0 + lane;
     double sum = 0.0;
     int64_t i = lo;
-    for (; i + 4 <= hi; i += 4) {
-      int64_t row[4];
+    if constexpr (sizeof(Tc) == 4) {
+      float h0 = 0.f, l0 = 0.f;
+      auto add = [&](float v) {
+        float s_, e_;
+        two_sum(h0, v, s_, e_);
+        h0 = s_;
+        l0 = __fadd_rn(l0, e_);
+      };
+      for (; i + 4 <= hi; i += 4) {
+        int32_t row[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) row[u] = clamp_idx(T.perm[i + u], T.m);
-      double v[4] = {0.0, 0.0, 0.0, 0.0};
-      if (c < n) {
+        for (int u = 0; u < 4; ++u) row[u] = static_cast<int32_t>(clamp_idx(T.perm[i + u], T.m));
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (c < n) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = as_compute_double<Tin, Tc>(X, row[u] * T.ld + c);
+          for (int u = 0; u < 4; ++u) v[u] = static_cast<float>(X[row[u] * T.ld + c]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) add(v[u]);
       }
+      for (; i < hi; ++i) {
+        const int64_t row = clamp_idx(T.perm[i], T.m);
+        if (c < n) add(static_cast<float>(X[row * T.ld + c]));
+      }
+      sum = static_cast<double>(h0) + static_cast<double>(l0);
+    } else {
+      for (; i + 4 <= hi; i += 4) {
+        int64_t row[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) sum += v[u];
-    }
-    for (; i < hi; ++i) {
-      const int64_t row = clamp_idx(T.perm[i], T.m);
-      if (c < n) sum += as_compute_double<Tin, Tc>(X, row * T.ld + c);
+        for (int u = 0; u < 4; ++u) row[u] = clamp_idx(T.perm[i + u], T.m);
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        if (c < n) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = as_compute_double<Tin, Tc>(X, row[u] * T.ld + c);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sum += v[u];
+      }
+      for (; i < hi; ++i) {
+        const int64_t row = clamp_idx(T.perm[i], T.m);
+        if (c < n) sum += as_compute_double<Tin, Tc>(X, row * T.ld + c);
+      }
     }
     if (c < n) T.piece[static_cast<int64_t>(k) * n + c] = sum;
   }
 }
 
 template <typename Tin, typename Tc>
-__global__ void __launch_bounds__(kHtBlock) ht_plan_kernel(HtArgs a, int total) {
+__global__ void __launch_bounds__(kHtBlock, 8) ht_plan_kernel(HtArgs a, int total) {  // 8 CTAs per SM: latency-bound
   pdl_enter();
   const int g = blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
   if (g >= total) return;
