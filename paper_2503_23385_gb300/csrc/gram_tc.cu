@@ -884,12 +884,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 // (M = 128, N = kout, 3 x TF32 in tensor memory) and the workers write Q's
 // split parts into the packed layout of the Gram of Q.
 //
-// Roles as in gram_pipe_kernel (TMA producer warp, MMA warp, 8 worker warps).
-// Tensor memory: pass 1 two sets x two accumulators of 128 columns; pass 2
-// two formation buffers of 32 columns and two accumulator sets of 128.
-// Each worker thread drains its TMEM lane (one row of D) into float-float
-// sums of the kk-wide row piece that belongs to its packed row position; the
-// pieces are added in a fixed order at the end.
+// Roles: a TMA producer warp, an MMA warp and three worker groups with loops
+// of their own that meet only at mbarriers: split (the lo parts of each X
+// tile; 2 warps in pass 2, 6 in pass 1), Q formation (pass 2: D1 from tensor
+// memory into the packed operand; 4 warps, one per TMEM lane quarter) and
+// drain (4 warps).  The MMA thread issues formations and Grams as their
+// inputs become ready.  Tensor memory: pass 1 two sets x two accumulators of
+// 128 columns; pass 2 two formation buffers of 32 columns and two
+// accumulator sets of 128.  Each drain thread adds its TMEM lane (one row of
+// D) into float-float sums of the kk-wide row piece that belongs to its
+// packed row position; the pieces are added in a fixed order at the end and
+// each CTA's partial is written as float-float pairs.
 constexpr int kPackStages = 3;  // pass-1 X stages (64 KB each)
 constexpr int kP2Stages = 4;    // pass-2 X stages (32 KB each)
 constexpr int kGroupWarps = 4;  // warps of the drain and Q-formation groups (one per TMEM lane quarter)
