@@ -1,5 +1,6 @@
 // Small dense n x n steps of CholeskyQR2 and the singular values.  One CTA
-// per instance (n <= 128), everything in shared memory.
+// per instance (n <= 128): for n <= 32 the matrix lives in registers (the
+// register-resident forms below), above in shared memory.
 //
 //  * chol_first:  R1 = chol(G1), semi-definite: a pivot below
 //                 rank_tol * G1_kk marks column k as dependent (zero row);
@@ -15,13 +16,15 @@
 // factorisations and the inverse run in FP32 -- R1 is only a preconditioner
 // (its rounding is removed by the second pass, and W is the exact inverse
 // used to form Q), and G2 = I + O(u) so R2 = chol(G2) in FP32 has an absolute
-// error of a few FP32 ulps -- while R = R2 R1 is formed in FP64; the Jacobi
-// sweeps run in FP32 accumulating V and each singular value is then the FP64
-// Rayleigh quotient ||R v_j|| / ||v_j||, whose error is second order in the
-// FP32 error of v_j.  FP64 dependent chains are slow on this GPU (tens of
-// cycles per FMA, hundreds per sqrt or divide), so the FP64 pivots use an
-// FP32 seed refined by two Newton steps for 1/sqrt(d), and dot products are
-// split across lanes.
+// error of a few FP32 ulps -- while R = R2 R1 is formed in extended precision
+// (FP64; float-float for n <= 32); the Jacobi sweeps run in FP32 accumulating
+// V and each singular value is then the Rayleigh quotient ||R v_j|| / ||v_j||
+// in extended precision, whose error is second order in the FP32 error of
+// v_j.  FP64 is slow on this GPU (about 2 FMA per SM per clock, 64 cycles of
+// latency, hundreds per sqrt or divide), so the FP64 pivots use an FP32 seed
+// refined by two Newton steps for 1/sqrt(d), dot products are split across
+// lanes, and the n <= 32 forms use float-float (exact FMA products,
+// compensated sums) instead.
 #include <cmath>
 
 #include "common.cuh"
