@@ -199,44 +199,92 @@ __global__ void __launch_bounds__(kHtBlock, 8) ht_plan_kernel(HtArgs a, int tota
 }
 
 // 2. carries: per (table, column), I_q = piece_q + (whole_q ? I_{q-1} : 0)
-// and carry_k = I_{k-1} for every chunk k that begins inside a run.
+// and carry_k = I_{k-1} for every chunk k that begins inside a run.  Thread
+// t of the CTA owns a contiguous range of chunks; its loads are issued in
+// batches of kScanBatch (flags and pieces both, the piece selected by the
+// flag afterwards) so that a range costs a few memory round trips; the
+// ranges' aggregates are combined by a segmented Hillis-Steele scan in
+// shared memory (log2 NT steps), then each thread walks its range again
+// from its carry-in and writes the carries.
+constexpr int kScanBatch = 8;
+constexpr int kScanWide = 1024;  // threads per column when a table has many chunks
+template <int NT>
 __device__ __forceinline__ void ht_scan_body(const HtTable& T, const int32_t* status, int c) {
-  __shared__ double s_agg[kHtBlock];
-  __shared__ int s_head[kHtBlock];
+  __shared__ double s_agg[NT];
+  __shared__ int s_head[NT];
+  __shared__ int s_skip;
   const int K = T.chunks;
-  if (K == 0 || timed_out(status)) return;
+  const int t = static_cast<int>(threadIdx.x);
+  if (t == 0) s_skip = (K == 0 || timed_out(status)) ? 1 : 0;
+  __syncthreads();
+  if (s_skip) return;
   const int n = T.n;
-  const int per = (K + kHtBlock - 1) / kHtBlock;
-  const int q0 = threadIdx.x * per, q1 = q0 + per < K ? q0 + per : K;
-  auto value = [&](int q) -> double {
-    return (q + 1 < K && (T.cflag[q + 1] & kInside)) ? T.piece[static_cast<int64_t>(q) * n + c] : 0.0;
+  const int per = (K + NT - 1) / NT;
+  const int q0 = t * per < K ? t * per : K, q1 = q0 + per < K ? q0 + per : K;
+  // flags f[u] of chunks qb + u (u <= kScanBatch: the next chunk's kInside
+  // bit decides whether piece qb + u counts) and the pieces themselves
+  uint32_t f[kScanBatch + 1];
+  double p[kScanBatch];
+  auto load = [&](int qb) {
+#pragma unroll
+    for (int u = 0; u <= kScanBatch; ++u) f[u] = qb + u < K ? T.cflag[qb + u] : 0u;
+#pragma unroll
+    for (int u = 0; u < kScanBatch; ++u) p[u] = qb + u < q1 ? T.piece[static_cast<int64_t>(qb + u) * n + c] : 0.0;
   };
   double agg = 0.0;
   int head = 0;
-  for (int q = q0; q < q1; ++q) {
-    if (!(T.cflag[q] & kWhole)) {
-      agg = 0.0;
-      head = 1;
+  for (int qb = q0; qb < q1; qb += kScanBatch) {
+    load(qb);
+#pragma unroll
+    for (int u = 0; u < kScanBatch; ++u) {
+      if (qb + u < q1) {
+        if (!(f[u] & kWhole)) {
+          agg = 0.0;
+          head = 1;
+        }
+        agg += (f[u + 1] & kInside) ? p[u] : 0.0;  // (an unused piece may be unset: selected, never added)
+      }
     }
-    agg += value(q);
   }
-  s_agg[threadIdx.x] = agg;
-  s_head[threadIdx.x] = head;
+  // inclusive segmented scan of the ranges' (aggregate, head) pairs
+  s_agg[t] = agg;
+  s_head[t] = head;
   __syncthreads();
-  int u = static_cast<int>(threadIdx.x) - 1;
-  while (u >= 0 && !s_head[u]) --u;
-  double I = 0.0;
-  for (int v = u < 0 ? 0 : u; v < static_cast<int>(threadIdx.x); ++v) I += s_agg[v];
-  for (int q = q0; q < q1; ++q) {
-    I = ((T.cflag[q] & kWhole) ? I : 0.0) + value(q);
-    if (q + 1 < K && (T.cflag[q + 1] & kInside)) T.carry[static_cast<int64_t>(q + 1) * n + c] = I;
+  for (int d = 1; d < NT; d <<= 1) {
+    double a2 = 0.0;
+    int h2 = 0;
+    if (t >= d) {
+      a2 = s_agg[t - d];
+      h2 = s_head[t - d];
+    }
+    __syncthreads();
+    if (t >= d) {
+      if (!head) agg = a2 + agg;
+      head |= h2;
+      s_agg[t] = agg;
+      s_head[t] = head;
+    }
+    __syncthreads();
+  }
+  double I = t > 0 ? s_agg[t - 1] : 0.0;
+  for (int qb = q0; qb < q1; qb += kScanBatch) {
+    load(qb);
+#pragma unroll
+    for (int u = 0; u < kScanBatch; ++u) {
+      if (qb + u < q1) {
+        const bool next_inside = (f[u + 1] & kInside) != 0;
+        I = ((f[u] & kWhole) ? I : 0.0) + (next_inside ? p[u] : 0.0);
+        if (next_inside) T.carry[static_cast<int64_t>(qb + u + 1) * n + c] = I;
+      }
+    }
   }
 }
 
-__global__ void __launch_bounds__(kHtBlock) ht_scan_kernel(HtArgs a, int n0) {
+template <int NT>
+__global__ void __launch_bounds__(NT) ht_scan_kernel(HtArgs a, int n0) {
   pdl_enter();
   const int t = static_cast<int>(blockIdx.x) < n0 ? 0 : 1;
-  ht_scan_body(a.t[t], a.status, t ? blockIdx.x - n0 : blockIdx.x);
+  ht_scan_body<NT>(a.t[t], a.status, t ? blockIdx.x - n0 : blockIdx.x);
 }
 
 __device__ __forceinline__ float tail_weight(float mo, int j) {
@@ -792,7 +840,11 @@ __global__ void __launch_bounds__(kHtStreamThreads)
 template <typename Tin, typename Tc>
 cudaError_t launch_typed_carry(const HtArgs& a, int total, int ncols, cudaStream_t s) {
   pdl_launch(ht_plan_kernel<Tin, Tc>, (total + kPlanWarps - 1) / kPlanWarps, kHtBlock, 0, s, a, total);
-  pdl_launch(ht_scan_kernel, ncols, kHtBlock, 0, s, a, a.t[0].chunks > 0 ? a.t[0].n : 0);
+  const int n0 = a.t[0].chunks > 0 ? a.t[0].n : 0;
+  if (a.t[0].chunks > 8 * kHtBlock || a.t[1].chunks > 8 * kHtBlock)
+    pdl_launch(ht_scan_kernel<kScanWide>, ncols, kScanWide, 0, s, a, n0);
+  else
+    pdl_launch(ht_scan_kernel<kHtBlock>, ncols, kHtBlock, 0, s, a, n0);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -930,7 +982,7 @@ __global__ void __launch_bounds__(kHtBlock) ht_scan_batched(BatchDev b, BatchJob
   const int j = batch_job(J, blockIdx.x);
   const Plan& P = b.plans[J.inst[j]];
   const HtTable T = ht_table(P, J.aux[j]);
-  ht_scan_body(T, &P.hdr->status, blockIdx.x - J.first[j]);
+  ht_scan_body<kHtBlock>(T, &P.hdr->status, blockIdx.x - J.first[j]);
 }
 
 // streaming pass: first[] counts CTAs; rows are copied with cp.async (no TMA)
