@@ -22,6 +22,8 @@ constexpr int kMaxPasses = 4;
 constexpr int kGramThreads = 256;
 constexpr int kGramTileRows = 64;
 
+constexpr int kMaxJacobiBlocks = 160;  // column blocks of the wide Jacobi (n <= 512 in blocks of >= 4)
+
 // Device-side header at the start of every workspace.
 struct alignas(256) DevHeader {
   int32_t status;            // figaro status bits (common.cuh)
@@ -38,6 +40,7 @@ struct alignas(256) DevHeader {
   uint32_t bar_gen;
   uint32_t sweep_any[3];     // per-sweep "a pair was rotated" flags of the wide Jacobi
   uint32_t pad2;
+  uint32_t blk_ver[kMaxJacobiBlocks];  // wide Jacobi: rounds completed on each column block
 };
 
 // Per-table buffers of the grouping and head/tail steps.

@@ -31,7 +31,9 @@
 //                              3: sigma(J) = sigma(R)) by blocks of w columns:
 //                              in each round the CTAs take disjoint pairs of
 //                              blocks and run one cyclic sweep over the 2w
-//                              columns of their pair in shared memory;
+//                              columns of their pair, on the pair's Gram in
+//                              shared memory, then apply the accumulated
+//                              rotation to U and V;
 //   * wide_sigma_kernel, wide_sort_kernel  sigma_j = ||R v_j|| / ||v_j|| in
 //                              FP64 (mixed; ||u_j|| for sigma_j below 1e-3
 //                              sigma_max) or ||u_j|| (plain), descending.
@@ -333,6 +335,30 @@ __device__ bool grid_sync(const Sync& g) {
 
 __device__ __forceinline__ bool timed_out(const int32_t* status) {
   return (*reinterpret_cast<const volatile int32_t*>(status) & kStatusTimeout) != 0;
+}
+
+// Waits (bounded) until column blocks b0 and b1 have completed k rounds:
+// the CTAs that wrote them in the previous round have published their
+// versions (release after the CTA's stores), so a block round waits for its
+// two producers only instead of for the whole grid.  Returns false on a
+// timeout (the timeout bit is then set) or when another CTA has timed out.
+__device__ bool wait_blocks(const uint32_t* ver, int b0, int b1, uint32_t k, const Sync& g) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    int64_t i = 0;
+    while (ld_acquire(ver + b0) < k || ld_acquire(ver + b1) < k) {
+      if (++i > g.limit || (ld_acquire(reinterpret_cast<const uint32_t*>(g.status)) & kStatusTimeout)) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    if (!ok) set_status(g.status, kStatusTimeout);
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 // ---------------------------------------------------- blocked Cholesky ----
@@ -641,20 +667,53 @@ __device__ __forceinline__ void rr_pair(int round, int g, int m, int& p, int& q)
   }
 }
 
-// JW: block width in columns (JW warps, one column pair each per inner round).
+// Four consecutive shared-memory entries (16-byte aligned).
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
+// JW: block width in columns; a CTA of JW warps works on a pair of blocks,
+// W2 = 2 JW columns of U (and V).  A block round (Section 3's one-sided
+// Jacobi, by blocks): the pair's columns are staged in shared memory
+// (column-major, column stride n + 1), their Gram G = S^T S is formed by
+// 4 x 4 register tiles over row splits (fixed reduction order, so G is
+// exactly symmetric), one cyclic sweep of two-sided rotations runs on G
+// (in each of the W2 - 1 inner rounds warp w rotates its pair: columns of G
+// and of the accumulated Q, a barrier, then rows of G), and U <- S Q and
+// V <- V Q are written back only when a rotation was applied.  An inner
+// round thus touches the W2 x W2 entries of G and Q instead of the 2 n W2
+// entries of the n-row columns of U and V; the rotation test is the column
+// test |g_pq| > tol sqrt(g_pp g_qq) on G.  (FP32 dot products and rotations
+// keep their accuracy relative to sqrt(g_pp g_qq) under column scaling, so
+// graded columns converge as in the column form.)
 template <typename T, bool kWithV, int JW>
 __global__ void __launch_bounds__(32 * JW) wide_jacobi_kernel(JacArgs a) {
   pdl_enter();
-  constexpr int kJacW = JW;
+  constexpr int W2 = 2 * JW;
+  constexpr int NT = 32 * JW;
+  constexpr int TD = W2 / 4;       // 4 x 4 tiles per dimension of G
+  constexpr int NTI = TD * TD;
+  constexpr int KS = NT / NTI;     // row splits of the Gram
+  constexpr int LG = W2 + 1;       // row stride of G
+  constexpr int kRowsPer = (kMaxWideWidth + NT - 1) / NT;  // rows of S staged per thread
+  static_assert(W2 % 4 == 0 && NT % NTI == 0 && W2 <= 32, "block shape");
   extern __shared__ __align__(16) unsigned char jsm[];
   const int n = a.n;
-  T* S = reinterpret_cast<T*>(jsm);                         // 2 kJacW columns of U
-  T* SV = S + static_cast<int64_t>(2 * kJacW) * n;          // and of V
+  const int ls = n + 1;                                          // column stride of S
+  T* S = reinterpret_cast<T*>(jsm);                              // W2 columns of n rows
+  T* Pg = S + static_cast<int64_t>(W2) * ls;                     // KS partial Grams
+  T* G = Pg + KS * W2 * W2;                                      // two W2 x LG buffers
+  T* Qm = G + 2 * W2 * LG;                                       // W2 x W2
   __shared__ int s_conv;
   if (timed_out(&a.h->status)) return;
   const Sync sync{&a.h->bar_count, &a.h->bar_gen, &a.h->status, a.spin_limit};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int np = a.nblk * kJacW;
+  const int np = a.nblk * JW;
   T* U = static_cast<T*>(a.U);
   T* V = static_cast<T*>(a.V);
   const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + tid, gs = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -668,19 +727,28 @@ __global__ void __launch_bounds__(32 * JW) wide_jacobi_kernel(JacArgs a) {
     a.h->sweep_any[1] = 0u;
     a.h->sweep_any[2] = 0u;
   }
+  uint32_t* ver = a.h->blk_ver;
+  if (gt < a.nblk) ver[gt] = 0u;
   // ||R||_F^2, the same sum in every CTA
-  __shared__ double s_part[32 * kJacW / 32];
+  __shared__ double s_part[JW];
   double f = 0.0;
-  for (int64_t e = tid; e < static_cast<int64_t>(n) * n; e += blockDim.x) {
-    const int r = static_cast<int>(e / n), c = static_cast<int>(e - static_cast<int64_t>(r) * n);
-    const double v = static_cast<double>(static_cast<T>(a.R[static_cast<int64_t>(r) * a.ldr + c]));
-    f += v * v;
+  for (int64_t e0 = tid; e0 < static_cast<int64_t>(n) * n; e0 += 8 * NT) {  // 8 loads in flight per thread
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t e = e0 + static_cast<int64_t>(u) * NT;
+      const int r = static_cast<int>(e / n), c = static_cast<int>(e - static_cast<int64_t>(r) * n);
+      v[u] = e < static_cast<int64_t>(n) * n ? static_cast<double>(static_cast<T>(a.R[static_cast<int64_t>(r) * a.ldr + c]))
+                                             : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) f += v[u] * v[u];
   }
   for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
   if (lane == 0) s_part[warp] = f;
   if (!grid_sync(sync)) return;
   double fro = 0.0;
-  for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) fro += s_part[w];
+  for (int w = 0; w < JW; ++w) fro += s_part[w];
   // columns below n eps64 ||R||_F are rounding noise of a rank-deficient R
   // and take no part in rotations (the FP64 unit even for FP32 sweeps: FP32
   // dot products keep their relative accuracy under column scaling, so
@@ -689,73 +757,154 @@ __global__ void __launch_bounds__(32 * JW) wide_jacobi_kernel(JacArgs a) {
   const T negligible = static_cast<T>((n * eps64) * (n * eps64) * fro);
   const T tol2 = static_cast<T>(a.tol) * static_cast<T>(a.tol);
   const int pairs = a.nblk / 2;
+  // Gram tile of this thread: rows [r0, r1) of split ks, entries (4 ti + u, 4 tj + v)
+  const int ks = tid / NTI, ti = (tid % NTI) / TD, tj = tid % TD;
+  const int rs = (n + KS - 1) / KS;
+  const int r0 = ks * rs < n ? ks * rs : n, r1 = r0 + rs < n ? r0 + rs : n;
   int sweep = 0;
   bool converged = false;
   for (; sweep < a.max_sweeps; ++sweep) {
     if (blockIdx.x == 0 && tid == 0) atomicExch(&a.h->sweep_any[(sweep + 1) % 3], 0u);
     for (int round = 0; round < a.nblk - 1; ++round) {
+      const uint32_t K = static_cast<uint32_t>(sweep * (a.nblk - 1) + round);  // rounds before this one
       for (int g = blockIdx.x; g < pairs; g += gridDim.x) {
         int bp, bq;
         rr_pair(round, g, a.nblk, bp, bq);
-        for (int e = tid; e < 2 * kJacW * n; e += blockDim.x) {
-          const int lc = e / n, r = e - lc * n;
-          const int c = lc < kJacW ? bp * kJacW + lc : bq * kJacW + lc - kJacW;
-          S[e] = U[static_cast<int64_t>(c) * n + r];
-          if (kWithV) SV[e] = V[static_cast<int64_t>(c) * n + r];
-        }
-        __syncthreads();
-        int any = 0;
-        for (int ir = 0; ir < 2 * kJacW - 1; ++ir) {
-          int p, q;
-          rr_pair(ir, warp, 2 * kJacW, p, q);
-          T* up = S + static_cast<int64_t>(p) * n;
-          T* uq = S + static_cast<int64_t>(q) * n;
-          T al = 0, be = 0, ga = 0;
-          for (int r = lane; r < n; r += 32) {
-            const T x = up[r], yv = uq[r];
-            al += x * x;
-            be += yv * yv;
-            ga += x * yv;
+        if (!wait_blocks(ver, bp, bq, K, sync)) return;
+        auto col_of = [&](int lc) { return lc < JW ? bp * JW + lc : bq * JW + lc - JW; };
+        // staging: every load of the thread is issued before its stores (one memory round trip)
+        {
+          T x[kRowsPer][W2];
+#pragma unroll
+          for (int h = 0; h < kRowsPer; ++h) {
+            const int r = tid + h * NT;
+#pragma unroll
+            for (int lc = 0; lc < W2; ++lc) x[h][lc] = r < n ? U[static_cast<int64_t>(col_of(lc)) * n + r] : T(0);
           }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            al += __shfl_xor_sync(0xffffffffu, al, o);
-            be += __shfl_xor_sync(0xffffffffu, be, o);
-            ga += __shfl_xor_sync(0xffffffffu, ga, o);
-          }
-          if (al > negligible && be > negligible && ga * ga > tol2 * al * be) {
-            T c, s;
-            jac_rotation(al, be, ga, c, s);
-            for (int r = lane; r < n; r += 32) {
-              const T x = up[r], yv = uq[r];
-              up[r] = c * x - s * yv;
-              uq[r] = s * x + c * yv;
+          for (int h = 0; h < kRowsPer; ++h) {
+            const int r = tid + h * NT;
+            if (r < n) {
+#pragma unroll
+              for (int lc = 0; lc < W2; ++lc) S[lc * ls + r] = x[h][lc];
             }
-            if (kWithV) {
-              T* vp = SV + static_cast<int64_t>(p) * n;
-              T* vq = SV + static_cast<int64_t>(q) * n;
-              for (int r = lane; r < n; r += 32) {
-                const T x = vp[r], yv = vq[r];
-                vp[r] = c * x - s * yv;
-                vq[r] = s * x + c * yv;
-              }
-            }
-            any = 1;
           }
+        }
+        for (int e = tid; e < W2 * W2; e += NT) Qm[e] = (e / W2 == e % W2) ? T(1) : T(0);
+        __syncthreads();
+        {
+          T acc[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+          const T* si = S + (4 * ti) * ls;
+          const T* sj = S + (4 * tj) * ls;
+          for (int r = r0; r < r1; ++r) {
+            T x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              x[u] = si[u * ls + r];
+              y[u] = sj[u * ls + r];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Pg[(ks * W2 + 4 * ti + u) * W2 + 4 * tj + v] = acc[u][v];
+        }
+        __syncthreads();
+        for (int e = tid; e < W2 * W2; e += NT) {
+          T s_ = T(0);
+          for (int k = 0; k < KS; ++k) s_ += Pg[k * W2 * W2 + e];
+          G[(e / W2) * LG + e % W2] = s_;
+        }
+        __syncthreads();
+        // inner sweep on G, double-buffered, one barrier per inner round: lane
+        // j forms the rotation of its own column pair (j, j') and warp w the
+        // rows p, q of its pair of G' = J^T G J (and of Q J) from the previous
+        // G.  With (c, s) the pair's rotation and sg_j = -s for the lower
+        // column, +s for the upper: (G J)[k][j] = c G[k][j] + sg_j G[k][j'].
+        int any = 0;
+        T* Gc = G;
+        T* Gn = G + W2 * LG;
+        constexpr int M1 = W2 - 1;
+        for (int ir = 0; ir < M1; ++ir) {
+          int p, q;
+          rr_pair(ir, warp, W2, p, q);
+          const int j = lane < W2 ? lane : 0;  // lanes beyond W2 mirror lane 0 and store nothing
+          int jp = (2 * ir - j) % M1;
+          jp += jp < 0 ? M1 : 0;
+          jp = j == ir ? M1 : jp;
+          jp = j == M1 ? ir : jp;
+          const int lo = j < jp ? j : jp, hi = j < jp ? jp : j;
+          const T al = Gc[lo * LG + lo], be = Gc[hi * LG + hi], ga = Gc[lo * LG + hi];
+          const T gpj = Gc[p * LG + j], gpjp = Gc[p * LG + jp], gqj = Gc[q * LG + j], gqjp = Gc[q * LG + jp];
+          const T qpj = Qm[p * W2 + j], qpjp = Qm[p * W2 + jp], qqj = Qm[q * W2 + j], qqjp = Qm[q * W2 + jp];
+          const bool rot = al > negligible && be > negligible && ga * ga > tol2 * al * be;
+          T c = T(1), s = T(0);
+          if (rot) jac_rotation(al, be, ga, c, s);
+          const T sg = j < jp ? -s : s;
+          const T cw = __shfl_sync(0xffffffffu, c, p), sw = __shfl_sync(0xffffffffu, s, p);  // the pair (p, q)
+          const T hp = c * gpj + sg * gpjp, hq = c * gqj + sg * gqjp;
+          __syncwarp();  // rows p, q of Q are read above by the lanes that own their partners
+          if (lane < W2) {
+            Gn[p * LG + j] = cw * hp - sw * hq;
+            Gn[q * LG + j] = sw * hp + cw * hq;
+            Qm[p * W2 + j] = c * qpj + sg * qpjp;
+            Qm[q * W2 + j] = c * qqj + sg * qqjp;
+          }
+          any |= rot ? 1 : 0;
           __syncthreads();
+          T* t_ = Gc;
+          Gc = Gn;
+          Gn = t_;
         }
         any = __syncthreads_or(any);
-        for (int e = tid; e < 2 * kJacW * n; e += blockDim.x) {
-          const int lc = e / n, r = e - lc * n;
-          const int c = lc < kJacW ? bp * kJacW + lc : bq * kJacW + lc - kJacW;
-          U[static_cast<int64_t>(c) * n + r] = S[e];
-          if (kWithV) V[static_cast<int64_t>(c) * n + r] = SV[e];
+        if (any) {
+          // U <- S Q and V <- V Q, one row per thread (coalesced in the column-major U and V)
+          // (Q read four entries at a time: broadcast loads shared by the warp)
+          auto times_q = [&](const T (&x)[W2], T* dst, int r) {
+#pragma unroll 2
+            for (int j4 = 0; j4 < W2; j4 += 4) {
+              T o[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+              for (int k = 0; k < W2; ++k) {
+                T qv[4];
+                ld4(Qm + k * W2 + j4, qv);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) o[v] = fma(x[k], qv[v], o[v]);
+              }
+#pragma unroll
+              for (int v = 0; v < 4; ++v) dst[static_cast<int64_t>(col_of(j4 + v)) * n + r] = o[v];
+            }
+          };
+          for (int r = tid; r < n; r += NT) {
+            T x[W2];
+#pragma unroll
+            for (int k = 0; k < W2; ++k) x[k] = S[k * ls + r];
+            times_q(x, U, r);
+            if (kWithV) {
+#pragma unroll
+              for (int k = 0; k < W2; ++k) x[k] = V[static_cast<int64_t>(col_of(k)) * n + r];
+              times_q(x, V, r);
+            }
+          }
+          if (tid == 0) atomicOr(&a.h->sweep_any[sweep % 3], 1u);
         }
-        if (any && tid == 0) atomicOr(&a.h->sweep_any[sweep % 3], 1u);
-        __syncthreads();
+        __syncthreads();  // every store of the CTA is issued
+        if (tid == 0) {
+          __threadfence();
+          st_release(ver + bp, K + 1);
+          st_release(ver + bq, K + 1);
+        }
       }
-      if (!grid_sync(sync)) return;
     }
+    if (!grid_sync(sync)) return;  // the sweep's flag is complete
     if (tid == 0) s_conv = ld_acquire(&a.h->sweep_any[sweep % 3]) == 0u;
     __syncthreads();
     if (s_conv) {
@@ -1082,7 +1231,10 @@ cudaError_t launch_jacobi_w(const Plan& p, JacArgs a, cudaStream_t s) {
   int nblk = (a.n + JW - 1) / JW;
   nblk += nblk & 1;
   a.nblk = nblk;
-  const size_t smem = sizeof(T) * (kWithV ? 2 : 1) * 2 * JW * static_cast<size_t>(a.n);
+  // S (2 JW columns, stride n + 1), the row-split partial Grams, G and Q
+  constexpr size_t W2 = 2 * JW, KS = 32 * JW / ((W2 / 4) * (W2 / 4));
+  const size_t smem = sizeof(T) * (W2 * (static_cast<size_t>(a.n) + 1) + KS * W2 * W2 + 2 * W2 * (W2 + 1) + W2 * W2);
+  if (nblk > kMaxJacobiBlocks) return cudaErrorInvalidValue;
   cudaError_t err = cudaFuncSetAttribute(wide_jacobi_kernel<T, kWithV, JW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
