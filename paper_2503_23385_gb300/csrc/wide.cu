@@ -829,11 +829,21 @@ __global__ void __launch_bounds__(32 * JW) wide_jacobi_kernel(JacArgs a) {
         // rows p, q of its pair of G' = J^T G J (and of Q J) from the previous
         // G.  With (c, s) the pair's rotation and sg_j = -s for the lower
         // column, +s for the upper: (G J)[k][j] = c G[k][j] + sg_j G[k][j'].
+        // no pair of the block passes the rotation test: the sweep would leave G unchanged
+        int need = 0;
+        for (int e = tid; e < W2 * W2; e += NT) {
+          const int i = e / W2, j = e % W2;
+          if (i < j) {
+            const T al = G[i * LG + i], be = G[j * LG + j], ga = G[i * LG + j];
+            need |= (al > negligible && be > negligible && ga * ga > tol2 * al * be) ? 1 : 0;
+          }
+        }
+        need = __syncthreads_or(need);
         int any = 0;
         T* Gc = G;
         T* Gn = G + W2 * LG;
         constexpr int M1 = W2 - 1;
-        for (int ir = 0; ir < M1; ++ir) {
+        for (int ir = 0; need && ir < M1; ++ir) {
           int p, q;
           rr_pair(ir, warp, W2, p, q);
           const int j = lane < W2 ? lane : 0;  // lanes beyond W2 mirror lane 0 and store nothing
