@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(kHtBlock, 8) ht_plan_kernel(HtArgs a, int tota
 // flag afterwards) so that a range costs a few memory round trips; the
 // ranges' aggregates are combined by a segmented Hillis-Steele scan in
 // shared memory (log2 NT steps), then each thread walks its range again
-// from its carry-in and writes the carries.
+// from its carry-in and writes the carries.  A first look at the flags alone
+// ends the kernel when no chunk begins inside a run.
 constexpr int kScanBatch = 8;
 constexpr int kScanWide = 1024;  // threads per column when a table has many chunks
 template <int NT>
@@ -221,6 +222,16 @@ __device__ __forceinline__ void ht_scan_body(const HtTable& T, const int32_t* st
   const int n = T.n;
   const int per = (K + NT - 1) / NT;
   const int q0 = t * per < K ? t * per : K, q1 = q0 + per < K ? q0 + per : K;
+  // nothing to do unless a chunk begins inside a run (uniform keys: no run is longer than L);
+  // the flags alone decide it, before any piece is read
+  {
+    uint32_t in = 0u;
+    for (int qb = q0; qb < q1; qb += kScanBatch) {
+#pragma unroll
+      for (int u = 1; u <= kScanBatch; ++u) in |= (qb + u <= q1 && qb + u < K) ? T.cflag[qb + u] : 0u;
+    }
+    if (!__syncthreads_or((in & kInside) != 0u)) return;
+  }
   // flags f[u] of chunks qb + u (u <= kScanBatch: the next chunk's kInside
   // bit decides whether piece qb + u counts) and the pieces themselves
   uint32_t f[kScanBatch + 1];
