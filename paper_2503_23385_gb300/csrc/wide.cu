@@ -17,7 +17,7 @@
 //   * wide_reduce_kernel  G = the sum of the partials in a fixed order
 //                         (bitwise reproducible).
 // Dense n x n steps, each one cooperative launch whose CTAs meet at grid
-// barriers with bounded waits:
+// barriers (the Jacobi: per-block waits between rounds) with bounded waits:
 //   * wide_chol_first_kernel   blocked right-looking semi-definite Cholesky
 //                              of G1 (32-column panels; a pivot below
 //                              rank_tol * G1_kk marks the column dependent,
@@ -683,9 +683,13 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
 // (column-major, column stride n + 1), their Gram G = S^T S is formed by
 // 4 x 4 register tiles over row splits (fixed reduction order, so G is
 // exactly symmetric), one cyclic sweep of two-sided rotations runs on G
-// (in each of the W2 - 1 inner rounds warp w rotates its pair: columns of G
-// and of the accumulated Q, a barrier, then rows of G), and U <- S Q and
-// V <- V Q are written back only when a rotation was applied.  An inner
+// (in each of the W2 - 1 inner rounds every lane forms the rotation of its
+// column pair and warp w writes rows p, q of J^T G J, from the previous
+// buffer, and of Q J: one barrier per inner round; the sweep is skipped
+// when no pair of G passes the rotation test), and U <- S Q and V <- V Q
+// are written back only when a rotation was applied.  Between rounds a CTA
+// waits for the two CTAs that wrote its blocks (per-block round counters);
+// the grid meets once per sweep to complete the convergence flag.  An inner
 // round thus touches the W2 x W2 entries of G and Q instead of the 2 n W2
 // entries of the n-row columns of U and V; the rotation test is the column
 // test |g_pq| > tol sqrt(g_pp g_qq) on G.  (FP32 dot products and rotations
