@@ -64,15 +64,33 @@ typedef enum figaro_status {
   FIGARO_ERR_NOT_SPD = 4,              /* Cholesky met a non-finite pivot (NaN/Inf in the input) */
   FIGARO_ERR_NO_CONVERGENCE = 5,       /* Jacobi reached max sweeps; sigma is still written */
   FIGARO_ERR_DEVICE_TIMEOUT = 6,       /* a bounded device-side wait gave up; results are invalid */
-  FIGARO_ERR_UNSUPPORTED = 7           /* width or size outside the limits above */
+  FIGARO_ERR_UNSUPPORTED = 7,          /* width or size outside the limits above */
+  /* A factorisation found a column with a non-zero norm numerically dependent
+   * on the columns before it (pivot below rank_tol times its diagonal): the
+   * join is rank-deficient, or too ill-conditioned for the path (on the mixed
+   * path a condition number of a few hundred along some direction suffices).
+   * R (with a zero row there) and sigma are still written, and
+   * figaro_info.dependent_columns counts the zero rows.  Rerun with
+   * FIGARO_PATH_FP64 or FIGARO_FLAG_SHIFTED_CHOLQR3 for an ill-conditioned
+   * full-rank join; set FIGARO_FLAG_ALLOW_RANK_DEFICIENT to accept the
+   * zero rows (a rank-deficient join) without this status.                */
+  FIGARO_ERR_RANK_DEFICIENT = 8
 } figaro_status;
 
 typedef enum figaro_dtype { FIGARO_F32 = 0, FIGARO_F64 = 1 } figaro_dtype;
 
 /* FIGARO_PATH_FP64: every step in FP64 (the plain reference form).
- * FIGARO_PATH_MIXED: head/tail in FP32 with compensated sums, Gram products
- * in FP32 with FP64 cross-block accumulation, CholeskyQR2 correction,
- * Cholesky and the final Jacobi values in FP64.                             */
+ * FIGARO_PATH_MIXED: head/tail in FP32 with compensated (float-float) group
+ * sums; Gram products on the tensor cores in 3xTF32 (split operands) with
+ * FP32 accumulation drained into float-float or FP64 partial sums; the two
+ * n x n Cholesky factorisations, the triangular inverse and the Jacobi
+ * sweeps in FP32; the assembly in extended precision: the inverse refined
+ * by one Newton step and R = R2 R1 formed in float-float (n <= 32) or FP64,
+ * and each singular value an extended-precision Rayleigh quotient
+ * ||R v_j|| / ||v_j|| (the FP32 column norm below 1e-3 sigma_max).  Its
+ * error against the FP64 oracle is about 2e-7 (R and sigma, relative
+ * Frobenius) on well-conditioned joins; per singular value it grows with
+ * sigma_max / sigma_j.                                                       */
 typedef enum figaro_path { FIGARO_PATH_FP64 = 0, FIGARO_PATH_MIXED = 1 } figaro_path;
 
 typedef enum figaro_memory { FIGARO_MEM_DEVICE = 0, FIGARO_MEM_HOST = 1 } figaro_memory;
@@ -95,7 +113,20 @@ enum {
    * yet, time the candidate schedules on this batch first (the call then
    * waits for the stream; it must not be made during stream capture, where
    * the flag is ignored) and keep the fastest for later calls. */
-  FIGARO_FLAG_AUTOTUNE = 1 << 2
+  FIGARO_FLAG_AUTOTUNE = 1 << 2,
+  /* Dependent columns (zero rows of R) are accepted silently: the call does
+   * not report FIGARO_ERR_RANK_DEFICIENT (figaro_info still counts them). */
+  FIGARO_FLAG_ALLOW_RANK_DEFICIENT = 1 << 3,
+  /* Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa,
+   * SIAM J. Sci. Comput. 42 (2020)) in place of CholeskyQR2: the first
+   * factorisation is of G1 + s I (s = 10 n u trace(G1), u = 2^-24 on the
+   * mixed path and 2^-53 on the FP64 path, on the non-zero diagonal), which
+   * succeeds for ill-conditioned joins, and a third Gram pass follows.  It
+   * costs one more pass over the reduced matrix; the FP64 path then handles
+   * condition numbers up to about 1e14, the mixed path up to about 1e4
+   * (beyond which its FP32 data cannot resolve the small directions).  Single
+   * calls only: figaro_batch_join runs such instances one after another.   */
+  FIGARO_FLAG_SHIFTED_CHOLQR3 = 1 << 4
 };
 
 typedef struct figaro_table {
@@ -183,8 +214,11 @@ FIGARO_API figaro_status figaro_join_head_tail(const figaro_table* A, const figa
 
 /*
  * figaro_join_qr_r -- R of QR(J) (Section 1: R with R^T R = J^T J), by a
- * CholeskyQR2 of the reduced matrix.  Dependent columns (a short or
- * rank-deficient join) get zero rows in R.
+ * CholeskyQR2 of the reduced matrix (CholeskyQR3 with
+ * FIGARO_FLAG_SHIFTED_CHOLQR3).  Dependent columns (a short or rank-deficient
+ * join) get zero rows in R, and the call's device status is then
+ * FIGARO_ERR_RANK_DEFICIENT unless FIGARO_FLAG_ALLOW_RANK_DEFICIENT is set;
+ * a column that is zero in J gets a zero row without that status.
  */
 FIGARO_API figaro_status figaro_join_qr_r(const figaro_table* A, const figaro_table* B, const figaro_options* opt, double* R,
                                int64_t ldr, void* ws, size_t ws_bytes, void* stream);
@@ -244,12 +278,17 @@ FIGARO_API figaro_status figaro_join_least_squares(const figaro_table* A, const 
  * The scratch is one fixed array of FIGARO_FIXED_SCRATCH_BYTES per device,
  * reserved when the library's device code is loaded on that device.  An
  * input pair whose figaro_workspace_size exceeds it is rejected with
- * FIGARO_ERR_WORKSPACE_TOO_SMALL before any device work is enqueued.
+ * FIGARO_ERR_WORKSPACE_TOO_SMALL before any device work is enqueued.  That
+ * size depends on the device's SM count (per-SM partial sums): on a 152-SM
+ * GB300 the limit is about 1.4e5 + 1.4e5 rows at 8 + 8 FP32 columns and
+ * 7.9e4 + 7.9e4 rows at 16 + 16.
  * Arguments, layouts and outputs are those of figaro_join_singular_values;
  * the device is the one that holds the first non-empty device-resident
- * table, else the current device.  The first call on a device looks up the
- * scratch address (a host-side query, done once per device): make that first
- * call outside any stream capture.  Nothing in the scratch needs to start at
+ * table, else the current device.  Every call looks up the scratch's address
+ * in the current context (a host-side query that allocates nothing; not
+ * cached, so a cudaDeviceReset or another context is followed correctly).
+ * The first call on a device may load the library's device code there:
+ * make it outside any stream capture.  Nothing in the scratch needs to start at
  * zero: every call clears the counters and flags it uses before using them.
  * Calls share the one array, so two calls in flight on the same device at
  * the same time race (wrong results or FIGARO_ERR_DEVICE_TIMEOUT): order
@@ -307,14 +346,16 @@ FIGARO_API figaro_status figaro_get_status(const void* ws, void* stream);
 
 /* Facts about the last call that used workspace `ws` (waits for `stream`):
  * distinct keys of A and of B, keys present in both (key groups), rows of
- * the reduced matrix (sum over groups of m1g + m2g - 1), Jacobi sweeps run. */
+ * the reduced matrix (sum over groups of m1g + m2g - 1), Jacobi sweeps run,
+ * and the columns the final factorisation marked dependent (zero rows of R,
+ * including columns that are zero in J).                                   */
 typedef struct figaro_info {
   int64_t num_runs_a;
   int64_t num_runs_b;
   int64_t num_groups;
   int64_t reduced_rows;
   int32_t jacobi_sweeps;
-  int32_t reserved;
+  int32_t dependent_columns;
 } figaro_info;
 
 FIGARO_API figaro_status figaro_get_info(const void* ws, void* stream, figaro_info* info);

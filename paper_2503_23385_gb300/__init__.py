@@ -21,7 +21,8 @@ __all__ = [
     "workspace_size", "join_group", "join_head_tail", "join_qr_r", "join_singular_values", "join_qr_svd",
     "join_qr_svd_host", "batch_join", "get_status", "Solver", "STATUS_NAMES", "event_array", "kernel_launches",
     "host_workspace_size", "PHASES", "NUM_PHASE_EVENTS", "join_singular_values_fixed", "FIXED_SCRATCH_BYTES",
-    "BatchSolver", "FLAG_AUTOTUNE", "join_least_squares", "LsqSolver", "join_svd",
+    "BatchSolver", "FLAG_AUTOTUNE", "join_least_squares", "LsqSolver", "join_svd", "get_info",
+    "FLAG_ALLOW_RANK_DEFICIENT", "FLAG_SHIFTED_CHOLQR3",
 ]
 
 PATH_FP64, PATH_MIXED = 0, 1
@@ -30,8 +31,10 @@ F32, F64 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 FLAG_HOST_OUTPUT = 1
 FLAG_AUTOTUNE = 1 << 2
+FLAG_ALLOW_RANK_DEFICIENT = 1 << 3
+FLAG_SHIFTED_CHOLQR3 = 1 << 4
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "WORKSPACE_TOO_SMALL", 3: "CUDA", 4: "NOT_SPD",
-                5: "NO_CONVERGENCE", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED"}
+                5: "NO_CONVERGENCE", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED", 8: "RANK_DEFICIENT"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libfigaro.so")
@@ -61,7 +64,8 @@ class Options(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("num_runs_a", ctypes.c_int64), ("num_runs_b", ctypes.c_int64), ("num_groups", ctypes.c_int64),
-                ("reduced_rows", ctypes.c_int64), ("jacobi_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("reduced_rows", ctypes.c_int64), ("jacobi_sweeps", ctypes.c_int32),
+                ("dependent_columns", ctypes.c_int32)]
 
 
 class Grouping(ctypes.Structure):
@@ -418,9 +422,10 @@ def join_least_squares(A, B, stream=None, workspace=None, **opts):
 def join_singular_values_fixed(A, B, sigma, R=None, stream=None, **opts) -> int:
     """figaro_join_singular_values_fixed: sigma (and R when given) of the
     join into caller-owned float64 device tensors, with the library's own
-    fixed scratch (FIXED_SCRATCH_BYTES per device).  Returns the scratch's
-    device address, which the C calls figaro_get_status / figaro_get_info
-    accept as their workspace argument."""
+    fixed scratch (FIXED_SCRATCH_BYTES per device).  Waits for the stream and
+    raises FigaroError on a non-OK device status, like the other wrappers.
+    Returns the scratch's device address, which the C calls
+    figaro_get_status / figaro_get_info accept as their workspace argument."""
     lib = library()
     ta, tb = _device_table(*A), _device_table(*B)
     o = _options(**opts)
@@ -431,6 +436,7 @@ def join_singular_values_fixed(A, B, sigma, R=None, stream=None, **opts) -> int:
     _check(lib.figaro_join_singular_values_fixed(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(o),
                                                  ctypes.c_void_p(sigma.data_ptr()), rp, ldr, ctypes.byref(scratch),
                                                  _stream_handle(stream)), "figaro_join_singular_values_fixed")
+    _check(lib.figaro_get_status(scratch, _stream_handle(stream)), "figaro_join_singular_values_fixed (device status)")
     return int(scratch.value or 0)
 
 
@@ -522,12 +528,13 @@ class BatchSolver:
 
 
 def get_info(workspace, stream=None) -> dict:
-    """Key runs, key groups, reduced rows and Jacobi sweeps of the last call."""
+    """Key runs, key groups, reduced rows, Jacobi sweeps and dependent columns
+    (zero rows of R) of the last call."""
     lib = library()
     out = Info()
     _check(lib.figaro_get_info(ctypes.c_void_p(workspace.data_ptr()), _stream_handle(stream), ctypes.byref(out)),
            "figaro_get_info")
-    return {f: int(getattr(out, f)) for f, _ in Info._fields_ if f != "reserved"}
+    return {f: int(getattr(out, f)) for f, _ in Info._fields_}
 
 
 def get_status(workspace, stream=None) -> int:

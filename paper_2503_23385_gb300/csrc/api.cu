@@ -244,6 +244,8 @@ figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, con
   c.p.spin_limit = o.spin_limit;
   c.p.rank_tol = o.rank_tol;
   c.p.withhold = (o.flags & FIGARO_FLAG_TEST_WITHHOLD) ? 1 : 0;
+  c.p.report_rank = (o.flags & FIGARO_FLAG_ALLOW_RANK_DEFICIENT) ? 0 : c.p.n;
+  c.p.shifted = (o.flags & FIGARO_FLAG_SHIFTED_CHOLQR3) ? 1 : 0;
   c.s = static_cast<cudaStream_t>(stream);
   if (o.phase_events) {
     c.events = true;
@@ -300,6 +302,14 @@ figaro_status run_factor(Call& c, double* R_dev, int64_t ldr) {
   FIGARO_TRY(c.mark(5));
   FIGARO_TRY(launch_gram_pass(c.p, 2, c.s));
   FIGARO_TRY(c.mark(6));
+  if (c.p.shifted) {
+    // shifted CholeskyQR3: the shifted first pass leaves Q = M R1^{-1} with a
+    // moderate condition number; the factor R' = R2 R1 of the second pass
+    // preconditions a third pass (W = R'^{-1}, Gram of M W, R = R3 R')
+    FIGARO_TRY(launch_chol_second(c.p, nullptr, ldr, c.s));
+    FIGARO_TRY(launch_refactor(c.p, c.s));
+    FIGARO_TRY(launch_gram_pass(c.p, 2, c.s));
+  }
   FIGARO_TRY(launch_chol_second(c.p, R_dev, ldr, c.s));
   FIGARO_TRY(c.mark(7));
   return FIGARO_OK;
@@ -323,28 +333,21 @@ figaro_status run_qr_svd(Call& c, double* R_out, int64_t ldr, double* sigma, int
 }
 
 // Library-owned scratch of figaro_join_singular_values_fixed (a fixed-size
-// device array, so the call needs no allocation).  Its address is looked up
-// once per device, with that device current.
+// device array, so the call needs no allocation).  In host code the array's
+// name is not a device address: every call asks the runtime for the address
+// of the current device's copy (a host-side query that allocates nothing).
+// The address is not cached, because it belongs to the context the
+// library's device code was loaded into: after a cudaDeviceReset, or in
+// another context, the module is loaded again and the array can move.
 __device__ __align__(256) unsigned char g_fixed_scratch[FIGARO_FIXED_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_fixed_mu;
-void* g_fixed_ptr[kMaxDevices] = {};
-
 figaro_status fixed_scratch(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return FIGARO_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return FIGARO_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_fixed_mu);
-  if (!g_fixed_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_fixed_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return FIGARO_ERR_CUDA;
-    }
-    g_fixed_ptr[dev] = p;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_fixed_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return FIGARO_ERR_CUDA;
   }
-  *out = g_fixed_ptr[dev];
+  *out = p;
   return FIGARO_OK;
 }
 
@@ -827,6 +830,8 @@ figaro_status figaro_join_least_squares(const figaro_table* A, const figaro_tabl
   figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
   if (st != FIGARO_OK) return st;
   if (c.p.n < 2) return FIGARO_ERR_INVALID_ARG;  // at least one feature besides the label
+  // a label that depends on the features is an exact fit, not a rank defect
+  if (c.p.report_rank > c.p.n - 1) c.p.report_rank = c.p.n - 1;
   const int host_out = opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT);
   st = run_grouping(c);
   if (st != FIGARO_OK) return st;
@@ -906,7 +911,8 @@ figaro_status figaro_batch_join(int32_t count, const figaro_table* A, const figa
     if (st != FIGARO_OK) return st;
     base += one;
     if (!R[i] && !sigma[i]) continue;
-    const bool narrow = c.p.n <= kMaxWidth;
+    // (the shifted CholeskyQR3's third pass runs in single calls only)
+    const bool narrow = c.p.n <= kMaxWidth && !c.p.shifted;
     const bool device_io = A[i].memory == FIGARO_MEM_DEVICE && B[i].memory == FIGARO_MEM_DEVICE && !host_out;
     if (narrow && device_io) {
       batched.push_back(c);
@@ -957,7 +963,7 @@ figaro_status figaro_batch_schedule(int32_t count, const figaro_table* A, const 
     Call c;
     plan_layout(c.p, nullptr, A[i].m, A[i].n, B[i].m, B[i].n, A[i].dtype == FIGARO_F64, o.path == FIGARO_PATH_MIXED,
                 0, 0, sm_count());
-    if (c.p.n <= kMaxWidth) calls.push_back(c);
+    if (c.p.n <= kMaxWidth && !(o.flags & FIGARO_FLAG_SHIFTED_CHOLQR3)) calls.push_back(c);
   }
   const BatchSchedule sc = schedule_for(calls);
   *gram_rows_per_cta = sc.gram_rows_per_cta;
@@ -993,6 +999,7 @@ figaro_status figaro_get_status(const void* ws, void* stream) {
   if (bits & kStatusTimeout) return FIGARO_ERR_DEVICE_TIMEOUT;
   if (bits & kStatusNotSpd) return FIGARO_ERR_NOT_SPD;
   if (bits & kStatusNoConvergence) return FIGARO_ERR_NO_CONVERGENCE;
+  if (bits & kStatusRankDrop) return FIGARO_ERR_RANK_DEFICIENT;
   return FIGARO_OK;
 }
 
@@ -1008,7 +1015,7 @@ figaro_status figaro_get_info(const void* ws, void* stream, figaro_info* info) {
   info->num_groups = h.num_groups;
   info->reduced_rows = h.reduced_rows;
   info->jacobi_sweeps = h.jacobi_sweeps;
-  info->reserved = 0;
+  info->dependent_columns = h.dep_cols;
   return FIGARO_OK;
 }
 
@@ -1022,6 +1029,9 @@ const char* figaro_status_string(figaro_status s) {
     case FIGARO_ERR_NO_CONVERGENCE: return "Jacobi SVD did not converge within the sweep limit";
     case FIGARO_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait gave up";
     case FIGARO_ERR_UNSUPPORTED: return "unsupported size or width";
+    case FIGARO_ERR_RANK_DEFICIENT:
+      return "a column was found numerically dependent (R has a zero row there): the join is rank-deficient "
+             "or too ill-conditioned for this path";
   }
   return "unknown status";
 }

@@ -12,6 +12,9 @@ enum : int32_t {
   kStatusNotSpd = 1 << 4,
   kStatusNoConvergence = 1 << 5,
   kStatusTimeout = 1 << 6,
+  // a factorisation marked a column with a non-zero norm dependent (its pivot
+  // fell below rank_tol times its diagonal) and the call reports that column
+  kStatusRankDrop = 1 << 7,
 };
 
 __device__ __forceinline__ void set_status(int32_t* word, int32_t bit) { atomicOr(word, bit); }

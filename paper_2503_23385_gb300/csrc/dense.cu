@@ -45,9 +45,11 @@ __device__ void chol_inplace(T* A, int n, const T* diag0, int32_t* act, T tol, T
   const int c0 = threadIdx.x & 31, r0 = threadIdx.x >> 5, rstep = blockDim.x >> 5;
   for (int k = 0; k < n; ++k) {
     const T d = A[k * n + k];
-    int ok = act[k];
+    const int was = act[k];
+    int ok = was;
     if (!isfinite(d)) ok = 0;
     if (!(d > tol * diag0[k]) || !(diag0[k] > T(0))) ok = 0;
+    const bool dropped = was && !ok && isfinite(d) && diag0[k] > T(0);
     const T yk = ok ? rsqrt_pivot(d) : T(0);
     if (yk != T(0)) {
       const T y2 = yk * yk;
@@ -58,6 +60,7 @@ __device__ void chol_inplace(T* A, int n, const T* diag0, int32_t* act, T tol, T
     }
     if (threadIdx.x == 0) {
       if (!isfinite(d)) set_status(status, kStatusNotSpd);
+      if (dropped) note_dropped(status, k);
       act[k] = ok;
       y[k] = yk;
     }
@@ -121,25 +124,44 @@ __device__ void tri_inverse_inplace(T* A, int n, const int32_t* act, T* x) {
   }
 }
 
+// Shift of the shifted CholeskyQR3 (Fukaya et al., SIAM J. Sci. Comput. 42
+// (2020)): shift_rel times the trace of G, added to the non-zero diagonal
+// entries, so that the factorisation of an ill-conditioned G succeeds.
+__device__ __forceinline__ double gram_shift(const double* G, int n, double shift_rel) {
+  if (!(shift_rel > 0.0)) return 0.0;
+  double tr = 0.0;
+  for (int k = 0; k < n; ++k) tr += G[k * n + k];
+  return shift_rel * tr;
+}
+
+// First factorisation (n <= 128): R1 = chol(G1 + shift) and W = R1^{-1}.
+// from_r: G holds an upper-triangular R instead (the shifted CholeskyQR3's
+// second factor); R1 = R and W = R^{-1} on the columns with R_kk != 0.
 template <typename T, bool kSmall>
 __device__ __forceinline__ void chol_first_body(const double* G, int n, double tol, double* R1, double* W, float* Wf,
-                                                int32_t* active, int32_t* status) {
+                                                int32_t* active, int32_t* status, double shift_rel, int from_r) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* A = reinterpret_cast<T*>(smraw);  // n x n
   T* diag0 = A + n * n;
   T* y = diag0 + n;
   T* x = y + n;
   int32_t* act = reinterpret_cast<int32_t*>(x + n);
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = static_cast<T>(G[e]);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    diag0[k] = static_cast<T>(G[k * n + k]);
-    act[k] = 1;
-  }
-  __syncthreads();
-  chol_inplace<T>(A, n, diag0, act, static_cast<T>(tol), y, status);
+  const double shift = from_r ? 0.0 : gram_shift(G, n, shift_rel);
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    R1[e] = (j >= i && act[i]) ? static_cast<double>(A[e]) : 0.0;
+    const double g = G[e];
+    A[e] = static_cast<T>(i == j && g > 0.0 ? g + shift : g);
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double g = G[k * n + k];
+    diag0[k] = static_cast<T>(g > 0.0 ? g + shift : g);
+    act[k] = from_r ? (g != 0.0) : 1;
+  }
+  __syncthreads();
+  if (!from_r) chol_inplace<T>(A, n, diag0, act, static_cast<T>(tol), y, status);
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    R1[e] = (j >= i && act[i]) ? (from_r ? G[e] : static_cast<double>(A[e])) : 0.0;
   }
   for (int k = threadIdx.x; k < n; k += blockDim.x) active[k] = act[k];
   __syncthreads();
@@ -171,9 +193,9 @@ __device__ __forceinline__ void chol_first_body(const double* G, int n, double t
 
 template <typename T, bool kSmall>
 __global__ void __launch_bounds__(1024) chol_first_kernel(const double* G, int n, double tol, double* R1, double* W, float* Wf,
-                                  int32_t* active, int32_t* status) {
+                                  int32_t* active, int32_t* status, double shift_rel, int from_r) {
   pdl_enter();
-  chol_first_body<T, kSmall>(G, n, tol, R1, W, Wf, active, status);
+  chol_first_body<T, kSmall>(G, n, tol, R1, W, Wf, active, status, shift_rel, from_r);
 }
 
 // Upper-triangular product C = A B on n x n row-major matrices, one thread
@@ -229,6 +251,11 @@ __device__ __forceinline__ void chol_second_body(const double* G2, int n, double
   __syncthreads();
   const double* X = Xg;
   chol_inplace<T>(A, n, diag0, act, static_cast<T>(tol), y, status);
+  if (threadIdx.x == 0) {
+    int dep = 0;
+    for (int k = 0; k < n; ++k) dep += act[k] ? 0 : 1;
+    header_of(status)->dep_cols = dep;
+  }
   // R = R2 X (both upper triangular) in FP64; rows of dependent columns are zero
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
@@ -543,6 +570,7 @@ __device__ __forceinline__ uint32_t chol8w(T (&a)[4], int n, T tol, uint32_t mas
         if (lane == 0) set_status(status, kStatusNotSpd);
       }
       if (!(d > tol * d0) || !(d0 > T(0))) ok = false;
+      if (!ok && ((mask >> k) & 1u) && isfinite(d) && d0 > T(0) && lane == 0) note_dropped(status, k);
       const T yk = ok ? rsqrt_pivot(d) : T(0);
       const T rk = lane >= k ? ak * yk : T(0);
       set_row_reg(a, k >> 3, rk);
@@ -598,26 +626,32 @@ __device__ __forceinline__ void inv8w(const T (&a)[4], T (&w)[4], int n, uint32_
     for (int s = 0; s < 4; ++s) w[s] = T(0);
 }
 
-// First factorisation for n <= 32: R1 = chol(G1), W = R1^{-1} (8 warps).
+// First factorisation for n <= 32: R1 = chol(G1 + shift), W = R1^{-1} (8
+// warps; the shift and from_r as in chol_first_body).
 template <typename T>
 __device__ __forceinline__ void chol_first32_body(const double* G, int n, double tol, double* R1, double* W, float* Wf,
-                                                  int32_t* active, int32_t* status) {
+                                                  int32_t* active, int32_t* status, double shift_rel, int from_r) {
   __shared__ T buf[2 * kSmallN], diag0[kSmallN], dinv[kSmallN];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool col = lane < n;
+  const double shift = from_r ? 0.0 : gram_shift(G, n, shift_rel);
   T a[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int i = warp + 8 * s;
-    a[s] = (i < n && col) ? static_cast<T>(G[i * n + lane]) : T(0);
+    const double g = (i < n && col) ? G[i * n + lane] : 0.0;
+    a[s] = static_cast<T>(i == lane && g > 0.0 ? g + shift : g);
   }
   const uint32_t all = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
-  const uint32_t mask = chol8w<T>(a, n, static_cast<T>(tol), all, buf, diag0, status);
+  const uint32_t mask =
+      from_r ? __ballot_sync(0xffffffffu, col && G[lane * n + lane] != 0.0) & all
+             : chol8w<T>(a, n, static_cast<T>(tol), all, buf, diag0, status);
   if (warp == 0 && col) active[lane] = (mask >> lane) & 1u;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int i = warp + 8 * s;
-    if (i < n && col) R1[i * n + lane] = static_cast<double>(a[s]);
+    if (i < n && col) R1[i * n + lane] = from_r ? (i <= lane && ((mask >> i) & 1u) ? G[i * n + lane] : 0.0)
+                                                : static_cast<double>(a[s]);
   }
   __syncthreads();  // buf is reused by the inverse
   T w[4];
@@ -643,9 +677,9 @@ __device__ __forceinline__ void chol_first32_body(const double* G, int n, double
 template <typename T>
 __global__ void __launch_bounds__(kC8Threads) chol_first32_kernel(const double* G, int n, double tol, double* R1,
                                                                   double* W, float* Wf, int32_t* active,
-                                                                  int32_t* status) {
+                                                                  int32_t* status, double shift_rel, int from_r) {
   pdl_enter();
-  chol_first32_body<T>(G, n, tol, R1, W, Wf, active, status);
+  chol_first32_body<T>(G, n, tol, R1, W, Wf, active, status, shift_rel, from_r);
 }
 
 // Float-float helpers for the mixed path's second factorisation (FP64
@@ -687,7 +721,8 @@ __device__ __forceinline__ void chol_second32_body(const double* G2, int n, doub
     sX[i * LD + lane] = x;
     if (refine) sW[i * LD + lane] = (i < n && col) ? Wf[i * n + lane] : 0.f;
   }
-  chol8w<T>(a, n, static_cast<T>(tol), mask1, buf, diag0, status);
+  const uint32_t mask2 = chol8w<T>(a, n, static_cast<T>(tol), mask1, buf, diag0, status);
+  if (threadIdx.x == 0) header_of(status)->dep_cols = n - __popc(mask2 & (n >= 32 ? 0xffffffffu : ((1u << n) - 1u)));
 #pragma unroll
   for (int s = 0; s < 4; ++s) sR2[(warp + 8 * s) * LD + lane] = a[s];
   if constexpr (sizeof(T) == 4) {
@@ -987,7 +1022,7 @@ template <typename T, bool kSmall>
 __global__ void __launch_bounds__(1024) chol_first_batched(BatchDev b, BatchJobs J) {
   pdl_enter();
   const Plan& P = b.plans[J.inst[blockIdx.x]];
-  chol_first_body<T, kSmall>(P.G1, P.n, dense_tol(P), P.R1, P.W, P.Wf, P.active, &P.hdr->status);
+  chol_first_body<T, kSmall>(P.G1, P.n, dense_tol(P), P.R1, P.W, P.Wf, P.active, &P.hdr->status, 0.0, 0);
 }
 
 template <typename T>
@@ -1013,7 +1048,7 @@ template <typename T>
 __global__ void __launch_bounds__(kC8Threads) chol_first32_batched(BatchDev b, BatchJobs J) {
   pdl_enter();
   const Plan& P = b.plans[J.inst[blockIdx.x]];
-  chol_first32_body<T>(P.G1, P.n, dense_tol(P), P.R1, P.W, P.Wf, P.active, &P.hdr->status);
+  chol_first32_body<T>(P.G1, P.n, dense_tol(P), P.R1, P.W, P.Wf, P.active, &P.hdr->status, 0.0, 0);
 }
 
 template <typename T>
@@ -1043,30 +1078,46 @@ static int dense_threads(int n) {
   return t;
 }
 
+// Relative shift of the shifted CholeskyQR3's first factorisation: 10 n u
+// times trace(G1), u the unit roundoff of the Gram products (2^-24 on the
+// mixed path, 2^-53 on the FP64 path).
+static double shift_rel(const Plan& p) {
+  if (!p.shifted) return 0.0;
+  return 10.0 * p.n * (p.mixed ? 5.9604644775390625e-8 : 1.1102230246251565e-16);
+}
+
 template <typename T>
-static cudaError_t chol_first_t(const Plan& p, cudaStream_t s) {
+static cudaError_t chol_first_t(const Plan& p, cudaStream_t s, int from_r) {
   const int n = p.n;
+  const double* G = from_r ? p.R : p.G1;
+  const double sr = from_r ? 0.0 : shift_rel(p);
   // the column-per-thread inverse needs a second n x n buffer (when it fits)
   const bool small = sizeof(T) * 2 * static_cast<size_t>(n) * n <= 96 * 1024;
   size_t smem = sizeof(T) * (static_cast<size_t>(n) * n + 3 * n) + sizeof(int32_t) * (n + 4) + 16;
   if (small) smem += sizeof(T) * static_cast<size_t>(n) * n;
   if (n <= kSmallN) {
-    pdl_launch(chol_first32_kernel<T>, 1, kC8Threads, 0, s, p.G1, n, default_tol(p), p.R1, p.W, p.Wf, p.active,
-               &p.hdr->status);
+    pdl_launch(chol_first32_kernel<T>, 1, kC8Threads, 0, s, G, n, default_tol(p), p.R1, p.W, p.Wf, p.active,
+               &p.hdr->status, sr, from_r);
     count_launches(1);
     return cudaGetLastError();
   }
   auto kern = small ? chol_first_kernel<T, true> : chol_first_kernel<T, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  pdl_launch(kern, 1, dense_threads(n), smem, s, p.G1, n, default_tol(p), p.R1, p.W, p.Wf, p.active, &p.hdr->status);
+  pdl_launch(kern, 1, dense_threads(n), smem, s, G, n, default_tol(p), p.R1, p.W, p.Wf, p.active, &p.hdr->status,
+             sr, from_r);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chol_first(const Plan& p, cudaStream_t s) {
   if (p.wide) return launch_wide_chol_first(p, s);
-  return p.mixed ? chol_first_t<float>(p, s) : chol_first_t<double>(p, s);
+  return p.mixed ? chol_first_t<float>(p, s, 0) : chol_first_t<double>(p, s, 0);
+}
+
+cudaError_t launch_refactor(const Plan& p, cudaStream_t s) {
+  if (p.wide) return launch_wide_refactor(p, s);
+  return p.mixed ? chol_first_t<float>(p, s, 1) : chol_first_t<double>(p, s, 1);
 }
 
 template <typename T>

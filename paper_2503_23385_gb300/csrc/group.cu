@@ -67,9 +67,11 @@ __device__ __forceinline__ uint32_t* tile_offsets(const TableWork& T, int pass) 
   return tile_counts(T, pass) + static_cast<int64_t>(T.tiles) * kRadixBins;
 }
 
-__global__ void reset_kernel(DevHeader* h) {
+__global__ void reset_kernel(DevHeader* h, int report_rank) {
   pdl_enter();
   h->status = 0;
+  h->report_rank = report_rank;
+  h->dep_cols = 0;
   for (int i = 0; i < 8; ++i) h->ticket[i] = 0;
   h->kmin[0] = h->kmin[1] = 0xffffffffu;
   h->kmax[0] = h->kmax[1] = 0u;
@@ -585,6 +587,8 @@ __global__ void batch_reset_kernel(BatchDev b) {
   if (threadIdx.x == 0) {
     DevHeader* h = P.hdr;
     h->status = 0;
+    h->report_rank = P.report_rank;
+    h->dep_cols = 0;
     for (int i = 0; i < 8; ++i) h->ticket[i] = 0;
     h->kmin[0] = h->kmin[1] = 0xffffffffu;
     h->kmax[0] = h->kmax[1] = 0u;
@@ -642,7 +646,7 @@ int64_t group_status_words(int tiles) {
 cudaError_t launch_reset(const Plan& p, cudaStream_t s) {
   // the header; the sort's per-tile counts and offsets and the run counts are
   // rewritten by every call
-  pdl_launch(reset_kernel, 1, 1, 0, s, p.hdr);
+  pdl_launch(reset_kernel, 1, 1, 0, s, p.hdr, p.report_rank);
   count_launches(1);
   // the histograms are accumulated with atomics: clear them too
   for (int t = 0; t < 2; ++t)

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include "common.cuh"
+
 namespace figaro {
 
 constexpr int kMaxWidth = 128;          // n1 + n2 limit of the one-CTA dense n x n kernels
@@ -27,7 +29,7 @@ constexpr int kMaxJacobiBlocks = 160;  // column blocks of the wide Jacobi (n <=
 // Device-side header at the start of every workspace.
 struct alignas(256) DevHeader {
   int32_t status;            // figaro status bits (common.cuh)
-  int32_t pad0;
+  int32_t report_rank;       // a dropped column k < report_rank makes the status FIGARO_ERR_RANK_DEFICIENT
   uint32_t ticket[8];        // persistent-grid work tickets
   uint32_t kmin[2];          // ordered-key range per table (A = 0, B = 1)
   uint32_t kmax[2];
@@ -35,7 +37,7 @@ struct alignas(256) DevHeader {
   int64_t num_groups;
   int64_t reduced_rows;      // sum over matched keys of (m1g + m2g - 1)
   int32_t jacobi_sweeps;
-  int32_t pad1;
+  int32_t dep_cols;          // columns the last factorisation marked dependent (zero rows of R)
   uint32_t bar_count;        // grid barrier of the cooperative dense kernels (wide path)
   uint32_t bar_gen;
   uint32_t sweep_any[3];     // per-sweep "a pair was rotated" flags of the wide Jacobi
@@ -88,6 +90,8 @@ struct Plan {
   int64_t spin_limit = 0;
   double rank_tol = 0.0;
   int withhold = 0;             // test-only fault injection (see FIGARO_FLAG_TEST_WITHHOLD)
+  int report_rank = 0;          // leading columns whose drop raises FIGARO_ERR_RANK_DEFICIENT (0: none)
+  int shifted = 0;              // shifted CholeskyQR3: shift G1, then a third Gram pass
   int64_t lut_size = 0;         // entries of each table's key lookup table
   DevHeader* hdr = nullptr;
   void* head = nullptr;         // m1 x n slots, compute type
@@ -148,6 +152,15 @@ struct BatchDev {
   int count;
 };
 
+// The workspace header that holds a status word (the header's first member).
+__device__ __forceinline__ DevHeader* header_of(int32_t* status) { return reinterpret_cast<DevHeader*>(status); }
+
+// A factorisation marked column k dependent although its norm is not zero:
+// recorded as FIGARO_ERR_RANK_DEFICIENT when the call reports column k.
+__device__ __forceinline__ void note_dropped(int32_t* status, int k) {
+  if (k < header_of(status)->report_rank) set_status(status, kStatusRankDrop);
+}
+
 // Job j of a launch for CTA b (binary search over first[]).
 __device__ __forceinline__ int batch_job(const BatchJobs& J, int b) {
   int lo = 0, hi = J.njobs - 1;
@@ -200,6 +213,9 @@ cudaError_t launch_ht_carry(const Plan& p, cudaStream_t s);
 cudaError_t launch_ht_main(const Plan& p, cudaStream_t s);
 cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s);
 cudaError_t launch_chol_first(const Plan& p, cudaStream_t s);
+// Shifted CholeskyQR3 between its second and third passes: R1 = R (the
+// second pass's factor), W = R^{-1} on the columns with a non-zero diagonal.
+cudaError_t launch_refactor(const Plan& p, cudaStream_t s);
 cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);
 cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
 cudaError_t launch_lsq(const Plan& p, double* beta, double* residual, cudaStream_t s);
@@ -240,6 +256,7 @@ cudaError_t launch_gram_tc_batch(const Plan* dev_plans, const Plan* host_plans, 
 int64_t wide_gram_jobs(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms);
 cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s);
 cudaError_t launch_wide_chol_first(const Plan& p, cudaStream_t s);
+cudaError_t launch_wide_refactor(const Plan& p, cudaStream_t s);
 cudaError_t launch_wide_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);
 cudaError_t launch_wide_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
 cudaError_t launch_svd_v(const Plan& p, const double* R, int64_t ldr, double* sigma, double* V, int64_t ldv,

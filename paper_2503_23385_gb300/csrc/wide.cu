@@ -392,14 +392,17 @@ __device__ bool chol_blocked(T* A, int n, const T* diag0, int32_t* act, T* y, T 
       for (int j = 0; j < kb; ++j) {
         const int col = k0 + j;
         const T d = sm.d[j][j];
-        int ok = act[col];
+        const int was = act[col];
+        int ok = was;
         if (!isfinite(d)) ok = 0;
         if (!(d > tol * diag0[col]) || !(diag0[col] > T(0))) ok = 0;
+        const bool dropped = was && !ok && isfinite(d) && diag0[col] > T(0);
         const T yj = ok ? rsqrt_pivot(d) : T(0);
         __syncthreads();  // every thread has read the pivot
         if (tid >= j && tid < kb) sm.d[j][tid] *= yj;
         if (tid == 0) {
           if (!isfinite(d)) set_status(sync.status, kStatusNotSpd);
+          if (dropped) note_dropped(sync.status, col);
           act[col] = ok;
           y[col] = yj;
           sm.y[j] = yj;
@@ -522,6 +525,8 @@ struct DenseArgs {
   double* R_out;
   int64_t ldr;
   int refine;
+  double shift_rel;    // shifted CholeskyQR3: relative shift of the first factorisation
+  int from_r;          // first factorisation: G holds the upper-triangular R to invert
   DevHeader* h;
   int64_t spin_limit;
 };
@@ -544,18 +549,30 @@ __global__ void __launch_bounds__(kWThreads) wide_chol_first_kernel(DenseArgs a)
   T* d0 = static_cast<T*>(a.d0);
   const int64_t nn = static_cast<int64_t>(n) * n;
   const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, gs = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t e = gt; e < nn; e += gs) A[e] = static_cast<T>(a.G[e]);
+  // shifted CholeskyQR3: shift_rel trace(G) on the non-zero diagonal entries
+  double shift = 0.0;
+  if (a.shift_rel > 0.0 && !a.from_r) {
+    for (int k = 0; k < n; ++k) shift += a.G[static_cast<int64_t>(k) * n + k];
+    shift *= a.shift_rel;
+  }
+  for (int64_t e = gt; e < nn; e += gs) {
+    const int64_t i = e / n, j = e - i * n;
+    const double g = a.G[e];
+    A[e] = static_cast<T>(i == j && g > 0.0 ? g + shift : g);
+  }
   for (int64_t k = gt; k < n; k += gs) {
-    d0[k] = static_cast<T>(a.G[k * n + k]);
-    a.active[k] = 1;
+    const double g = a.G[k * n + k];
+    d0[k] = static_cast<T>(g > 0.0 ? g + shift : g);
+    a.active[k] = a.from_r ? (g != 0.0) : 1;
   }
   if (!grid_sync(sync)) return;
-  if (!chol_blocked<T>(A, n, d0, a.active, y, static_cast<T>(a.tol), sync, sm)) return;
+  // from_r: G is the upper-triangular R of the previous pass, inverted as is
+  if (!a.from_r && !chol_blocked<T>(A, n, d0, a.active, y, static_cast<T>(a.tol), sync, sm)) return;
   inverse_columns<T>(A, Wt, n, a.active, reinterpret_cast<T*>(wcol_raw));
   if (!grid_sync(sync)) return;
   for (int64_t e = gt; e < nn; e += gs) {
     const int i = static_cast<int>(e / n), j = static_cast<int>(e - static_cast<int64_t>(i) * n);
-    a.R1[e] = (j >= i && a.active[i]) ? static_cast<double>(A[e]) : 0.0;
+    a.R1[e] = (j >= i && a.active[i]) ? (a.from_r ? a.G[e] : static_cast<double>(A[e])) : 0.0;
     // dependent columns pass through the second pass unchanged (identity)
     double w = (j >= i) ? static_cast<double>(Wt[e]) : 0.0;
     if (i == j && !a.active[i]) w = 1.0;
@@ -617,6 +634,11 @@ __global__ void __launch_bounds__(kWThreads) wide_chol_second_kernel(DenseArgs a
   }
   if (!grid_sync(sync)) return;
   if (!chol_blocked<T>(A, n, d0, act, y, static_cast<T>(a.tol), sync, sm)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int dep = 0;
+    for (int k = 0; k < n; ++k) dep += act[k] ? 0 : 1;
+    a.h->dep_cols = dep;
+  }
   // R = R2 X in FP64; rows of dependent columns are zero
   for (int64_t e = gt; e < nn; e += gs) {
     const int i = static_cast<int>(e / n), j = static_cast<int>(e - static_cast<int64_t>(i) * n);
@@ -1213,8 +1235,15 @@ cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_wide_chol_first(const Plan& p, cudaStream_t s) {
+static cudaError_t wide_first(const Plan& p, int from_r, cudaStream_t s) {
   DenseArgs a = dense_args(p, 0, nullptr, 0);
+  if (from_r) {
+    a.G = p.R;
+    a.from_r = 1;
+  } else if (p.shifted) {
+    // 10 n u trace(G1), u the unit roundoff of the Gram products
+    a.shift_rel = 10.0 * p.n * (p.mixed ? 5.9604644775390625e-8 : 1.1102230246251565e-16);
+  }
   const size_t wsm = static_cast<size_t>(kWThreads / 32) * p.n * (p.mixed ? 4 : 8);
   cudaError_t err;
   if (p.mixed) {
@@ -1231,6 +1260,10 @@ cudaError_t launch_wide_chol_first(const Plan& p, cudaStream_t s) {
   count_launches(1);
   return err;
 }
+
+cudaError_t launch_wide_chol_first(const Plan& p, cudaStream_t s) { return wide_first(p, 0, s); }
+
+cudaError_t launch_wide_refactor(const Plan& p, cudaStream_t s) { return wide_first(p, 1, s); }
 
 cudaError_t launch_wide_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s) {
   DenseArgs a = dense_args(p, 1, R_out, ldr);

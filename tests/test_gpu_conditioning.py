@@ -1,0 +1,188 @@
+"""Rank deficiency and ill-conditioning through the C ABI.
+
+Section 1 defines R as the Cholesky factor of J^T J.  A CholeskyQR reaches
+it from the Gram matrix, whose condition number is the square of J's, so a
+Gram-based factorisation cannot tell a column whose residual against the
+columns before it is below the Gram's rounding level from a dependent one.
+The library then gives that column a zero row of R and reports it:
+
+* the call's device status is FIGARO_ERR_RANK_DEFICIENT (8) unless
+  FIGARO_FLAG_ALLOW_RANK_DEFICIENT is set, R and sigma are still written,
+  and figaro_info.dependent_columns counts the zero rows;
+* FIGARO_FLAG_SHIFTED_CHOLQR3 factors G1 + s I first (shifted CholeskyQR3)
+  and adds a third Gram pass, which recovers ill-conditioned full-rank joins.
+
+The stress form of the wide workload (B = B0 V D V^T with a random
+orthogonal V, condition number 1e8: no column scaling undoes it) is checked
+on both paths: the plain FP64 CholeskyQR2 reports it, the shifted CholeskyQR3
+meets the FP64 bar, and the mixed path either meets its bar or reports it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import config, make_pair, random_orthogonal, Table
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-6}
+RANK_DEFICIENT = 8
+
+
+@pytest.fixture(scope="module")
+def fg():
+    import paper_2503_23385_gb300 as fg
+    fg.library()
+    return fg
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def dev(torch, T):
+    return (torch.from_numpy(np.ascontiguousarray(T.x)).cuda(), torch.from_numpy(np.ascontiguousarray(T.key)).cuda())
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def as_f32(T):
+    return Table(T.x.astype(np.float32), T.key)
+
+
+def run(fg, torch, A, B, path, flags=0):
+    """(R, sigma, device status, info) of one call; the status is read, not raised."""
+    a, b = dev(torch, A), dev(torch, B)
+    solver = fg.Solver(a, b, path=path, flags=flags)
+    R, s = solver(a, b)
+    status = solver.status()
+    info = solver.info()
+    return R.cpu().numpy(), s.cpu().numpy(), status, info
+
+
+def graded_b(n2, cond, seed):
+    """B's mixing V D V^T with singular values from 1 down to 1/cond."""
+    v = random_orthogonal(np.random.default_rng(seed), n2)
+    d = cond ** (-np.arange(n2) / (n2 - 1))
+    return (v * d) @ v.T
+
+
+def test_short_join_is_reported_and_allowed(fg, torch):
+    """2 join rows, 5 columns: 3 columns are dependent on the others."""
+    rng = np.random.default_rng(81)
+    A = Table(rng.standard_normal((5, 3)), np.array([0, 1, 2, 3, 4], np.int32))
+    B = Table(rng.standard_normal((4, 2)), np.array([0, 9, 9, 1], np.int32))
+    for path in ("fp64", "mixed"):
+        Rref, sref = oracle.join_r_sigma(*((as_f32(A).x, A.key, as_f32(B).x, B.key) if path == "mixed"
+                                           else (A.x, A.key, B.x, B.key)), route="materialized")
+        R, s, st, info = run(fg, torch, A, B, path)
+        assert st == RANK_DEFICIENT, path
+        assert info["dependent_columns"] == 3, (path, info)
+        assert rel(R, Rref) <= TOL[path] and rel(s, sref) <= TOL[path]  # still written
+        R2, s2, st2, info2 = run(fg, torch, A, B, path, flags=fg.FLAG_ALLOW_RANK_DEFICIENT)
+        assert st2 == 0 and info2["dependent_columns"] == 3
+        assert np.array_equal(R, R2) and np.array_equal(s, s2)
+        with pytest.raises(fg.FigaroError) as e:
+            fg.join_qr_svd(dev(torch, A), dev(torch, B), path=path)
+        assert e.value.status == RANK_DEFICIENT
+
+
+def test_empty_join_and_zero_column_are_not_reported(fg, torch):
+    """A column that is zero in J gets a zero row of R without the status:
+    nothing numerical was decided there."""
+    rng = np.random.default_rng(82)
+    A = Table(rng.standard_normal((50, 3)), np.zeros(50, np.int32))
+    B = Table(rng.standard_normal((40, 2)), np.ones(40, np.int32))
+    for path in ("fp64", "mixed"):
+        R, s, st, info = run(fg, torch, A, B, path)
+        assert st == 0 and np.all(R == 0) and np.all(s == 0)
+        assert info["dependent_columns"] == 5
+    A, B = make_pair(3000, 4, 2500, 3, 40, np.float64, "normal", seed=83)
+    x = A.x.copy()
+    x[:, 2] = 0.0
+    A = Table(x, A.key)
+    for path in ("fp64", "mixed"):
+        Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key)
+        R, s, st, info = run(fg, torch, A, B, path)
+        assert st == 0 and info["dependent_columns"] == 1
+        assert np.all(R[2] == 0)
+        assert rel(R, Rref) <= TOL[path] and rel(s, sref) <= TOL[path]
+
+
+@pytest.mark.parametrize("n1,n2", [(16, 16), (40, 30), (100, 60)], ids=["32", "70", "160-wide"])
+def test_duplicated_column_counted(fg, torch, n1, n2):
+    A, B = make_pair(3000, n1, 2500, n2, 30, np.float64, "normal", seed=84 + n1)
+    x = A.x.copy()
+    x[:, 5] = x[:, 1]
+    A = Table(x, A.key)
+    for path in ("fp64", "mixed"):
+        R, s, st, info = run(fg, torch, A, B, path)
+        assert st == RANK_DEFICIENT and info["dependent_columns"] == 1, (path, st, info)
+        assert np.all(R[5] == 0)
+        _, _, st2, _ = run(fg, torch, A, B, path, flags=fg.FLAG_ALLOW_RANK_DEFICIENT)
+        assert st2 == 0
+
+
+@pytest.mark.parametrize("n1,n2", [(16, 16), (48, 48), (128, 128)], ids=["32", "96", "256-wide"])
+def test_ill_conditioned_full_rank(fg, torch, n1, n2):
+    """cond(J) about 1e4 along directions that are not columns.  The FP64
+    path meets its bar with CholeskyQR2 and with the shifted CholeskyQR3.  The
+    mixed path's CholeskyQR2 reports the join (its FP32 Gram cannot resolve a
+    pivot of cond^-2 = 1e-8); its shifted CholeskyQR3 factors it, to within
+    a bound proportional to the condition number."""
+    A, B = make_pair(6000, n1, 5000, n2, 60, np.float64, "normal", seed=90 + n1)
+    B = Table(np.ascontiguousarray(B.x @ graded_b(n2, 1e4, 91 + n2)), B.key)
+    for path in ("fp64", "mixed"):
+        Ar, Br = (A, B) if path == "fp64" else (as_f32(A), as_f32(B))
+        Rref, sref = oracle.join_r_sigma(Ar.x, Ar.key, Br.x, Br.key)
+        if path == "fp64":
+            R, s, st, info = run(fg, torch, A, B, path)
+            assert st == 0 and info["dependent_columns"] == 0
+            assert rel(R, Rref) <= 1e-10 and rel(s, sref) <= 1e-10, (rel(R, Rref), rel(s, sref))
+        else:
+            R, s, st, info = run(fg, torch, A, B, path)
+            assert st == RANK_DEFICIENT and info["dependent_columns"] >= 1
+        R, s, st, info = run(fg, torch, A, B, path, flags=fg.FLAG_SHIFTED_CHOLQR3)
+        assert st == 0 and info["dependent_columns"] == 0, (path, st, info)
+        tol = 1e-10 if path == "fp64" else 1e-4
+        assert rel(R, Rref) <= tol and rel(s, sref) <= tol, (path, rel(R, Rref), rel(s, sref))
+        assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+
+
+def test_shifted_cholqr3_on_well_conditioned_joins(fg, torch):
+    """The third pass changes nothing a well-conditioned join needs: both
+    paths keep their bars with the flag."""
+    A, B = make_pair(20000, 8, 15000, 8, 300, np.float32, "normal", seed=95)
+    Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key)
+    for path in ("fp64", "mixed"):
+        R, s, st, _ = run(fg, torch, A, B, path, flags=fg.FLAG_SHIFTED_CHOLQR3)
+        assert st == 0
+        assert rel(R, Rref) <= TOL[path] and rel(s, sref) <= TOL[path], (path, rel(R, Rref), rel(s, sref))
+
+
+def test_c4_stress_variant(fg, torch):
+    """The wide ill-conditioned workload at 2 % of its rows with B = B0 V D V^T
+    (condition 1e8 along random directions).  FP64 CholeskyQR2 reports the
+    join; the shifted CholeskyQR3 on the FP64 path meets the FP64 bar (R and
+    sigma in relative Frobenius norm, and every singular value to 1e-7
+    relative); the mixed path, whose FP32 data cannot resolve singular
+    values below ~1e-7 sigma_max, either meets its bar or reports the join."""
+    A, B = config("c4_stress", scale=0.02)
+    Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key, route="reduced")
+    assert sref[0] / sref[-1] > 1e7
+    R, s, st, info = run(fg, torch, A, B, "fp64")
+    assert st == RANK_DEFICIENT and info["dependent_columns"] >= 1
+    R, s, st, info = run(fg, torch, A, B, "fp64", flags=fg.FLAG_SHIFTED_CHOLQR3)
+    assert st == 0 and info["dependent_columns"] == 0, info
+    assert rel(R, Rref) <= 1e-10 and rel(s, sref) <= 1e-10, (rel(R, Rref), rel(s, sref))
+    assert np.max(np.abs(s - sref) / sref) <= 1e-7, np.max(np.abs(s - sref) / sref)
+    for flags in (0, fg.FLAG_SHIFTED_CHOLQR3):
+        R, s, st, info = run(fg, torch, A, B, "mixed", flags=flags)
+        ok = rel(R, Rref) <= TOL["mixed"] and rel(s, sref) <= TOL["mixed"]
+        assert st == RANK_DEFICIENT or (st == 0 and ok), (flags, st, rel(R, Rref), rel(s, sref))

@@ -14,6 +14,9 @@ benchmark configurations:
           {8, 16, 32, 64}, FP32 N(0,1), K = max(1, min(m1, m2) // 10) keys.
 * ``c4``  2e5 + 2e5 rows, 256 + 256 FP32 features; A N(0,1), B = B0 * D with
           D_jj = 10^(-8 j / (n2 - 1)) (column scaling, condition 1e8), 100 keys.
+* ``c4_stress``  c4 with truly ill-conditioned B = B0 V D V^T, V a random
+          (Haar) orthogonal matrix: the small singular directions are not
+          columns, so no column scaling undoes them (condition 1e8).
 * ``paper_shape``  the paper's own experiment: one key (Cartesian product),
           m rows per table, U(0,1) features.
 
@@ -74,6 +77,13 @@ def zipf_keys(rng, m, num_keys, s, ids):
     return ids[rank].astype(np.int32)
 
 
+def random_orthogonal(rng, n):
+    """A Haar-distributed n x n orthogonal matrix: the orthogonal factor of a
+    Gaussian matrix with its columns' signs fixed (Mezzadri, Notices AMS 2007)."""
+    q, r = np.linalg.qr(rng.standard_normal(size=(n, n)))
+    return q * np.sign(np.diag(r))
+
+
 def make_pair(m1, n1, m2, n2, num_keys, dtype=np.float32, dist="normal", seed=0, key_offset=0):
     """Two tables with uniform keys over [key_offset, key_offset + num_keys)."""
     ra, rb = _rng(seed * 2 + 1), _rng(seed * 2 + 2)
@@ -86,7 +96,7 @@ def config(name: str, scale: float = 1.0, rank: int = 0):
     """Tables of a named configuration.  ``scale`` < 1 shrinks the row counts
     (and key counts in proportion) for quick runs; ``rank`` selects an
     independent replica (different seed) for multi-process runs."""
-    cfg = {"c0": 0, "c1": 1, "c2": 2, "c3": 3, "c4": 4, "paper_shape": 5}[name]
+    cfg = {"c0": 0, "c1": 1, "c2": 2, "c3": 3, "c4": 4, "paper_shape": 5, "c4_stress": 4}[name]
     seed = BASE_SEED + 1000 * cfg + 100000 * rank
 
     def rows(v):
@@ -104,14 +114,19 @@ def config(name: str, scale: float = 1.0, rank: int = 0):
         A = Table(_features(ra, m1, 32, "uniform_pm1", np.float32), zipf_keys(ra, m1, nk, 1.2, ids))
         B = Table(_features(rb, m2, 32, "uniform_pm1", np.float32), zipf_keys(rb, m2, nk, 1.2, ids))
         return A, B
-    if name == "c4":
+    if name in ("c4", "c4_stress"):
         nk = 100
         ra, rb = _rng(seed + 1), _rng(seed + 2)
         m = rows(200_000)
         A = Table(_features(ra, m, 256, "normal", np.float32), uniform_keys(ra, m, nk))
         b0 = rb.standard_normal(size=(m, 256))
         d = 10.0 ** (-8.0 * np.arange(256) / 255.0)
-        B = Table(np.ascontiguousarray((b0 * d).astype(np.float32)), uniform_keys(rb, m, nk))
+        if name == "c4":
+            b = b0 * d
+        else:
+            v = random_orthogonal(_rng(seed + 9), 256)
+            b = b0 @ (v * d) @ v.T
+        B = Table(np.ascontiguousarray(b.astype(np.float32)), uniform_keys(rb, m, nk))
         return A, B
     if name == "paper_shape":
         m = rows(1600)
