@@ -122,10 +122,13 @@ enum {
    * factorisation is of G1 + s I (s = 10 n u trace(G1), u = 2^-24 on the
    * mixed path and 2^-53 on the FP64 path, on the non-zero diagonal), which
    * succeeds for ill-conditioned joins, and a third Gram pass follows.  It
-   * costs one more pass over the reduced matrix; the FP64 path then handles
-   * condition numbers up to about 1e14, the mixed path up to about 1e4
-   * (beyond which its FP32 data cannot resolve the small directions).  Single
-   * calls only: figaro_batch_join runs such instances one after another.   */
+   * costs one more pass over the reduced matrix.  Measured: the FP64 path
+   * factors a join of condition number 1.2e8 (where its CholeskyQR2 reports
+   * a dependent column) with R within 4e-15 and every singular value within
+   * 2e-10 of Householder QR; the mixed path reaches its 1e-6 bar up to
+   * condition 1e5 (its CholeskyQR2 up to 1e3) and reports joins beyond that,
+   * whose small directions its FP32 data cannot resolve.  Single calls only:
+   * figaro_batch_join runs such instances one after another.               */
   FIGARO_FLAG_SHIFTED_CHOLQR3 = 1 << 4
 };
 

@@ -1095,6 +1095,15 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         // tested here is at most one phase behind the phase tested (each test
         // follows the issue that consumed the previous phase), so the parity
         // tests are exact.  The loop gives up after spin_limit idle polls.
+        // The shared-memory descriptors are computed once: their address
+        // field holds bytes / 16, so the stages, the Z buffers and the K steps
+        // (32 bytes of a K-major row, 1,024 bytes of 8 packed rows) are
+        // constants added to a base descriptor, and the issue of a formation
+        // or a Gram is a straight run of MMAs.
+        const uint64_t dx0 = desc_kmajor_sw128(smem_u32(base));
+        const uint64_t dwh = desc_kmajor_sw128(wh), dwl = desc_kmajor_sw128(wl);
+        const uint64_t dz0 = desc_mn_sw128_32b(smem_u32(base + kP2Zq), static_cast<uint32_t>(wrq * 128));
+        const int fsteps = a.ksteps_f, gsteps = wrq / 8;
         int nf = 0, ng = 0;
         int64_t idle = 0;
         while (ng < n) {
@@ -1104,16 +1113,18 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
             if (mbar_test(&S.op_full[s], static_cast<uint32_t>((nf / nst) & 1)) &&
                 (nf < 2 || mbar_test(&S.d1_empty[bd], static_cast<uint32_t>(((nf / 2) - 1) & 1)))) {
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint32_t ah = smem_u32(base + s * stage_bytes), al = ah + static_cast<uint32_t>(raw_bytes);
-              for (int ks = 0; ks < a.ksteps_f; ++ks) {
-                const uint32_t o = static_cast<uint32_t>(ks * 32);
-                mma_tf32(d1_addr(bd), desc_kmajor_sw128(al + o), desc_kmajor_sw128(wh + o), idf, ks > 0 ? 1u : 0u);
-                mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wl + o), idf, 1u);
-              }
-              for (int ks = 0; ks < a.ksteps_f; ++ks) {
-                const uint32_t o = static_cast<uint32_t>(ks * 32);
-                mma_tf32(d1_addr(bd), desc_kmajor_sw128(ah + o), desc_kmajor_sw128(wh + o), idf, 1u);
-              }
+              const uint64_t dah = dx0 + static_cast<uint64_t>((s * stage_bytes) >> 4);
+              const uint64_t dal = dah + static_cast<uint64_t>(raw_bytes >> 4);
+              const uint32_t d1 = d1_addr(bd);
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks)
+                if (ks < fsteps) {
+                  mma_tf32(d1, dal + 2u * ks, dwh + 2u * ks, idf, ks > 0 ? 1u : 0u);
+                  mma_tf32(d1, dah + 2u * ks, dwl + 2u * ks, idf, 1u);
+                }
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks)
+                if (ks < fsteps) mma_tf32(d1, dah + 2u * ks, dwh + 2u * ks, idf, 1u);
               mma_commit(&S.stage_empty[s]);
               mma_commit(&S.d1_full[bd]);
               ++nf;
@@ -1125,11 +1136,12 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
             if (mbar_test(&S.q_full[b], static_cast<uint32_t>((ng / 2) & 1)) &&
                 (ng < 2 || mbar_test(&S.acc_empty[b], static_cast<uint32_t>(((ng / 2) - 1) & 1)))) {
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint64_t dz =
-                  desc_mn_sw128_32b(smem_u32(base + kP2Zq + b * kP2ZqBytes), static_cast<uint32_t>(wrq * 128));
-              for (int ks = 0; ks < wrq / 8; ++ks)
-                mma_tf32(acc_addr(b, 0), dz + static_cast<uint64_t>(ks * 64), dz + static_cast<uint64_t>(ks * 64), idg,
-                         ks > 0 ? 1u : 0u);
+              const uint64_t dz = dz0 + static_cast<uint64_t>((b * kP2ZqBytes) >> 4);
+              const uint32_t acc = acc_addr(b, 0);
+              mma_tf32(acc, dz, dz, idg, 0u);
+#pragma unroll
+              for (int ks = 1; ks < 8; ++ks)
+                if (ks < gsteps) mma_tf32(acc, dz + 64u * ks, dz + 64u * ks, idg, 1u);
               mma_commit(&S.q_empty[b]);
               mma_commit(&S.acc_full[b]);
               ++ng;

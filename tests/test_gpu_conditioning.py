@@ -134,8 +134,8 @@ def test_ill_conditioned_full_rank(fg, torch, n1, n2):
     """cond(J) about 1e4 along directions that are not columns.  The FP64
     path meets its bar with CholeskyQR2 and with the shifted CholeskyQR3.  The
     mixed path's CholeskyQR2 reports the join (its FP32 Gram cannot resolve a
-    pivot of cond^-2 = 1e-8); its shifted CholeskyQR3 factors it, to within
-    a bound proportional to the condition number."""
+    pivot of cond^-2 = 1e-8); its shifted CholeskyQR3 factors it within the
+    mixed path's usual bar (measured ~3e-7 at condition 1e4 and 1e5)."""
     A, B = make_pair(6000, n1, 5000, n2, 60, np.float64, "normal", seed=90 + n1)
     B = Table(np.ascontiguousarray(B.x @ graded_b(n2, 1e4, 91 + n2)), B.key)
     for path in ("fp64", "mixed"):
@@ -150,7 +150,7 @@ def test_ill_conditioned_full_rank(fg, torch, n1, n2):
             assert st == RANK_DEFICIENT and info["dependent_columns"] >= 1
         R, s, st, info = run(fg, torch, A, B, path, flags=fg.FLAG_SHIFTED_CHOLQR3)
         assert st == 0 and info["dependent_columns"] == 0, (path, st, info)
-        tol = 1e-10 if path == "fp64" else 1e-4
+        tol = TOL[path]
         assert rel(R, Rref) <= tol and rel(s, sref) <= tol, (path, rel(R, Rref), rel(s, sref))
         assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
 

@@ -327,7 +327,8 @@ def test_narrow_graded_columns(fg, torch):
     d = 10.0 ** (-6.0 * np.arange(16) / 15.0)
     B = Table(np.ascontiguousarray(B.x * d), B.key)
     dd = np.concatenate([np.ones(16), d])
-    for path, tol, tol_sv in (("fp64", 1e-10, 1e-9), ("mixed", 1e-6, 1e-3)):
+    # per-sigma bars: the FP64 path reaches ~1e-14, the mixed path ~6e-7 here
+    for path, tol, tol_sv in (("fp64", 1e-10, 1e-9), ("mixed", 1e-6, 5e-6)):
         Rref, sref = oracle_ref(A, B, path)
         R, s = gpu_r_sigma(fg, torch, A, B, path)
         assert rel(R, Rref) <= tol and rel(s, sref) <= tol

@@ -94,7 +94,8 @@ def test_c4_shape_column_scaled(fg, torch):
     assert A.n + B.n == 512
     Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key, route="reduced")
     d = np.concatenate([np.ones(A.n), 10.0 ** (-8.0 * np.arange(B.n) / (B.n - 1))])
-    for path, tol, tol_sv in (("fp64", 1e-10, 1e-8), ("mixed", 1e-6, 1e-3)):
+    # per-sigma bars: the FP64 path reaches ~1e-13, the mixed path ~2e-5 here
+    for path, tol, tol_sv in (("fp64", 1e-10, 1e-8), ("mixed", 1e-6, 2e-4)):
         R, s = run(fg, torch, A, B, path)
         assert rel(R, Rref) <= tol and rel(s, sref) <= tol
         escaled = rel(R / d, Rref / d)
