@@ -62,6 +62,40 @@ def parse():
     return ap.parse_args()
 
 
+# FP64 FMA issue on this GPU, measured by a clock64 microbenchmark on one SM
+# (1.9 FMA per SM per clock): 152 SMs x 1.9 x 2 flops x 2,070 MHz
+FP64_PEAK_TFLOPS = 152 * 1.9 * 2 * 2070e6 / 1e12
+
+
+def host_cpu():
+    """Host cores and CPU model (for the oracle's timing rows)."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    if low.startswith("model name"):
+                        break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def gram_pass_flops(A, B, heads, pass2):
+    """Algorithmic flops (2 per FMA) of one CholeskyQR Gram pass over the
+    reduced matrix: the symmetric Gram (k (k + 1) / 2 FMA per row of a block of
+    width k) and, in pass 2, the formation Q = X W (k x kout FMA per row)."""
+    n = A.n + B.n
+    blocks = [(heads, n, n), (A.m, A.n, n), (B.m, B.n, B.n)]
+    f = 0.0
+    for rows, k, kout in blocks:
+        w = kout if pass2 else k
+        f += rows * (w * (w + 1) / 2 + (k * kout if pass2 else 0))
+    return 2.0 * f
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -223,7 +257,8 @@ def run_reference(args, rank, world):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.config], "path": "oracle O1 per instance"},
-                "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample},
+                "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample,
+                                 **host_cpu()},
                 "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -245,7 +280,8 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.config], "path": "oracle O1 (materialised join, Householder QR, "
                        "one-sided Jacobi)"},
-            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample,
+                                 **host_cpu()},
             "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -372,14 +408,20 @@ def main():
     ein = A.x.itemsize
     heads = info.get("num_runs_a", 0) if isinstance(info, dict) else 0
     gram_bytes = sum(T.m * T.n * s for T in (A, B)) + heads * n * s
+    roofline_avg = None
     if n <= 128:
-        gram_ms = (phases["gram1"] + phases["gram2"]) / 2
-        g_achieved = gram_bytes / (gram_ms / 1e3) / 1e9
-        roofline = {"kernel": "gram_pack_kernel: one CholeskyQR Gram pass (head, A-tail and B-tail launches + "
-                              "reduce), average of the two passes",
-                    "bound": "hbm", "achieved": g_achieved, "peak": hbm, "unit": "GB/s", "frac": g_achieved / hbm,
+        # the dominant launch group is the second pass (formation Q = X W and the Gram of Q); the
+        # average of the two passes is reported beside it
+        g2 = gram_bytes / (phases["gram2"] / 1e3) / 1e9
+        roofline = {"kernel": "gram_pack_kernel: CholeskyQR pass 2 (head, A-tail and B-tail launches + reduce)",
+                    "bound": "hbm", "achieved": g2, "peak": hbm, "unit": "GB/s", "frac": g2 / hbm,
                     "traffic": measured_traffic("gram_pass", args.config), "bytes_per_launch": gram_bytes,
                     "peak_source": peak_kind}
+        gram_ms = (phases["gram1"] + phases["gram2"]) / 2
+        g_avg = gram_bytes / (gram_ms / 1e3) / 1e9
+        roofline_avg = {"kernel": "gram_pack_kernel: one CholeskyQR Gram pass, average of the two passes",
+                        "bound": "hbm", "achieved": g_avg, "peak": hbm, "unit": "GB/s", "frac": g_avg / hbm,
+                        "bytes_per_launch": gram_bytes, "peak_source": peak_kind}
     else:
         # wide joins: pass 1 of the CUDA-core tile Gram (64 x 64 upper tiles), bound by FP32 FMA issue;
         # flops of the tiles it computes, against 152 SMs x 128 FP32 lanes x 2 flops x the max SM clock
@@ -449,11 +491,67 @@ def main():
             fm = statistics.mean(f_ms)
             d = np.linalg.norm((solver.R - s64.R).cpu().numpy()) / np.linalg.norm(s64.R.cpu().numpy())
             ds = np.linalg.norm((solver.sigma - s64.sigma).cpu().numpy()) / np.linalg.norm(s64.sigma.cpu().numpy())
+            # phase times of the FP64 path (one call with the phase events)
+            s64p = fg.Solver(tA, tB, path="fp64", phase_events=ev_arr)
+            flush.fill_(1)
+            s64p(tA, tB, stream=stream)
+            evs[-1].synchronize()
+            ph64 = {name: evs[i].elapsed_time(evs[i + 1]) for i, name in enumerate(fg.PHASES)}
+            # its dominant kernel: the second Gram pass on CUDA cores, bound by FP64 FMA issue
+            f2 = gram_pass_flops(A, B, heads, True)
+            tf = f2 / (ph64["gram2"] / 1e3) / 1e12
             fp64 = {"value": world * rows / (fm / 1e3), "unit": "rows/s", "ms_per_step": fm,
-                    "mixed_vs_fp64_rel_err_R": float(d), "mixed_vs_fp64_rel_err_sigma": float(ds)}
+                    "mixed_vs_fp64_rel_err_R": float(d), "mixed_vs_fp64_rel_err_sigma": float(ds),
+                    "phases_ms": ph64,
+                    "roofline": {"kernel": "gram_kernel<double>: CholeskyQR pass 2 (CUDA cores, FP64)", "bound": "alu",
+                                 "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": tf / FP64_PEAK_TFLOPS, "flops_per_launch": f2,
+                                 "peak_source": "measured FP64 FMA issue: 1.9 per SM per clock x 152 SMs x 2 x "
+                                                "2070 MHz"}}
+            del s64p
             del s64
         except Exception as exc:
             fp64 = {"error": repr(exc)}
+
+    # ---- pre-sorted tables (G13: the paper times inputs already in key order) --
+    presorted = None
+    if args.task == "qr_svd" and args.config in ("c1", "c2", "c0"):
+        try:
+            pa, pb = np.argsort(A.key, kind="stable"), np.argsort(B.key, kind="stable")
+            sA = (torch.from_numpy(np.ascontiguousarray(A.x[pa])).to(dev), torch.from_numpy(A.key[pa]).to(dev))
+            sB = (torch.from_numpy(np.ascontiguousarray(B.x[pb])).to(dev), torch.from_numpy(B.key[pb]).to(dev))
+            sp = fg.Solver(sA, sB, path=args.path, flags=fg.FLAG_PRESORTED)
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    sp(sA, sB, stream=stream)
+            stream.synchronize()
+            gp = None
+            if graph is not None:
+                gp = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gp, stream=stream, capture_error_mode="relaxed"):
+                    sp(sA, sB, stream=stream)
+            p_ms = []
+            with torch.cuda.stream(stream):
+                for _ in range(max(3, min(args.steps, 50))):
+                    flush.fill_(1)
+                    s0.record(stream)
+                    if gp is not None:
+                        gp.replay()
+                    else:
+                        sp(sA, sB, stream=stream)
+                    s1.record(stream)
+                    s1.synchronize()
+                    p_ms.append(s0.elapsed_time(s1))
+            st = sp.status(stream)
+            if st != 0:
+                raise fg.FigaroError(st, "presorted")
+            pm = statistics.mean(p_ms)
+            presorted = {"value": world * rows / (pm / 1e3), "unit": "rows/s", "ms_per_step": pm,
+                         "what": "tables in key order (host-sorted once, outside the timing), FIGARO_FLAG_PRESORTED: "
+                                 "the grouping without the radix sort"}
+            del sp, gp, sA, sB
+        except Exception as exc:
+            presorted = {"error": repr(exc)}
 
     # ---- materialised-join QR baseline (torch / cuSOLVER on J) ----------
     mat = None
@@ -467,7 +565,7 @@ def main():
         rps, dt, srows, jrows = oracle_rows_per_s(A, B, keys)
         cpu = {"value": rps, "unit": "rows/s", "cores": 1, "kind": "oracle",
                "sample": f"rows with one of the first {keys} key ids: {srows} input rows, {jrows} join rows, "
-                         f"{dt:.1f} s (O1: materialised join, Householder QR, one-sided Jacobi)"}
+                         f"{dt:.1f} s (O1: materialised join, Householder QR, one-sided Jacobi)", **host_cpu()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
@@ -476,9 +574,10 @@ def main():
                 "config": {"workload": WORKLOADS[args.config], "path": args.path, "rows_per_gpu": rows,
                            "graph": graph is not None, "gram_engine": args.gram_engine, "task": args.task,
                            "l2": "inputs 136 MB + ~300 MB workspace exceed L2; 256 MB flush between steps"},
-                "roofline": roofline, "roofline_head_tail": roofline_ht, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "roofline_gram_avg": roofline_avg, "roofline_head_tail": roofline_ht,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "phases_ms": phases, "instance": info,
-                "fp64_path": fp64, "materialized_baseline": mat}
+                "fp64_path": fp64, "presorted": presorted, "materialized_baseline": mat}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -629,7 +728,7 @@ def run_batch(args, rank, world, torch, dist, fg, dev, local):
         rps, dt, srows, used, jrows = oracle_batch_rows_per_s(inst, 12.0)
         cpu = {"value": rps, "unit": "rows/s", "cores": 1, "kind": "oracle",
                "sample": f"the first {used} of the 512 instances: {srows} input rows, {jrows} join rows, {dt:.1f} s "
-                         f"(O1: materialised join, Householder QR, one-sided Jacobi, per instance)"}
+                         f"(O1: materialised join, Householder QR, one-sided Jacobi, per instance)", **host_cpu()}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -674,16 +773,30 @@ def materialized_baseline(torch, A, B, dev, stream):
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        torch.linalg.qr(J[:4096], mode="r")
-        t0.record()
-        R = torch.linalg.qr(J, mode="r")[1]
-        torch.linalg.svdvals(R)
-        t1.record()
-        t1.synchronize()
-        ms = t0.elapsed_time(t1)
-        del J
-        return {"value": (A.m + B.m) / (ms / 1e3), "unit": "rows/s", "ms": ms, "join_rows": join_rows,
-                "dtype": "f32", "what": "torch.linalg.qr(J, mode='r') + svdvals(R) on the materialised join"}
+
+        def timed(Jm):
+            torch.linalg.qr(Jm[:4096], mode="r")
+            t0.record()
+            R = torch.linalg.qr(Jm, mode="r")[1]
+            torch.linalg.svdvals(R)
+            t1.record()
+            t1.synchronize()
+            return t0.elapsed_time(t1)
+
+        ms = timed(J)
+        out = {"value": (A.m + B.m) / (ms / 1e3), "unit": "rows/s", "ms": ms, "join_rows": join_rows,
+               "dtype": "f32", "what": "torch.linalg.qr(J, mode='r') + svdvals(R) on the materialised join"}
+        free, _ = torch.cuda.mem_get_info(dev)
+        if 2 * bytes_needed * 2.5 < free:  # J in FP64 beside J in FP32, and the QR's work space
+            J64 = J.double()
+            del J
+            ms64 = timed(J64)
+            del J64
+            out["fp64"] = {"value": (A.m + B.m) / (ms64 / 1e3), "unit": "rows/s", "ms": ms64, "dtype": "f64"}
+        else:
+            del J
+            out["fp64"] = {"skipped": f"J in FP64 needs {2 * bytes_needed / 1e9:.1f} GB"}
+        return out
     except Exception as exc:
         return {"error": repr(exc)}
 

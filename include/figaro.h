@@ -129,7 +129,15 @@ enum {
    * condition 1e5 (its CholeskyQR2 up to 1e3) and reports joins beyond that,
    * whose small directions its FP32 data cannot resolve.  Single calls only:
    * figaro_batch_join runs such instances one after another.               */
-  FIGARO_FLAG_SHIFTED_CHOLQR3 = 1 << 4
+  FIGARO_FLAG_SHIFTED_CHOLQR3 = 1 << 4,
+  /* Each table's rows are already in ascending key order (non-decreasing
+   * int32 keys; Section 2 of the paper assumes such inputs).  The radix sort
+   * is skipped: the permutation is the identity and the keys are the sorted
+   * keys.  Within a key the rows keep their order, as after the stable sort.
+   * A table that is not in order makes the call's device status
+   * FIGARO_ERR_INVALID_ARG (results invalid).  Single calls only:
+   * figaro_batch_join runs such instances one after another.              */
+  FIGARO_FLAG_PRESORTED = 1 << 5
 };
 
 typedef struct figaro_table {

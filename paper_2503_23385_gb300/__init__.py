@@ -22,7 +22,7 @@ __all__ = [
     "join_qr_svd_host", "batch_join", "get_status", "Solver", "STATUS_NAMES", "event_array", "kernel_launches",
     "host_workspace_size", "PHASES", "NUM_PHASE_EVENTS", "join_singular_values_fixed", "FIXED_SCRATCH_BYTES",
     "BatchSolver", "FLAG_AUTOTUNE", "join_least_squares", "LsqSolver", "join_svd", "get_info",
-    "FLAG_ALLOW_RANK_DEFICIENT", "FLAG_SHIFTED_CHOLQR3",
+    "FLAG_ALLOW_RANK_DEFICIENT", "FLAG_SHIFTED_CHOLQR3", "FLAG_PRESORTED",
 ]
 
 PATH_FP64, PATH_MIXED = 0, 1
@@ -33,6 +33,7 @@ FLAG_HOST_OUTPUT = 1
 FLAG_AUTOTUNE = 1 << 2
 FLAG_ALLOW_RANK_DEFICIENT = 1 << 3
 FLAG_SHIFTED_CHOLQR3 = 1 << 4
+FLAG_PRESORTED = 1 << 5
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "WORKSPACE_TOO_SMALL", 3: "CUDA", 4: "NOT_SPD",
                 5: "NO_CONVERGENCE", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED", 8: "RANK_DEFICIENT"}
 

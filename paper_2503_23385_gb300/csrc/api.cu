@@ -246,6 +246,7 @@ figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, con
   c.p.withhold = (o.flags & FIGARO_FLAG_TEST_WITHHOLD) ? 1 : 0;
   c.p.report_rank = (o.flags & FIGARO_FLAG_ALLOW_RANK_DEFICIENT) ? 0 : c.p.n;
   c.p.shifted = (o.flags & FIGARO_FLAG_SHIFTED_CHOLQR3) ? 1 : 0;
+  c.p.presorted = (o.flags & FIGARO_FLAG_PRESORTED) ? 1 : 0;
   c.s = static_cast<cudaStream_t>(stream);
   if (o.phase_events) {
     c.events = true;
@@ -911,8 +912,8 @@ figaro_status figaro_batch_join(int32_t count, const figaro_table* A, const figa
     if (st != FIGARO_OK) return st;
     base += one;
     if (!R[i] && !sigma[i]) continue;
-    // (the shifted CholeskyQR3's third pass runs in single calls only)
-    const bool narrow = c.p.n <= kMaxWidth && !c.p.shifted;
+    // (the shifted CholeskyQR3's third pass and the presorted grouping run in single calls only)
+    const bool narrow = c.p.n <= kMaxWidth && !c.p.shifted && !c.p.presorted;
     const bool device_io = A[i].memory == FIGARO_MEM_DEVICE && B[i].memory == FIGARO_MEM_DEVICE && !host_out;
     if (narrow && device_io) {
       batched.push_back(c);
@@ -963,7 +964,7 @@ figaro_status figaro_batch_schedule(int32_t count, const figaro_table* A, const 
     Call c;
     plan_layout(c.p, nullptr, A[i].m, A[i].n, B[i].m, B[i].n, A[i].dtype == FIGARO_F64, o.path == FIGARO_PATH_MIXED,
                 0, 0, sm_count());
-    if (c.p.n <= kMaxWidth && !(o.flags & FIGARO_FLAG_SHIFTED_CHOLQR3)) calls.push_back(c);
+    if (c.p.n <= kMaxWidth && !(o.flags & (FIGARO_FLAG_SHIFTED_CHOLQR3 | FIGARO_FLAG_PRESORTED))) calls.push_back(c);
   }
   const BatchSchedule sc = schedule_for(calls);
   *gram_rows_per_cta = sc.gram_rows_per_cta;
@@ -997,6 +998,7 @@ figaro_status figaro_get_status(const void* ws, void* stream) {
       cudaSuccess)
     return FIGARO_ERR_CUDA;
   if (bits & kStatusTimeout) return FIGARO_ERR_DEVICE_TIMEOUT;
+  if (bits & kStatusUnsorted) return FIGARO_ERR_INVALID_ARG;
   if (bits & kStatusNotSpd) return FIGARO_ERR_NOT_SPD;
   if (bits & kStatusNoConvergence) return FIGARO_ERR_NO_CONVERGENCE;
   if (bits & kStatusRankDrop) return FIGARO_ERR_RANK_DEFICIENT;

@@ -15,6 +15,8 @@ enum : int32_t {
   // a factorisation marked a column with a non-zero norm dependent (its pivot
   // fell below rank_tol times its diagonal) and the call reports that column
   kStatusRankDrop = 1 << 7,
+  // FIGARO_FLAG_PRESORTED was set but a table's keys are not in ascending order
+  kStatusUnsorted = 1 << 8,
 };
 
 __device__ __forceinline__ void set_status(int32_t* word, int32_t bit) { atomicOr(word, bit); }

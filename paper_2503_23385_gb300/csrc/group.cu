@@ -126,6 +126,44 @@ __device__ __forceinline__ void key_hist_body(const TableWork& T, int t, DevHead
   }
 }
 
+// Tables already in key order (FIGARO_FLAG_PRESORTED; the paper's setting,
+// Section 2): the identity permutation, the keys as the sorted keys, the key
+// range, and a check that the order holds (a table that is not in order
+// sets kStatusUnsorted; the later steps stay in bounds either way).
+__global__ void __launch_bounds__(kSortThreads) presorted_kernel(TwoTables a) {
+  pdl_enter();
+  int tile;
+  const int t = table_of(a, blockIdx.x, tile);
+  const TableWork& T = a.t[t];
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  int bad = 0;
+  const int64_t base = static_cast<int64_t>(tile) * kSortTile;
+  for (int it = 0; it < kSortItems; ++it) {
+    const int64_t i = base + it * kSortThreads + threadIdx.x;
+    if (i < T.m) {
+      const int32_t k = T.key[i];
+      const uint32_t u = key_to_ordered(k);
+      lo = min(lo, u);
+      hi = max(hi, u);
+      if (i > 0 && T.key[i - 1] > k) bad = 1;
+      T.perm[i] = static_cast<int32_t>(i);
+      T.sorted_key[i] = k;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (lo <= hi) {
+      atomicMin(&a.h->kmin[t], lo);
+      atomicMax(&a.h->kmax[t], hi);
+    }
+    if (bad) set_status(&a.h->status, kStatusUnsorted);
+  }
+}
+
 __global__ void __launch_bounds__(kSortThreads) key_hist_kernel(TwoTables a) {
   pdl_enter();
   int tile;
@@ -676,19 +714,25 @@ cudaError_t launch_grouping(const Plan& p, cudaStream_t s) {
     if (err != cudaSuccess) return err;
     if (dev >= 0 && dev < 64) granted[dev] = 1;
   }
-  pdl_launch(key_hist_kernel, a.nb, kSortThreads, 0, s, a);
-  // passes past the key range's highest differing digit return at once
-  for (int pass = 0; pass < kMaxPasses; ++pass) {
-    if (pass > 0) pdl_launch(tile_count_kernel, a.nb, kSortThreads, 0, s, a, pass);
-    pdl_launch(tile_scan_kernel, 2 * kRadixBins, kRadixBins, 0, s, a, pass);
-    pdl_launch(sort_pass_kernel, a.nb, kSortThreads, kSortSmem, s, a, pass);
+  if (p.presorted) {
+    pdl_launch(presorted_kernel, a.nb, kSortThreads, 0, s, a);
+    count_launches(1);
+  } else {
+    pdl_launch(key_hist_kernel, a.nb, kSortThreads, 0, s, a);
+    // passes past the key range's highest differing digit return at once
+    for (int pass = 0; pass < kMaxPasses; ++pass) {
+      if (pass > 0) pdl_launch(tile_count_kernel, a.nb, kSortThreads, 0, s, a, pass);
+      pdl_launch(tile_scan_kernel, 2 * kRadixBins, kRadixBins, 0, s, a, pass);
+      pdl_launch(sort_pass_kernel, a.nb, kSortThreads, kSortSmem, s, a, pass);
+    }
+    count_launches(1 + 3 * kMaxPasses - 1);
   }
   pdl_launch(run_count_kernel, a.nb, kSortThreads, 0, s, a);
   pdl_launch(runs_kernel, a.nb, kSortThreads, 0, s, a);
   const int64_t mm = p.t[0].m > p.t[1].m ? p.t[0].m : p.t[1].m;
   const int mb = static_cast<int>((mm + 255) / 256);
   if (mb > 0) pdl_launch(match_kernel, mb, 256, 0, s, a);
-  count_launches(3 + 3 * kMaxPasses - 1 + (mb > 0 ? 1 : 0));
+  count_launches(2 + (mb > 0 ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -92,6 +92,7 @@ struct Plan {
   int withhold = 0;             // test-only fault injection (see FIGARO_FLAG_TEST_WITHHOLD)
   int report_rank = 0;          // leading columns whose drop raises FIGARO_ERR_RANK_DEFICIENT (0: none)
   int shifted = 0;              // shifted CholeskyQR3: shift G1, then a third Gram pass
+  int presorted = 0;            // the tables are in key order: no radix sort (identity permutation)
   int64_t lut_size = 0;         // entries of each table's key lookup table
   DevHeader* hdr = nullptr;
   void* head = nullptr;         // m1 x n slots, compute type

@@ -371,3 +371,29 @@ def test_narrow_rank_deficient(fg, torch, n1, n2, dup):
         assert s[-1] <= 10 * tol * s[0], (path, s[-1] / s[0])
         assert rel(s, sref) <= tol, (path, rel(s, sref))
         assert rel(R.T @ R, G) <= tol, (path, rel(R.T @ R, G))
+
+
+def test_presorted_tables_skip_the_sort(fg, torch):
+    """FIGARO_FLAG_PRESORTED (Section 2's setting: inputs sorted by the join
+    attribute): on tables already in key order the call skips the radix sort
+    and gives bitwise the results of the sorting path (a stable sort of
+    sorted keys is the identity); the grouping is the oracle's; a table that
+    is not in order is reported as an invalid argument."""
+    A, B = make_pair(30000, 8, 20000, 8, 700, np.float32, "normal", seed=97)
+    pa, pb = np.argsort(A.key, kind="stable"), np.argsort(B.key, kind="stable")
+    As, Bs = Table(np.ascontiguousarray(A.x[pa]), A.key[pa]), Table(np.ascontiguousarray(B.x[pb]), B.key[pb])
+    for path in ("fp64", "mixed"):
+        R0, s0 = gpu_r_sigma(fg, torch, As, Bs, path)
+        R1, s1 = gpu_r_sigma(fg, torch, As, Bs, path, flags=fg.FLAG_PRESORTED)
+        assert np.array_equal(R0, R1) and np.array_equal(s0, s1), path
+    ga, gb, G = fg.join_group(dev(torch, As), dev(torch, Bs), flags=fg.FLAG_PRESORTED)
+    oa, ob = oracle.group(As.key), oracle.group(Bs.key)
+    for g, o in ((ga, oa), (gb, ob)):
+        assert np.array_equal(g["perm"].cpu().numpy(), np.arange(o["perm"].size))
+        assert np.array_equal(g["perm"].cpu().numpy(), o["perm"])
+        assert np.array_equal(g["run_key"].cpu().numpy(), o["uniq"])
+        assert np.array_equal(g["run_offset"].cpu().numpy(), o["offset"])
+    assert G == oracle.match(oa, ob)["key"].size
+    with pytest.raises(fg.FigaroError) as e:
+        fg.join_qr_svd(dev(torch, A), dev(torch, Bs), flags=fg.FLAG_PRESORTED)
+    assert e.value.status == 1
