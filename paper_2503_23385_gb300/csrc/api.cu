@@ -162,11 +162,49 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
 
 namespace {
 
+// Library-owned side streams for staging host tables (created once per
+// device; calls that stage at the same time share them, which orders their
+// copies but never their results).
+constexpr int kStageStreams = 4;
+std::mutex g_stage_mu;
+cudaStream_t g_stage_streams[64][kStageStreams] = {};
+
+cudaError_t stage_streams(cudaStream_t (&out)[kStageStreams]) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  for (int i = 0; i < kStageStreams; ++i) {
+    if (!g_stage_streams[dev][i]) {
+      e = cudaStreamCreateWithFlags(&g_stage_streams[dev][i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+    out[i] = g_stage_streams[dev][i];
+  }
+  return cudaSuccess;
+}
+
 struct Call {
   Plan p;
   cudaStream_t s = nullptr;
   cudaEvent_t ev[FIGARO_NUM_PHASE_EVENTS] = {};
   bool events = false;
+  // host tables: the feature copies run on side streams while the call's
+  // stream groups the keys; the call's stream waits for them (join_staging)
+  // before the first step that reads features
+  cudaEvent_t staged[kStageStreams] = {};
+  int nstaged = 0;
+  cudaError_t join_staging() {
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < nstaged; ++i) {
+      const cudaError_t e = cudaStreamWaitEvent(s, staged[i], 0);
+      if (e != cudaSuccess && err == cudaSuccess) err = e;
+      cudaEventDestroy(staged[i]);
+    }
+    nstaged = 0;
+    return err;
+  }
   cudaError_t mark(int i) {
     if (!events) return cudaSuccess;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -257,17 +295,17 @@ figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, con
   }
   const figaro_table* tabs[2] = {A, B};
   const size_t ei = in_f64 ? 8 : 4;
+  bool staging = false;
   for (int t = 0; t < 2; ++t) {
     TableWork& T = c.p.t[t];
     const figaro_table* src = tabs[t];
     if (src->memory == FIGARO_MEM_HOST) {
+      // the keys on the call's stream: key grouping needs nothing else
       if (src->m > 0) {
-        cudaError_t e1 = cudaMemcpy2DAsync(const_cast<void*>(T.x), static_cast<size_t>(src->n) * ei, src->x,
-                                           static_cast<size_t>(src->ld) * ei, static_cast<size_t>(src->n) * ei,
-                                           static_cast<size_t>(src->m), cudaMemcpyHostToDevice, c.s);
-        cudaError_t e2 = cudaMemcpyAsync(const_cast<int32_t*>(T.key), src->key, sizeof(int32_t) * src->m,
-                                         cudaMemcpyHostToDevice, c.s);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) return FIGARO_ERR_CUDA;
+        if (cudaMemcpyAsync(const_cast<int32_t*>(T.key), src->key, sizeof(int32_t) * src->m, cudaMemcpyHostToDevice,
+                            c.s) != cudaSuccess)
+          return FIGARO_ERR_CUDA;
+        staging = true;
       }
     } else {
       T.x = src->x;
@@ -275,8 +313,55 @@ figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, con
       T.ld = src->ld;
     }
   }
+  if (staging) {
+    // the features in halves of each table on the side streams, after the
+    // call's stream has reached this point (the staging area may still be
+    // read by an earlier call on the same workspace)
+    cudaStream_t ss[kStageStreams];
+    cudaEvent_t fork = nullptr;
+    if (stage_streams(ss) != cudaSuccess || cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(fork, c.s) != cudaSuccess)
+      return FIGARO_ERR_CUDA;
+    int part = 0;
+    cudaError_t err = cudaSuccess;
+    for (int t = 0; t < 2 && err == cudaSuccess; ++t) {
+      const figaro_table* src = tabs[t];
+      if (src->memory != FIGARO_MEM_HOST || src->m == 0) continue;
+      TableWork& T = c.p.t[t];
+      const int64_t half = (src->m + 1) / 2;
+      for (int h = 0; h < 2 && err == cudaSuccess; ++h) {
+        const int64_t r0 = h * half, r1 = h ? src->m : half;
+        if (r1 <= r0) continue;
+        cudaStream_t st = ss[part];
+        cudaEvent_t done = nullptr;
+        err = cudaStreamWaitEvent(st, fork, 0);
+        if (err == cudaSuccess)
+          err = cudaMemcpy2DAsync(static_cast<char*>(const_cast<void*>(T.x)) + static_cast<size_t>(r0) * src->n * ei,
+                                  static_cast<size_t>(src->n) * ei,
+                                  static_cast<const char*>(src->x) + static_cast<size_t>(r0) * src->ld * ei,
+                                  static_cast<size_t>(src->ld) * ei, static_cast<size_t>(src->n) * ei,
+                                  static_cast<size_t>(r1 - r0), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+        if (err == cudaSuccess) err = cudaEventRecord(done, st);
+        if (done) c.staged[c.nstaged++] = done;
+        ++part;
+      }
+    }
+    cudaEventDestroy(fork);
+    if (err != cudaSuccess) {
+      c.join_staging();
+      return FIGARO_ERR_CUDA;
+    }
+  }
   return FIGARO_OK;
 }
+
+// Joins a call's staging copies into its stream when the entry point returns
+// (also on an early error return, so no copy is left unordered).
+struct StageJoin {
+  Call& c;
+  ~StageJoin() { c.join_staging(); }
+};
 
 #define FIGARO_TRY(expr)                                   \
   do {                                                     \
@@ -293,6 +378,7 @@ figaro_status run_grouping(Call& c) {
 }
 
 figaro_status run_factor(Call& c, double* R_dev, int64_t ldr) {
+  FIGARO_TRY(c.join_staging());  // the features are read from here on
   FIGARO_TRY(launch_ht_carry(c.p, c.s));
   FIGARO_TRY(c.mark(2));
   FIGARO_TRY(launch_ht_main(c.p, c.s));
@@ -739,6 +825,7 @@ figaro_status figaro_join_group(const figaro_table* A, const figaro_table* B, co
     if (!g->run_offset) return FIGARO_ERR_INVALID_ARG;
   }
   Call c;
+  StageJoin join_at_exit{c};
   figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
   if (st != FIGARO_OK) return st;
   for (int t = 0; t < 2; ++t) {
@@ -768,6 +855,7 @@ figaro_status figaro_join_head_tail(const figaro_table* A, const figaro_table* B
                                     void* head, void* tail_a, void* tail_b, void* ws, size_t ws_bytes,
                                     void* stream) {
   Call c;
+  StageJoin join_at_exit{c};
   figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
   if (st != FIGARO_OK) return st;
   if ((A->m > 0 && (!head || !tail_a)) || (B->m > 0 && !tail_b)) return FIGARO_ERR_INVALID_ARG;
@@ -778,6 +866,7 @@ figaro_status figaro_join_head_tail(const figaro_table* A, const figaro_table* B
   if (B->m > 0) c.p.t[1].tail = tail_b;
   st = run_grouping(c);
   if (st != FIGARO_OK) return st;
+  FIGARO_TRY(c.join_staging());
   FIGARO_TRY(launch_ht_carry(c.p, c.s));
   FIGARO_TRY(launch_ht_main(c.p, c.s));
   return FIGARO_OK;
@@ -787,6 +876,7 @@ figaro_status figaro_join_qr_r(const figaro_table* A, const figaro_table* B, con
                                int64_t ldr, void* ws, size_t ws_bytes, void* stream) {
   if (!R) return FIGARO_ERR_INVALID_ARG;
   Call c;
+  StageJoin join_at_exit{c};
   figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
   if (st != FIGARO_OK) return st;
   if (ldr < c.p.n) return FIGARO_ERR_INVALID_ARG;
@@ -799,6 +889,7 @@ figaro_status figaro_join_singular_values(const figaro_table* A, const figaro_ta
                                           void* stream) {
   if (!sigma) return FIGARO_ERR_INVALID_ARG;
   Call c;
+  StageJoin join_at_exit{c};
   figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
   if (st != FIGARO_OK) return st;
   if (R_out && ldr < c.p.n) return FIGARO_ERR_INVALID_ARG;
@@ -812,6 +903,7 @@ figaro_status figaro_join_svd(const figaro_table* A, const figaro_table* B, cons
   if (!sigma || !V) return FIGARO_ERR_INVALID_ARG;
   if (opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT)) return FIGARO_ERR_UNSUPPORTED;
   Call c;
+  StageJoin join_at_exit{c};
   figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
   if (st != FIGARO_OK) return st;
   if (ldv < c.p.n || (R_out && ldr < c.p.n)) return FIGARO_ERR_INVALID_ARG;
@@ -828,6 +920,7 @@ figaro_status figaro_join_least_squares(const figaro_table* A, const figaro_tabl
                                         double* beta, double* residual, void* ws, size_t ws_bytes, void* stream) {
   if (!beta || !residual) return FIGARO_ERR_INVALID_ARG;
   Call c;
+  StageJoin join_at_exit{c};
   figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
   if (st != FIGARO_OK) return st;
   if (c.p.n < 2) return FIGARO_ERR_INVALID_ARG;  // at least one feature besides the label
@@ -908,6 +1001,7 @@ figaro_status figaro_batch_join(int32_t count, const figaro_table* A, const figa
     figaro_options oi = resolve(opt);
     oi.phase_events = nullptr;
     Call c;
+    StageJoin join_at_exit{c};
     st = prepare(c, &A[i], &B[i], &oi, base, one, stream);
     if (st != FIGARO_OK) return st;
     base += one;
