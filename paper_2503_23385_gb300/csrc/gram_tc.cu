@@ -145,13 +145,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// L2 prefetch of the same box (no shared memory, no completion to track).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(map), "r"(x), "r"(y) : "memory");
+}
+
 __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
-// Round to the nearest TF32 value (ties away from zero; only the low part of a
-// split is rounded, so the tie rule is immaterial to the error bound).
+// Round to the nearest TF32 value, ties away from zero (the tie rule does not
+// enter the error bounds of the splits).
 __device__ __forceinline__ float tf32_rn(float v) {
   return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
@@ -555,6 +560,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 
+// One lane of the (fully active) warp: the issuer of a warp-wide MMA loop.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t e;
+  asm volatile("{ .reg .pred p; elect.sync _|p, 0xffffffff; selp.u32 %0, 1, 0, p; }" : "=r"(e));
+  return e != 0;
+}
+
 __device__ __forceinline__ void mbar_arrive_cta(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
@@ -868,33 +880,47 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Packed-operand engine: one M = N = 128 MMA per K step.
+// Packed-operand engine: one M = 128 MMA per K step.
 //
-// tcgen05.mma costs about the same issue time for every shape up to
-// M = 128 x N = 64, so the Gram is laid out to make each MMA as large as the
-// tensor core allows.  For a block of width kk in {4, 8, 16, 32}, R = 64 / kk
-// consecutive rows are packed side by side into one 64-column "wide row",
-// and the split parts form Z = [hi | lo] (128 columns, MN-major, 32-byte-atom
-// 128-byte swizzle, four 32-column panels).  D = Z^T Z then holds, for each
-// packed row position r, the blocks hi_r^T hi_r, hi_r^T lo_r, lo_r^T hi_r and
-// lo_r^T lo_r on the diagonal of its 2 x 2 block grid; their sum over r is
-// the Gram of the full FP32 values (every cross term kept, so the split adds
-// no truncation).  Pass 1 reads the packed rows straight from memory (the
-// rows of a block are contiguous).  Pass 2 forms Q = X W per tile of 128 rows
-// (M = 128, N = kout, 3 x TF32 in tensor memory) and the workers write Q's
-// split parts into the packed layout of the Gram of Q.
+// A kind::tf32 MMA with M = 128 and K = 8 takes about 41, 49, 65 and 129
+// tensor-pipe cycles at N = 32, 64, 128 and 256 (measured on this GPU), so
+// the Gram is laid out to make each MMA as large as the tensor core allows.
+// For a block of width kk in {4, 8, 16, 32}, R = 64 / kk consecutive rows are
+// packed side by side into one 64-column "wide row", and the split parts
+// form Z = [hi | lo] (128 columns, MN-major, 32-byte-atom 128-byte swizzle,
+// four 32-column panels).
+//
+// Pass 1 reads the packed rows straight from memory (the rows of a block are
+// contiguous; hi = the raw value, which the tensor core truncates to TF32)
+// and accumulates D = Z^T Z: for each packed row position r the blocks
+// hi_r^T hi_r, hi_r^T lo_r, lo_r^T hi_r and lo_r^T lo_r on the diagonal of
+// its 2 x 2 block grid, whose sum over r is the Gram of the full FP32 values.
+//
+// Pass 2 forms Q = X W per tile of 128 rows in tensor memory with two MMAs
+// per K step, X_hi [W_hi | W_lo] (N = 2 np) and X_lo W_hi (N = np), and Q is
+// their sum X_hi W_hi + (X_hi W_lo + X_lo W_hi).  Q is split with hi = Q
+// rounded to the nearest TF32 value and lo = Q - hi rounded to TF32, and the
+// Gram MMA is D = Z^T H (N = 64: B is the hi half of Z), which holds
+// H_r^T H_r (hi lanes) and L_r^T H_r (lo lanes); the symmetrised sum
+// H^T H + L^T H + H^T L takes the lo lanes twice.  The dropped L^T L term is
+// below 2^-22 of |Q|^2 per product (2^-11 per lo part), under the FP32
+// rounding of the formation itself.
 //
 // Roles: a TMA producer warp, an MMA warp and three worker groups with loops
 // of their own that meet only at mbarriers: split (the lo parts of each X
 // tile; 2 warps in pass 2, 6 in pass 1), Q formation (pass 2: D1 from tensor
 // memory into the packed operand; 4 warps, one per TMEM lane quarter) and
-// drain (4 warps).  The MMA thread issues formations and Grams as their
-// inputs become ready.  Tensor memory: pass 1 two sets x two accumulators of
-// 128 columns; pass 2 two formation buffers of 32 columns and two
-// accumulator sets of 128.  Each drain thread adds its TMEM lane (one row of
-// D) into float-float sums of the kk-wide row piece that belongs to its
-// packed row position; the pieces are added in a fixed order at the end and
-// each CTA's partial is written as float-float pairs.
+// drain (4 warps).  The MMA warp runs its loop warp-wide (warp votes keep the
+// loop state and the descriptors uniform) and one elected lane issues the
+// formations and Grams as their inputs become ready.  The producer prefetches
+// the tile that will next reuse a stage into L2 when it loads the stage.
+// Tensor memory: pass 1 two sets x two accumulators of 128 columns; pass 2
+// two formation buffers of 2 np columns, two of np and two accumulators of
+// 64.  Each drain thread adds its TMEM lane (one row of D) into float-float
+// sums of the kk-wide row piece that belongs to its packed row position; the
+// pieces are added in a fixed order at the end and each CTA's partial is
+// written as float-float pairs.  Each pass is its own kernel (template P2),
+// so that a kernel carries only the loops it runs.
 constexpr int kPackStages = 3;  // pass-1 X stages (64 KB each)
 constexpr int kP2Stages = 4;    // pass-2 X stages (32 KB each)
 constexpr int kGroupWarps = 4;  // warps of the drain and Q-formation groups (one per TMEM lane quarter)
@@ -958,14 +984,61 @@ __device__ __forceinline__ int z_offset(int w, int col, int wr) {
   return p * wr * 128 + w * 128 + ((((c >> 3) ^ (w & 3))) << 5) + ((c & 7) << 2);
 }
 
-template <int KK>
+// Pass-2 split of one landed X tile by the split warps (thread st: rows st,
+// st + 32 kSplitWarps, ...): the CPR 16-byte chunks of each row that the
+// formation reads (chunk c sits at c ^ (r mod 8) of the 128-byte swizzle;
+// columns past k were zero-filled by the copy).  All loads are issued before
+// any store; rows at or past `rows` are cleared in both parts.
+template <int CPR>
+__device__ __forceinline__ void split_rows_p2(float4* X4, float4* L4, int st, bool full, int64_t row0, int64_t rows) {
+  constexpr int kRows = kTileRows / (32 * kSplitWarps);
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 v[kRows][CPR];
+#pragma unroll
+  for (int t = 0; t < kRows; ++t) {
+    const int r = st + t * 32 * kSplitWarps;
+#pragma unroll
+    for (int c = 0; c < CPR; ++c) v[t][c] = X4[r * 8 + (c ^ (r & 7))];
+  }
+  if (full) {
+#pragma unroll
+    for (int t = 0; t < kRows; ++t) {
+      const int r = st + t * 32 * kSplitWarps;
+#pragma unroll
+      for (int c = 0; c < CPR; ++c) {
+        const float4 x = v[t][c];
+        L4[r * 8 + (c ^ (r & 7))] = make_float4(tf32_rn(x.x - tf32_hi(x.x)), tf32_rn(x.y - tf32_hi(x.y)),
+                                                tf32_rn(x.z - tf32_hi(x.z)), tf32_rn(x.w - tf32_hi(x.w)));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < kRows; ++t) {
+      const int r = st + t * 32 * kSplitWarps;
+      const bool clear = row0 + r >= rows;
+#pragma unroll
+      for (int c = 0; c < CPR; ++c) {
+        const int e = r * 8 + (c ^ (r & 7));
+        const float4 x = v[t][c];
+        if (clear) X4[e] = zero4;
+        L4[e] = clear ? zero4
+                      : make_float4(tf32_rn(x.x - tf32_hi(x.x)), tf32_rn(x.y - tf32_hi(x.y)),
+                                    tf32_rn(x.z - tf32_hi(x.z)), tf32_rn(x.w - tf32_hi(x.w)));
+      }
+    }
+  }
+}
+
+// P2 selects the pass at compile time (a.W != nullptr in pass 2), so that each
+// kernel holds only its own pass's loops.
+template <int KK, bool P2>
 __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const PackArgs& a, int cta, int G) {
   constexpr int RR = 64 / KK;  // rows per packed row
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ PipeSmem S;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool pass2 = a.W != nullptr;
+  constexpr bool pass2 = P2;
   const int64_t rows = a.rows_dev ? *a.rows_dev : a.rows;
   // pass 1: tiles of 128 packed rows (128 R rows); pass 2: tiles of 128 rows
   const int64_t tile_rows = pass2 ? kTileRows : static_cast<int64_t>(kTileRows) * a.rr;
@@ -1003,23 +1076,20 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (pass2 && warp >= 2) {  // W^T (np rows x k, K-major 128-byte swizzle): hi and lo parts, zero padded
+  if (pass2 && warp >= 2) {
+    // [W_hi; W_lo]^T: 2 np rows x k, K-major 128-byte swizzle, zero padded;
+    // the W_lo rows start at row np (a multiple of 16: whole 8-row atoms)
     constexpr int kStagers = kPackThreads - 64;
     const int wt = tid - 64;
-    float* wh = reinterpret_cast<float*>(base + kP2Wh);
-    float* wl = reinterpret_cast<float*>(base + kP2Wl);
-    for (int e = wt; e < 32 * 32; e += kStagers) {
-      wh[e] = 0.f;
-      wl[e] = 0.f;
-    }
+    unsigned char* wb = base + kP2Wh;
+    for (int e = wt; e < 2 * 32 * 32; e += kStagers) reinterpret_cast<float*>(wb)[e] = 0.f;
     asm volatile("bar.sync 1, %0;" ::"n"(kStagers) : "memory");
     for (int e = wt; e < a.kout * a.k; e += kStagers) {
       const int nn = e / a.k, kc = e - nn * a.k;
       const float v = (kc <= nn) ? a.W[static_cast<int64_t>(kc) * a.wld + nn] : 0.f;  // W upper triangular
-      const int off = sw128_offset(nn, kc, 32 * 128);
       const float h = tf32_hi(v);
-      *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wh) + off) = h;
-      *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wl) + off) = tf32_rn(v - h);
+      *reinterpret_cast<float*>(wb + sw128_offset(nn, kc, 32 * 128)) = h;
+      *reinterpret_cast<float*>(wb + sw128_offset(a.np + nn, kc, 32 * 128)) = tf32_rn(v - h);
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1027,9 +1097,12 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = S.tmem_base;
-  auto d1_addr = [&](int b) { return tmem + static_cast<uint32_t>(b * 32); };
+  // pass 2: D1[b] (2 np <= 64 columns: X_hi W_hi | X_hi W_lo), D1s[b] (np <= 32:
+  // X_lo W_hi) and the Gram accumulators (64 columns each)
+  auto d1_addr = [&](int b) { return tmem + static_cast<uint32_t>(b * 64); };
+  auto d1s_addr = [&](int b) { return tmem + 128u + static_cast<uint32_t>(b * 32); };
   auto acc_addr = [&](int b, int q) {
-    return pass2 ? tmem + 64u + static_cast<uint32_t>(b * 128) : tmem + static_cast<uint32_t>(b * 256 + q * 128);
+    return pass2 ? tmem + 192u + static_cast<uint32_t>(b * 64) : tmem + static_cast<uint32_t>(b * 256 + q * 128);
   };
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   // The tensor core reads an FP32 operand as TF32 by ignoring its low 13
@@ -1038,6 +1111,56 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
   auto lo_of = [](float4 v) {
     return make_float4(tf32_rn(v.x - tf32_hi(v.x)), tf32_rn(v.y - tf32_hi(v.y)), tf32_rn(v.z - tf32_hi(v.z)),
                        tf32_rn(v.w - tf32_hi(v.w)));
+  };
+  // Q = X W (TMEM lane qt = row of the tile) into the packed Gram operand: row
+  // qt is packed row qt / R, position qt mod R (columns (qt mod R) KK + c).
+  // A warp forms the rows of its lane quarter: the row of Q into registers,
+  // X_hi W_hi + (X_hi W_lo + X_lo W_hi), D1 released as soon as it is read,
+  // then the split parts into the Z buffer.
+  auto q_form = [&](int i, int quarter) -> bool {
+    constexpr int QH = KK;
+    constexpr int cbase = 0;
+    const int b = i & 1;
+    const int qt = quarter * 32 + lane;
+    const int w = qt / RR, c0 = (qt % RR) * KK + cbase;
+    if (!warp_wait(S, &S.d1_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t lanes = (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(cbase);
+    constexpr int QC = QH < 16 ? QH : 16;  // columns per TMEM read
+    float v[QH];
+#pragma unroll
+    for (int cc = 0; cc < QH; cc += QC) {
+      uint32_t qb[QC], qs[QC], qx[QC];
+      tmem_ld_nowait<QC>(d1_addr(b) + lanes + static_cast<uint32_t>(cc), qb);
+      tmem_ld_nowait<QC>(d1_addr(b) + lanes + static_cast<uint32_t>(a.np + cc), qs);
+      tmem_ld_nowait<QC>(d1s_addr(b) + lanes + static_cast<uint32_t>(cc), qx);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int e = 0; e < QC; ++e)
+        v[cc + e] = __fadd_rn(__uint_as_float(qb[e]), __fadd_rn(__uint_as_float(qs[e]), __uint_as_float(qx[e])));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) mbar_arrive_cta(&S.d1_empty[b]);
+    if (i >= 2 && !warp_wait(S, &S.q_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
+      return false;
+    const bool live = tile_index(i) * kTileRows + qt < rows;
+    unsigned char* zq = base + kP2Zq + b * kP2ZqBytes;
+#pragma unroll
+    for (int g = 0; g < QH / 4; ++g) {
+      float4 h = zero4, l = zero4;
+      if (live) {
+        h = make_float4(tf32_rn(v[4 * g]), tf32_rn(v[4 * g + 1]), tf32_rn(v[4 * g + 2]), tf32_rn(v[4 * g + 3]));
+        l = make_float4(tf32_rn(v[4 * g] - h.x), tf32_rn(v[4 * g + 1] - h.y), tf32_rn(v[4 * g + 2] - h.z),
+                        tf32_rn(v[4 * g + 3] - h.w));
+      }
+      *reinterpret_cast<float4*>(zq + z_offset(w, c0 + 4 * g, wrq)) = h;
+      *reinterpret_cast<float4*>(zq + z_offset(w, 64 + c0 + 4 * g, wrq)) = l;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) mbar_arrive_cta(&S.q_full[b]);
+    return true;
   };
 
   if (warp == 0) {
@@ -1060,6 +1183,13 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
           tma_load_2d(dst, tmx, 0, y, &S.tma_full[s]);
           tma_load_2d(dst + kPanelBytes, tmx, 32, y, &S.tma_full[s]);
         }
+        // the tile that will next reuse this stage goes to L2 now, so that its
+        // copy, issued when the stage frees, does not wait on HBM
+        if (i + nst < n) {
+          const int yp = static_cast<int>(tile_index(i + nst) * kTileRows);
+          tma_prefetch_2d(tmx, 0, yp);
+          if (!pass2) tma_prefetch_2d(tmx, 32, yp);
+        }
         issued = i + 1;
       }
       for (int i = issued > nst ? issued - nst : 0; i < issued; ++i)
@@ -1068,11 +1198,9 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issue
-    if (lane == 0) {
-      const uint32_t idg = idesc_tf32(128, 128, 1);
-      const uint32_t idf = idesc_tf32(128, a.np);
-      const uint32_t wh = smem_u32(base + kP2Wh), wl = smem_u32(base + kP2Wl);
-      if (!pass2) {
+    const uint32_t idg = idesc_tf32(128, 128, 1);
+    if (!pass2) {
+      if (lane == 0) {
         for (int i = 0; i < n; ++i) {
           const int s = i % nst, b = i & 1;
           if (!pipe_wait(S, &S.op_full[s], static_cast<uint32_t>((i / nst) & 1), a.spin_limit, a.status)) break;
@@ -1088,81 +1216,96 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
           mma_commit(&S.stage_empty[s]);
           mma_commit(&S.acc_full[b]);
         }
-      } else {
-        // Formations F(j) (D1[j & 1] = X_j W, 3 x TF32, the large term last) and
-        // Grams G(i) are issued as their inputs become ready: F one or two
-        // tiles ahead of G as the formation buffers allow.  Every barrier
-        // tested here is at most one phase behind the phase tested (each test
-        // follows the issue that consumed the previous phase), so the parity
-        // tests are exact.  The loop gives up after spin_limit idle polls.
-        // The shared-memory descriptors are computed once: their address
-        // field holds bytes / 16, so the stages, the Z buffers and the K steps
-        // (32 bytes of a K-major row, 1,024 bytes of 8 packed rows) are
-        // constants added to a base descriptor, and the issue of a formation
-        // or a Gram is a straight run of MMAs.
-        const uint64_t dx0 = desc_kmajor_sw128(smem_u32(base));
-        const uint64_t dwh = desc_kmajor_sw128(wh), dwl = desc_kmajor_sw128(wl);
-        const uint64_t dz0 = desc_mn_sw128_32b(smem_u32(base + kP2Zq), static_cast<uint32_t>(wrq * 128));
-        const int fsteps = a.ksteps_f, gsteps = wrq / 8;
-        int nf = 0, ng = 0;
-        int64_t idle = 0;
-        while (ng < n) {
-          bool progress = false;
-          if (nf < n) {
-            const int s = nf % nst, bd = nf & 1;
-            if (mbar_test(&S.op_full[s], static_cast<uint32_t>((nf / nst) & 1)) &&
-                (nf < 2 || mbar_test(&S.d1_empty[bd], static_cast<uint32_t>(((nf / 2) - 1) & 1)))) {
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint64_t dah = dx0 + static_cast<uint64_t>((s * stage_bytes) >> 4);
-              const uint64_t dal = dah + static_cast<uint64_t>(raw_bytes >> 4);
-              const uint32_t d1 = d1_addr(bd);
+        mma_commit(&S.done);
+        drain_wait(&S.done, 0u, a.spin_limit, a.status);
+      }
+    } else {
+      // Formations F(j) (D1[j & 1] = X_j W, 3 x TF32, the large term last) and
+      // Grams G(i) are issued as their inputs become ready: F one or two
+      // tiles ahead of G as the formation buffers allow.  Every barrier
+      // tested here is at most one phase behind the phase tested (each test
+      // follows the issue that consumed the previous phase), so the parity
+      // tests are exact.  The loop gives up after spin_limit idle polls.
+      // The shared-memory descriptors are computed once: their address
+      // field holds bytes / 16, so the stages, the Z buffers and the K steps
+      // (32 bytes of a K-major row, 1,024 bytes of 8 packed rows) are
+      // constants added to a base descriptor, and the issue of a formation
+      // or a Gram is a straight run of MMAs.  The whole warp runs the loop
+      // and decides by warp votes, so the loop state and the descriptors
+      // are warp-uniform; one elected lane issues every MMA and commit.
+      const bool leader = elect_one();
+      const uint32_t idf2 = idesc_tf32(128, 2 * a.np);  // X_hi [W_hi | W_lo]
+      const uint32_t idf = idesc_tf32(128, a.np);       // X_lo W_hi
+      const uint64_t dx0 = desc_kmajor_sw128(smem_u32(base));
+      const uint64_t dwh = desc_kmajor_sw128(smem_u32(base + kP2Wh));
+      const uint64_t dz0 = desc_mn_sw128_32b(smem_u32(base + kP2Zq), static_cast<uint32_t>(wrq * 128));
+      const uint32_t idq = idesc_tf32(128, 64, 1);  // D = Z^T H: B is the first 64 columns of Z
+      const int fsteps = a.ksteps_f, gsteps = wrq / 8;
+      int nf = 0, ng = 0;
+      int64_t idle = 0;
+      while (ng < n) {
+        bool progress = false;
+        if (nf < n) {
+          const int s = nf % nst, bd = nf & 1;
+          const bool ready = mbar_test(&S.op_full[s], static_cast<uint32_t>((nf / nst) & 1)) &&
+                             (nf < 2 || mbar_test(&S.d1_empty[bd], static_cast<uint32_t>(((nf / 2) - 1) & 1)));
+          if (__all_sync(0xffffffffu, ready)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t dah = dx0 + static_cast<uint64_t>((s * stage_bytes) >> 4);
+            const uint64_t dal = dah + static_cast<uint64_t>(raw_bytes >> 4);
+            const uint32_t d1 = d1_addr(bd), d1s = d1s_addr(bd);
+            if (leader) {
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks)
                 if (ks < fsteps) {
-                  mma_tf32(d1, dal + 2u * ks, dwh + 2u * ks, idf, ks > 0 ? 1u : 0u);
-                  mma_tf32(d1, dah + 2u * ks, dwl + 2u * ks, idf, 1u);
+                  mma_tf32(d1, dah + 2u * ks, dwh + 2u * ks, idf2, ks > 0 ? 1u : 0u);
+                  mma_tf32(d1s, dal + 2u * ks, dwh + 2u * ks, idf, ks > 0 ? 1u : 0u);
                 }
-#pragma unroll
-              for (int ks = 0; ks < 4; ++ks)
-                if (ks < fsteps) mma_tf32(d1, dah + 2u * ks, dwh + 2u * ks, idf, 1u);
               mma_commit(&S.stage_empty[s]);
               mma_commit(&S.d1_full[bd]);
-              ++nf;
-              progress = true;
             }
-          }
-          if (ng < nf) {
-            const int b = ng & 1;
-            if (mbar_test(&S.q_full[b], static_cast<uint32_t>((ng / 2) & 1)) &&
-                (ng < 2 || mbar_test(&S.acc_empty[b], static_cast<uint32_t>(((ng / 2) - 1) & 1)))) {
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint64_t dz = dz0 + static_cast<uint64_t>((b * kP2ZqBytes) >> 4);
-              const uint32_t acc = acc_addr(b, 0);
-              mma_tf32(acc, dz, dz, idg, 0u);
-#pragma unroll
-              for (int ks = 1; ks < 8; ++ks)
-                if (ks < gsteps) mma_tf32(acc, dz + 64u * ks, dz + 64u * ks, idg, 1u);
-              mma_commit(&S.q_empty[b]);
-              mma_commit(&S.acc_full[b]);
-              ++ng;
-              progress = true;
-            }
-          }
-          if (progress) {
-            idle = 0;
-          } else if (*reinterpret_cast<volatile int*>(&S.abort)) {
-            break;
-          } else if (++idle > a.spin_limit) {
-            set_status(a.status, kStatusTimeout);
-            *reinterpret_cast<volatile int*>(&S.abort) = 1;
-            break;
-          } else if (idle > 8) {
-            __nanosleep(32);  // leave the issue slots to the worker warps while nothing is ready
+            __syncwarp();
+            ++nf;
+            progress = true;
           }
         }
+        if (ng < nf) {
+          const int b = ng & 1;
+          const bool ready = mbar_test(&S.q_full[b], static_cast<uint32_t>((ng / 2) & 1)) &&
+                             (ng < 2 || mbar_test(&S.acc_empty[b], static_cast<uint32_t>(((ng / 2) - 1) & 1)));
+          if (__all_sync(0xffffffffu, ready)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t dz = dz0 + static_cast<uint64_t>((b * kP2ZqBytes) >> 4);
+            const uint32_t acc = acc_addr(b, 0);
+            if (leader) {
+              mma_tf32(acc, dz, dz, idq, 0u);
+#pragma unroll
+              for (int ks = 1; ks < 8; ++ks)
+                if (ks < gsteps) mma_tf32(acc, dz + 64u * ks, dz + 64u * ks, idq, 1u);
+              mma_commit(&S.q_empty[b]);
+              mma_commit(&S.acc_full[b]);
+            }
+            __syncwarp();
+            ++ng;
+            progress = true;
+          }
+        }
+        if (progress) {
+          idle = 0;
+        } else if (__any_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&S.abort) != 0)) {
+          break;
+        } else if (++idle > a.spin_limit) {
+          if (leader) set_status(a.status, kStatusTimeout);
+          *reinterpret_cast<volatile int*>(&S.abort) = 1;
+          break;
+        } else if (idle > 8) {
+          __nanosleep(32);  // leave the issue slots to the worker warps while nothing is ready
+        }
       }
-      mma_commit(&S.done);
-      drain_wait(&S.done, 0u, a.spin_limit, a.status);
+      if (leader) {  // the same lane that issued the MMAs: its commit tracks all of them
+        mma_commit(&S.done);
+        drain_wait(&S.done, 0u, a.spin_limit, a.status);
+      }
     }
   } else if (warp >= split_warp0) {
     // ------------------------------------------------------------ split
@@ -1203,19 +1346,13 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         // rows r = st, st + nth, ...: the 16-byte chunks c < 2 ceil(k / 8) the
         // formation reads (chunk c sits at c ^ (r mod 8) of the 128-byte
         // swizzle; columns past k are zero-filled by the copy)
-        const int cpr = 2 * a.ksteps_f;
-        for (int r = st; r < kTileRows; r += nth) {
-          const bool clear = !full && t0 * kTileRows + r >= rows;
-          float4 v[8];
-#pragma unroll
-          for (int c = 0; c < 8; ++c) v[c] = c < cpr ? X4[r * 8 + (c ^ (r & 7))] : zero4;
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (c < cpr) {
-              const int e = r * 8 + (c ^ (r & 7));
-              if (clear) X4[e] = zero4;
-              L4[e] = clear ? zero4 : lo_of(v[c]);
-            }
+        // (the chunk count is a compile-time constant of each case: straight-line code)
+        const int64_t row0 = t0 * kTileRows;
+        switch (a.ksteps_f) {
+          case 1: split_rows_p2<2>(X4, L4, st, full, row0, rows); break;
+          case 2: split_rows_p2<4>(X4, L4, st, full, row0, rows); break;
+          case 3: split_rows_p2<6>(X4, L4, st, full, row0, rows); break;
+          default: split_rows_p2<8>(X4, L4, st, full, row0, rows); break;
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1224,39 +1361,8 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
     }
   } else if (warp >= 2 + kGroupWarps) {
     // ------------------------------------------------------------ Q formation (pass 2)
-    // Q = X W (TMEM lane qt = row of the tile) into the packed Gram operand:
-    // row qt is packed row qt / R, position qt mod R (columns (qt mod R) KK + c)
-    const int quarter = warp & 3;
-    const int qt = quarter * 32 + lane;
-    const int w = qt / RR, c0 = (qt % RR) * KK;
-    for (int i = 0; i < n; ++i) {
-      const int b = i & 1;
-      if (!warp_wait(S, &S.d1_full[b], static_cast<uint32_t>((i / 2) & 1), a.spin_limit, a.status)) break;
-      if (i >= 2 && !warp_wait(S, &S.q_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
-        break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t q[KK];
-      tmem_ld_nowait<KK>(d1_addr(b) + (static_cast<uint32_t>(quarter * 32) << 16), q);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const bool live = tile_index(i) * kTileRows + qt < rows;
-      unsigned char* zq = base + kP2Zq + b * kP2ZqBytes;
-#pragma unroll
-      for (int g = 0; g < KK / 4; ++g) {
-        float4 h = zero4;
-        if (live)
-          h = make_float4(__uint_as_float(q[4 * g]), __uint_as_float(q[4 * g + 1]), __uint_as_float(q[4 * g + 2]),
-                          __uint_as_float(q[4 * g + 3]));
-        *reinterpret_cast<float4*>(zq + z_offset(w, c0 + 4 * g, wrq)) = h;
-        *reinterpret_cast<float4*>(zq + z_offset(w, 64 + c0 + 4 * g, wrq)) = lo_of(h);
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive_cta(&S.d1_empty[b]);
-        mbar_arrive_cta(&S.q_full[b]);
-      }
-    }
+    for (int i = 0; i < n; ++i)
+      if (!q_form(i, warp & 3)) break;
   } else {
     // ------------------------------------------------------------ drain
     // This thread's TMEM lane is row i = 32 quarter + lane of D; within its
@@ -1299,18 +1405,24 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
           for (int hh = 0; hh < 2; ++hh) {
             uint32_t rh[16], rl[16];
             tmem_ld_nowait<16>(acc + static_cast<uint32_t>(hh * 16), rh);
-            tmem_ld_nowait<16>(acc + 64u + static_cast<uint32_t>(hh * 16), rl);
+            if (!pass2) tmem_ld_nowait<16>(acc + 64u + static_cast<uint32_t>(hh * 16), rl);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (pass2) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              grp[hh * 16 + j] = __fadd_rn(grp[hh * 16 + j], __fadd_rn(__uint_as_float(rh[j]), __uint_as_float(rl[j])));
+              for (int j = 0; j < 16; ++j) grp[hh * 16 + j] = __fadd_rn(grp[hh * 16 + j], __uint_as_float(rh[j]));
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                grp[hh * 16 + j] =
+                    __fadd_rn(grp[hh * 16 + j], __fadd_rn(__uint_as_float(rh[j]), __uint_as_float(rl[j])));
+            }
           }
         } else {
           uint32_t rh[C][KK], rl[C][KK];
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             tmem_ld_nowait<KK>(acc + static_cast<uint32_t>(c * KK), rh[c]);
-            tmem_ld_nowait<KK>(acc + 64u + static_cast<uint32_t>(c * KK), rl[c]);
+            if (!pass2) tmem_ld_nowait<KK>(acc + 64u + static_cast<uint32_t>(c * KK), rl[c]);
           }
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
@@ -1318,7 +1430,8 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
             if (c == mine) {
 #pragma unroll
               for (int j = 0; j < KK; ++j)
-                grp[j] = __fadd_rn(grp[j], __fadd_rn(__uint_as_float(rh[c][j]), __uint_as_float(rl[c][j])));
+                grp[j] = __fadd_rn(grp[j], pass2 ? __uint_as_float(rh[c][j])
+                                                 : __fadd_rn(__uint_as_float(rh[c][j]), __uint_as_float(rl[c][j])));
             }
         }
       }
@@ -1340,10 +1453,14 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
     for (int j = 0; j < KK; ++j) pieces[i128 * 32 + j] = make_float2(fh[j], fl[j]);
     asm volatile("bar.sync 2, %0;" ::"n"(32 * kGroupWarps) : "memory");
     double* part = a.part + static_cast<int64_t>(cta) * a.kout * a.kout;
+    // pass 2 holds H^T H (hi lanes) and L^T H (lo lanes): the symmetrised sum
+    // H^T H + L^T H + H^T L takes the lo lanes twice (exact scaling)
+    const float lo_w = pass2 ? 2.f : 1.f;
     auto gram_entry = [&](int ra, int cbb, float& h, float& l) {
       for (int half = 0; half < 2; ++half)
         for (int r = 0; r < RR; ++r) {
-          const float2 p = pieces[(half * 64 + r * KK + ra) * 32 + cbb];
+          float2 p = pieces[(half * 64 + r * KK + ra) * 32 + cbb];
+          if (half == 1) p = make_float2(lo_w * p.x, lo_w * p.y);
           float s_, e_;
           two_sum(h, p.x, s_, e_);
           h = s_;
@@ -1369,11 +1486,11 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
   }
 }
 
-template <int KK>
+template <int KK, bool P2>
 __global__ void __launch_bounds__(kPackThreads, 1)
     gram_pack_kernel(const __grid_constant__ CUtensorMap tmx, PackArgs a) {
   pdl_enter();
-  gram_pack_body<KK>(&tmx, a, blockIdx.x, gridDim.x);
+  gram_pack_body<KK, P2>(&tmx, a, blockIdx.x, gridDim.x);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() { return tensor_map_encoder(); }
@@ -1502,12 +1619,12 @@ __device__ __forceinline__ int tc_batch_job(const TcBatch& B, int cta) {
   return lo;
 }
 
-template <int KK>
+template <int KK, bool P2>
 __global__ void __launch_bounds__(kPackThreads, 1) gram_pack_batched(const __grid_constant__ TcBatch B) {
   pdl_enter();
   const int j = tc_batch_job(B, blockIdx.x);
   const PackArgs a = pack_args_of(B.plans[B.inst[j]], B.pass, B.blk[j]);
-  gram_pack_body<KK>(&B.maps[j], a, blockIdx.x - B.first[j], B.first[j + 1] - B.first[j]);
+  gram_pack_body<KK, P2>(&B.maps[j], a, blockIdx.x - B.first[j], B.first[j + 1] - B.first[j]);
 }
 
 template <int NP>
@@ -1577,13 +1694,15 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    static int granted[64][4] = {};
+    static int granted[64][8] = {};
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
-    const int which = kk == 4 ? 0 : (kk == 8 ? 1 : (kk == 16 ? 2 : 3));
-    void (*kern)(const CUtensorMap, PackArgs) =
-        which == 0 ? gram_pack_kernel<4> : (which == 1 ? gram_pack_kernel<8> : (which == 2 ? gram_pack_kernel<16> : gram_pack_kernel<32>));
+    const int which = (kk == 4 ? 0 : (kk == 8 ? 1 : (kk == 16 ? 2 : 3))) + (W ? 4 : 0);
+    void (*const kerns[8])(const CUtensorMap, PackArgs) = {
+        gram_pack_kernel<4, false>, gram_pack_kernel<8, false>, gram_pack_kernel<16, false>, gram_pack_kernel<32, false>,
+        gram_pack_kernel<4, true>,  gram_pack_kernel<8, true>,  gram_pack_kernel<16, true>,  gram_pack_kernel<32, true>};
+    void (*kern)(const CUtensorMap, PackArgs) = kerns[which];
     if (dev < 0 || dev >= 64 || !granted[dev][which]) {
       err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPackSmemBytes);
       if (err != cudaSuccess) return err;
@@ -1730,9 +1849,13 @@ cudaError_t launch_gram_tc_batch(const Plan* dev_plans, const Plan* host_plans, 
                                  const TcJob* jobs, int njobs, size_t smem, cudaStream_t s) {
   if (njobs == 0) return cudaSuccess;
   void (*kern)(const TcBatch) = nullptr;
-  if (engine == 1)
-    kern = variant == 0 ? gram_pack_batched<4>
-                        : (variant == 1 ? gram_pack_batched<8> : (variant == 2 ? gram_pack_batched<16> : gram_pack_batched<32>));
+  if (engine == 1) {
+    void (*const kerns[8])(const TcBatch) = {gram_pack_batched<4, false>, gram_pack_batched<8, false>,
+                                             gram_pack_batched<16, false>, gram_pack_batched<32, false>,
+                                             gram_pack_batched<4, true>,  gram_pack_batched<8, true>,
+                                             gram_pack_batched<16, true>, gram_pack_batched<32, true>};
+    kern = kerns[(variant & 3) + (pass == 2 ? 4 : 0)];
+  }
   else
     kern = variant == 0 ? gram_tc_batched<32> : gram_tc_batched<64>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
