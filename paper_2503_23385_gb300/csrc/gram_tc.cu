@@ -1220,8 +1220,8 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         drain_wait(&S.done, 0u, a.spin_limit, a.status);
       }
     } else {
-      // Formations F(j) (D1[j & 1] = X_j W, 3 x TF32, the large term last) and
-      // Grams G(i) are issued as their inputs become ready: F one or two
+      // Formations F(j) (D1[j & 1] = X_hi [W_hi | W_lo], D1s[j & 1] = X_lo W_hi)
+      // and Grams G(i) are issued as their inputs become ready: F one or two
       // tiles ahead of G as the formation buffers allow.  Every barrier
       // tested here is at most one phase behind the phase tested (each test
       // follows the issue that consumed the previous phase), so the parity
