@@ -1635,6 +1635,258 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_batched(const __grid_const
   gram_tc_body<NP>(&B.maps[j], a, blockIdx.x - B.first[j], B.first[j + 1] - B.first[j]);
 }
 
+
+// ---------------------------------------------------------------------------
+// Tiled Gram of wide blocks: one CTA per (block, 128 x 128 upper tile pair
+// (ti, tj), row split) accumulates C = X_i^T X_j over its rows in 3 x TF32,
+// C = H_i^T H_j + (H_i^T L_j + L_i^T H_j): the large products and the two
+// correction products go to separate tensor-memory accumulators (a truncated
+// FP32 accumulator then loses bits only relative to what it holds), both
+// double-buffered (4 x 128 of the 512 columns).  Per stage of 32 rows the
+// producer copies the tiles' 32-column panels (32-byte-atom 128-byte swizzle:
+// the MN-major operand layout), the split warps write the lo parts beside
+// them, and the MMA warp issues 4 K steps x 3 MMAs (M = N = 128, K = 8).
+// Every two stages (64 rows) the drain warps add both accumulators into FP32
+// registers; every 8 drains (512 rows) and at the end each drain thread adds
+// its 64 entries of the tile into the job's FP64 partial (its own row, so no
+// two threads touch one entry).
+constexpr int kWtRows = 32;                        // rows per stage
+constexpr int kWtStages = 3;
+constexpr int kWtPanel = kWtRows * 128;            // 32 rows x 32 columns (4 KB)
+constexpr int kWtTileBytes = 4 * kWtPanel;         // one 128-column tile of a stage
+constexpr int kWtStage = 4 * kWtTileBytes;         // hi of tiles i, j; lo of tiles i, j
+constexpr int kWtSmem = kWtStages * kWtStage + 1024;
+constexpr int kWtDrainWarps = 8;                   // two per TMEM lane quarter, 64 columns each
+constexpr int kWtSplitWarps = 4;
+constexpr int kWtWarps = 2 + kWtDrainWarps + kWtSplitWarps;
+constexpr int kWtThreads = 32 * kWtWarps;
+constexpr int kWtFold = 8;                         // drains per FP64 fold
+
+struct WideTcArgs {
+  CUtensorMap map[3];
+  WideTcBlock b[3];
+  int job0[3];
+  double* part;
+  int32_t* status;
+  int64_t spin_limit;
+};
+
+__global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __grid_constant__ WideTcArgs A) {
+  pdl_enter();
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ PipeSmem S;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int bi = 0;
+  while (bi < 2 && static_cast<int>(blockIdx.x) >= A.job0[bi] + A.b[bi].njobs) ++bi;
+  const WideTcBlock& B = A.b[bi];
+  const CUtensorMap* map = &A.map[bi];
+  const int job = static_cast<int>(blockIdx.x) - A.job0[bi];
+  const int tile = job / B.splits, split = job - tile * B.splits;
+  int ti = 0, len = B.tiles, t = tile;  // upper tile pair (ti <= tj), row-major over the upper triangle
+  while (t >= len) {
+    t -= len;
+    ++ti;
+    --len;
+  }
+  const int tj = ti + t;
+  const bool two = ti != tj;
+  const int64_t rows_all = B.rows_dev ? (*B.rows_dev < B.rows ? *B.rows_dev : B.rows) : B.rows;
+  const int64_t r0 = static_cast<int64_t>(split) * B.split_rows;
+  int64_t r1 = r0 + B.split_rows;
+  if (r1 > rows_all) r1 = rows_all;
+  const int nst = r1 > r0 ? static_cast<int>((r1 - r0 + kWtRows - 1) / kWtRows) : 0;
+  const int ngroups = (nst + 1) / 2;
+  double* part = A.part + B.pbase + static_cast<int64_t>(job) * kWideTcTile * kWideTcTile;
+
+  if (tid == 0) {
+    for (int q = 0; q < kWtStages; ++q) {
+      mbar_init(&S.tma_full[q], 1);
+      mbar_init(&S.stage_empty[q], 1);
+      mbar_init(&S.op_full[q], kWtSplitWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.acc_full[b], 1);
+      mbar_init(&S.acc_empty[b], kWtDrainWarps);
+    }
+    mbar_init(&S.done, 1);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem_base;
+  const int tile_bytes = (two ? 2 : 1) * kWtTileBytes;  // hi bytes copied per stage
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int s = 0; s < nst; ++s) {
+        const int q = s % kWtStages;
+        if (s >= kWtStages && !pipe_wait(S, &S.stage_empty[q], static_cast<uint32_t>(((s / kWtStages) - 1) & 1),
+                                         A.spin_limit, A.status))
+          break;
+        unsigned char* dst = base + q * kWtStage;
+        const int y = static_cast<int>(r0 + static_cast<int64_t>(s) * kWtRows);
+        expect_tx(&S.tma_full[q], static_cast<uint32_t>(tile_bytes));
+        for (int p = 0; p < 4; ++p) tma_load_2d(dst + p * kWtPanel, map, ti * kWideTcTile + 32 * p, y, &S.tma_full[q]);
+        if (two)
+          for (int p = 0; p < 4; ++p)
+            tma_load_2d(dst + kWtTileBytes + p * kWtPanel, map, tj * kWideTcTile + 32 * p, y, &S.tma_full[q]);
+        issued = s + 1;
+      }
+      for (int s = issued > kWtStages ? issued - kWtStages : 0; s < issued; ++s)
+        drain_wait(&S.tma_full[s % kWtStages], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status);
+    }
+  } else if (warp >= 2 + kWtDrainWarps) {
+    // ------------------------------------------------------------ split
+    // lo = TF32(x - hi) beside each copied panel; rows at or past the job's
+    // end (the block's last rows, or rows past the device row count) are
+    // cleared in both parts
+    const int st = tid - 32 * (2 + kWtDrainWarps);
+    const int nf4 = tile_bytes / 16;
+    for (int s = 0; s < nst; ++s) {
+      const int q = s % kWtStages;
+      if (!warp_wait(S, &S.tma_full[q], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status)) break;
+      float4* X4 = reinterpret_cast<float4*>(base + q * kWtStage);
+      float4* L4 = reinterpret_cast<float4*>(base + q * kWtStage + 2 * kWtTileBytes);
+      const int64_t valid = r1 - (r0 + static_cast<int64_t>(s) * kWtRows);  // rows of this stage in the job
+      for (int e0 = st; e0 < nf4; e0 += 4 * 32 * kWtSplitWarps) {
+        float4 v[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int e = e0 + m * 32 * kWtSplitWarps;
+          v[m] = e < nf4 ? X4[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int e = e0 + m * 32 * kWtSplitWarps;
+          if (e < nf4) {
+            const int row = (e & (kWtPanel / 16 - 1)) >> 3;  // 8 float4 per 128-byte row of a panel
+            if (row >= valid) {
+              X4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+              L4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+              const float4 x = v[m];
+              L4[e] = make_float4(tf32_rn(x.x - tf32_hi(x.x)), tf32_rn(x.y - tf32_hi(x.y)), tf32_rn(x.z - tf32_hi(x.z)),
+                                  tf32_rn(x.w - tf32_hi(x.w)));
+            }
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&S.op_full[q]);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue
+    // warp-wide loop (every wait answers all lanes alike), one elected issuer
+    const bool leader = elect_one();
+    const uint32_t idg = idesc_tf32(128, 128, 1);
+    const uint64_t d0 = desc_mn_sw128_32b(smem_u32(base), kWtPanel);
+    for (int s = 0; s < nst; ++s) {
+      const int q = s % kWtStages, g = s / 2, b = g & 1;
+      if (!warp_wait(S, &S.op_full[q], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status)) break;
+      if ((s & 1) == 0 && g >= 2 &&
+          !warp_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((g / 2) - 1) & 1), A.spin_limit, A.status))
+        break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t dhi = d0 + static_cast<uint64_t>((q * kWtStage) >> 4);
+      const uint64_t dhj = two ? dhi + static_cast<uint64_t>(kWtTileBytes >> 4) : dhi;
+      const uint64_t dli = dhi + static_cast<uint64_t>((2 * kWtTileBytes) >> 4);
+      const uint64_t dlj = dhj + static_cast<uint64_t>((2 * kWtTileBytes) >> 4);
+      const uint32_t big = tmem + static_cast<uint32_t>(b * 256), small = big + 128u;
+      if (leader) {
+#pragma unroll
+        for (int k = 0; k < kWtRows / 8; ++k) {  // K steps of 8 rows (1 KB of each panel)
+          const uint32_t acc = ((s & 1) == 0 && k == 0) ? 0u : 1u;
+          const uint64_t o = static_cast<uint64_t>(64 * k);
+          mma_tf32(big, dhi + o, dhj + o, idg, acc);
+          mma_tf32(small, dhi + o, dlj + o, idg, acc);
+          mma_tf32(small, dli + o, dhj + o, idg, 1u);
+        }
+        mma_commit(&S.stage_empty[q]);
+        if ((s & 1) == 1 || s == nst - 1) mma_commit(&S.acc_full[b]);
+      }
+      __syncwarp();
+    }
+    if (leader) {  // the lane that issued the MMAs: its commit tracks all of them
+      mma_commit(&S.done);
+      drain_wait(&S.done, 0u, A.spin_limit, A.status);
+    }
+  } else {
+    // ------------------------------------------------------------ drain
+    // thread: row 32 quarter + lane of the tile, columns [64 half, 64 half + 64)
+    const int dw = warp - 2, quarter = warp & 3, half = dw >> 2;
+    const int row = quarter * 32 + lane;
+    const uint32_t lanes = (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(64 * half);
+    double* prow = part + static_cast<int64_t>(row) * kWideTcTile + 64 * half;
+    float acc[64];
+#pragma unroll
+    for (int e = 0; e < 64; ++e) acc[e] = 0.f;
+    bool first = true;
+    // the first fold stores, later ones add without reading back (each entry
+    // belongs to this thread alone, so its additions keep program order)
+    auto fold = [&]() {
+      // (each conversion sits with its store, so that one FP64 value is live at a time)
+      if (first) {
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+          asm volatile("{ .reg .f64 a, b; cvt.f64.f32 a, %1; cvt.f64.f32 b, %2; st.global.v2.f64 [%0], {a, b}; }" ::"l"(
+                           prow + 2 * e),
+                       "f"(acc[2 * e]), "f"(acc[2 * e + 1])
+                       : "memory");
+      } else {
+#pragma unroll
+        for (int e = 0; e < 64; ++e)
+          asm volatile("{ .reg .f64 a; cvt.f64.f32 a, %1; red.global.add.f64 [%0], a; }" ::"l"(prow + e), "f"(acc[e])
+                       : "memory");
+      }
+#pragma unroll
+      for (int e = 0; e < 64; ++e) acc[e] = 0.f;
+      first = false;
+    };
+    int since = 0;
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1;
+      if (!warp_wait(S, &S.acc_full[b], static_cast<uint32_t>((g / 2) & 1), A.spin_limit, A.status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t big = tmem + static_cast<uint32_t>(b * 256) + lanes, small = big + 128u;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t hb[16], hs[16];
+        tmem_ld_nowait<16>(big + static_cast<uint32_t>(16 * c), hb);
+        tmem_ld_nowait<16>(small + static_cast<uint32_t>(16 * c), hs);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          acc[16 * c + e] = __fadd_rn(acc[16 * c + e], __fadd_rn(__uint_as_float(hb[e]), __uint_as_float(hs[e])));
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&S.acc_empty[b]);
+      if (++since == kWtFold) {
+        fold();
+        since = 0;
+      }
+    }
+    if (first || since > 0) fold();  // (a job without rows writes zeros)
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 }  // namespace
 
 // The packed engine writes symmetrised upper-triangle partials; the others
@@ -1646,6 +1898,49 @@ bool gram_tc_packs(int k, int kout, bool pass2) {
 
 // The tensor-core engine handles a Gram block when TMA can address X
 // (k a multiple of 4) and the block fits the 64-column tile.
+bool wide_tc_eligible(const float* X, int64_t ld, int kout) {
+  return X != nullptr && kout >= 1 && ld >= kout && ld % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+         encoder() != nullptr;
+}
+
+cudaError_t launch_wide_gram_tc(const WideTcBlock b[3], double* part, int32_t* status, int64_t spin_limit,
+                                cudaStream_t s) {
+  WideTcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  int jobs = 0;
+  for (int i = 0; i < 3; ++i) {
+    a.b[i] = b[i];
+    a.job0[i] = jobs;
+    jobs += b[i].njobs;
+    if (b[i].njobs == 0) continue;
+    if (!wide_tc_eligible(b[i].X, b[i].ld, b[i].kout)) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(b[i].kout), static_cast<cuuint64_t>(b[i].rows > 0 ? b[i].rows : 1)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(b[i].ld) * 4};
+    cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kWtRows)};
+    cuuint32_t es[2] = {1, 1};
+    const CUresult cr = encoder()(&a.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(b[i].X), dims,
+                                  strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  if (jobs == 0) return cudaSuccess;
+  a.part = part;
+  a.status = status;
+  a.spin_limit = spin_limit;
+  static int granted[64] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64 || !granted[dev]) {
+    err = cudaFuncSetAttribute(wide_gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWtSmem);
+    if (err != cudaSuccess) return err;
+    if (dev >= 0 && dev < 64) granted[dev] = 1;
+  }
+  pdl_launch(wide_gram_tc_kernel, jobs, kWtThreads, kWtSmem, s, a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 bool gram_tc_supported(int k, int kout) { return k % 4 == 0 && k <= 64 && kout <= 64 && encoder() != nullptr; }
 
 cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,

@@ -254,8 +254,31 @@ cudaError_t launch_gram_tc_batch(const Plan* dev_plans, const Plan* host_plans, 
                                  const TcJob* jobs, int njobs, size_t smem, cudaStream_t s);
 
 // Wide path (wide.cu).
-int64_t wide_gram_jobs(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms);
+// Doubles of the wide Gram partial buffer (both engines' jobs of either pass).
+int64_t wide_gram_part_doubles(int64_t m1, int n1, int64_t m2, int n2, int num_sms, int mixed);
 cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s);
+
+// Tensor-core Gram of wide FP32 blocks (gram_tc.cu): for each block b with
+// njobs > 0, one CTA per (upper 128 x 128 tile pair, row split) writes the
+// tile's sum over its split as 128 x 128 doubles at part + pbase + job * 16384
+// (job = tile index * splits + split; a job's rows are [split * split_rows,
+// min(rows, (split + 1) * split_rows)) with rows = min(rows, *rows_dev)).
+// X is row-major FP32 (ld elements, ld and the base 16-byte aligned).
+constexpr int kWideTcTile = 128;
+struct WideTcBlock {
+  const float* X;
+  int64_t ld;
+  int kout;
+  int64_t rows;
+  const int64_t* rows_dev;
+  int tiles, splits;
+  int64_t split_rows;
+  int njobs;
+  int64_t pbase;
+};
+bool wide_tc_eligible(const float* X, int64_t ld, int kout);
+cudaError_t launch_wide_gram_tc(const WideTcBlock b[3], double* part, int32_t* status, int64_t spin_limit,
+                                cudaStream_t s);
 cudaError_t launch_wide_chol_first(const Plan& p, cudaStream_t s);
 cudaError_t launch_wide_refactor(const Plan& p, cudaStream_t s);
 cudaError_t launch_wide_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);

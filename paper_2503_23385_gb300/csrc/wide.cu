@@ -69,6 +69,15 @@ struct WideBlock {
   int job0, njobs;          // Gram jobs
   void* Q;                  // formation output (rows x kout)
   int fjob0, fjobs;         // formation jobs: row tiles x column tiles
+  // the engine that computes the block's Gram: CUDA cores (the fields above;
+  // njobs = 0 when the tensor cores do it) or the tensor-core tile Gram
+  int tc;                   // 1: tensor cores (FP32 input, mixed path)
+  int tc_tiles, tc_splits, tc_njobs;
+  int64_t tc_split_rows;
+  // partials of the block as the reduce reads them: tw x tw doubles per job,
+  // rtiles x (rtiles + 1) / 2 tiles of rsplits jobs from pbase (doubles)
+  int tw, rtiles, rsplits;
+  int64_t pbase;
 };
 
 struct WideArgs {
@@ -209,18 +218,19 @@ __global__ void __launch_bounds__(kWThreads) wide_reduce_kernel(WideArgs a) {
   double tot = 0.0;
   for (int b = 0; b < 3; ++b) {
     const WideBlock& B = a.b[b];
-    if (B.njobs == 0 || lo < B.off || hi >= B.off + B.kout) continue;
-    const int ii = lo - B.off, jj = hi - B.off;
-    const int ti = ii / kWT, tj = jj / kWT;
-    const int64_t base = static_cast<int64_t>(B.job0) + static_cast<int64_t>(upper_index(ti, tj, B.tiles)) * B.splits;
-    const double* p = a.part + base * kWT * kWT + (ii % kWT) * kWT + (jj % kWT);
+    if (B.rsplits == 0 || lo < B.off || hi >= B.off + B.kout) continue;
+    const int ii = lo - B.off, jj = hi - B.off, tw = B.tw;
+    const int ti = ii / tw, tj = jj / tw;
+    const int64_t tt = static_cast<int64_t>(tw) * tw;
+    const double* p = a.part + B.pbase + static_cast<int64_t>(upper_index(ti, tj, B.rtiles)) * B.rsplits * tt +
+                      (ii % tw) * tw + (jj % tw);
     double t0 = 0.0, t1 = 0.0;
     int s = 0;
-    for (; s + 1 < B.splits; s += 2) {
-      t0 += p[static_cast<int64_t>(s) * kWT * kWT];
-      t1 += p[static_cast<int64_t>(s + 1) * kWT * kWT];
+    for (; s + 1 < B.rsplits; s += 2) {
+      t0 += p[static_cast<int64_t>(s) * tt];
+      t1 += p[static_cast<int64_t>(s + 1) * tt];
     }
-    if (s < B.splits) t0 += p[static_cast<int64_t>(s) * kWT * kWT];
+    if (s < B.rsplits) t0 += p[static_cast<int64_t>(s) * tt];
     tot += t0 + t1;
   }
   a.G[e] = tot;
@@ -1101,15 +1111,19 @@ __global__ void __launch_bounds__(kMaxWideWidth) wide_sort_v_kernel(const double
 
 // ---------------------------------------------------------- host side ----
 
-void wide_geometry(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms, WideBlock b[3], int* gram_jobs,
-                   int* form_jobs) {
+// Jobs of each block's Gram.  tc_mask bit i: block i (0 head, 1 A tails,
+// 2 B tails) runs on the tensor cores.  CUDA-core jobs come first in the
+// partial buffer (64 x 64 doubles each), tensor-core jobs after them
+// (128 x 128 each); *part_doubles is the buffer's size.
+void wide_geometry(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms, int tc_mask, WideBlock b[3],
+                   int* gram_jobs, int* form_jobs, int* tc_jobs, int64_t* part_doubles) {
   const int n = n1 + n2;
   const int64_t rows[3] = {m1, m1, m2};
   const int ks[3] = {n, n1, n2};
   const int kouts[3] = {n, pass == 1 ? n1 : n, n2};
   const int offs[3] = {0, 0, n1};
   const int w0s[3] = {0, 0, n1};
-  int gj = 0, fj = 0;
+  int gj = 0, fj = 0, tj = 0;
   for (int i = 0; i < 3; ++i) {
     WideBlock& B = b[i];
     B = WideBlock{};
@@ -1118,26 +1132,61 @@ void wide_geometry(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms
     B.off = offs[i];
     B.w0 = w0s[i];
     B.rows = rows[i];
-    B.tiles = (B.kout + kWT - 1) / kWT;
-    B.ntiles = B.tiles * (B.tiles + 1) / 2;
-    const int64_t target = 4 * static_cast<int64_t>(num_sms) / B.ntiles;
-    int64_t splits = (B.rows + 1023) / 1024;
-    if (splits > target) splits = target;
-    if (splits < 1) splits = 1;
-    int64_t sr = (B.rows + splits - 1) / splits;
-    sr = (sr + kWRows - 1) / kWRows * kWRows;
-    if (sr < kWRows) sr = kWRows;
-    B.split_rows = sr;
-    B.splits = B.rows > 0 ? static_cast<int>((B.rows + sr - 1) / sr) : 0;
-    B.job0 = gj;
-    B.njobs = B.ntiles * B.splits;
-    gj += B.njobs;
+    B.tc = (tc_mask >> i) & 1;
+    B.tiles = (B.kout + kWT - 1) / kWT;  // (also the formation's column tiles)
+    if (!B.tc) {
+      B.ntiles = B.tiles * (B.tiles + 1) / 2;
+      const int64_t target = 4 * static_cast<int64_t>(num_sms) / B.ntiles;
+      int64_t splits = (B.rows + 1023) / 1024;
+      if (splits > target) splits = target;
+      if (splits < 1) splits = 1;
+      int64_t sr = (B.rows + splits - 1) / splits;
+      sr = (sr + kWRows - 1) / kWRows * kWRows;
+      if (sr < kWRows) sr = kWRows;
+      B.split_rows = sr;
+      B.splits = B.rows > 0 ? static_cast<int>((B.rows + sr - 1) / sr) : 0;
+      B.job0 = gj;
+      B.njobs = B.ntiles * B.splits;
+      gj += B.njobs;
+      B.tw = kWT;
+      B.rtiles = B.tiles;
+      B.rsplits = B.splits;
+    } else {
+      B.tc_tiles = (B.kout + kWideTcTile - 1) / kWideTcTile;
+      const int nt = B.tc_tiles * (B.tc_tiles + 1) / 2;
+      int64_t target = 2 * static_cast<int64_t>(num_sms) / nt;
+      if (target < 1) target = 1;
+      int64_t splits = (B.rows + 1023) / 1024;
+      if (splits > target) splits = target;
+      if (splits < 1) splits = 1;
+      int64_t sr = (B.rows + splits - 1) / splits;
+      sr = (sr + 63) / 64 * 64;  // whole drains of 64 rows
+      B.tc_split_rows = sr;
+      B.tc_splits = B.rows > 0 ? static_cast<int>((B.rows + sr - 1) / sr) : 0;
+      B.tc_njobs = nt * B.tc_splits;
+      B.tw = kWideTcTile;
+      B.rtiles = B.tc_tiles;
+      B.rsplits = B.tc_splits;
+    }
     B.fjob0 = fj;
     B.fjobs = pass == 2 && B.rows > 0 ? static_cast<int>((B.rows + kWT - 1) / kWT) * B.tiles : 0;
     fj += B.fjobs;
   }
+  int64_t pb = static_cast<int64_t>(gj) * kWT * kWT;
+  for (int i = 0; i < 3; ++i) {
+    WideBlock& B = b[i];
+    if (!B.tc) {
+      B.pbase = static_cast<int64_t>(B.job0) * kWT * kWT;
+    } else {
+      B.pbase = pb;
+      pb += static_cast<int64_t>(B.tc_njobs) * kWideTcTile * kWideTcTile;
+      tj += B.tc_njobs;
+    }
+  }
   *gram_jobs = gj;
   *form_jobs = fj;
+  *tc_jobs = tj;
+  *part_doubles = pb;
 }
 
 double wide_tol(const Plan& p) { return p.rank_tol > 0 ? p.rank_tol : (p.mixed ? 1e-5 : 1e-13); }
@@ -1185,19 +1234,39 @@ int dense_grid(const Plan& p) { return p.num_sms > 0 ? p.num_sms : 1; }
 
 }  // namespace
 
-int64_t wide_gram_jobs(int pass, int64_t m1, int n1, int64_t m2, int n2, int num_sms) {
-  WideBlock b[3];
-  int gj = 0, fj = 0;
-  wide_geometry(pass, m1, n1, m2, n2, num_sms, b, &gj, &fj);
-  return gj;
+int64_t wide_gram_part_doubles(int64_t m1, int n1, int64_t m2, int n2, int num_sms, int mixed) {
+  int64_t most = 0;
+  for (int pass = 1; pass <= 2; ++pass)
+    for (int mask = 0; mask <= (mixed ? 6 : 0); mask += 2) {  // every choice of the tail blocks' engines
+      WideBlock b[3];
+      int gj = 0, fj = 0, tj = 0;
+      int64_t pd = 0;
+      wide_geometry(pass, m1, n1, m2, n2, num_sms, mask, b, &gj, &fj, &tj, &pd);
+      if (pd > most) most = pd;
+    }
+  return most;
 }
 
 cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   WideArgs a{};
-  wide_geometry(pass, p.t[0].m, p.n1, p.t[1].m, p.n2, p.num_sms, a.b, &a.gram_jobs, &a.form_jobs);
-  const int es = p.mixed ? 4 : 8;
   const void* X[3] = {p.head, p.t[0].tail, p.t[1].tail};
   const int ld[3] = {p.n, p.n1, p.n2};
+  // the tail blocks' Grams on the tensor cores (mixed path; the head block,
+  // about one row per key group, stays on CUDA cores)
+  int tc_mask = 0;
+  if (p.mixed) {
+    const int kq[3] = {p.n, pass == 1 ? p.n1 : p.n, p.n2};
+    for (int i = 1; i < 3; ++i) {
+      const void* G = pass == 1 ? X[i] : p.wq[i];
+      const int64_t lg = pass == 1 ? ld[i] : kq[i];
+      if (wide_tc_eligible(static_cast<const float*>(G), lg, kq[i])) tc_mask |= 1 << i;
+    }
+  }
+  int tc_jobs = 0;
+  int64_t part_doubles = 0;
+  wide_geometry(pass, p.t[0].m, p.n1, p.t[1].m, p.n2, p.num_sms, tc_mask, a.b, &a.gram_jobs, &a.form_jobs, &tc_jobs,
+                &part_doubles);
+  const int es = p.mixed ? 4 : 8;
   for (int i = 0; i < 3; ++i) {
     a.b[i].X = X[i];
     a.b[i].ldx = ld[i];
@@ -1228,6 +1297,16 @@ cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     else
       pdl_launch(wide_gram_kernel<double>, a.gram_jobs, kWThreads, 0, s, a);
     count_launches(1);
+  }
+  if (tc_jobs > 0) {
+    WideTcBlock tb[3];
+    for (int i = 0; i < 3; ++i) {
+      const WideBlock& B = a.b[i];
+      tb[i] = WideTcBlock{static_cast<const float*>(B.X), B.ldx, B.kout, B.rows, B.rows_dev, B.tc_tiles, B.tc_splits,
+                          B.tc_split_rows, B.tc ? B.tc_njobs : 0, B.pbase};
+    }
+    const cudaError_t err = launch_wide_gram_tc(tb, p.wpart, &p.hdr->status, p.spin_limit, s);
+    if (err != cudaSuccess) return err;
   }
   const int64_t ne = static_cast<int64_t>(p.n) * p.n;
   pdl_launch(wide_reduce_kernel, static_cast<int>((ne + kWThreads - 1) / kWThreads), kWThreads, 0, s, a);
