@@ -105,6 +105,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def tf32_peak():
+    """Dense TF32 tensor rate for a kernel timed inside a long step: the measured
+    sustained BF16 GEMM rate times the nominal TF32 / BF16 ratio (1.1 / 2.25)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]) * 1.1 / 2.25, "measured bf16 sustained x 1.1 / 2.25"
+    except Exception:
+        return 1700.0 * 1.1 / 2.25, "fallback bf16 sustained x 1.1 / 2.25"
+
+
 def max_over_ranks(total_ms, world, device):
     """The slowest rank's time (every rank runs its own instance; the job
     ends when the slowest one does)."""
@@ -422,9 +433,20 @@ def main():
         roofline_avg = {"kernel": "gram_pack_kernel: one CholeskyQR Gram pass, average of the two passes",
                         "bound": "hbm", "achieved": g_avg, "peak": hbm, "unit": "GB/s", "frac": g_avg / hbm,
                         "bytes_per_launch": gram_bytes, "peak_source": peak_kind}
+    elif args.path == "mixed":
+        # wide joins, mixed path: pass 1's tail blocks run the tensor-core tile Gram (128 x 128 upper
+        # tiles, 3 x TF32: three tensor products per FP32 product); tensor flops of the tiles it computes
+        # over the pass's time (the head block's CUDA-core tiles and the reduce included)
+        tiles = lambda k: ((k + 127) // 128) * ((k + 127) // 128 + 1) // 2
+        flops = 3 * 2.0 * 128 * 128 * (A.m * tiles(A.n) + B.m * tiles(B.n))
+        tpeak, tsrc = tf32_peak()
+        achieved_tf = flops / (phases["gram1"] / 1e3) / 1e12
+        roofline = {"kernel": "wide_gram_tc_kernel, Gram pass 1 (tcgen05 kind::tf32, 3 x TF32)", "bound": "tensor",
+                    "achieved": achieved_tf, "peak": tpeak, "unit": "TFLOP/s", "frac": achieved_tf / tpeak,
+                    "traffic": None, "flops_per_launch": flops, "peak_source": tsrc}
     else:
-        # wide joins: pass 1 of the CUDA-core tile Gram (64 x 64 upper tiles), bound by FP32 FMA issue;
-        # flops of the tiles it computes, against 152 SMs x 128 FP32 lanes x 2 flops x the max SM clock
+        # wide joins, FP64 path: pass 1 of the CUDA-core tile Gram (64 x 64 upper tiles), bound by FP64 FMA
+        # issue is reported in fp64_path; here the FP32-ALU form of the same line
         tiles = lambda k: ((k + 63) // 64) * ((k + 63) // 64 + 1) // 2
         flops = 2.0 * 64 * 64 * (A.m * tiles(A.n) + B.m * tiles(B.n) + heads * tiles(n))
         alu_peak = 152 * 128 * 2 * 2070e6 / 1e12
