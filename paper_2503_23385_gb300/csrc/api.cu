@@ -134,6 +134,10 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
     const size_t qcols[3] = {static_cast<size_t>(n), static_cast<size_t>(n), static_cast<size_t>(n2)};
     for (int blk = 0; blk < 3; ++blk) p.wq[blk] = b.take<char>(qrows[blk] * qcols[blk] * ec);
     p.wpart = b.take<double>(static_cast<size_t>(wide_gram_part_doubles(m1, n1, m2, n2, num_sms, p.mixed)));
+    if (p.mixed) {
+      p.wt = b.take<float>(static_cast<size_t>(n) * n);
+      p.wtlo = b.take<float>(static_cast<size_t>(n) * n);
+    }
     const size_t nn = static_cast<size_t>(n) * n;
     p.Aw = b.take<char>(nn * ec);
     p.Tw = b.take<char>(nn * ec);

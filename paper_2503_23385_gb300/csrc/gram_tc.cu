@@ -1887,6 +1887,226 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __gri
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core formation of wide blocks: Q = X W[w0:w0+k, w0:w0+kout] in
+// 3 x TF32, Q = X_hi W_hi + (X_hi W_lo + X_lo W_hi).  One CTA per (block,
+// 128-column tile ct of Q, range of 128-row tiles).  A stage is one 32-column
+// K panel: the X panel (128 rows, K-major 128-byte swizzle) and its lo part,
+// and the panel of W^T (128 output columns) with its lo part, prepared once
+// per pass.  K panels that meet only zeros of the upper-triangular W
+// (features past the tile's last column) are skipped.  Every two panels the
+// drain warps add the two accumulators (large products, corrections) into
+// FP32 registers; at the end of a row tile they store its rows of Q.
+constexpr int kWfPanel = 128 * 128;   // 128 rows x 32 columns (16 KB)
+constexpr int kWfStage = 4 * kWfPanel;  // X, X lo, W^T, W^T lo
+constexpr int kWfSmem = kWtStages * kWfStage + 1024;
+
+struct WideFormArgs {
+  CUtensorMap xmap[3];
+  CUtensorMap wmap, wlmap;
+  WideFormBlock b[3];
+  int job0[3];
+  int32_t* status;
+  int64_t spin_limit;
+};
+
+// W^T and its TF32 lo parts (W upper triangular: W^T[c][f] = W[f][c] for f <= c).
+__global__ void wide_form_prep_kernel(const float* W, int n, float* WT, float* WTlo) {
+  pdl_enter();
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= static_cast<int64_t>(n) * n) return;
+  const int c = static_cast<int>(e / n), f = static_cast<int>(e - static_cast<int64_t>(c) * n);
+  const float v = f <= c ? W[static_cast<int64_t>(f) * n + c] : 0.f;
+  WT[e] = v;
+  WTlo[e] = tf32_rn(v - tf32_hi(v));
+}
+
+__global__ void __launch_bounds__(kWtThreads, 1) wide_form_tc_kernel(const __grid_constant__ WideFormArgs A) {
+  pdl_enter();
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ PipeSmem S;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int bi = 0;
+  while (bi < 2 && static_cast<int>(blockIdx.x) >= A.job0[bi] + A.b[bi].njobs) ++bi;
+  const WideFormBlock& B = A.b[bi];
+  const CUtensorMap* xmap = &A.xmap[bi];
+  const int job = static_cast<int>(blockIdx.x) - A.job0[bi];
+  const int ct = job / B.splits, split = job - ct * B.splits;
+  const int64_t rows_all = B.rows_dev ? (*B.rows_dev < B.rows ? *B.rows_dev : B.rows) : B.rows;
+  const int nrt_all = static_cast<int>((rows_all + 127) / 128);
+  const int rt0 = split * B.rt_per_split;
+  int nrt = nrt_all - rt0;
+  if (nrt > B.rt_per_split) nrt = B.rt_per_split;
+  if (nrt < 0) nrt = 0;
+  int nkp = (B.k + 31) / 32;
+  if (nkp > 4 * ct + 4) nkp = 4 * ct + 4;  // W^T rows of the tile end at column 128 ct + 127
+  const int nst = nrt * nkp;
+  const int gpr = (nkp + 1) / 2;  // drain groups per row tile
+  const int ngroups = nrt * gpr;
+
+  if (tid == 0) {
+    for (int q = 0; q < kWtStages; ++q) {
+      mbar_init(&S.tma_full[q], 1);
+      mbar_init(&S.stage_empty[q], 1);
+      mbar_init(&S.op_full[q], kWtSplitWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.acc_full[b], 1);
+      mbar_init(&S.acc_empty[b], kWtDrainWarps);
+    }
+    mbar_init(&S.done, 1);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int s = 0; s < nst; ++s) {
+        const int q = s % kWtStages, rt = rt0 + s / nkp, kp = s % nkp;
+        if (s >= kWtStages && !pipe_wait(S, &S.stage_empty[q], static_cast<uint32_t>(((s / kWtStages) - 1) & 1),
+                                         A.spin_limit, A.status))
+          break;
+        unsigned char* dst = base + q * kWfStage;
+        expect_tx(&S.tma_full[q], static_cast<uint32_t>(3 * kWfPanel));
+        tma_load_2d(dst, xmap, 32 * kp, 128 * rt, &S.tma_full[q]);
+        tma_load_2d(dst + 2 * kWfPanel, &A.wmap, B.w0 + 32 * kp, B.w0 + 128 * ct, &S.tma_full[q]);
+        tma_load_2d(dst + 3 * kWfPanel, &A.wlmap, B.w0 + 32 * kp, B.w0 + 128 * ct, &S.tma_full[q]);
+        issued = s + 1;
+      }
+      for (int s = issued > kWtStages ? issued - kWtStages : 0; s < issued; ++s)
+        drain_wait(&S.tma_full[s % kWtStages], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status);
+    }
+  } else if (warp >= 2 + kWtDrainWarps) {
+    // ------------------------------------------------------------ split (X lo; rows past the block's end cleared)
+    const int st = tid - 32 * (2 + kWtDrainWarps);
+    constexpr int NT = 32 * kWtSplitWarps;
+    for (int s = 0; s < nst; ++s) {
+      const int q = s % kWtStages, rt = rt0 + s / nkp;
+      if (!warp_wait(S, &S.tma_full[q], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status)) break;
+      float4* X4 = reinterpret_cast<float4*>(base + q * kWfStage);
+      float4* L4 = reinterpret_cast<float4*>(base + q * kWfStage + kWfPanel);
+      const int64_t valid = rows_all - static_cast<int64_t>(rt) * 128;
+      for (int e0 = st; e0 < kWfPanel / 16; e0 += 4 * NT) {
+        float4 v[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) v[m] = X4[e0 + m * NT];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int e = e0 + m * NT;
+          if ((e >> 3) >= valid) {  // row e / 8 of the panel (128-byte rows)
+            X4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            L4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+          } else {
+            const float4 x = v[m];
+            L4[e] = make_float4(tf32_rn(x.x - tf32_hi(x.x)), tf32_rn(x.y - tf32_hi(x.y)), tf32_rn(x.z - tf32_hi(x.z)),
+                                tf32_rn(x.w - tf32_hi(x.w)));
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&S.op_full[q]);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue (warp-wide loop, one elected issuer)
+    const bool leader = elect_one();
+    const uint32_t idf = idesc_tf32(128, 128);  // both operands K-major
+    const uint64_t d0 = desc_kmajor_sw128(smem_u32(base));
+    for (int s = 0; s < nst; ++s) {
+      const int q = s % kWtStages, kp = s % nkp;
+      const int g = (s / nkp) * gpr + kp / 2, b = g & 1;
+      const bool first_of_group = (kp & 1) == 0;
+      const bool last_of_group = (kp & 1) == 1 || kp == nkp - 1;
+      if (!warp_wait(S, &S.op_full[q], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status)) break;
+      if (first_of_group && g >= 2 &&
+          !warp_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((g / 2) - 1) & 1), A.spin_limit, A.status))
+        break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t dx = d0 + static_cast<uint64_t>((q * kWfStage) >> 4);
+      const uint64_t dxl = dx + static_cast<uint64_t>(kWfPanel >> 4);
+      const uint64_t dw = dx + static_cast<uint64_t>((2 * kWfPanel) >> 4);
+      const uint64_t dwl = dx + static_cast<uint64_t>((3 * kWfPanel) >> 4);
+      const uint32_t big = tmem + static_cast<uint32_t>(b * 256), small = big + 128u;
+      if (leader) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {  // K steps of 8 columns (32 bytes of each 128-byte row)
+          const uint32_t acc = (first_of_group && k == 0) ? 0u : 1u;
+          const uint64_t o = static_cast<uint64_t>(2 * k);
+          mma_tf32(big, dx + o, dw + o, idf, acc);
+          mma_tf32(small, dx + o, dwl + o, idf, acc);
+          mma_tf32(small, dxl + o, dw + o, idf, 1u);
+        }
+        mma_commit(&S.stage_empty[q]);
+        if (last_of_group) mma_commit(&S.acc_full[b]);
+      }
+      __syncwarp();
+    }
+    if (leader) {
+      mma_commit(&S.done);
+      drain_wait(&S.done, 0u, A.spin_limit, A.status);
+    }
+  } else {
+    // ------------------------------------------------------------ drain and store
+    // thread: row 32 quarter + lane of the row tile, columns [64 half, 64 half + 64) of the column tile
+    const int dw = warp - 2, quarter = warp & 3, half = dw >> 2;
+    const int row = quarter * 32 + lane;
+    const uint32_t lanes = (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(64 * half);
+    const int c0 = ct * 128 + 64 * half;
+    float acc[64];
+#pragma unroll
+    for (int e = 0; e < 64; ++e) acc[e] = 0.f;
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1;
+      if (!warp_wait(S, &S.acc_full[b], static_cast<uint32_t>((g / 2) & 1), A.spin_limit, A.status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t big = tmem + static_cast<uint32_t>(b * 256) + lanes, small = big + 128u;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t hb[16], hs[16];
+        tmem_ld_nowait<16>(big + static_cast<uint32_t>(16 * c), hb);
+        tmem_ld_nowait<16>(small + static_cast<uint32_t>(16 * c), hs);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          acc[16 * c + e] = __fadd_rn(acc[16 * c + e], __fadd_rn(__uint_as_float(hb[e]), __uint_as_float(hs[e])));
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&S.acc_empty[b]);
+      if ((g % gpr) == gpr - 1) {  // the row tile is complete: its row of Q, then a fresh sum
+        const int64_t r = static_cast<int64_t>(rt0 + g / gpr) * 128 + row;
+        if (r < rows_all) {
+          float* qrow = B.Q + r * B.kout;
+#pragma unroll
+          for (int e = 0; e < 64; e += 4)
+            if (c0 + e < B.kout)
+              *reinterpret_cast<float4*>(qrow + c0 + e) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+        }
+#pragma unroll
+        for (int e = 0; e < 64; ++e) acc[e] = 0.f;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 }  // namespace
 
 // The packed engine writes symmetrised upper-triangle partials; the others
@@ -1937,6 +2157,56 @@ cudaError_t launch_wide_gram_tc(const WideTcBlock b[3], double* part, int32_t* s
     if (dev >= 0 && dev < 64) granted[dev] = 1;
   }
   pdl_launch(wide_gram_tc_kernel, jobs, kWtThreads, kWtSmem, s, a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_form_prep(const float* W, int n, float* WT, float* WTlo, cudaStream_t s) {
+  const int64_t ne = static_cast<int64_t>(n) * n;
+  pdl_launch(wide_form_prep_kernel, static_cast<int>((ne + 255) / 256), 256, 0, s, W, n, WT, WTlo);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_form_tc(const WideFormBlock b[3], const float* WT, const float* WTlo, int n, int32_t* status,
+                                int64_t spin_limit, cudaStream_t s) {
+  WideFormArgs a;
+  std::memset(&a, 0, sizeof(a));
+  auto encode = [](CUtensorMap* m, const float* p, int64_t inner, int64_t outer, int64_t ld) {
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer > 0 ? outer : 1)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 4};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t es[2] = {1, 1};
+    return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (n % 4 != 0 || !wide_tc_eligible(WT, n, n) || !wide_tc_eligible(WTlo, n, n)) return cudaErrorInvalidValue;
+  if (!encode(&a.wmap, WT, n, n, n) || !encode(&a.wlmap, WTlo, n, n, n)) return cudaErrorInvalidValue;
+  int jobs = 0;
+  for (int i = 0; i < 3; ++i) {
+    a.b[i] = b[i];
+    a.job0[i] = jobs;
+    jobs += b[i].njobs;
+    if (b[i].njobs == 0) continue;
+    if (!wide_tc_eligible(b[i].X, b[i].ldx, b[i].k) || b[i].kout % 4 != 0 ||
+        (reinterpret_cast<uintptr_t>(b[i].Q) & 15) != 0)
+      return cudaErrorInvalidValue;
+    if (!encode(&a.xmap[i], b[i].X, b[i].k, b[i].rows, b[i].ldx)) return cudaErrorInvalidValue;
+  }
+  if (jobs == 0) return cudaSuccess;
+  a.status = status;
+  a.spin_limit = spin_limit;
+  static int granted[64] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64 || !granted[dev]) {
+    err = cudaFuncSetAttribute(wide_form_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWfSmem);
+    if (err != cudaSuccess) return err;
+    if (dev >= 0 && dev < 64) granted[dev] = 1;
+  }
+  pdl_launch(wide_form_tc_kernel, jobs, kWtThreads, kWfSmem, s, a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -114,7 +114,9 @@ struct Plan {
   // partials, and n x n work arrays of the multi-CTA dense steps
   int wide = 0;
   void* wq[3] = {nullptr, nullptr, nullptr};  // head (m1 x n), A tails (m1 x n), B tails (m2 x n2)
-  double* wpart = nullptr;                    // wide Gram partials, 64 x 64 doubles per job
+  double* wpart = nullptr;                    // wide Gram partials (64 x 64 or 128 x 128 doubles per job)
+  float* wt = nullptr;                        // mixed wide path: W^T (n x n) and its TF32 lo parts
+  float* wtlo = nullptr;
   void* Aw = nullptr;                         // n x n compute type (in-place Cholesky)
   void* Tw = nullptr;                         // n x n compute type (inverse)
   double* Xw = nullptr;                       // n x n FP64 (refined R1)
@@ -277,6 +279,23 @@ struct WideTcBlock {
   int64_t pbase;
 };
 bool wide_tc_eligible(const float* X, int64_t ld, int kout);
+
+// Tensor-core formation Q = X W[w0:w0+k, w0:w0+kout] of wide FP32 blocks
+// (gram_tc.cu), 3 x TF32: one CTA per (128-column tile of Q, range of
+// rt_per_split 128-row tiles).  WT / WTlo: W^T (n x n row-major, W upper
+// triangular) and its TF32 lo parts, from launch_wide_form_prep.
+struct WideFormBlock {
+  const float* X;
+  int64_t ldx;
+  int k, kout, w0;
+  int64_t rows;
+  const int64_t* rows_dev;
+  float* Q;  // rows x kout, leading dimension kout
+  int ctiles, splits, rt_per_split, njobs;
+};
+cudaError_t launch_wide_form_prep(const float* W, int n, float* WT, float* WTlo, cudaStream_t s);
+cudaError_t launch_wide_form_tc(const WideFormBlock b[3], const float* WT, const float* WTlo, int n, int32_t* status,
+                                int64_t spin_limit, cudaStream_t s);
 cudaError_t launch_wide_gram_tc(const WideTcBlock b[3], double* part, int32_t* status, int64_t spin_limit,
                                 cudaStream_t s);
 cudaError_t launch_wide_chol_first(const Plan& p, cudaStream_t s);

@@ -1279,12 +1279,49 @@ cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   a.G = pass == 1 ? p.G1 : p.G2;
   a.n = p.n;
   (void)es;
-  if (pass == 2 && a.form_jobs > 0) {
-    if (p.mixed)
-      pdl_launch(wide_form_kernel<float>, a.form_jobs, kWThreads, 0, s, a);
-    else
-      pdl_launch(wide_form_kernel<double>, a.form_jobs, kWThreads, 0, s, a);
-    count_launches(1);
+  // pass 2, mixed path: the tail blocks' formations on the tensor cores (W^T
+  // and its lo parts prepared once), the rest on CUDA cores
+  WideFormBlock fb[3];
+  int form_tc = 0;
+  if (pass == 2 && p.mixed && p.wt && p.n % 4 == 0) {
+    for (int i = 0; i < 3; ++i) {
+      WideBlock& B = a.b[i];
+      fb[i] = WideFormBlock{};
+      if (i == 0 || B.rows <= 0 || B.kout % 4 != 0 || !wide_tc_eligible(static_cast<const float*>(X[i]), ld[i], B.k))
+        continue;
+      const int ctiles = (B.kout + 127) / 128;
+      const int nrt = static_cast<int>((B.rows + 127) / 128);
+      int splits = (2 * p.num_sms + ctiles - 1) / ctiles;
+      if (splits > nrt) splits = nrt;
+      if (splits < 1) splits = 1;
+      const int rps = (nrt + splits - 1) / splits;
+      splits = (nrt + rps - 1) / rps;
+      fb[i] = WideFormBlock{static_cast<const float*>(X[i]), ld[i], B.k, B.kout, B.w0, B.rows, B.rows_dev,
+                            static_cast<float*>(p.wq[i]), ctiles, splits, rps, ctiles * splits};
+      B.fjobs = 0;  // not for the CUDA-core formation
+      form_tc += fb[i].njobs;
+    }
+    if (form_tc > 0) {
+      int fj = 0;
+      for (int i = 0; i < 3; ++i) {
+        a.b[i].fjob0 = fj;
+        fj += a.b[i].fjobs;
+      }
+      a.form_jobs = fj;
+      cudaError_t err = launch_wide_form_prep(p.Wf, p.n, p.wt, p.wtlo, s);
+      if (err != cudaSuccess) return err;
+      err = launch_wide_form_tc(fb, p.wt, p.wtlo, p.n, &p.hdr->status, p.spin_limit, s);
+      if (err != cudaSuccess) return err;
+    }
+  }
+  if (pass == 2 && (a.form_jobs > 0 || form_tc > 0)) {
+    if (a.form_jobs > 0) {
+      if (p.mixed)
+        pdl_launch(wide_form_kernel<float>, a.form_jobs, kWThreads, 0, s, a);
+      else
+        pdl_launch(wide_form_kernel<double>, a.form_jobs, kWThreads, 0, s, a);
+      count_launches(1);
+    }
     // the Grams of pass 2 read Q
     for (int i = 0; i < 3; ++i) {
       a.b[i].X = p.wq[i];
