@@ -890,21 +890,21 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 // form Z = [hi | lo] (128 columns, MN-major, 32-byte-atom 128-byte swizzle,
 // four 32-column panels).
 //
-// Pass 1 reads the packed rows straight from memory (the rows of a block are
-// contiguous; hi = the raw value, which the tensor core truncates to TF32)
-// and accumulates D = Z^T Z: for each packed row position r the blocks
-// hi_r^T hi_r, hi_r^T lo_r, lo_r^T hi_r and lo_r^T lo_r on the diagonal of
-// its 2 x 2 block grid, whose sum over r is the Gram of the full FP32 values.
+// Both passes accumulate D = Z^T H (N = 64: B is the hi half of Z), which
+// holds, for each packed row position r, H_r^T H_r (hi lanes) and L_r^T H_r
+// (lo lanes); the symmetrised sum H^T H + L^T H + H^T L takes the lo lanes
+// twice, and L^T L is left out.  Pass 1 reads the packed rows straight from
+// memory (the rows of a block are contiguous; hi = the raw value, which the
+// tensor core truncates to TF32; |lo| < 2^-10 |v|), so its dropped term is at
+// most 2^-20 of |v|^2 per product: the first factor only has to make Q well
+// conditioned, and the second pass measures Q itself.
 //
 // Pass 2 forms Q = X W per tile of 128 rows in tensor memory with two MMAs
 // per K step, X_hi [W_hi | W_lo] (N = 2 np) and X_lo W_hi (N = np), and Q is
 // their sum X_hi W_hi + (X_hi W_lo + X_lo W_hi).  Q is split with hi = Q
-// rounded to the nearest TF32 value and lo = Q - hi rounded to TF32, and the
-// Gram MMA is D = Z^T H (N = 64: B is the hi half of Z), which holds
-// H_r^T H_r (hi lanes) and L_r^T H_r (lo lanes); the symmetrised sum
-// H^T H + L^T H + H^T L takes the lo lanes twice.  The dropped L^T L term is
-// below 2^-22 of |Q|^2 per product (2^-11 per lo part), under the FP32
-// rounding of the formation itself.
+// rounded to the nearest TF32 value and lo = Q - hi rounded to TF32, so the
+// dropped L^T L term is below 2^-22 of |Q|^2 per product (2^-11 per lo
+// part), under the FP32 rounding of the formation itself.
 //
 // Roles: a TMA producer warp, an MMA warp and three worker groups with loops
 // of their own that meet only at mbarriers: split (the lo parts of each X
@@ -1198,7 +1198,7 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issue
-    const uint32_t idg = idesc_tf32(128, 128, 1);
+    const uint32_t idh = idesc_tf32(128, 64, 1);  // D = Z^T H: B is the first 64 columns of Z
     if (!pass2) {
       if (lane == 0) {
         for (int i = 0; i < n; ++i) {
@@ -1211,7 +1211,7 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
           const uint64_t dz = desc_mn_sw128_32b(smem_u32(base + s * stage_bytes), kPanelBytes);
 #pragma unroll
           for (int ks = 0; ks < kTileRows / 8; ++ks)
-            mma_tf32(acc_addr(b, ks & 1), dz + static_cast<uint64_t>(ks * 64), dz + static_cast<uint64_t>(ks * 64), idg,
+            mma_tf32(acc_addr(b, ks & 1), dz + static_cast<uint64_t>(ks * 64), dz + static_cast<uint64_t>(ks * 64), idh,
                      ks >= 2 ? 1u : 0u);
           mma_commit(&S.stage_empty[s]);
           mma_commit(&S.acc_full[b]);
@@ -1403,35 +1403,22 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         if constexpr (KK == 32) {  // the whole chunk is this lane's: two halves of 16 columns
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
-            uint32_t rh[16], rl[16];
+            uint32_t rh[16];
             tmem_ld_nowait<16>(acc + static_cast<uint32_t>(hh * 16), rh);
-            if (!pass2) tmem_ld_nowait<16>(acc + 64u + static_cast<uint32_t>(hh * 16), rl);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (pass2) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) grp[hh * 16 + j] = __fadd_rn(grp[hh * 16 + j], __uint_as_float(rh[j]));
-            } else {
-#pragma unroll
-              for (int j = 0; j < 16; ++j)
-                grp[hh * 16 + j] =
-                    __fadd_rn(grp[hh * 16 + j], __fadd_rn(__uint_as_float(rh[j]), __uint_as_float(rl[j])));
-            }
+            for (int j = 0; j < 16; ++j) grp[hh * 16 + j] = __fadd_rn(grp[hh * 16 + j], __uint_as_float(rh[j]));
           }
         } else {
-          uint32_t rh[C][KK], rl[C][KK];
+          uint32_t rh[C][KK];
 #pragma unroll
-          for (int c = 0; c < C; ++c) {
-            tmem_ld_nowait<KK>(acc + static_cast<uint32_t>(c * KK), rh[c]);
-            if (!pass2) tmem_ld_nowait<KK>(acc + 64u + static_cast<uint32_t>(c * KK), rl[c]);
-          }
+          for (int c = 0; c < C; ++c) tmem_ld_nowait<KK>(acc + static_cast<uint32_t>(c * KK), rh[c]);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int c = 0; c < C; ++c)
             if (c == mine) {
 #pragma unroll
-              for (int j = 0; j < KK; ++j)
-                grp[j] = __fadd_rn(grp[j], pass2 ? __uint_as_float(rh[c][j])
-                                                 : __fadd_rn(__uint_as_float(rh[c][j]), __uint_as_float(rl[c][j])));
+              for (int j = 0; j < KK; ++j) grp[j] = __fadd_rn(grp[j], __uint_as_float(rh[c][j]));
             }
         }
       }
@@ -1455,7 +1442,7 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
     double* part = a.part + static_cast<int64_t>(cta) * a.kout * a.kout;
     // pass 2 holds H^T H (hi lanes) and L^T H (lo lanes): the symmetrised sum
     // H^T H + L^T H + H^T L takes the lo lanes twice (exact scaling)
-    const float lo_w = pass2 ? 2.f : 1.f;
+    const float lo_w = 2.f;
     auto gram_entry = [&](int ra, int cbb, float& h, float& l) {
       for (int half = 0; half < 2; ++half)
         for (int r = 0; r < RR; ++r) {
