@@ -151,7 +151,40 @@ def measured_traffic(kernel, cfg):
 
 # ------------------------------------------------------------ clocks ------
 
+class NvmlClocks:
+    """The SM clock and the clock-event reasons read through NVML (the driver's
+    libnvidia-ml, read-only queries)."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, index):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise OSError("nvmlDeviceGetHandleByIndex")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        if self.reasons_fn is None:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint(0)
+        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 else None
+
+    def sample(self):
+        clk, rs = self.ct.c_uint(0), self.ct.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(clk)) != 0:
+            return None
+        names = []
+        if self.reasons_fn(self.h, self.ct.byref(rs)) == 0:
+            names = [n for bit, n in self.REASONS.items() if rs.value & bit]
+        return float(clk.value), names
+
+
 class ClockSampler:
+    """SM clocks and throttle reasons during the timed region: NVML read about
+    every millisecond on a thread, or nvidia-smi every 10 ms where NVML cannot
+    be loaded."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -159,8 +192,27 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
+        self.nvml = None
+        self.thread = None
+        self.samples = []
+
+    def _loop(self):
+        while not self.stop.is_set():
+            s = self.nvml.sample()
+            if s is not None:
+                self.samples.append(s)
+            time.sleep(0.001)
 
     def __enter__(self):
+        import threading
+        try:
+            self.nvml = NvmlClocks(self.dev)
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -171,6 +223,9 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         self.out = ""
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -180,6 +235,11 @@ class ClockSampler:
         return False
 
     def summary(self):
+        if self.nvml is not None and self.samples:
+            sm = [c for c, _ in self.samples]
+            reasons = sorted({n for _, ns in self.samples for n in ns})
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.nvml.max_mhz or max(sm), "reasons": reasons,
+                    "samples": len(sm), "source": "nvml"}
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in (self.out or "").splitlines():
@@ -197,7 +257,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi"}
 
 
 # -------------------------------------------------------------- oracle ----
