@@ -336,12 +336,14 @@ figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, con
         cudaStream_t st = ss[part];
         cudaEvent_t done = nullptr;
         err = cudaStreamWaitEvent(st, fork, 0);
-        if (err == cudaSuccess)
-          err = cudaMemcpy2DAsync(static_cast<char*>(const_cast<void*>(T.x)) + static_cast<size_t>(r0) * src->n * ei,
-                                  static_cast<size_t>(src->n) * ei,
-                                  static_cast<const char*>(src->x) + static_cast<size_t>(r0) * src->ld * ei,
-                                  static_cast<size_t>(src->ld) * ei, static_cast<size_t>(src->n) * ei,
-                                  static_cast<size_t>(r1 - r0), cudaMemcpyHostToDevice, st);
+        char* dst = static_cast<char*>(const_cast<void*>(T.x)) + static_cast<size_t>(r0) * src->n * ei;
+        const char* from = static_cast<const char*>(src->x) + static_cast<size_t>(r0) * src->ld * ei;
+        if (err == cudaSuccess && src->ld == src->n)  // dense rows: one contiguous copy
+          err = cudaMemcpyAsync(dst, from, static_cast<size_t>(r1 - r0) * src->n * ei, cudaMemcpyHostToDevice, st);
+        else if (err == cudaSuccess)
+          err = cudaMemcpy2DAsync(dst, static_cast<size_t>(src->n) * ei, from, static_cast<size_t>(src->ld) * ei,
+                                  static_cast<size_t>(src->n) * ei, static_cast<size_t>(r1 - r0), cudaMemcpyHostToDevice,
+                                  st);
         if (err == cudaSuccess) err = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
         if (err == cudaSuccess) err = cudaEventRecord(done, st);
         if (done) c.staged[c.nstaged++] = done;
