@@ -145,6 +145,13 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
     p.yw = b.take<char>(static_cast<size_t>(n) * ec);
     p.d0w = b.take<char>(static_cast<size_t>(n) * ec);
   }
+  // narrow mixed plans with n in (64, 128]: Q of the A tails and W^T for the
+  // tensor-core formation and tile Gram of pass 2 (narrow_q_tc)
+  if (!p.wide && mixed && n > 64 && n % 4 == 0) {
+    p.wq[1] = b.take<char>(static_cast<size_t>(m1 > 0 ? m1 : 1) * n * 4);
+    p.wt = b.take<float>(static_cast<size_t>(n) * n);
+    p.wtlo = b.take<float>(static_cast<size_t>(n) * n);
+  }
   // the block Jacobi's columns (wide widths, and singular vectors at every width)
   p.Uw = b.take<char>(static_cast<size_t>(n + 32) * n * ec);
   p.Vw = b.take<char>(static_cast<size_t>(n + 32) * n * ec);

@@ -216,7 +216,8 @@ struct ReduceArgs {
   int kout[3];
   int off[3];     // diagonal offset of the block inside G
   int sym[3];     // partial format: 0 FP64 upper triangle; 1 FP64 P with G = (P + P^T) / 2 (general
-                  // tensor-core engine); 2 float-float pairs, upper triangle (packed tensor-core engine)
+                  // tensor-core engine); 2 float-float pairs, upper triangle (packed tensor-core engine);
+                  // 3 FP64 upper triangle of 128 x 128 tiles (the tile Gram, one tile pair: kout <= 128)
   int n;
   double* G;
 };
@@ -251,10 +252,11 @@ __device__ __forceinline__ void gram_reduce_body(const ReduceArgs& a, int bid) {
     const int ii = lo - a.off[b], jj = hi - a.off[b];
     const bool in = a.part[b] && ok && ii >= 0 && jj >= 0 && ii < ko && jj < ko;
     cnt[b] = in ? a.count[b] : 0;
-    stride[b] = static_cast<int64_t>(ko) * ko;
+    const int pitch = a.sym[b] == 3 ? kWideTcTile : ko;
+    stride[b] = static_cast<int64_t>(pitch) * pitch;
     const unsigned long long* base = reinterpret_cast<const unsigned long long*>(a.part[b]);
-    p0[b] = in ? base + ii * ko + jj : nullptr;
-    p1[b] = in ? base + jj * ko + ii : nullptr;  // the transposed entry (symmetrised partials)
+    p0[b] = in ? base + ii * pitch + jj : nullptr;
+    p1[b] = in ? base + jj * pitch + ii : nullptr;  // the transposed entry (symmetrised partials)
     maxc = a.count[b] > maxc ? a.count[b] : maxc;
     any64 = any64 || (a.part[b] && a.sym[b] != 2);
   }
@@ -526,6 +528,17 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     a.tile_rows = gram_tile_rows(a.k, a.kout, a.W != nullptr, elem);
     a.part = p.gpart[b];
     int grid = p.ggrid[b];
+    if (pass == 2 && b == 1 && p.gram_engine != 1 && narrow_q_tc(p)) {  // Q written, then the tile Gram
+      int count = 0;
+      const cudaError_t err = launch_narrow_q_gram_tc(p, &count, s);
+      if (err != cudaSuccess) return err;
+      r.part[b] = p.gpart[b];
+      r.count[b] = count;
+      r.kout[b] = a.kout;
+      r.off[b] = 0;
+      r.sym[b] = 3;
+      continue;
+    }
     const bool tc = p.mixed && p.gram_engine != 1 && gram_tc_supported(a.k, a.kout);
     cudaError_t err;
     if (tc) {

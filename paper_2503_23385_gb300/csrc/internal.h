@@ -294,6 +294,11 @@ struct WideFormBlock {
   int ctiles, splits, rt_per_split, njobs;
 };
 cudaError_t launch_wide_form_prep(const float* W, int n, float* WT, float* WTlo, cudaStream_t s);
+// Narrow mixed plans with n in (64, 128]: the A-tail block of pass 2 on the
+// tensor cores (wide.cu); the partials of block 1 in the reduce's format 3.
+bool narrow_q_tc(const Plan& p);
+int narrow_q_tc_splits(const Plan& p, int64_t* split_rows);
+cudaError_t launch_narrow_q_gram_tc(const Plan& p, int* count, cudaStream_t s);
 cudaError_t launch_wide_form_tc(const WideFormBlock b[3], const float* WT, const float* WTlo, int n, int32_t* status,
                                 int64_t spin_limit, cudaStream_t s);
 cudaError_t launch_wide_gram_tc(const WideTcBlock b[3], double* part, int32_t* status, int64_t spin_limit,

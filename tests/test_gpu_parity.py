@@ -273,6 +273,33 @@ def test_gram_engines_agree_with_oracle(fg, torch, shape):
     assert rel(out[fg.GRAM_SIMT], out[fg.GRAM_TCGEN05]) <= 1e-6
 
 
+@pytest.mark.parametrize("shape", [(20000, 64, 15000, 64, 300), (9001, 32, 12345, 64, 77), (5000, 64, 6000, 8, 40)],
+                         ids=["128", "96-ragged", "72"])
+def test_wide_q_tail_block_on_tensor_cores(fg, torch, shape):
+    """Joins of 65 to 128 columns: in a single call, pass 2 of the A tails
+    (Q has n columns, more than the narrow tensor-core engines take) runs the
+    tensor-core formation and tile Gram.  Both engine settings meet the
+    mixed-path bar and agree; a batch holding the same join (which keeps the
+    block on CUDA cores) does too."""
+    m1, n1, m2, n2, K = shape
+    A, B = make_pair(m1, n1, m2, n2, K, np.float32, "normal", seed=m1 + n2)
+    Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key)
+    out = {}
+    for eng in (fg.GRAM_SIMT, fg.GRAM_AUTO):
+        R, s = fg.join_qr_svd(dev(torch, A), dev(torch, B), path="mixed", gram_engine=eng)
+        R, s = R.cpu().numpy(), s.cpu().numpy()
+        assert rel(R, Rref) <= 1e-6 and rel(s, sref) <= 1e-6, (eng, rel(R, Rref), rel(s, sref))
+        out[eng] = R
+    assert rel(out[fg.GRAM_SIMT], out[fg.GRAM_AUTO]) <= 1e-6
+    small = make_pair(3000, 8, 2000, 16, 30, np.float32, "normal", seed=7)
+    outs, ws = fg.batch_join([(dev(torch, A), dev(torch, B)), (dev(torch, small[0]), dev(torch, small[1]))])
+    torch.cuda.synchronize()
+    Rb, sb = outs[0]
+    assert rel(Rb.cpu().numpy(), Rref) <= 1e-6 and rel(sb.cpu().numpy(), sref) <= 1e-6
+    R2, s2 = oracle.join_r_sigma(small[0].x, small[0].key, small[1].x, small[1].key)
+    assert rel(outs[1][0].cpu().numpy(), R2) <= 1e-6 and rel(outs[1][1].cpu().numpy(), s2) <= 1e-6
+
+
 # ---------------------------------------------------------- status codes --
 
 def test_status_codes(fg, torch):
