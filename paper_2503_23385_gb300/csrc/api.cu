@@ -126,7 +126,14 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
       size_t sz = static_cast<size_t>(grid) * kouts[q] * kouts[q];
       if (sz > most) most = sz;
     }
+    // narrow mixed plans with n in (64, 128]: room for the tile Gram's
+    // 128 x 128 partials of pass 2 on the A tails (one per 1024 rows at most)
+    if (blk == 1 && !p.wide && mixed && n > 64 && n % 4 == 0) {
+      const int64_t tiles = std::min<int64_t>(std::max<int64_t>(1, ceil_div(m1, 1024)), 2 * num_sms);
+      most = std::max(most, static_cast<size_t>(tiles) * kWideTcTile * kWideTcTile);
+    }
     p.gslices[blk] = 0;
+    p.gcap[blk] = p.wide ? 1 : static_cast<int64_t>(most);
     p.gpart[blk] = b.take<double>(p.wide ? 1 : most);
   }
   if (p.wide) {
@@ -483,7 +490,11 @@ __global__ void upload_kernel(const __grid_constant__ UploadChunk c) {
 // Bytes of the batch area (plans, outputs, job lists) for `count` instances.
 size_t batch_area_bytes(int count) {
   const size_t lists = 24, per_list = (3 * static_cast<size_t>(count) + 1) * 3 * sizeof(int32_t) + 256;
-  return ((sizeof(Plan) + sizeof(BatchOut)) * static_cast<size_t>(count) + lists * per_list + 4096 + 255) &
+  // the table launches of the wide tensor-core kernels: an entry of each kind
+  // and three CTA offsets per instance
+  const size_t tables = (sizeof(WideTcEntry) + sizeof(WideFormEntry) + sizeof(WidePrepEntry) + 3 * sizeof(int32_t)) *
+                            static_cast<size_t>(count) + 6 * 64;
+  return ((sizeof(Plan) + sizeof(BatchOut)) * static_cast<size_t>(count) + lists * per_list + tables + 4096 + 255) &
          ~static_cast<size_t>(255);
 }
 
@@ -500,8 +511,8 @@ struct JobList {
 
 struct Blob {
   std::vector<unsigned char> bytes;
-  size_t put(const void* src, size_t n) {
-    size_t off = (bytes.size() + 15) & ~static_cast<size_t>(15);
+  size_t put(const void* src, size_t n, size_t align = 16) {
+    size_t off = (bytes.size() + align - 1) & ~(align - 1);
     bytes.resize(off + n);
     if (n) std::memcpy(bytes.data() + off, src, n);
     return off;
@@ -552,6 +563,14 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   size_t gram_smem[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   size_t dsm[3][3] = {};
   int dthr[3][3] = {};
+  // pass 2 of A-tail blocks with n in (64, 128] on the mixed path: table
+  // launches of the tensor-core formation and tile Gram (entries 64-byte
+  // aligned in the batch area)
+  std::vector<WideTcEntry> qt;
+  std::vector<WideFormEntry> qf;
+  std::vector<WidePrepEntry> qp;
+  std::vector<int32_t> qt0{0}, qf0{0}, qp0{0};
+  const bool q_tables = (reinterpret_cast<uintptr_t>(area) & 63) == 0;
   int64_t total_chunks = 0;
   for (int i = 0; i < count; ++i)
     for (int t = 0; t < 2; ++t) total_chunks += calls[i].p.t[t].m > 0 ? calls[i].p.t[t].chunks : 0;
@@ -574,6 +593,24 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
     match.add(i, 0, static_cast<int>((mm + 255) / 256));
     for (int pass = 1; pass <= 2; ++pass)
       for (int b = 0; b < 3; ++b) {
+        if (pass == 2 && b == 1 && q_tables && p.gram_engine != 1 && narrow_q_tc(p)) {
+          WideFormBlock fb;
+          WideTcBlock tb;
+          narrow_q_tc_blocks(p, sched.gram_rows_per_cta, &fb, &tb);
+          WideFormEntry fe;
+          WideTcEntry te;
+          if (wide_form_encode(fb, &fe) && wide_tc_encode(tb, &te)) {
+            qf.push_back(fe);
+            qf0.push_back(qf0.back() + fb.njobs);
+            qt.push_back(te);
+            qt0.push_back(qt0.back() + tb.njobs);
+            qp.push_back(WidePrepEntry{p.Wf, p.wt, p.wtlo, p.n});
+            qp0.push_back(qp0.back() + (p.n * p.n + 255) / 256);
+            calls[i].p.gcount[1][1] = tb.njobs;
+            calls[i].p.gsym[1][1] = 3;
+            continue;
+          }
+        }
         int tv = 0;
         int64_t tile_rows = 0;
         size_t tsm = 0;
@@ -625,6 +662,16 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   for (int q = 0; q < 2; ++q)
     for (int v = 0; v < 4; ++v) Jgram[q][v] = stage_jobs(blob, gram[q][v], fix, &Jgram[q][v]);
   Jreduce = stage_jobs(blob, reduce, fix, &Jreduce);
+  const int nq = static_cast<int>(qt.size());
+  size_t off_qt = 0, off_qf = 0, off_qp = 0, off_qt0 = 0, off_qf0 = 0, off_qp0 = 0;
+  if (nq > 0) {
+    off_qt = blob.put(qt.data(), sizeof(WideTcEntry) * nq, 64);
+    off_qf = blob.put(qf.data(), sizeof(WideFormEntry) * nq, 64);
+    off_qp = blob.put(qp.data(), sizeof(WidePrepEntry) * nq);
+    off_qt0 = blob.put(qt0.data(), sizeof(int32_t) * (nq + 1));
+    off_qf0 = blob.put(qf0.data(), sizeof(int32_t) * (nq + 1));
+    off_qp0 = blob.put(qp0.data(), sizeof(int32_t) * (nq + 1));
+  }
   JobList* dl[3] = {dense1, dense2, dense3};
   for (int st = 0; st < 3; ++st)
     for (int v = 0; v < 3; ++v) Jd[st][v] = stage_jobs(blob, dl[st][v], fix, &Jd[st][v]);
@@ -672,6 +719,17 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
         FIGARO_TRY(launch_gram_tc_batch(b.plans, plans.data(), pass, e + 1, v, jobs.data(), static_cast<int>(jobs.size()),
                                         tc_smem[pass - 1][e][v], s));
       }
+    if (pass == 2 && nq > 0) {  // W^T of each instance, Q = X W, then the tile Gram of Q
+      auto at = [&](size_t off) { return area + off; };
+      FIGARO_TRY(launch_wide_prep_table(reinterpret_cast<const WidePrepEntry*>(at(off_qp)),
+                                        reinterpret_cast<const int32_t*>(at(off_qp0)), nq, qp0.back(), s));
+      FIGARO_TRY(launch_wide_form_tc_table(reinterpret_cast<const WideFormEntry*>(at(off_qf)),
+                                           reinterpret_cast<const int32_t*>(at(off_qf0)), nq, qf0.back(),
+                                           p0.spin_limit, s));
+      FIGARO_TRY(launch_wide_gram_tc_table(reinterpret_cast<const WideTcEntry*>(at(off_qt)),
+                                           reinterpret_cast<const int32_t*>(at(off_qt0)), nq, qt0.back(),
+                                           p0.spin_limit, s));
+    }
     FIGARO_TRY(launch_batch_gram(b, pass, none, none_smem, Jreduce, mixed, s));
     return FIGARO_OK;
   };

@@ -1658,17 +1658,14 @@ struct WideTcArgs {
   int64_t spin_limit;
 };
 
-__global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __grid_constant__ WideTcArgs A) {
-  pdl_enter();
+// One job of the tile Gram: block B (its rows in tensor map `map`), partials
+// of all its jobs from part_all.
+__device__ __forceinline__ void wide_gram_tc_body(const WideTcBlock& B, const CUtensorMap* map, int job,
+                                                  double* part_all, int32_t* status, int64_t spin_limit) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ PipeSmem S;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int bi = 0;
-  while (bi < 2 && static_cast<int>(blockIdx.x) >= A.job0[bi] + A.b[bi].njobs) ++bi;
-  const WideTcBlock& B = A.b[bi];
-  const CUtensorMap* map = &A.map[bi];
-  const int job = static_cast<int>(blockIdx.x) - A.job0[bi];
   const int tile = job / B.splits, split = job - tile * B.splits;
   int ti = 0, len = B.tiles, t = tile;  // upper tile pair (ti <= tj), row-major over the upper triangle
   while (t >= len) {
@@ -1684,7 +1681,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __gri
   if (r1 > rows_all) r1 = rows_all;
   const int nst = r1 > r0 ? static_cast<int>((r1 - r0 + kWtRows - 1) / kWtRows) : 0;
   const int ngroups = (nst + 1) / 2;
-  double* part = A.part + B.pbase + static_cast<int64_t>(job) * kWideTcTile * kWideTcTile;
+  double* part = part_all + static_cast<int64_t>(job) * kWideTcTile * kWideTcTile;
 
   if (tid == 0) {
     for (int q = 0; q < kWtStages; ++q) {
@@ -1718,7 +1715,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __gri
       for (int s = 0; s < nst; ++s) {
         const int q = s % kWtStages;
         if (s >= kWtStages && !pipe_wait(S, &S.stage_empty[q], static_cast<uint32_t>(((s / kWtStages) - 1) & 1),
-                                         A.spin_limit, A.status))
+                                         spin_limit, status))
           break;
         unsigned char* dst = base + q * kWtStage;
         const int y = static_cast<int>(r0 + static_cast<int64_t>(s) * kWtRows);
@@ -1730,7 +1727,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __gri
         issued = s + 1;
       }
       for (int s = issued > kWtStages ? issued - kWtStages : 0; s < issued; ++s)
-        drain_wait(&S.tma_full[s % kWtStages], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status);
+        drain_wait(&S.tma_full[s % kWtStages], static_cast<uint32_t>((s / kWtStages) & 1), spin_limit, status);
     }
   } else if (warp >= 2 + kWtDrainWarps) {
     // ------------------------------------------------------------ split
@@ -1741,7 +1738,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __gri
     const int nf4 = tile_bytes / 16;
     for (int s = 0; s < nst; ++s) {
       const int q = s % kWtStages;
-      if (!warp_wait(S, &S.tma_full[q], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status)) break;
+      if (!warp_wait(S, &S.tma_full[q], static_cast<uint32_t>((s / kWtStages) & 1), spin_limit, status)) break;
       float4* X4 = reinterpret_cast<float4*>(base + q * kWtStage);
       float4* L4 = reinterpret_cast<float4*>(base + q * kWtStage + 2 * kWtTileBytes);
       const int64_t valid = r1 - (r0 + static_cast<int64_t>(s) * kWtRows);  // rows of this stage in the job
@@ -1780,9 +1777,9 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __gri
     const uint64_t d0 = desc_mn_sw128_32b(smem_u32(base), kWtPanel);
     for (int s = 0; s < nst; ++s) {
       const int q = s % kWtStages, g = s / 2, b = g & 1;
-      if (!warp_wait(S, &S.op_full[q], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status)) break;
+      if (!warp_wait(S, &S.op_full[q], static_cast<uint32_t>((s / kWtStages) & 1), spin_limit, status)) break;
       if ((s & 1) == 0 && g >= 2 &&
-          !warp_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((g / 2) - 1) & 1), A.spin_limit, A.status))
+          !warp_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((g / 2) - 1) & 1), spin_limit, status))
         break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t dhi = d0 + static_cast<uint64_t>((q * kWtStage) >> 4);
@@ -1806,7 +1803,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __gri
     }
     if (leader) {  // the lane that issued the MMAs: its commit tracks all of them
       mma_commit(&S.done);
-      drain_wait(&S.done, 0u, A.spin_limit, A.status);
+      drain_wait(&S.done, 0u, spin_limit, status);
     }
   } else {
     // ------------------------------------------------------------ drain
@@ -1843,7 +1840,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __gri
     int since = 0;
     for (int g = 0; g < ngroups; ++g) {
       const int b = g & 1;
-      if (!warp_wait(S, &S.acc_full[b], static_cast<uint32_t>((g / 2) & 1), A.spin_limit, A.status)) break;
+      if (!warp_wait(S, &S.acc_full[b], static_cast<uint32_t>((g / 2) & 1), spin_limit, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t big = tmem + static_cast<uint32_t>(b * 256) + lanes, small = big + 128u;
 #pragma unroll
@@ -1874,6 +1871,44 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __gri
   }
 }
 
+// Entry of a table launch: the highest i with job0[i] <= x (entries own
+// [job0[i], job0[i + 1]) CTAs).
+__device__ __forceinline__ int table_entry(const int32_t* __restrict__ job0, int nb, int x) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (job0[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Tensor maps that reach a launch through device memory (written there by an
+// earlier kernel): order those generic-proxy writes before this thread's
+// tensor copies.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+}
+
+__global__ void __launch_bounds__(kWtThreads, 1) wide_gram_tc_kernel(const __grid_constant__ WideTcArgs A) {
+  pdl_enter();
+  int bi = 0;
+  while (bi < 2 && static_cast<int>(blockIdx.x) >= A.job0[bi] + A.b[bi].njobs) ++bi;
+  const WideTcBlock& B = A.b[bi];
+  wide_gram_tc_body(B, &A.map[bi], static_cast<int>(blockIdx.x) - A.job0[bi], A.part + B.pbase, A.status,
+                    A.spin_limit);
+}
+
+__global__ void __launch_bounds__(kWtThreads, 1)
+    wide_gram_tc_table_kernel(const WideTcEntry* __restrict__ E, const int32_t* __restrict__ job0, int nb,
+                              int64_t spin_limit) {
+  pdl_enter();
+  const int bi = table_entry(job0, nb, static_cast<int>(blockIdx.x));
+  const WideTcEntry& e = E[bi];
+  tensormap_acquire(&e.map);
+  wide_gram_tc_body(e.b, &e.map, static_cast<int>(blockIdx.x) - job0[bi], e.b.part, e.b.status, spin_limit);
+}
+
 // ---------------------------------------------------------------------------
 // Tensor-core formation of wide blocks: Q = X W[w0:w0+k, w0:w0+kout] in
 // 3 x TF32, Q = X_hi W_hi + (X_hi W_lo + X_lo W_hi).  One CTA per (block,
@@ -1898,9 +1933,7 @@ struct WideFormArgs {
 };
 
 // W^T and its TF32 lo parts (W upper triangular: W^T[c][f] = W[f][c] for f <= c).
-__global__ void wide_form_prep_kernel(const float* W, int n, float* WT, float* WTlo) {
-  pdl_enter();
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void wide_form_prep_at(const float* W, int n, float* WT, float* WTlo, int64_t e) {
   if (e >= static_cast<int64_t>(n) * n) return;
   const int c = static_cast<int>(e / n), f = static_cast<int>(e - static_cast<int64_t>(c) * n);
   const float v = f <= c ? W[static_cast<int64_t>(f) * n + c] : 0.f;
@@ -1908,17 +1941,20 @@ __global__ void wide_form_prep_kernel(const float* W, int n, float* WT, float* W
   WTlo[e] = tf32_rn(v - tf32_hi(v));
 }
 
-__global__ void __launch_bounds__(kWtThreads, 1) wide_form_tc_kernel(const __grid_constant__ WideFormArgs A) {
+__global__ void wide_form_prep_kernel(const float* W, int n, float* WT, float* WTlo) {
   pdl_enter();
+  wide_form_prep_at(W, n, WT, WTlo, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+}
+
+// One job of the formation: block B, its X rows in xmap, W^T and its lo parts
+// in wmap and wlmap.
+__device__ __forceinline__ void wide_form_tc_body(const WideFormBlock& B, const CUtensorMap* xmap,
+                                                  const CUtensorMap* wmap, const CUtensorMap* wlmap, int job,
+                                                  int32_t* status, int64_t spin_limit) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ PipeSmem S;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int bi = 0;
-  while (bi < 2 && static_cast<int>(blockIdx.x) >= A.job0[bi] + A.b[bi].njobs) ++bi;
-  const WideFormBlock& B = A.b[bi];
-  const CUtensorMap* xmap = &A.xmap[bi];
-  const int job = static_cast<int>(blockIdx.x) - A.job0[bi];
   const int ct = job / B.splits, split = job - ct * B.splits;
   const int64_t rows_all = B.rows_dev ? (*B.rows_dev < B.rows ? *B.rows_dev : B.rows) : B.rows;
   const int nrt_all = static_cast<int>((rows_all + 127) / 128);
@@ -1963,17 +1999,17 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_form_tc_kernel(const __gri
       for (int s = 0; s < nst; ++s) {
         const int q = s % kWtStages, rt = rt0 + s / nkp, kp = s % nkp;
         if (s >= kWtStages && !pipe_wait(S, &S.stage_empty[q], static_cast<uint32_t>(((s / kWtStages) - 1) & 1),
-                                         A.spin_limit, A.status))
+                                         spin_limit, status))
           break;
         unsigned char* dst = base + q * kWfStage;
         expect_tx(&S.tma_full[q], static_cast<uint32_t>(3 * kWfPanel));
         tma_load_2d(dst, xmap, 32 * kp, 128 * rt, &S.tma_full[q]);
-        tma_load_2d(dst + 2 * kWfPanel, &A.wmap, B.w0 + 32 * kp, B.w0 + 128 * ct, &S.tma_full[q]);
-        tma_load_2d(dst + 3 * kWfPanel, &A.wlmap, B.w0 + 32 * kp, B.w0 + 128 * ct, &S.tma_full[q]);
+        tma_load_2d(dst + 2 * kWfPanel, wmap, B.w0 + 32 * kp, B.w0 + 128 * ct, &S.tma_full[q]);
+        tma_load_2d(dst + 3 * kWfPanel, wlmap, B.w0 + 32 * kp, B.w0 + 128 * ct, &S.tma_full[q]);
         issued = s + 1;
       }
       for (int s = issued > kWtStages ? issued - kWtStages : 0; s < issued; ++s)
-        drain_wait(&S.tma_full[s % kWtStages], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status);
+        drain_wait(&S.tma_full[s % kWtStages], static_cast<uint32_t>((s / kWtStages) & 1), spin_limit, status);
     }
   } else if (warp >= 2 + kWtDrainWarps) {
     // ------------------------------------------------------------ split (X lo; rows past the block's end cleared)
@@ -1981,7 +2017,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_form_tc_kernel(const __gri
     constexpr int NT = 32 * kWtSplitWarps;
     for (int s = 0; s < nst; ++s) {
       const int q = s % kWtStages, rt = rt0 + s / nkp;
-      if (!warp_wait(S, &S.tma_full[q], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status)) break;
+      if (!warp_wait(S, &S.tma_full[q], static_cast<uint32_t>((s / kWtStages) & 1), spin_limit, status)) break;
       float4* X4 = reinterpret_cast<float4*>(base + q * kWfStage);
       float4* L4 = reinterpret_cast<float4*>(base + q * kWfStage + kWfPanel);
       const int64_t valid = rows_all - static_cast<int64_t>(rt) * 128;
@@ -2016,9 +2052,9 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_form_tc_kernel(const __gri
       const int g = (s / nkp) * gpr + kp / 2, b = g & 1;
       const bool first_of_group = (kp & 1) == 0;
       const bool last_of_group = (kp & 1) == 1 || kp == nkp - 1;
-      if (!warp_wait(S, &S.op_full[q], static_cast<uint32_t>((s / kWtStages) & 1), A.spin_limit, A.status)) break;
+      if (!warp_wait(S, &S.op_full[q], static_cast<uint32_t>((s / kWtStages) & 1), spin_limit, status)) break;
       if (first_of_group && g >= 2 &&
-          !warp_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((g / 2) - 1) & 1), A.spin_limit, A.status))
+          !warp_wait(S, &S.acc_empty[b], static_cast<uint32_t>(((g / 2) - 1) & 1), spin_limit, status))
         break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t dx = d0 + static_cast<uint64_t>((q * kWfStage) >> 4);
@@ -2042,7 +2078,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_form_tc_kernel(const __gri
     }
     if (leader) {
       mma_commit(&S.done);
-      drain_wait(&S.done, 0u, A.spin_limit, A.status);
+      drain_wait(&S.done, 0u, spin_limit, status);
     }
   } else {
     // ------------------------------------------------------------ drain and store
@@ -2056,7 +2092,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_form_tc_kernel(const __gri
     for (int e = 0; e < 64; ++e) acc[e] = 0.f;
     for (int g = 0; g < ngroups; ++g) {
       const int b = g & 1;
-      if (!warp_wait(S, &S.acc_full[b], static_cast<uint32_t>((g / 2) & 1), A.spin_limit, A.status)) break;
+      if (!warp_wait(S, &S.acc_full[b], static_cast<uint32_t>((g / 2) & 1), spin_limit, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t big = tmem + static_cast<uint32_t>(b * 256) + lanes, small = big + 128u;
 #pragma unroll
@@ -2094,6 +2130,36 @@ __global__ void __launch_bounds__(kWtThreads, 1) wide_form_tc_kernel(const __gri
   }
 }
 
+__global__ void __launch_bounds__(kWtThreads, 1) wide_form_tc_kernel(const __grid_constant__ WideFormArgs A) {
+  pdl_enter();
+  int bi = 0;
+  while (bi < 2 && static_cast<int>(blockIdx.x) >= A.job0[bi] + A.b[bi].njobs) ++bi;
+  wide_form_tc_body(A.b[bi], &A.xmap[bi], &A.wmap, &A.wlmap, static_cast<int>(blockIdx.x) - A.job0[bi], A.status,
+                    A.spin_limit);
+}
+
+__global__ void __launch_bounds__(kWtThreads, 1)
+    wide_form_tc_table_kernel(const WideFormEntry* __restrict__ E, const int32_t* __restrict__ job0, int nb,
+                              int64_t spin_limit) {
+  pdl_enter();
+  const int bi = table_entry(job0, nb, static_cast<int>(blockIdx.x));
+  const WideFormEntry& e = E[bi];
+  tensormap_acquire(&e.xmap);
+  tensormap_acquire(&e.wmap);
+  tensormap_acquire(&e.wlmap);
+  wide_form_tc_body(e.b, &e.xmap, &e.wmap, &e.wlmap, static_cast<int>(blockIdx.x) - job0[bi], e.b.status,
+                    spin_limit);
+}
+
+__global__ void wide_prep_table_kernel(const WidePrepEntry* __restrict__ E, const int32_t* __restrict__ cta0,
+                                       int nb) {
+  pdl_enter();
+  const int bi = table_entry(cta0, nb, static_cast<int>(blockIdx.x));
+  const WidePrepEntry& e = E[bi];
+  wide_form_prep_at(e.W, e.n, e.WT, e.WTlo,
+                    static_cast<int64_t>(static_cast<int>(blockIdx.x) - cta0[bi]) * blockDim.x + threadIdx.x);
+}
+
 }  // namespace
 
 // The packed engine writes symmetrised upper-triangle partials; the others
@@ -2110,6 +2176,54 @@ bool wide_tc_eligible(const float* X, int64_t ld, int kout) {
          encoder() != nullptr;
 }
 
+namespace {
+
+// The rows of a tile-Gram block: 32-column by kWtRows-row boxes (32-byte
+// atoms of the 128-byte swizzle, the MN-major operand layout).
+bool encode_wt_map(CUtensorMap* m, const WideTcBlock& b) {
+  if (!wide_tc_eligible(b.X, b.ld, b.kout)) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(b.kout), static_cast<cuuint64_t>(b.rows > 0 ? b.rows : 1)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(b.ld) * 4};
+  cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kWtRows)};
+  cuuint32_t es[2] = {1, 1};
+  return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(b.X), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Operands of the formation: 32-column by 128-row boxes, K-major 128-byte swizzle.
+bool encode_wf_map(CUtensorMap* m, const float* p, int64_t inner, int64_t outer, int64_t ld) {
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer > 0 ? outer : 1)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 4};
+  cuuint32_t box[2] = {32, 128};
+  cuuint32_t es[2] = {1, 1};
+  return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool form_block_ok(const WideFormBlock& b) {
+  return wide_tc_eligible(b.X, b.ldx, b.k) && b.kout % 4 == 0 && (reinterpret_cast<uintptr_t>(b.Q) & 15) == 0;
+}
+
+bool form_w_ok(const float* WT, const float* WTlo, int n) {
+  return n % 4 == 0 && wide_tc_eligible(WT, n, n) && wide_tc_eligible(WTlo, n, n);
+}
+
+// Dynamic shared memory above 48 KB, granted once per device and kernel.
+template <typename K>
+cudaError_t grant_smem(K kern, int bytes, int* granted) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev >= 0 && dev < 64 && granted[dev]) return cudaSuccess;
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (err == cudaSuccess && dev >= 0 && dev < 64) granted[dev] = 1;
+  return err;
+}
+
+}  // namespace
+
 cudaError_t launch_wide_gram_tc(const WideTcBlock b[3], double* part, int32_t* status, int64_t spin_limit,
                                 cudaStream_t s) {
   WideTcArgs a;
@@ -2120,30 +2234,61 @@ cudaError_t launch_wide_gram_tc(const WideTcBlock b[3], double* part, int32_t* s
     a.job0[i] = jobs;
     jobs += b[i].njobs;
     if (b[i].njobs == 0) continue;
-    if (!wide_tc_eligible(b[i].X, b[i].ld, b[i].kout)) return cudaErrorInvalidValue;
-    cuuint64_t dims[2] = {static_cast<cuuint64_t>(b[i].kout), static_cast<cuuint64_t>(b[i].rows > 0 ? b[i].rows : 1)};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(b[i].ld) * 4};
-    cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kWtRows)};
-    cuuint32_t es[2] = {1, 1};
-    const CUresult cr = encoder()(&a.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(b[i].X), dims,
-                                  strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    if (!encode_wt_map(&a.map[i], b[i])) return cudaErrorInvalidValue;
   }
   if (jobs == 0) return cudaSuccess;
   a.part = part;
   a.status = status;
   a.spin_limit = spin_limit;
   static int granted[64] = {};
-  int dev = 0;
-  cudaError_t err = cudaGetDevice(&dev);
+  const cudaError_t err = grant_smem(wide_gram_tc_kernel, kWtSmem, granted);
   if (err != cudaSuccess) return err;
-  if (dev < 0 || dev >= 64 || !granted[dev]) {
-    err = cudaFuncSetAttribute(wide_gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWtSmem);
-    if (err != cudaSuccess) return err;
-    if (dev >= 0 && dev < 64) granted[dev] = 1;
-  }
   pdl_launch(wide_gram_tc_kernel, jobs, kWtThreads, kWtSmem, s, a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+bool wide_tc_encode(const WideTcBlock& b, WideTcEntry* e) {
+  std::memset(static_cast<void*>(e), 0, sizeof(*e));
+  e->b = b;
+  return b.part != nullptr && b.status != nullptr && encode_wt_map(&e->map, b);
+}
+
+bool wide_form_encode(const WideFormBlock& b, WideFormEntry* e) {
+  std::memset(static_cast<void*>(e), 0, sizeof(*e));
+  e->b = b;
+  return b.status != nullptr && form_block_ok(b) && form_w_ok(b.WT, b.WTlo, b.n) &&
+         encode_wf_map(&e->xmap, b.X, b.k, b.rows, b.ldx) && encode_wf_map(&e->wmap, b.WT, b.n, b.n, b.n) &&
+         encode_wf_map(&e->wlmap, b.WTlo, b.n, b.n, b.n);
+}
+
+cudaError_t launch_wide_gram_tc_table(const WideTcEntry* e, const int32_t* job0, int nb, int ctas,
+                                      int64_t spin_limit, cudaStream_t s) {
+  if (nb <= 0 || ctas <= 0) return cudaSuccess;
+  if ((reinterpret_cast<uintptr_t>(e) & 63) != 0) return cudaErrorInvalidValue;
+  static int granted[64] = {};
+  const cudaError_t err = grant_smem(wide_gram_tc_table_kernel, kWtSmem, granted);
+  if (err != cudaSuccess) return err;
+  pdl_launch(wide_gram_tc_table_kernel, ctas, kWtThreads, kWtSmem, s, e, job0, nb, spin_limit);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_form_tc_table(const WideFormEntry* e, const int32_t* job0, int nb, int ctas,
+                                      int64_t spin_limit, cudaStream_t s) {
+  if (nb <= 0 || ctas <= 0) return cudaSuccess;
+  if ((reinterpret_cast<uintptr_t>(e) & 63) != 0) return cudaErrorInvalidValue;
+  static int granted[64] = {};
+  const cudaError_t err = grant_smem(wide_form_tc_table_kernel, kWfSmem, granted);
+  if (err != cudaSuccess) return err;
+  pdl_launch(wide_form_tc_table_kernel, ctas, kWtThreads, kWfSmem, s, e, job0, nb, spin_limit);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_prep_table(const WidePrepEntry* e, const int32_t* cta0, int nb, int ctas, cudaStream_t s) {
+  if (nb <= 0 || ctas <= 0) return cudaSuccess;
+  pdl_launch(wide_prep_table_kernel, ctas, 256, 0, s, e, cta0, nb);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -2159,40 +2304,23 @@ cudaError_t launch_wide_form_tc(const WideFormBlock b[3], const float* WT, const
                                 int64_t spin_limit, cudaStream_t s) {
   WideFormArgs a;
   std::memset(&a, 0, sizeof(a));
-  auto encode = [](CUtensorMap* m, const float* p, int64_t inner, int64_t outer, int64_t ld) {
-    cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer > 0 ? outer : 1)};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 4};
-    cuuint32_t box[2] = {32, 128};
-    cuuint32_t es[2] = {1, 1};
-    return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-  };
-  if (n % 4 != 0 || !wide_tc_eligible(WT, n, n) || !wide_tc_eligible(WTlo, n, n)) return cudaErrorInvalidValue;
-  if (!encode(&a.wmap, WT, n, n, n) || !encode(&a.wlmap, WTlo, n, n, n)) return cudaErrorInvalidValue;
+  if (!form_w_ok(WT, WTlo, n)) return cudaErrorInvalidValue;
+  if (!encode_wf_map(&a.wmap, WT, n, n, n) || !encode_wf_map(&a.wlmap, WTlo, n, n, n)) return cudaErrorInvalidValue;
   int jobs = 0;
   for (int i = 0; i < 3; ++i) {
     a.b[i] = b[i];
     a.job0[i] = jobs;
     jobs += b[i].njobs;
     if (b[i].njobs == 0) continue;
-    if (!wide_tc_eligible(b[i].X, b[i].ldx, b[i].k) || b[i].kout % 4 != 0 ||
-        (reinterpret_cast<uintptr_t>(b[i].Q) & 15) != 0)
-      return cudaErrorInvalidValue;
-    if (!encode(&a.xmap[i], b[i].X, b[i].k, b[i].rows, b[i].ldx)) return cudaErrorInvalidValue;
+    if (!form_block_ok(b[i])) return cudaErrorInvalidValue;
+    if (!encode_wf_map(&a.xmap[i], b[i].X, b[i].k, b[i].rows, b[i].ldx)) return cudaErrorInvalidValue;
   }
   if (jobs == 0) return cudaSuccess;
   a.status = status;
   a.spin_limit = spin_limit;
   static int granted[64] = {};
-  int dev = 0;
-  cudaError_t err = cudaGetDevice(&dev);
+  const cudaError_t err = grant_smem(wide_form_tc_kernel, kWfSmem, granted);
   if (err != cudaSuccess) return err;
-  if (dev < 0 || dev >= 64 || !granted[dev]) {
-    err = cudaFuncSetAttribute(wide_form_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWfSmem);
-    if (err != cudaSuccess) return err;
-    if (dev >= 0 && dev < 64) granted[dev] = 1;
-  }
   pdl_launch(wide_form_tc_kernel, jobs, kWtThreads, kWfSmem, s, a);
   count_launches(1);
   return cudaGetLastError();

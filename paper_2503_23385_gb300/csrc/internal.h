@@ -127,9 +127,11 @@ struct Plan {
   double* sigw = nullptr;                     // 2n: unsorted singular values, FP32-sweep column norms
   // batched calls: Gram partials written per (pass, block) and their format
   // (0 FP64 upper triangle, 1 FP64 P with G = (P + P^T) / 2 from the general
-  // tensor-core engine, 2 float-float pairs from the packed engine)
+  // tensor-core engine, 2 float-float pairs from the packed engine, 3 FP64
+  // 128 x 128 tiles from the tile Gram)
   int gcount[2][3] = {{0, 0, 0}, {0, 0, 0}};
   int gsym[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  int64_t gcap[3] = {0, 0, 0};  // doubles of gpart[b]
 };
 
 // Batched execution (figaro_batch_join): every instance's plan sits in device
@@ -277,6 +279,8 @@ struct WideTcBlock {
   int64_t split_rows;
   int njobs;
   int64_t pbase;
+  double* part = nullptr;      // table launches: the block's partials (job j at part + j x 128^2)
+  int32_t* status = nullptr;   // table launches: the block's device status word
 };
 bool wide_tc_eligible(const float* X, int64_t ld, int kout);
 
@@ -292,12 +296,46 @@ struct WideFormBlock {
   const int64_t* rows_dev;
   float* Q;  // rows x kout, leading dimension kout
   int ctiles, splits, rt_per_split, njobs;
+  const float* WT = nullptr;    // table launches: W^T and its lo parts (n x n) of the block's instance
+  const float* WTlo = nullptr;
+  int n = 0;
+  int32_t* status = nullptr;    // table launches: the block's device status word
 };
 cudaError_t launch_wide_form_prep(const float* W, int n, float* WT, float* WTlo, cudaStream_t s);
+
+// Table launches of the two wide tensor-core kernels (batched calls): one
+// launch covers any number of blocks, each with its own tensor maps, status
+// word and partials, read from device memory (64-byte aligned entries, copied
+// there before the launch); job0[i] = the first CTA of entry i, job0[nb] = all
+// CTAs.  The W^T preparation of many instances runs the same way.
+struct alignas(64) WideTcEntry {
+  CUtensorMap map;
+  WideTcBlock b;
+};
+struct alignas(64) WideFormEntry {
+  CUtensorMap xmap, wmap, wlmap;
+  WideFormBlock b;
+};
+struct WidePrepEntry {
+  const float* W;
+  float* WT;
+  float* WTlo;
+  int n;
+};
+bool wide_tc_encode(const WideTcBlock& b, WideTcEntry* e);      // false: not addressable by TMA
+bool wide_form_encode(const WideFormBlock& b, WideFormEntry* e);
+cudaError_t launch_wide_gram_tc_table(const WideTcEntry* e, const int32_t* job0, int nb, int ctas,
+                                      int64_t spin_limit, cudaStream_t s);
+cudaError_t launch_wide_form_tc_table(const WideFormEntry* e, const int32_t* job0, int nb, int ctas,
+                                      int64_t spin_limit, cudaStream_t s);
+cudaError_t launch_wide_prep_table(const WidePrepEntry* e, const int32_t* cta0, int nb, int ctas, cudaStream_t s);
 // Narrow mixed plans with n in (64, 128]: the A-tail block of pass 2 on the
 // tensor cores (wide.cu); the partials of block 1 in the reduce's format 3.
 bool narrow_q_tc(const Plan& p);
-int narrow_q_tc_splits(const Plan& p, int64_t* split_rows);
+// rows_min: the fewest rows of a split (rounded up to 1024)
+int narrow_q_tc_splits(const Plan& p, int64_t rows_min, int64_t* split_rows);
+// the formation and tile Gram blocks of such a plan (splits of >= rows_min rows)
+void narrow_q_tc_blocks(const Plan& p, int64_t rows_min, WideFormBlock* fb, WideTcBlock* tb);
 cudaError_t launch_narrow_q_gram_tc(const Plan& p, int* count, cudaStream_t s);
 cudaError_t launch_wide_form_tc(const WideFormBlock b[3], const float* WT, const float* WTlo, int n, int32_t* status,
                                 int64_t spin_limit, cudaStream_t s);

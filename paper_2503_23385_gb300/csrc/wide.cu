@@ -1357,48 +1357,54 @@ cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s) {
 // 128 tile pair; partials [splits][128][128] in p.gpart[1], format 3 of the
 // reduce).
 bool narrow_q_tc(const Plan& p) {
-  // (the partial buffer of block 1, ggrid[1] x n^2 doubles, must hold at least one 128 x 128 tile)
+  // (the partial buffer of block 1 must hold at least one 128 x 128 tile)
   return p.mixed && !p.wide && p.n > 64 && p.n <= kWideTcTile && p.n % 4 == 0 && p.n1 % 4 == 0 && p.wq[1] &&
-         p.wt && p.t[0].m > 0 &&
-         static_cast<int64_t>(p.ggrid[1]) * p.n * p.n >= static_cast<int64_t>(kWideTcTile) * kWideTcTile &&
+         p.wt && p.t[0].m > 0 && p.gcap[1] >= static_cast<int64_t>(kWideTcTile) * kWideTcTile &&
          wide_tc_eligible(static_cast<const float*>(p.t[0].tail), p.n1, p.n1);
 }
 
-int narrow_q_tc_splits(const Plan& p, int64_t* split_rows) {
+int narrow_q_tc_splits(const Plan& p, int64_t rows_min, int64_t* split_rows) {
   const int64_t rows = p.t[0].m;
-  // the partial buffer of block 1 holds ggrid[1] x n^2 doubles
-  int64_t cap = static_cast<int64_t>(p.ggrid[1]) * p.n * p.n / (kWideTcTile * kWideTcTile);
-  int64_t splits = (rows + 1023) / 1024;
+  const int64_t per = rows_min > 1024 ? rows_min : 1024;
+  const int64_t cap = p.gcap[1] / (static_cast<int64_t>(kWideTcTile) * kWideTcTile);
+  int64_t splits = (rows + per - 1) / per;
   if (splits > 2 * static_cast<int64_t>(p.num_sms)) splits = 2 * static_cast<int64_t>(p.num_sms);
   if (splits > cap) splits = cap;
   if (splits < 1) splits = 1;
   int64_t sr = (rows + splits - 1) / splits;
-  sr = (sr + 63) / 64 * 64;
+  sr = (sr + 127) / 128 * 128;  // whole row tiles of the formation
   *split_rows = sr;
   return static_cast<int>((rows + sr - 1) / sr);
 }
 
-cudaError_t launch_narrow_q_gram_tc(const Plan& p, int* count, cudaStream_t s) {
+void narrow_q_tc_blocks(const Plan& p, int64_t rows_min, WideFormBlock* fb, WideTcBlock* tb) {
   const int n = p.n;
   const int64_t rows = p.t[0].m;
   const float* X = static_cast<const float*>(p.t[0].tail);
-  cudaError_t err = launch_wide_form_prep(p.Wf, n, p.wt, p.wtlo, s);
+  int64_t sr = 0;
+  const int splits = narrow_q_tc_splits(p, rows_min, &sr);
+  // formation: one CTA per split of sr / 128 row tiles (the Gram's splits)
+  const int rps = static_cast<int>(sr / 128);
+  *fb = WideFormBlock{X, p.n1, p.n1, n, 0, rows, nullptr, static_cast<float*>(p.wq[1]), 1, splits, rps, splits};
+  fb->WT = p.wt;
+  fb->WTlo = p.wtlo;
+  fb->n = n;
+  fb->status = &p.hdr->status;
+  *tb = WideTcBlock{static_cast<const float*>(p.wq[1]), n, n, rows, nullptr, 1, splits, sr, splits, 0};
+  tb->part = p.gpart[1];
+  tb->status = &p.hdr->status;
+}
+
+cudaError_t launch_narrow_q_gram_tc(const Plan& p, int* count, cudaStream_t s) {
+  cudaError_t err = launch_wide_form_prep(p.Wf, p.n, p.wt, p.wtlo, s);
   if (err != cudaSuccess) return err;
   WideFormBlock fb[3] = {};
-  const int nrt = static_cast<int>((rows + 127) / 128);
-  int fsplits = nrt < 2 * p.num_sms ? nrt : 2 * p.num_sms;
-  if (fsplits < 1) fsplits = 1;
-  const int rps = (nrt + fsplits - 1) / fsplits;
-  fsplits = (nrt + rps - 1) / rps;
-  fb[0] = WideFormBlock{X, p.n1, p.n1, n, 0, rows, nullptr, static_cast<float*>(p.wq[1]), 1, fsplits, rps, fsplits};
-  err = launch_wide_form_tc(fb, p.wt, p.wtlo, n, &p.hdr->status, p.spin_limit, s);
-  if (err != cudaSuccess) return err;
-  int64_t sr = 0;
-  const int splits = narrow_q_tc_splits(p, &sr);
   WideTcBlock tb[3] = {};
-  tb[0] = WideTcBlock{static_cast<const float*>(p.wq[1]), n, n, rows, nullptr, 1, splits, sr, splits, 0};
+  narrow_q_tc_blocks(p, 0, &fb[0], &tb[0]);
+  err = launch_wide_form_tc(fb, p.wt, p.wtlo, p.n, &p.hdr->status, p.spin_limit, s);
+  if (err != cudaSuccess) return err;
   err = launch_wide_gram_tc(tb, p.gpart[1], &p.hdr->status, p.spin_limit, s);
-  *count = splits;
+  *count = tb[0].njobs;
   return err;
 }
 
