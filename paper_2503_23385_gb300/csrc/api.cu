@@ -484,7 +484,12 @@ struct UploadChunk {
 
 __global__ void upload_kernel(const __grid_constant__ UploadChunk c) {
   pdl_enter();
-  for (int i = threadIdx.x; i < c.bytes; i += blockDim.x) c.dst[i] = c.data[i];
+  // 16-byte words where the destination allows, then the bytes of the tail
+  const int nv = (reinterpret_cast<uintptr_t>(c.dst) & 15) == 0 ? c.bytes / 16 : 0;
+  const uint4* src = reinterpret_cast<const uint4*>(c.data);
+  uint4* dst = reinterpret_cast<uint4*>(c.dst);
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) dst[i] = src[i];
+  for (int i = 16 * nv + static_cast<int>(threadIdx.x); i < c.bytes; i += blockDim.x) c.dst[i] = c.data[i];
 }
 
 // Bytes of the batch area (plans, outputs, job lists) for `count` instances.
@@ -634,7 +639,12 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
         calls[i].p.gcount[pass - 1][b] = ctas;
         calls[i].p.gsym[pass - 1][b] = 0;
       }
-    reduce.add(i, 0, (p.n * p.n + 31) / 32);
+    // the reduce: a warp per 32 outputs when every block has few partials
+    int most = 0;
+    for (int q = 0; q < 2; ++q)
+      for (int b = 0; b < 3; ++b) most = std::max(most, p.gcount[q][b] > 0 ? p.gcount[q][b] : p.ggrid[b]);
+    if (most <= 64) reduce.add(i, 1, (p.n * p.n + 32 * kReduceWarps - 1) / (32 * kReduceWarps));
+    else reduce.add(i, 0, (p.n * p.n + 31) / 32);
     JobList* dl[3] = {dense1, dense2, dense3};
     for (int step = 1; step <= 3; ++step) {
       if (step == 3 && !outs[i].sigma) continue;

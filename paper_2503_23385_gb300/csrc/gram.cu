@@ -222,21 +222,25 @@ struct ReduceArgs {
   double* G;
 };
 
-constexpr int kReduceWarps = 16;
 
 // G = sum of the three blocks' partials in a fixed order (deterministic).
-// A block owns 32 consecutive outputs (one per lane); its warps interleave
-// over the partials.  Each thread issues the loads of up to five partials of
-// every block before its first addition (the loads are latency-bound).
-// Partials of the packed tensor-core engine are float-float pairs and are
-// summed in float-float (FP64 arithmetic is slow on this GPU); the others are
-// FP64.  Warp 0 adds the warps' sums.
+// Two layouts: with many partials (kPerWarp false) a block owns 32
+// consecutive outputs (one per lane) and its warps interleave over the
+// partials, warp 0 adding the warps' sums; with few (batched calls, a few
+// dozen per block) every warp owns 32 outputs and sums all their partials
+// itself, so that a block covers 16 times as many outputs.  Each thread
+// issues the loads of up to five partials of every block before its first
+// addition (the loads are latency-bound).  Partials of the packed
+// tensor-core engine are float-float pairs and are summed in float-float
+// (FP64 arithmetic is slow on this GPU); the others are FP64.
+template <bool kPerWarp>
 __device__ __forceinline__ void gram_reduce_body(const ReduceArgs& a, int bid) {
-  __shared__ double sd[kReduceWarps][33];
-  __shared__ float2 sf[kReduceWarps][33];
+  __shared__ double sd[kPerWarp ? 1 : kReduceWarps][33];
+  __shared__ float2 sf[kPerWarp ? 1 : kReduceWarps][33];
   constexpr int kPer = 5;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int e = bid * 32 + lane;
+  const int e = (kPerWarp ? bid * kReduceWarps + warp : bid) * 32 + lane;
+  const int cfirst = kPerWarp ? 0 : warp, cstep = kPerWarp ? 1 : kReduceWarps;
   const bool ok = e < a.n * a.n;
   const int i = ok ? e / a.n : 0, j = ok ? e - (e / a.n) * a.n : 0;
   const int lo = i < j ? i : j, hi = i < j ? j : i;
@@ -262,13 +266,13 @@ __device__ __forceinline__ void gram_reduce_body(const ReduceArgs& a, int bid) {
   }
   double t[4] = {0.0, 0.0, 0.0, 0.0};
   float fh = 0.f, fl = 0.f;
-  for (int c0 = 0; c0 < maxc; c0 += kPer * kReduceWarps) {
+  for (int c0 = 0; c0 < maxc; c0 += kPer * cstep) {
     unsigned long long v[3][kPer], w[3][kPer];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
-        const int c = c0 + warp + k * kReduceWarps;
+        const int c = c0 + cfirst + k * cstep;
         const bool live = c < cnt[b];
         v[b][k] = live ? p0[b][c * stride[b]] : 0ull;
         w[b][k] = live && a.sym[b] == 1 ? p1[b][c * stride[b]] : 0ull;
@@ -284,11 +288,15 @@ __device__ __forceinline__ void gram_reduce_body(const ReduceArgs& a, int bid) {
           two_sum(fh, q.x, s_, e_);
           fh = s_;
           fl = __fadd_rn(fl, __fadd_rn(e_, q.y));
-        } else if (c0 + warp + k * kReduceWarps < cnt[b]) {
+        } else if (c0 + cfirst + k * cstep < cnt[b]) {
           const double d = __longlong_as_double(static_cast<long long>(v[b][k]));
           t[k & 3] += a.sym[b] == 1 ? 0.5 * (d + __longlong_as_double(static_cast<long long>(w[b][k]))) : d;
         }
       }
+  }
+  if (kPerWarp) {
+    if (ok) a.G[e] = static_cast<double>(fh) + static_cast<double>(fl) + (any64 ? (t[0] + t[1]) + (t[2] + t[3]) : 0.0);
+    return;
   }
   sd[warp][lane] = any64 ? (t[0] + t[1]) + (t[2] + t[3]) : 0.0;
   sf[warp][lane] = make_float2(fh, fl);
@@ -316,7 +324,7 @@ __device__ __forceinline__ void gram_reduce_body(const ReduceArgs& a, int bid) {
 
 __global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_kernel(ReduceArgs a) {
   pdl_enter();
-  gram_reduce_body(a, blockIdx.x);
+  gram_reduce_body<false>(a, blockIdx.x);
 }
 
 // Geometry of one Gram block: kout padded to 4, the upper 4 x 4 register
@@ -399,7 +407,8 @@ __host__ __device__ inline ReduceArgs reduce_args_of(const Plan& p, int pass) {
 
 // ---- batched forms (CUDA-core Gram): Gram jobs are (instance, block) with
 // aux = block and p.ggrid[block] CTAs; reduce jobs are instances with
-// ceil(n^2 / 32) CTAs
+// aux = 1 and ceil(n^2 / 512) CTAs (a warp per 32 outputs) when every block
+// has few partials, else aux = 0 and ceil(n^2 / 32) CTAs
 template <typename T, int TPT>
 __global__ void __launch_bounds__(kGramThreads) gram_batched(BatchDev bd, BatchJobs J, int pass) {
   pdl_enter();
@@ -420,7 +429,8 @@ __global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_batched(BatchDe
   const int j = batch_job(J, blockIdx.x);
   if (threadIdx.x == 0) s_r = reduce_args_of(bd.plans[J.inst[j]], pass);
   __syncthreads();
-  gram_reduce_body(s_r, blockIdx.x - J.first[j]);
+  if (J.aux[j]) gram_reduce_body<true>(s_r, blockIdx.x - J.first[j]);  // few partials: a warp per 32 outputs
+  else gram_reduce_body<false>(s_r, blockIdx.x - J.first[j]);
 }
 
 template <typename T>

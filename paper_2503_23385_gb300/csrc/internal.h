@@ -23,6 +23,7 @@ constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;
 constexpr int kGramThreads = 256;
 constexpr int kGramTileRows = 64;
+constexpr int kReduceWarps = 16;  // warps of a Gram-reduce CTA
 
 constexpr int kMaxJacobiBlocks = 160;  // column blocks of the wide Jacobi (n <= 512 in blocks of >= 4)
 
