@@ -398,6 +398,7 @@ figaro_status run_factor(Call& c, double* R_dev, int64_t ldr) {
   FIGARO_TRY(c.join_staging());  // the features are read from here on
   FIGARO_TRY(launch_ht_carry(c.p, c.s));
   FIGARO_TRY(c.mark(2));
+  ht_plan_gram1(c.p);  // pass 1 of the tail blocks inside the head/tail stream, where it applies
   FIGARO_TRY(launch_ht_main(c.p, c.s));
   FIGARO_TRY(c.mark(3));
   FIGARO_TRY(launch_gram_pass(c.p, 1, c.s));

@@ -538,6 +538,14 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     a.tile_rows = gram_tile_rows(a.k, a.kout, a.W != nullptr, elem);
     a.part = p.gpart[b];
     int grid = p.ggrid[b];
+    if (pass == 1 && b >= 1 && p.ht_gram[b - 1] > 0) {  // partials written by the head/tail stream
+      r.part[b] = p.gpart[b];
+      r.count[b] = p.ht_gram[b - 1];
+      r.kout[b] = a.kout;
+      r.off[b] = b == 2 ? p.n1 : 0;
+      r.sym[b] = 2;
+      continue;
+    }
     if (pass == 2 && b == 1 && p.gram_engine != 1 && narrow_q_tc(p)) {  // Q written, then the tile Gram
       int count = 0;
       const cudaError_t err = launch_narrow_q_gram_tc(p, &count, s);

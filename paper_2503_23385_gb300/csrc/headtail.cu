@@ -68,6 +68,8 @@ struct HtTable {
   uint32_t* cflag;  // chunks
   double* piece;    // chunks x n
   double* carry;    // chunks x n
+  double* gram;     // pass-1 Gram partials of the tails (null: not accumulated here): per CTA of the
+                    // table n x n slots, upper triangle, a float-float pair (hi, lo) in each
 };
 
 struct HtArgs {
@@ -435,6 +437,16 @@ __device__ __forceinline__ void tma_gather4(void* dst, const CUtensorMap* map, i
 __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
+// D += A B for one m16n8k8 TF32 warp MMA (A 16 x 8 row-major fragments a,
+// B 8 x 8 column-major fragments b0, b1; FP32 accumulators).
+__device__ __forceinline__ void mma_m16n8k8_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kHtConsumers) : "memory"); }
 
 // Running sum of a run: float-float (hi, lo) on the mixed path, one double
@@ -612,6 +624,17 @@ __device__ __forceinline__ void ht_stream_body(const CUtensorMap* tm, const HtAr
   }
   Tc* HD = static_cast<Tc*>(a.head);
   Tc* TL = static_cast<Tc*>(T.tail);
+  // Pass 1 of the Gram of this table's tails, when T.gram is set (FP32, 8
+  // or 16 columns): after a tile's tails are written they also replace its
+  // rows in the stage, and every consumer warp adds T_k^T T_k of its 8-row
+  // steps k of the tile in 3 x TF32 (hi x hi + hi x lo + lo x hi) with warp
+  // MMAs (m16n8k8; the A and B fragments of T^T T are the same four values
+  // per lane), accumulating its 16 x 16 partial in FP32 over the CTA's
+  // tiles.  The stage is released after the next tile's first barrier, when
+  // every thread is past it.
+  constexpr bool kGramOk = V == 4 && sizeof(Tin) == 4 && sizeof(Tc) == 4;
+  const bool fuse = kGramOk && T.gram != nullptr;
+  float gd0[4] = {0.f, 0.f, 0.f, 0.f}, gd1[4] = {0.f, 0.f, 0.f, 0.f};  // G[:, 0:8], G[:, 8:16] fragments
   __shared__ int s_failed;
   if (ct == 0) s_failed = 0;
   for (int u = 0; u < ntiles; ++u) {
@@ -623,6 +646,7 @@ __device__ __forceinline__ void ht_stream_body(const CUtensorMap* tm, const HtAr
     }
     consumers_sync();
     if (s_failed) break;
+    if (fuse && u > 0 && ct == 0) mbar_arrive(&empty[(u - 1) % kHtStages]);  // tile u - 1's Gram rows are read
     const unsigned char* sb = sm + st * L.stage_bytes;
     const Tin* xs = reinterpret_cast<const Tin*>(sb + L.x);
     const int64_t r0 = R0 + static_cast<int64_t>(u) * TR;
@@ -748,6 +772,7 @@ __device__ __forceinline__ void ht_stream_body(const CUtensorMap* tm, const HtAr
           loc[k] += xv[k];
         }
         store4(TL + (r0 + r) * n + cg * 4, out);
+        if (fuse) store4(const_cast<Tc*>(reinterpret_cast<const Tc*>(xrow)) + r * n, out);  // (this thread's own row slice)
         const int32_t slot = hs_s[r];
         if (slot >= 0) {
           Tc* hrow = HD + static_cast<int64_t>(slot) * a.ld_head;
@@ -834,12 +859,67 @@ __device__ __forceinline__ void ht_stream_body(const CUtensorMap* tm, const HtAr
       }
     }
     consumers_sync();
-    if (ct == 0) mbar_arrive(&empty[st]);
+    if (fuse) {
+      const float* tt = reinterpret_cast<const float*>(sb + L.x);  // the tile's tails, rows of n
+      const int gq = (ct & 31) >> 2, tq = ct & 3;
+      const int ksteps = (cnt + 7) >> 3;
+      for (int ks = ct >> 5; ks < ksteps; ks += kHtConsumers / 32) {
+        const int ra = ks * 8 + tq, rb = ra + 4;
+        const float v[4] = {ra < cnt ? tt[ra * n + gq] : 0.f, (n > 8 && ra < cnt) ? tt[ra * n + gq + 8] : 0.f,
+                            rb < cnt ? tt[rb * n + gq] : 0.f, (n > 8 && rb < cnt) ? tt[rb * n + gq + 8] : 0.f};
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          h[k] = __float_as_uint(v[k]) & 0xffffe000u;  // TF32 hi: truncation
+          l[k] = (__float_as_uint(__fsub_rn(v[k], __uint_as_float(h[k]))) + 0x1000u) & 0xffffe000u;  // lo, rounded
+        }
+        mma_m16n8k8_tf32(gd0, l, h[0], h[2]);
+        mma_m16n8k8_tf32(gd0, h, l[0], l[2]);
+        mma_m16n8k8_tf32(gd0, h, h[0], h[2]);
+        if (n > 8) {
+          mma_m16n8k8_tf32(gd1, l, h[1], h[3]);
+          mma_m16n8k8_tf32(gd1, h, l[1], l[3]);
+          mma_m16n8k8_tf32(gd1, h, h[1], h[3]);
+        }
+      }
+    } else if (ct == 0) {
+      mbar_arrive(&empty[st]);
+    }
+  }
+  if (fuse && !s_failed) {
+    // the row groups' sums through the stage area (every tile has been
+    // consumed: no copy is in flight), then the CTA's partial
+    consumers_sync();
+    float* red = reinterpret_cast<float*>(sm) + (ct >> 5) * 256;  // [warp][16][16]
+    const int gq = (ct & 31) >> 2, tq = ct & 3;
+    red[gq * 16 + 2 * tq] = gd0[0];
+    red[gq * 16 + 2 * tq + 1] = gd0[1];
+    red[(gq + 8) * 16 + 2 * tq] = gd0[2];
+    red[(gq + 8) * 16 + 2 * tq + 1] = gd0[3];
+    red[gq * 16 + 8 + 2 * tq] = gd1[0];
+    red[gq * 16 + 8 + 2 * tq + 1] = gd1[1];
+    red[(gq + 8) * 16 + 8 + 2 * tq] = gd1[2];
+    red[(gq + 8) * 16 + 8 + 2 * tq + 1] = gd1[3];
+    consumers_sync();
+    const float* all = reinterpret_cast<const float*>(sm);
+    float2* part = reinterpret_cast<float2*>(T.gram + static_cast<int64_t>(cb) * n * n);
+    for (int e = ct; e < n * n; e += kHtConsumers) {
+      const int i = e / n, j = e - (e / n) * n;
+      if (i > j) continue;  // (upper triangle)
+      float hh = 0.f, ll = 0.f;
+      for (int w = 0; w < kHtConsumers / 32; ++w) {
+        float s_, e_;
+        two_sum(hh, all[w * 256 + i * 16 + j], s_, e_);
+        hh = s_;
+        ll = __fadd_rn(ll, e_);
+      }
+      part[i * n + j] = make_float2(hh, ll);
+    }
   }
 }
 
 template <typename Tin, typename Tc, int V>
-__global__ void __launch_bounds__(kHtStreamThreads)
+__global__ void __launch_bounds__(kHtStreamThreads, 3)  // three CTAs per SM (shared memory allows three)
     ht_stream_kernel(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1, HtArgs a,
                      int g0, int g1, int64_t spin_limit) {
   pdl_enter();
@@ -877,12 +957,10 @@ bool row_gather_map(CUtensorMap* map, const HtTable& T, int es_in) {
   return r == CUDA_SUCCESS;
 }
 
+// Shared memory of the stream kernel for the tables of `a` (granted above 48
+// KB once per device and size) and its CTAs per SM.
 template <typename Tin, typename Tc, int V>
-cudaError_t launch_typed_main(HtArgs a, int num_sms, int64_t spin_limit, cudaStream_t s) {
-  CUtensorMap maps[2];
-  std::memset(maps, 0, sizeof(maps));
-  for (int t = 0; t < 2; ++t)
-    a.t[t].gather = a.t[t].chunks > 0 && row_gather_map(&maps[t], a.t[t], static_cast<int>(sizeof(Tin)));
+cudaError_t ht_stream_setup(const HtArgs& a, int* smem_out, int* occ_out) {
   int smem = 0;
   for (int t = 0; t < 2; ++t)
     if (a.t[t].chunks > 0) {
@@ -907,15 +985,36 @@ cudaError_t launch_typed_main(HtArgs a, int num_sms, int64_t spin_limit, cudaStr
     if (occ < 1) occ = 1;
     if (cache) per_sm[dev] = occ;
   }
-  // CTAs per table in proportion to its chunks, at most one per chunk
+  *smem_out = smem;
+  *occ_out = occ;
+  return cudaSuccess;
+}
+
+// CTAs per table in proportion to its chunks, at most one per chunk.
+void ht_split(const HtArgs& a, int G, int* g0_out, int* g1_out) {
   const int c0 = a.t[0].chunks, c1 = a.t[1].chunks;
-  const int G = num_sms * occ;
   int g0 = c0 > 0 ? static_cast<int>((static_cast<int64_t>(G) * c0 + (c0 + c1) - 1) / (c0 + c1)) : 0;
   if (c0 > 0 && g0 < 1) g0 = 1;
   if (g0 > c0) g0 = c0;
   int g1 = c1 > 0 ? G - g0 : 0;
   if (c1 > 0 && g1 < 1) g1 = 1;
   if (g1 > c1) g1 = c1;
+  *g0_out = g0;
+  *g1_out = g1;
+}
+
+// grid: the CTAs per table planned by ht_plan_gram1 (both 0: split here)
+template <typename Tin, typename Tc, int V>
+cudaError_t launch_typed_main(HtArgs a, int num_sms, const int grid[2], int64_t spin_limit, cudaStream_t s) {
+  CUtensorMap maps[2];
+  std::memset(maps, 0, sizeof(maps));
+  for (int t = 0; t < 2; ++t)
+    a.t[t].gather = a.t[t].chunks > 0 && row_gather_map(&maps[t], a.t[t], static_cast<int>(sizeof(Tin)));
+  int smem = 0, occ = 0;
+  const cudaError_t err = ht_stream_setup<Tin, Tc, V>(a, &smem, &occ);
+  if (err != cudaSuccess) return err;
+  int g0 = grid[0], g1 = grid[1];
+  if (g0 + g1 == 0) ht_split(a, num_sms * occ, &g0, &g1);
   if (g0 + g1 == 0) return cudaSuccess;
   pdl_launch(ht_stream_kernel<Tin, Tc, V>, g0 + g1, kHtStreamThreads, smem, s, maps[0], maps[1], a, g0, g1, spin_limit);
   count_launches(1);
@@ -1071,28 +1170,62 @@ cudaError_t launch_ht_carry(const Plan& p, cudaStream_t s) {
                  : launch_typed_carry<float, double>(a, grid, ncols, s);
 }
 
+// The 4-column path needs both tables' widths to be 4 x a power of two <=
+// 128 and 16-byte aligned tail rows.
+static bool ht_use_v4(const HtArgs& a) {
+  bool v4 = true;
+  for (int t = 0; t < 2; ++t)
+    if (a.t[t].chunks > 0) v4 = v4 && ht_v4_ok(a.t[t]);
+  return v4;
+}
+
 cudaError_t launch_ht_main(const Plan& p, cudaStream_t s) {
-  const HtArgs a = make_args(p);
+  HtArgs a = make_args(p);
   const int grid = a.t[0].chunks + a.t[1].chunks;
   if (grid == 0) return cudaSuccess;
   const bool in64 = p.t[0].in_f64 != 0;
   const int sms = p.num_sms;
   const int64_t sl = p.spin_limit;
-  // the 4-column path needs both tables' widths to be 4 x a power of two <= 128
-  // and 16-byte aligned tail rows
-  bool v4 = true;
-  for (int t = 0; t < 2; ++t) {
-    if (a.t[t].chunks == 0) continue;
-    const int n = a.t[t].n, cg = n / 4;
-    v4 = v4 && n % 4 == 0 && cg >= 1 && cg <= 32 && (cg & (cg - 1)) == 0 &&
-         (reinterpret_cast<uintptr_t>(a.t[t].tail) & 15u) == 0;
+  const bool v4 = ht_use_v4(a);
+  const int* g = p.ht_grid;
+  if (p.ht_gram[0] > 0 || p.ht_gram[1] > 0) {  // (planned for the FP32 4-column kernel only)
+    if (in64 || !p.mixed || !v4) return cudaErrorInvalidValue;
+    for (int t = 0; t < 2; ++t) a.t[t].gram = p.ht_gram[t] > 0 ? p.gpart[1 + t] : nullptr;
   }
   if (in64) {
-    if (p.mixed) return v4 ? launch_typed_main<double, float, 4>(a, sms, sl, s) : launch_typed_main<double, float, 1>(a, sms, sl, s);
-    return v4 ? launch_typed_main<double, double, 4>(a, sms, sl, s) : launch_typed_main<double, double, 1>(a, sms, sl, s);
+    if (p.mixed) return v4 ? launch_typed_main<double, float, 4>(a, sms, g, sl, s) : launch_typed_main<double, float, 1>(a, sms, g, sl, s);
+    return v4 ? launch_typed_main<double, double, 4>(a, sms, g, sl, s) : launch_typed_main<double, double, 1>(a, sms, g, sl, s);
   }
-  if (p.mixed) return v4 ? launch_typed_main<float, float, 4>(a, sms, sl, s) : launch_typed_main<float, float, 1>(a, sms, sl, s);
-  return v4 ? launch_typed_main<float, double, 4>(a, sms, sl, s) : launch_typed_main<float, double, 1>(a, sms, sl, s);
+  if (p.mixed) return v4 ? launch_typed_main<float, float, 4>(a, sms, g, sl, s) : launch_typed_main<float, float, 1>(a, sms, g, sl, s);
+  return v4 ? launch_typed_main<float, double, 4>(a, sms, g, sl, s) : launch_typed_main<float, double, 1>(a, sms, g, sl, s);
+}
+
+void ht_plan_gram1(Plan& p) {
+  p.ht_grid[0] = p.ht_grid[1] = 0;
+  p.ht_gram[0] = p.ht_gram[1] = 0;
+  if (!p.mixed || p.t[0].in_f64 || p.gram_engine != 0 || p.wide) return;  // (0: the automatic engine)
+  const HtArgs a = make_args(p);
+  if (a.t[0].chunks + a.t[1].chunks == 0 || !ht_use_v4(a)) return;
+  bool any = false;
+  for (int t = 0; t < 2; ++t) {
+    const int n = a.t[t].n;
+    any = any || (a.t[t].chunks > 0 && (n == 8 || n == 16));
+  }
+  if (!any) return;
+  int smem = 0, occ = 0;
+  if (ht_stream_setup<float, float, 4>(a, &smem, &occ) != cudaSuccess) return;
+  int g[2] = {0, 0};
+  ht_split(a, p.num_sms * occ, &g[0], &g[1]);
+  for (int t = 0; t < 2; ++t) {
+    const int n = a.t[t].n;
+    if (a.t[t].chunks > 0 && (n == 8 || n == 16) && p.gpart[1 + t] &&
+        static_cast<int64_t>(g[t]) * n * n <= p.gcap[1 + t])
+      p.ht_gram[t] = g[t];
+  }
+  if (p.ht_gram[0] > 0 || p.ht_gram[1] > 0) {
+    p.ht_grid[0] = g[0];
+    p.ht_grid[1] = g[1];
+  }
 }
 
 }  // namespace figaro

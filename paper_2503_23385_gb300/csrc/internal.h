@@ -94,6 +94,11 @@ struct Plan {
   int report_rank = 0;          // leading columns whose drop raises FIGARO_ERR_RANK_DEFICIENT (0: none)
   int shifted = 0;              // shifted CholeskyQR3: shift G1, then a third Gram pass
   int presorted = 0;            // the tables are in key order: no radix sort (identity permutation)
+  // pass 1 of the tail blocks inside the head/tail stream (ht_plan_gram1):
+  // the stream's CTAs per table, and per table the number of float-float
+  // Gram partials of its tails those CTAs write (0: the Gram pass reads the tails)
+  int ht_grid[2] = {0, 0};
+  int ht_gram[2] = {0, 0};
   int64_t lut_size = 0;         // entries of each table's key lookup table
   DevHeader* hdr = nullptr;
   void* head = nullptr;         // m1 x n slots, compute type
@@ -217,6 +222,10 @@ cudaError_t launch_reset(const Plan& p, cudaStream_t s);
 cudaError_t launch_grouping(const Plan& p, cudaStream_t s);
 cudaError_t launch_ht_carry(const Plan& p, cudaStream_t s);
 cudaError_t launch_ht_main(const Plan& p, cudaStream_t s);
+// Decides, before launch_ht_main, which tables' pass-1 Gram partials the
+// head/tail stream accumulates (mixed path, FP32 tables of 8 or 16
+// columns on the 4-column consumers, automatic Gram engine).
+void ht_plan_gram1(Plan& p);
 cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s);
 cudaError_t launch_chol_first(const Plan& p, cudaStream_t s);
 // Shifted CholeskyQR3 between its second and third passes: R1 = R (the
