@@ -127,8 +127,9 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
       if (sz > most) most = sz;
     }
     // narrow mixed plans with n in (64, 128]: room for the tile Gram's
-    // 128 x 128 partials of pass 2 on the A tails (one per 1024 rows at most)
-    if (blk == 1 && !p.wide && mixed && n > 64 && n % 4 == 0) {
+    // 128 x 128 partials of the head rows and of pass 2 on the A tails (one
+    // per 1024 rows at most)
+    if (blk <= 1 && !p.wide && mixed && n > 64 && n % 4 == 0) {
       const int64_t tiles = std::min<int64_t>(std::max<int64_t>(1, ceil_div(m1, 1024)), 2 * num_sms);
       most = std::max(most, static_cast<size_t>(tiles) * kWideTcTile * kWideTcTile);
     }
@@ -152,9 +153,10 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
     p.yw = b.take<char>(static_cast<size_t>(n) * ec);
     p.d0w = b.take<char>(static_cast<size_t>(n) * ec);
   }
-  // narrow mixed plans with n in (64, 128]: Q of the A tails and W^T for the
-  // tensor-core formation and tile Gram of pass 2 (narrow_q_tc)
+  // narrow mixed plans with n in (64, 128]: Q of the head rows and of the A
+  // tails and W^T for the tensor-core formation and tile Gram of pass 2 (narrow_tc)
   if (!p.wide && mixed && n > 64 && n % 4 == 0) {
+    p.wq[0] = b.take<char>(static_cast<size_t>(m1 > 0 ? m1 : 1) * n * 4);
     p.wq[1] = b.take<char>(static_cast<size_t>(m1 > 0 ? m1 : 1) * n * 4);
     p.wt = b.take<float>(static_cast<size_t>(n) * n);
     p.wtlo = b.take<float>(static_cast<size_t>(n) * n);
@@ -496,10 +498,11 @@ __global__ void upload_kernel(const __grid_constant__ UploadChunk c) {
 // Bytes of the batch area (plans, outputs, job lists) for `count` instances.
 size_t batch_area_bytes(int count) {
   const size_t lists = 24, per_list = (3 * static_cast<size_t>(count) + 1) * 3 * sizeof(int32_t) + 256;
-  // the table launches of the wide tensor-core kernels: an entry of each kind
-  // and three CTA offsets per instance
-  const size_t tables = (sizeof(WideTcEntry) + sizeof(WideFormEntry) + sizeof(WidePrepEntry) + 3 * sizeof(int32_t)) *
-                            static_cast<size_t>(count) + 6 * 64;
+  // the table launches of the wide tensor-core kernels: per instance at most
+  // three tile-Gram entries, two formation entries, one W^T entry and their
+  // CTA offsets
+  const size_t tables = (3 * sizeof(WideTcEntry) + 2 * sizeof(WideFormEntry) + sizeof(WidePrepEntry) +
+                         6 * sizeof(int32_t)) * static_cast<size_t>(count) + 12 * 128;
   return ((sizeof(Plan) + sizeof(BatchOut)) * static_cast<size_t>(count) + lists * per_list + tables + 4096 + 255) &
          ~static_cast<size_t>(255);
 }
@@ -569,14 +572,18 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   size_t gram_smem[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   size_t dsm[3][3] = {};
   int dthr[3][3] = {};
-  // pass 2 of A-tail blocks with n in (64, 128] on the mixed path: table
-  // launches of the tensor-core formation and tile Gram (entries 64-byte
-  // aligned in the batch area)
-  std::vector<WideTcEntry> qt;
-  std::vector<WideFormEntry> qf;
-  std::vector<WidePrepEntry> qp;
-  std::vector<int32_t> qt0{0}, qf0{0}, qp0{0};
-  const bool q_tables = (reinterpret_cast<uintptr_t>(area) & 63) == 0;
+  // blocks with n in (64, 128] output columns on the mixed path (the head
+  // rows in both passes, the A tails in pass 2): per pass, table launches of
+  // the W^T preparation, the tensor-core formation and the tile Gram
+  // (entries 128-byte aligned in the batch area)
+  struct QTables {
+    std::vector<WideTcEntry> t;
+    std::vector<WideFormEntry> f;
+    std::vector<WidePrepEntry> w;
+    std::vector<int32_t> t0{0}, f0{0}, w0{0};
+    size_t off_t = 0, off_f = 0, off_w = 0, off_t0 = 0, off_f0 = 0, off_w0 = 0;
+  } qtab[2];
+  const bool q_tables = (reinterpret_cast<uintptr_t>(area) & 127) == 0;
   int64_t total_chunks = 0;
   for (int i = 0; i < count; ++i)
     for (int t = 0; t < 2; ++t) total_chunks += calls[i].p.t[t].m > 0 ? calls[i].p.t[t].chunks : 0;
@@ -597,23 +604,30 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
     }
     const int64_t mm = std::max(p.t[0].m, p.t[1].m);
     match.add(i, 0, static_cast<int>((mm + 255) / 256));
+    bool prep_added = false;
     for (int pass = 1; pass <= 2; ++pass)
       for (int b = 0; b < 3; ++b) {
-        if (pass == 2 && b == 1 && q_tables && p.gram_engine != 1 && narrow_q_tc(p)) {
+        if (q_tables && narrow_tc(p, pass, b)) {
           WideFormBlock fb;
           WideTcBlock tb;
-          narrow_q_tc_blocks(p, sched.gram_rows_per_cta, &fb, &tb);
+          narrow_tc_blocks(p, pass, b, sched.gram_rows_per_cta, &fb, &tb);
           WideFormEntry fe;
           WideTcEntry te;
-          if (wide_form_encode(fb, &fe) && wide_tc_encode(tb, &te)) {
-            qf.push_back(fe);
-            qf0.push_back(qf0.back() + fb.njobs);
-            qt.push_back(te);
-            qt0.push_back(qt0.back() + tb.njobs);
-            qp.push_back(WidePrepEntry{p.Wf, p.wt, p.wtlo, p.n});
-            qp0.push_back(qp0.back() + (p.n * p.n + 255) / 256);
-            calls[i].p.gcount[1][1] = tb.njobs;
-            calls[i].p.gsym[1][1] = 3;
+          if ((pass == 1 || wide_form_encode(fb, &fe)) && wide_tc_encode(tb, &te)) {
+            QTables& Q = qtab[pass - 1];
+            if (pass == 2) {
+              Q.f.push_back(fe);
+              Q.f0.push_back(Q.f0.back() + fb.njobs);
+              if (!prep_added) {
+                Q.w.push_back(WidePrepEntry{p.Wf, p.wt, p.wtlo, p.n});
+                Q.w0.push_back(Q.w0.back() + (p.n * p.n + 255) / 256);
+                prep_added = true;
+              }
+            }
+            Q.t.push_back(te);
+            Q.t0.push_back(Q.t0.back() + tb.njobs);
+            calls[i].p.gcount[pass - 1][b] = tb.njobs;
+            calls[i].p.gsym[pass - 1][b] = 3;
             continue;
           }
         }
@@ -646,6 +660,14 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
       for (int b = 0; b < 3; ++b) most = std::max(most, p.gcount[q][b] > 0 ? p.gcount[q][b] : p.ggrid[b]);
     if (most <= 64) reduce.add(i, 1, (p.n * p.n + 32 * kReduceWarps - 1) / (32 * kReduceWarps));
     else reduce.add(i, 0, (p.n * p.n + 31) / 32);
+  }
+  // the n x n steps: one CTA per instance, the widest instances first (their
+  // CTAs take longest, so the others fill in around them)
+  std::vector<int> by_width(count);
+  for (int i = 0; i < count; ++i) by_width[i] = i;
+  std::stable_sort(by_width.begin(), by_width.end(), [&](int a, int b) { return calls[a].p.n > calls[b].p.n; });
+  for (int i : by_width) {
+    const Plan& p = calls[i].p;
     JobList* dl[3] = {dense1, dense2, dense3};
     for (int step = 1; step <= 3; ++step) {
       if (step == 3 && !outs[i].sigma) continue;
@@ -673,15 +695,19 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   for (int q = 0; q < 2; ++q)
     for (int v = 0; v < 4; ++v) Jgram[q][v] = stage_jobs(blob, gram[q][v], fix, &Jgram[q][v]);
   Jreduce = stage_jobs(blob, reduce, fix, &Jreduce);
-  const int nq = static_cast<int>(qt.size());
-  size_t off_qt = 0, off_qf = 0, off_qp = 0, off_qt0 = 0, off_qf0 = 0, off_qp0 = 0;
-  if (nq > 0) {
-    off_qt = blob.put(qt.data(), sizeof(WideTcEntry) * nq, 64);
-    off_qf = blob.put(qf.data(), sizeof(WideFormEntry) * nq, 64);
-    off_qp = blob.put(qp.data(), sizeof(WidePrepEntry) * nq);
-    off_qt0 = blob.put(qt0.data(), sizeof(int32_t) * (nq + 1));
-    off_qf0 = blob.put(qf0.data(), sizeof(int32_t) * (nq + 1));
-    off_qp0 = blob.put(qp0.data(), sizeof(int32_t) * (nq + 1));
+  for (QTables& Q : qtab) {
+    if (!Q.t.empty()) {
+      Q.off_t = blob.put(Q.t.data(), sizeof(WideTcEntry) * Q.t.size(), 128);
+      Q.off_t0 = blob.put(Q.t0.data(), sizeof(int32_t) * Q.t0.size());
+    }
+    if (!Q.f.empty()) {
+      Q.off_f = blob.put(Q.f.data(), sizeof(WideFormEntry) * Q.f.size(), 128);
+      Q.off_f0 = blob.put(Q.f0.data(), sizeof(int32_t) * Q.f0.size());
+    }
+    if (!Q.w.empty()) {
+      Q.off_w = blob.put(Q.w.data(), sizeof(WidePrepEntry) * Q.w.size());
+      Q.off_w0 = blob.put(Q.w0.data(), sizeof(int32_t) * Q.w0.size());
+    }
   }
   JobList* dl[3] = {dense1, dense2, dense3};
   for (int st = 0; st < 3; ++st)
@@ -730,16 +756,20 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
         FIGARO_TRY(launch_gram_tc_batch(b.plans, plans.data(), pass, e + 1, v, jobs.data(), static_cast<int>(jobs.size()),
                                         tc_smem[pass - 1][e][v], s));
       }
-    if (pass == 2 && nq > 0) {  // W^T of each instance, Q = X W, then the tile Gram of Q
+    const QTables& Q = qtab[pass - 1];
+    if (!Q.t.empty()) {  // (pass 2: W^T of each instance and Q = X W first) the tile Gram
       auto at = [&](size_t off) { return area + off; };
-      FIGARO_TRY(launch_wide_prep_table(reinterpret_cast<const WidePrepEntry*>(at(off_qp)),
-                                        reinterpret_cast<const int32_t*>(at(off_qp0)), nq, qp0.back(), s));
-      FIGARO_TRY(launch_wide_form_tc_table(reinterpret_cast<const WideFormEntry*>(at(off_qf)),
-                                           reinterpret_cast<const int32_t*>(at(off_qf0)), nq, qf0.back(),
-                                           p0.spin_limit, s));
-      FIGARO_TRY(launch_wide_gram_tc_table(reinterpret_cast<const WideTcEntry*>(at(off_qt)),
-                                           reinterpret_cast<const int32_t*>(at(off_qt0)), nq, qt0.back(),
-                                           p0.spin_limit, s));
+      if (!Q.w.empty())
+        FIGARO_TRY(launch_wide_prep_table(reinterpret_cast<const WidePrepEntry*>(at(Q.off_w)),
+                                          reinterpret_cast<const int32_t*>(at(Q.off_w0)),
+                                          static_cast<int>(Q.w.size()), Q.w0.back(), s));
+      if (!Q.f.empty())
+        FIGARO_TRY(launch_wide_form_tc_table(reinterpret_cast<const WideFormEntry*>(at(Q.off_f)),
+                                             reinterpret_cast<const int32_t*>(at(Q.off_f0)),
+                                             static_cast<int>(Q.f.size()), Q.f0.back(), p0.spin_limit, s));
+      FIGARO_TRY(launch_wide_gram_tc_table(reinterpret_cast<const WideTcEntry*>(at(Q.off_t)),
+                                           reinterpret_cast<const int32_t*>(at(Q.off_t0)),
+                                           static_cast<int>(Q.t.size()), Q.t0.back(), p0.spin_limit, s));
     }
     FIGARO_TRY(launch_batch_gram(b, pass, none, none_smem, Jreduce, mixed, s));
     return FIGARO_OK;

@@ -212,6 +212,127 @@ __device__ __forceinline__ double upper_dot(const TA* A, const TB* B, int n, int
   return s0 + s1;
 }
 
+// hi + lo += x y exactly up to the final rounding of lo (the product's
+// rounding error recovered by an FMA, the sum by TwoSum).
+__device__ __forceinline__ void ff_fma(float& hi, float& lo, float x, float y) {
+  const float p = x * y;
+  const float e = fmaf(x, y, -p);
+  float s, t;
+  two_sum(hi, p, s, t);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+}
+
+// Offset of row i of a packed upper triangle (rows i..n-1 of lengths n - i).
+__device__ __forceinline__ int tri_row(int n, int i) { return i * n - (i * (i - 1)) / 2; }
+
+// Mixed-path second factorisation and R for 32 < n <= 128 (one CTA): as the
+// n <= 32 form, E = I - W R1 in float-float from the exact FP32 values of W
+// and R1, X = R1 + R1 E kept as the pair (R1 masked, the FP32 correction
+// R1 E), R = R2 X in float-float.  Shared memory: A (n x n, G2 then R2) and
+// three packed upper triangles (R1 then the X head, W then the X correction,
+// E).  Xg receives X in FP64, as the FP64 form writes it.
+__device__ __forceinline__ void chol_second_ff_body(const double* G2, int n, double tol, const double* R1,
+                                                    const float* Wf, const int32_t* active, double* Xg, double* R,
+                                                    double* R_out, int64_t ldr, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nt = n * (n + 1) / 2;
+  float* A = reinterpret_cast<float*>(smraw);
+  float* diag0 = A + n * n;
+  float* y = diag0 + n;
+  int32_t* act = reinterpret_cast<int32_t*>(y + n);
+  float* tX = reinterpret_cast<float*>(act + n);  // R1, then X's head
+  float* tL = tX + nt;                              // W, then X's correction
+  float* tE = tL + nt;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = static_cast<float>(G2[e]);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    diag0[k] = static_cast<float>(G2[k * n + k]);
+    act[k] = active[k];
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    if (j < i) continue;
+    const int t = tri_row(n, i) + (j - i);
+    tX[t] = static_cast<float>(R1[e]);  // (exact: R1 holds FP32 values)
+    tL[t] = Wf[e];
+  }
+  __syncthreads();
+  // E = I - W R1 on the independent columns
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    if (j < i) continue;
+    float ev = 0.f;
+    if (act[i] && act[j]) {
+      float hi = 0.f, lo = 0.f;
+      const int wi = tri_row(n, i) - i;  // W[i][k] = tL[wi + k]
+      int kj = tri_row(n, i) + (j - i);  // R1[k][j], k = i..j
+      for (int k = i; k <= j; ++k) {
+        ff_fma(hi, lo, tL[wi + k], tX[kj]);
+        kj += n - k - 1;
+      }
+      float t0, t1;
+      two_sum(i == j ? 1.f : 0.f, -hi, t0, t1);
+      ev = __fadd_rn(t0, __fadd_rn(t1, -lo));
+    }
+    tE[tri_row(n, i) + (j - i)] = ev;
+  }
+  __syncthreads();
+  // the correction R1 E (FP32: it is ~1e-7 of R1) into W's triangle
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    if (j < i) continue;
+    float c = 0.f;
+    if (act[i] && act[j]) {
+      const int ri = tri_row(n, i) - i;
+      int kj = tri_row(n, i) + (j - i);
+      for (int k = i; k <= j; ++k) {
+        c = fmaf(tX[ri + k], tE[kj], c);
+        kj += n - k - 1;
+      }
+    }
+    tL[tri_row(n, i) + (j - i)] = c;
+  }
+  __syncthreads();
+  // X's head: R1 on the independent columns, the identity on the dependent diagonal
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    double xd = 0.0;
+    if (j >= i) {
+      const int t = tri_row(n, i) + (j - i);
+      float x = (act[i] && act[j]) ? tX[t] : 0.f;
+      if (i == j && !act[i]) x = 1.f;
+      tX[t] = x;
+      xd = static_cast<double>(x) + static_cast<double>(tL[t]);
+    }
+    Xg[e] = xd;
+  }
+  __syncthreads();
+  chol_inplace<float>(A, n, diag0, act, static_cast<float>(tol), y, status);
+  if (threadIdx.x == 0) {
+    int dep = 0;
+    for (int k = 0; k < n; ++k) dep += act[k] ? 0 : 1;
+    header_of(status)->dep_cols = dep;
+  }
+  // R = R2 X (both upper triangular); rows of dependent columns are zero
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    double r = 0.0;
+    if (j >= i && act[i]) {
+      float hi = 0.f, lo = 0.f;
+      int kj = tri_row(n, i) + (j - i);
+      for (int k = i; k <= j; ++k) {
+        const float r2 = A[i * n + k];
+        ff_fma(hi, lo, r2, tX[kj]);
+        lo = fmaf(r2, tL[kj], lo);
+        kj += n - k - 1;
+      }
+      r = static_cast<double>(hi) + static_cast<double>(lo);
+    }
+    R[e] = r;
+    if (R_out) R_out[static_cast<int64_t>(i) * ldr + j] = r;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void chol_second_body(const double* G2, int n, double tol, const double* R1, const double* Wd,
                                                  const int32_t* active, int refine, double* Xg, double* R,
@@ -265,11 +386,26 @@ __device__ __forceinline__ void chol_second_body(const double* G2, int n, double
   }
 }
 
+// Shared memory of the one-CTA second factorisation: the float-float form
+// (mixed path) or the FP64 one.
+__host__ __device__ inline size_t chol_second_smem(int n, bool mixed) {
+  if (mixed)
+    return (sizeof(float) * (static_cast<size_t>(n) * n + 2 * n) + sizeof(int32_t) * n +
+            3 * sizeof(float) * static_cast<size_t>(n) * (n + 1) / 2 + 15) & ~size_t(15);
+  return (sizeof(double) * (static_cast<size_t>(n) * n + 2 * n) + sizeof(int32_t) * n + 15) & ~size_t(15);
+}
+
 template <typename T, bool kSmall>
 __global__ void __launch_bounds__(1024) chol_second_kernel(const double* G2, int n, double tol, const double* R1, const double* Wd,
-                                   const int32_t* active, int refine, double* Xg, double* R, double* R_out,
-                                   int64_t ldr, int32_t* status) {
+                                   const float* Wf, const int32_t* active, int refine, double* Xg, double* R,
+                                   double* R_out, int64_t ldr, int32_t* status) {
   pdl_enter();
+  if constexpr (sizeof(T) == 4) {
+    if (refine) {
+      chol_second_ff_body(G2, n, tol, R1, Wf, active, Xg, R, R_out, ldr, status);
+      return;
+    }
+  }
   chol_second_body<T>(G2, n, tol, R1, Wd, active, refine, Xg, R, R_out, ldr, status);
 }
 
@@ -298,10 +434,27 @@ __device__ __forceinline__ void rotation(double al, double be, double ga, double
   s = c * t;
 }
 
+// Shared memory of the one-CTA Jacobi before the bf16 tails of R (mixed path):
+// U and V (np x n each with V), sigma and the column norms (np doubles each),
+// R in FP64 when V is kept and n <= 64, the pairing table.
+__host__ __device__ inline size_t jacobi_smem_base(int n, int es, bool with_v) {
+  const size_t np = static_cast<size_t>(n + (n & 1));
+  size_t b = es * np * n * (with_v ? 2 : 1) + 2 * sizeof(double) * np;
+  if (with_v && n <= 64) b += sizeof(double) * static_cast<size_t>(n) * n;
+  return b + sizeof(short2) * (np - 1) * (np / 2);
+}
+// the bf16 tails of R (n x n) follow at a 16-byte boundary (mixed path, V kept)
+__host__ __device__ inline size_t jacobi_rlo_offset(int n, int es) { return (jacobi_smem_base(n, es, true) + 15) & ~size_t(15); }
+__host__ __device__ inline size_t jacobi_smem(int n, int es, bool with_v) {
+  return with_v && es == 4 ? jacobi_rlo_offset(n, es) + 2 * static_cast<size_t>(n) * n : jacobi_smem_base(n, es, with_v);
+}
+
 // One-sided Jacobi.  U (and V) column-major in shared memory; LPP lanes per
 // column pair (32 / LPP pairs per warp), NPL rows of each column per lane;
 // the round-robin pairing is tabulated once.  A pair is rotated while
-// |u_p.u_q|^2 > tol^2 |u_p|^2 |u_q|^2.
+// |u_p.u_q|^2 > tol^2 |u_p|^2 |u_q|^2.  With several pairs per warp, the
+// pair groups of a warp visit their rows in rotated order (group gw starts
+// at row block gw), so that at each step they read different banks.
 template <typename T, bool kWithV, int NPL, int LPP>
 __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in,
                                             double* sigma, int32_t* status, int32_t* sweeps_out) {
@@ -369,7 +522,7 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
         T al = 0, be = 0, ga = 0;
 #pragma unroll
         for (int i = 0; i < NPL; ++i) {
-          const int r = sub + LPP * i;
+          const int r = sub + LPP * ((i + gw) % NPL);
           x[i] = (live && r < n) ? up[r] : T(0);
           y[i] = (live && r < n) ? uq[r] : T(0);
           al += x[i] * x[i];
@@ -387,7 +540,7 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
           rotation(al, be, ga, c, s);
 #pragma unroll
           for (int i = 0; i < NPL; ++i) {
-            const int r = sub + LPP * i;
+            const int r = sub + LPP * ((i + gw) % NPL);
             if (r < n) {
               up[r] = c * x[i] - s * y[i];
               uq[r] = s * x[i] + c * y[i];
@@ -398,7 +551,7 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
             T* vq = V + static_cast<int64_t>(pq.y) * n;
 #pragma unroll
             for (int i = 0; i < NPL; ++i) {
-              const int r = sub + LPP * i;
+              const int r = sub + LPP * ((i + gw) % NPL);
               if (r < n) {
                 const T xv = vp[r], yv = vq[r];
                 vp[r] = c * xv - s * yv;
@@ -431,52 +584,115 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
       if (lane == 0) unrm[j] = sqrt(un);
     }
     __syncthreads();
-    // sigma_j^2 = sum_i (R v_j)_i^2 / ||v_j||^2 in FP64, one thread per (i, j).
-    // U is no longer needed: its storage (np * n floats = np * n / 2 doubles)
-    // holds the squared terms for np / 2 rows i at a time.
-    double* acc = reinterpret_cast<double*>(U);
-    for (int j = warp; j < n; j += nwarps) sig[j] = 0.0;
-    const int ipass = np / 2;
-    for (int i0 = 0; i0 < n; i0 += ipass) {
-      const int i1 = i0 + ipass < n ? i0 + ipass : n;
+    if constexpr (sizeof(T) == 4) {
+      // sigma_j^2 = sum_i (R v_j)_i^2 / ||v_j||^2 with (R v_j)_i in
+      // float-float: R is split once into FP32 heads (in V's storage) and
+      // bf16 tails (their product with v only feeds the low word), V^T goes
+      // into U's storage (U and V are no longer needed), so that a warp's
+      // lanes (consecutive j) read consecutive words while R[i][k] is one
+      // broadcast; warp w takes the 32 columns of block w % jb and the rows
+      // i = w / jb (mod ig).  The groups' sums meet in the pairing table's
+      // storage.  (FP64 arithmetic is slow on this GPU: one FP64 operation per
+      // entry of R, none per product.)
+      float* VT = reinterpret_cast<float*>(U);
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int j = e / n, k = e - (e / n) * n;
+        VT[k * n + j] = V[e];
+      }
       __syncthreads();
-      for (int e = threadIdx.x; e < (i1 - i0) * n; e += blockDim.x) {
-        const int j = e / (i1 - i0), i = i0 + e % (i1 - i0);
-        const T* vj = V + static_cast<int64_t>(j) * n;
-        double y0 = 0.0, y1 = 0.0;
-        int k = i;
-        if (r_in_smem) {
-          for (; k + 1 < n; k += 2) {
-            y0 += Rs[i * n + k] * static_cast<double>(vj[k]);
-            y1 += Rs[i * n + k + 1] * static_cast<double>(vj[k + 1]);
-          }
-          if (k < n) y0 += Rs[i * n + k] * static_cast<double>(vj[k]);
-        } else {
-          for (; k < n; ++k) y0 += R[static_cast<int64_t>(i) * ldr + k] * static_cast<double>(vj[k]);
+      float* Rh = reinterpret_cast<float*>(V);
+      uint16_t* Rl = reinterpret_cast<uint16_t*>(smraw + jacobi_rlo_offset(n, static_cast<int>(sizeof(T))));
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, k = e - (e / n) * n;
+        const double r = k >= i ? R[static_cast<int64_t>(i) * ldr + k] : 0.0;
+        const float rh = static_cast<float>(r);
+        Rh[e] = rh;
+        Rl[e] = static_cast<uint16_t>(__float_as_uint(static_cast<float>(r - static_cast<double>(rh))) >> 16);
+      }
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {  // ||v_j||^2, kept in sig until the end
+        double den = 0.0;
+        for (int k = 0; k < n; ++k) {
+          const double v = static_cast<double>(VT[k * n + j]);
+          den += v * v;
         }
-        const double yy = y0 + y1;
-        acc[e] = yy * yy;
+        sig[j] = den;
+      }
+      double* gsum = reinterpret_cast<double*>(pairs);
+      const int jb = (n + 31) / 32;
+      const int ig = nwarps / jb > 0 ? nwarps / jb : 1;
+      __syncthreads();
+      for (int w = warp; w < jb * ig; w += nwarps) {
+        const int j = (w % jb) * 32 + lane, grp = w / jb;
+        if (j >= n) continue;
+        double num = 0.0;
+        for (int i = grp; i < n; i += ig) {
+          float hi = 0.f, lo = 0.f;
+          for (int k = i; k < n; ++k) {
+            const float v = VT[k * n + j];
+            ff_fma(hi, lo, Rh[i * n + k], v);
+            lo = fmaf(__uint_as_float(static_cast<uint32_t>(Rl[i * n + k]) << 16), v, lo);
+          }
+          const double yd = static_cast<double>(hi) + static_cast<double>(lo);
+          num += yd * yd;
+        }
+        gsum[grp * n + j] = num;
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double num = 0.0;
+        for (int g = 0; g < ig; ++g) num += gsum[g * n + j];
+        const double den = sig[j];
+        sig[j] = den > 0.0 ? sqrt(num / den) : 0.0;
+      }
+      __syncthreads();
+    } else {
+      for (int j = warp; j < n; j += nwarps) sig[j] = 0.0;
+      // sigma_j^2 = sum_i (R v_j)_i^2 / ||v_j||^2 in FP64, one thread per (i, j).
+      // U is no longer needed: its storage (np * n floats = np * n / 2 doubles)
+      // holds the squared terms for np / 2 rows i at a time.
+      double* acc = reinterpret_cast<double*>(U);
+      const int ipass = np / 2;
+      for (int i0 = 0; i0 < n; i0 += ipass) {
+        const int i1 = i0 + ipass < n ? i0 + ipass : n;
+        __syncthreads();
+        for (int e = threadIdx.x; e < (i1 - i0) * n; e += blockDim.x) {
+          const int j = e / (i1 - i0), i = i0 + e % (i1 - i0);
+          const T* vj = V + static_cast<int64_t>(j) * n;
+          double y0 = 0.0, y1 = 0.0;
+          int k = i;
+          if (r_in_smem) {
+            for (; k + 1 < n; k += 2) {
+              y0 += Rs[i * n + k] * static_cast<double>(vj[k]);
+              y1 += Rs[i * n + k + 1] * static_cast<double>(vj[k + 1]);
+            }
+            if (k < n) y0 += Rs[i * n + k] * static_cast<double>(vj[k]);
+          } else {
+            for (; k < n; ++k) y0 += R[static_cast<int64_t>(i) * ldr + k] * static_cast<double>(vj[k]);
+          }
+          const double yy = y0 + y1;
+          acc[e] = yy * yy;
+        }
+        __syncthreads();
+        for (int j = warp; j < n; j += nwarps) {
+          double num = 0.0;
+          for (int i = lane; i < i1 - i0; i += 32) num += acc[j * (i1 - i0) + i];
+          for (int o = 16; o > 0; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
+          if (lane == 0) sig[j] += num;
+        }
       }
       __syncthreads();
       for (int j = warp; j < n; j += nwarps) {
-        double num = 0.0;
-        for (int i = lane; i < i1 - i0; i += 32) num += acc[j * (i1 - i0) + i];
-        for (int o = 16; o > 0; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
-        if (lane == 0) sig[j] += num;
+        double den = 0.0;
+        const T* vj = V + static_cast<int64_t>(j) * n;
+        for (int i = lane; i < n; i += 32) {
+          const double v = static_cast<double>(vj[i]);
+          den += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) den += __shfl_xor_sync(0xffffffffu, den, o);
+        if (lane == 0) sig[j] = den > 0.0 ? sqrt(sig[j] / den) : 0.0;
       }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int j = warp; j < n; j += nwarps) {
-      double den = 0.0;
-      const T* vj = V + static_cast<int64_t>(j) * n;
-      for (int i = lane; i < n; i += 32) {
-        const double v = static_cast<double>(vj[i]);
-        den += v * v;
-      }
-      for (int o = 16; o > 0; o >>= 1) den += __shfl_xor_sync(0xffffffffu, den, o);
-      if (lane == 0) sig[j] = den > 0.0 ? sqrt(sig[j] / den) : 0.0;
-    }
-    __syncthreads();
     double umax = 0.0;
     for (int k = 0; k < n; ++k) umax = unrm[k] > umax ? unrm[k] : umax;
     __syncthreads();
@@ -507,7 +723,7 @@ __device__ __forceinline__ void jacobi_body(const double* R, int64_t ldr, int n,
 }
 
 template <typename T, bool kWithV, int NPL, int LPP>
-__global__ void __launch_bounds__(1024) jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in, double* sigma,
+__global__ void __launch_bounds__(512) jacobi_kernel(const double* R, int64_t ldr, int n, int max_sweeps, double tol_in, double* sigma,
                               int32_t* status, int32_t* sweeps_out) {
   pdl_enter();
   jacobi_body<T, kWithV, NPL, LPP>(R, ldr, n, max_sweeps, tol_in, sigma, status, sweeps_out);
@@ -527,6 +743,7 @@ __host__ __device__ inline double jacobi_tol(const Plan& p) {
 // matrix is held by lane c, and row i by warp i mod 8 (register i / 8) for
 // the factorisations, or by warp i / (32 / JW) for the Jacobi sweeps.
 constexpr int kSmallN = 32;
+constexpr int kJacobiLPP = 8;  // lanes per column pair of the shared-memory Jacobi (4 pairs per warp)
 constexpr int kC8Warps = 8;  // warps of the small factorisations (rows i = warp + 8 s, s < 4)
 constexpr int kC8Threads = 32 * kC8Warps;
 
@@ -1030,16 +1247,22 @@ __global__ void __launch_bounds__(1024) chol_second_batched(BatchDev b, BatchJob
   pdl_enter();
   const int i = J.inst[blockIdx.x];
   const Plan& P = b.plans[i];
+  if constexpr (sizeof(T) == 4) {
+    if (P.mixed) {
+      chol_second_ff_body(P.G2, P.n, dense_tol(P), P.R1, P.Wf, P.active, P.G1, P.R, b.out[i].R, P.n, &P.hdr->status);
+      return;
+    }
+  }
   chol_second_body<T>(P.G2, P.n, dense_tol(P), P.R1, P.W, P.active, P.mixed, P.G1, P.R, b.out[i].R, P.n,
                       &P.hdr->status);
 }
 
 template <typename T, bool kWithV, int NPL>
-__global__ void __launch_bounds__(1024) jacobi_batched(BatchDev b, BatchJobs J) {
+__global__ void __launch_bounds__(512) jacobi_batched(BatchDev b, BatchJobs J) {
   pdl_enter();
   const int i = J.inst[blockIdx.x];
   const Plan& P = b.plans[i];
-  jacobi_body<T, kWithV, NPL, 32>(P.R, P.n, P.n, P.max_sweeps, jacobi_tol(P), b.out[i].sigma, &P.hdr->status,
+  jacobi_body<T, kWithV, NPL, kJacobiLPP>(P.R, P.n, P.n, P.max_sweeps, jacobi_tol(P), b.out[i].sigma, &P.hdr->status,
                                   &P.hdr->jacobi_sweeps);
 }
 
@@ -1123,8 +1346,7 @@ cudaError_t launch_refactor(const Plan& p, cudaStream_t s) {
 template <typename T>
 static cudaError_t chol_second_t(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s) {
   const int n = p.n;
-  size_t smem = ((sizeof(T) * (static_cast<size_t>(n) * n + 2 * n) + sizeof(int32_t) * n + 15) & ~size_t(15));
-  if (p.mixed) smem += sizeof(double) * static_cast<size_t>(n) * n;
+  const size_t smem = chol_second_smem(n, p.mixed != 0);
   if (n <= kSmallN) {
     pdl_launch(chol_second32_kernel<T>, 1, kC8Threads, 0, s, p.G2, n, default_tol(p), p.R1, p.Wf, p.active,
                p.mixed ? 1 : 0, p.R, R_out, ldr, &p.hdr->status);
@@ -1135,8 +1357,8 @@ static cudaError_t chol_second_t(const Plan& p, double* R_out, int64_t ldr, cuda
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
   // G1 is consumed by the first factorisation: its storage holds the refined inverse
-  pdl_launch(kern, 1, dense_threads(n), smem, s, p.G2, n, default_tol(p), p.R1, p.W, p.active, p.mixed ? 1 : 0, p.G1, p.R,
-                                         R_out, ldr, &p.hdr->status);
+  pdl_launch(kern, 1, dense_threads(n), smem, s, p.G2, n, default_tol(p), p.R1, p.W, p.Wf, p.active, p.mixed ? 1 : 0,
+             p.G1, p.R, R_out, ldr, &p.hdr->status);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1152,10 +1374,8 @@ static cudaError_t jacobi_t(const Plan& p, const double* R, int64_t ldr, double*
   const int np = n + (n & 1);
   const int npairs = np / 2;
   int threads = 32 * ((npairs + 32 / LPP - 1) / (32 / LPP));
-  if (threads > 1024) threads = 1024;
-  size_t smem = sizeof(T) * static_cast<size_t>(np) * n * (kWithV ? 2 : 1) + 2 * sizeof(double) * np;
-  if (kWithV && n <= 64) smem += sizeof(double) * static_cast<size_t>(n) * n;
-  smem += sizeof(short2) * static_cast<size_t>(np - 1) * npairs;
+  if (threads > 512) threads = 512;  // (the launch bound; n <= 128 needs at most 16 warps)
+  const size_t smem = jacobi_smem(n, static_cast<int>(sizeof(T)), kWithV);
   cudaError_t err = cudaFuncSetAttribute(jacobi_kernel<T, kWithV, NPL, LPP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
@@ -1180,19 +1400,19 @@ cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* s
     // FP32 sweeps stop at |u_p . u_q| <= 1e-5 ||u_p|| ||u_q||: the FP64
     // Rayleigh quotient then has a relative error of order 1e-10 / gap
     if (n <= kSmallN) return jacobi32_t<float, true>(p, R, ldr, sigma, 1e-5, s);
-    if (n <= 64) return jacobi_t<float, true, 2>(p, R, ldr, sigma, 1e-5, s);
-    return jacobi_t<float, true, 4>(p, R, ldr, sigma, 1e-5, s);
+    if (n <= 64) return jacobi_t<float, true, 8, kJacobiLPP>(p, R, ldr, sigma, 1e-5, s);
+    return jacobi_t<float, true, 16, kJacobiLPP>(p, R, ldr, sigma, 1e-5, s);
   }
   const double tol = 4.0 * n * 1.1102230246251565e-16;
   if (n <= kSmallN) return jacobi32_t<double, false>(p, R, ldr, sigma, tol, s);
-  if (n <= 64) return jacobi_t<double, false, 2>(p, R, ldr, sigma, tol, s);
-  return jacobi_t<double, false, 4>(p, R, ldr, sigma, tol, s);
+  if (n <= 64) return jacobi_t<double, false, 8, kJacobiLPP>(p, R, ldr, sigma, tol, s);
+  return jacobi_t<double, false, 16, kJacobiLPP>(p, R, ldr, sigma, tol, s);
 }
 
 // Batched dense steps.  step 1: first Cholesky (variant 0: column-per-thread
 // inverse with a second n x n buffer, 1: in-place inverse, 2: n <= 32 in one
 // warp); step 2: second Cholesky and R (variant 1: n <= 32); step 3: Jacobi
-// (variant 0: n <= 32 in registers, 1 and 2: 2 and 4 rows per lane).
+// (variant 0: n <= 32 in registers, 1 and 2: 8 and 16 rows per lane, 8 lanes per pair).
 template <typename T>
 static size_t chol_first_smem(int n, bool small) {
   size_t smem = sizeof(T) * (static_cast<size_t>(n) * n + 3 * n) + sizeof(int32_t) * (n + 4) + 16;
@@ -1222,25 +1442,20 @@ void dense_batch_info(const Plan& p, int step, int* variant, size_t* smem, int* 
       return;
     }
     *variant = 0;
-    *smem = ((es * (static_cast<size_t>(n) * n + 2 * n) + sizeof(int32_t) * n + 15) & ~size_t(15)) +
-            (p.mixed ? sizeof(double) * static_cast<size_t>(n) * n : 0);
+    *smem = chol_second_smem(n, p.mixed != 0);
     *threads = dense_threads(n);
   } else {
     const int np = n + (n & 1), npairs = np / 2;
-    const int npl = n <= 32 ? 1 : (n <= 64 ? 2 : 4);
-    *variant = npl == 1 ? 0 : (npl == 2 ? 1 : 2);
-    if (npl == 1) {  // register-resident form
+    *variant = n <= 32 ? 0 : (n <= 64 ? 1 : 2);
+    if (n <= 32) {  // register-resident form
       *threads = 32 * kJacobi32Warps;
       *smem = 0;
       return;
     }
-    int t = 32 * npairs;  // one warp per pair (32 lanes per pair)
-    *threads = t > 1024 ? 1024 : t;
-    const bool with_v = p.mixed != 0;
-    size_t sm = es * static_cast<size_t>(np) * n * (with_v ? 2 : 1) + 2 * sizeof(double) * np;
-    if (with_v && n <= 64) sm += sizeof(double) * static_cast<size_t>(n) * n;
-    sm += sizeof(short2) * static_cast<size_t>(np - 1) * npairs;
-    *smem = sm;
+    constexpr int kPairsPerWarp = 32 / kJacobiLPP;
+    int t = 32 * ((npairs + kPairsPerWarp - 1) / kPairsPerWarp);
+    *threads = t > 512 ? 512 : t;  // (the launch bound)
+    *smem = jacobi_smem(n, static_cast<int>(es), p.mixed != 0);
   }
 }
 
@@ -1277,12 +1492,12 @@ cudaError_t launch_batch_dense(const BatchDev& b, int step, const BatchJobs jobs
   } else {
     if (mixed) {
       e = launch_bucket(jacobi32_batched<float, true>, b, jobs[0], smem[0], threads[0], s);
-      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<float, true, 2>, b, jobs[1], smem[1], threads[1], s);
-      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<float, true, 4>, b, jobs[2], smem[2], threads[2], s);
+      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<float, true, 8>, b, jobs[1], smem[1], threads[1], s);
+      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<float, true, 16>, b, jobs[2], smem[2], threads[2], s);
     } else {
       e = launch_bucket(jacobi32_batched<double, false>, b, jobs[0], smem[0], threads[0], s);
-      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<double, false, 2>, b, jobs[1], smem[1], threads[1], s);
-      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<double, false, 4>, b, jobs[2], smem[2], threads[2], s);
+      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<double, false, 8>, b, jobs[1], smem[1], threads[1], s);
+      if (e == cudaSuccess) e = launch_bucket(jacobi_batched<double, false, 16>, b, jobs[2], smem[2], threads[2], s);
     }
   }
   return e;

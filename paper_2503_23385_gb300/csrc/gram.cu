@@ -506,6 +506,14 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   if (p.wide) return launch_wide_gram_pass(p, pass, s);
   const int elem = p.mixed ? 4 : 8;
   // block 0 = head rows, 1 = A tails, 2 = B tails
+  // n in (64, 128]: the blocks with n output columns on the tile Gram (one launch for both)
+  bool ntc[3] = {false, false, false};
+  int ncount[3] = {0, 0, 0};
+  for (int b = 0; b < 2; ++b) ntc[b] = narrow_tc(p, pass, b);
+  if (ntc[0] || ntc[1]) {
+    const cudaError_t err = launch_narrow_tc(p, pass, ntc, ncount, s);
+    if (err != cudaSuccess) return err;
+  }
   ReduceArgs r{};
   r.n = p.n;
   r.G = pass == 1 ? p.G1 : p.G2;
@@ -546,12 +554,9 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
       r.sym[b] = 2;
       continue;
     }
-    if (pass == 2 && b == 1 && p.gram_engine != 1 && narrow_q_tc(p)) {  // Q written, then the tile Gram
-      int count = 0;
-      const cudaError_t err = launch_narrow_q_gram_tc(p, &count, s);
-      if (err != cudaSuccess) return err;
+    if (ntc[b]) {  // launched above
       r.part[b] = p.gpart[b];
-      r.count[b] = count;
+      r.count[b] = ncount[b];
       r.kout[b] = a.kout;
       r.off[b] = 0;
       r.sym[b] = 3;

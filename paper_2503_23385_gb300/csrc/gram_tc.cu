@@ -2265,7 +2265,7 @@ bool wide_form_encode(const WideFormBlock& b, WideFormEntry* e) {
 cudaError_t launch_wide_gram_tc_table(const WideTcEntry* e, const int32_t* job0, int nb, int ctas,
                                       int64_t spin_limit, cudaStream_t s) {
   if (nb <= 0 || ctas <= 0) return cudaSuccess;
-  if ((reinterpret_cast<uintptr_t>(e) & 63) != 0) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(e) & 127) != 0) return cudaErrorInvalidValue;
   static int granted[64] = {};
   const cudaError_t err = grant_smem(wide_gram_tc_table_kernel, kWtSmem, granted);
   if (err != cudaSuccess) return err;
@@ -2277,7 +2277,7 @@ cudaError_t launch_wide_gram_tc_table(const WideTcEntry* e, const int32_t* job0,
 cudaError_t launch_wide_form_tc_table(const WideFormEntry* e, const int32_t* job0, int nb, int ctas,
                                       int64_t spin_limit, cudaStream_t s) {
   if (nb <= 0 || ctas <= 0) return cudaSuccess;
-  if ((reinterpret_cast<uintptr_t>(e) & 63) != 0) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(e) & 127) != 0) return cudaErrorInvalidValue;
   static int granted[64] = {};
   const cudaError_t err = grant_smem(wide_form_tc_table_kernel, kWfSmem, granted);
   if (err != cudaSuccess) return err;

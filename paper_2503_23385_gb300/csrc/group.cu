@@ -269,12 +269,35 @@ __global__ void __launch_bounds__(kRadixBins) tile_scan_kernel(TwoTables a, int 
   tile_scan_body(a.t[t], t, a.h, blockIdx.x % kRadixBins, pass);
 }
 
-// one CTA per (table job, digit)
+// Batched form: one CTA per table job (a batch's tables have few tiles),
+// thread d walks digit d's tile counts in order from the keys of the smaller
+// digits (a block-wide exclusive scan of the pass's histogram).
 __global__ void __launch_bounds__(kRadixBins) tile_scan_batched(BatchDev b, BatchJobs J, int pass) {
   pdl_enter();
-  const int j = blockIdx.x / kRadixBins;
+  const int j = blockIdx.x;
   const Plan& P = b.plans[J.inst[j]];
-  tile_scan_body(P.t[J.aux[j]], J.aux[j], P.hdr, blockIdx.x % kRadixBins, pass);
+  const int t = J.aux[j];
+  const TableWork& T = P.t[t];
+  if (T.tiles == 0 || pass >= num_passes(P.hdr, t)) return;
+  const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
+  __shared__ uint32_t s_w[kRadixBins / 32];
+  const uint32_t h = T.hist[pass * kRadixBins + d];
+  uint32_t incl = h;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  uint32_t run = incl - h;
+  for (int w = 0; w < warp; ++w) run += s_w[w];
+  const uint32_t* tc = tile_counts(T, pass);
+  uint32_t* to = tile_offsets(T, pass);
+  for (int tile = 0; tile < T.tiles; ++tile) {
+    const uint32_t x = tc[static_cast<int64_t>(tile) * kRadixBins + d];
+    to[static_cast<int64_t>(tile) * kRadixBins + d] = run;
+    run += x;
+  }
 }
 
 // One stable LSD pass over digit `pass` (the scatter of reduce-then-scan).
@@ -661,7 +684,7 @@ cudaError_t launch_batch_grouping(const BatchDev& b, const BatchJobs& tiles, con
     pdl_launch(key_hist_batched, tiles.ctas, kSortThreads, 0, s, b, tiles);
     for (int pass = 0; pass < kMaxPasses; ++pass) {
       if (pass > 0) pdl_launch(tile_count_batched, tiles.ctas, kSortThreads, 0, s, b, tiles, pass);
-      pdl_launch(tile_scan_batched, tiles.njobs * kRadixBins, kRadixBins, 0, s, b, tiles, pass);
+      pdl_launch(tile_scan_batched, tiles.njobs, kRadixBins, 0, s, b, tiles, pass);
       pdl_launch(sort_pass_batched, tiles.ctas, kSortThreads, kSortSmem, s, b, tiles, pass);
     }
     pdl_launch(run_count_batched, tiles.ctas, kSortThreads, 0, s, b, tiles);

@@ -315,14 +315,14 @@ cudaError_t launch_wide_form_prep(const float* W, int n, float* WT, float* WTlo,
 
 // Table launches of the two wide tensor-core kernels (batched calls): one
 // launch covers any number of blocks, each with its own tensor maps, status
-// word and partials, read from device memory (64-byte aligned entries, copied
-// there before the launch); job0[i] = the first CTA of entry i, job0[nb] = all
+// word and partials, read from device memory (entries 128-byte aligned, the
+// alignment of CUtensorMap, copied there before the launch); job0[i] = the first CTA of entry i, job0[nb] = all
 // CTAs.  The W^T preparation of many instances runs the same way.
-struct alignas(64) WideTcEntry {
+struct alignas(128) WideTcEntry {
   CUtensorMap map;
   WideTcBlock b;
 };
-struct alignas(64) WideFormEntry {
+struct alignas(128) WideFormEntry {
   CUtensorMap xmap, wmap, wlmap;
   WideFormBlock b;
 };
@@ -339,14 +339,16 @@ cudaError_t launch_wide_gram_tc_table(const WideTcEntry* e, const int32_t* job0,
 cudaError_t launch_wide_form_tc_table(const WideFormEntry* e, const int32_t* job0, int nb, int ctas,
                                       int64_t spin_limit, cudaStream_t s);
 cudaError_t launch_wide_prep_table(const WidePrepEntry* e, const int32_t* cta0, int nb, int ctas, cudaStream_t s);
-// Narrow mixed plans with n in (64, 128]: the A-tail block of pass 2 on the
-// tensor cores (wide.cu); the partials of block 1 in the reduce's format 3.
-bool narrow_q_tc(const Plan& p);
+// Narrow mixed plans with n in (64, 128]: the head rows (both passes) and
+// the A tails (pass 2) on the tensor-core formation and tile Gram (wide.cu);
+// partials of block b in the reduce's format 3.
+bool narrow_tc(const Plan& p, int pass, int b);
 // rows_min: the fewest rows of a split (rounded up to 1024)
-int narrow_q_tc_splits(const Plan& p, int64_t rows_min, int64_t* split_rows);
-// the formation and tile Gram blocks of such a plan (splits of >= rows_min rows)
-void narrow_q_tc_blocks(const Plan& p, int64_t rows_min, WideFormBlock* fb, WideTcBlock* tb);
-cudaError_t launch_narrow_q_gram_tc(const Plan& p, int* count, cudaStream_t s);
+int narrow_tc_splits(const Plan& p, int b, int64_t rows_min, int64_t* split_rows);
+// the formation (pass 2) and tile Gram blocks of block b (splits of >= rows_min rows)
+void narrow_tc_blocks(const Plan& p, int pass, int b, int64_t rows_min, WideFormBlock* fb, WideTcBlock* tb);
+// single calls: blocks 0 and 1 where use[b], partial counts into count[b]
+cudaError_t launch_narrow_tc(const Plan& p, int pass, const bool use[3], int count[3], cudaStream_t s);
 cudaError_t launch_wide_form_tc(const WideFormBlock b[3], const float* WT, const float* WTlo, int n, int32_t* status,
                                 int64_t spin_limit, cudaStream_t s);
 cudaError_t launch_wide_gram_tc(const WideTcBlock b[3], double* part, int32_t* status, int64_t spin_limit,

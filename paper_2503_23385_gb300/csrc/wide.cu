@@ -1351,22 +1351,35 @@ cudaError_t launch_wide_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Narrow mixed plans with n in (64, 128]: pass 2 of the A-tail block (Q has
-// kout = n columns, more than the narrow tensor-core engines take) by the
-// tensor-core formation (Q written to p.wq[1]) and the tile Gram (one 128 x
-// 128 tile pair; partials [splits][128][128] in p.gpart[1], format 3 of the
-// reduce).
-bool narrow_q_tc(const Plan& p) {
-  // (the partial buffer of block 1 must hold at least one 128 x 128 tile)
-  return p.mixed && !p.wide && p.n > 64 && p.n <= kWideTcTile && p.n % 4 == 0 && p.n1 % 4 == 0 && p.wq[1] &&
-         p.wt && p.t[0].m > 0 && p.gcap[1] >= static_cast<int64_t>(kWideTcTile) * kWideTcTile &&
-         wide_tc_eligible(static_cast<const float*>(p.t[0].tail), p.n1, p.n1);
+// Narrow mixed plans with n in (64, 128]: the Gram blocks with n output
+// columns, more than the narrow tensor-core engines take, on the tile Gram
+// (one 128 x 128 tile pair; partials [splits][128][128] in p.gpart[b],
+// format 3 of the reduce): the head rows in pass 1 (X = the head rows, their
+// count read on the device) and, after the tensor-core formation Q = X W into
+// p.wq[b], the head rows and the A tails in pass 2.
+static const float* narrow_tc_x(const Plan& p, int b, int64_t* ld, int* k) {
+  *ld = b == 0 ? p.n : p.n1;
+  *k = b == 0 ? p.n : p.n1;
+  return static_cast<const float*>(b == 0 ? p.head : p.t[0].tail);
 }
 
-int narrow_q_tc_splits(const Plan& p, int64_t rows_min, int64_t* split_rows) {
-  const int64_t rows = p.t[0].m;
+bool narrow_tc(const Plan& p, int pass, int b) {
+  if (!(b == 0 || (b == 1 && pass == 2))) return false;
+  if (!(p.mixed && !p.wide && p.gram_engine != 1 && p.n > 64 && p.n <= kWideTcTile && p.n % 4 == 0 &&
+        p.n1 % 4 == 0 && p.t[0].m > 0 && p.wt && p.wq[b]))
+    return false;
+  // (the partial buffer must hold at least one 128 x 128 tile)
+  if (p.gcap[b] < static_cast<int64_t>(kWideTcTile) * kWideTcTile) return false;
+  int64_t ld = 0;
+  int k = 0;
+  const float* X = narrow_tc_x(p, b, &ld, &k);
+  return wide_tc_eligible(X, ld, k);
+}
+
+int narrow_tc_splits(const Plan& p, int b, int64_t rows_min, int64_t* split_rows) {
+  const int64_t rows = p.t[0].m;  // (head rows: at most m1, their count read on the device)
   const int64_t per = rows_min > 1024 ? rows_min : 1024;
-  const int64_t cap = p.gcap[1] / (static_cast<int64_t>(kWideTcTile) * kWideTcTile);
+  const int64_t cap = p.gcap[b] / (static_cast<int64_t>(kWideTcTile) * kWideTcTile);
   int64_t splits = (rows + per - 1) / per;
   if (splits > 2 * static_cast<int64_t>(p.num_sms)) splits = 2 * static_cast<int64_t>(p.num_sms);
   if (splits > cap) splits = cap;
@@ -1377,35 +1390,52 @@ int narrow_q_tc_splits(const Plan& p, int64_t rows_min, int64_t* split_rows) {
   return static_cast<int>((rows + sr - 1) / sr);
 }
 
-void narrow_q_tc_blocks(const Plan& p, int64_t rows_min, WideFormBlock* fb, WideTcBlock* tb) {
+void narrow_tc_blocks(const Plan& p, int pass, int b, int64_t rows_min, WideFormBlock* fb, WideTcBlock* tb) {
   const int n = p.n;
   const int64_t rows = p.t[0].m;
-  const float* X = static_cast<const float*>(p.t[0].tail);
+  const int64_t* rows_dev = b == 0 ? &p.hdr->num_runs[0] : nullptr;
+  int64_t ld = 0;
+  int k = 0;
+  const float* X = narrow_tc_x(p, b, &ld, &k);
   int64_t sr = 0;
-  const int splits = narrow_q_tc_splits(p, rows_min, &sr);
-  // formation: one CTA per split of sr / 128 row tiles (the Gram's splits)
-  const int rps = static_cast<int>(sr / 128);
-  *fb = WideFormBlock{X, p.n1, p.n1, n, 0, rows, nullptr, static_cast<float*>(p.wq[1]), 1, splits, rps, splits};
-  fb->WT = p.wt;
-  fb->WTlo = p.wtlo;
-  fb->n = n;
-  fb->status = &p.hdr->status;
-  *tb = WideTcBlock{static_cast<const float*>(p.wq[1]), n, n, rows, nullptr, 1, splits, sr, splits, 0};
-  tb->part = p.gpart[1];
+  const int splits = narrow_tc_splits(p, b, rows_min, &sr);
+  *fb = WideFormBlock{};
+  if (pass == 2) {  // formation: one CTA per split of sr / 128 row tiles (the Gram's splits)
+    const int rps = static_cast<int>(sr / 128);
+    *fb = WideFormBlock{X, ld, k, n, 0, rows, rows_dev, static_cast<float*>(p.wq[b]), 1, splits, rps, splits};
+    fb->WT = p.wt;
+    fb->WTlo = p.wtlo;
+    fb->n = n;
+    fb->status = &p.hdr->status;
+    X = static_cast<const float*>(p.wq[b]);
+    ld = n;
+  }
+  *tb = WideTcBlock{X, ld, n, rows, rows_dev, 1, splits, sr, splits, 0};
+  tb->part = p.gpart[b];
   tb->status = &p.hdr->status;
 }
 
-cudaError_t launch_narrow_q_gram_tc(const Plan& p, int* count, cudaStream_t s) {
-  cudaError_t err = launch_wide_form_prep(p.Wf, p.n, p.wt, p.wtlo, s);
-  if (err != cudaSuccess) return err;
+cudaError_t launch_narrow_tc(const Plan& p, int pass, const bool use[3], int count[3], cudaStream_t s) {
   WideFormBlock fb[3] = {};
   WideTcBlock tb[3] = {};
-  narrow_q_tc_blocks(p, 0, &fb[0], &tb[0]);
-  err = launch_wide_form_tc(fb, p.wt, p.wtlo, p.n, &p.hdr->status, p.spin_limit, s);
-  if (err != cudaSuccess) return err;
-  err = launch_wide_gram_tc(tb, p.gpart[1], &p.hdr->status, p.spin_limit, s);
-  *count = tb[0].njobs;
-  return err;
+  bool form = false;
+  for (int b = 0; b < 2; ++b) {
+    count[b] = 0;
+    if (!use[b]) continue;
+    narrow_tc_blocks(p, pass, b, 0, &fb[b], &tb[b]);
+    // one launch for both blocks: partials of block 1 at their offset from block 0's buffer (one workspace)
+    tb[b].pbase = p.gpart[b] - p.gpart[0];
+    count[b] = tb[b].njobs;
+    form = form || fb[b].njobs > 0;
+  }
+  cudaError_t err;
+  if (form) {
+    err = launch_wide_form_prep(p.Wf, p.n, p.wt, p.wtlo, s);
+    if (err != cudaSuccess) return err;
+    err = launch_wide_form_tc(fb, p.wt, p.wtlo, p.n, &p.hdr->status, p.spin_limit, s);
+    if (err != cudaSuccess) return err;
+  }
+  return launch_wide_gram_tc(tb, p.gpart[0], &p.hdr->status, p.spin_limit, s);
 }
 
 static cudaError_t wide_first(const Plan& p, int from_r, cudaStream_t s) {
