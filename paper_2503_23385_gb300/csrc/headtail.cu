@@ -630,8 +630,9 @@ __device__ __forceinline__ void ht_stream_body(const CUtensorMap* tm, const HtAr
   // steps k of the tile in 3 x TF32 (hi x hi + hi x lo + lo x hi) with warp
   // MMAs (m16n8k8; the A and B fragments of T^T T are the same four values
   // per lane), accumulating its 16 x 16 partial in FP32 over the CTA's
-  // tiles.  The stage is released after the next tile's first barrier, when
-  // every thread is past it.
+  // tiles (as D = H^T H + (2L)^T H, whose symmetric part is the Gram: two MMAs
+  // per 8-column block instead of three).  The stage is released after the
+  // next tile's first barrier, when every thread is past it.
   constexpr bool kGramOk = V == 4 && sizeof(Tin) == 4 && sizeof(Tc) == 4;
   const bool fuse = kGramOk && T.gram != nullptr;
   float gd0[4] = {0.f, 0.f, 0.f, 0.f}, gd1[4] = {0.f, 0.f, 0.f, 0.f};  // G[:, 0:8], G[:, 8:16] fragments
@@ -867,18 +868,17 @@ __device__ __forceinline__ void ht_stream_body(const CUtensorMap* tm, const HtAr
         const int ra = ks * 8 + tq, rb = ra + 4;
         const float v[4] = {ra < cnt ? tt[ra * n + gq] : 0.f, (n > 8 && ra < cnt) ? tt[ra * n + gq + 8] : 0.f,
                             rb < cnt ? tt[rb * n + gq] : 0.f, (n > 8 && rb < cnt) ? tt[rb * n + gq + 8] : 0.f};
-        uint32_t h[4], l[4];
+        uint32_t h[4], l2[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           h[k] = __float_as_uint(v[k]) & 0xffffe000u;  // TF32 hi: truncation
-          l[k] = (__float_as_uint(__fsub_rn(v[k], __uint_as_float(h[k]))) + 0x1000u) & 0xffffe000u;  // lo, rounded
+          const uint32_t lo = (__float_as_uint(__fsub_rn(v[k], __uint_as_float(h[k]))) + 0x1000u) & 0xffffe000u;
+          l2[k] = __float_as_uint(2.f * __uint_as_float(lo));  // 2 lo (exact): D = H^T H + (2L)^T H, G = (D + D^T) / 2
         }
-        mma_m16n8k8_tf32(gd0, l, h[0], h[2]);
-        mma_m16n8k8_tf32(gd0, h, l[0], l[2]);
+        mma_m16n8k8_tf32(gd0, l2, h[0], h[2]);
         mma_m16n8k8_tf32(gd0, h, h[0], h[2]);
         if (n > 8) {
-          mma_m16n8k8_tf32(gd1, l, h[1], h[3]);
-          mma_m16n8k8_tf32(gd1, h, l[1], l[3]);
+          mma_m16n8k8_tf32(gd1, l2, h[1], h[3]);
           mma_m16n8k8_tf32(gd1, h, h[1], h[3]);
         }
       }
@@ -909,7 +909,11 @@ __device__ __forceinline__ void ht_stream_body(const CUtensorMap* tm, const HtAr
       float hh = 0.f, ll = 0.f;
       for (int w = 0; w < kHtConsumers / 32; ++w) {
         float s_, e_;
-        two_sum(hh, all[w * 256 + i * 16 + j], s_, e_);
+        // (the symmetric part of D: halving is exact)
+        two_sum(hh, 0.5f * all[w * 256 + i * 16 + j], s_, e_);
+        hh = s_;
+        ll = __fadd_rn(ll, e_);
+        two_sum(hh, 0.5f * all[w * 256 + j * 16 + i], s_, e_);
         hh = s_;
         ll = __fadd_rn(ll, e_);
       }
