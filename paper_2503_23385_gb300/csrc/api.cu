@@ -209,18 +209,31 @@ struct Call {
   bool events = false;
   // host tables: the feature copies run on side streams while the call's
   // stream groups the keys; the call's stream waits for them (join_staging)
-  // before the first step that reads features
+  // before the first step that reads features, table by table where the
+  // head/tail step runs per table
   cudaEvent_t staged[kStageStreams] = {};
+  int staged_table[kStageStreams] = {};
   int nstaged = 0;
-  cudaError_t join_staging() {
+  cudaError_t join_staging(int table = -1) {
     cudaError_t err = cudaSuccess;
+    int kept = 0;
     for (int i = 0; i < nstaged; ++i) {
+      if (table >= 0 && staged_table[i] != table) {
+        staged[kept] = staged[i];
+        staged_table[kept++] = staged_table[i];
+        continue;
+      }
       const cudaError_t e = cudaStreamWaitEvent(s, staged[i], 0);
       if (e != cudaSuccess && err == cudaSuccess) err = e;
       cudaEventDestroy(staged[i]);
     }
-    nstaged = 0;
+    nstaged = kept;
     return err;
+  }
+  bool staged_both() const {
+    bool t0 = false, t1 = false;
+    for (int i = 0; i < nstaged; ++i) (staged_table[i] ? t1 : t0) = true;
+    return t0 && t1;
   }
   cudaError_t mark(int i) {
     if (!events) return cudaSuccess;
@@ -339,6 +352,8 @@ figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, con
     if (stage_streams(ss) != cudaSuccess || cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventRecord(fork, c.s) != cudaSuccess)
       return FIGARO_ERR_CUDA;
+    // (table B's copies start when table A's have landed: the link is shared,
+    // so A arrives in half the time and its head/tail step overlaps B's copy)
     int part = 0;
     cudaError_t err = cudaSuccess;
     for (int t = 0; t < 2 && err == cudaSuccess; ++t) {
@@ -346,12 +361,14 @@ figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, con
       if (src->memory != FIGARO_MEM_HOST || src->m == 0) continue;
       TableWork& T = c.p.t[t];
       const int64_t half = (src->m + 1) / 2;
+      const int earlier = c.nstaged;  // table A's copies, when t = 1
       for (int h = 0; h < 2 && err == cudaSuccess; ++h) {
         const int64_t r0 = h * half, r1 = h ? src->m : half;
         if (r1 <= r0) continue;
         cudaStream_t st = ss[part];
         cudaEvent_t done = nullptr;
         err = cudaStreamWaitEvent(st, fork, 0);
+        for (int i = 0; i < earlier && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(st, c.staged[i], 0);
         char* dst = static_cast<char*>(const_cast<void*>(T.x)) + static_cast<size_t>(r0) * src->n * ei;
         const char* from = static_cast<const char*>(src->x) + static_cast<size_t>(r0) * src->ld * ei;
         if (err == cudaSuccess && src->ld == src->n)  // dense rows: one contiguous copy
@@ -362,7 +379,10 @@ figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, con
                                   st);
         if (err == cudaSuccess) err = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
         if (err == cudaSuccess) err = cudaEventRecord(done, st);
-        if (done) c.staged[c.nstaged++] = done;
+        if (done) {
+          c.staged_table[c.nstaged] = t;
+          c.staged[c.nstaged++] = done;
+        }
         ++part;
       }
     }
@@ -397,11 +417,23 @@ figaro_status run_grouping(Call& c) {
 }
 
 figaro_status run_factor(Call& c, double* R_dev, int64_t ldr) {
-  FIGARO_TRY(c.join_staging());  // the features are read from here on
-  FIGARO_TRY(launch_ht_carry(c.p, c.s));
-  FIGARO_TRY(c.mark(2));
+  // both tables staged from host memory: the head/tail step runs per table,
+  // each as its features land
+  c.p.ht_split = c.staged_both() ? 1 : 0;
   ht_plan_gram1(c.p);  // pass 1 of the tail blocks inside the head/tail stream, where it applies
-  FIGARO_TRY(launch_ht_main(c.p, c.s));
+  if (c.p.ht_split) {
+    for (int t = 0; t < 2; ++t) {
+      FIGARO_TRY(c.join_staging(t));
+      FIGARO_TRY(launch_ht_carry(c.p, c.s, t));
+      if (t == 0) FIGARO_TRY(c.mark(2));
+      FIGARO_TRY(launch_ht_main(c.p, c.s, t));
+    }
+  } else {
+    FIGARO_TRY(c.join_staging());  // the features are read from here on
+    FIGARO_TRY(launch_ht_carry(c.p, c.s));
+    FIGARO_TRY(c.mark(2));
+    FIGARO_TRY(launch_ht_main(c.p, c.s));
+  }
   FIGARO_TRY(c.mark(3));
   FIGARO_TRY(launch_gram_pass(c.p, 1, c.s));
   FIGARO_TRY(c.mark(4));

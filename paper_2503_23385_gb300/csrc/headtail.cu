@@ -1162,8 +1162,18 @@ int ht_chunk_rows(int n, int in_f64, int mixed) {
   return L;
 }
 
-cudaError_t launch_ht_carry(const Plan& p, cudaStream_t s) {
-  const HtArgs a = make_args(p);
+// Arguments of the head/tail step restricted to table `only` (-1: both).
+static HtArgs args_for(const Plan& p, int only) {
+  HtArgs a = make_args(p);
+  if (only >= 0) {
+    a.t[1 - only].chunks = 0;
+    a.c0 = a.t[0].chunks;
+  }
+  return a;
+}
+
+cudaError_t launch_ht_carry(const Plan& p, cudaStream_t s, int only) {
+  const HtArgs a = args_for(p, only);
   const int grid = a.t[0].chunks + a.t[1].chunks;
   if (grid == 0) return cudaSuccess;
   const int ncols = (a.t[0].chunks > 0 ? a.t[0].n : 0) + (a.t[1].chunks > 0 ? a.t[1].n : 0);
@@ -1183,18 +1193,19 @@ static bool ht_use_v4(const HtArgs& a) {
   return v4;
 }
 
-cudaError_t launch_ht_main(const Plan& p, cudaStream_t s) {
-  HtArgs a = make_args(p);
+cudaError_t launch_ht_main(const Plan& p, cudaStream_t s, int only) {
+  HtArgs a = args_for(p, only);
   const int grid = a.t[0].chunks + a.t[1].chunks;
   if (grid == 0) return cudaSuccess;
   const bool in64 = p.t[0].in_f64 != 0;
   const int sms = p.num_sms;
   const int64_t sl = p.spin_limit;
   const bool v4 = ht_use_v4(a);
-  const int* g = p.ht_grid;
+  int g[2] = {p.ht_grid[0], p.ht_grid[1]};
+  if (only >= 0) g[1 - only] = 0;
   if (p.ht_gram[0] > 0 || p.ht_gram[1] > 0) {  // (planned for the FP32 4-column kernel only)
     if (in64 || !p.mixed || !v4) return cudaErrorInvalidValue;
-    for (int t = 0; t < 2; ++t) a.t[t].gram = p.ht_gram[t] > 0 ? p.gpart[1 + t] : nullptr;
+    for (int t = 0; t < 2; ++t) a.t[t].gram = p.ht_gram[t] > 0 && a.t[t].chunks > 0 ? p.gpart[1 + t] : nullptr;
   }
   if (in64) {
     if (p.mixed) return v4 ? launch_typed_main<double, float, 4>(a, sms, g, sl, s) : launch_typed_main<double, float, 1>(a, sms, g, sl, s);
@@ -1219,7 +1230,15 @@ void ht_plan_gram1(Plan& p) {
   int smem = 0, occ = 0;
   if (ht_stream_setup<float, float, 4>(a, &smem, &occ) != cudaSuccess) return;
   int g[2] = {0, 0};
-  ht_split(a, p.num_sms * occ, &g[0], &g[1]);
+  if (p.ht_split) {  // one launch per table, each on the whole GPU
+    for (int t = 0; t < 2; ++t) {
+      int g0 = 0, g1 = 0;
+      ht_split(args_for(p, t), p.num_sms * occ, &g0, &g1);
+      g[t] = t ? g1 : g0;
+    }
+  } else {
+    ht_split(a, p.num_sms * occ, &g[0], &g[1]);
+  }
   for (int t = 0; t < 2; ++t) {
     const int n = a.t[t].n;
     if (a.t[t].chunks > 0 && (n == 8 || n == 16) && p.gpart[1 + t] &&

@@ -99,6 +99,7 @@ struct Plan {
   // Gram partials of its tails those CTAs write (0: the Gram pass reads the tails)
   int ht_grid[2] = {0, 0};
   int ht_gram[2] = {0, 0};
+  int ht_split = 0;  // the head/tail step runs per table (host-staged tables), each launch on the whole GPU
   int64_t lut_size = 0;         // entries of each table's key lookup table
   DevHeader* hdr = nullptr;
   void* head = nullptr;         // m1 x n slots, compute type
@@ -220,8 +221,9 @@ size_t plan_layout(Plan& p, const void* ws_base, int64_t m1, int n1, int64_t m2,
 // Launchers (each returns the first CUDA error it meets).
 cudaError_t launch_reset(const Plan& p, cudaStream_t s);
 cudaError_t launch_grouping(const Plan& p, cudaStream_t s);
-cudaError_t launch_ht_carry(const Plan& p, cudaStream_t s);
-cudaError_t launch_ht_main(const Plan& p, cudaStream_t s);
+// only: the table to process (-1: both in one launch)
+cudaError_t launch_ht_carry(const Plan& p, cudaStream_t s, int only = -1);
+cudaError_t launch_ht_main(const Plan& p, cudaStream_t s, int only = -1);
 // Decides, before launch_ht_main, which tables' pass-1 Gram partials the
 // head/tail stream accumulates (mixed path, FP32 tables of 8 or 16
 // columns on the 4-column consumers, automatic Gram engine).

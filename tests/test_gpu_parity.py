@@ -276,11 +276,11 @@ def test_gram_engines_agree_with_oracle(fg, torch, shape):
 @pytest.mark.parametrize("shape", [(20000, 64, 15000, 64, 300), (9001, 32, 12345, 64, 77), (5000, 64, 6000, 8, 40)],
                          ids=["128", "96-ragged", "72"])
 def test_wide_q_tail_block_on_tensor_cores(fg, torch, shape):
-    """Joins of 65 to 128 columns: in a single call, pass 2 of the A tails
-    (Q has n columns, more than the narrow tensor-core engines take) runs the
-    tensor-core formation and tile Gram.  Both engine settings meet the
-    mixed-path bar and agree; a batch holding the same join (which keeps the
-    block on CUDA cores) does too."""
+    """Joins of 65 to 128 columns: the Gram blocks with n output columns, more
+    than the narrow tensor-core engines take (the head rows in both passes,
+    pass 2 of the A tails after the tensor-core formation Q = X W), run the
+    tile Gram.  Both engine settings meet the mixed-path bar and agree; a batch
+    holding the same join (table launches of the same kernels) does too."""
     m1, n1, m2, n2, K = shape
     A, B = make_pair(m1, n1, m2, n2, K, np.float32, "normal", seed=m1 + n2)
     Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key)
@@ -298,6 +298,32 @@ def test_wide_q_tail_block_on_tensor_cores(fg, torch, shape):
     assert rel(Rb.cpu().numpy(), Rref) <= 1e-6 and rel(sb.cpu().numpy(), sref) <= 1e-6
     R2, s2 = oracle.join_r_sigma(small[0].x, small[0].key, small[1].x, small[1].key)
     assert rel(outs[1][0].cpu().numpy(), R2) <= 1e-6 and rel(outs[1][1].cpu().numpy(), s2) <= 1e-6
+
+
+@pytest.mark.parametrize("shape", [(20000, 16, 15000, 8, 300), (257, 8, 1000, 16, 20), (9001, 16, 123, 16, 40),
+                                   (3000, 8, 4000, 32, 50)],
+                         ids=["16+8", "ragged-tile", "short-B", "8+32-one-table"])
+def test_tail_gram_inside_head_tail_stream(fg, torch, shape):
+    """Mixed path, FP32 tables of 8 or 16 columns, automatic engine: the
+    head/tail stream also accumulates the pass-1 Gram of those tables' tails
+    (3xTF32 warp MMAs on each tile), so pass 1 launches the Gram only for the
+    head rows and the other tables.  The result meets the mixed-path bar and
+    agrees with the tensor-core engine setting, whose pass 1 reads the tails;
+    the automatic call makes fewer launches."""
+    m1, n1, m2, n2, K = shape
+    A, B = make_pair(m1, n1, m2, n2, K, np.float32, "normal", seed=m1 + 3 * n2)
+    Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key)
+    out, launches = {}, {}
+    for eng in (fg.GRAM_TCGEN05, fg.GRAM_AUTO):
+        before = fg.kernel_launches()
+        R, s = fg.join_qr_svd(dev(torch, A), dev(torch, B), path="mixed", gram_engine=eng)
+        torch.cuda.synchronize()
+        launches[eng] = fg.kernel_launches() - before
+        R, s = R.cpu().numpy(), s.cpu().numpy()
+        assert rel(R, Rref) <= 1e-6 and rel(s, sref) <= 1e-6, (eng, rel(R, Rref), rel(s, sref))
+        out[eng] = R
+    assert rel(out[fg.GRAM_TCGEN05], out[fg.GRAM_AUTO]) <= 1e-6
+    assert launches[fg.GRAM_AUTO] < launches[fg.GRAM_TCGEN05], launches
 
 
 # ---------------------------------------------------------- status codes --
