@@ -114,6 +114,13 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t da, uint64_t d
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
+// One lane of the (converged) warp, chosen by the hardware.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t e;
+  asm volatile("{ .reg .pred p; elect.sync _|p, 0xffffffff; selp.u32 %0, 1, 0, p; }" : "=r"(e));
+  return e != 0;
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -347,24 +354,36 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArg
     __syncthreads();
     uint32_t ah = smem_u32(X), al = smem_u32(Xl);
     if (pass2) {
-      if (tid == 0) {  // D1 = X W (3 x TF32), the large term last
+      if (warp == 0) {  // D1 = X W (3 x TF32), the large term last
+        // the warp runs the issue (descriptors built once: their address
+        // field is bytes / 16, so K steps are constants added to a base),
+        // one elected lane issues the straight run of MMAs
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool leader = elect_one();
         const uint32_t idf = idesc_tf32(128, a.np);
-        const uint32_t wh = smem_u32(base + a.off_wh), wl = smem_u32(base + a.off_wl);
-        uint32_t acc = 0;
-        for (int ks = 0; ks < a.ksteps_f; ++ks) {
-          const uint32_t ao = static_cast<uint32_t>((ks >> 2) * kPanelBytes + (ks & 3) * 32);
-          const uint32_t bo = static_cast<uint32_t>((ks >> 2) * a.wpanel_bytes + (ks & 3) * 32);
-          mma_tf32(d1, desc_kmajor_sw128(al + ao), desc_kmajor_sw128(wh + bo), idf, acc);
-          acc = 1;
-          mma_tf32(d1, desc_kmajor_sw128(ah + ao), desc_kmajor_sw128(wl + bo), idf, 1);
+        const uint64_t dah = desc_kmajor_sw128(ah), dal = desc_kmajor_sw128(al);
+        const uint64_t dwh = desc_kmajor_sw128(smem_u32(base + a.off_wh));
+        const uint64_t dwl = desc_kmajor_sw128(smem_u32(base + a.off_wl));
+        const int wp16 = a.wpanel_bytes >> 4, ksf = a.ksteps_f;
+        if (leader) {
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks)
+            if (ks < ksf) {
+              const uint64_t ao = static_cast<uint64_t>((ks >> 2) * (kPanelBytes >> 4) + (ks & 3) * 2);
+              const uint64_t bo = static_cast<uint64_t>((ks >> 2) * wp16 + (ks & 3) * 2);
+              mma_tf32(d1, dal + ao, dwh + bo, idf, ks > 0 ? 1u : 0u);
+              mma_tf32(d1, dah + ao, dwl + bo, idf, 1u);
+            }
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks)
+            if (ks < ksf) {
+              const uint64_t ao = static_cast<uint64_t>((ks >> 2) * (kPanelBytes >> 4) + (ks & 3) * 2);
+              const uint64_t bo = static_cast<uint64_t>((ks >> 2) * wp16 + (ks & 3) * 2);
+              mma_tf32(d1, dah + ao, dwh + bo, idf, 1u);
+            }
+          mma_commit(&bar_f);
         }
-        for (int ks = 0; ks < a.ksteps_f; ++ks) {
-          const uint32_t ao = static_cast<uint32_t>((ks >> 2) * kPanelBytes + (ks & 3) * 32);
-          const uint32_t bo = static_cast<uint32_t>((ks >> 2) * a.wpanel_bytes + (ks & 3) * 32);
-          mma_tf32(d1, desc_kmajor_sw128(ah + ao), desc_kmajor_sw128(wh + bo), idf, 1);
-        }
-        mma_commit(&bar_f);
+        __syncwarp();
       }
       if (!mbar_wait(&bar_f, f_phase, a.spin_limit)) {
         if (tid == 0) {
@@ -411,22 +430,30 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArg
       ah = smem_u32(qh);
       al = smem_u32(ql);
     }
-    if (tid == 0) {  // Gram MMAs, both operands MN-major: P += hi^T (2 lo) + hi^T hi
+    if (warp == 0) {  // Gram MMAs, both operands MN-major: P += hi^T (2 lo) + hi^T hi (issued as the formation)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const bool leader = elect_one();
       const uint32_t idg = idesc_tf32(a.mg, a.np, 1);
       constexpr int kSteps = kTileRows / 8, kPer = kSteps / kHiAcc;
-      for (int q = 0; q < kHiAcc; ++q) {
-        const uint32_t d = dacc + static_cast<uint32_t>(q * NP);
-        for (int s = 0; s < kPer; ++s) {
-          const uint32_t o = static_cast<uint32_t>((q * kPer + s) * 1024);
-          mma_tf32(d, desc_mn_sw128_32b(ah + o, panel_mn), desc_mn_sw128_32b(al + o, panel_mn), idg, s > 0 ? 1u : 0u);
+      const uint64_t dh = desc_mn_sw128_32b(ah, panel_mn), dl = desc_mn_sw128_32b(al, panel_mn);
+      if (leader) {
+#pragma unroll
+        for (int q = 0; q < kHiAcc; ++q) {
+          const uint32_t d = dacc + static_cast<uint32_t>(q * NP);
+#pragma unroll
+          for (int s = 0; s < kPer; ++s) {
+            const uint64_t o = static_cast<uint64_t>(((q * kPer + s) * 1024) >> 4);
+            mma_tf32(d, dh + o, dl + o, idg, s > 0 ? 1u : 0u);
+          }
+#pragma unroll
+          for (int s = 0; s < kPer; ++s) {
+            const uint64_t o = static_cast<uint64_t>(((q * kPer + s) * 1024) >> 4);
+            mma_tf32(d, dh + o, dh + o, idg, 1u);
+          }
         }
-        for (int s = 0; s < kPer; ++s) {
-          const uint32_t o = static_cast<uint32_t>((q * kPer + s) * 1024);
-          mma_tf32(d, desc_mn_sw128_32b(ah + o, panel_mn), desc_mn_sw128_32b(ah + o, panel_mn), idg, 1u);
-        }
+        mma_commit(&bar_g);
       }
-      mma_commit(&bar_g);
+      __syncwarp();
     }
     pending_g = true;
   }
@@ -561,12 +588,6 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
 }
 
 // One lane of the (fully active) warp: the issuer of a warp-wide MMA loop.
-__device__ __forceinline__ bool elect_one() {
-  uint32_t e;
-  asm volatile("{ .reg .pred p; elect.sync _|p, 0xffffffff; selp.u32 %0, 1, 0, p; }" : "=r"(e));
-  return e != 0;
-}
-
 __device__ __forceinline__ void mbar_arrive_cta(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
