@@ -50,7 +50,9 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTileRows = 128;
 constexpr int kPanelBytes = kTileRows * 128;  // one 32-column panel of an X tile
-constexpr int kHiAcc = 4;  // accumulators per tile (4 K-steps of 8 rows each)
+constexpr int kHiAcc = 4;  // accumulators per tile of the pipelined engine (4 K-steps of 8 rows each)
+constexpr int kTcAcc = 2;  // accumulators per tile of the general engine (8 K-steps each; with the formation
+                           // buffer 3 x 64 columns of tensor memory, so that two CTAs share an SM)
 
 struct TcArgs {
   int k;             // columns of X (multiple of 4)
@@ -70,6 +72,7 @@ struct TcArgs {
   int64_t spin_limit;
   // shared memory offsets (bytes from the 1024-aligned base)
   int off_x[2], off_xlo, off_wh, off_wl, off_qh, off_ql;
+  int alias;         // pass 2, wide Q: one X buffer, Q's lo part over X and its lo part (two CTAs per SM)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -208,8 +211,8 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArg
   const bool pass2 = a.W != nullptr;
   const int64_t rows = a.rows_dev ? *a.rows_dev : a.rows;
   const int64_t ntiles = (rows + kTileRows - 1) / kTileRows;
-  // formation result + kHiAcc Gram accumulators, NP columns each
-  constexpr uint32_t kCols = (kHiAcc + 1) * NP;
+  // formation result + kTcAcc Gram accumulators, NP columns each
+  constexpr uint32_t kCols = (kTcAcc + 1) * NP;
   const uint32_t tmem_cols = kCols <= 32 ? 32 : (kCols <= 64 ? 64 : (kCols <= 128 ? 128 : (kCols <= 256 ? 256 : 512)));
 
   if (tid == 0) {
@@ -248,7 +251,7 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArg
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t d1 = tmem;                                   // formation result: 128 lanes x NP
-  const uint32_t dacc = tmem + static_cast<uint32_t>(NP);    // kHiAcc Gram accumulators of NP columns
+  const uint32_t dacc = tmem + static_cast<uint32_t>(NP);    // kTcAcc Gram accumulators of NP columns
   const uint32_t tile_bytes = static_cast<uint32_t>(a.kpanels * kPanelBytes);
 
   // prologue: the first tile of this block (each later tile is loaded one
@@ -276,7 +279,7 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArg
       float sum[32], v[32];
       tmem_ld32(dacc + (static_cast<uint32_t>(warp * 32) << 16) + c0, sum);
 #pragma unroll 1
-      for (int q = 1; q < kHiAcc; ++q) {
+      for (int q = 1; q < kTcAcc; ++q) {
         tmem_ld32(dacc + (static_cast<uint32_t>(warp * 32) << 16) + q * NP + c0, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) sum[j] = __fadd_rn(sum[j], v[j]);
@@ -297,7 +300,7 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArg
   bool pending_g = false;  // Gram MMAs committed and not yet waited for
   uint32_t g_phase = 0, f_phase = 0;
   for (int64_t rt = cta; rt < ntiles; rt += G, ++it) {
-    const int buf = it & 1;
+    const int buf = a.alias ? 0 : (it & 1);
     float* X = reinterpret_cast<float*>(base + a.off_x[buf]);
     float* Xl = reinterpret_cast<float*>(base + a.off_xlo);
     if (pending_g) {  // the previous tile's Gram MMAs: operands and accumulators become free
@@ -313,16 +316,22 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArg
       if (s_abort) break;
       drain();
     }
-    if (tid == 0) {  // the other buffer is free: load the next tile into it
-      const int64_t nt = rt + static_cast<int64_t>(G);
-      if (nt < ntiles) {
-        expect_tx(&bar_tma[buf ^ 1], tile_bytes);
+    if (tid == 0) {
+      if (!a.alias) {  // the other buffer is free: load the next tile into it
+        const int64_t nt = rt + static_cast<int64_t>(G);
+        if (nt < ntiles) {
+          expect_tx(&bar_tma[buf ^ 1], tile_bytes);
+          for (int p = 0; p < a.kpanels; ++p)
+            tma_load_2d(base + a.off_x[buf ^ 1] + p * kPanelBytes, tmx, p * 32, static_cast<int>(nt * kTileRows),
+                        &bar_tma[buf ^ 1]);
+        }
+      } else if (it > 0) {  // one buffer (the first tile came with the prologue): the previous Gram is done
+        expect_tx(&bar_tma[0], tile_bytes);
         for (int p = 0; p < a.kpanels; ++p)
-          tma_load_2d(base + a.off_x[buf ^ 1] + p * kPanelBytes, tmx, p * 32, static_cast<int>(nt * kTileRows),
-                      &bar_tma[buf ^ 1]);
+          tma_load_2d(base + a.off_x[0] + p * kPanelBytes, tmx, p * 32, static_cast<int>(rt * kTileRows), &bar_tma[0]);
       }
     }
-    if (!mbar_wait(&bar_tma[buf], static_cast<uint32_t>((it >> 1) & 1), a.spin_limit)) {
+    if (!mbar_wait(&bar_tma[buf], static_cast<uint32_t>(a.alias ? (it & 1) : ((it >> 1) & 1)), a.spin_limit)) {
       if (tid == 0) {
         set_status(a.status, kStatusTimeout);
         s_abort = 1;
@@ -434,11 +443,11 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* tmx, const TcArg
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const bool leader = elect_one();
       const uint32_t idg = idesc_tf32(a.mg, a.np, 1);
-      constexpr int kSteps = kTileRows / 8, kPer = kSteps / kHiAcc;
+      constexpr int kSteps = kTileRows / 8, kPer = kSteps / kTcAcc;
       const uint64_t dh = desc_mn_sw128_32b(ah, panel_mn), dl = desc_mn_sw128_32b(al, panel_mn);
       if (leader) {
 #pragma unroll
-        for (int q = 0; q < kHiAcc; ++q) {
+        for (int q = 0; q < kTcAcc; ++q) {
           const uint32_t d = dacc + static_cast<uint32_t>(q * NP);
 #pragma unroll
           for (int s = 0; s < kPer; ++s) {
@@ -1534,6 +1543,21 @@ __host__ __device__ inline Geometry geometry(int k, int kout, bool pass2) {
   a.off_wl = pass2 ? geo_take(off, a.kpanels * a.wpanel_bytes) : 0;
   a.off_qh = pass2 ? geo_take(off, a.qpanels * kPanelBytes) : 0;
   a.off_ql = pass2 ? geo_take(off, a.qpanels * kPanelBytes) : 0;
+  a.alias = 0;
+  if (pass2 && off + 1024 > 110 * 1024 && 2 * xb >= a.qpanels * kPanelBytes) {
+    // too large for two CTAs per SM: X single-buffered (each tile loaded once
+    // the previous tile's Gram is done) and Q's lo part over X and X's lo
+    // part, which the formation has consumed by then
+    off = 0;
+    a.off_x[0] = geo_take(off, xb);
+    a.off_xlo = geo_take(off, xb);  // (directly after X: one region of 2 xb bytes)
+    a.off_x[1] = a.off_x[0];
+    a.off_wh = geo_take(off, a.kpanels * a.wpanel_bytes);
+    a.off_wl = geo_take(off, a.kpanels * a.wpanel_bytes);
+    a.off_qh = geo_take(off, a.qpanels * kPanelBytes);
+    a.off_ql = a.off_x[0];
+    a.alias = 1;
+  }
   g.smem = static_cast<size_t>(off) + 1024;  // + alignment of the dynamic base
   return g;
 }
