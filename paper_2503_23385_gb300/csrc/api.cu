@@ -535,8 +535,10 @@ size_t batch_area_bytes(int count) {
   // CTA offsets
   const size_t tables = (3 * sizeof(WideTcEntry) + 2 * sizeof(WideFormEntry) + sizeof(WidePrepEntry) +
                          6 * sizeof(int32_t)) * static_cast<size_t>(count) + 12 * 128;
-  return ((sizeof(Plan) + sizeof(BatchOut)) * static_cast<size_t>(count) + lists * per_list + tables + 4096 + 255) &
-         ~static_cast<size_t>(255);
+  // per pass the jobs' Gram arguments (three blocks) and reduce arguments of every instance
+  const size_t args = 2 * (3 * batch_gram_args_bytes() + batch_reduce_args_bytes()) * static_cast<size_t>(count) + 512;
+  return ((sizeof(Plan) + sizeof(BatchOut)) * static_cast<size_t>(count) + lists * per_list + tables + args + 4096 +
+          255) & ~static_cast<size_t>(255);
 }
 
 struct JobList {
@@ -744,7 +746,16 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   JobList* dl[3] = {dense1, dense2, dense3};
   for (int st = 0; st < 3; ++st)
     for (int v = 0; v < 3; ++v) Jd[st][v] = stage_jobs(blob, dl[st][v], fix, &Jd[st][v]);
-  if (blob.bytes.size() > area_bytes) return FIGARO_ERR_WORKSPACE_TOO_SMALL;
+  // after the uploaded part: per pass the jobs' Gram and reduce arguments,
+  // written on the device at the start of each Gram pass
+  const size_t gab = batch_gram_args_bytes() * 3 * count, rab = batch_reduce_args_bytes() * count;
+  const size_t off_args = (blob.bytes.size() + 255) & ~static_cast<size_t>(255);
+  size_t off_gargs[2], off_rargs[2];
+  for (int q = 0; q < 2; ++q) {
+    off_gargs[q] = off_args + q * (gab + rab + 16);
+    off_rargs[q] = (off_gargs[q] + gab + 15) & ~static_cast<size_t>(15);
+  }
+  if (blob.bytes.size() > area_bytes || off_rargs[1] + rab > area_bytes) return FIGARO_ERR_WORKSPACE_TOO_SMALL;
   for (auto& f : fix) {
     f.first->first = reinterpret_cast<const int32_t*>(area + f.second[0]);
     f.first->inst = reinterpret_cast<const int32_t*>(area + f.second[1]);
@@ -781,7 +792,10 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   const size_t none_smem[4] = {0, 0, 0, 0};
   auto gram_pass = [&](int pass) -> figaro_status {
     const BatchJobs empty{};
-    FIGARO_TRY(launch_batch_gram(b, pass, Jgram[pass - 1], gram_smem[pass - 1], empty, mixed, s));
+    void* gargs = area + off_gargs[pass - 1];
+    void* rargs = area + off_rargs[pass - 1];
+    FIGARO_TRY(launch_batch_args(b, pass, gargs, rargs, s));
+    FIGARO_TRY(launch_batch_gram(b, pass, Jgram[pass - 1], gram_smem[pass - 1], empty, mixed, gargs, rargs, s));
     for (int e = 0; e < 2; ++e)
       for (int v = 0; v < 4; ++v) {
         const auto& jobs = tc[pass - 1][e][v];
@@ -803,7 +817,7 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
                                            reinterpret_cast<const int32_t*>(at(Q.off_t0)),
                                            static_cast<int>(Q.t.size()), Q.t0.back(), p0.spin_limit, s));
     }
-    FIGARO_TRY(launch_batch_gram(b, pass, none, none_smem, Jreduce, mixed, s));
+    FIGARO_TRY(launch_batch_gram(b, pass, none, none_smem, Jreduce, mixed, gargs, rargs, s));
     return FIGARO_OK;
   };
   figaro_status gs = gram_pass(1);

@@ -409,12 +409,25 @@ __host__ __device__ inline ReduceArgs reduce_args_of(const Plan& p, int pass) {
 // aux = block and p.ggrid[block] CTAs; reduce jobs are instances with
 // aux = 1 and ceil(n^2 / 512) CTAs (a warp per 32 outputs) when every block
 // has few partials, else aux = 0 and ceil(n^2 / 32) CTAs
+// (the arguments of each CTA's job are precomputed on the host when `args`
+// is set: computing them from the plan is a chain of dependent loads by one
+// thread, which dominated launches of thousands of small CTAs)
+template <typename A>
+__device__ __forceinline__ void copy_args(A* dst, const A* src) {
+  static_assert(sizeof(A) % 4 == 0, "word copy");
+  const uint32_t* s_ = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d_ = reinterpret_cast<uint32_t*>(dst);
+  for (int w = threadIdx.x; w < static_cast<int>(sizeof(A) / 4); w += blockDim.x) d_[w] = s_[w];
+}
+
 template <typename T, int TPT>
-__global__ void __launch_bounds__(kGramThreads) gram_batched(BatchDev bd, BatchJobs J, int pass) {
+__global__ void __launch_bounds__(kGramThreads) gram_batched(BatchDev bd, BatchJobs J, int pass, const GramArgs* args) {
   pdl_enter();
   __shared__ GramArgs s_a;
   const int j = batch_job(J, blockIdx.x);
-  if (threadIdx.x == 0) {
+  if (args) {
+    copy_args(&s_a, args + static_cast<int64_t>(J.inst[j]) * 3 + J.aux[j]);
+  } else if (threadIdx.x == 0) {
     int64_t rows = 0;
     int tpt = 0;
     s_a = gram_args_of(bd.plans[J.inst[j]], pass, J.aux[j], &rows, &tpt);
@@ -423,11 +436,13 @@ __global__ void __launch_bounds__(kGramThreads) gram_batched(BatchDev bd, BatchJ
   gram_body<T, TPT>(s_a, blockIdx.x - J.first[j], J.first[j + 1] - J.first[j]);
 }
 
-__global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_batched(BatchDev bd, BatchJobs J, int pass) {
+__global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_batched(BatchDev bd, BatchJobs J, int pass,
+                                                                        const ReduceArgs* args) {
   pdl_enter();
   __shared__ ReduceArgs s_r;
   const int j = batch_job(J, blockIdx.x);
-  if (threadIdx.x == 0) s_r = reduce_args_of(bd.plans[J.inst[j]], pass);
+  if (args) copy_args(&s_r, args + J.inst[j]);
+  else if (threadIdx.x == 0) s_r = reduce_args_of(bd.plans[J.inst[j]], pass);
   __syncthreads();
   if (J.aux[j]) gram_reduce_body<true>(s_r, blockIdx.x - J.first[j]);  // few partials: a warp per 32 outputs
   else gram_reduce_body<false>(s_r, blockIdx.x - J.first[j]);
@@ -435,17 +450,19 @@ __global__ void __launch_bounds__(32 * kReduceWarps) gram_reduce_batched(BatchDe
 
 template <typename T>
 cudaError_t launch_batch_gram_t(const BatchDev& b, int pass, const BatchJobs* by_tpt, const size_t* smem,
-                                const BatchJobs& reduce, cudaStream_t s) {
+                                const BatchJobs& reduce, const void* gargs, const void* rargs, cudaStream_t s) {
   for (int q = 0; q < 4; ++q) {
     if (by_tpt[q].njobs == 0) continue;
     auto kern = q == 0 ? gram_batched<T, 1> : (q == 1 ? gram_batched<T, 2> : (q == 2 ? gram_batched<T, 4> : gram_batched<T, 8>));
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem[q]));
     if (err != cudaSuccess) return err;
-    pdl_launch(kern, by_tpt[q].ctas, kGramThreads, smem[q], s, b, by_tpt[q], pass);
+    pdl_launch(kern, by_tpt[q].ctas, kGramThreads, smem[q], s, b, by_tpt[q], pass,
+               static_cast<const GramArgs*>(gargs));
     count_launches(1);
   }
   if (reduce.njobs > 0) {
-    pdl_launch(gram_reduce_batched, reduce.ctas, 32 * kReduceWarps, 0, s, b, reduce, pass);
+    pdl_launch(gram_reduce_batched, reduce.ctas, 32 * kReduceWarps, 0, s, b, reduce, pass,
+               static_cast<const ReduceArgs*>(rargs));
     count_launches(1);
   }
   return cudaGetLastError();
@@ -491,9 +508,39 @@ void gram_batch_block(const Plan& p, int pass, int b, int* variant, int* ctas, s
 }
 
 cudaError_t launch_batch_gram(const BatchDev& b, int pass, const BatchJobs by_tpt[4], const size_t smem[4],
-                              const BatchJobs& reduce, int mixed, cudaStream_t s) {
-  return mixed ? launch_batch_gram_t<float>(b, pass, by_tpt, smem, reduce, s)
-               : launch_batch_gram_t<double>(b, pass, by_tpt, smem, reduce, s);
+                              const BatchJobs& reduce, int mixed, const void* gargs, const void* rargs,
+                              cudaStream_t s) {
+  return mixed ? launch_batch_gram_t<float>(b, pass, by_tpt, smem, reduce, gargs, rargs, s)
+               : launch_batch_gram_t<double>(b, pass, by_tpt, smem, reduce, gargs, rargs, s);
+}
+
+size_t batch_gram_args_bytes() { return sizeof(GramArgs); }
+size_t batch_reduce_args_bytes() { return sizeof(ReduceArgs); }
+
+namespace {
+// One thread per (instance, block) and per instance for the reduce: each
+// derives its job's arguments from the plan once, in parallel.
+__global__ void batch_args_kernel(BatchDev bd, int pass, GramArgs* ga, ReduceArgs* ra) {
+  pdl_enter();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 4 * bd.count) return;
+  const int i = e >> 2, k = e & 3;
+  if (k < 3) {
+    int64_t rows = 0;
+    int tpt = 0;
+    ga[static_cast<int64_t>(i) * 3 + k] = gram_args_of(bd.plans[i], pass, k, &rows, &tpt);
+  } else {
+    ra[i] = reduce_args_of(bd.plans[i], pass);
+  }
+}
+}  // namespace
+
+cudaError_t launch_batch_args(const BatchDev& b, int pass, void* gargs, void* rargs, cudaStream_t s) {
+  if (b.count == 0) return cudaSuccess;
+  pdl_launch(batch_args_kernel, (4 * b.count + 255) / 256, 256, 0, s, b, pass, static_cast<GramArgs*>(gargs),
+             static_cast<ReduceArgs*>(rargs));
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 bool gram_tc_supported(int k, int kout);

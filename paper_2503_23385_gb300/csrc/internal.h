@@ -251,8 +251,15 @@ cudaError_t launch_batch_ht(const BatchDev& b, const BatchJobs& plan, int plan_t
 //   Gram (CUDA cores): by_tpt[v] = (instance, block) jobs of variant v with
 //   the block's CTAs (aux = block), reduce = one job per instance
 void gram_batch_block(const Plan& p, int pass, int b, int* variant, int* ctas, size_t* smem);
+// gargs / rargs: device arrays of the jobs' Gram arguments ([instance][block])
+// and reduce arguments ([instance]) for this pass, written by
+// launch_batch_args (null: each CTA derives its own from the plan)
 cudaError_t launch_batch_gram(const BatchDev& b, int pass, const BatchJobs by_tpt[4], const size_t smem[4],
-                              const BatchJobs& reduce, int mixed, cudaStream_t s);
+                              const BatchJobs& reduce, int mixed, const void* gargs, const void* rargs,
+                              cudaStream_t s);
+size_t batch_gram_args_bytes();
+size_t batch_reduce_args_bytes();
+cudaError_t launch_batch_args(const BatchDev& b, int pass, void* gargs, void* rargs, cudaStream_t s);
 
 //   dense n x n steps (step 1, 2, 3 = first Cholesky, second Cholesky + R,
 //   Jacobi): one CTA per instance, jobs[v] the instances of variant v
