@@ -545,9 +545,12 @@ cudaError_t launch_batch_args(const BatchDev& b, int pass, void* gargs, void* ra
 
 bool gram_tc_supported(int k, int kout);
 bool gram_tc_packs(int k, int kout, bool pass2);
+// X1, k1, rows1: pass 2, a second block with the same W block and Gram
+// (its rows follow the first block's in one launch; k1 <= k)
 cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,
                                  int kout, double* part, int grid_max, int num_sms, int* grid_used, int32_t* status,
-                                 int64_t spin_limit, int withhold, cudaStream_t s);
+                                 int64_t spin_limit, int withhold, cudaStream_t s, const void* X1 = nullptr, int k1 = 0,
+                                 int64_t rows1 = 0);
 
 cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   if (p.wide) return launch_wide_gram_pass(p, pass, s);
@@ -564,7 +567,15 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
   ReduceArgs r{};
   r.n = p.n;
   r.G = pass == 1 ? p.G1 : p.G2;
+  // pass 2, n <= 32 on the packed engine: the head rows' Q = H W and the A
+  // tails' Q = T W[0:n1, :] have the same width and W block (the tails' K
+  // columns past n1 read as zeros), so both run in one launch whose partials
+  // hold their sum (the head block's fixed costs were most of its launch)
+  const bool pair01 = pass == 2 && p.mixed && p.gram_engine != 1 && !ntc[0] && !ntc[1] && p.t[0].m > 0 &&
+                      gram_tc_supported(p.n, p.n) && gram_tc_supported(p.n1, p.n) && gram_tc_packs(p.n, p.n, true) &&
+                      gram_tc_packs(p.n1, p.n, true) && p.n1 <= p.n;
   for (int b = 0; b < 3; ++b) {
+    if (pair01 && b == 1) continue;  // (launched with the head rows)
     GramArgs a{};
     int64_t rows;
     if (b == 0) {
@@ -613,8 +624,12 @@ cudaError_t launch_gram_pass(const Plan& p, int pass, cudaStream_t s) {
     cudaError_t err;
     if (tc) {
       const float* Wb = pass == 2 ? p.Wf + static_cast<int64_t>(a.w0) * p.n + a.w0 : nullptr;
-      err = launch_gram_tc_block(a.X, a.k, rows, a.rows_dev, Wb, p.n, a.kout, a.part, p.ggrid[b], p.num_sms, &grid,
-                                 &p.hdr->status, p.spin_limit, p.withhold, s);
+      if (pair01 && b == 0)
+        err = launch_gram_tc_block(a.X, a.k, rows, a.rows_dev, Wb, p.n, a.kout, a.part, p.ggrid[b], p.num_sms, &grid,
+                                   &p.hdr->status, p.spin_limit, p.withhold, s, p.t[0].tail, p.n1, p.t[0].m);
+      else
+        err = launch_gram_tc_block(a.X, a.k, rows, a.rows_dev, Wb, p.n, a.kout, a.part, p.ggrid[b], p.num_sms, &grid,
+                                   &p.hdr->status, p.spin_limit, p.withhold, s);
     } else {
       err = p.mixed ? launch_gram_block<float>(a, tpt, grid, s) : launch_gram_block<double>(a, tpt, grid, s);
     }

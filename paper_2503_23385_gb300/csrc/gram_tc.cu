@@ -1005,6 +1005,7 @@ struct PackArgs {
   int32_t* status;
   int64_t spin_limit;
   int withhold;    // test-only: the producer never loads its first tile
+  int64_t rows1;   // pass 2: rows of a second block (its own tensor map, the same W and Gram), 0: none
 };
 
 // Byte offset of column col (0..127) of packed row w in a Z panel set whose
@@ -1062,7 +1063,8 @@ __device__ __forceinline__ void split_rows_p2(float4* X4, float4* L4, int st, bo
 // P2 selects the pass at compile time (a.W != nullptr in pass 2), so that each
 // kernel holds only its own pass's loops.
 template <int KK, bool P2>
-__device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const PackArgs& a, int cta, int G) {
+__device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const CUtensorMap* tmx1, const PackArgs& a,
+                                               int cta, int G) {
   constexpr int RR = 64 / KK;  // rows per packed row
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1070,9 +1072,22 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr bool pass2 = P2;
   const int64_t rows = a.rows_dev ? *a.rows_dev : a.rows;
-  // pass 1: tiles of 128 packed rows (128 R rows); pass 2: tiles of 128 rows
+  // pass 1: tiles of 128 packed rows (128 R rows); pass 2: tiles of 128 rows,
+  // those of the first block, then (rows1 > 0) those of the second from tmx1
   const int64_t tile_rows = pass2 ? kTileRows : static_cast<int64_t>(kTileRows) * a.rr;
-  const int64_t ntiles_all = (rows + tile_rows - 1) / tile_rows;
+  const int64_t nt0 = (rows + tile_rows - 1) / tile_rows;
+  const int64_t ntiles_all = nt0 + (pass2 && a.rows1 > 0 ? (a.rows1 + tile_rows - 1) / tile_rows : 0);
+  // tile t: its tensor map, first row within its block and the block's rows
+  auto tile_src = [&](int64_t t, int64_t& r0, int64_t& lim) -> const CUtensorMap* {
+    if (t < nt0) {
+      r0 = t * tile_rows;
+      lim = rows;
+      return tmx;
+    }
+    r0 = (t - nt0) * tile_rows;
+    lim = a.rows1;
+    return tmx1;
+  };
   const int n = ntiles_all > cta ? static_cast<int>((ntiles_all - 1 - cta) / G + 1) : 0;
   auto tile_index = [&](int i) -> int64_t { return static_cast<int64_t>(cta) + static_cast<int64_t>(i) * G; };
   const int nst = pass2 ? kP2Stages : kPackStages;  // X stages in flight
@@ -1174,7 +1189,9 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
     if (lane == 0) mbar_arrive_cta(&S.d1_empty[b]);
     if (i >= 2 && !warp_wait(S, &S.q_empty[b], static_cast<uint32_t>(((i / 2) - 1) & 1), a.spin_limit, a.status))
       return false;
-    const bool live = tile_index(i) * kTileRows + qt < rows;
+    int64_t qr0 = 0, qlim = 0;
+    tile_src(tile_index(i), qr0, qlim);
+    const bool live = qr0 + qt < qlim;
     unsigned char* zq = base + kP2Zq + b * kP2ZqBytes;
 #pragma unroll
     for (int g = 0; g < QH / 4; ++g) {
@@ -1206,8 +1223,10 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         unsigned char* dst = base + s * stage_bytes;
         const int y = static_cast<int>(tile_index(i) * kTileRows);
         if (pass2) {
+          int64_t r0 = 0, lim = 0;
+          const CUtensorMap* m = tile_src(tile_index(i), r0, lim);
           expect_tx(&S.tma_full[s], kPanelBytes);
-          tma_load_2d(dst, tmx, 0, y, &S.tma_full[s]);
+          tma_load_2d(dst, m, 0, static_cast<int>(r0), &S.tma_full[s]);
         } else {  // 128 packed rows x 64 columns: two 32-column panels
           expect_tx(&S.tma_full[s], 2 * kPanelBytes);
           tma_load_2d(dst, tmx, 0, y, &S.tma_full[s]);
@@ -1216,9 +1235,15 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         // the tile that will next reuse this stage goes to L2 now, so that its
         // copy, issued when the stage frees, does not wait on HBM
         if (i + nst < n) {
-          const int yp = static_cast<int>(tile_index(i + nst) * kTileRows);
-          tma_prefetch_2d(tmx, 0, yp);
-          if (!pass2) tma_prefetch_2d(tmx, 32, yp);
+          if (pass2) {
+            int64_t r0 = 0, lim = 0;
+            const CUtensorMap* m = tile_src(tile_index(i + nst), r0, lim);
+            tma_prefetch_2d(m, 0, static_cast<int>(r0));
+          } else {
+            const int yp = static_cast<int>(tile_index(i + nst) * kTileRows);
+            tma_prefetch_2d(tmx, 0, yp);
+            tma_prefetch_2d(tmx, 32, yp);
+          }
         }
         issued = i + 1;
       }
@@ -1346,7 +1371,9 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
       float4* X4 = reinterpret_cast<float4*>(base + s * stage_bytes);
       float4* L4 = reinterpret_cast<float4*>(base + s * stage_bytes + raw_bytes);
       const int64_t t0 = tile_index(i);
-      const bool full = (t0 + 1) * tile_rows <= rows;  // no row of the tile lies past the end
+      int64_t r0 = 0, lim = 0;
+      tile_src(t0, r0, lim);
+      const bool full = r0 + tile_rows <= lim;  // no row of the tile lies past the end of its block
       if (!pass2) {
         // 2 panels of 128 packed rows (2,048 float4), loads before stores in batches of 4
         constexpr int kVec = kP1Stage / 2 / 16;
@@ -1377,12 +1404,11 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
         // formation reads (chunk c sits at c ^ (r mod 8) of the 128-byte
         // swizzle; columns past k are zero-filled by the copy)
         // (the chunk count is a compile-time constant of each case: straight-line code)
-        const int64_t row0 = t0 * kTileRows;
         switch (a.ksteps_f) {
-          case 1: split_rows_p2<2>(X4, L4, st, full, row0, rows); break;
-          case 2: split_rows_p2<4>(X4, L4, st, full, row0, rows); break;
-          case 3: split_rows_p2<6>(X4, L4, st, full, row0, rows); break;
-          default: split_rows_p2<8>(X4, L4, st, full, row0, rows); break;
+          case 1: split_rows_p2<2>(X4, L4, st, full, r0, lim); break;
+          case 2: split_rows_p2<4>(X4, L4, st, full, r0, lim); break;
+          case 3: split_rows_p2<6>(X4, L4, st, full, r0, lim); break;
+          default: split_rows_p2<8>(X4, L4, st, full, r0, lim); break;
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1505,9 +1531,9 @@ __device__ __forceinline__ void gram_pack_body(const CUtensorMap* tmx, const Pac
 
 template <int KK, bool P2>
 __global__ void __launch_bounds__(kPackThreads, 1)
-    gram_pack_kernel(const __grid_constant__ CUtensorMap tmx, PackArgs a) {
+    gram_pack_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmx1, PackArgs a) {
   pdl_enter();
-  gram_pack_body<KK, P2>(&tmx, a, blockIdx.x, gridDim.x);
+  gram_pack_body<KK, P2>(&tmx, &tmx1, a, blockIdx.x, gridDim.x);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() { return tensor_map_encoder(); }
@@ -1656,7 +1682,7 @@ __global__ void __launch_bounds__(kPackThreads, 1) gram_pack_batched(const __gri
   pdl_enter();
   const int j = tc_batch_job(B, blockIdx.x);
   const PackArgs a = pack_args_of(B.plans[B.inst[j]], B.pass, B.blk[j]);
-  gram_pack_body<KK, P2>(&B.maps[j], a, blockIdx.x - B.first[j], B.first[j + 1] - B.first[j]);
+  gram_pack_body<KK, P2>(&B.maps[j], &B.maps[j], a, blockIdx.x - B.first[j], B.first[j + 1] - B.first[j]);
 }
 
 template <int NP>
@@ -2375,12 +2401,14 @@ bool gram_tc_supported(int k, int kout) { return k % 4 == 0 && k <= 64 && kout <
 
 cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64_t* rows_dev, const float* W, int wld,
                                  int kout, double* part, int grid_max, int num_sms, int* grid_used, int32_t* status,
-                                 int64_t spin_limit, int withhold, cudaStream_t s) {
+                                 int64_t spin_limit, int withhold, cudaStream_t s, const void* X1, int k1,
+                                 int64_t rows1) {
   const int kk = W ? kout : k;
+  if (X1 && !(W && k1 >= 1 && k1 <= k && gram_tc_packs(k, kout, true))) return cudaErrorInvalidValue;
   if (gram_tc_packs(k, kout, W != nullptr)) {  // packed-operand engine: persistent CTAs, one per SM
     const int rr = 64 / kk;
     const int64_t tile_rows = W ? kTileRows : static_cast<int64_t>(kTileRows) * rr;
-    int grid = static_cast<int>((rows + tile_rows - 1) / tile_rows);
+    int grid = static_cast<int>((rows + tile_rows - 1) / tile_rows + (X1 ? (rows1 + tile_rows - 1) / tile_rows : 0));
     if (grid > num_sms) grid = num_sms;
     if (grid > grid_max) grid = grid_max;
     if (grid < 1) grid = 1;
@@ -2400,16 +2428,23 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
     a.status = status;
     a.spin_limit = spin_limit;
     a.withhold = withhold;
-    CUtensorMap map;
+    a.rows1 = X1 ? rows1 : 0;
+    CUtensorMap map, map1;
     cuuint32_t box[2] = {32, static_cast<cuuint32_t>(kTileRows)};
     cuuint32_t es[2] = {1, 1};
     CUresult cr;
-    if (W) {  // rows of X, K-major operand of the formation product
-      cuuint64_t dims[2] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows > 0 ? rows : 1)};
-      cuuint64_t strides[1] = {static_cast<cuuint64_t>(k) * 4};
-      cr = encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // rows of X (k columns; the 32-column box reads zeros past them), K-major operand of the formation product
+    auto x_map = [&](CUtensorMap* m, const void* Xp, int kc, int64_t nr) {
+      cuuint64_t dims[2] = {static_cast<cuuint64_t>(kc), static_cast<cuuint64_t>(nr > 0 ? nr : 1)};
+      cuuint64_t strides[1] = {static_cast<cuuint64_t>(kc) * 4};
+      return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(Xp), dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    };
+    if (W) {
+      cr = x_map(&map, X, k, rows);
+      if (cr == CUDA_SUCCESS) cr = X1 ? x_map(&map1, X1, k1, rows1) : CUDA_SUCCESS;
+      if (!X1) map1 = map;
     } else {  // packed rows: rr consecutive rows = one 64-column row (the last one may run into the next array)
       const int64_t wrows = (rows + rr - 1) / rr;
       cuuint64_t dims[2] = {64, static_cast<cuuint64_t>(wrows > 0 ? wrows : 1)};
@@ -2417,6 +2452,7 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
       cr = encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      map1 = map;
     }
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
     static int granted[64][8] = {};
@@ -2424,16 +2460,16 @@ cudaError_t launch_gram_tc_block(const void* X, int k, int64_t rows, const int64
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     const int which = (kk == 4 ? 0 : (kk == 8 ? 1 : (kk == 16 ? 2 : 3))) + (W ? 4 : 0);
-    void (*const kerns[8])(const CUtensorMap, PackArgs) = {
+    void (*const kerns[8])(const CUtensorMap, const CUtensorMap, PackArgs) = {
         gram_pack_kernel<4, false>, gram_pack_kernel<8, false>, gram_pack_kernel<16, false>, gram_pack_kernel<32, false>,
         gram_pack_kernel<4, true>,  gram_pack_kernel<8, true>,  gram_pack_kernel<16, true>,  gram_pack_kernel<32, true>};
-    void (*kern)(const CUtensorMap, PackArgs) = kerns[which];
+    void (*kern)(const CUtensorMap, const CUtensorMap, PackArgs) = kerns[which];
     if (dev < 0 || dev >= 64 || !granted[dev][which]) {
       err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPackSmemBytes);
       if (err != cudaSuccess) return err;
       if (dev >= 0 && dev < 64) granted[dev][which] = 1;
     }
-    pdl_launch(kern, grid, kPackThreads, kPackSmemBytes, s, map, a);
+    pdl_launch(kern, grid, kPackThreads, kPackSmemBytes, s, map, map1, a);
     count_launches(1);
     return cudaGetLastError();
   }
