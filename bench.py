@@ -488,7 +488,7 @@ def main():
         # the dominant launch group is the second pass (formation Q = X W and the Gram of Q); the
         # average of the two passes is reported beside it
         g2 = gram_bytes / (phases["gram2"] / 1e3) / 1e9
-        roofline = {"kernel": "gram_pack_kernel: CholeskyQR pass 2 (head, A-tail and B-tail launches + reduce)",
+        roofline = {"kernel": "gram_pack_kernel: CholeskyQR pass 2 (head rows with the A tails in one launch, B tails, reduce)",
                     "bound": "hbm", "achieved": g2, "peak": hbm, "unit": "GB/s", "frac": g2 / hbm,
                     "traffic": measured_traffic("gram_pass", args.config), "bytes_per_launch": gram_bytes,
                     "peak_source": peak_kind}
