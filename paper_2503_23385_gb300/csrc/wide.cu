@@ -879,36 +879,56 @@ __global__ void __launch_bounds__(32 * JW) wide_jacobi_kernel(JacArgs a) {
         T* Gc = G;
         T* Gn = G + W2 * LG;
         constexpr int M1 = W2 - 1;
-        for (int ir = 0; need && ir < M1; ++ir) {
-          int p, q;
-          rr_pair(ir, warp, W2, p, q);
-          const int j = lane < W2 ? lane : 0;  // lanes beyond W2 mirror lane 0 and store nothing
-          int jp = (2 * ir - j) % M1;
-          jp += jp < 0 ? M1 : 0;
-          jp = j == ir ? M1 : jp;
-          jp = j == M1 ? ir : jp;
-          const int lo = j < jp ? j : jp, hi = j < jp ? jp : j;
-          const T al = Gc[lo * LG + lo], be = Gc[hi * LG + hi], ga = Gc[lo * LG + hi];
-          const T gpj = Gc[p * LG + j], gpjp = Gc[p * LG + jp], gqj = Gc[q * LG + j], gqjp = Gc[q * LG + jp];
-          const T qpj = Qm[p * W2 + j], qpjp = Qm[p * W2 + jp], qqj = Qm[q * W2 + j], qqjp = Qm[q * W2 + jp];
-          const bool rot = al > negligible && be > negligible && ga * ga > tol2 * al * be;
-          T c = T(1), s = T(0);
-          if (rot) jac_rotation(al, be, ga, c, s);
-          const T sg = j < jp ? -s : s;
-          const T cw = __shfl_sync(0xffffffffu, c, p), sw = __shfl_sync(0xffffffffu, s, p);  // the pair (p, q)
-          const T hp = c * gpj + sg * gpjp, hq = c * gqj + sg * gqjp;
-          __syncwarp();  // rows p, q of Q are read above by the lanes that own their partners
-          if (lane < W2) {
-            Gn[p * LG + j] = cw * hp - sw * hq;
-            Gn[q * LG + j] = sw * hp + cw * hq;
-            Qm[p * W2 + j] = c * qpj + sg * qpjp;
-            Qm[q * W2 + j] = c * qqj + sg * qqjp;
+        // the first IW warps run the inner sweep, PPW pairs each per inner
+        // round, and meet at a barrier of their own (a barrier of all the
+        // CTA's warps per inner round cost more than the round's work)
+        constexpr int IW = JW < 4 ? JW : 4;
+        constexpr int PPW = (W2 / 2) / IW;
+        static_assert(IW * PPW == W2 / 2, "inner sweep split");
+        if (warp < IW) {
+          for (int ir = 0; need && ir < M1; ++ir) {
+            const int j = lane < W2 ? lane : 0;  // lanes beyond W2 mirror lane 0 and store nothing
+            int jp = (2 * ir - j) % M1;
+            jp += jp < 0 ? M1 : 0;
+            jp = j == ir ? M1 : jp;
+            jp = j == M1 ? ir : jp;
+            const int lo = j < jp ? j : jp, hi = j < jp ? jp : j;
+            const T al = Gc[lo * LG + lo], be = Gc[hi * LG + hi], ga = Gc[lo * LG + hi];
+            const bool rot = al > negligible && be > negligible && ga * ga > tol2 * al * be;
+            T c = T(1), s = T(0);
+            if (rot) jac_rotation(al, be, ga, c, s);
+            const T sg = j < jp ? -s : s;
+            int pp[PPW], qq[PPW];
+            T gp[PPW], gq[PPW], qp[PPW], qqv[PPW];
+#pragma unroll
+            for (int t = 0; t < PPW; ++t) {
+              rr_pair(ir, warp + t * IW, W2, pp[t], qq[t]);
+              const int p = pp[t], q = qq[t];
+              const T gpj = Gc[p * LG + j], gpjp = Gc[p * LG + jp], gqj = Gc[q * LG + j], gqjp = Gc[q * LG + jp];
+              const T qpj = Qm[p * W2 + j], qpjp = Qm[p * W2 + jp], qqj = Qm[q * W2 + j], qqjp = Qm[q * W2 + jp];
+              const T cw = __shfl_sync(0xffffffffu, c, p), sw = __shfl_sync(0xffffffffu, s, p);  // the pair (p, q)
+              const T hp = c * gpj + sg * gpjp, hq = c * gqj + sg * gqjp;
+              gp[t] = cw * hp - sw * hq;
+              gq[t] = sw * hp + cw * hq;
+              qp[t] = c * qpj + sg * qpjp;
+              qqv[t] = c * qqj + sg * qqjp;
+            }
+            __syncwarp();  // rows p, q of Q are read above by the lanes that own their partners
+            if (lane < W2) {
+#pragma unroll
+              for (int t = 0; t < PPW; ++t) {
+                Gn[pp[t] * LG + j] = gp[t];
+                Gn[qq[t] * LG + j] = gq[t];
+                Qm[pp[t] * W2 + j] = qp[t];
+                Qm[qq[t] * W2 + j] = qqv[t];
+              }
+            }
+            any |= rot ? 1 : 0;
+            asm volatile("bar.sync 2, %0;" ::"n"(32 * IW) : "memory");
+            T* t_ = Gc;
+            Gc = Gn;
+            Gn = t_;
           }
-          any |= rot ? 1 : 0;
-          __syncthreads();
-          T* t_ = Gc;
-          Gc = Gn;
-          Gn = t_;
         }
         any = __syncthreads_or(any);
         if (any) {
