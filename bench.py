@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-materialized", action="store_true")
+    ap.add_argument("--sigma", default="jacobi", choices=["jacobi", "dqds"],
+                    help="singular values of R by one-sided Jacobi or by bidiagonalisation and dqds (n <= 128)")
     ap.add_argument("--cpu-sample-keys", type=int, default=0)
     return ap.parse_args()
 
@@ -393,7 +395,8 @@ def main():
     ev_arr = fg.event_array(evs)
     engine = {"auto": fg.GRAM_AUTO, "simt": fg.GRAM_SIMT, "tcgen05": fg.GRAM_TCGEN05}[args.gram_engine]
     solver_cls = fg.LsqSolver if args.task == "lstsq" else fg.Solver
-    solver = solver_cls(tA, tB, path=args.path, phase_events=ev_arr, gram_engine=engine)
+    sig_flags = fg.FLAG_SIGMA_DQDS if (args.sigma == "dqds" and args.task == "qr_svd") else 0
+    solver = solver_cls(tA, tB, path=args.path, phase_events=ev_arr, gram_engine=engine, flags=sig_flags)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -670,6 +673,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32" if args.path == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.config], "path": args.path, "rows_per_gpu": rows,
                            "graph": graph is not None, "gram_engine": args.gram_engine, "task": args.task,
+                           "sigma": args.sigma,
                            "l2": "inputs 136 MB + ~300 MB workspace exceed L2; 256 MB flush between steps"},
                 "roofline": roofline, roofline_avg_key: roofline_avg, "roofline_head_tail": roofline_ht,
                 "cpu_baseline": cpu, "e2e": e2e,
@@ -705,7 +709,8 @@ def run_batch(args, rank, world, torch, dist, fg, dev, local):
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(fg.NUM_PHASE_EVENTS)]
     ev_arr = fg.event_array(evs)
     # the first call tunes the schedule on this batch (outside the capture)
-    solver = fg.BatchSolver(pairs, path=args.path, flags=fg.FLAG_AUTOTUNE)
+    sig_flags = fg.FLAG_SIGMA_DQDS if args.sigma == "dqds" else 0
+    solver = fg.BatchSolver(pairs, path=args.path, flags=fg.FLAG_AUTOTUNE | sig_flags)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
@@ -831,6 +836,7 @@ def run_batch(args, rank, world, torch, dist, fg, dev, local):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.path == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOADS["c3"], "path": args.path, "rows_per_gpu": rows, "graph": True,
+                           "sigma": args.sigma,
                            "instances": len(inst), "schedule (autotuned)": solver.schedule(),
                            "l2": f"inputs {(xs.nbytes + ks.nbytes) / 1e9:.1f} GB exceed L2; 256 MB flush between steps"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,

@@ -10,7 +10,8 @@
  * J is never formed.  The path is: stable radix sort of each table by key,
  * runs and matched keys, the per-key-group QR head and QR tail rows of
  * Claim 1 (weighted by sqrt(m2g) on A's side and sqrt(m1g) on B's side), a
- * CholeskyQR2 of that reduced matrix, and a one-sided Jacobi SVD of R.
+ * CholeskyQR2 of that reduced matrix, and a one-sided Jacobi SVD of R (or,
+ * with FIGARO_FLAG_SIGMA_DQDS, bidiagonalisation of R and dqds).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -137,7 +138,17 @@ enum {
    * A table that is not in order makes the call's device status
    * FIGARO_ERR_INVALID_ARG (results invalid).  Single calls only:
    * figaro_batch_join runs such instances one after another.              */
-  FIGARO_FLAG_PRESORTED = 1 << 5
+  FIGARO_FLAG_PRESORTED = 1 << 5,
+  /* figaro_join_singular_values and figaro_batch_join: sigma from R by
+   * Householder bidiagonalisation and dqds (Section 3 names this
+   * square-root-free method for the case where only the singular values are
+   * wanted; see figaro_triangular_singular_values) instead of one-sided
+   * Jacobi.  FP64 on both paths.  Widths n1 + n2 <= 128 (wider joins return
+   * FIGARO_ERR_UNSUPPORTED); figaro_join_svd, which needs the rotations,
+   * returns FIGARO_ERR_UNSUPPORTED with it.  figaro_info.jacobi_sweeps then
+   * counts dqds transforms; FIGARO_ERR_NO_CONVERGENCE means dqds ran out of
+   * transforms (30 n + 64) and sigma holds its current estimates.           */
+  FIGARO_FLAG_SIGMA_DQDS = 1 << 6
 };
 
 typedef struct figaro_table {
@@ -241,6 +252,28 @@ FIGARO_API figaro_status figaro_join_qr_r(const figaro_table* A, const figaro_ta
 FIGARO_API figaro_status figaro_join_singular_values(const figaro_table* A, const figaro_table* B, const figaro_options* opt,
                                           double* sigma, double* R_out, int64_t ldr, void* ws, size_t ws_bytes,
                                           void* stream);
+
+/*
+ * figaro_triangular_singular_values -- singular values of `count` upper
+ * triangular n x n matrices (Section 3: sigma(J) = sigma(R); the method is
+ * the one the section names for singular values alone, the square-root-free
+ * dqds of Rutishauser in the differential form of Fernando and Parlett).
+ * Matrix b is R + b * stride (device, FP64, row-major with leading dimension
+ * ldr >= n; only the upper triangle is read, so the lower one may hold
+ * anything).  Each is reduced to upper bidiagonal form by Householder
+ * reflections from both sides in FP64 (backward error of order eps ||R||),
+ * then dqds with shifts finds the squares of the bidiagonal's singular
+ * values to high relative accuracy.  sigma + b * n (device) receives the
+ * n values, descending; info (device, may be NULL) receives per matrix the
+ * number of dqds transforms, or -1 when dqds stopped after 30 n + 64
+ * transforms (sigma then holds its current estimates; NaN when the matrix
+ * holds NaN or Inf).  1 <= n <= 128 (else FIGARO_ERR_UNSUPPORTED for
+ * n > 128, FIGARO_ERR_INVALID_ARG for n < 1); stride >= 0; count >= 0
+ * (0 enqueues nothing).  One CTA per matrix, enqueued on `stream`; needs
+ * no workspace.  The device is the one that holds R.
+ */
+FIGARO_API figaro_status figaro_triangular_singular_values(const double* R, int64_t ldr, int64_t stride, int32_t n,
+                                                int32_t count, double* sigma, int32_t* info, void* stream);
 
 /*
  * figaro_join_svd -- singular values and right singular vectors of J

@@ -22,7 +22,8 @@ __all__ = [
     "join_qr_svd_host", "batch_join", "get_status", "Solver", "STATUS_NAMES", "event_array", "kernel_launches",
     "host_workspace_size", "PHASES", "NUM_PHASE_EVENTS", "join_singular_values_fixed", "FIXED_SCRATCH_BYTES",
     "BatchSolver", "FLAG_AUTOTUNE", "join_least_squares", "LsqSolver", "join_svd", "get_info",
-    "FLAG_ALLOW_RANK_DEFICIENT", "FLAG_SHIFTED_CHOLQR3", "FLAG_PRESORTED",
+    "FLAG_ALLOW_RANK_DEFICIENT", "FLAG_SHIFTED_CHOLQR3", "FLAG_PRESORTED", "FLAG_SIGMA_DQDS",
+    "triangular_singular_values",
 ]
 
 PATH_FP64, PATH_MIXED = 0, 1
@@ -34,6 +35,7 @@ FLAG_AUTOTUNE = 1 << 2
 FLAG_ALLOW_RANK_DEFICIENT = 1 << 3
 FLAG_SHIFTED_CHOLQR3 = 1 << 4
 FLAG_PRESORTED = 1 << 5
+FLAG_SIGMA_DQDS = 1 << 6
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "WORKSPACE_TOO_SMALL", 3: "CUDA", 4: "NOT_SPD",
                 5: "NO_CONVERGENCE", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED", 8: "RANK_DEFICIENT"}
 
@@ -77,7 +79,7 @@ class Grouping(ctypes.Structure):
 EXPORTS = ["figaro_default_options", "figaro_workspace_size", "figaro_join_group", "figaro_join_head_tail",
            "figaro_join_qr_r", "figaro_join_singular_values", "figaro_batch_workspace_size", "figaro_batch_join",
            "figaro_get_status", "figaro_get_info", "figaro_status_string", "figaro_version",
-           "figaro_kernel_launches", "figaro_join_singular_values_fixed"]
+           "figaro_kernel_launches", "figaro_join_singular_values_fixed", "figaro_triangular_singular_values"]
 FIXED_SCRATCH_BYTES = 32 << 20
 NUM_PHASE_EVENTS = 9
 PHASES = ["grouping", "ht_carry", "head_tail", "gram1", "chol1", "gram2", "chol2", "jacobi"]
@@ -106,6 +108,7 @@ def library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.figaro_join_singular_values.argtypes = [P(Table), P(Table), P(Options), vp, vp, I64, vp, sz, vp]
         lib.figaro_join_singular_values_fixed.argtypes = [P(Table), P(Table), P(Options), vp, vp, I64, P(vp), vp]
         lib.figaro_batch_workspace_size.argtypes = [I32, P(Table), P(Table), P(Options), P(sz)]
+        lib.figaro_triangular_singular_values.argtypes = [vp, I64, I64, I32, I32, vp, vp, vp]
         lib.figaro_batch_join.argtypes = [I32, P(Table), P(Table), P(Options), P(vp), P(vp), vp, sz, vp]
         lib.figaro_get_status.argtypes = [vp, vp]
         lib.figaro_get_info.argtypes = [vp, vp, P(Info)]
@@ -375,6 +378,28 @@ def join_qr_svd_host(A, B, R_out, sigma_out, workspace, stream=None, **opts):
     _check(lib.figaro_join_singular_values(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(o), ctypes.c_void_p(sptr),
                                            ctypes.c_void_p(rptr), n, ctypes.c_void_p(workspace.data_ptr()),
                                            workspace.numel(), _stream_handle(stream)), "figaro_join_singular_values")
+
+
+def triangular_singular_values(R, stream=None):
+    """Singular values of upper-triangular FP64 device matrices by
+    bidiagonalisation and dqds (figaro_triangular_singular_values).  R is
+    (n, n) or (count, n, n), rows contiguous; only the upper triangle is read.
+    Returns (sigma, info): sigma (count, n) descending (or (n,)), info the
+    dqds transforms per matrix as an int32 device tensor (-1: stopped early)."""
+    torch = _torch()
+    lib = library()
+    single = R.dim() == 2
+    Rb = R.unsqueeze(0) if single else R
+    if Rb.dtype != torch.float64 or not Rb.is_cuda or Rb.stride(-1) != 1 or Rb.shape[-2] != Rb.shape[-1]:
+        raise FigaroError(1, "R must be a float64 CUDA tensor with contiguous rows")
+    count, n = Rb.shape[0], Rb.shape[-1]
+    sigma = torch.empty((count, n), dtype=torch.float64, device=Rb.device)
+    info = torch.empty(count, dtype=torch.int32, device=Rb.device)
+    _check(lib.figaro_triangular_singular_values(ctypes.c_void_p(Rb.data_ptr()), Rb.stride(1),
+                                                 Rb.stride(0) if count > 1 else 0, n, count,
+                                                 ctypes.c_void_p(sigma.data_ptr()), ctypes.c_void_p(info.data_ptr()),
+                                                 _stream_handle(stream)), "figaro_triangular_singular_values")
+    return (sigma[0], info) if single else (sigma, info)
 
 
 def join_svd(A, B, stream=None, workspace=None, **opts):

@@ -270,6 +270,7 @@ figaro_status check_pair(const figaro_table* A, const figaro_table* B, const fig
   const int64_t n = static_cast<int64_t>(A->n) + B->n;
   if (n > kMaxWideWidth || (n > kMaxWidth && (A->n > kMaxTableWidth || B->n > kMaxTableWidth)))
     return FIGARO_ERR_UNSUPPORTED;
+  if (o && (o->flags & FIGARO_FLAG_SIGMA_DQDS) && n > kMaxWidth) return FIGARO_ERR_UNSUPPORTED;
   return FIGARO_OK;
 }
 
@@ -315,6 +316,7 @@ figaro_status prepare(Call& c, const figaro_table* A, const figaro_table* B, con
   c.p.report_rank = (o.flags & FIGARO_FLAG_ALLOW_RANK_DEFICIENT) ? 0 : c.p.n;
   c.p.shifted = (o.flags & FIGARO_FLAG_SHIFTED_CHOLQR3) ? 1 : 0;
   c.p.presorted = (o.flags & FIGARO_FLAG_PRESORTED) ? 1 : 0;
+  c.p.sigma_dqds = (o.flags & FIGARO_FLAG_SIGMA_DQDS) ? 1 : 0;
   c.s = static_cast<cudaStream_t>(stream);
   if (o.phase_events) {
     c.events = true;
@@ -460,7 +462,10 @@ figaro_status run_qr_svd(Call& c, double* R_out, int64_t ldr, double* sigma, int
   const int n = c.p.n;
   st = run_factor(c, host_out ? nullptr : R_out, ldr);
   if (st != FIGARO_OK) return st;
-  if (sigma) FIGARO_TRY(launch_jacobi(c.p, c.p.R, n, host_out ? c.p.sigma : sigma, c.s));
+  if (sigma) {
+    double* sg = host_out ? c.p.sigma : sigma;
+    FIGARO_TRY(c.p.sigma_dqds ? launch_sigma_dqds(c.p, c.p.R, n, sg, c.s) : launch_jacobi(c.p, c.p.R, n, sg, c.s));
+  }
   FIGARO_TRY(c.mark(8));
   if (host_out) {
     if (R_out)
@@ -707,7 +712,12 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
       if (step == 3 && !outs[i].sigma) continue;
       int v = 0, thr = 0;
       size_t sm = 0;
-      dense_batch_info(p, step, &v, &sm, &thr);
+      if (step == 3 && p.sigma_dqds) {
+        sm = sigma_dqds_smem(p.n, p.mixed);
+        thr = sigma_dqds_threads();
+      } else {
+        dense_batch_info(p, step, &v, &sm, &thr);
+      }
       dl[step - 1][v].add(i, 0, 1);
       dsm[step - 1][v] = std::max(dsm[step - 1][v], sm);
       dthr[step - 1][v] = std::max(dthr[step - 1][v], thr);
@@ -830,7 +840,10 @@ figaro_status run_batched(std::vector<Call>& calls, const std::vector<BatchOut>&
   FIGARO_TRY(ev.mark(6));
   FIGARO_TRY(launch_batch_dense(b, 2, Jd[1], dsm[1], dthr[1], mixed, s));
   FIGARO_TRY(ev.mark(7));
-  FIGARO_TRY(launch_batch_dense(b, 3, Jd[2], dsm[2], dthr[2], mixed, s));
+  if (calls[0].p.sigma_dqds)
+    FIGARO_TRY(launch_batch_sigma_dqds(b, Jd[2][0], dsm[2][0], mixed, s));
+  else
+    FIGARO_TRY(launch_batch_dense(b, 3, Jd[2], dsm[2], dthr[2], mixed, s));
   FIGARO_TRY(ev.mark(8));
   return FIGARO_OK;
 }
@@ -1056,7 +1069,7 @@ figaro_status figaro_join_svd(const figaro_table* A, const figaro_table* B, cons
                               double* V, int64_t ldv, double* R_out, int64_t ldr, void* ws, size_t ws_bytes,
                               void* stream) {
   if (!sigma || !V) return FIGARO_ERR_INVALID_ARG;
-  if (opt && (opt->flags & FIGARO_FLAG_HOST_OUTPUT)) return FIGARO_ERR_UNSUPPORTED;
+  if (opt && (opt->flags & (FIGARO_FLAG_HOST_OUTPUT | FIGARO_FLAG_SIGMA_DQDS))) return FIGARO_ERR_UNSUPPORTED;
   Call c;
   StageJoin join_at_exit{c};
   figaro_status st = prepare(c, A, B, opt, ws, ws_bytes, stream);
@@ -1095,6 +1108,17 @@ figaro_status figaro_join_least_squares(const figaro_table* A, const figaro_tabl
     FIGARO_TRY(cudaMemcpyAsync(beta, b_dev, sizeof(double) * (c.p.n - 1), cudaMemcpyDeviceToHost, c.s));
     FIGARO_TRY(cudaMemcpyAsync(residual, r_dev, sizeof(double), cudaMemcpyDeviceToHost, c.s));
   }
+  return FIGARO_OK;
+}
+
+figaro_status figaro_triangular_singular_values(const double* R, int64_t ldr, int64_t stride, int32_t n,
+                                                int32_t count, double* sigma, int32_t* info, void* stream) {
+  if (!R || !sigma || n < 1 || count < 0 || ldr < n || stride < 0) return FIGARO_ERR_INVALID_ARG;
+  if (n > kMaxWidth) return FIGARO_ERR_UNSUPPORTED;
+  if (count == 0) return FIGARO_OK;
+  figaro_status st = bind_device(R);
+  if (st != FIGARO_OK) return st;
+  FIGARO_TRY(launch_sigma_dqds_many(R, ldr, stride, n, count, sigma, info, static_cast<cudaStream_t>(stream)));
   return FIGARO_OK;
 }
 

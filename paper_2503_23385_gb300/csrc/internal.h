@@ -94,6 +94,7 @@ struct Plan {
   int report_rank = 0;          // leading columns whose drop raises FIGARO_ERR_RANK_DEFICIENT (0: none)
   int shifted = 0;              // shifted CholeskyQR3: shift G1, then a third Gram pass
   int presorted = 0;            // the tables are in key order: no radix sort (identity permutation)
+  int sigma_dqds = 0;           // singular values by bidiagonalisation and dqds instead of Jacobi
   // pass 1 of the tail blocks inside the head/tail stream (ht_plan_gram1):
   // the stream's CTAs per table, and per table the number of float-float
   // Gram partials of its tails those CTAs write (0: the Gram pass reads the tails)
@@ -235,6 +236,15 @@ cudaError_t launch_chol_first(const Plan& p, cudaStream_t s);
 cudaError_t launch_refactor(const Plan& p, cudaStream_t s);
 cudaError_t launch_chol_second(const Plan& p, double* R_out, int64_t ldr, cudaStream_t s);
 cudaError_t launch_jacobi(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
+// Singular values by bidiagonalisation and dqds (sigma.cu; n <= kMaxWidth):
+// one CTA per matrix; the header's sweep counter receives the number of dqds
+// transforms, or -1 when dqds stopped early.  mixed = 1: FP32 stages; 0:
+// FP64 bidiagonalisation and float-float dqds (also the direct entry point).
+size_t sigma_dqds_smem(int n, int mixed);
+int sigma_dqds_threads();
+cudaError_t launch_sigma_dqds(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s);
+cudaError_t launch_sigma_dqds_many(const double* R, int64_t ldr, int64_t stride, int n, int count, double* sigma,
+                                   int32_t* info, cudaStream_t s);
 cudaError_t launch_lsq(const Plan& p, double* beta, double* residual, cudaStream_t s);
 
 // Batched launchers: every instance of a batch in one launch per phase.
@@ -266,6 +276,8 @@ cudaError_t launch_batch_args(const BatchDev& b, int pass, void* gargs, void* ra
 void dense_batch_info(const Plan& p, int step, int* variant, size_t* smem, int* threads);
 cudaError_t launch_batch_dense(const BatchDev& b, int step, const BatchJobs jobs[3], const size_t smem[3],
                                const int threads[3], int mixed, cudaStream_t s);
+//   the sigma step by dqds instead of Jacobi: one CTA per instance
+cudaError_t launch_batch_sigma_dqds(const BatchDev& b, const BatchJobs& J, size_t smem, int mixed, cudaStream_t s);
 
 //   Gram (tensor cores): jobs of one engine variant, in launches of up to
 //   192 jobs whose tensor maps travel as kernel arguments
