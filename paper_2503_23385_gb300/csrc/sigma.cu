@@ -44,9 +44,13 @@ constexpr int kSigWarps = kSigThreads / 32;
 constexpr int kCand = 33;  // entries between i and i + 1 of a lane's candidate arrays (bank spread)
 
 __host__ __device__ constexpr int sig_lda(int n) { return n | 1; }  // odd stride: column walks are conflict-free
-// doubles of the first region: the matrix, later the lanes' candidate arrays (2 x kCand x n values of <= 8 bytes)
-__host__ __device__ constexpr int sig_region(int n) {
-  return n * sig_lda(n) > 2 * kCand * n ? n * sig_lda(n) : 2 * kCand * n;
+__host__ __device__ constexpr size_t sig_al8(size_t b) { return (b + 7) & ~size_t(7); }
+// Bytes of the first region: the matrix in T, later the lanes' candidate
+// arrays (2 x kCand x n values of NT), and at least 8 doubles (a reduction).
+template <typename T, typename NT>
+__host__ __device__ constexpr size_t sig_region_bytes(int n) {
+  return sig_al8(sizeof(T) * n * sig_lda(n) > sizeof(NT) * 2 * kCand * n ? sizeof(T) * n * sig_lda(n)
+                                                                          : sizeof(NT) * 2 * kCand * n);
 }
 
 // ---------------------------------------------------------------- numbers --
@@ -365,14 +369,14 @@ __device__ int sig_dqds(typename Num::T* q, typename Num::T* e, int n, double* l
   return failed ? -1 : transforms;
 }
 
-// Shared-memory layout (bytes, 8-byte aligned pieces): region (sig_region
-// doubles: the matrix in T, later the candidates in Num::T), q / e / w (n T
-// each), part (kSigThreads T), red (2 kSigWarps T), qq / ee (n Num::T each),
-// lam (n doubles), stk (3 n doubles).
-__host__ __device__ constexpr size_t sig_al8(size_t b) { return (b + 7) & ~size_t(7); }
+// Shared-memory layout (bytes, 8-byte aligned pieces): region (the matrix
+// in T, later the candidates in Num::T), q / e / w (n T each), part
+// (kSigThreads T), red (2 kSigWarps T), qq / ee (n Num::T each), lam (n
+// doubles), stk (3 n doubles).  The FP32 form needs half the bytes of the
+// accurate one, so more CTAs share an SM in a batch.
 template <typename T, typename NT>
 __host__ __device__ constexpr size_t sig_smem_bytes(int n) {
-  return sizeof(double) * sig_region(n) + sig_al8(sizeof(T) * (3 * n + kSigThreads + 2 * kSigWarps)) +
+  return sig_region_bytes<T, NT>(n) + sig_al8(sizeof(T) * (3 * n + kSigThreads + 2 * kSigWarps)) +
          sig_al8(sizeof(NT) * 2 * n) + sizeof(double) * 4 * n;
 }
 
@@ -390,7 +394,7 @@ __device__ void sigma_dqds_body(const double* R, int64_t ldr, int n, double* sig
   const int lda = sig_lda(n);
   char* base = reinterpret_cast<char*>(sig_sm);
   T* A = reinterpret_cast<T*>(base);
-  char* p1 = base + sizeof(double) * sig_region(n);
+  char* p1 = base + sig_region_bytes<T, NT>(n);
   T* q = reinterpret_cast<T*>(p1);
   T* e = q + n;
   T* w = e + n;
@@ -421,7 +425,7 @@ __device__ void sigma_dqds_body(const double* R, int64_t ldr, int n, double* sig
     return;
   }
   for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  double* wmax = sig_sm;  // kSigWarps doubles at the start of the matrix region (>= 66 doubles)
+  double* wmax = sig_sm;  // kSigWarps doubles at the start of the matrix region (>= 264 bytes)
   if ((tid & 31) == 0) wmax[tid >> 5] = amax;
   __syncthreads();
   amax = 0.0;
