@@ -553,12 +553,12 @@ def main():
         sh = torch.zeros(n, dtype=torch.float64).pin_memory()
         wsh = torch.empty(fg.host_workspace_size(hA, hB, path=args.path), dtype=torch.uint8, device=dev)
         for _ in range(2):
-            fg.join_qr_svd_host(hA, hB, Rh, sh, wsh, stream=stream, path=args.path)
+            fg.join_qr_svd_host(hA, hB, Rh, sh, wsh, stream=stream, path=args.path, flags=sig_flags)
         stream.synchronize()
         e_ms = []
         for _ in range(max(3, min(args.steps, 10))):
             s0.record(stream)
-            fg.join_qr_svd_host(hA, hB, Rh, sh, wsh, stream=stream, path=args.path)
+            fg.join_qr_svd_host(hA, hB, Rh, sh, wsh, stream=stream, path=args.path, flags=sig_flags)
             s1.record(stream)
             s1.synchronize()
             e_ms.append(s0.elapsed_time(s1))
@@ -620,7 +620,7 @@ def main():
             pa, pb = np.argsort(A.key, kind="stable"), np.argsort(B.key, kind="stable")
             sA = (torch.from_numpy(np.ascontiguousarray(A.x[pa])).to(dev), torch.from_numpy(A.key[pa]).to(dev))
             sB = (torch.from_numpy(np.ascontiguousarray(B.x[pb])).to(dev), torch.from_numpy(B.key[pb]).to(dev))
-            sp = fg.Solver(sA, sB, path=args.path, flags=fg.FLAG_PRESORTED)
+            sp = fg.Solver(sA, sB, path=args.path, flags=fg.FLAG_PRESORTED | sig_flags)
             with torch.cuda.stream(stream):
                 for _ in range(3):
                     sp(sA, sB, stream=stream)

@@ -143,10 +143,16 @@ enum {
    * Householder bidiagonalisation and dqds (Section 3 names this
    * square-root-free method for the case where only the singular values are
    * wanted; see figaro_triangular_singular_values) instead of one-sided
-   * Jacobi.  FP64 on both paths.  Widths n1 + n2 <= 128 (wider joins return
-   * FIGARO_ERR_UNSUPPORTED); figaro_join_svd, which needs the rotations,
-   * returns FIGARO_ERR_UNSUPPORTED with it.  figaro_info.jacobi_sweeps then
-   * counts dqds transforms; FIGARO_ERR_NO_CONVERGENCE means dqds ran out of
+   * Jacobi.  Up to 128 columns the FP64 path bidiagonalises in FP64 and runs
+   * dqds in float-float, the mixed path runs both in FP32 (normwise error of
+   * order 2^-24 ||R||, no per-value relative accuracy for graded spectra);
+   * wider joins (up to 512) take the FP64 / float-float form in one CTA on
+   * either path, much slower than the block Jacobi.  Householder
+   * bidiagonalisation keeps the values to absolute accuracy (of order
+   * n u ||R||), not to the relative accuracy one-sided Jacobi reaches on
+   * column-graded R.  figaro_join_svd, which needs the rotations, returns
+   * FIGARO_ERR_UNSUPPORTED with it.  figaro_info.jacobi_sweeps then counts
+   * dqds transforms; FIGARO_ERR_NO_CONVERGENCE means dqds ran out of
    * transforms (30 n + 64) and sigma holds its current estimates.           */
   FIGARO_FLAG_SIGMA_DQDS = 1 << 6
 };

@@ -371,7 +371,8 @@ def join_qr_svd_host(A, B, R_out, sigma_out, workspace, stream=None, **opts):
     status of the enqueue; synchronise the stream before reading outputs."""
     lib = library()
     ta, tb = _host_table(*A), _host_table(*B)
-    o = _options(flags=FLAG_HOST_OUTPUT, **opts)
+    flags = FLAG_HOST_OUTPUT | opts.pop("flags", 0)
+    o = _options(flags=flags, **opts)
     n = ta.n + tb.n
     rptr = R_out.data_ptr() if hasattr(R_out, "data_ptr") else R_out.ctypes.data
     sptr = sigma_out.data_ptr() if hasattr(sigma_out, "data_ptr") else sigma_out.ctypes.data

@@ -270,7 +270,6 @@ figaro_status check_pair(const figaro_table* A, const figaro_table* B, const fig
   const int64_t n = static_cast<int64_t>(A->n) + B->n;
   if (n > kMaxWideWidth || (n > kMaxWidth && (A->n > kMaxTableWidth || B->n > kMaxTableWidth)))
     return FIGARO_ERR_UNSUPPORTED;
-  if (o && (o->flags & FIGARO_FLAG_SIGMA_DQDS) && n > kMaxWidth) return FIGARO_ERR_UNSUPPORTED;
   return FIGARO_OK;
 }
 

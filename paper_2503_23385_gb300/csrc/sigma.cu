@@ -155,8 +155,12 @@ __device__ __forceinline__ T sig_block_sum(T v, T* red) {
 }
 
 // Threads per output of a column or row sum over `len` outputs: the block
-// splits into S = kSigThreads / C slices of C >= len outputs each.
-__device__ __forceinline__ int sig_width(int len) { return len <= 32 ? 32 : (len <= 64 ? 64 : 128); }
+// splits into S = kSigThreads / C slices of C >= len outputs each; beyond
+// 128 outputs C = kSigThreads (S = 1) and each thread sums whole columns or
+// rows c, c + C, ...
+__device__ __forceinline__ int sig_width(int len) {
+  return len <= 32 ? 32 : (len <= 64 ? 64 : (len <= 128 ? 128 : kSigThreads));
+}
 
 // Householder bidiagonalisation of the n x n matrix A (row-major, stride lda,
 // shared memory; overwritten).  Writes q[k] = d_k^2 and e[k] = f_k^2 (k < n-1)
@@ -177,21 +181,32 @@ __device__ void sig_bidiagonalise(T* A, int lda, int n, T* q, T* e, T* w, T* par
       const T v0 = x0 - dk;  // v = x - d_k e_1; H = I - beta v v^T
       const T beta = T(-1) / (dk * v0);
       const int len = n - k - 1, C = sig_width(len), S = kSigThreads / C;
-      const int c = tid % C, s = tid / C, j = k + 1 + c;
+      const int c = tid % C, s = tid / C;
       // w_j = beta v^T A[k:, j]
-      T acc = T(0);
-      if (j < n)
-        for (int i = k + s; i < n; i += S) acc += (i == k ? v0 : A[i * lda + k]) * A[i * lda + j];
-      part[s * C + c] = acc;
-      __syncthreads();
-      if (tid < len) {
-        T t = T(0);
-        for (int u = 0; u < S; ++u) t += part[u * C + tid];
-        w[tid] = beta * t;
+      if (S > 1) {
+        const int j = k + 1 + c;
+        T acc = T(0);
+        if (j < n)
+          for (int i = k + s; i < n; i += S) acc += (i == k ? v0 : A[i * lda + k]) * A[i * lda + j];
+        part[s * C + c] = acc;
+        __syncthreads();
+        if (tid < len) {
+          T t = T(0);
+          for (int u = 0; u < S; ++u) t += part[u * C + tid];
+          w[tid] = beta * t;
+        }
+        __syncthreads();
+      } else {  // whole columns: each thread updates only the columns it summed
+        for (int cc = c; cc < len; cc += C) {
+          const int j = k + 1 + cc;
+          T acc = T(0);
+          for (int i = k; i < n; ++i) acc += (i == k ? v0 : A[i * lda + k]) * A[i * lda + j];
+          w[cc] = beta * acc;
+        }
       }
-      __syncthreads();
-      if (j < n) {
-        const T wj = w[c];
+      for (int cc = c; cc < len; cc += C) {
+        const int j = k + 1 + cc;
+        const T wj = w[cc];
         for (int i = k + s; i < n; i += S) A[i * lda + j] -= (i == k ? v0 : A[i * lda + k]) * wj;
       }
       __syncthreads();
@@ -211,26 +226,34 @@ __device__ void sig_bidiagonalise(T* A, int lda, int n, T* q, T* e, T* w, T* par
       const T u0 = y0 - fk;
       const T beta = T(-1) / (fk * u0);
       const int len = n - k - 1, C = sig_width(len), S = kSigThreads / C;
-      const int r = tid % C, s = tid / C, i = k + 1 + r;
+      const int r = tid % C, s = tid / C;
       // z_i = beta A[i, k+1:] u
-      T acc = T(0);
-      if (i < n)
-        for (int j = k + 1 + s; j < n; j += S) acc += A[i * lda + j] * (j == k + 1 ? u0 : A[k * lda + j]);
-      part[s * C + r] = acc;
-      __syncthreads();
-      if (tid < len) {
-        T t = T(0);
-        for (int u = 0; u < S; ++u) t += part[u * C + tid];
-        w[tid] = beta * t;
+      if (S > 1) {
+        const int i = k + 1 + r;
+        T acc = T(0);
+        if (i < n)
+          for (int j = k + 1 + s; j < n; j += S) acc += A[i * lda + j] * (j == k + 1 ? u0 : A[k * lda + j]);
+        part[s * C + r] = acc;
+        __syncthreads();
+        if (tid < len) {
+          T t = T(0);
+          for (int u = 0; u < S; ++u) t += part[u * C + tid];
+          w[tid] = beta * t;
+        }
+      } else {  // whole rows
+        for (int rr = r; rr < len; rr += C) {
+          const int i = k + 1 + rr;
+          T acc = T(0);
+          for (int j = k + 1; j < n; ++j) acc += A[i * lda + j] * (j == k + 1 ? u0 : A[k * lda + j]);
+          w[rr] = beta * acc;
+        }
       }
       __syncthreads();
-      // A[k+1:, k+1:] -= z u^T: thread (c, s) walks column k+1+c over the rows of slice s
-      {
-        const int c = tid % C, j = k + 1 + c;
-        if (j < n) {
-          const T uj = j == k + 1 ? u0 : A[k * lda + j];
-          for (int ii = k + 1 + s; ii < n; ii += S) A[ii * lda + j] -= w[ii - k - 1] * uj;
-        }
+      // A[k+1:, k+1:] -= z u^T: thread (c, s) walks columns k+1+c, k+1+c+C, ... over the rows of slice s
+      for (int cc = r; cc < len; cc += C) {
+        const int j = k + 1 + cc;
+        const T uj = j == k + 1 ? u0 : A[k * lda + j];
+        for (int ii = k + 1 + s; ii < n; ii += S) A[ii * lda + j] -= w[ii - k - 1] * uj;
       }
       __syncthreads();
     }
@@ -374,9 +397,11 @@ __device__ int sig_dqds(typename Num::T* q, typename Num::T* e, int n, double* l
 // (kSigThreads T), red (2 kSigWarps T), qq / ee (n Num::T each), lam (n
 // doubles), stk (3 n doubles).  The FP32 form needs half the bytes of the
 // accurate one, so more CTAs share an SM in a batch.
+// The wide form (n > 128) keeps the matrix and the candidates in global
+// scratch and only the rest in shared memory.
 template <typename T, typename NT>
-__host__ __device__ constexpr size_t sig_smem_bytes(int n) {
-  return sig_region_bytes<T, NT>(n) + sig_al8(sizeof(T) * (3 * n + kSigThreads + 2 * kSigWarps)) +
+__host__ __device__ constexpr size_t sig_smem_bytes(int n, bool wide = false) {
+  return (wide ? 0 : sig_region_bytes<T, NT>(n)) + sig_al8(sizeof(T) * (3 * n + kSigThreads + 2 * kSigWarps)) +
          sig_al8(sizeof(NT) * 2 * n) + sizeof(double) * 4 * n;
 }
 
@@ -385,16 +410,19 @@ __host__ __device__ constexpr size_t sig_smem_bytes(int n) {
 // descending.  T: arithmetic of the bidiagonalisation, Num: of dqds.
 // *count_out (if not null) receives the number of dqds transforms, or -1
 // when dqds stopped early or R holds NaN or Inf (then also
-// kStatusNoConvergence in *status, if not null).
+// kStatusNoConvergence in *status, if not null).  gA (n x n T) and gcand
+// (2 kCand n NT), both global, hold the matrix and the candidates when not
+// null (the wide form); else both live in shared memory.
 template <typename T, typename Num>
 __device__ void sigma_dqds_body(const double* R, int64_t ldr, int n, double* sigma, int32_t* status,
-                                int32_t* count_out) {
+                                int32_t* count_out, T* gA = nullptr, typename Num::T* gcand = nullptr) {
   using NT = typename Num::T;
   extern __shared__ __align__(16) double sig_sm[];
-  const int lda = sig_lda(n);
+  const bool wide = gA != nullptr;
+  const int lda = wide ? n : sig_lda(n);
   char* base = reinterpret_cast<char*>(sig_sm);
-  T* A = reinterpret_cast<T*>(base);
-  char* p1 = base + sig_region_bytes<T, NT>(n);
+  T* A = wide ? gA : reinterpret_cast<T*>(base);
+  char* p1 = base + (wide ? 0 : sig_region_bytes<T, NT>(n));
   T* q = reinterpret_cast<T*>(p1);
   T* e = q + n;
   T* w = e + n;
@@ -425,7 +453,8 @@ __device__ void sigma_dqds_body(const double* R, int64_t ldr, int n, double* sig
     return;
   }
   for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  double* wmax = sig_sm;  // kSigWarps doubles at the start of the matrix region (>= 264 bytes)
+  // kSigWarps doubles: the start of the matrix region (>= 264 bytes), or part (wide form, T = double)
+  double* wmax = wide ? reinterpret_cast<double*>(part) : sig_sm;
   if ((tid & 31) == 0) wmax[tid >> 5] = amax;
   __syncthreads();
   amax = 0.0;
@@ -451,7 +480,7 @@ __device__ void sigma_dqds_body(const double* R, int64_t ldr, int n, double* sig
     if (i < n - 1) ee[i] = Num::from(static_cast<double>(e[i]));
   }
   __syncwarp();
-  NT* cq = reinterpret_cast<NT*>(base);
+  NT* cq = wide ? gcand : reinterpret_cast<NT*>(base);
   const int res = sig_dqds<Num>(qq, ee, n, lam, cq, cq + kCand * n, stk);
   // descending order: rank of each value among all (ties by index)
   const double unscale = ldexp(1.0, ex);
@@ -475,6 +504,14 @@ __global__ void __launch_bounds__(kSigThreads) sigma_dqds_kernel(const double* R
                                                                  int32_t* status, int32_t* count_out) {
   pdl_enter();
   sigma_dqds_body<T, Num>(R, ldr, n, sigma, status, count_out);
+}
+
+// n in (128, 512]: one CTA, the matrix and candidates in global scratch (accurate form on both paths)
+__global__ void __launch_bounds__(kSigThreads) sigma_dqds_wide_kernel(const double* R, int64_t ldr, int n,
+                                                                      double* sigma, int32_t* status,
+                                                                      int32_t* count_out, double* gA, FF* gcand) {
+  pdl_enter();
+  sigma_dqds_body<double, FFNum>(R, ldr, n, sigma, status, count_out, gA, gcand);
 }
 
 // count matrices R + b * stride, sigma + b * n, info[b] (accurate form)
@@ -502,6 +539,18 @@ size_t sigma_dqds_smem(int n, int mixed) {
 int sigma_dqds_threads() { return kSigThreads; }
 
 cudaError_t launch_sigma_dqds(const Plan& p, const double* R, int64_t ldr, double* sigma, cudaStream_t s) {
+  if (p.n > kMaxWidth) {
+    // the factorisation's n x n scratch is free by now: G1 holds the matrix
+    // (n^2 doubles), G2 the candidates (2 kCand n float-float pairs <= n^2 doubles)
+    const size_t smem = sig_smem_bytes<double, FF>(p.n, true);
+    cudaError_t err = cudaFuncSetAttribute(sigma_dqds_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    err = pdl_launch(sigma_dqds_wide_kernel, 1, kSigThreads, smem, s, R, ldr, p.n, sigma, &p.hdr->status,
+                     &p.hdr->jacobi_sweeps, p.G1, reinterpret_cast<FF*>(p.G2));
+    count_launches(1);
+    return err != cudaSuccess ? err : cudaGetLastError();
+  }
   const size_t smem = sigma_dqds_smem(p.n, p.mixed);
   auto kern = p.mixed ? sigma_dqds_kernel<float, F32Num> : sigma_dqds_kernel<double, FFNum>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
