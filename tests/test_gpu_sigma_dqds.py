@@ -163,7 +163,8 @@ def test_join_flag_matches_oracle(fg, torch, path, shape):
 @pytest.mark.gpu
 def test_batch_flag_matches_single_calls(fg, torch):
     pairs, refs = [], []
-    for i, (n1, n2) in enumerate([(4, 4), (16, 16), (30, 34), (8, 24)]):
+    # (100, 100): a wide instance, which the batch runs as a call of its own (the wide form)
+    for i, (n1, n2) in enumerate([(4, 4), (16, 16), (30, 34), (8, 24), (100, 100)]):
         A, B = make_pair(3000 + 500 * i, n1, 2500 + 300 * i, n2, 50 + 10 * i, np.float32, "normal", seed=4200 + i)
         refs.append(oracle.join_r_sigma(A.x, A.key, B.x, B.key, route="reduced")[1])
         pairs.append(tuple((torch.from_numpy(np.ascontiguousarray(T.x)).cuda(),
@@ -172,8 +173,9 @@ def test_batch_flag_matches_single_calls(fg, torch):
     for (R, s), sref in zip(outs, refs):
         s = s.cpu().numpy()
         assert np.linalg.norm(s - sref) / np.linalg.norm(sref) <= 1e-6
-        s2, _ = fg.triangular_singular_values(R)
-        assert np.max(np.abs(s - s2.cpu().numpy())) <= 1e-6 * s[0]  # FP32 stages on the mixed path
+        if len(s) <= 128:  # the direct call's limit
+            s2, _ = fg.triangular_singular_values(R)
+            assert np.max(np.abs(s - s2.cpu().numpy())) <= 1e-6 * s[0]  # FP32 stages on the mixed path
 
 
 @pytest.mark.gpu
