@@ -93,6 +93,9 @@ def test_c1_full_size(fg, torch):
         assert rel(R, Rref) <= TOL[path] and rel(s, sref) <= TOL[path], (path, rel(R, Rref), rel(s, sref))
         Rg, sg = graph_call(fg, torch, a, b, path)
         assert np.array_equal(Rg, R) and np.array_equal(sg, s), path
+        # sigma by bidiagonalisation and dqds on the same join
+        _, sd = fg.join_qr_svd(a, b, path=path, flags=fg.FLAG_SIGMA_DQDS)
+        assert rel(sd.cpu().numpy(), sref) <= TOL[path], (path, "dqds", rel(sd.cpu().numpy(), sref))
 
 
 def test_c2_full_size_zipf(fg, torch):
@@ -105,6 +108,8 @@ def test_c2_full_size_zipf(fg, torch):
         R, s = fg.join_qr_svd(a, b, path=path)
         R, s = R.cpu().numpy(), s.cpu().numpy()
         assert rel(R, Rref) <= TOL[path] and rel(s, sref) <= TOL[path], (path, rel(R, Rref), rel(s, sref))
+        _, sd = fg.join_qr_svd(a, b, path=path, flags=fg.FLAG_SIGMA_DQDS)
+        assert rel(sd.cpu().numpy(), sref) <= TOL[path], (path, "dqds", rel(sd.cpu().numpy(), sref))
 
 
 def test_c3_128_uncapped_instances(fg, torch):
@@ -120,3 +125,8 @@ def test_c3_128_uncapped_instances(fg, torch):
             eR, es = rel(R.cpu().numpy(), Rref), rel(s.cpu().numpy(), sref)
             worst = max(worst, eR, es)
         assert worst <= TOL[path], (path, worst)
+        # the batch with sigma by bidiagonalisation and dqds
+        outs, ws = fg.batch_join(pairs, path=path, flags=fg.FLAG_SIGMA_DQDS)
+        torch.cuda.synchronize()
+        worst = max(rel(s.cpu().numpy(), sref) for (_, sref), (_, s) in zip(refs, outs))
+        assert worst <= TOL[path], (path, "dqds", worst)
