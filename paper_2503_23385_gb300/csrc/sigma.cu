@@ -262,6 +262,64 @@ __device__ void sig_bidiagonalise(T* A, int lda, int n, T* q, T* e, T* w, T* par
   __syncthreads();
 }
 
+// The same reflections for n <= 32 in warp 0 alone (no block barriers):
+// lane j owns column j for the column sums and updates and row j for the
+// row sums; the matrix stays in shared memory.
+template <typename T>
+__device__ void sig_bidiagonalise_warp(T* A, int lda, int n, T* q, T* e, T* w) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < n; ++k) {
+    // ---- left reflection: x = A[k:, k] -> (d_k, 0, ..., 0)
+    T p = lane > k && lane < n ? A[lane * lda + k] * A[lane * lda + k] : T(0);
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    const T x0 = A[k * lda + k];
+    T dk = x0;
+    if (p > T(0) && k + 1 < n) {
+      const T alpha = sqrt(x0 * x0 + p);
+      dk = x0 >= T(0) ? -alpha : alpha;
+      const T v0 = x0 - dk;
+      const T beta = T(-1) / (dk * v0);
+      const int j = lane;
+      if (j > k && j < n) {
+        T acc = v0 * A[k * lda + j];
+        for (int i = k + 1; i < n; ++i) acc += A[i * lda + k] * A[i * lda + j];
+        const T wj = beta * acc;
+        A[k * lda + j] -= v0 * wj;
+        for (int i = k + 1; i < n; ++i) A[i * lda + j] -= A[i * lda + k] * wj;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) q[k] = dk * dk;
+    if (k + 1 >= n) break;
+    // ---- right reflection: y = A[k, k+1:] -> (f_k, 0, ..., 0)
+    p = lane > k + 1 && lane < n ? A[k * lda + lane] * A[k * lda + lane] : T(0);
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    const T y0 = A[k * lda + k + 1];
+    T fk = y0;
+    if (p > T(0)) {
+      const T alpha = sqrt(y0 * y0 + p);
+      fk = y0 >= T(0) ? -alpha : alpha;
+      const T u0 = y0 - fk;
+      const T beta = T(-1) / (fk * u0);
+      if (lane > k && lane < n) {  // z_i = beta A[i, k+1:] u, row i = lane
+        const int i = lane;
+        T acc = A[i * lda + k + 1] * u0;
+        for (int j = k + 2; j < n; ++j) acc += A[i * lda + j] * A[k * lda + j];
+        w[i] = beta * acc;
+      }
+      __syncwarp();
+      if (lane > k && lane < n) {  // column j = lane: A[k+1:, j] -= z u_j
+        const int j = lane;
+        const T uj = j == k + 1 ? u0 : A[k * lda + j];
+        for (int i = k + 1; i < n; ++i) A[i * lda + j] -= w[i] * uj;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) e[k] = fk * fk;
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------------- dqds --
 
 // dqds on q[0..n-1], e[0..n-2] (warp 0; every lane holds the same scalar
@@ -473,8 +531,13 @@ __device__ void sigma_dqds_body(const double* R, int64_t ldr, int n, double* sig
     A[i * lda + j] = static_cast<T>(j >= i ? R[static_cast<int64_t>(i) * ldr + j] * scale : 0.0);
   }
   __syncthreads();
-  sig_bidiagonalise<T>(A, lda, n, q, e, w, part, red);
-  if (tid >= 32) return;
+  if (n <= 32) {  // warp 0 alone
+    if (tid >= 32) return;
+    sig_bidiagonalise_warp<T>(A, lda, n, q, e, w);
+  } else {
+    sig_bidiagonalise<T>(A, lda, n, q, e, w, part, red);
+    if (tid >= 32) return;
+  }
   for (int i = tid; i < n; i += 32) {
     qq[i] = Num::from(static_cast<double>(q[i]));
     if (i < n - 1) ee[i] = Num::from(static_cast<double>(e[i]));
