@@ -70,6 +70,8 @@ def _load():
     lib.oracle_sign_normalise.argtypes = [_f64p, _int]
     lib.oracle_jacobi_sigma.argtypes = [_f64p, _int, _f64p, _int]
     lib.oracle_jacobi_sigma.restype = _int
+    lib.oracle_jacobi_svd.argtypes = [_f64p, _int, _f64p, _f64p, _int]
+    lib.oracle_jacobi_svd.restype = _int
     lib.oracle_join_rows.argtypes = [_i32p, _i64, _i32p, _i64]
     lib.oracle_join_rows.restype = _i64
     tab = [_f64p, _i64, _int, _i64, _i32p]
@@ -236,6 +238,23 @@ def jacobi_sigma(R, max_sweeps: int = 60):
     if sweeps < 0:
         raise RuntimeError("oracle Jacobi did not converge")
     return s
+
+
+def jacobi_svd(R, max_sweeps: int = 60):
+    """(sigma, V) of a square matrix by one-sided Jacobi with the rotations
+    accumulated: sigma descending, column j of V the unit right singular vector
+    of sigma_j with its largest-magnitude component positive."""
+    lib = _load()
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.float64))
+    n = R.shape[0]
+    if n == 0:
+        return np.zeros(0), np.zeros((0, 0))
+    s = np.zeros(n, dtype=np.float64)
+    V = np.zeros((n, n), dtype=np.float64)
+    sweeps = lib.oracle_jacobi_svd(R, n, s, V, max_sweeps)
+    if sweeps < 0:
+        raise RuntimeError("oracle Jacobi did not converge")
+    return s, V
 
 
 def qr_head(X):

@@ -253,6 +253,102 @@ int oracle_jacobi_sigma(const double* Rin, int n, double* sigma, int max_sweeps)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Singular values and right singular vectors of a square R (Section 1's    */
+/* applications: the SVD of J, e.g. for its principal components; Section 3:*/
+/* J = Q R, so J and R share sigma and V).  The same cyclic one-sided       */
+/* Jacobi as oracle_jacobi_sigma, with every rotation also applied to the    */
+/* columns of V (V starts as I, so R V = U keeps orthogonal columns and      */
+/* sigma_j = ||U_j||).  Output: sigma descending, V row-major (column j the  */
+/* unit right singular vector of sigma_j), each column's largest-magnitude   */
+/* component made positive.  Returns the sweeps, or -1 without convergence.  */
+/* ------------------------------------------------------------------------ */
+int oracle_jacobi_svd(const double* Rin, int n, double* sigma, double* Vout, int max_sweeps) {
+  double* U = (double*)malloc(sizeof(double) * (size_t)n * n); /* column-major */
+  double* V = (double*)malloc(sizeof(double) * (size_t)n * n); /* column-major */
+  int* order = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  double* norm = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      U[(int64_t)j * n + i] = Rin[(int64_t)i * n + j];
+      V[(int64_t)j * n + i] = i == j ? 1.0 : 0.0;
+    }
+  const double tol = (double)n * 1.1102230246251565e-16; /* n * 2^-53 */
+  double fro2 = 0.0;
+  for (int64_t e = 0; e < (int64_t)n * n; ++e) fro2 += U[e] * U[e];
+  const double negligible = tol * tol * fro2;
+  int sweeps = 0, converged = n <= 1;
+  while (!converged && sweeps < max_sweeps) {
+    double off = 0.0;
+    for (int p = 0; p < n - 1; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        double* up = U + (int64_t)p * n;
+        double* uq = U + (int64_t)q * n;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int i = 0; i < n; ++i) {
+          a += up[i] * up[i];
+          b += uq[i] * uq[i];
+          g += up[i] * uq[i];
+        }
+        if (a <= negligible || b <= negligible || g == 0.0) continue;
+        double rel = fabs(g) / sqrt(a * b);
+        if (rel > off) off = rel;
+        if (rel <= tol) continue;
+        double zeta = (b - a) / (2.0 * g);
+        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        double s = c * t;
+        for (int i = 0; i < n; ++i) {
+          double x = up[i], y = uq[i];
+          up[i] = c * x - s * y;
+          uq[i] = s * x + c * y;
+        }
+        if (g_mutation != 8) { /* planted (8): V not rotated */
+          double* vp = V + (int64_t)p * n;
+          double* vq = V + (int64_t)q * n;
+          for (int i = 0; i < n; ++i) {
+            double x = vp[i], y = vq[i];
+            vp[i] = c * x - s * y;
+            vq[i] = s * x + c * y;
+          }
+        }
+      }
+    }
+    ++sweeps;
+    if (off <= tol) converged = 1;
+  }
+  for (int j = 0; j < n; ++j) {
+    double s2 = 0.0;
+    for (int i = 0; i < n; ++i) s2 += U[(int64_t)j * n + i] * U[(int64_t)j * n + i];
+    norm[j] = sqrt(s2);
+    order[j] = j;
+  }
+  /* insertion sort of the column indices by descending norm (stable) */
+  for (int i = 1; i < n; ++i) {
+    int v = order[i];
+    int j = i - 1;
+    while (j >= 0 && norm[order[j]] < norm[v]) {
+      order[j + 1] = order[j];
+      --j;
+    }
+    order[j + 1] = v;
+  }
+  for (int j = 0; j < n; ++j) {
+    const double* vc = V + (int64_t)order[j] * n;
+    sigma[j] = norm[order[j]];
+    int big = 0;
+    for (int i = 1; i < n; ++i)
+      if (fabs(vc[i]) > fabs(vc[big])) big = i;
+    const double sg = vc[big] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < n; ++i) Vout[(int64_t)i * n + j] = sg * vc[i];
+  }
+  free(U);
+  free(V);
+  free(order);
+  free(norm);
+  return converged ? sweeps : -1;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Grouping of both tables (helper used by O1, O2, O3).                      */
 /* ------------------------------------------------------------------------ */
 typedef struct {

@@ -1,5 +1,7 @@
 """figaro_join_svd: sigma and the right singular vectors V of the join,
-against the FP64 oracle (sigma, and V of the oracle's R by LAPACK, J = Q R)."""
+against the FP64 oracle (sigma, and V of the oracle's R by the oracle's
+Jacobi with accumulated rotations, pinned by LAPACK in test_oracle_svd.py;
+J = Q R)."""
 import numpy as np
 import pytest
 
@@ -34,21 +36,14 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def signed(V):
-    """Columns with their largest-magnitude entry positive."""
-    idx = np.argmax(np.abs(V), axis=0)
-    return V * np.sign(V[idx, np.arange(V.shape[1])])
-
-
 @pytest.mark.parametrize("shape", [(3000, 4, 2500, 4, 60), (20000, 16, 15000, 16, 500), (3000, 100, 2000, 60, 40)],
                          ids=["8", "32", "160-wide"])
 def test_svd_matches_oracle(fg, torch, shape):
     m1, n1, m2, n2, keys = shape
     A, B = make_pair(m1, n1, m2, n2, keys, np.float32, "normal", seed=900 + n1)
     Rref, sref = oracle.join_r_sigma(A.x, A.key, B.x, B.key, route="reduced")
-    # V of R (right singular vectors of J) by LAPACK on the oracle's R
-    _, sv, Vt = np.linalg.svd(Rref)
-    Vref = signed(Vt.T)
+    # V of R (right singular vectors of J, the largest component of each column positive)
+    sv, Vref = oracle.jacobi_svd(Rref)
     gaps = np.min(np.abs(np.diff(sv)) / sv[0])
     for path in ("fp64", "mixed"):
         s, V, R = fg.join_svd(dev(torch, A), dev(torch, B), path=path)
