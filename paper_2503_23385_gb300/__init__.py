@@ -35,7 +35,7 @@ FLAG_AUTOTUNE = 1 << 2
 FLAG_ALLOW_RANK_DEFICIENT = 1 << 3
 FLAG_SHIFTED_CHOLQR3 = 1 << 4
 FLAG_PRESORTED = 1 << 5
-FLAG_SIGMA_DQDS = 1 << 6
+FLAG_SIGMA_DQDS = 1 << 6  # sigma by bidiagonalisation and dqds instead of one-sided Jacobi
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "WORKSPACE_TOO_SMALL", 3: "CUDA", 4: "NOT_SPD",
                 5: "NO_CONVERGENCE", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED", 8: "RANK_DEFICIENT"}
 

@@ -237,3 +237,15 @@ def test_flag_rejected_where_it_cannot_apply():
     A.ld = B.ld = 8
     assert lib.figaro_join_svd(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), one, one, 16, None, 16, one, 1 << 20,
                                None) == 7
+
+
+def test_binding_rejects_what_the_call_cannot_take():
+    """The Python wrapper refuses CPU tensors, other dtypes and non-square
+    matrices before calling the library (no device needed)."""
+    import torch
+    import paper_2503_23385_gb300 as fg
+    for bad in (torch.zeros((4, 4), dtype=torch.float64),        # host memory
+                torch.zeros((4, 4), dtype=torch.float32),        # not FP64
+                torch.zeros((3, 4, 5), dtype=torch.float64)):    # not square
+        with pytest.raises(fg.FigaroError):
+            fg.triangular_singular_values(bad)
